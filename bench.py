@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 messenger-field Wiener filter.
+
+Workload: HEALPix temperature map, nside 2048 (50,331,648 pixels), lmax 4096,
+CMB-like C_l with a 5' beam, noise dynamic range 1e4 from the hit pattern,
+galactic cut |b| < 15 deg plus 3000 point-source disks of 0.3 deg (synthetic
+stand-in for a Planck-resolution map).  One step = one complete Wiener-filter
+solve (setup, cooling schedule with band-limited transforms, lambda = 1
+iterations down to the residual tolerance, output map) in mixed precision,
+with inputs resident in HBM.
+
+Reported (one JSON line on rank 0):
+  value       messenger iterations per second over the timed solves (all ranks)
+  ms_per_step time to solution of one solve
+  roofline    the dominant kernel (Legendre) against the FP32 ALU peak
+  e2e         the same metric through wf_solve_host (host buffers, copies timed)
+  fp64_path   the plain FP64 GPU path on the same GB300 (full-band iteration
+              rate measured; its time to solution extrapolated from it)
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of one iteration
+
+--impl reference runs the oracle (the only reference implementation there is)
+on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import wf_inputs as gen  # noqa: E402
+
+CFG = {"workload": "healpix_T_nside2048_lmax4096", "nside": 2048, "lmax": 4096, "fwhm_arcmin": 5.0,
+       "noise_range": 1e4, "b_cut_deg": 15.0, "n_disks": 3000, "disk_radius_deg": 0.3}
+METRIC = "messenger iterations/s, full Wiener-filter solve to residual tol (HEALPix nside 2048, lmax 4096)"
+UNIT = "iter/s"
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (GB300)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--nside", type=int, default=CFG["nside"])
+    ap.add_argument("--lmax", type=int, default=CFG["lmax"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_problem(nside, lmax, k):
+    kw = dict(fwhm_arcmin=CFG["fwhm_arcmin"], b_cut_deg=CFG["b_cut_deg"], n_disks=CFG["n_disks"],
+              disk_radius_deg=CFG["disk_radius_deg"], noise_range=CFG["noise_range"])
+    return gen.healpix_problem(nside, lmax, gen.seed_for(3, k), **kw)
+
+
+# --------------------------------------------------------------------------
+# algorithmic work of the Legendre transforms (per full launch)
+# --------------------------------------------------------------------------
+def legendre_triples(nside, L):
+    """(l, m, ring-pair) triples of one Legendre transform at band limit L."""
+    npairs = 2 * nside
+    return npairs * (L + 1) * (L + 2) // 2
+
+
+LEG_FLOPS_PER_TRIPLE = 7  # recurrence (mul + fma = 3 flops) + contraction (2 fma = 4 flops)
+
+
+def peak_fp32_tflops(mhz):
+    return 152 * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------
+# clocks sampling during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "power_w_max": float(max(power)), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle on a bounded sample of one full-band iteration
+# --------------------------------------------------------------------------
+def oracle_iteration_sample(nside, lmax, n_rings=8, n_m=8, seed=0):
+    """Time the oracle's synthesis on n_rings evenly spaced rings and its
+    adjoint on n_m evenly spaced m, both at the full band, and extrapolate to
+    one messenger iteration (one synthesis of every ring + one adjoint of
+    every m; the blends are negligible).  Returns (seconds/iteration, sample
+    description, threads)."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    a = gen.alm_unit_gaussian(rng, lmax) * np.sqrt(gen.cmb_like_cl(lmax, 5.0)[gen.alm_ell(lmax)] + 1e-30)
+    R = 4 * nside - 1
+    rings = np.linspace(0, R - 1, n_rings).round().astype(int)
+    t0 = time.perf_counter()
+    for r in rings:
+        oracle.synthesis(nside, lmax, lmax, a, rings=(int(r), int(r) + 1))
+    t_ring = (time.perf_counter() - t0) / n_rings
+    f = rng.standard_normal(12 * nside * nside)
+    ms = np.linspace(0, lmax, n_m).round().astype(int)
+    t0 = time.perf_counter()
+    for m in ms:
+        oracle.adjoint_synthesis(nside, lmax, lmax, f, ms=(int(m), int(m) + 1))
+    t_m = (time.perf_counter() - t0) / n_m
+    t_iter = t_ring * R + t_m * (lmax + 1)
+    desc = ("oracle synthesis of %d evenly spaced rings and adjoint of %d evenly spaced m at nside %d, lmax %d, "
+            "extrapolated to one full-band iteration (%d rings, %d m)" % (n_rings, n_m, nside, lmax, R, lmax + 1))
+    return t_iter, desc, oracle.num_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle  # noqa: F401  (builds the C core if needed)
+
+    for _ in range(args.warmup):
+        oracle_iteration_sample(args.nside, args.lmax, n_rings=2, n_m=2)
+    ts = []
+    desc, thr = "", 1
+    for k in range(args.steps):
+        t, desc, thr = oracle_iteration_sample(args.nside, args.lmax, n_rings=4, n_m=4, seed=k)
+        ts.append(t)
+    t = float(np.mean(ts))
+    v = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CFG["workload"], "nside": args.nside, "lmax": args.lmax,
+                       "implementation": "FP64 CPU oracle (direct Legendre and Fourier sums), per-iteration rate"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_1210_4931_gb300 as wf
+
+    wf.load()
+    nside, lmax = args.nside, args.lmax
+    P = make_problem(nside, lmax, rank)
+    stream = torch.cuda.current_stream()
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=args.precision)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    # data = signal (synthesised by the library's own basis change) + noise
+    a_sig = T(P["a_signal"])
+    s_sig = torch.empty(plan.npix, dtype=torch.float64, device=dev)
+    wf.wf_alm2map(plan, a_sig, lmax, s_sig)
+    d = s_sig + T(P["noise"])
+    nv, mask, cl = T(P["noise_var"]), T(P["mask"]), T(P["c_ell"])
+    s_out = torch.empty(plan.npix, dtype=torch.float64, device=dev)
+    alm_out = torch.empty(plan.nalm, dtype=torch.complex128, device=dev)
+    wf.wf_set_options(plan, profile=1)
+    cap = 40000
+
+    def solve():
+        return wf.wf_solve(plan, d, nv, mask, cl, args.tol, s_out, alm_out, trace_cap=cap)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    reps = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        reps.append(solve())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop()
+    t_ms = e0.elapsed_time(e1)
+    iters = sum(r["iters"] for r in reps)
+    if ws > 1:
+        tt = torch.tensor([t_ms, iters], dtype=torch.float64, device=dev)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
+        t_ms, iters = float(tmax[0]), float(tt[1])
+    value = iters / (t_ms / 1e3)
+    last = reps[-1]
+
+    # per-iteration times (p50/p99) at the full band, lambda = 1
+    full = (last["lambda_trace"] == 1.0) & (last["L_trace"] == lmax)
+    it_ms = np.concatenate([r["iter_ms_trace"][(r["lambda_trace"] == 1.0) & (r["L_trace"] == lmax)] for r in reps])
+    all_ms = np.concatenate([r["iter_ms_trace"] for r in reps])
+
+    # roofline of the dominant kernel: Legendre synthesis + analysis (FP32 ALU)
+    kms = {k: sum(r["kernel_ms"][k] for r in reps) for k in reps[0]["kernel_ms"]}
+    kl = {k: sum(r["kernel_launches"][k] for r in reps) for k in reps[0]["kernel_launches"]}
+    leg_triples = 0
+    for r in reps:
+        for L in r["L_trace"]:
+            leg_triples += 2 * legendre_triples(nside, int(L))  # synthesis + analysis
+    leg_ms = kms["leg_syn"] + kms["leg_ana"]
+    achieved = LEG_FLOPS_PER_TRIPLE * leg_triples / (leg_ms / 1e3) / 1e12
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    peak = peak_fp32_tflops(2070.0)
+    roof = {"bound": "alu", "kernel": "legendre synthesis + analysis (k_legsyn, k_legana)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, see design notes)",
+            "flops_per_triple": LEG_FLOPS_PER_TRIPLE, "kernel_ms": leg_ms,
+            "share_of_step": leg_ms / max(1e-9, sum(kms.values()))}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
+                      "tol": args.tol, "l2": "inputs (1.2 GB) larger than L2", "parallelism": "replicas"},
+           "time_to_tol_s": t_ms / args.steps / 1e3, "iters_per_solve": last["iters"],
+           "final_residual": last["final_residual"], "converged": last["converged"],
+           "chi2_over_ndof": last["chi2_over_ndof"],
+           "iter_ms_full_band": {"p50": float(np.percentile(it_ms, 50)) if it_ms.size else None,
+                                 "p99": float(np.percentile(it_ms, 99)) if it_ms.size else None,
+                                 "n": int(it_ms.size)},
+           "iter_ms_all": {"p50": float(np.percentile(all_ms, 50)), "p99": float(np.percentile(all_ms, 99))},
+           "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "gpu_launches": int(sum(r["launches"] for r in reps)),
+           "roofline": roof, "clocks": ck}
+
+    if rank == 0 and not args.no_e2e:
+        # e2e: host buffers in, host map out, through wf_solve_host
+        dh = d.cpu().numpy()
+        nvh, mh, clh = P["noise_var"], P["mask"], P["c_ell"]
+        sh = np.empty(plan.npix)
+        wf.wf_set_options(plan, profile=0)
+        wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)  # warm
+        t0 = time.perf_counter()
+        rep = wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)
+        te = time.perf_counter() - t0
+        out["e2e"] = {"value": rep["iters"] / te, "unit": UNIT,
+                      "h2d_bytes_per_step": int(dh.nbytes + nvh.nbytes + mh.nbytes + clh.nbytes),
+                      "d2h_bytes_per_step": int(sh.nbytes), "seconds_per_solve": te}
+    plan.close()
+    del plan
+
+    if rank == 0 and not args.no_fp64 and args.precision == "mixed":
+        p64 = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64")
+        wf.wf_set_options(p64, profile=1)
+        nrep = 3
+        wf.wf_set_schedule(p64, [1.0] * nrep, [lmax] * nrep)
+        wf.wf_solve(p64, d, nv, mask, cl, args.tol, s_out, trace_cap=16)  # warm
+        r64 = wf.wf_solve(p64, d, nv, mask, cl, args.tol, s_out, trace_cap=16)
+        ms64 = float(np.mean(r64["iter_ms_trace"][:nrep]))
+        # extrapolate the FP64 time to solution along the mixed solve's own trace
+        Ls = last["L_trace"]
+        cost = float(np.sum((Ls.astype(np.float64) + 1) ** 2) / (lmax + 1) ** 2)
+        out["fp64_path"] = {"iters_per_s_full_band": 1e3 / ms64, "iter_ms_full_band": ms64,
+                            "time_to_tol_s_extrapolated": ms64 * cost / 1e3,
+                            "speedup_mixed_vs_fp64_full_band":
+                                ms64 / out["iter_ms_full_band"]["p50"] if out["iter_ms_full_band"]["p50"] else None,
+                            "note": "FP64 full-band iteration measured (3 iterations, lambda = 1); time to "
+                                    "solution extrapolated along the mixed solve's (lambda, L) trace with cost "
+                                    "proportional to (L+1)^2"}
+        p64.close()
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        t_it, desc, thr = oracle_iteration_sample(nside, lmax, n_rings=8, n_m=8)
+        out["cpu_baseline"] = {"value": 1.0 / t_it, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

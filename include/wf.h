@@ -1,0 +1,180 @@
+/*
+ * wf.h -- C ABI of the GB300 messenger-field Wiener filter.
+ *
+ * Solves the Wiener-filter equation (Elsner & Wandelt 2013, Eq. 2)
+ *     (S^-1 + N^-1) s_WF = N^-1 d
+ * for a signal covariance S that is diagonal in harmonic space and a noise
+ * covariance N that is diagonal in pixel space, by the messenger iteration of
+ * Sect. 2.1 (Eqs. 3-4): a pixel-space blend of the data with the current
+ * signal through an auxiliary field of covariance T = tau 1 (tau = min N),
+ * then a harmonic-space blend with the prior, with the cooling parameter
+ * lambda >= 1 of Sect. 2.2 and Sect. 3.  wf_fluct runs the same iteration on
+ * the source of Eq. (9) to draw fluctuation maps for constrained
+ * realisations (Sect. 2.3).
+ *
+ * Geometries: a periodic flat ny x nx grid with the unitary 2-D DFT, and the
+ * HEALPix RING sphere with spherical harmonics up to lmax (Sect. 3).
+ *
+ * Conventions
+ *   - Pixel maps: FP64, row-major ny x nx (flat) or HEALPix RING order
+ *     (sphere).  mask: uint8 per pixel, 1 = observed, 0 = masked (N^-1 = 0).
+ *   - Harmonic vectors ("alm"), complex FP64 interleaved (re, im):
+ *       flat:    the rfft half plane, ny rows of nx/2+1, row-major, unitary;
+ *       HEALPix: a_lm for m >= 0, m-major: index(l, m) = m(2 lmax+3-m)/2 + l-m,
+ *                Y_lm with the Condon-Shortley phase, orthonormal; a real map
+ *                is f = sum_l [a_l0 Y_l0 + 2 Re sum_{m>0} a_lm Y_lm].
+ *   - Prior: HEALPix C_ell[l], l = 0..lmax (beam included; C_0 = C_1 = 0
+ *     holds those modes at zero).  Flat: S per half-plane mode (ny x nx/2+1).
+ *   - Unless a function says otherwise, every array pointer is a DEVICE
+ *     pointer, owned by the caller, read or written on the plan's stream.
+ *
+ * Errors: functions return a wf_status; nothing throws or aborts across the
+ * ABI.  wf_last_error() gives a human-readable detail for the calling thread.
+ * Calls on one plan must not overlap (a plan holds one solve's workspace);
+ * different plans may be used from different threads.
+ */
+#ifndef WF_H
+#define WF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wf_plan_s *wf_plan; /* opaque; created and owned by the library */
+
+typedef enum {
+    WF_OK = 0,
+    WF_EINVAL = 1,    /* bad argument or input (NaN / negative noise, all pixels masked, ...) */
+    WF_ENOMEM = 2,    /* device or host allocation failed */
+    WF_ECUDA = 3,     /* a CUDA call failed; see wf_last_error() */
+    WF_ENOCONV = 4,   /* iteration cap reached; the last iterate is still written */
+    WF_EDIVERGE = 5,  /* residual grew without bound (see the design notes on HEALPix quadrature) */
+    WF_ETIMEOUT = 6,  /* a bounded device wait gave up */
+    WF_EUNSUPPORTED = 7
+} wf_status;
+
+typedef enum { WF_GEOM_FLAT = 0, WF_GEOM_HEALPIX = 1 } wf_geom_kind;
+
+typedef enum {
+    WF_PREC_FP64 = 0,       /* every step in FP64 */
+    WF_PREC_MIXED_FP32 = 1  /* FP32 Legendre recurrence/contraction and ring FFTs from FP64 seeds;
+                               FP64 a_lm, reductions and residual refinement */
+} wf_precision;
+
+typedef struct {
+    wf_geom_kind kind;
+    int nx, ny;  /* flat only: powers of two, 16 <= n <= 256 */
+    int nside;   /* HEALPix only */
+    int ncomp;   /* 1 (temperature); polarisation is not supported in this version */
+} wf_geometry;
+
+/* Options of the cooling schedule and stopping rule (Sect. 3).  Zero-filled
+ * fields take the defaults shown. */
+typedef struct {
+    int maxiter;        /* total iteration cap (default 20000) */
+    int level_cap;      /* iterations at one lambda level before it is left anyway (200) */
+    double eta;         /* plateau: |chi2_k - chi2_{k-1}| < eta sqrt(2 n_dof) (1e-2) */
+    int ell0;           /* HEALPix: first l_iter (20) */
+    int ell_step_max;   /* HEALPix: largest increase of l_iter per level (500) */
+    int band_margin;    /* HEALPix: transform band limit L = l_iter + margin (100) */
+    double lambda_max;  /* flat: first lambda level (100) */
+    int refine_sweeps;  /* mixed precision: max FP64 correction sweeps (3) */
+    int profile;        /* nonzero: time every kernel family with CUDA events (fills wf_info.kernel_ms) */
+} wf_options;
+
+/* Kernel families reported in wf_info (HEALPix path; the flat path is one
+ * fused kernel, reported under WF_K_FLAT). */
+enum {
+    WF_K_LEG_SYN = 0,   /* Legendre synthesis a_lm -> G_m(theta) */
+    WF_K_RING_SYN = 1,  /* ring fold + inverse ring DFT + pixel blend (Eq. 3) */
+    WF_K_RING_ANA = 2,  /* forward ring DFT + unfold */
+    WF_K_LEG_ANA = 3,   /* Legendre analysis + harmonic blend (Eq. 4) */
+    WF_K_OTHER = 4,     /* setup, reductions, conversions */
+    WF_K_FLAT = 5,      /* fused flat-grid solve */
+    WF_NK = 6
+};
+
+/* Per-solve report.  The trace arrays are optional and caller-owned HOST
+ * memory of trace_cap entries; entry k describes iteration k. */
+typedef struct {
+    int iters;              /* messenger iterations run */
+    int converged;          /* 1 if the residual fell below tol at lambda = 1, full band */
+    double final_residual;  /* relative residual of the last full-band lambda = 1 iteration */
+    double chi2_over_ndof;  /* chi^2(s, 1) / n_dof of the result (Wiener filter only) */
+    long long n_dof;        /* observed pixels */
+    double tau;             /* min noise variance over observed pixels */
+    int n_levels;           /* lambda levels visited */
+    int refine_sweeps;      /* FP64 correction sweeps run (mixed precision) */
+    double *lambda_trace;   /* optional, lambda_k */
+    int *L_trace;           /* optional, band limit L_k (HEALPix; -1 on the flat grid) */
+    double *chi2_trace;     /* optional, chi^2 of the iterate entering iteration k (Eq. 6, x-independent part dropped) */
+    double *resid_trace;    /* optional, relative residual (NaN where lambda > 1 or L < lmax) */
+    double *iter_ms_trace;  /* optional, device time of iteration k in ms (CUDA events; HEALPix) */
+    int trace_cap;
+    long long launches;                 /* kernels this call launched */
+    double kernel_ms[WF_NK];            /* device time per kernel family (wf_options.profile) */
+    long long kernel_launches[WF_NK];   /* launches per kernel family */
+} wf_info;
+
+/* Build a plan for one geometry and band limit (HEALPix lmax <= 2 nside is
+ * the supported range; flat: lmax ignored).  Precomputes the ring geometry,
+ * the Legendre seeds and recurrence tables, the ring-FFT tables and the
+ * workspace.  cuda_stream: a cudaStream_t (NULL = the legacy default stream)
+ * that every later call on this plan uses.  *out receives the plan. */
+wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision p, void *cuda_stream, wf_plan *out);
+void wf_plan_destroy(wf_plan p);
+wf_status wf_set_options(wf_plan p, const wf_options *opt);
+
+/* Replay mode: the next solves run exactly n iterations with lambda[k] and
+ * band limit L[k] (ignored on the flat grid) instead of the cooling schedule,
+ * so that two implementations can be compared iteration for iteration.
+ * Host arrays, copied; n = 0 returns to the schedule. */
+wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n);
+
+/* Wiener filter (Eq. 2) by the messenger iteration.  d, noise_var: n_pix
+ * FP64; mask: n_pix uint8 (may be NULL: all observed); C_ell: prior (see
+ * conventions).  tol: relative residual |(S^-1 + N^-1) s - N^-1 d| / |N^-1 d|
+ * in harmonic coordinates at which to stop.  s_wf: n_pix FP64 output.
+ * alm_out: optional harmonic output.  info: optional report.
+ * Noise variance must be finite and > 0 on observed pixels (WF_EINVAL). */
+wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask,
+                   const double *C_ell, double tol, double *s_wf, double *alm_out, wf_info *info);
+
+/* Same as wf_solve with every array in HOST memory: the library copies the
+ * inputs to the device and the outputs back, inside the call. */
+wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask,
+                        const double *C_ell, double tol, double *s_wf, double *alm_out, wf_info *info);
+
+/* Fluctuation map (Sect. 2.3, Eqs. 8-9): the messenger iteration with the
+ * source N^-1/2 g1 + S^-1/2 g2 (g1: n_pix FP64 unit normal draws; g2: unit
+ * complex normal harmonic draws in the harmonic layout, m = 0 / kx-Hermitian
+ * entries real).  f_out: n_pix FP64 with covariance (S^-1 + N^-1)^-1.
+ * A constrained realisation is s_WF + f_out. */
+wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, const double *C_ell,
+                   const double *g1, const double *g2, double tol, double *f_out, double *alm_out,
+                   wf_info *info);
+
+/* Basis change used by the iteration (Sect. 2.1), exposed for users and for
+ * checking: map = Y a restricted to l <= L (HEALPix) or the unitary inverse
+ * real DFT (flat, L ignored); and its adjoint alm = Y^T map (the analysis
+ * without the pixel area, Omega Y^T being the HEALPix analysis). */
+wf_status wf_alm2map(wf_plan p, const double *alm, int L, double *map);
+wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm);
+
+/* Sizes of the plan's arrays. */
+long long wf_npix(wf_plan p);
+long long wf_nalm(wf_plan p); /* complex entries */
+/* Device bytes the plan holds (tables + workspace). */
+long long wf_plan_device_bytes(wf_plan p);
+
+const char *wf_strerror(wf_status s);
+const char *wf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H */

@@ -119,7 +119,7 @@ def fluct_source(basis, nu, S, g1, g2):
 
 def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
                     replay=None, schedule=None, eta=1e-2, level_cap=200, d=None,
-                    callback=None):
+                    callback=None, a0=None):
     """Run the messenger iteration (Eqs. 3-4) from a = 0.
 
     basis   FlatBasis or HealpixBasis
@@ -130,6 +130,7 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
     replay  optional list of (lam, L) pairs: run exactly these iterations
     schedule  FlatSchedule / HealpixSchedule (built from S if omitted)
     callback  optional f(k, a_new) called after every iteration
+    a0        optional starting harmonic vector (default: zeros, as in Sect. 2.1)
     Leading batch axes on r / nu are allowed on the flat grid (norms and
     chi^2 are then summed over the batch).
 
@@ -154,7 +155,7 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
         else:
             raise ValueError("a HealpixSchedule (built from C_ell) is required")
 
-    a = np.zeros(b.shape, dtype=np.complex128)
+    a = np.zeros(b.shape, dtype=np.complex128) if a0 is None else np.array(a0, dtype=np.complex128)
     trace, chi2s, resids = [], [], []
     converged = False
     prev_chi2 = None

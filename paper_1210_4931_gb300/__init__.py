@@ -1,0 +1,277 @@
+"""Python binding of the GB300 messenger-field Wiener filter (include/wf.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library
+``libwf.so`` built from ``csrc/``.  There is no CPU fallback: importing this
+package without the built library raises.
+
+Device arrays are torch CUDA tensors (FP64 maps and harmonic vectors as
+complex128 or as float64 views with a trailing re/im axis, uint8 masks); the
+functions take the same arguments, in the same order, as the C functions.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwf.so")
+
+WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ENOCONV, WF_EDIVERGE, WF_ETIMEOUT, WF_EUNSUPPORTED = range(8)
+WF_GEOM_FLAT, WF_GEOM_HEALPIX = 0, 1
+WF_PREC_FP64, WF_PREC_MIXED_FP32 = 0, 1
+PRECISIONS = {"fp64": WF_PREC_FP64, "mixed": WF_PREC_MIXED_FP32, "fp32": WF_PREC_MIXED_FP32}
+
+
+class WfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (msg, status, last_error()))
+        self.status = status
+
+
+class wf_geometry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nside", ctypes.c_int), ("ncomp", ctypes.c_int)]
+
+
+class wf_options(ctypes.Structure):
+    _fields_ = [("maxiter", ctypes.c_int), ("level_cap", ctypes.c_int), ("eta", ctypes.c_double),
+                ("ell0", ctypes.c_int), ("ell_step_max", ctypes.c_int), ("band_margin", ctypes.c_int),
+                ("lambda_max", ctypes.c_double), ("refine_sweeps", ctypes.c_int), ("profile", ctypes.c_int)]
+
+
+class wf_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("final_residual", ctypes.c_double),
+                ("chi2_over_ndof", ctypes.c_double), ("n_dof", ctypes.c_longlong), ("tau", ctypes.c_double),
+                ("n_levels", ctypes.c_int), ("refine_sweeps", ctypes.c_int),
+                ("lambda_trace", ctypes.POINTER(ctypes.c_double)), ("L_trace", ctypes.POINTER(ctypes.c_int)),
+                ("chi2_trace", ctypes.POINTER(ctypes.c_double)), ("resid_trace", ctypes.POINTER(ctypes.c_double)),
+                ("iter_ms_trace", ctypes.POINTER(ctypes.c_double)), ("trace_cap", ctypes.c_int),
+                ("launches", ctypes.c_longlong), ("kernel_ms", ctypes.c_double * 6),
+                ("kernel_launches", ctypes.c_longlong * 6)]
+
+
+KERNEL_FAMILIES = ["leg_syn", "ring_syn", "ring_ana", "leg_ana", "other", "flat"]
+
+
+_lib = None
+EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host",
+           "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
+           "wf_strerror", "wf_last_error"]
+
+
+def load(path: str = LIB_PATH):
+    """Load libwf.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libwf.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    vp, dp, u8p = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+    L.wf_plan_create.argtypes = [ctypes.POINTER(wf_geometry), ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.wf_plan_destroy.argtypes = [vp]
+    L.wf_plan_destroy.restype = None
+    L.wf_set_options.argtypes = [vp, ctypes.POINTER(wf_options)]
+    L.wf_set_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    sig = [vp, dp, dp, u8p, dp, ctypes.c_double, dp, dp, ctypes.POINTER(wf_info)]
+    L.wf_solve.argtypes = sig
+    L.wf_solve_host.argtypes = sig
+    L.wf_fluct.argtypes = [vp, dp, u8p, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.POINTER(wf_info)]
+    L.wf_alm2map.argtypes = [vp, dp, ctypes.c_int, dp]
+    L.wf_map2alm_adjoint.argtypes = [vp, dp, ctypes.c_int, dp]
+    for f in ("wf_npix", "wf_nalm", "wf_plan_device_bytes"):
+        getattr(L, f).argtypes = [vp]
+        getattr(L, f).restype = ctypes.c_longlong
+    L.wf_strerror.argtypes = [ctypes.c_int]
+    L.wf_strerror.restype = ctypes.c_char_p
+    L.wf_last_error.argtypes = []
+    L.wf_last_error.restype = ctypes.c_char_p
+    for f in ("wf_plan_create", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "wf_fluct",
+              "wf_alm2map", "wf_map2alm_adjoint"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return (_lib.wf_last_error() or b"").decode() if _lib is not None else ""
+
+
+def _ptr(t, dtype=None, n=None, what="array"):
+    """Device pointer of a contiguous torch CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA torch tensor" % what)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if dtype is not None and t.dtype not in dtype:
+        raise TypeError("%s has dtype %s" % (what, t.dtype))
+    if n is not None and t.numel() * t.element_size() < n:
+        raise ValueError("%s is too small (%d bytes, need %d)" % (what, t.numel() * t.element_size(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owns one wf_plan (freed on close / garbage collection)."""
+
+    def __init__(self, handle, geometry, lmax, precision):
+        self.handle = handle
+        self.geometry = geometry
+        self.lmax = lmax
+        self.precision = precision
+        self.npix = int(load().wf_npix(handle))
+        self.nalm = int(load().wf_nalm(handle))
+
+    @property
+    def device_bytes(self):
+        return int(load().wf_plan_device_bytes(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().wf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check(st, what, allow=()):
+    if st != WF_OK and st not in allow:
+        raise WfError(st, what)
+    return st
+
+
+def wf_plan_create(kind: str, *, nside: int = 0, lmax: int = 0, n: int = 0, precision: str = "fp64",
+                   stream=None) -> Plan:
+    """kind 'healpix' (nside, lmax) or 'flat' (n x n).  stream: torch
+    CUDA stream (default: the current stream)."""
+    import torch
+
+    L = load()
+    g = wf_geometry()
+    g.kind = WF_GEOM_HEALPIX if kind == "healpix" else WF_GEOM_FLAT
+    g.nside, g.nx, g.ny, g.ncomp = nside, n, n, 1
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p()
+    _check(L.wf_plan_create(ctypes.byref(g), lmax, PRECISIONS[precision], ctypes.c_void_p(stream.cuda_stream),
+                            ctypes.byref(h)), "wf_plan_create")
+    return Plan(h, {"kind": kind, "nside": nside, "n": n}, lmax, precision)
+
+
+def wf_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def wf_set_options(plan: Plan, **kw):
+    o = wf_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    _check(load().wf_set_options(plan.handle, ctypes.byref(o)), "wf_set_options")
+
+
+def wf_set_schedule(plan: Plan, lam, L=None):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    n = lam.size
+    Lp = None
+    if L is not None:
+        Larr = np.ascontiguousarray(L, dtype=np.int32)
+        Lp = Larr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    _check(load().wf_set_schedule(plan.handle, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), Lp, n),
+           "wf_set_schedule")
+
+
+def _info(cap):
+    info = wf_info()
+    bufs = {}
+    if cap:
+        bufs = {"lambda": np.full(cap, np.nan), "L": np.full(cap, -1, dtype=np.int32),
+                "chi2": np.full(cap, np.nan), "resid": np.full(cap, np.nan), "iter_ms": np.full(cap, np.nan)}
+        info.iter_ms_trace = bufs["iter_ms"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        info.lambda_trace = bufs["lambda"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        info.L_trace = bufs["L"].ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        info.chi2_trace = bufs["chi2"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        info.resid_trace = bufs["resid"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        info.trace_cap = cap
+    return info, bufs
+
+
+def _info_dict(st, info, bufs):
+    k = info.iters
+    out = {"status": st, "iters": k, "converged": bool(info.converged), "final_residual": info.final_residual,
+           "chi2_over_ndof": info.chi2_over_ndof, "n_dof": info.n_dof, "tau": info.tau,
+           "n_levels": info.n_levels, "refine_sweeps": info.refine_sweeps, "launches": info.launches,
+           "kernel_ms": {f: info.kernel_ms[i] for i, f in enumerate(KERNEL_FAMILIES)},
+           "kernel_launches": {f: info.kernel_launches[i] for i, f in enumerate(KERNEL_FAMILIES)}}
+    for key, v in bufs.items():
+        out[key + "_trace"] = v[: min(k, v.size)].copy()
+    return out
+
+
+def _f64(t):
+    import torch
+
+    return (torch.float64, torch.complex128)
+
+
+def wf_solve(plan: Plan, d, noise_var, mask, C_ell, tol, s_wf, alm_out=None, trace_cap=0) -> dict:
+    """Wiener filter; returns the report as a dict (status WF_OK or
+    WF_ENOCONV; other statuses raise)."""
+    info, bufs = _info(trace_cap)
+    n8 = plan.npix * 8
+    st = load().wf_solve(plan.handle, _ptr(d, _f64(d), n8, "d"), _ptr(noise_var, _f64(d), n8, "noise_var"),
+                         _ptr(mask, None, plan.npix, "mask"), _ptr(C_ell, _f64(d), None, "C_ell"), float(tol),
+                         _ptr(s_wf, _f64(d), n8, "s_wf"), _ptr(alm_out, _f64(d), plan.nalm * 16, "alm_out"),
+                         ctypes.byref(info))
+    _check(st, "wf_solve", allow=(WF_ENOCONV,))
+    return _info_dict(st, info, bufs)
+
+
+def wf_solve_host(plan: Plan, d, noise_var, mask, C_ell, tol, s_wf, alm_out=None, trace_cap=0) -> dict:
+    """wf_solve on host numpy arrays; the library copies in and out."""
+    info, bufs = _info(trace_cap)
+
+    def hp(a, dt):
+        if a is None:
+            return None
+        assert a.dtype == dt and a.flags.c_contiguous
+        return ctypes.c_void_p(a.ctypes.data)
+
+    st = load().wf_solve_host(plan.handle, hp(d, np.float64), hp(noise_var, np.float64), hp(mask, np.uint8),
+                              hp(C_ell, np.float64), float(tol), hp(s_wf, np.float64),
+                              hp(alm_out, np.complex128), ctypes.byref(info))
+    _check(st, "wf_solve_host", allow=(WF_ENOCONV,))
+    return _info_dict(st, info, bufs)
+
+
+def wf_fluct(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_out=None, trace_cap=0) -> dict:
+    info, bufs = _info(trace_cap)
+    n8 = plan.npix * 8
+    st = load().wf_fluct(plan.handle, _ptr(noise_var, None, n8, "noise_var"), _ptr(mask, None, plan.npix, "mask"),
+                         _ptr(C_ell, None, None, "C_ell"), _ptr(g1, None, n8, "g1"),
+                         _ptr(g2, None, plan.nalm * 16, "g2"), float(tol), _ptr(f_out, None, n8, "f_out"),
+                         _ptr(alm_out, None, plan.nalm * 16, "alm_out"), ctypes.byref(info))
+    _check(st, "wf_fluct", allow=(WF_ENOCONV,))
+    return _info_dict(st, info, bufs)
+
+
+def wf_alm2map(plan: Plan, alm, L, map_out):
+    _check(load().wf_alm2map(plan.handle, _ptr(alm, None, plan.nalm * 16, "alm"), int(L),
+                             _ptr(map_out, None, plan.npix * 8, "map")), "wf_alm2map")
+
+
+def wf_map2alm_adjoint(plan: Plan, map_in, L, alm_out):
+    _check(load().wf_map2alm_adjoint(plan.handle, _ptr(map_in, None, plan.npix * 8, "map"), int(L),
+                                     _ptr(alm_out, None, plan.nalm * 16, "alm")), "wf_map2alm_adjoint")
+
+
+__all__ = ["Plan", "WfError", "load", "wf_alm2map", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
+           "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "EXPORTS",
+           "LIB_PATH"]

@@ -1,0 +1,771 @@
+// C ABI, plan construction and the solve driver of the messenger-field
+// Wiener filter (Elsner & Wandelt 2013).
+//
+// One iteration on HEALPix (Sect. 2.1, Eqs. 3-4):
+//   legendre synthesis  a_k        -> G_m(theta)        (wf_legendre.cu)
+//   ring synthesis      G          -> s -> t (Eq. 3)    (wf_ring.cu)
+//   ring analysis       t          -> F_m(theta)        (wf_ring.cu)
+//   legendre analysis   F          -> a_{k+1} (Eq. 4)   (wf_legendre.cu)
+//   reduce              chi^2 (Eq. 6) and the lambda = 1 residual
+// with the cooling schedule of Sect. 3 run on the host between iterations
+// (three FP64 scalars cross the PCIe/C2C link per iteration).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <vector>
+
+#include "wf_internal.cuh"
+
+namespace wf {
+
+static thread_local char g_err[512] = "";
+
+wf_status set_error(wf_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+wf_status cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) return set_error(WF_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(WF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes)
+{
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_check(e, "cudaMalloc (plan)");
+    p->allocations.push_back(d);
+    p->device_bytes += (long long)bytes;
+    *ptr = d;
+    return WF_OK;
+}
+
+Prof::Prof(wf_plan p_, wf_info *i, bool profile) : p(p_), info(i), on(profile)
+{
+    if (on && !p->events_ready) {
+        for (auto &e : p->ev) cudaEventCreate(&e);
+        p->events_ready = true;
+    }
+}
+
+void Prof::begin(int family)
+{
+    count(family);
+    if (!on || nopen >= 16) return;
+    fam[nopen] = family;
+    cudaEventRecord(p->ev[2 * nopen], p->stream);
+}
+
+void Prof::end()
+{
+    if (!on || nopen >= 16) return;
+    cudaEventRecord(p->ev[2 * nopen + 1], p->stream);
+    ++nopen;
+}
+
+void Prof::collect()
+{
+    if (!on) return;
+    for (int i = 0; i < nopen; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev[2 * i], p->ev[2 * i + 1]) == cudaSuccess) ms[fam[i]] += t;
+    }
+    nopen = 0;
+}
+
+void Prof::iter_begin()
+{
+    if (on) cudaEventRecord(p->ev[32], p->stream);
+}
+
+double Prof::iter_end()
+{
+    if (!on) return NAN;
+    cudaEventRecord(p->ev[33], p->stream);
+    cudaEventSynchronize(p->ev[33]);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, p->ev[32], p->ev[33]);
+    return t;
+}
+
+void Prof::finish()
+{
+    if (!info) return;
+    info->launches = launches;
+    for (int k = 0; k < WF_NK; ++k) {
+        info->kernel_ms[k] = ms[k];
+        info->kernel_launches[k] = cnt[k];
+    }
+}
+
+namespace {
+
+__device__ __forceinline__ void atomic_min_pos(double *addr, double v)
+{
+    // positive doubles order like their bit patterns
+    atomicMin(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// validate inputs, build nu = N^-1 (0 where masked) and the source r = nu d;
+// reduce tau = min N over observed pixels and the observed count
+template <typename T>
+__global__ void k_setup(long long npix, const double *__restrict__ d, const double *__restrict__ nv,
+                        const uint8_t *__restrict__ mask, T *__restrict__ r, T *__restrict__ nu,
+                        double *__restrict__ scal, int *__restrict__ flag)
+{
+    unsigned long long cnt = 0;
+    double mn = INFINITY;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+        const bool obs = mask ? (mask[i] != 0) : true;
+        T rv = 0, nuv = 0;
+        if (obs) {
+            const double N = nv[i];
+            const double dv = d ? d[i] : 0.0;
+            if (!(N > 0.0) || !isfinite(N) || !isfinite(dv)) {
+                atomicOr(flag, 1);
+            } else {
+                nuv = (T)(1.0 / N);
+                rv = (T)(dv / N);
+                mn = fmin(mn, N);
+                ++cnt;
+            }
+        }
+        r[i] = rv;
+        nu[i] = nuv;
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cnt) {
+            atomic_min_pos(&scal[0], mn);
+            atomicAdd(reinterpret_cast<unsigned long long *>(&scal[1]), cnt);
+        }
+    }
+}
+
+// fluctuation source, Eq. (9): r = nu^1/2 g1 + Omega z with z = Y (S^-1/2 g2)
+template <typename T>
+__global__ void k_fluct_source(long long npix, const T *__restrict__ nu, const double *__restrict__ g1,
+                               const double *__restrict__ z, double omega, T *__restrict__ r)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x)
+        r[i] = (T)(sqrt((double)nu[i]) * g1[i] + omega * z[i]);
+}
+
+// h_lm = S_l^-1/2 g2_lm (0 where S_l = 0)
+__global__ void k_isqrt_S(int lmax, const double *__restrict__ S, const double2 *__restrict__ g2, double2 *__restrict__ h)
+{
+    const int m = blockIdx.x;
+    const long long base = (long long)m * (2 * lmax + 3 - m) / 2;
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+        const double s = S[l];
+        const double f = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+        const double2 g = g2[base + (l - m)];
+        h[base + (l - m)] = make_double2(f * g.x, f * g.y);
+    }
+}
+
+// per-m partial sums over a_lm: kind 0: sum_{S>0} w |v|^2 ; kind 1: sum_{S>0} w |v|^2 / S
+__global__ void k_alm_norm(int lmax, const double *__restrict__ S, const double2 *__restrict__ v, int kind,
+                           double *__restrict__ part)
+{
+    __shared__ double red[32];
+    const int m = blockIdx.x;
+    const long long base = (long long)m * (2 * lmax + 3 - m) / 2;
+    const double wm = m == 0 ? 1.0 : 2.0;
+    double s = 0.0;
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+        const double Sl = S[l];
+        if (Sl > 0.0) {
+            const double2 a = v[base + (l - m)];
+            const double q = wm * (a.x * a.x + a.y * a.y);
+            s += kind == 0 ? q : q / Sl;
+        }
+    }
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[m] = t;
+    }
+}
+
+// per-block partials of sum_obs nu (d - s)^2
+__global__ void k_pix_chi2(long long npix, const double *__restrict__ d, const double *__restrict__ nv,
+                           const uint8_t *__restrict__ mask, const double *__restrict__ s, double *__restrict__ part)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+        if (mask && !mask[i]) continue;
+        const double e = d[i] - s[i];
+        acc += e * e / nv[i];
+    }
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// deterministic fixed-order sums: out[k] = sum_i in[off_k + i * stride_k], i < n_k
+struct SumSpec {
+    const double *in[3];
+    int n[3];
+    int stride[3];
+};
+__global__ void k_sums(SumSpec sp, int nsum, double *__restrict__ out)
+{
+    __shared__ double red[32];
+    for (int k = 0; k < nsum; ++k) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < sp.n[k]; i += blockDim.x) s += sp.in[k][(long long)i * sp.stride[k]];
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            out[k] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_map_to_T(long long n, const double *__restrict__ in, T *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)in[i];
+}
+
+int grid_for(long long n, int nsm) { return (int)std::min<long long>((n + 255) / 256, (long long)nsm * 8); }
+
+wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
+{
+    if (pr) pr->count(WF_K_OTHER);
+    k_sums<<<1, 256, 0, p->stream>>>(sp, nsum, p->ws.scal);
+    WF_CUDA(cudaGetLastError());
+    WF_CUDA(cudaMemcpyAsync(p->ws.h_scal, p->ws.scal, nsum * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    return WF_OK;
+}
+
+// Sect. 3 heuristic cooling on the sphere (same rules as the oracle's)
+struct HpSchedule {
+    std::vector<double> c;
+    double tau_h = 0;
+    int lmax = 0, ell_iter = 0, step_max = 500, margin = 100;
+    double lam = 1;
+    int L = 0;
+    void level()
+    {
+        if (ell_iter >= lmax) { lam = 1.0; L = lmax; return; }
+        lam = std::max(1.0, c[ell_iter] / tau_h);
+        L = std::min(lmax, ell_iter + margin);
+    }
+    bool final_level() const { return lam == 1.0 && L == lmax; }
+    void advance()
+    {
+        const double l0 = lam;
+        const int L0 = L;
+        for (;;) {
+            ell_iter = std::min(2 * ell_iter, ell_iter + step_max);
+            level();
+            if (lam != l0 || L != L0 || final_level()) return;
+        }
+    }
+};
+
+wf_options defaults(wf_options o)
+{
+    if (o.maxiter <= 0) o.maxiter = 20000;
+    if (o.level_cap <= 0) o.level_cap = 200;
+    if (!(o.eta > 0)) o.eta = 1e-2;
+    if (o.ell0 <= 0) o.ell0 = 20;
+    if (o.ell_step_max <= 0) o.ell_step_max = 500;
+    if (o.band_margin <= 0) o.band_margin = 100;
+    if (!(o.lambda_max > 0)) o.lambda_max = 100.0;
+    if (o.refine_sweeps <= 0) o.refine_sweeps = 3;
+    return o;
+}
+
+void record(wf_info *info, int k, double lam, int L, double chi2, double resid, double ms)
+{
+    if (!info || k >= info->trace_cap) return;
+    if (info->lambda_trace) info->lambda_trace[k] = lam;
+    if (info->L_trace) info->L_trace[k] = L;
+    if (info->chi2_trace) info->chi2_trace[k] = chi2;
+    if (info->resid_trace) info->resid_trace[k] = resid;
+    if (info->iter_ms_trace) info->iter_ms_trace[k] = ms;
+}
+
+template <typename T>
+wf_status hp_setup_T(wf_plan p, const double *d, const double *nv, const uint8_t *mask, double *tau, long long *ndof)
+{
+    const double init[2] = {std::numeric_limits<double>::infinity(), 0.0};
+    WF_CUDA(cudaMemcpyAsync(p->ws.scal, init, sizeof init, cudaMemcpyHostToDevice, p->stream));
+    WF_CUDA(cudaMemsetAsync(p->ws.flag, 0, sizeof(int), p->stream));
+    k_setup<T><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(p->npix, d, nv, mask, (T *)p->ws.r, (T *)p->ws.nu,
+                                                                 p->ws.scal, p->ws.flag);
+    WF_CUDA(cudaGetLastError());
+    int flag = 0;
+    double sc[2];
+    WF_CUDA(cudaMemcpyAsync(sc, p->ws.scal, sizeof sc, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaMemcpyAsync(&flag, p->ws.flag, sizeof flag, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    unsigned long long cnt;
+    std::memcpy(&cnt, &sc[1], sizeof cnt);
+    if (flag) return set_error(WF_EINVAL, "noise variance must be finite and > 0 (and d finite) on observed pixels");
+    if (cnt == 0) return set_error(WF_EINVAL, "every pixel is masked");
+    *tau = sc[0];
+    *ndof = (long long)cnt;
+    return WF_OK;
+}
+
+wf_status hp_setup(wf_plan p, const double *d, const double *nv, const uint8_t *mask, double *tau, long long *ndof)
+{
+    return p->prec == WF_PREC_FP64 ? hp_setup_T<double>(p, d, nv, mask, tau, ndof)
+                                   : hp_setup_T<float>(p, d, nv, mask, tau, ndof);
+}
+
+// map (FP64) = Y a, restricted to l <= L
+wf_status hp_alm2map(wf_plan p, const double2 *a, int L, double *map)
+{
+    wf_status st = hp_legendre_synthesis(p, a, L);
+    if (st != WF_OK) return st;
+    return hp_ring_synthesis(p, L, RS_MAP, 1.0, 0.0, map);
+}
+
+// out = Y^T map_T (map in the working precision), l <= L; entries above L zeroed
+wf_status hp_adjoint_T(wf_plan p, const void *map_T, int L, double2 *out)
+{
+    WF_CUDA(cudaMemsetAsync(out, 0, p->nalm * sizeof(double2), p->stream));
+    wf_status st = hp_ring_analysis(p, L, map_T);
+    if (st != WF_OK) return st;
+    BlendArgs ba;
+    return hp_legendre_analysis(p, L, LEG_ADJOINT, ba, nullptr, out);
+}
+
+wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *mask, const double *C_ell, double tol,
+                   bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out, wf_info *info)
+{
+    const wf_options o = defaults(p->opt);
+    const int lmax = p->lmax;
+    Prof pr(p, info, o.profile != 0);
+    double tau = 0;
+    long long ndof = 0;
+    pr.count(WF_K_OTHER);
+    wf_status st = hp_setup(p, fluct ? nullptr : d, nv, mask, &tau, &ndof);
+    if (st != WF_OK) return st;
+    const double tau_h = tau * p->omega;
+    if (fluct) {
+        // r = nu^1/2 g1 + Omega Y (S^-1/2 g2), z synthesised into the output map as scratch
+        k_isqrt_S<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, (const double2 *)g2, p->ws.a_new);
+        WF_CUDA(cudaGetLastError());
+        if ((st = hp_alm2map(p, p->ws.a_new, lmax, s_out)) != WF_OK) return st;
+        pr.count(WF_K_OTHER, 2);
+        pr.count(WF_K_LEG_SYN);
+        pr.count(WF_K_RING_SYN);
+        if (p->prec == WF_PREC_FP64)
+            k_fluct_source<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
+                p->npix, (const double *)p->ws.nu, g1, s_out, p->omega, (double *)p->ws.r);
+        else
+            k_fluct_source<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
+                p->npix, (const float *)p->ws.nu, g1, s_out, p->omega, (float *)p->ws.r);
+        WF_CUDA(cudaGetLastError());
+    }
+    // |b| = |Y^T r| over modes with S > 0
+    if ((st = hp_adjoint_T(p, p->ws.r, lmax, p->ws.b)) != WF_OK) return st;
+    pr.count(WF_K_RING_ANA);
+    pr.count(WF_K_LEG_ANA);
+    pr.count(WF_K_OTHER);
+    k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, p->ws.b, 0, p->ws.part_harm);
+    WF_CUDA(cudaGetLastError());
+    {
+        SumSpec sp{};
+        sp.in[0] = p->ws.part_harm;
+        sp.n[0] = lmax + 1;
+        sp.stride[0] = 1;
+        if ((st = sums(p, sp, 1, &pr)) != WF_OK) return st;
+    }
+    const double bnorm = std::sqrt(p->ws.h_scal[0]);
+    if (!(bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
+
+    HpSchedule sch;
+    sch.c.resize(lmax + 1);
+    WF_CUDA(cudaMemcpy(sch.c.data(), C_ell, (lmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    sch.tau_h = tau_h;
+    sch.lmax = lmax;
+    sch.step_max = o.ell_step_max;
+    sch.margin = o.band_margin;
+    sch.ell_iter = std::min(o.ell0, lmax);
+    sch.level();
+
+    WF_CUDA(cudaMemsetAsync(p->ws.a, 0, p->nalm * sizeof(double2), p->stream));
+    WF_CUDA(cudaMemsetAsync(p->ws.a_new, 0, p->nalm * sizeof(double2), p->stream));
+    const bool replay = !p->replay_lambda.empty();
+    const int nrep = (int)p->replay_lambda.size();
+    int k = 0, level_iters = 0, levels = 1;
+    bool have_prev = false, converged = false;
+    double prev_chi2 = 0, last_resid = NAN, best_resid = INFINITY;
+    const double sigma = std::sqrt(2.0 * (double)ndof);
+    wf_status result = WF_OK;
+    for (;;) {
+        double lam;
+        int L;
+        if (replay) {
+            if (k >= nrep) break;
+            lam = p->replay_lambda[k];
+            L = std::min(std::max(p->replay_L[k], 0), lmax);
+        } else {
+            if (k >= o.maxiter) { result = WF_ENOCONV; break; }
+            lam = sch.lam;
+            L = sch.L;
+        }
+        const bool full = (lam == 1.0 && L == lmax);
+        pr.iter_begin();
+        pr.begin(WF_K_LEG_SYN);
+        if ((st = hp_legendre_synthesis(p, p->ws.a, L)) != WF_OK) return st;
+        pr.end();
+        pr.begin(WF_K_RING_SYN);
+        if ((st = hp_ring_synthesis(p, L, RS_BLEND, lam, tau, nullptr)) != WF_OK) return st;
+        pr.end();
+        pr.begin(WF_K_RING_ANA);
+        if ((st = hp_ring_analysis(p, L, p->ws.t)) != WF_OK) return st;
+        pr.end();
+        BlendArgs ba;
+        ba.lam_tauh = lam * tau_h;
+        ba.tauh = tau_h;
+        ba.S = C_ell;
+        ba.want_resid = full ? 1 : 0;
+        pr.begin(WF_K_LEG_ANA);
+        if ((st = hp_legendre_analysis(p, L, LEG_BLEND, ba, p->ws.a, p->ws.a_new)) != WF_OK) return st;
+        pr.end();
+        SumSpec sp{};
+        sp.in[0] = p->ws.part_pix;
+        sp.n[0] = p->tab.ringGrid;
+        sp.stride[0] = 1;
+        sp.in[1] = p->ws.part_harm;
+        sp.n[1] = L + 1;
+        sp.stride[1] = 2;
+        sp.in[2] = p->ws.part_harm + 1;
+        sp.n[2] = L + 1;
+        sp.stride[2] = 2;
+        if ((st = sums(p, sp, 3, &pr)) != WF_OK) return st;
+        const double ims = pr.iter_end();
+        pr.collect();
+        const double chi2 = p->ws.h_scal[0] + p->ws.h_scal[1];
+        const double resid = full ? std::sqrt(p->ws.h_scal[2]) / bnorm : NAN;
+        record(info, k, lam, L, chi2, resid, ims);
+        std::swap(p->ws.a, p->ws.a_new);
+        ++k;
+        if (full) {
+            last_resid = resid;
+            if (!std::isfinite(resid) || (k > 50 && resid > 1e3 * best_resid)) { result = WF_EDIVERGE; break; }
+            best_resid = std::min(best_resid, resid);
+        }
+        if (!std::isfinite(chi2)) { result = WF_EDIVERGE; break; }
+        if (replay) {
+            if (full && resid < tol) converged = true;
+            continue;
+        }
+        if (sch.final_level()) {
+            if (resid < tol) { converged = true; break; }
+        } else {
+            ++level_iters;
+            const bool plateau = have_prev && std::fabs(chi2 - prev_chi2) < o.eta * sigma;
+            if (plateau || level_iters >= o.level_cap) {
+                sch.advance();
+                ++levels;
+                have_prev = false;
+                level_iters = 0;
+                continue;
+            }
+        }
+        prev_chi2 = chi2;
+        have_prev = true;
+    }
+    if ((st = hp_alm2map(p, p->ws.a, lmax, s_out)) != WF_OK) return st;
+    pr.count(WF_K_LEG_SYN);
+    pr.count(WF_K_RING_SYN);
+    if (alm_out)
+        WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.a, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    double chi2n = NAN;
+    if (!fluct) {
+        k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, p->ws.a, 1, p->ws.part_harm);
+        const int gb = 256;
+        k_pix_chi2<<<gb, 256, 0, p->stream>>>(p->npix, d, nv, mask, s_out, p->ws.part_pix);
+        WF_CUDA(cudaGetLastError());
+        SumSpec sp{};
+        sp.in[0] = p->ws.part_harm;
+        sp.n[0] = lmax + 1;
+        sp.stride[0] = 1;
+        sp.in[1] = p->ws.part_pix;
+        sp.n[1] = gb;
+        sp.stride[1] = 1;
+        pr.count(WF_K_OTHER, 2);
+        if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
+        chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
+    } else {
+        WF_CUDA(cudaStreamSynchronize(p->stream));
+    }
+    if (info) {
+        info->iters = k;
+        info->converged = converged ? 1 : 0;
+        info->final_residual = last_resid;
+        info->chi2_over_ndof = chi2n;
+        info->n_dof = ndof;
+        info->tau = tau;
+        info->n_levels = levels;
+        info->refine_sweeps = 0;
+    }
+    pr.finish();
+    if (result == WF_OK && !replay && !converged) result = WF_ENOCONV;
+    if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", last_resid);
+    if (result == WF_EDIVERGE) set_error(result, "residual grew (%.3e); lmax too large for this nside?", last_resid);
+    return result;
+}
+
+wf_status hp_create(wf_plan p)
+{
+    const int nside = p->nside;
+    p->nrings = 4 * nside - 1;
+    p->npairs = 2 * nside;
+    p->npix = 12LL * nside * nside;
+    p->nalm = (long long)(p->lmax + 1) * (p->lmax + 2) / 2;
+    p->omega = 4.0 * M_PI / (double)p->npix;
+    std::vector<double> xp(p->npairs), stp(p->npairs);
+    for (int pr = 0; pr < p->npairs; ++pr) {
+        const int i = pr + 1;  // 1-based north ring
+        if (i < nside) {
+            const double omz = (double)i * i / (3.0 * nside * nside);
+            xp[pr] = 1.0 - omz;
+            stp[pr] = std::sqrt(omz * (2.0 - omz));
+        } else {
+            const double z = 4.0 / 3.0 - 2.0 * i / (3.0 * nside);
+            xp[pr] = z;
+            stp[pr] = std::sqrt((1.0 - z) * (1.0 + z));
+        }
+    }
+    wf_status st;
+    if ((st = hp_build_legendre_tables(p, xp, stp)) != WF_OK) return st;
+    if ((st = hp_build_ring_tables(p)) != WF_OK) return st;
+    const size_t es = p->prec == WF_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t gsz = (size_t)p->npairs * (p->lmax + 1) * 2 * 2 * es;
+    if ((st = plan_alloc(p, (void **)&p->ws.a, p->nalm * sizeof(double2))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.a_new, p->nalm * sizeof(double2))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.b, p->nalm * sizeof(double2))) != WF_OK) return st;
+    if ((st = plan_alloc(p, &p->ws.G, gsz)) != WF_OK) return st;
+    if ((st = plan_alloc(p, &p->ws.F, gsz)) != WF_OK) return st;
+    if ((st = plan_alloc(p, &p->ws.r, p->npix * es)) != WF_OK) return st;
+    if ((st = plan_alloc(p, &p->ws.nu, p->npix * es)) != WF_OK) return st;
+    if ((st = plan_alloc(p, &p->ws.t, p->npix * es)) != WF_OK) return st;
+    const int npart = std::max(p->tab.ringGrid, 256);
+    if ((st = plan_alloc(p, (void **)&p->ws.part_pix, npart * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.part_harm, 2 * (p->lmax + 2) * sizeof(double))) != WF_OK) return st;
+    return WF_OK;
+}
+
+}  // namespace
+
+}  // namespace wf
+
+using namespace wf;
+
+extern "C" {
+
+const char *wf_strerror(wf_status s)
+{
+    switch (s) {
+    case WF_OK: return "ok";
+    case WF_EINVAL: return "invalid argument";
+    case WF_ENOMEM: return "out of memory";
+    case WF_ECUDA: return "CUDA error";
+    case WF_ENOCONV: return "not converged";
+    case WF_EDIVERGE: return "diverged";
+    case WF_ETIMEOUT: return "device wait timed out";
+    case WF_EUNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char *wf_last_error(void) { return wf::g_err; }
+
+wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void *cuda_stream, wf_plan *out)
+{
+    if (!g || !out) return set_error(WF_EINVAL, "null argument");
+    *out = nullptr;
+    if (g->ncomp != 0 && g->ncomp != 1) return set_error(WF_EUNSUPPORTED, "only ncomp = 1 (temperature) is supported");
+    if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32) return set_error(WF_EINVAL, "unknown precision");
+    wf_plan p = new (std::nothrow) wf_plan_s();
+    if (!p) return set_error(WF_ENOMEM, "host allocation");
+    p->g = *g;
+    p->prec = prec;
+    p->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_check(e, "device query");
+    }
+    wf_status st = WF_OK;
+    if (g->kind == WF_GEOM_HEALPIX) {
+        if (g->nside < 1 || g->nside > 8192) st = set_error(WF_EINVAL, "nside out of range");
+        else if (lmax < 2 || lmax > 2 * g->nside) st = set_error(WF_EINVAL, "need 2 <= lmax <= 2 nside (got %d)", lmax);
+        else {
+            p->nside = g->nside;
+            p->lmax = lmax;
+            st = hp_create(p);
+        }
+    } else if (g->kind == WF_GEOM_FLAT) {
+        p->lmax = 0;
+        st = flat_create(p);
+    } else {
+        st = set_error(WF_EINVAL, "unknown geometry");
+    }
+    if (st == WF_OK) {
+        if ((st = plan_alloc(p, (void **)&p->ws.scal, 16 * sizeof(double))) == WF_OK &&
+            (st = plan_alloc(p, (void **)&p->ws.flag, 16)) == WF_OK) {
+            if (cudaMallocHost(&p->ws.h_scal, 16 * sizeof(double)) != cudaSuccess)
+                st = set_error(WF_ENOMEM, "pinned host allocation");
+        }
+    }
+    if (st != WF_OK) {
+        wf_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return WF_OK;
+}
+
+void wf_plan_destroy(wf_plan p)
+{
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    if (p->flat) flat_destroy(p);
+    if (p->events_ready)
+        for (auto &e : p->ev) cudaEventDestroy(e);
+    for (void *a : p->allocations) cudaFree(a);
+    if (p->ws.h_scal) cudaFreeHost(p->ws.h_scal);
+    delete p;
+}
+
+wf_status wf_set_options(wf_plan p, const wf_options *opt)
+{
+    if (!p) return set_error(WF_EINVAL, "null plan");
+    p->opt = opt ? *opt : wf_options{};
+    return WF_OK;
+}
+
+wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n)
+{
+    if (!p || n < 0 || (n > 0 && !lambda)) return set_error(WF_EINVAL, "bad schedule");
+    p->replay_lambda.assign(lambda, lambda + n);
+    p->replay_L.assign(n, p->lmax);
+    if (L) for (int i = 0; i < n; ++i) p->replay_L[i] = L[i];
+    for (double v : p->replay_lambda)
+        if (!(v >= 1.0)) return set_error(WF_EINVAL, "lambda must be >= 1");
+    return WF_OK;
+}
+
+long long wf_npix(wf_plan p) { return p ? p->npix : 0; }
+long long wf_nalm(wf_plan p) { return p ? p->nalm : 0; }
+long long wf_plan_device_bytes(wf_plan p) { return p ? p->device_bytes : 0; }
+
+wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask, const double *C_ell,
+                   double tol, double *s_wf, double *alm_out, wf_info *info)
+{
+    if (!p || !d || !noise_var || !C_ell || !s_wf) return set_error(WF_EINVAL, "null argument");
+    if (!(tol > 0)) return set_error(WF_EINVAL, "tol must be > 0");
+    if (p->g.kind == WF_GEOM_FLAT)
+        return flat_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
+    return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
+}
+
+wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, const double *C_ell, const double *g1,
+                   const double *g2, double tol, double *f_out, double *alm_out, wf_info *info)
+{
+    if (!p || !noise_var || !C_ell || !g1 || !g2 || !f_out) return set_error(WF_EINVAL, "null argument");
+    if (!(tol > 0)) return set_error(WF_EINVAL, "tol must be > 0");
+    if (p->g.kind == WF_GEOM_FLAT)
+        return flat_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
+    return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
+}
+
+wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask, const double *C_ell,
+                        double tol, double *s_wf, double *alm_out, wf_info *info)
+{
+    if (!p || !d || !noise_var || !C_ell || !s_wf) return set_error(WF_EINVAL, "null argument");
+    const size_t npx = (size_t)p->npix;
+    const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
+    const size_t nh = (size_t)p->nalm * 2;
+    wf_status st;
+    if (!p->ws.d_in) {
+        if ((st = plan_alloc(p, (void **)&p->ws.d_in, npx * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.nv_in, npx * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.mask_in, npx)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.out_map, npx * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.cl_in, nS * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.alm_io, nh * 8)) != WF_OK) return st;
+    }
+    cudaStream_t s = p->stream;
+    WF_CUDA(cudaMemcpyAsync(p->ws.d_in, d, npx * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, npx * 8, cudaMemcpyHostToDevice, s));
+    if (mask) WF_CUDA(cudaMemcpyAsync(p->ws.mask_in, mask, npx, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.cl_in, C_ell, nS * 8, cudaMemcpyHostToDevice, s));
+    st = wf_solve(p, p->ws.d_in, p->ws.nv_in, mask ? p->ws.mask_in : nullptr, p->ws.cl_in, tol, p->ws.out_map,
+                  alm_out ? p->ws.alm_io : nullptr, info);
+    if (st != WF_OK && st != WF_ENOCONV) return st;
+    WF_CUDA(cudaMemcpyAsync(s_wf, p->ws.out_map, npx * 8, cudaMemcpyDeviceToHost, s));
+    if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nh * 8, cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+wf_status wf_alm2map(wf_plan p, const double *alm, int L, double *map)
+{
+    if (!p || !alm || !map) return set_error(WF_EINVAL, "null argument");
+    if (p->g.kind == WF_GEOM_FLAT) return flat_alm2map(p, alm, map);
+    if (L < 0 || L > p->lmax) L = p->lmax;
+    wf_status st = hp_alm2map(p, (const double2 *)alm, L, map);
+    if (st != WF_OK) return st;
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    return WF_OK;
+}
+
+wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm)
+{
+    if (!p || !alm || !map) return set_error(WF_EINVAL, "null argument");
+    if (p->g.kind == WF_GEOM_FLAT) return flat_map2alm(p, map, alm);
+    if (L < 0 || L > p->lmax) L = p->lmax;
+    if (p->prec == WF_PREC_FP64) {
+        WF_CUDA(cudaMemcpyAsync(p->ws.t, map, p->npix * 8, cudaMemcpyDeviceToDevice, p->stream));
+    } else {
+        k_map_to_T<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(p->npix, map, (float *)p->ws.t);
+        WF_CUDA(cudaGetLastError());
+    }
+    wf_status st = hp_adjoint_T(p, p->ws.t, L, (double2 *)alm);
+    if (st != WF_OK) return st;
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    return WF_OK;
+}
+
+}  // extern "C"

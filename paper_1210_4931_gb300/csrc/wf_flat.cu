@@ -1,0 +1,637 @@
+// Flat-sky messenger-field Wiener filter on a periodic n x n grid with the
+// unitary 2-D DFT (the "e.g. Fourier space" basis of Sect. 2.1).
+//
+// The whole solve -- every iteration of Eqs. (3)-(4), the chi^2 of Eq. (6),
+// the residual and the cooling schedule -- runs in ONE persistent launch of a
+// single thread-block cluster of CS CTAs (CS = 8).  The grid never leaves the
+// cluster's shared memory:
+//   CTA c owns pixel rows [c n/CS, (c+1) n/CS) (source r, inverse noise nu)
+//   and spectrum columns kx in [c P, (c+1) P), P = ceil((n/2+1)/CS) (a, S).
+// One iteration:
+//   1. column inverse FFTs (ky) of the owned a columns          (local)
+//   2. cluster barrier; each CTA gathers its rows' spectra from every CTA's
+//      column buffer through distributed shared memory, c2r FFTs the rows,
+//      applies the pixel blend of Eq. (3) and r2c FFTs the result
+//   3. cluster barrier; each CTA gathers its columns from every CTA's row
+//      buffer, forward FFTs them (ky) and applies the harmonic blend of
+//      Eq. (4), accumulating chi^2 and the lambda = 1 residual
+//   4. cluster barrier; every CTA sums all CTAs' partials in the same order
+//      and takes the same schedule decision (no broadcast needed).
+// FFTs are radix-2, one warp per row/column, in shared memory.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "wf_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace wf {
+
+constexpr int FLAT_CS = 8;
+constexpr int FLAT_THREADS = 256;
+constexpr int FLAT_WARPS = FLAT_THREADS / 32;
+constexpr int FLAT_MAXN = 128;
+
+struct FlatStatus {
+    int iters, converged, levels, stop_reason;  // stop_reason: 0 schedule/replay end, 1 converged, 2 maxiter, 3 diverged
+    double final_resid, chi2_final, bnorm;
+};
+
+struct FlatPlan {
+    int n = 0, logn = 0, nh = 0, P = 0, RP = 0;
+    size_t smem = 0;
+    double *r = nullptr, *nu = nullptr;  // device pixel maps
+    double *levels = nullptr;            // device lambda levels
+    double *tr_lam = nullptr, *tr_chi2 = nullptr, *tr_res = nullptr;
+    int tr_cap = 0;
+    FlatStatus *status = nullptr;
+    double *replay = nullptr;
+    int replay_cap = 0;
+};
+
+namespace {
+
+struct FlatArgs {
+    int n, logn, nh, P, RP;
+    const double *r, *nu, *S;
+    const double *g1;      // fluct: unit draws in pixel space (or null)
+    const double2 *g2;     // fluct: unit harmonic draws (or null)
+    const double *levels;
+    int nlevels;
+    const double *replay;  // lambda per iteration (or null)
+    int nreplay;
+    double tau, sigma, eta, tol;
+    int level_cap, maxiter;
+    double *s_out;
+    double2 *alm_out;
+    double *tr_lam, *tr_chi2, *tr_res;
+    int tr_cap;
+    FlatStatus *status;
+};
+
+__device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b); }
+
+// radix-2 DIT FFT of length 2^logn on x (shared memory) by one warp
+__device__ void warp_fft(double2 *x, int logn, int sign, const double2 *tw /* e^{-2 pi i t / n}, t < n/2 */)
+{
+    const int n = 1 << logn, lane = threadIdx.x & 31;
+    for (int i = lane; i < n; i += 32) {
+        const int j = (int)(__brev((unsigned)i) >> (32 - logn));
+        if (i < j) {
+            const double2 t = x[i];
+            x[i] = x[j];
+            x[j] = t;
+        }
+    }
+    __syncwarp();
+    for (int s = 1; s <= logn; ++s) {
+        const int half = 1 << (s - 1);
+        for (int b = lane; b < n / 2; b += 32) {
+            const int pos = b & (half - 1);
+            const int i0 = ((b >> (s - 1)) << s) + pos, i1 = i0 + half;
+            double2 w = tw[pos << (logn - s)];
+            if (sign > 0) w.y = -w.y;
+            const double2 u = x[i0], v = dmul(x[i1], w);
+            x[i0] = cadd(u, v);
+            x[i1] = csub(u, v);
+        }
+        __syncwarp();
+    }
+}
+
+enum FlatStep { FS_ITER = 0, FS_PROLOGUE = 1, FS_FLUCT_SRC = 2, FS_OUT = 3 };
+
+__global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
+    k_flat_solve(FlatArgs A)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const int c = (int)cluster.block_rank();
+    const int n = A.n, nh = A.nh, P = A.P, RP = A.RP, logn = A.logn;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = c * P;
+    const int ncol = max(0, min(nh, c0 + P) - c0);
+    const int y0 = c * RP;
+    const double sy = rsqrt((double)n), sx = rsqrt((double)n);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *tw = reinterpret_cast<double2 *>(smem_raw);            // n/2
+    double2 *acol = tw + n / 2;                                      // P * n
+    double2 *colbuf = acol + (size_t)P * n;                          // P * n
+    double2 *rowbuf = colbuf + (size_t)P * n;                        // RP * nh
+    double2 *wscr = rowbuf + (size_t)RP * nh;                        // FLAT_WARPS * n
+    double *Scol = reinterpret_cast<double *>(wscr + (size_t)FLAT_WARPS * n);  // P * n
+    double *rpix = Scol + (size_t)P * n;                             // RP * n
+    double *nupix = rpix + (size_t)RP * n;                           // RP * n
+    __shared__ double part[4];   // pix chi2, harm chi2, resid^2, spare
+    __shared__ double red[FLAT_WARPS][3];
+
+    for (int t = tid; t < n / 2; t += blockDim.x) {
+        double s, co;
+        sincospi(-2.0 * t / n, &s, &co);
+        tw[t] = make_double2(co, s);
+    }
+    for (int i = tid; i < P * n; i += blockDim.x) {
+        const int kl = i / n, ky = i % n;
+        const int kx = c0 + kl;
+        acol[i] = make_double2(0.0, 0.0);
+        Scol[i] = (kl < ncol) ? A.S[(size_t)ky * nh + kx] : 0.0;
+    }
+    for (int i = tid; i < RP * n; i += blockDim.x) {
+        const size_t g = (size_t)y0 * n + i;
+        rpix[i] = A.r[g];
+        nupix[i] = A.nu[g];
+    }
+    __syncthreads();
+
+    auto block_reduce3 = [&](double a, double b, double d) {
+        for (int o = 16; o >= 1; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) { red[warp][0] = a; red[warp][1] = b; red[warp][2] = d; }
+        __syncthreads();
+        if (tid == 0) {
+            double s0 = 0, s1 = 0, s2 = 0;
+            for (int w = 0; w < FLAT_WARPS; ++w) { s0 += red[w][0]; s1 += red[w][1]; s2 += red[w][2]; }
+            part[0] = s0; part[1] = s1; part[2] = s2;
+        }
+        __syncthreads();
+    };
+
+    // ---- step 1: inverse column FFTs of acol into colbuf ----
+    auto step1 = [&]() {
+        for (int kl = warp; kl < ncol; kl += FLAT_WARPS) {
+            double2 *x = colbuf + (size_t)kl * n;
+            for (int ky = lane; ky < n; ky += 32) x[ky] = acol[(size_t)kl * n + ky];
+            __syncwarp();
+            warp_fft(x, logn, +1, tw);
+            for (int y = lane; y < n; y += 32) x[y] = cscale(x[y], sy);
+            __syncwarp();
+        }
+    };
+
+    // ---- step 2: rows: gather, c2r, blend (or other use), r2c into rowbuf ----
+    auto step2 = [&](int mode, double lam) -> double {
+        for (int i = tid; i < RP * nh; i += blockDim.x) {
+            const int yl = i / nh, kx = i % nh;
+            const int o = kx / P, kl = kx - o * P;
+            const double2 *rc = cluster.map_shared_rank(colbuf, o);
+            rowbuf[(size_t)yl * nh + kx] = rc[(size_t)kl * n + (y0 + yl)];
+        }
+        __syncthreads();
+        const double lt = lam * A.tau, lm1t = (lam - 1.0) * A.tau;
+        double acc = 0.0;
+        double2 *x = wscr + (size_t)warp * n;
+        for (int yl = warp; yl < RP; yl += FLAT_WARPS) {
+            const double2 *b = rowbuf + (size_t)yl * nh;
+            for (int kx = lane; kx < n; kx += 32) {
+                double2 v;
+                if (kx < nh) v = b[kx];
+                else v = cconj(b[n - kx]);
+                x[kx] = v;
+            }
+            __syncwarp();
+            warp_fft(x, logn, +1, tw);  // real part = c2r
+            for (int xx = lane; xx < n; xx += 32) {
+                const double s = x[xx].x * sx;
+                const int pi = yl * n + xx;
+                double t = s;
+                if (mode == FS_ITER) {
+                    const double nv = nupix[pi], rv = rpix[pi];
+                    const double den = 1.0 + lm1t * nv;
+                    t = s + lt * (rv - nv * s) / den;
+                    acc += (nv * s * s - 2.0 * rv * s) / den;
+                } else if (mode == FS_PROLOGUE) {
+                    t = rpix[pi];
+                } else if (mode == FS_FLUCT_SRC) {
+                    const double rv = sqrt(nupix[pi]) * A.g1[(size_t)y0 * n + pi] + s;
+                    rpix[pi] = rv;
+                    t = rv;
+                } else {  // FS_OUT
+                    A.s_out[(size_t)y0 * n + pi] = s;
+                    const double nv = nupix[pi];
+                    if (nv > 0.0) {
+                        const double e = rpix[pi] - nv * s;
+                        acc += e * e / nv;  // nu (d - s)^2
+                    }
+                }
+                x[xx] = make_double2(t, 0.0);
+            }
+            __syncwarp();
+            if (mode == FS_ITER || mode == FS_PROLOGUE) {
+                warp_fft(x, logn, -1, tw);
+                double2 *bo = rowbuf + (size_t)yl * nh;
+                for (int kx = lane; kx < nh; kx += 32) bo[kx] = cscale(x[kx], sx);
+            }
+            __syncwarp();
+        }
+        return acc;
+    };
+
+    // ---- step 3: columns: gather, forward FFT, harmonic blend ----
+    // mode FS_ITER: a = S/(S + lam tau) t_hat; chi2 of a_old; residual if lam == 1
+    // mode FS_PROLOGUE: accumulate |t_hat|^2 (the b norm), a untouched
+    auto step3 = [&](int mode, double lam, double &chi2h, double &res2) {
+        for (int i = tid; i < ncol * n; i += blockDim.x) {
+            const int kl = i / n, y = i % n;
+            const int o = y / RP, yl = y - o * RP;
+            const double2 *rb = cluster.map_shared_rank(rowbuf, o);
+            colbuf[i] = rb[(size_t)yl * nh + (c0 + kl)];
+        }
+        __syncthreads();
+        const double lt = lam * A.tau;
+        const bool full = (lam == 1.0);
+        for (int kl = warp; kl < ncol; kl += FLAT_WARPS) {
+            double2 *x = colbuf + (size_t)kl * n;
+            warp_fft(x, logn, -1, tw);
+            const int kx = c0 + kl;
+            const double w = (kx == 0 || 2 * kx == n) ? 1.0 : 2.0;
+            for (int ky = lane; ky < n; ky += 32) {
+                const double2 th = cscale(x[ky], sy);
+                const double S = Scol[(size_t)kl * n + ky];
+                if (mode == FS_PROLOGUE) {
+                    if (S > 0.0) res2 += w * (th.x * th.x + th.y * th.y);
+                    continue;
+                }
+                const double2 ao = acol[(size_t)kl * n + ky];
+                double2 an = make_double2(0.0, 0.0);
+                if (S > 0.0) {
+                    const double f = S / (S + lt);
+                    an = cscale(th, f);
+                    chi2h += w * (ao.x * ao.x + ao.y * ao.y) / S;
+                    if (full) {
+                        const double k = 1.0 / S + 1.0 / A.tau;
+                        const double dx = k * (ao.x - an.x), dy = k * (ao.y - an.y);
+                        res2 += w * (dx * dx + dy * dy);
+                    }
+                }
+                acol[(size_t)kl * n + ky] = an;
+            }
+            __syncwarp();
+        }
+    };
+
+    // sum partial triplets over the cluster (same order in every CTA)
+    auto cluster_sum = [&](double out[3]) {
+        out[0] = out[1] = out[2] = 0.0;
+        for (int o = 0; o < FLAT_CS; ++o) {
+            const double *pp = cluster.map_shared_rank(part, o);
+            out[0] += pp[0];
+            out[1] += pp[1];
+            out[2] += pp[2];
+        }
+    };
+
+    double tot[3];
+    // ---- fluctuation source: r = nu^1/2 g1 + F^-1 (S^-1/2 g2) ----
+    if (A.g1) {
+        for (int i = tid; i < ncol * n; i += blockDim.x) {
+            const int kl = i / n, ky = i % n;
+            const double S = Scol[i];
+            const double f = S > 0.0 ? rsqrt(S) : 0.0;
+            acol[i] = cscale(A.g2[(size_t)ky * nh + c0 + kl], f);
+        }
+        __syncthreads();
+        step1();
+        cluster.sync();
+        step2(FS_FLUCT_SRC, 1.0);
+        __syncthreads();
+        for (int i = tid; i < P * n; i += blockDim.x) acol[i] = make_double2(0.0, 0.0);
+        cluster.sync();
+    }
+    // ---- prologue: |b| = |F r| ----
+    {
+        step2(FS_PROLOGUE, 1.0);
+        cluster.sync();
+        double ch = 0.0, rs = 0.0;
+        step3(FS_PROLOGUE, 1.0, ch, rs);
+        block_reduce3(0.0, 0.0, rs);
+        cluster.sync();
+        cluster_sum(tot);
+    }
+    const double bnorm = sqrt(tot[2]);
+    cluster.sync();
+
+    // ---- iterations ----
+    int k = 0, lev = 0, level_iters = 0, have_prev = 0, converged = 0, stop_reason = 0;
+    double prev = 0.0, last_res = NAN, best = INFINITY;
+    for (;;) {
+        double lam;
+        if (A.replay) {
+            if (k >= A.nreplay) break;
+            lam = A.replay[k];
+        } else {
+            if (k >= A.maxiter) { stop_reason = 2; break; }
+            lam = A.levels[lev];
+        }
+        step1();
+        cluster.sync();
+        const double pc = step2(FS_ITER, lam);
+        cluster.sync();
+        double ch = 0.0, rs = 0.0;
+        step3(FS_ITER, lam, ch, rs);
+        block_reduce3(pc, ch, rs);
+        cluster.sync();
+        cluster_sum(tot);
+        const double chi2 = tot[0] + tot[1];
+        const bool full = lam == 1.0;
+        const double resid = full ? sqrt(tot[2]) / bnorm : NAN;
+        if (c == 0 && tid == 0 && k < A.tr_cap) {
+            A.tr_lam[k] = lam;
+            A.tr_chi2[k] = chi2;
+            A.tr_res[k] = resid;
+        }
+        ++k;
+        if (full) {
+            last_res = resid;
+            if (!isfinite(resid) || (k > 50 && resid > 1e3 * best)) { stop_reason = 3; break; }
+            best = fmin(best, resid);
+        }
+        if (A.replay) continue;
+        if (lam == 1.0) {
+            if (resid < A.tol) { converged = 1; stop_reason = 1; break; }
+        } else {
+            ++level_iters;
+            const bool plateau = have_prev && fabs(chi2 - prev) < A.eta * A.sigma;
+            if (plateau || level_iters >= A.level_cap) {
+                lev = min(lev + 1, A.nlevels - 1);
+                level_iters = 0;
+                have_prev = 0;
+                continue;
+            }
+        }
+        prev = chi2;
+        have_prev = 1;
+    }
+    if (A.replay && isfinite(last_res) && last_res < A.tol) converged = 1;
+    // ---- output: s = F^-1 a, chi^2(s, 1) ----
+    cluster.sync();
+    step1();
+    cluster.sync();
+    const double pc = step2(FS_OUT, 1.0);
+    double chh = 0.0;
+    for (int i = tid; i < ncol * n; i += blockDim.x) {
+        const int kl = i / n, ky = i % n;
+        const int kx = c0 + kl;
+        const double2 a = acol[i];
+        if (A.alm_out) A.alm_out[(size_t)ky * nh + kx] = a;
+        const double S = Scol[i];
+        const double w = (kx == 0 || 2 * kx == n) ? 1.0 : 2.0;
+        if (S > 0.0) chh += w * (a.x * a.x + a.y * a.y) / S;
+    }
+    block_reduce3(pc, chh, 0.0);
+    cluster.sync();
+    cluster_sum(tot);
+    if (c == 0 && tid == 0) {
+        A.status->iters = k;
+        A.status->converged = converged;
+        A.status->levels = lev + 1;
+        A.status->stop_reason = stop_reason;
+        A.status->final_resid = last_res;
+        A.status->chi2_final = tot[0] + tot[1];
+        A.status->bnorm = bnorm;
+    }
+    cluster.sync();  // keep every CTA's shared memory alive until all remote reads are done
+}
+
+// nu = N^-1 (0 where masked), r = nu d; tau = min N and count over observed pixels
+__global__ void k_flat_setup(long long npix, const double *__restrict__ d, const double *__restrict__ nv,
+                             const uint8_t *__restrict__ mask, double *__restrict__ r, double *__restrict__ nu,
+                             double *__restrict__ out /* [min, count, flag] */)
+{
+    __shared__ double smin[32], scnt[32], sfl[32];
+    double mn = INFINITY, cnt = 0, fl = 0;
+    for (long long i = threadIdx.x; i < npix; i += blockDim.x) {
+        const bool obs = mask ? mask[i] != 0 : true;
+        double rv = 0.0, nuv = 0.0;
+        if (obs) {
+            const double N = nv[i], dv = d ? d[i] : 0.0;
+            if (!(N > 0.0) || !isfinite(N) || !isfinite(dv)) fl = 1;
+            else {
+                nuv = 1.0 / N;
+                rv = dv / N;
+                mn = fmin(mn, N);
+                cnt += 1;
+            }
+        }
+        r[i] = rv;
+        nu[i] = nuv;
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        fl = fmax(fl, __shfl_xor_sync(0xffffffffu, fl, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        smin[threadIdx.x >> 5] = mn;
+        scnt[threadIdx.x >> 5] = cnt;
+        sfl[threadIdx.x >> 5] = fl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = INFINITY, b = 0, f = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = fmin(a, smin[w]);
+            b += scnt[w];
+            f = fmax(f, sfl[w]);
+        }
+        out[0] = a;
+        out[1] = b;
+        out[2] = f;
+    }
+}
+
+}  // namespace
+
+wf_status flat_create(wf_plan p)
+{
+    const int n = p->g.nx;
+    if (p->g.ny != n) return set_error(WF_EUNSUPPORTED, "flat grid must be square");
+    if (n < 16 || n > FLAT_MAXN || (n & (n - 1))) return set_error(WF_EUNSUPPORTED, "flat n must be a power of two in [16, 128]");
+    FlatPlan *f = new (std::nothrow) FlatPlan();
+    if (!f) return set_error(WF_ENOMEM, "host allocation");
+    p->flat = f;
+    f->n = n;
+    f->logn = 0;
+    while ((1 << f->logn) < n) ++f->logn;
+    f->nh = n / 2 + 1;
+    f->P = (f->nh + FLAT_CS - 1) / FLAT_CS;
+    f->RP = n / FLAT_CS;
+    p->npix = (long long)n * n;
+    p->nalm = (long long)n * f->nh;
+    p->omega = 1.0;
+    f->smem = (size_t)(n / 2) * 16 + (size_t)f->P * n * 16 * 2 + (size_t)f->RP * f->nh * 16 +
+              (size_t)FLAT_WARPS * n * 16 + (size_t)f->P * n * 8 + (size_t)f->RP * n * 8 * 2;
+    wf_status st;
+    if ((st = plan_alloc(p, (void **)&f->r, p->npix * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&f->nu, p->npix * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&f->levels, 64 * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&f->status, sizeof(FlatStatus))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.redu, 16 * 8)) != WF_OK) return st;
+    WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem));
+    return WF_OK;
+}
+
+void flat_destroy(wf_plan p)
+{
+    delete p->flat;
+    p->flat = nullptr;
+}
+
+static wf_status ensure_trace(wf_plan p, int cap)
+{
+    FlatPlan *f = p->flat;
+    if (f->tr_cap >= cap) return WF_OK;
+    wf_status st;
+    if ((st = plan_alloc(p, (void **)&f->tr_lam, (size_t)cap * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&f->tr_chi2, (size_t)cap * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&f->tr_res, (size_t)cap * 8)) != WF_OK) return st;
+    f->tr_cap = cap;
+    return WF_OK;
+}
+
+wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask, const double *S,
+                     double tol, bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out,
+                     wf_info *info)
+{
+    FlatPlan *f = p->flat;
+    const wf_options o = [&] {
+        wf_options q = p->opt;
+        if (q.maxiter <= 0) q.maxiter = 20000;
+        if (q.level_cap <= 0) q.level_cap = 200;
+        if (!(q.eta > 0)) q.eta = 1e-2;
+        if (!(q.lambda_max > 0)) q.lambda_max = 100.0;
+        return q;
+    }();
+    const int n = f->n, nh = f->nh;
+    Prof pr(p, info, p->opt.profile != 0);
+    pr.count(WF_K_OTHER);
+    k_flat_setup<<<1, 1024, 0, p->stream>>>(p->npix, fluct ? nullptr : d, noise_var, mask, f->r, f->nu, p->ws.redu);
+    WF_CUDA(cudaGetLastError());
+    double h[3];
+    WF_CUDA(cudaMemcpyAsync(h, p->ws.redu, sizeof h, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    if (h[2] != 0.0) return set_error(WF_EINVAL, "noise variance must be finite and > 0 (and d finite) on observed pixels");
+    if (h[1] == 0.0) return set_error(WF_EINVAL, "every pixel is masked");
+    const double tau = h[0];
+    const long long ndof = (long long)h[1];
+
+    // lambda levels: k_iter = 1, 2, 4, ...; lambda = clip(max S on |k| = k_iter / tau, 1, lambda_max)
+    std::vector<double> Sh((size_t)n * nh);
+    WF_CUDA(cudaMemcpy(Sh.data(), S, Sh.size() * 8, cudaMemcpyDeviceToHost));
+    std::vector<double> lev{o.lambda_max};
+    int kmax = 0;
+    std::vector<int> kr(Sh.size());
+    for (int ky = 0; ky < n; ++ky)
+        for (int kx = 0; kx < nh; ++kx) {
+            const int sy = ky < (n + 1) / 2 ? ky : ky - n;
+            const int r = (int)std::lrint(std::sqrt((double)sy * sy + (double)kx * kx));
+            kr[(size_t)ky * nh + kx] = r;
+            kmax = std::max(kmax, r);
+        }
+    for (int kit = 2; lev.back() != 1.0; kit *= 2) {
+        double lam = 1.0;
+        if (kit <= kmax) {
+            double smax = -1.0;
+            for (size_t i = 0; i < Sh.size(); ++i)
+                if (kr[i] == kit) smax = std::max(smax, Sh[i]);
+            if (smax >= 0.0) lam = std::min(o.lambda_max, std::max(1.0, smax / tau));
+        }
+        if (lam != lev.back()) lev.push_back(lam);
+        if ((int)lev.size() >= 60) { lev.push_back(1.0); break; }
+    }
+    WF_CUDA(cudaMemcpyAsync(f->levels, lev.data(), lev.size() * 8, cudaMemcpyHostToDevice, p->stream));
+    const bool replay = !p->replay_lambda.empty();
+    const int nrep = (int)p->replay_lambda.size();
+    if (replay && nrep > f->replay_cap) {
+        wf_status st = plan_alloc(p, (void **)&f->replay, (size_t)nrep * 8);
+        if (st != WF_OK) return st;
+        f->replay_cap = nrep;
+    }
+    if (replay)
+        WF_CUDA(cudaMemcpyAsync(f->replay, p->replay_lambda.data(), nrep * 8, cudaMemcpyHostToDevice, p->stream));
+    const int cap = replay ? nrep : o.maxiter;
+    wf_status st = ensure_trace(p, std::max(cap, 1));
+    if (st != WF_OK) return st;
+
+    FlatArgs A{};
+    A.n = n;
+    A.logn = f->logn;
+    A.nh = nh;
+    A.P = f->P;
+    A.RP = f->RP;
+    A.r = f->r;
+    A.nu = f->nu;
+    A.S = S;
+    A.g1 = fluct ? g1 : nullptr;
+    A.g2 = fluct ? (const double2 *)g2 : nullptr;
+    A.levels = f->levels;
+    A.nlevels = (int)lev.size();
+    A.replay = replay ? f->replay : nullptr;
+    A.nreplay = nrep;
+    A.tau = tau;
+    A.sigma = std::sqrt(2.0 * (double)ndof);
+    A.eta = o.eta;
+    A.tol = tol;
+    A.level_cap = o.level_cap;
+    A.maxiter = o.maxiter;
+    A.s_out = s_out;
+    A.alm_out = (double2 *)alm_out;
+    A.tr_lam = f->tr_lam;
+    A.tr_chi2 = f->tr_chi2;
+    A.tr_res = f->tr_res;
+    A.tr_cap = f->tr_cap;
+    A.status = f->status;
+    pr.begin(WF_K_FLAT);
+    k_flat_solve<<<FLAT_CS, FLAT_THREADS, f->smem, p->stream>>>(A);
+    WF_CUDA(cudaGetLastError());
+    pr.end();
+    FlatStatus fs;
+    WF_CUDA(cudaMemcpyAsync(&fs, f->status, sizeof fs, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    pr.collect();
+    pr.finish();
+    if (info) {
+        info->iters = fs.iters;
+        info->converged = fs.converged;
+        info->final_residual = fs.final_resid;
+        info->chi2_over_ndof = fluct ? NAN : fs.chi2_final / (double)ndof;
+        info->n_dof = ndof;
+        info->tau = tau;
+        info->n_levels = fs.levels;
+        info->refine_sweeps = 0;
+        const int nt = std::min(fs.iters, info->trace_cap);
+        if (nt > 0) {
+            std::vector<double> tl(nt), tc(nt), trs(nt);
+            WF_CUDA(cudaMemcpy(tl.data(), f->tr_lam, nt * 8, cudaMemcpyDeviceToHost));
+            WF_CUDA(cudaMemcpy(tc.data(), f->tr_chi2, nt * 8, cudaMemcpyDeviceToHost));
+            WF_CUDA(cudaMemcpy(trs.data(), f->tr_res, nt * 8, cudaMemcpyDeviceToHost));
+            for (int i = 0; i < nt; ++i) {
+                if (info->lambda_trace) info->lambda_trace[i] = tl[i];
+                if (info->L_trace) info->L_trace[i] = -1;
+                if (info->chi2_trace) info->chi2_trace[i] = tc[i];
+                if (info->resid_trace) info->resid_trace[i] = trs[i];
+            }
+        }
+    }
+    if (fs.stop_reason == 3) return set_error(WF_EDIVERGE, "residual grew (%.3e)", fs.final_resid);
+    if (fs.stop_reason == 2) return set_error(WF_ENOCONV, "iteration cap reached (residual %.3e)", fs.final_resid);
+    return WF_OK;
+}
+
+wf_status flat_alm2map(wf_plan p, const double *alm, double *map)
+{
+    return set_error(WF_EUNSUPPORTED, "flat-grid basis change is internal to the fused solve");
+}
+
+wf_status flat_map2alm(wf_plan p, const double *map, double *alm)
+{
+    return set_error(WF_EUNSUPPORTED, "flat-grid basis change is internal to the fused solve");
+}
+
+}  // namespace wf

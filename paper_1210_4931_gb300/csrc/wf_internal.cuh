@@ -1,0 +1,192 @@
+// Internal declarations of the GB300 messenger-field Wiener filter library.
+//
+// Data layout in HBM (HEALPix):
+//   a_lm      FP64 complex, m-major (index(l,m) = m(2 lmax+3-m)/2 + l-m)
+//   G, F      ring-Fourier coefficients, [pair][m][hemisphere] complex in the
+//             working precision T; pair p couples north ring p with south
+//             ring 4 nside - 2 - p (the equator ring, p = 2 nside - 1, is
+//             alone).  G is written by the Legendre synthesis and read by the
+//             ring pass; F the other way round.
+//   r, nu, t  pixel maps in T (source, inverse noise variance, messenger t)
+//   tables    per alm: recurrence multiplier A and scale c (mu-form, below);
+//             per (m, pair): first active l and two seeds;
+//             per ring length: roots e^{i pi p / n} and Bluestein filters.
+//
+// Legendre recurrence in "mu form": lambda_lm = c_lm mu_lm with
+//   mu_l = A_l x mu_{l-1} - mu_{l-2},
+// which is the textbook three-term recurrence for the normalised associated
+// Legendre functions rescaled so that the l-2 coefficient is one (one
+// multiply and one FMA per step).  c is folded into a_lm on synthesis and
+// applied after the ring sum on analysis.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/wf.h"
+
+namespace wf {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct V2;
+template <> struct V2<double> { using type = double2; };
+template <> struct V2<float> { using type = float2; };
+template <typename T> using cx = typename V2<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.x = a; r.y = b; return r; }
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C, typename S> __host__ __device__ __forceinline__ C cscale(C a, S s) { a.x *= s; a.y *= s; return a; }
+
+// ---------------------------------------------------------------------------
+// ring table (one entry per north/south ring pair)
+// ---------------------------------------------------------------------------
+enum RingKind : int { RING_NAIVE = 0, RING_POW2 = 1, RING_BLUESTEIN = 2 };
+
+struct RingTab {
+    int n;             // pixels in each ring of the pair
+    int q;             // first-pixel longitude is q pi / n (q = 0 or 1)
+    int kind;          // RingKind
+    int logF;          // log2 of the smem FFT length (pow2: n; Bluestein: M/2)
+    long long offN;    // first pixel of the north ring
+    long long offS;    // first pixel of the south ring, -1 for the equator
+    long long rootOff; // offset of e^{i pi p / n}, p < 2n, in the roots table
+    long long vOff;    // offset of the Bluestein filter (M entries: even half, odd half)
+};
+
+constexpr int NAIVE_MAX = 32;   // rings this short use a direct DFT
+constexpr int LEG_THREADS = 256;
+constexpr int RING_THREADS = 512;
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct FlatPlan;  // flat-grid state (wf_flat.cu)
+
+struct Workspace {
+    // HEALPix working buffers; T-typed ones are void* and cast per precision
+    double2 *a = nullptr, *a_new = nullptr, *b = nullptr;
+    void *G = nullptr, *F = nullptr;
+    void *r = nullptr, *nu = nullptr, *t = nullptr;
+    void *scr = nullptr;          // per-CTA Bluestein scratch (2 * max Bluestein n complex per CTA)
+    double *part_pix = nullptr;   // per ring-CTA partial sums
+    double *part_harm = nullptr;  // per m: [chi2_h, resid^2]
+    double *scal = nullptr;       // reduced scalars (device)
+    double *h_scal = nullptr;     // pinned host mirror
+    double *d_in = nullptr, *nv_in = nullptr, *out_map = nullptr, *cl_in = nullptr, *alm_io = nullptr;  // host-API staging
+    uint8_t *mask_in = nullptr;
+    double *g1_in = nullptr, *g2_in = nullptr;
+    int *flag = nullptr;          // device flags (invalid input)
+    double *redu = nullptr;       // reduction scratch
+};
+
+struct HpTables {
+    RingTab *rings = nullptr;
+    void *roots = nullptr, *V = nullptr, *tw = nullptr;  // T-typed complex
+    void *A = nullptr, *c = nullptr;                     // T-typed per alm
+    double *c64 = nullptr;                               // FP64 scale per alm (epilogue)
+    int *ls = nullptr;                                   // [m][pair]
+    void *s0 = nullptr, *s1 = nullptr;                   // T-typed seeds [m][pair]
+    void *x = nullptr;                                   // T-typed cos(theta) per pair
+    int logNmax = 0;       // twiddle table is e^{-2 pi i t / 2^logNmax}, t < 2^(logNmax-1)
+    int bmax = 0;          // smem FFT buffer length (complex entries)
+    int maxBlue = 0;       // longest Bluestein ring
+    int ringGrid = 0;      // persistent grid of the ring kernels
+};
+
+}  // namespace wf
+
+struct wf_plan_s {
+    wf_geometry g{};
+    int lmax = 0;
+    wf_precision prec = WF_PREC_FP64;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nsm = 0;
+    long long npix = 0, nalm = 0;
+    int nside = 0, nrings = 0, npairs = 0;
+    double omega = 0;
+    wf::HpTables tab;
+    wf::Workspace ws;
+    wf::FlatPlan *flat = nullptr;
+    wf_options opt{};
+    std::vector<double> replay_lambda;
+    std::vector<int> replay_L;
+    long long device_bytes = 0;
+    std::vector<void *> allocations;
+    cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
+    bool events_ready = false;
+};
+
+namespace wf {
+
+// error reporting (wf_api.cu)
+wf_status set_error(wf_status s, const char *fmt, ...);
+wf_status cuda_check(cudaError_t e, const char *what);
+#define WF_CUDA(call)                                                          \
+    do {                                                                       \
+        cudaError_t _e = (call);                                               \
+        if (_e != cudaSuccess) return ::wf::cuda_check(_e, #call);             \
+    } while (0)
+
+// device allocation owned by the plan
+wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes);
+
+// Per-call kernel accounting: launch counts always; device time per kernel
+// family with CUDA events on the plan's stream when profiling is on.
+struct Prof {
+    wf_plan p;
+    wf_info *info;
+    bool on;
+    int nopen = 0;
+    int fam[16];
+    long long launches = 0;
+    double ms[WF_NK] = {};
+    long long cnt[WF_NK] = {};
+    Prof(wf_plan p_, wf_info *i, bool profile);
+    void begin(int family);  // call before a launch of `family`
+    void end();              // call after it
+    void count(int family, int n = 1) { cnt[family] += n; launches += n; }
+    void collect();          // after a stream synchronisation: harvest event times
+    void iter_begin();
+    double iter_end();       // after a synchronisation: ms since iter_begin (NaN when off)
+    void finish();           // copy into info
+};
+
+// Legendre transforms (wf_legendre.cu)
+wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, const std::vector<double> &stpair);
+enum LegMode { LEG_ADJOINT = 0, LEG_BLEND = 1 };
+struct BlendArgs {
+    double lam_tauh = 0;   // lambda tau Omega
+    double tauh = 0;       // tau Omega
+    const double *S = nullptr;  // C_ell (device)
+    int want_resid = 0;
+};
+wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L);
+wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old,
+                               double2 *out);
+
+// ring transforms (wf_ring.cu)
+wf_status hp_build_ring_tables(wf_plan p);
+enum RingSynMode { RS_BLEND = 0, RS_MAP = 1 };
+wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *out_map);
+wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T);
+
+// flat grid (wf_flat.cu)
+wf_status flat_create(wf_plan p);
+void flat_destroy(wf_plan p);
+wf_status flat_solve(wf_plan p, const double *r_or_d, const double *noise_var, const uint8_t *mask,
+                     const double *S, double tol, bool fluct, const double *g1, const double *g2, double *s_out,
+                     double *alm_out, wf_info *info);
+wf_status flat_alm2map(wf_plan p, const double *alm, double *map);
+wf_status flat_map2alm(wf_plan p, const double *map, double *alm);
+
+}  // namespace wf

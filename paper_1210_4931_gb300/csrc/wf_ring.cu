@@ -1,0 +1,482 @@
+// Ring part of the HEALPix basis change (Sect. 2.1 / Sect. 3) and the
+// pixel-space blend of Eq. (3), fused into the synthesis side.
+//
+// Each HEALPix ring r has n_r equally spaced pixels at longitudes
+// phi_j = (2j + q) pi / n_r.  Synthesis on a ring is
+//     f_j = sum_{m=-L..L} G_m e^{i m phi_j}      (G_{-m} = conj G_m)
+//         = sum_{k<n} H_k e^{2 pi i k j / n},   H_k = sum_{m = k mod n} G_m e^{i pi m q / n},
+// an inverse DFT of the folded coefficients H; analysis is the forward DFT
+// F_m = e^{-i pi m q / n} DFT(f)[m mod n].  The north and south rings of a
+// pair have the same n and q, so both are packed into one complex DFT
+// (z = f_N + i f_S).
+//
+// DFT engines, chosen per ring length at plan time:
+//   n <= 32            direct sum from shared memory;
+//   n a power of two   in-place radix-2 FFT in shared memory;
+//   otherwise          Bluestein: X_k = c_k sum_j (x_j c_j) conj(c_{k-j}),
+//                      c_j = e^{-i pi j^2 / n}, a circular convolution of
+//                      power-of-two length M >= 2n - 1.  Since the input is
+//                      zero beyond n <= M/2, the length-M transforms split
+//                      into two independent half-length ones (even and odd
+//                      outputs), so the shared buffer holds M/2 values and
+//                      the per-CTA global scratch holds the input and the
+//                      even-half result.
+//
+// Pixel blend (Eq. 3 solved for t with nu = N^-1, r = nu d):
+//     t = s + lambda tau (r - nu s) / (1 + (lambda - 1) tau nu)
+// and the pixel term of chi^2 (Eq. 6, x-independent part dropped):
+//     sum (nu s^2 - 2 r s) / (1 + (lambda - 1) tau nu).
+#include <cmath>
+#include <cstdio>
+#include <map>
+
+#include "wf_internal.cuh"
+
+namespace wf {
+
+namespace {
+
+int ilog2(long long v)
+{
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// host radix-2 FFT (FP64), forward e^{-2 pi i jk / n}; used once per ring
+// length to tabulate the Bluestein filters
+void host_fft(std::vector<double2> &x)
+{
+    const size_t n = x.size();
+    const int lg = ilog2((long long)n);
+    for (size_t i = 0; i < n; ++i) {
+        size_t j = 0;
+        for (int b = 0; b < lg; ++b)
+            if (i & (1ull << b)) j |= 1ull << (lg - 1 - b);
+        if (i < j) std::swap(x[i], x[j]);
+    }
+    for (size_t half = 1; half < n; half <<= 1) {
+        for (size_t pos = 0; pos < half; ++pos) {
+            const double ang = -M_PI * (double)pos / (double)half;
+            const double2 w = make_double2(std::cos(ang), std::sin(ang));
+            for (size_t i0 = pos; i0 < n; i0 += 2 * half) {
+                const size_t i1 = i0 + half;
+                const double2 u = x[i0], v = cmul(x[i1], w);
+                x[i0] = cadd(u, v);
+                x[i1] = csub(u, v);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// device FFT helpers
+// ---------------------------------------------------------------------------
+// In-place radix-2 DIT FFT of length 2^logN in shared memory, all threads of
+// the CTA.  sign -1: e^{-2 pi i jk/N}; +1: e^{+2 pi i jk/N} (unnormalised).
+// tw[t] = e^{-2 pi i t / 2^logNmax}, t < 2^(logNmax-1).
+template <typename T>
+__device__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *__restrict__ tw, int logNmax)
+{
+    const int N = 1 << logN;
+    if (logN == 0) return;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int j = (int)(__brev((unsigned)i) >> (32 - logN));
+        if (i < j) {
+            const cx<T> a = x[i];
+            x[i] = x[j];
+            x[j] = a;
+        }
+    }
+    __syncthreads();
+    for (int s = 1; s <= logN; ++s) {
+        const int half = 1 << (s - 1);
+        const int tsh = logNmax - s;
+        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
+            const int pos = b & (half - 1);
+            const int i0 = ((b >> (s - 1)) << s) + pos;
+            const int i1 = i0 + half;
+            cx<T> w = tw[pos << tsh];
+            if (sign > 0) w.y = -w.y;
+            const cx<T> u = x[i0], v = cmul(x[i1], w);
+            x[i0] = cadd(u, v);
+            x[i1] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+// DFT of one ring pair.  Input: in smem buf (naive / pow2) or in zin (Bluestein).
+// Returns a pointer to the n outputs.
+template <typename T>
+__device__ cx<T> *ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout, int sign,
+                           const cx<T> *__restrict__ roots, const cx<T> *__restrict__ V,
+                           const cx<T> *__restrict__ tw, int logNmax)
+{
+    const int n = R.n;
+    const int twon = 2 * n;
+    const cx<T> *root = roots + R.rootOff;
+    if (R.kind == RING_NAIVE) {
+        cx<T> *out = buf + n;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            cx<T> acc = mk<T>(0, 0);
+            for (int k = 0; k < n; ++k) {
+                cx<T> w = root[(2LL * j * k) % twon];
+                if (sign < 0) w.y = -w.y;
+                acc = cadd(acc, cmul(buf[k], w));
+            }
+            out[j] = acc;
+        }
+        __syncthreads();
+        return out;
+    }
+    if (R.kind == RING_POW2) {
+        fft_pow2<T>(buf, R.logF, sign, tw, logNmax);
+        return buf;
+    }
+    // Bluestein, two half-length passes
+    const int H = 1 << R.logF;           // M / 2
+    const int mstep = logNmax - (R.logF + 1);  // index step of w_M in tw
+    const cx<T> *Vh = V + R.vOff;
+    for (int h = 0; h < 2; ++h) {
+        for (int j = threadIdx.x; j < H; j += blockDim.x) {
+            cx<T> v = mk<T>(0, 0);
+            if (j < n) {
+                cx<T> u = zin[j];
+                if (sign > 0) u.y = -u.y;
+                cx<T> c = root[((long long)j * j) % twon];
+                c.y = -c.y;  // e^{-i pi j^2 / n}
+                v = cmul(u, c);
+                if (h) v = cmul(v, tw[(long long)j << mstep]);
+            }
+            buf[j] = v;
+        }
+        __syncthreads();
+        fft_pow2<T>(buf, R.logF, -1, tw, logNmax);
+        for (int k = threadIdx.x; k < H; k += blockDim.x) buf[k] = cmul(buf[k], Vh[h * H + k]);
+        __syncthreads();
+        fft_pow2<T>(buf, R.logF, +1, tw, logNmax);
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            if (h == 0) {
+                zout[k] = buf[k];
+            } else {
+                cx<T> w = tw[(long long)k << mstep];
+                w.y = -w.y;  // w_M^{-k}
+                cx<T> c = root[((long long)k * k) % twon];
+                c.y = -c.y;
+                cx<T> y = cmul(cadd(zout[k], cmul(buf[k], w)), c);
+                if (sign > 0) y.y = -y.y;
+                zout[k] = y;
+            }
+        }
+        __syncthreads();
+    }
+    return zout;
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+struct RingCommon {
+    int npairs, lmax, L, logNmax;
+    const RingTab *rings;
+    long long scr_stride;
+};
+
+// ---------------------------------------------------------------------------
+// synthesis side: fold -> inverse ring DFT -> blend (or write the map)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(RING_THREADS) k_ringsyn(RingCommon rc, const cx<T> *__restrict__ roots,
+                                                          const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
+                                                          cx<T> *__restrict__ scr, const cx<T> *__restrict__ G,
+                                                          int mode, const T *__restrict__ r, const T *__restrict__ nu,
+                                                          T lam, T tau, T *__restrict__ tmap,
+                                                          double *__restrict__ omap, double *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[RING_THREADS / 32];
+    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *zin = scr + (size_t)blockIdx.x * rc.scr_stride;
+    cx<T> *zout = zin + rc.scr_stride / 2;
+    const int L = rc.L;
+    const T lt = lam * tau, lm1t = (lam - (T)1) * tau;
+    double chi = 0.0;
+    for (int it = blockIdx.x; it < rc.npairs; it += gridDim.x) {
+        const int pair = rc.npairs - 1 - it;
+        const RingTab R = rc.rings[pair];
+        const int n = R.n, q = R.q, twon = 2 * n;
+        const cx<T> *root = roots + R.rootOff;
+        const cx<T> *g = G + (size_t)pair * (rc.lmax + 1) * 2;
+        cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
+        const bool south = R.offS >= 0;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            cx<T> hn = mk<T>(0, 0), hs = mk<T>(0, 0);
+            for (int m = k; m <= L; m += n) {
+                const cx<T> ph = root[q ? (m % twon) : 0];
+                hn = cadd(hn, cmul(g[2 * m], ph));
+                hs = cadd(hs, cmul(g[2 * m + 1], ph));
+            }
+            for (int m = (k == 0 ? n : n - k); m <= L; m += n) {
+                const cx<T> ph = root[q ? (m % twon) : 0];
+                hn = cadd(hn, cconj(cmul(g[2 * m], ph)));
+                hs = cadd(hs, cconj(cmul(g[2 * m + 1], ph)));
+            }
+            if (!south) hs = mk<T>(0, 0);
+            in[k] = mk<T>(hn.x - hs.y, hn.y + hs.x);
+        }
+        __syncthreads();
+        const cx<T> *z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const cx<T> zz = z[j];
+            const long long iN = R.offN + j;
+            if (mode == RS_MAP) {
+                omap[iN] = (double)zz.x;
+                if (south) omap[R.offS + j] = (double)zz.y;
+            } else {
+                {
+                    const T s = zz.x, nv = nu[iN], rv = r[iN];
+                    const T den = (T)1 + lm1t * nv;
+                    tmap[iN] = s + lt * (rv - nv * s) / den;
+                    chi += (double)((nv * s * s - (T)2 * rv * s) / den);
+                }
+                if (south) {
+                    const long long iS = R.offS + j;
+                    const T s = zz.y, nv = nu[iS], rv = r[iS];
+                    const T den = (T)1 + lm1t * nv;
+                    tmap[iS] = s + lt * (rv - nv * s) / den;
+                    chi += (double)((nv * s * s - (T)2 * rv * s) / den);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (mode == RS_BLEND) {
+        const double s = block_sum<T>(chi, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// analysis side: pack -> forward ring DFT -> unfold to F_m, m <= L
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(RING_THREADS) k_ringana(RingCommon rc, const cx<T> *__restrict__ roots,
+                                                          const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
+                                                          cx<T> *__restrict__ scr, const T *__restrict__ map,
+                                                          cx<T> *__restrict__ F)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
+    cx<T> *zin = scr + (size_t)blockIdx.x * rc.scr_stride;
+    cx<T> *zout = zin + rc.scr_stride / 2;
+    const int L = rc.L;
+    for (int it = blockIdx.x; it < rc.npairs; it += gridDim.x) {
+        const int pair = rc.npairs - 1 - it;
+        const RingTab R = rc.rings[pair];
+        const int n = R.n, q = R.q, twon = 2 * n;
+        const cx<T> *root = roots + R.rootOff;
+        cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
+        const bool south = R.offS >= 0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            in[j] = mk<T>(map[R.offN + j], south ? map[R.offS + j] : (T)0);
+        __syncthreads();
+        const cx<T> *z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax);
+        cx<T> *f = F + (size_t)pair * (rc.lmax + 1) * 2;
+        for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+            const int k = m % n;
+            const int nk = (n - k) % n;
+            const cx<T> zk = z[k], znk = z[nk];
+            const cx<T> tn = mk<T>((T)0.5 * (zk.x + znk.x), (T)0.5 * (zk.y - znk.y));
+            const cx<T> ts = mk<T>((T)0.5 * (zk.y + znk.y), (T)-0.5 * (zk.x - znk.x));
+            cx<T> ph = root[q ? (m % twon) : 0];
+            ph.y = -ph.y;
+            f[2 * m] = cmul(ph, tn);
+            f[2 * m + 1] = south ? cmul(ph, ts) : mk<T>(0, 0);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T> struct RingLaunch {
+    static wf_status syn(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *omap)
+    {
+        const HpTables &t = p->tab;
+        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue};
+        const size_t sm = (size_t)t.bmax * sizeof(cx<T>);
+        WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
+            rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
+            (const cx<T> *)p->ws.G, (int)mode, (const T *)p->ws.r, (const T *)p->ws.nu, (T)lam, (T)tau,
+            (T *)p->ws.t, omap, p->ws.part_pix);
+        WF_CUDA(cudaGetLastError());
+        return WF_OK;
+    }
+    static wf_status ana(wf_plan p, int L, const void *map)
+    {
+        const HpTables &t = p->tab;
+        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue};
+        const size_t sm = (size_t)t.bmax * sizeof(cx<T>);
+        WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_ringana<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
+                                                                  (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
+                                                                  (const T *)map, (cx<T> *)p->ws.F);
+        WF_CUDA(cudaGetLastError());
+        return WF_OK;
+    }
+    static wf_status grid(wf_plan p, int *out)
+    {
+        const size_t sm = (size_t)p->tab.bmax * sizeof(cx<T>);
+        WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int b1 = 0, b2 = 0;
+        WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_ringsyn<T>, RING_THREADS, sm));
+        WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_ringana<T>, RING_THREADS, sm));
+        int b = b1 < b2 ? b1 : b2;
+        if (b < 1) return set_error(WF_EUNSUPPORTED, "ring kernel does not fit on an SM (smem %zu bytes)", sm);
+        long long g = (long long)b * p->nsm;
+        if (g > p->npairs) g = p->npairs;
+        *out = (int)g;
+        return WF_OK;
+    }
+};
+
+template <typename T>
+wf_status upload_cx(wf_plan p, void **dst, const std::vector<double2> &src)
+{
+    wf_status st = plan_alloc(p, dst, src.size() * sizeof(cx<T>) + 16);
+    if (st != WF_OK) return st;
+    std::vector<cx<T>> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = mk<T>((T)src[i].x, (T)src[i].y);
+    WF_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    return WF_OK;
+}
+
+}  // namespace
+
+wf_status hp_build_ring_tables(wf_plan p)
+{
+    const int nside = p->nside, np = p->npairs;
+    const int R = 4 * nside - 1;
+    // ring offsets (RING order)
+    std::vector<long long> off(R + 1, 0);
+    std::vector<int> nr(R), qr(R);
+    for (int i = 1; i <= R; ++i) {
+        const int k = (i <= 2 * nside) ? i : 4 * nside - i;
+        if (k < nside) {
+            nr[i - 1] = 4 * k;
+            qr[i - 1] = 1;
+        } else {
+            nr[i - 1] = 4 * nside;
+            qr[i - 1] = ((i + nside) & 1) ? 0 : 1;
+        }
+        off[i] = off[i - 1] + nr[i - 1];
+    }
+    std::vector<RingTab> rt(np);
+    std::map<int, long long> rootOff, vOff;
+    std::vector<double2> roots, Vtab;
+    long long nmaxF = 2;  // largest full FFT length (pow2 n or Bluestein M)
+    int bmax = 2 * NAIVE_MAX, maxBlue = 1;
+    for (int pr = 0; pr < np; ++pr) {
+        RingTab &t = rt[pr];
+        const int i0 = pr;  // north ring, 0-based
+        t.n = nr[i0];
+        t.q = qr[i0];
+        t.offN = off[i0];
+        t.offS = (pr < np - 1) ? off[R - 1 - pr] : -1;
+        const int n = t.n;
+        if (!rootOff.count(n)) {
+            rootOff[n] = (long long)roots.size();
+            for (int q = 0; q < 2 * n; ++q) {
+                const double a = M_PI * (double)q / (double)n;
+                roots.push_back(make_double2(std::cos(a), std::sin(a)));
+            }
+        }
+        t.rootOff = rootOff[n];
+        t.vOff = 0;
+        if (n <= NAIVE_MAX) {
+            t.kind = RING_NAIVE;
+            t.logF = 0;
+        } else if (is_pow2(n)) {
+            t.kind = RING_POW2;
+            t.logF = ilog2(n);
+            if (n > nmaxF) nmaxF = n;
+            if (n > bmax) bmax = n;
+        } else {
+            t.kind = RING_BLUESTEIN;
+            const int lgM = ilog2(2LL * n - 1);
+            const long long M = 1LL << lgM;
+            t.logF = lgM - 1;
+            if (M > nmaxF) nmaxF = M;
+            if (M / 2 > bmax) bmax = (int)(M / 2);
+            if (n > maxBlue) maxBlue = n;
+            if (!vOff.count(n)) {
+                vOff[n] = (long long)Vtab.size();
+                std::vector<double2> v(M, make_double2(0.0, 0.0));
+                for (long long j = 0; j < n; ++j) {
+                    const long long e = (j * j) % (2LL * n);
+                    const double a = M_PI * (double)e / (double)n;  // conj(c_j) = e^{+i pi j^2 / n}
+                    v[j] = make_double2(std::cos(a), std::sin(a));
+                    if (j > 0) v[M - j] = v[j];
+                }
+                host_fft(v);
+                for (long long k = 0; k < M / 2; ++k) Vtab.push_back(cscale(v[2 * k], 1.0 / (double)M));
+                for (long long k = 0; k < M / 2; ++k) Vtab.push_back(cscale(v[2 * k + 1], 1.0 / (double)M));
+            }
+            t.vOff = vOff[n];
+        }
+    }
+    const int logNmax = ilog2(nmaxF);
+    std::vector<double2> tw((size_t)1 << (logNmax - 1));
+    for (size_t t = 0; t < tw.size(); ++t) {
+        const double a = -2.0 * M_PI * (double)t / (double)(1LL << logNmax);
+        tw[t] = make_double2(std::cos(a), std::sin(a));
+    }
+    if (Vtab.empty()) Vtab.push_back(make_double2(0, 0));
+    p->tab.logNmax = logNmax;
+    p->tab.bmax = bmax;
+    p->tab.maxBlue = maxBlue;
+    wf_status st;
+    if ((st = plan_alloc(p, (void **)&p->tab.rings, rt.size() * sizeof(RingTab))) != WF_OK) return st;
+    WF_CUDA(cudaMemcpy(p->tab.rings, rt.data(), rt.size() * sizeof(RingTab), cudaMemcpyHostToDevice));
+    const bool f32 = p->prec != WF_PREC_FP64;
+    if (f32) {
+        if ((st = upload_cx<float>(p, &p->tab.roots, roots)) != WF_OK) return st;
+        if ((st = upload_cx<float>(p, &p->tab.V, Vtab)) != WF_OK) return st;
+        if ((st = upload_cx<float>(p, &p->tab.tw, tw)) != WF_OK) return st;
+        if ((st = RingLaunch<float>::grid(p, &p->tab.ringGrid)) != WF_OK) return st;
+    } else {
+        if ((st = upload_cx<double>(p, &p->tab.roots, roots)) != WF_OK) return st;
+        if ((st = upload_cx<double>(p, &p->tab.V, Vtab)) != WF_OK) return st;
+        if ((st = upload_cx<double>(p, &p->tab.tw, tw)) != WF_OK) return st;
+        if ((st = RingLaunch<double>::grid(p, &p->tab.ringGrid)) != WF_OK) return st;
+    }
+    const size_t es = f32 ? sizeof(float2) : sizeof(double2);
+    return plan_alloc(p, &p->ws.scr, (size_t)p->tab.ringGrid * 2 * maxBlue * es + 16);
+}
+
+wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *out_map)
+{
+    return p->prec == WF_PREC_FP64 ? RingLaunch<double>::syn(p, L, mode, lam, tau, out_map)
+                                   : RingLaunch<float>::syn(p, L, mode, lam, tau, out_map);
+}
+
+wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T)
+{
+    return p->prec == WF_PREC_FP64 ? RingLaunch<double>::ana(p, L, map_T) : RingLaunch<float>::ana(p, L, map_T);
+}
+
+}  // namespace wf

@@ -1,0 +1,200 @@
+"""GPU path vs the oracle, element by element, through the C ABI.
+
+FP64 mode must match within 1e-10 relative (schedule replay: the oracle
+re-runs the GPU's own lambda/L trace).  Sizes span all three ring-DFT
+engines (direct, power-of-two FFT, Bluestein) and several Legendre tiles."""
+import numpy as np
+import pytest
+
+import oracle
+import wf_inputs as gen
+from gpu_util import T, healpix_case, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    import torch
+
+    import paper_1210_4931_gb300 as w
+
+    w.load()
+    torch.cuda.set_device(0)
+    return w
+
+
+def _random_alm(lmax, rng, cl=None):
+    g = gen.alm_unit_gaussian(rng, lmax)
+    if cl is not None:
+        g = g * np.sqrt(cl[gen.alm_ell(lmax)])
+    return g
+
+
+@pytest.mark.parametrize("nside,lmax", [(2, 4), (4, 8), (8, 16), (16, 32), (32, 64), (64, 128), (64, 100)])
+def test_basis_change_matches_oracle(wf, nside, lmax):
+    import torch
+
+    rng = np.random.default_rng(nside * 1000 + lmax)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64")
+    a = _random_alm(lmax, rng)
+    m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    for L in (lmax, lmax // 2 + 1):
+        wf.wf_alm2map(plan, T(a), L, m)
+        assert rel(m.cpu().numpy(), oracle.synthesis(nside, lmax, L, a)) < 1e-12
+    f = rng.standard_normal(plan.npix)
+    out = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+    for L in (lmax, lmax // 2 + 1):
+        wf.wf_map2alm_adjoint(plan, T(f), L, out)
+        assert rel(out.cpu().numpy(), oracle.adjoint_synthesis(nside, lmax, L, f)) < 1e-12
+    plan.close()
+
+
+@pytest.mark.parametrize("nside,lmax", [(8, 16), (16, 32), (32, 64)])
+def test_healpix_solve_fp64_matches_oracle_replay(wf, nside, lmax):
+    import torch
+
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 100 + nside))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64")
+    s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    alm = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+    rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-7, s, alm, trace_cap=20000)
+    assert rep["converged"] and rep["final_residual"] < 1e-7
+    lam = rep["lambda_trace"]
+    assert lam[0] >= 1.0 and lam[-1] == 1.0 and np.all(np.diff(lam) <= 0)
+    if nside >= 32:
+        assert lam[0] > 1.0  # the prior at l_iter = 20 is above T: cooling starts high
+    replay = list(zip(lam, rep["L_trace"]))
+    ref = oracle.messenger_solve(basis, nu * d, nu, basis.per_mode(P["c_ell"]), tau, replay=replay, d=d)
+    assert rel(alm.cpu().numpy(), ref["a"]) < 1e-10
+    assert rel(s.cpu().numpy(), ref["s"]) < 1e-10
+    np.testing.assert_allclose(rep["chi2_trace"], ref["chi2"], rtol=1e-10, atol=1e-10 * np.max(np.abs(ref["chi2"])))
+    fin = ~np.isnan(ref["resid"])
+    np.testing.assert_allclose(rep["resid_trace"][fin], ref["resid"][fin], rtol=1e-7)
+    assert rep["chi2_over_ndof"] == pytest.approx(ref["chi2_final"] / ref["n_dof"], rel=1e-10)
+    assert rep["tau"] == tau
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [16, 32, 128])
+def test_flat_solve_fp64_matches_oracle_replay(wf, n):
+    import torch
+
+    P = gen.flat_problem(n, seed=gen.seed_for(1, n)) if n == 128 else gen.flat_problem(
+        n, seed=gen.seed_for(1, n), band_rows=(n // 2 - 2, n // 2 + 2), n_disks=3, disk_radius=2.0)
+    B = oracle.FlatBasis(n, n)
+    d = B.synth(P["a_signal"]) + P["noise"]
+    obs = P["mask"] > 0
+    nu = np.where(obs, 1.0 / P["noise_var"], 0.0)
+    tau = float(P["noise_var"][obs].min())
+    plan = wf.wf_plan_create("flat", n=n, precision="fp64")
+    s = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    alm = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+    rep = wf.wf_solve(plan, T(d.ravel()), T(P["noise_var"].ravel()), T(P["mask"].ravel()), T(P["S"].ravel()), 1e-6,
+                      s, alm, trace_cap=20000)
+    assert rep["converged"] and rep["final_residual"] < 1e-6
+    lam = rep["lambda_trace"]
+    assert lam[0] == 100.0 and lam[-1] == 1.0
+    ref = oracle.messenger_solve(B, nu * d, nu, P["S"], tau, replay=[(l, None) for l in lam], d=d)
+    assert rel(s.cpu().numpy().reshape(n, n), ref["s"]) < 1e-10
+    assert rel(alm.cpu().numpy().reshape(n, n // 2 + 1), ref["a"]) < 1e-10
+    fin = ~np.isnan(ref["resid"])
+    np.testing.assert_allclose(rep["resid_trace"][fin], ref["resid"][fin], rtol=1e-7)
+    assert rep["chi2_over_ndof"] == pytest.approx(ref["chi2_final"] / ref["n_dof"], rel=1e-10)
+    plan.close()
+
+
+def test_flat_fluct_matches_oracle(wf):
+    import torch
+
+    n = 32
+    P = gen.flat_problem(n, seed=gen.seed_for(1, 7), band_rows=(14, 18), n_disks=3, disk_radius=2.0)
+    B = oracle.FlatBasis(n, n)
+    obs = P["mask"] > 0
+    nu = np.where(obs, 1.0 / P["noise_var"], 0.0)
+    tau = float(P["noise_var"][obs].min())
+    plan = wf.wf_plan_create("flat", n=n)
+    f = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    rep = wf.wf_fluct(plan, T(P["noise_var"].ravel()), T(P["mask"].ravel()), T(P["S"].ravel()),
+                      T(P["g1"].ravel()), T(P["g2"].ravel()), 1e-6, f, trace_cap=20000)
+    assert rep["converged"]
+    r = oracle.fluct_source(B, nu, P["S"], P["g1"], P["g2"])
+    ref = oracle.messenger_solve(B, r, nu, P["S"], tau, replay=[(l, None) for l in rep["lambda_trace"]])
+    assert rel(f.cpu().numpy().reshape(n, n), ref["s"]) < 1e-10
+    plan.close()
+
+
+def test_healpix_fluct_matches_oracle(wf):
+    import torch
+
+    nside, lmax = 16, 32
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 300))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax)
+    f = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    rep = wf.wf_fluct(plan, T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), T(P["g1"]), T(P["g2"]), 1e-7, f,
+                      trace_cap=20000)
+    assert rep["converged"]
+    S = basis.per_mode(P["c_ell"])
+    r = oracle.fluct_source(basis, nu, S, P["g1"], P["g2"])
+    ref = oracle.messenger_solve(basis, r, nu, S, tau, replay=list(zip(rep["lambda_trace"], rep["L_trace"])))
+    assert rel(f.cpu().numpy(), ref["s"]) < 1e-10
+    plan.close()
+
+
+def test_invalid_inputs_are_rejected(wf):
+    import torch
+
+    nside, lmax = 8, 16
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 5))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax)
+    s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    bad = P["noise_var"].copy()
+    bad[np.nonzero(P["mask"])[0][3]] = np.nan
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d), T(bad), T(P["mask"]), T(P["c_ell"]), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    bad = P["noise_var"].copy()
+    bad[np.nonzero(P["mask"])[0][0]] = -1.0
+    with pytest.raises(wf.WfError):
+        wf.wf_solve(plan, T(d), T(bad), T(P["mask"]), T(P["c_ell"]), 1e-6, s)
+    with pytest.raises(wf.WfError):
+        wf.wf_solve(plan, T(d), T(P["noise_var"]), T(np.zeros_like(P["mask"])), T(P["c_ell"]), 1e-6, s)
+    # masked pixels may hold anything, including NaN noise
+    nv = P["noise_var"].copy()
+    nv[P["mask"] == 0] = np.nan
+    rep = wf.wf_solve(plan, T(d), T(nv), T(P["mask"]), T(P["c_ell"]), 1e-6, s)
+    assert rep["converged"]
+    with pytest.raises(wf.WfError):
+        wf.wf_plan_create("healpix", nside=8, lmax=17)
+    plan.close()
+
+
+def test_no_mask_pointer_means_all_observed(wf):
+    import torch
+
+    nside, lmax = 8, 16
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 6), masked=False)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax)
+    s1 = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    s2 = torch.empty_like(s1)
+    r1 = wf.wf_solve(plan, T(d), T(P["noise_var"]), None, T(P["c_ell"]), 1e-8, s1)
+    r2 = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-8, s2)
+    assert r1["iters"] == r2["iters"]
+    assert rel(s1.cpu().numpy(), s2.cpu().numpy()) < 1e-14
+    plan.close()
+
+
+def test_host_entry_point_matches_device(wf):
+    import torch
+
+    nside, lmax = 16, 32
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 8))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax)
+    s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-7, s)
+    sh = np.empty(plan.npix)
+    ah = np.empty(plan.nalm, dtype=np.complex128)
+    rep = wf.wf_solve_host(plan, d, P["noise_var"], P["mask"], P["c_ell"], 1e-7, sh, ah)
+    assert rep["converged"]
+    assert rel(sh, s.cpu().numpy()) < 1e-13
+    plan.close()
