@@ -83,6 +83,8 @@ typedef struct {
     double lambda_max;  /* flat: first lambda level (100) */
     int refine_sweeps;  /* mixed precision: max FP64 correction sweeps (3) */
     int profile;        /* nonzero: time every kernel family with CUDA events (fills wf_info.kernel_ms) */
+    double mixed_kappa; /* mixed precision: modes with S_l / (tau Omega) >= kappa run in FP64 (3e4) */
+    int mixed_lc;       /* mixed precision: > 0 forces the FP64 block l < mixed_lc, < 0 disables it, 0 = auto */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one
@@ -108,6 +110,7 @@ typedef struct {
     double tau;             /* min noise variance over observed pixels */
     int n_levels;           /* lambda levels visited */
     int refine_sweeps;      /* FP64 correction sweeps run (mixed precision) */
+    int mixed_lc;           /* FP64 block l < mixed_lc used by the mixed-precision transforms */
     double *lambda_trace;   /* optional, lambda_k */
     int *L_trace;           /* optional, band limit L_k (HEALPix; -1 on the flat grid) */
     double *chi2_trace;     /* optional, chi^2 of the iterate entering iteration k (Eq. 6, x-independent part dropped) */
@@ -172,6 +175,7 @@ long long wf_plan_device_bytes(wf_plan p);
 
 const char *wf_strerror(wf_status s);
 const char *wf_last_error(void);
+
 
 #ifdef __cplusplus
 }

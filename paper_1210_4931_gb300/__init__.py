@@ -37,13 +37,14 @@ class wf_geometry(ctypes.Structure):
 class wf_options(ctypes.Structure):
     _fields_ = [("maxiter", ctypes.c_int), ("level_cap", ctypes.c_int), ("eta", ctypes.c_double),
                 ("ell0", ctypes.c_int), ("ell_step_max", ctypes.c_int), ("band_margin", ctypes.c_int),
-                ("lambda_max", ctypes.c_double), ("refine_sweeps", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("lambda_max", ctypes.c_double), ("refine_sweeps", ctypes.c_int), ("profile", ctypes.c_int),
+                ("mixed_kappa", ctypes.c_double), ("mixed_lc", ctypes.c_int)]
 
 
 class wf_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("final_residual", ctypes.c_double),
                 ("chi2_over_ndof", ctypes.c_double), ("n_dof", ctypes.c_longlong), ("tau", ctypes.c_double),
-                ("n_levels", ctypes.c_int), ("refine_sweeps", ctypes.c_int),
+                ("n_levels", ctypes.c_int), ("refine_sweeps", ctypes.c_int), ("mixed_lc", ctypes.c_int),
                 ("lambda_trace", ctypes.POINTER(ctypes.c_double)), ("L_trace", ctypes.POINTER(ctypes.c_int)),
                 ("chi2_trace", ctypes.POINTER(ctypes.c_double)), ("resid_trace", ctypes.POINTER(ctypes.c_double)),
                 ("iter_ms_trace", ctypes.POINTER(ctypes.c_double)), ("trace_cap", ctypes.c_int),
@@ -207,7 +208,8 @@ def _info_dict(st, info, bufs):
     k = info.iters
     out = {"status": st, "iters": k, "converged": bool(info.converged), "final_residual": info.final_residual,
            "chi2_over_ndof": info.chi2_over_ndof, "n_dof": info.n_dof, "tau": info.tau,
-           "n_levels": info.n_levels, "refine_sweeps": info.refine_sweeps, "launches": info.launches,
+           "n_levels": info.n_levels, "refine_sweeps": info.refine_sweeps, "mixed_lc": info.mixed_lc,
+           "launches": info.launches,
            "kernel_ms": {f: info.kernel_ms[i] for i, f in enumerate(KERNEL_FAMILIES)},
            "kernel_launches": {f: info.kernel_launches[i] for i, f in enumerate(KERNEL_FAMILIES)}}
     for key, v in bufs.items():

@@ -303,6 +303,7 @@ wf_options defaults(wf_options o)
     if (o.band_margin <= 0) o.band_margin = 100;
     if (!(o.lambda_max > 0)) o.lambda_max = 100.0;
     if (o.refine_sweeps <= 0) o.refine_sweeps = 3;
+    if (!(o.mixed_kappa > 0)) o.mixed_kappa = 3e4;
     return o;
 }
 
@@ -375,6 +376,21 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     wf_status st = hp_setup(p, fluct ? nullptr : d, nv, mask, &tau, &ndof);
     if (st != WF_OK) return st;
     const double tau_h = tau * p->omega;
+    HpSchedule sch;
+    sch.c.resize(lmax + 1);
+    WF_CUDA(cudaMemcpy(sch.c.data(), C_ell, (lmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    // Mixed precision: the messenger iteration contracts a mode by about
+    // tau_h / S_l per iteration where the mask leaves it unconstrained, so a
+    // systematic operator error larger than that margin makes the iteration
+    // grow.  Modes with S_l / tau_h >= kappa take the FP64 block.
+    int lc = 0;
+    if (p->prec != WF_PREC_FP64) {
+        if (o.mixed_lc > 0) lc = std::min(o.mixed_lc, lmax + 1);
+        else if (o.mixed_lc == 0)
+            for (int l = lmax; l >= 0; --l)
+                if (sch.c[l] / tau_h >= o.mixed_kappa) { lc = l + 1; break; }
+        if ((st = hp_set_low_block(p, lc)) != WF_OK) return st;
+    }
     if (fluct) {
         // r = nu^1/2 g1 + Omega Y (S^-1/2 g2), z synthesised into the output map as scratch
         k_isqrt_S<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, (const double2 *)g2, p->ws.a_new);
@@ -408,9 +424,6 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     const double bnorm = std::sqrt(p->ws.h_scal[0]);
     if (!(bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
 
-    HpSchedule sch;
-    sch.c.resize(lmax + 1);
-    WF_CUDA(cudaMemcpy(sch.c.data(), C_ell, (lmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
     sch.tau_h = tau_h;
     sch.lmax = lmax;
     sch.step_max = o.ell_step_max;
@@ -535,6 +548,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         info->tau = tau;
         info->n_levels = levels;
         info->refine_sweeps = 0;
+        info->mixed_lc = lc;
     }
     pr.finish();
     if (result == WF_OK && !replay && !converged) result = WF_ENOCONV;
@@ -572,6 +586,9 @@ wf_status hp_create(wf_plan p)
     if ((st = plan_alloc(p, (void **)&p->ws.a, p->nalm * sizeof(double2))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&p->ws.a_new, p->nalm * sizeof(double2))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&p->ws.b, p->nalm * sizeof(double2))) != WF_OK) return st;
+    if (p->prec != WF_PREC_FP64 &&
+        (st = plan_alloc(p, (void **)&p->ws.b_low, p->nalm * sizeof(double2))) != WF_OK)
+        return st;
     if ((st = plan_alloc(p, &p->ws.G, gsz)) != WF_OK) return st;
     if ((st = plan_alloc(p, &p->ws.F, gsz)) != WF_OK) return st;
     if ((st = plan_alloc(p, &p->ws.r, p->npix * es)) != WF_OK) return st;

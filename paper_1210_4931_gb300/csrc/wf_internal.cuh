@@ -77,6 +77,8 @@ struct Workspace {
     void *G = nullptr, *F = nullptr;
     void *r = nullptr, *nu = nullptr, *t = nullptr;
     void *scr = nullptr;          // per-CTA Bluestein scratch (2 * max Bluestein n complex per CTA)
+    double2 *Glow = nullptr;      // mixed: FP64-block synthesis coefficients [pair][glow_cap][hemisphere]
+    double2 *b_low = nullptr;     // mixed: FP64-block analysis output (alm layout, m < lc)
     double *part_pix = nullptr;   // per ring-CTA partial sums
     double *part_harm = nullptr;  // per m: [chi2_h, resid^2]
     double *scal = nullptr;       // reduced scalars (device)
@@ -91,12 +93,19 @@ struct Workspace {
 struct HpTables {
     RingTab *rings = nullptr;
     void *roots = nullptr, *V = nullptr, *tw = nullptr;  // T-typed complex
-    void *A = nullptr, *c = nullptr;                     // T-typed per alm
-    double *c64 = nullptr;                               // FP64 scale per alm (epilogue)
-    int *ls = nullptr;                                   // [m][pair]
-    void *s0 = nullptr, *s1 = nullptr;                   // T-typed seeds [m][pair]
-    void *x = nullptr;                                   // T-typed cos(theta) per pair
-    int logNmax = 0;       // twiddle table is e^{-2 pi i t / 2^logNmax}, t < 2^(logNmax-1)
+    // FP64 recurrence (always present): per alm A, c; per (m, pair) first l and seeds; per pair x
+    double *A64 = nullptr, *c64 = nullptr;
+    int *ls = nullptr;
+    double *s0_64 = nullptr, *s1_64 = nullptr;
+    double *x64 = nullptr;
+    // mixed precision: FP32 A and B = A - 2 per alm, x and w = 1 - x per pair,
+    // and the FP32 seeds that start the recurrence at max(l_s, l_c) (m < l_c)
+    float *A32 = nullptr, *B32 = nullptr, *x32 = nullptr, *w32 = nullptr;
+    int *ls_mx = nullptr;
+    float *s0_mx = nullptr, *s1_mx = nullptr;
+    int lc_mx = 0;         // FP64 block l < lc_mx of the mixed path
+    int glow_cap = 0;      // row length of the FP64-block ring coefficients
+    int logNmax = 0;       // twiddle table is e^{-2 pi i t / 2^logNmax}, t < 2^logNmax
     int bmax = 0;          // smem FFT buffer length (complex entries)
     int maxBlue = 0;       // longest Bluestein ring
     int ringGrid = 0;      // persistent grid of the ring kernels
@@ -170,6 +179,7 @@ struct BlendArgs {
     const double *S = nullptr;  // C_ell (device)
     int want_resid = 0;
 };
+wf_status hp_set_low_block(wf_plan p, int lc);
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L);
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old,
                                double2 *out);

@@ -9,10 +9,26 @@
 //
 // North/south ring pairs share lambda up to (-1)^(l-m): synthesis keeps an
 // even and an odd partial sum per pair, analysis folds F_N +- F_S before the
-// sum.  The recurrence runs in "mu form" (see wf_internal.cuh) from per-(m,
-// pair) seeds at the first l where |lambda_lm| exceeds 2^-80 (computed in FP64
-// with an explicit binary exponent, since sin^m(theta) underflows FP64 near
-// the poles at large m); below that l every term is < 2^-80 and is dropped.
+// sum.  The recurrence runs in "mu form" (wf_internal.cuh) from per-(m, pair)
+// seeds at the first l where |lambda_lm| exceeds 2^-80 (computed in FP64 with
+// an explicit binary exponent, since sin^m(theta) underflows FP64 near the
+// poles at large m); below that l every term is < 2^-80 and is dropped.
+//
+// Two precisions:
+//   FP64     k_legsyn<double>, k_legana<double,...>: one ring pair per thread.
+//   mixed    k_legsyn_mx, k_legana_mx: FP32 recurrence and contraction, four
+//            ring pairs per thread in two packed f32x2 lanes (__ffma2_rn).
+//            Near the poles the plain recurrence mu_l = A x mu_{l-1} - mu_{l-2}
+//            loses ~1/sin(theta) digits (its two characteristic roots merge
+//            at x = 1), so rings with x > 0.4 run the same recurrence in
+//            difference form (Reinsch's modification):
+//                D_l = D_{l-1} + (B_l - A_l w) mu_{l-1},  mu_l = mu_{l-1} + D_l,
+//            w = 1 - x exact from the grid, B_l = A_l - 2 tabulated in FP64.
+//            The block l < l_c, where the messenger iteration's contraction
+//            margin tau_h / S_l is below the FP32 error, runs through the FP64
+//            kernels instead (the FP32 recurrence restarts at l_c from FP64
+//            seeds), so the mixed iteration keeps the FP64 iteration's
+//            stability on the modes that converge slowest.
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -24,8 +40,15 @@ namespace wf {
 namespace {
 
 constexpr double SEED_LOG2_THRESHOLD = -80.0;
+constexpr int MXP = 4;               // ring pairs per thread in the mixed synthesis
+constexpr int MXPA = 8;              // ring pairs per lane in the mixed analysis
+constexpr float X_DIFFERENCE_FORM = 0.4f;
+constexpr int BIG = INT_MAX / 2;
 
 __host__ __device__ inline long long mbase(int lmax, int m) { return (long long)m * (2 * lmax + 3 - m) / 2; }
+
+// first l of the FP32 range for m < lc: l_c rounded up to the parity of m
+__host__ __device__ inline int lcm_of(int lc, int m) { return m + 2 * ((lc - m + 1) / 2); }
 
 // ---------------------------------------------------------------------------
 // seeds: one thread per (m, pair), FP64 with a carried binary exponent
@@ -80,6 +103,51 @@ __global__ void k_seeds(int lmax, int npairs, const double *__restrict__ xp, con
     s1_out[idx] = s1;
 }
 
+// FP32 seeds of the mixed kernels for a given FP64 block l < lc: for m < lc
+// the FP32 recurrence starts at max(l_s, lcm) from FP64-accurate values
+__global__ void k_restart_seeds(int lmax, int npairs, int lc, const double *__restrict__ xp,
+                                const double *__restrict__ A, const int *__restrict__ ls_in,
+                                const double *__restrict__ s0_in, const double *__restrict__ s1_in,
+                                int *__restrict__ ls_out, float *__restrict__ s0_out, float *__restrict__ s1_out)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)(lmax + 1) * npairs) return;
+    const int m = (int)(idx / npairs);
+    const int p = (int)(idx % npairs);
+    int ls = ls_in[idx];
+    double s0 = s0_in[idx], s1 = s1_in[idx];
+    if (m < lc && ls <= lmax) {
+        const int l1 = lcm_of(lc, m);
+        if (ls < l1) {
+            if (l1 > lmax) {
+                ls = lmax + 1;
+                s0 = s1 = 0.0;
+            } else {
+                const long long base = mbase(lmax, m);
+                const double x = xp[p];
+                double a = s0, b = s1;  // mu_l, mu_{l+1} at l = ls
+                for (int l = ls + 2; l <= l1 + 1 && l <= lmax; ++l) {
+                    const double c2 = A[base + (l - m)] * x * b - a;
+                    a = b;
+                    b = c2;
+                }
+                // now (a, b) = (mu_{l1}, mu_{l1+1}), or (mu_{lmax-1}, mu_{lmax}) if l1 = lmax
+                if (l1 == lmax && ls + 1 < lmax) {
+                    s0 = b;
+                    s1 = 0.0;
+                } else {
+                    s0 = a;
+                    s1 = b;
+                }
+                ls = l1;
+            }
+        }
+    }
+    ls_out[idx] = ls;
+    s0_out[idx] = (float)s0;
+    s1_out[idx] = (float)s1;
+}
+
 template <typename T>
 __global__ void k_to_T(const double *__restrict__ in, T *__restrict__ out, long long n)
 {
@@ -88,26 +156,30 @@ __global__ void k_to_T(const double *__restrict__ in, T *__restrict__ out, long 
 }
 
 // ---------------------------------------------------------------------------
-// synthesis: CTA per (m, block of pairs); thread per pair
+// FP64 synthesis: CTA per (m, block of pairs); thread per pair.
+// lcut > 0: the FP64 block of the mixed path, l < lcm_of(lcut, m), output
+// into Gout with row stride gstride.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(LEG_THREADS) k_legsyn(int lmax, int L, int npairs, const double2 *__restrict__ alm,
-                                                        const T *__restrict__ A, const T *__restrict__ c,
+__global__ void __launch_bounds__(LEG_THREADS) k_legsyn(int lmax, int L, int npairs, int lcut,
+                                                        const double2 *__restrict__ alm, const T *__restrict__ A,
+                                                        const double *__restrict__ c64,
                                                         const int *__restrict__ ls_tab, const T *__restrict__ s0_tab,
                                                         const T *__restrict__ s1_tab, const T *__restrict__ xp,
-                                                        cx<T> *__restrict__ G)
+                                                        cx<T> *__restrict__ G, int gstride)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y;
-    const int nl = L - m + 1;
+    const int Lm = lcut > 0 ? min(L, lcm_of(lcut, m) - 1) : L;
+    const int nl = Lm - m + 1;
     const long long base = mbase(lmax, m);
     cx<T> *sac = reinterpret_cast<cx<T> *>(smem_raw);
     T *sA = reinterpret_cast<T *>(sac + (nl + 2));
     for (int i = threadIdx.x; i < nl + 2; i += blockDim.x) {
         if (i < nl) {
             const double2 a = alm[base + i];
-            const T cc = c[base + i];
-            sac[i] = mk<T>((T)a.x * cc, (T)a.y * cc);
+            const double cc = c64[base + i];
+            sac[i] = mk<T>((T)(a.x * cc), (T)(a.y * cc));
             sA[i] = A[base + i];
         } else {
             sac[i] = mk<T>(0, 0);
@@ -115,12 +187,11 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn(int lmax, int L, int npa
         }
     }
     __syncthreads();
-    const size_t pstride = (size_t)(lmax + 1) * 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
         const size_t sidx = (size_t)m * npairs + p;
         const int ls = ls_tab[sidx];
         T er = 0, ei = 0, orr = 0, oi = 0;
-        if (ls <= L) {
+        if (ls <= Lm) {
             const T x = xp[p];
             T mu0 = s0_tab[sidx], mu1 = s1_tab[sidx];
             int i = ls - m;
@@ -140,16 +211,15 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn(int lmax, int L, int npa
                 oi = fma(a1.y, mu1, oi);
             }
         }
-        cx<T> *g = G + (size_t)p * pstride + 2 * (size_t)m;
+        cx<T> *g = G + ((size_t)p * gstride + m) * 2;
         g[0] = mk<T>(er + orr, ei + oi);
         g[1] = mk<T>(er - orr, ei - oi);
     }
 }
 
 // ---------------------------------------------------------------------------
-// analysis: CTA per m; warp per 32 pairs; register chunks of CH values of l
-// reduced across the warp by a shuffle reduce-scatter, then added into FP64
-// shared accumulators.
+// warp reduce-scatter of CH complex values: lane i ends with the sum over the
+// warp of value (i >> (5 - log2 CH)).
 // ---------------------------------------------------------------------------
 template <typename T, int CH>
 __device__ __forceinline__ void warp_reduce_scatter(T (&vr)[CH], T (&vi)[CH], int lane)
@@ -181,19 +251,98 @@ template <int CH> struct Log2;
 template <> struct Log2<16> { static constexpr int v = 4; };
 template <> struct Log2<32> { static constexpr int v = 5; };
 
-template <typename T, int CH>
-__global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npairs, const cx<T> *__restrict__ F,
-                                                        const T *__restrict__ A, const int *__restrict__ ls_tab,
-                                                        const T *__restrict__ s0_tab, const T *__restrict__ s1_tab,
-                                                        const T *__restrict__ xp, const double *__restrict__ c64,
-                                                        int mode, double omega, BlendArgs ba,
-                                                        const double2 *__restrict__ a_old, double2 *__restrict__ out,
-                                                        double *__restrict__ part)
+__device__ __forceinline__ void block_reduce2(double &a, double &b, double (*red)[LEG_THREADS / 32])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0.0, y = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { x += red[0][w]; y += red[1][w]; }
+        a = x;
+        b = y;
+    }
+}
+
+// Eq. (4) epilogue shared by both precisions: t_hat = Omega (c acc + low),
+// a_new = S/(S + lam tau_h) t_hat, chi^2 of a_old, lambda = 1 residual.
+__device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long base, int mode, double omega,
+                                               const BlendArgs &ba, const double *__restrict__ c64,
+                                               const double2 *acc, const double2 *__restrict__ low, int low_lim,
+                                               const double2 *__restrict__ a_old, double2 *__restrict__ out,
+                                               double *__restrict__ part, double (*red)[LEG_THREADS / 32])
+{
+    double chi2 = 0.0, res2 = 0.0;
+    const double wm = (m == 0) ? 1.0 : 2.0;
+    for (int j = threadIdx.x; j <= lmax - m; j += blockDim.x) {
+        const int l = m + j;
+        const long long idx = base + j;
+        double2 b = make_double2(0.0, 0.0);
+        if (l <= L) {
+            b.x = c64[idx] * acc[j].x;
+            b.y = c64[idx] * acc[j].y;
+            if (low && l < low_lim) {
+                const double2 q = low[idx];
+                b.x += q.x;
+                b.y += q.y;
+            }
+        }
+        if (mode == LEG_ADJOINT) {
+            out[idx] = b;
+        } else {
+            const double S = ba.S[l];
+            const double2 ao = a_old[idx];
+            double2 an = make_double2(0.0, 0.0);
+            if (l <= L && S > 0.0) {
+                const double f = omega * S / (S + ba.lam_tauh);
+                an.x = f * b.x;
+                an.y = f * b.y;
+            }
+            if (S > 0.0) {
+                chi2 += wm * (ao.x * ao.x + ao.y * ao.y) / S;
+                if (ba.want_resid) {
+                    const double k = 1.0 / S + 1.0 / ba.tauh;
+                    const double dx = k * (ao.x - an.x), dy = k * (ao.y - an.y);
+                    res2 += wm * (dx * dx + dy * dy);
+                }
+            }
+            out[idx] = an;
+        }
+    }
+    if (mode == LEG_BLEND) {
+        block_reduce2(chi2, res2, red);
+        if (threadIdx.x == 0) {
+            part[2 * m] = chi2;
+            part[2 * m + 1] = res2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 analysis: CTA per m; warp per 32 pairs; register chunks of CH values
+// of l reduced across the warp, added into FP64 shared accumulators.
+// TF is the storage type of F (FP64 plans: double; FP64 block of the mixed
+// path: float).
+// ---------------------------------------------------------------------------
+template <typename T, typename TF, int CH>
+__global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npairs, int lcut,
+                                                        const cx<TF> *__restrict__ F, const T *__restrict__ A,
+                                                        const int *__restrict__ ls_tab, const T *__restrict__ s0_tab,
+                                                        const T *__restrict__ s1_tab, const T *__restrict__ xp,
+                                                        const double *__restrict__ c64, int mode, double omega,
+                                                        BlendArgs ba, const double2 *__restrict__ a_old,
+                                                        double2 *__restrict__ out, double *__restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2][LEG_THREADS / 32];
     const int m = blockIdx.x;
-    const int nl = L - m + 1;
+    const int Lm = lcut > 0 ? min(L, lcm_of(lcut, m) - 1) : L;
+    const int nl = Lm - m + 1;
     const int nlp = nl + CH + 2;
     const long long base = mbase(lmax, m);
     double2 *acc = reinterpret_cast<double2 *>(smem_raw);
@@ -206,27 +355,26 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int ngroups = (npairs + 31) / 32;
-    constexpr int BIG = INT_MAX / 2;
     for (int grp = warp; grp < ngroups; grp += nwarps) {
         const int p = grp * 32 + lane;
         const size_t sidx = (size_t)m * npairs + p;
         int ls = (p < npairs) ? ls_tab[sidx] : BIG;
-        if (ls > L) ls = BIG;
+        if (ls > Lm) ls = BIG;
         const int lmin = __reduce_min_sync(0xffffffffu, ls);
-        if (lmin > L) continue;
+        if (lmin > Lm) continue;
         cx<T> FE = mk<T>(0, 0), FO = mk<T>(0, 0);
         T x = 0, s0 = 0, s1 = 0;
-        if (ls <= L) {
-            const cx<T> *f = F + ((size_t)p * (lmax + 1) + m) * 2;
-            const cx<T> fn = f[0], fs = f[1];
-            FE = cadd(fn, fs);
-            FO = csub(fn, fs);
+        if (ls <= Lm) {
+            const cx<TF> *f = F + ((size_t)p * (lmax + 1) + m) * 2;
+            const cx<TF> fn = f[0], fs = f[1];
+            FE = mk<T>((T)fn.x + (T)fs.x, (T)fn.y + (T)fs.y);
+            FO = mk<T>((T)fn.x - (T)fs.x, (T)fn.y - (T)fs.y);
             x = xp[p];
             s0 = s0_tab[sidx];
             s1 = s1_tab[sidx];
         }
         T mua = 0, mub = 0;
-        for (int l0 = lmin; l0 <= L; l0 += CH) {
+        for (int l0 = lmin; l0 <= Lm; l0 += CH) {
             T vr[CH], vi[CH];
 #pragma unroll
             for (int i = 0; i < CH; i += 2) {
@@ -245,7 +393,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
             constexpr int sh = 5 - Log2<CH>::v;
             if ((lane & ((1 << sh) - 1)) == 0) {
                 const int l = l0 + (lane >> sh);
-                if (l <= L) {
+                if (l <= Lm) {
                     atomicAdd(&acc[l - m].x, (double)vr[0]);
                     atomicAdd(&acc[l - m].y, (double)vi[0]);
                 }
@@ -253,84 +401,381 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
         }
     }
     __syncthreads();
+    blend_epilogue(lmax, Lm, m, base, mode, omega, ba, c64, acc, nullptr, 0, a_old, out, part, red);
+}
 
-    double chi2 = 0.0, res2 = 0.0;
-    const double wm = (m == 0) ? 1.0 : 2.0;
-    for (int j = threadIdx.x; j <= lmax - m; j += blockDim.x) {
-        const int l = m + j;
-        const long long idx = base + j;
-        if (mode == LEG_ADJOINT) {
-            double2 v = make_double2(0.0, 0.0);
-            if (l <= L) { v.x = c64[idx] * acc[j].x; v.y = c64[idx] * acc[j].y; }
-            out[idx] = v;
-        } else {
-            const double S = ba.S[l];
-            const double2 ao = a_old[idx];
-            double2 an = make_double2(0.0, 0.0);
-            if (l <= L && S > 0.0) {
-                const double f = omega * c64[idx] * S / (S + ba.lam_tauh);
-                an.x = f * acc[j].x;
-                an.y = f * acc[j].y;
+// ---------------------------------------------------------------------------
+// mixed precision: FP32 kernels, four ring pairs per thread in two f32x2
+// packs, plain or difference-form recurrence by ring
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float get(const float2 &v, int k) { return k ? v.y : v.x; }
+__device__ __forceinline__ void put(float2 &v, int k, float a)
+{
+    if (k) v.y = a;
+    else v.x = a;
+}
+
+template <int NP> struct MxPairs {
+    static constexpr int NPK = NP / 2;
+    int ls[NP];
+    float s0[NP], s1[NP];
+    float2 X[NP / 2], W[NP / 2];
+    int lmin, lmaxs;
+    bool diff;
+};
+
+template <int NP>
+__device__ __forceinline__ void mx_load_pairs(MxPairs<NP> &P, int m, int L, int npairs, int p0,
+                                              const int *__restrict__ ls_tab, const float *__restrict__ s0_tab,
+                                              const float *__restrict__ s1_tab, const float *__restrict__ xp,
+                                              const float *__restrict__ wp)
+{
+    P.lmin = BIG;
+    P.lmaxs = -1;
+    float xs[NP], ws[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int p = p0 + k;
+        int ls = BIG;
+        float s0 = 0.f, s1 = 0.f, x = 0.f, w = 1.f;
+        if (p < npairs) {
+            const size_t sidx = (size_t)m * npairs + p;
+            ls = ls_tab[sidx];
+            if (ls > L) ls = BIG;
+            else {
+                s0 = s0_tab[sidx];
+                s1 = s1_tab[sidx];
             }
-            if (S > 0.0) {
-                chi2 += wm * (ao.x * ao.x + ao.y * ao.y) / S;
-                if (ba.want_resid) {
-                    const double k = 1.0 / S + 1.0 / ba.tauh;
-                    const double dx = k * (ao.x - an.x), dy = k * (ao.y - an.y);
-                    res2 += wm * (dx * dx + dy * dy);
+            x = xp[p];
+            w = wp[p];
+        }
+        P.ls[k] = ls;
+        P.s0[k] = s0;
+        P.s1[k] = s1;
+        xs[k] = x;
+        ws[k] = w;
+        if (ls < P.lmin) P.lmin = ls;
+        if (ls != BIG && ls > P.lmaxs) P.lmaxs = ls;
+    }
+#pragma unroll
+    for (int pk = 0; pk < NP / 2; ++pk) {
+        P.X[pk] = make_float2(xs[2 * pk], xs[2 * pk + 1]);
+        P.W[pk] = make_float2(ws[2 * pk], ws[2 * pk + 1]);
+    }
+    P.diff = xs[0] > X_DIFFERENCE_FORM;
+}
+
+// one double step (l, l+1) of the recurrence for both packs.
+// plain state: (Sa, Sb) = (mu_{l-2}, mu_{l-1}); difference state: (Sa, Sb) =
+// (D_{l-1}, mu_{l-1}).  Outputs mu_l (V0) and mu_{l+1} (V1).
+template <bool DIFF, bool INJECT, int NP>
+__device__ __forceinline__ void mx_step(const MxPairs<NP> &P, int l, float A0, float B0, float A1, float B1,
+                                        float2 (&Sa)[NP / 2], float2 (&Sb)[NP / 2], float2 (&V0)[NP / 2],
+                                        float2 (&V1)[NP / 2])
+{
+#pragma unroll
+    for (int pk = 0; pk < NP / 2; ++pk) {
+        if (DIFF) {
+            float2 D = Sa[pk], mu = Sb[pk];
+            D = __ffma2_rn(__ffma2_rn(dup(-A0), P.W[pk], dup(B0)), mu, D);
+            const float2 v0 = __fadd2_rn(mu, D);
+            D = __ffma2_rn(__ffma2_rn(dup(-A1), P.W[pk], dup(B1)), v0, D);
+            const float2 v1 = __fadd2_rn(v0, D);
+            V0[pk] = v0;
+            V1[pk] = v1;
+            Sa[pk] = D;
+            Sb[pk] = v1;
+        } else {
+            const float2 v0 = __ffma2_rn(__fmul2_rn(dup(A0), P.X[pk]), Sb[pk], neg2(Sa[pk]));
+            const float2 v1 = __ffma2_rn(__fmul2_rn(dup(A1), P.X[pk]), v0, neg2(Sb[pk]));
+            V0[pk] = v0;
+            V1[pk] = v1;
+            Sa[pk] = v0;
+            Sb[pk] = v1;
+        }
+        if (INJECT) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 2 * pk + h;
+                if (l == P.ls[k]) {
+                    put(V0[pk], h, P.s0[k]);
+                    put(V1[pk], h, P.s1[k]);
+                    if (DIFF) {
+                        put(Sa[pk], h, P.s1[k] - P.s0[k]);
+                        put(Sb[pk], h, P.s1[k]);
+                    } else {
+                        put(Sa[pk], h, P.s0[k]);
+                        put(Sb[pk], h, P.s1[k]);
+                    }
                 }
             }
-            out[idx] = an;
-        }
-    }
-    if (mode == LEG_BLEND) {
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            chi2 += __shfl_xor_sync(0xffffffffu, chi2, o);
-            res2 += __shfl_xor_sync(0xffffffffu, res2, o);
-        }
-        if (lane == 0) { red[0][warp] = chi2; red[1][warp] = res2; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int w = 0; w < nwarps; ++w) { a += red[0][w]; b += red[1][w]; }
-            part[2 * m] = a;
-            part[2 * m + 1] = b;
         }
     }
 }
 
+template <bool DIFF>
+__device__ __forceinline__ void mx_syn_run(const MxPairs<MXP> &P, int m, int L, const float4 *__restrict__ sAB,
+                                           const float4 *__restrict__ sac, float2 (&ER)[2], float2 (&EI)[2],
+                                           float2 (&OR)[2], float2 (&OI)[2])
+{
+    float2 Sa[2] = {dup(0.f), dup(0.f)}, Sb[2] = {dup(0.f), dup(0.f)};
+    float2 V0[2], V1[2];
+    int l = P.lmin;
+    for (; l <= L && l <= P.lmaxs; l += 2) {
+        const int j = (l - m) >> 1;
+        const float4 ab = sAB[j], ac = sac[j];
+        mx_step<DIFF, true, MXP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
+#pragma unroll
+        for (int pk = 0; pk < 2; ++pk) {
+            ER[pk] = __ffma2_rn(dup(ac.x), V0[pk], ER[pk]);
+            EI[pk] = __ffma2_rn(dup(ac.y), V0[pk], EI[pk]);
+            OR[pk] = __ffma2_rn(dup(ac.z), V1[pk], OR[pk]);
+            OI[pk] = __ffma2_rn(dup(ac.w), V1[pk], OI[pk]);
+        }
+    }
+    for (; l <= L; l += 2) {
+        const int j = (l - m) >> 1;
+        const float4 ab = sAB[j], ac = sac[j];
+        mx_step<DIFF, false, MXP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
+#pragma unroll
+        for (int pk = 0; pk < 2; ++pk) {
+            ER[pk] = __ffma2_rn(dup(ac.x), V0[pk], ER[pk]);
+            EI[pk] = __ffma2_rn(dup(ac.y), V0[pk], EI[pk]);
+            OR[pk] = __ffma2_rn(dup(ac.z), V1[pk], OR[pk]);
+            OI[pk] = __ffma2_rn(dup(ac.w), V1[pk], OI[pk]);
+        }
+    }
+}
+
+// shared-memory staging: per pair of l (l = m + 2j, l + 1):
+//   sAB[j] = (A_l, B_l, A_{l+1}, B_{l+1}),  sac[j] = (Re a'_l, Im a'_l, Re a'_{l+1}, Im a'_{l+1})
+__global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int npairs,
+                                                           const double2 *__restrict__ alm,
+                                                           const float *__restrict__ A, const float *__restrict__ B,
+                                                           const double *__restrict__ c64,
+                                                           const int *__restrict__ ls_tab,
+                                                           const float *__restrict__ s0_tab,
+                                                           const float *__restrict__ s1_tab,
+                                                           const float *__restrict__ xp, const float *__restrict__ wp,
+                                                           float2 *__restrict__ G)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = blockIdx.y;
+    const int nl = L - m + 1;
+    const int nj = (nl + 1) / 2 + 1;
+    const long long base = mbase(lmax, m);
+    float4 *sAB = reinterpret_cast<float4 *>(smem_raw);
+    float4 *sac = sAB + nj;
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+        float4 ab = make_float4(0.f, 0.f, 0.f, 0.f), ac = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int i0 = 2 * j, i1 = 2 * j + 1;
+        if (i0 < nl) {
+            const double2 a = alm[base + i0];
+            const double cc = c64[base + i0];
+            ab.x = A[base + i0];
+            ab.y = B[base + i0];
+            ac.x = (float)(a.x * cc);
+            ac.y = (float)(a.y * cc);
+        }
+        if (i1 < nl) {
+            const double2 a = alm[base + i1];
+            const double cc = c64[base + i1];
+            ab.z = A[base + i1];
+            ab.w = B[base + i1];
+            ac.z = (float)(a.x * cc);
+            ac.w = (float)(a.y * cc);
+        }
+        sAB[j] = ab;
+        sac[j] = ac;
+    }
+    __syncthreads();
+    const size_t pstride = (size_t)(lmax + 1) * 2;
+    for (int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * MXP; p0 < npairs; p0 += gridDim.x * blockDim.x * MXP) {
+        MxPairs<MXP> P;
+        mx_load_pairs<MXP>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
+        float2 ER[2] = {dup(0.f), dup(0.f)}, EI[2] = {dup(0.f), dup(0.f)};
+        float2 OR[2] = {dup(0.f), dup(0.f)}, OI[2] = {dup(0.f), dup(0.f)};
+        if (P.lmin <= L) {
+            if (P.diff) mx_syn_run<true>(P, m, L, sAB, sac, ER, EI, OR, OI);
+            else mx_syn_run<false>(P, m, L, sAB, sac, ER, EI, OR, OI);
+        }
+#pragma unroll
+        for (int k = 0; k < MXP; ++k) {
+            const int p = p0 + k;
+            if (p >= npairs) break;
+            const int pk = k >> 1, h = k & 1;
+            const float er = get(ER[pk], h), ei = get(EI[pk], h), orr = get(OR[pk], h), oi = get(OI[pk], h);
+            float2 *g = G + (size_t)p * pstride + 2 * (size_t)m;
+            g[0] = make_float2(er + orr, ei + oi);
+            g[1] = make_float2(er - orr, ei - oi);
+        }
+    }
+}
+
+// analysis: CTA per m; a warp covers 32 lanes x 4 pairs; chunks of 16 values
+// of l accumulate both packs in f32x2 registers, then are summed over the
+// pack lanes and reduced across the warp.
+constexpr int MX_CH = 16;
+
+template <bool DIFF>
+__device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L, int lmin_w,
+                                           const float *__restrict__ sA, const float *__restrict__ sB,
+                                           const float2 (&FEr)[MXPA / 2], const float2 (&FEi)[MXPA / 2],
+                                           const float2 (&FOr)[MXPA / 2], const float2 (&FOi)[MXPA / 2],
+                                           double2 *acc, int lane)
+{
+    constexpr int NPK = MXPA / 2;
+    float2 Sa[NPK], Sb[NPK], V0[NPK], V1[NPK];
+#pragma unroll
+    for (int pk = 0; pk < NPK; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
+    for (int l0 = lmin_w; l0 <= L; l0 += MX_CH) {
+        float2 AR[MX_CH], AI[MX_CH];
+        const bool inj = l0 <= P.lmaxs;
+#pragma unroll
+        for (int i = 0; i < MX_CH; i += 2) {
+            const int j = l0 - m + i;
+            const float A0 = sA[j], B0 = sB[j], A1 = sA[j + 1], B1 = sB[j + 1];
+            if (inj) mx_step<DIFF, true, MXPA>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
+            else mx_step<DIFF, false, MXPA>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
+            AR[i] = __fmul2_rn(FEr[0], V0[0]);
+            AI[i] = __fmul2_rn(FEi[0], V0[0]);
+            AR[i + 1] = __fmul2_rn(FOr[0], V1[0]);
+            AI[i + 1] = __fmul2_rn(FOi[0], V1[0]);
+#pragma unroll
+            for (int pk = 1; pk < NPK; ++pk) {
+                AR[i] = __ffma2_rn(FEr[pk], V0[pk], AR[i]);
+                AI[i] = __ffma2_rn(FEi[pk], V0[pk], AI[i]);
+                AR[i + 1] = __ffma2_rn(FOr[pk], V1[pk], AR[i + 1]);
+                AI[i + 1] = __ffma2_rn(FOi[pk], V1[pk], AI[i + 1]);
+            }
+        }
+        float vr[MX_CH], vi[MX_CH];
+#pragma unroll
+        for (int i = 0; i < MX_CH; ++i) {
+            vr[i] = AR[i].x + AR[i].y;
+            vi[i] = AI[i].x + AI[i].y;
+        }
+        warp_reduce_scatter<float, MX_CH>(vr, vi, lane);
+        if ((lane & 1) == 0) {
+            const int l = l0 + (lane >> 1);
+            if (l <= L) {
+                atomicAdd(&acc[l - m].x, (double)vr[0]);
+                atomicAdd(&acc[l - m].y, (double)vi[0]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(LEG_THREADS) k_legana_mx(int lmax, int L, int npairs, int lc,
+                                                           const float2 *__restrict__ F, const float *__restrict__ A,
+                                                           const float *__restrict__ B,
+                                                           const int *__restrict__ ls_tab,
+                                                           const float *__restrict__ s0_tab,
+                                                           const float *__restrict__ s1_tab,
+                                                           const float *__restrict__ xp, const float *__restrict__ wp,
+                                                           const double *__restrict__ c64, int mode, double omega,
+                                                           BlendArgs ba, const double2 *__restrict__ low,
+                                                           const double2 *__restrict__ a_old,
+                                                           double2 *__restrict__ out, double *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[2][LEG_THREADS / 32];
+    const int m = blockIdx.x;
+    const int nl = L - m + 1;
+    const int nlp = nl + MX_CH + 2;
+    const long long base = mbase(lmax, m);
+    double2 *acc = reinterpret_cast<double2 *>(smem_raw);
+    float *sA = reinterpret_cast<float *>(acc + nlp);
+    float *sB = sA + nlp;
+    for (int i = threadIdx.x; i < nlp; i += blockDim.x) {
+        acc[i] = make_double2(0.0, 0.0);
+        sA[i] = (i < nl) ? A[base + i] : 0.f;
+        sB[i] = (i < nl) ? B[base + i] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int per_group = 32 * MXPA;
+    const int ngroups = (npairs + per_group - 1) / per_group;
+    const size_t pstride = (size_t)(lmax + 1) * 2;
+    for (int grp = warp; grp < ngroups; grp += nwarps) {
+        const int p0 = grp * per_group + lane * MXPA;
+        MxPairs<MXPA> P;
+        mx_load_pairs<MXPA>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
+        // one recurrence form per warp: the shuffles below need warp-uniform control flow
+        P.diff = __shfl_sync(0xffffffffu, P.diff ? 1 : 0, 0) != 0;
+        const int lmin_w = __reduce_min_sync(0xffffffffu, P.lmin);
+        if (lmin_w > L) continue;
+        float fer[MXPA], fei[MXPA], forr[MXPA], foi[MXPA];
+#pragma unroll
+        for (int k = 0; k < MXPA; ++k) {
+            fer[k] = fei[k] = forr[k] = foi[k] = 0.f;
+            if (P.ls[k] != BIG) {
+                const float2 *f = F + (size_t)(p0 + k) * pstride + 2 * (size_t)m;
+                const float2 fn = f[0], fs = f[1];
+                fer[k] = fn.x + fs.x;
+                fei[k] = fn.y + fs.y;
+                forr[k] = fn.x - fs.x;
+                foi[k] = fn.y - fs.y;
+            }
+        }
+        float2 FEr[MXPA / 2], FEi[MXPA / 2], FOr[MXPA / 2], FOi[MXPA / 2];
+#pragma unroll
+        for (int pk = 0; pk < MXPA / 2; ++pk) {
+            FEr[pk] = make_float2(fer[2 * pk], fer[2 * pk + 1]);
+            FEi[pk] = make_float2(fei[2 * pk], fei[2 * pk + 1]);
+            FOr[pk] = make_float2(forr[2 * pk], forr[2 * pk + 1]);
+            FOi[pk] = make_float2(foi[2 * pk], foi[2 * pk + 1]);
+        }
+        if (P.diff) mx_ana_run<true>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+        else mx_ana_run<false>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+    }
+    __syncthreads();
+    const int low_lim = (low && m < lc) ? lcm_of(lc, m) : 0;
+    blend_epilogue(lmax, L, m, base, mode, omega, ba, c64, acc, low, low_lim, a_old, out, part, red);
+}
+
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
 template <typename T>
-size_t syn_smem(int L, int m0) { return (size_t)(L - m0 + 3) * (sizeof(cx<T>) + sizeof(T)) + 16; }
+size_t syn_smem(int L) { return (size_t)(L + 3) * (sizeof(cx<T>) + sizeof(T)) + 16; }
 
 template <typename T, int CH>
 size_t ana_smem(int L) { return (size_t)(L + 1 + CH + 2) * (sizeof(double2) + sizeof(T)) + 16; }
 
-template <typename T>
-wf_status launch_syn(wf_plan p, const double2 *alm, int L)
+size_t syn_mx_smem(int L) { return (size_t)((L + 2) / 2 + 2) * 2 * sizeof(float4) + 16; }
+size_t ana_mx_smem(int L) { return (size_t)(L + 1 + MX_CH + 2) * (sizeof(double2) + 2 * sizeof(float)) + 16; }
+
+wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *G, int gstride)
 {
     const HpTables &t = p->tab;
+    const int Lgrid = lcut > 0 ? std::min(L, lcut - 1) : L;
+    if (Lgrid < 0) return WF_OK;
     const int gx = (p->npairs + 4 * LEG_THREADS - 1) / (4 * LEG_THREADS);
-    dim3 grid(gx, L + 1);
-    const size_t sm = syn_smem<T>(L, 0);
-    WF_CUDA(cudaFuncSetAttribute(k_legsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_legsyn<T><<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, (const T *)t.A, (const T *)t.c, t.ls,
-                                                       (const T *)t.s0, (const T *)t.s1, (const T *)t.x,
-                                                       (cx<T> *)p->ws.G);
+    dim3 grid(gx, Lgrid + 1);
+    const size_t sm = syn_smem<double>(lcut > 0 ? std::min(L, lcut + 1) : L);
+    WF_CUDA(cudaFuncSetAttribute(k_legsyn<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_legsyn<double><<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, lcut, alm, t.A64, t.c64, t.ls,
+                                                            t.s0_64, t.s1_64, t.x64, G, gstride);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
 }
 
-template <typename T>
-wf_status launch_ana(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old, double2 *out)
+template <typename TF>
+wf_status launch_ana64(wf_plan p, int L, int lcut, const void *F, LegMode mode, const BlendArgs &ba,
+                       const double2 *a_old, double2 *out)
 {
-    constexpr int CH = sizeof(T) == 8 ? 16 : 32;
+    constexpr int CH = 16;
     const HpTables &t = p->tab;
-    const size_t sm = ana_smem<T, CH>(L);
-    WF_CUDA(cudaFuncSetAttribute(k_legana<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_legana<T, CH><<<L + 1, LEG_THREADS, sm, p->stream>>>(
-        p->lmax, L, p->npairs, (const cx<T> *)p->ws.F, (const T *)t.A, t.ls, (const T *)t.s0, (const T *)t.s1,
-        (const T *)t.x, t.c64, (int)mode, p->omega, ba, a_old, out, p->ws.part_harm);
+    const int Lgrid = lcut > 0 ? std::min(L, lcut - 1) : L;
+    if (Lgrid < 0) return WF_OK;
+    const size_t sm = ana_smem<double, CH>(lcut > 0 ? std::min(L, lcut + 1) : L);
+    WF_CUDA(cudaFuncSetAttribute(k_legana<double, TF, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_legana<double, TF, CH><<<Lgrid + 1, LEG_THREADS, sm, p->stream>>>(
+        p->lmax, L, p->npairs, lcut, (const cx<TF> *)F, t.A64, t.ls, t.s0_64, t.s1_64, t.x64, t.c64, (int)mode,
+        p->omega, ba, a_old, out, p->ws.part_harm);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
 }
@@ -344,88 +789,145 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
 {
     const int lmax = p->lmax, np = p->npairs;
     const long long nalm = p->nalm;
-    std::vector<double> A(nalm), c(nalm), log2c(lmax + 1);
+    std::vector<double> A(nalm), c(nalm), Bm2(nalm), log2c(lmax + 1);
     for (int m = 0; m <= lmax; ++m) {
         const long long b = mbase(lmax, m);
         auto coef = [m](int l) { return std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m)); };
         c[b] = 1.0;
+        if (m + 1 <= lmax) c[b + 1] = 1.0;
+        for (int l = m + 2; l <= lmax; ++l) c[b + (l - m)] = (coef(l) / coef(l - 1)) * c[b + (l - 2 - m)];
+        // scale the l - m odd chain so that c_l / c_{l-1} -> 1 at lmax: the
+        // multiplier A_l then tends to 2 x-independently, which the
+        // difference form needs
+        if (lmax - m >= 2) {
+            const double r = c[b + (lmax - m)] / c[b + (lmax - 1 - m)];
+            const double f = ((lmax - m) & 1) ? 1.0 / r : r;
+            for (int l = m + 1; l <= lmax; l += 2) c[b + (l - m)] *= f;
+        }
         A[b] = 0.0;
-        if (m + 1 <= lmax) {
-            c[b + 1] = 1.0;
-            A[b + 1] = std::sqrt(2.0 * m + 3.0);
-        }
-        for (int l = m + 2; l <= lmax; ++l) {
-            const double al = coef(l), alm1 = coef(l - 1);
-            c[b + (l - m)] = (al / alm1) * c[b + (l - 2 - m)];
-            A[b + (l - m)] = al * c[b + (l - 1 - m)] / c[b + (l - m)];
-        }
+        if (m + 1 <= lmax) A[b + 1] = std::sqrt(2.0 * m + 3.0) * c[b] / c[b + 1];
+        for (int l = m + 2; l <= lmax; ++l) A[b + (l - m)] = coef(l) * c[b + (l - 1 - m)] / c[b + (l - m)];
+        for (int l = m; l <= lmax; ++l) Bm2[b + (l - m)] = A[b + (l - m)] - 2.0;
         // log2 of sqrt((2m+1)/(4 pi) (2m)! / (2^m m!)^2)
         log2c[m] = 0.5 * (std::log(2.0 * m + 1.0) - std::log(4.0 * M_PI) + std::lgamma(2.0 * m + 1.0) -
                           2.0 * std::lgamma(m + 1.0) - 2.0 * m * std::log(2.0)) / std::log(2.0);
     }
+    std::vector<double> wpair(np);
+    for (int i = 0; i < np; ++i) wpair[i] = 1.0 - xpair[i];
+    // 1 - x exactly for the polar-cap rings (1 - z = k^2 / (3 nside^2))
+    for (int i = 0; i + 1 < p->nside && i < np; ++i)
+        wpair[i] = (double)(i + 1) * (i + 1) / (3.0 * p->nside * p->nside);
     const bool f32 = p->prec != WF_PREC_FP64;
-    const size_t es = f32 ? sizeof(float) : sizeof(double);
-    double *dA64 = nullptr, *dx64 = nullptr, *dst64 = nullptr, *dlog2c = nullptr, *ds0 = nullptr, *ds1 = nullptr;
+    double *dx64 = nullptr, *dst64 = nullptr, *dlog2c = nullptr;
     wf_status st;
-    if ((st = plan_alloc(p, (void **)&p->tab.c64, nalm * sizeof(double))) != WF_OK) return st;
-    WF_CUDA(cudaMalloc(&dA64, nalm * sizeof(double)));
-    WF_CUDA(cudaMalloc(&dx64, np * sizeof(double)));
+    HpTables &t = p->tab;
+    if ((st = plan_alloc(p, (void **)&t.c64, nalm * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&t.A64, nalm * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&t.x64, np * sizeof(double))) != WF_OK) return st;
     WF_CUDA(cudaMalloc(&dst64, np * sizeof(double)));
     WF_CUDA(cudaMalloc(&dlog2c, (lmax + 1) * sizeof(double)));
     const long long ns = (long long)(lmax + 1) * np;
-    if ((st = plan_alloc(p, (void **)&p->tab.ls, ns * sizeof(int))) != WF_OK) return st;
-    WF_CUDA(cudaMalloc(&ds0, ns * sizeof(double)));
-    WF_CUDA(cudaMalloc(&ds1, ns * sizeof(double)));
-    WF_CUDA(cudaMemcpy(dA64, A.data(), nalm * sizeof(double), cudaMemcpyHostToDevice));
-    WF_CUDA(cudaMemcpy(p->tab.c64, c.data(), nalm * sizeof(double), cudaMemcpyHostToDevice));
-    WF_CUDA(cudaMemcpy(dx64, xpair.data(), np * sizeof(double), cudaMemcpyHostToDevice));
+    if ((st = plan_alloc(p, (void **)&t.ls, ns * sizeof(int))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&t.s0_64, ns * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&t.s1_64, ns * sizeof(double))) != WF_OK) return st;
+    WF_CUDA(cudaMemcpy(t.A64, A.data(), nalm * sizeof(double), cudaMemcpyHostToDevice));
+    WF_CUDA(cudaMemcpy(t.c64, c.data(), nalm * sizeof(double), cudaMemcpyHostToDevice));
+    WF_CUDA(cudaMemcpy(t.x64, xpair.data(), np * sizeof(double), cudaMemcpyHostToDevice));
     WF_CUDA(cudaMemcpy(dst64, stpair.data(), np * sizeof(double), cudaMemcpyHostToDevice));
     WF_CUDA(cudaMemcpy(dlog2c, log2c.data(), (lmax + 1) * sizeof(double), cudaMemcpyHostToDevice));
     {
         const int th = 256;
         const long long nb = (ns + th - 1) / th;
-        k_seeds<<<(unsigned)nb, th, 0, p->stream>>>(lmax, np, dx64, dst64, dlog2c, dA64, p->tab.c64, p->tab.ls, ds0, ds1);
+        k_seeds<<<(unsigned)nb, th, 0, p->stream>>>(lmax, np, t.x64, dst64, dlog2c, t.A64, t.c64, t.ls, t.s0_64,
+                                                     t.s1_64);
         WF_CUDA(cudaGetLastError());
     }
-    if ((st = plan_alloc(p, &p->tab.A, nalm * es)) != WF_OK) return st;
-    if ((st = plan_alloc(p, &p->tab.c, nalm * es)) != WF_OK) return st;
-    if ((st = plan_alloc(p, &p->tab.s0, ns * es)) != WF_OK) return st;
-    if ((st = plan_alloc(p, &p->tab.s1, ns * es)) != WF_OK) return st;
-    if ((st = plan_alloc(p, &p->tab.x, np * es)) != WF_OK) return st;
-    const int cvb = 1024;
     if (f32) {
-        k_to_T<float><<<cvb, 256, 0, p->stream>>>(dA64, (float *)p->tab.A, nalm);
-        k_to_T<float><<<cvb, 256, 0, p->stream>>>(p->tab.c64, (float *)p->tab.c, nalm);
-        k_to_T<float><<<cvb, 256, 0, p->stream>>>(ds0, (float *)p->tab.s0, ns);
-        k_to_T<float><<<cvb, 256, 0, p->stream>>>(ds1, (float *)p->tab.s1, ns);
-        k_to_T<float><<<cvb, 256, 0, p->stream>>>(dx64, (float *)p->tab.x, np);
-    } else {
-        WF_CUDA(cudaMemcpyAsync(p->tab.A, dA64, nalm * 8, cudaMemcpyDeviceToDevice, p->stream));
-        WF_CUDA(cudaMemcpyAsync(p->tab.c, p->tab.c64, nalm * 8, cudaMemcpyDeviceToDevice, p->stream));
-        WF_CUDA(cudaMemcpyAsync(p->tab.s0, ds0, ns * 8, cudaMemcpyDeviceToDevice, p->stream));
-        WF_CUDA(cudaMemcpyAsync(p->tab.s1, ds1, ns * 8, cudaMemcpyDeviceToDevice, p->stream));
-        WF_CUDA(cudaMemcpyAsync(p->tab.x, dx64, np * 8, cudaMemcpyDeviceToDevice, p->stream));
+        if ((st = plan_alloc(p, (void **)&t.A32, nalm * sizeof(float))) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&t.B32, nalm * sizeof(float))) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&t.x32, np * sizeof(float))) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&t.w32, np * sizeof(float))) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&t.ls_mx, ns * sizeof(int))) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&t.s0_mx, ns * sizeof(float))) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&t.s1_mx, ns * sizeof(float))) != WF_OK) return st;
+        std::vector<float> Af(nalm), Bf(nalm), xf(np), wf(np);
+        for (long long i = 0; i < nalm; ++i) {
+            Af[i] = (float)A[i];
+            Bf[i] = (float)Bm2[i];
+        }
+        for (int i = 0; i < np; ++i) {
+            xf[i] = (float)xpair[i];
+            wf[i] = (float)wpair[i];
+        }
+        WF_CUDA(cudaMemcpy(t.A32, Af.data(), nalm * sizeof(float), cudaMemcpyHostToDevice));
+        WF_CUDA(cudaMemcpy(t.B32, Bf.data(), nalm * sizeof(float), cudaMemcpyHostToDevice));
+        WF_CUDA(cudaMemcpy(t.x32, xf.data(), np * sizeof(float), cudaMemcpyHostToDevice));
+        WF_CUDA(cudaMemcpy(t.w32, wf.data(), np * sizeof(float), cudaMemcpyHostToDevice));
+        t.lc_mx = -1;
+        if ((st = hp_set_low_block(p, 0)) != WF_OK) return st;
     }
-    WF_CUDA(cudaGetLastError());
     WF_CUDA(cudaStreamSynchronize(p->stream));
-    cudaFree(dA64);
-    cudaFree(dx64);
     cudaFree(dst64);
     cudaFree(dlog2c);
-    cudaFree(ds0);
-    cudaFree(ds1);
+    return WF_OK;
+}
+
+// Select the FP64 block l < lc of the mixed path and build the FP32 seeds
+// that restart the recurrence at lc (cached for the current lc).
+wf_status hp_set_low_block(wf_plan p, int lc)
+{
+    HpTables &t = p->tab;
+    if (p->prec == WF_PREC_FP64) return WF_OK;
+    if (lc < 0) lc = 0;
+    if (lc > p->lmax + 1) lc = p->lmax + 1;
+    if (lc == t.lc_mx) return WF_OK;
+    const long long ns = (long long)(p->lmax + 1) * p->npairs;
+    const int th = 256;
+    k_restart_seeds<<<(unsigned)((ns + th - 1) / th), th, 0, p->stream>>>(p->lmax, p->npairs, lc, t.x64, t.A64, t.ls,
+                                                                        t.s0_64, t.s1_64, t.ls_mx, t.s0_mx, t.s1_mx);
+    WF_CUDA(cudaGetLastError());
+    if (lc > 0 && lc > t.glow_cap) {
+        wf_status st = plan_alloc(p, (void **)&p->ws.Glow, (size_t)p->npairs * lc * 2 * sizeof(double2));
+        if (st != WF_OK) return st;
+        t.glow_cap = lc;
+    }
+    t.lc_mx = lc;
     return WF_OK;
 }
 
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
 {
-    return p->prec == WF_PREC_FP64 ? launch_syn<double>(p, alm, L) : launch_syn<float>(p, alm, L);
+    const HpTables &t = p->tab;
+    if (p->prec == WF_PREC_FP64) return launch_syn64(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1);
+    const int gx = (p->npairs + MXP * LEG_THREADS - 1) / (MXP * LEG_THREADS);
+    dim3 grid(gx, L + 1);
+    const size_t sm = syn_mx_smem(L);
+    WF_CUDA(cudaFuncSetAttribute(k_legsyn_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_legsyn_mx<<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, t.A32, t.B32, t.c64, t.ls_mx,
+                                                       t.s0_mx, t.s1_mx, t.x32, t.w32, (float2 *)p->ws.G);
+    WF_CUDA(cudaGetLastError());
+    if (t.lc_mx > 0) return launch_syn64(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap);
+    return WF_OK;
 }
 
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old, double2 *out)
 {
-    return p->prec == WF_PREC_FP64 ? launch_ana<double>(p, L, mode, ba, a_old, out)
-                                   : launch_ana<float>(p, L, mode, ba, a_old, out);
+    const HpTables &t = p->tab;
+    if (p->prec == WF_PREC_FP64) return launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out);
+    const double2 *low = nullptr;
+    if (t.lc_mx > 0) {
+        BlendArgs none;
+        wf_status st = launch_ana64<float>(p, L, t.lc_mx, p->ws.F, LEG_ADJOINT, none, nullptr, p->ws.b_low);
+        if (st != WF_OK) return st;
+        low = p->ws.b_low;
+    }
+    const size_t sm = ana_mx_smem(L);
+    WF_CUDA(cudaFuncSetAttribute(k_legana_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_legana_mx<<<L + 1, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, t.lc_mx, (const float2 *)p->ws.F,
+                                                        t.A32, t.B32, t.ls_mx, t.s0_mx, t.s1_mx, t.x32, t.w32, t.c64,
+                                                        (int)mode, p->omega, ba, low, a_old, out, p->ws.part_harm);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
 }
 
 }  // namespace wf

@@ -74,37 +74,131 @@ void host_fft(std::vector<double2> &x)
 // ---------------------------------------------------------------------------
 // device FFT helpers
 // ---------------------------------------------------------------------------
-// In-place radix-2 DIT FFT of length 2^logN in shared memory, all threads of
-// the CTA.  sign -1: e^{-2 pi i jk/N}; +1: e^{+2 pi i jk/N} (unnormalised).
-// tw[t] = e^{-2 pi i t / 2^logNmax}, t < 2^(logNmax-1).
+// In-place power-of-two FFT in shared memory by all threads of the CTA:
+// Stockham autosort passes with radix-8 butterflies held in registers (one
+// radix-2 or radix-4 head pass when log2 N is not a multiple of 3).  Each
+// pass reads every element once into registers, waits at a barrier, and
+// writes every element once, so shared memory sees 2 log8(N) round trips
+// instead of 2 log2(N) for radix-2.  sign -1: e^{-2 pi i jk/N}; +1:
+// e^{+2 pi i jk/N} (unnormalised).  tw[t] = e^{-2 pi i t / 2^logNmax}, full circle.
+// Supports N <= 8192 with RING_THREADS = 512 threads (two radix-8 butterflies per thread).
 template <typename T>
-__device__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *__restrict__ tw, int logNmax)
+__device__ __forceinline__ cx<T> mul_i(cx<T> a, int sign)
 {
-    const int N = 1 << logN;
-    if (logN == 0) return;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int j = (int)(__brev((unsigned)i) >> (32 - logN));
-        if (i < j) {
-            const cx<T> a = x[i];
-            x[i] = x[j];
-            x[j] = a;
+    return sign > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);  // (sign i) a
+}
+
+// Radix-R DFT in registers, in place, decimation in frequency: on return
+// v[k] holds output X[brev_R(k)] (bit-reversed index), which the caller
+// undoes at compile time when it stores.
+template <typename T>
+__device__ __forceinline__ void bfly(cx<T> &a, cx<T> &b)
+{
+    const cx<T> t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <typename T, int R> struct SmallDft;
+template <typename T> struct SmallDft<T, 2> {
+    static __device__ __forceinline__ void run(cx<T> (&v)[2], int) { bfly<T>(v[0], v[1]); }
+    static __device__ __forceinline__ constexpr int out(int k) { return k; }
+};
+template <typename T> struct SmallDft<T, 4> {
+    static __device__ __forceinline__ void run(cx<T> (&v)[4], int sign)
+    {
+        bfly<T>(v[0], v[2]);
+        bfly<T>(v[1], v[3]);
+        v[3] = mul_i<T>(v[3], sign);
+        bfly<T>(v[0], v[1]);
+        bfly<T>(v[2], v[3]);
+    }
+    static __device__ __forceinline__ constexpr int out(int k) { return ((k & 1) << 1) | ((k >> 1) & 1); }
+};
+template <typename T> struct SmallDft<T, 8> {
+    static __device__ __forceinline__ void run(cx<T> (&v)[8], int sign)
+    {
+        const T c = (T)0.70710678118654752440;
+        const T s = sign > 0 ? c : -c;
+        bfly<T>(v[0], v[4]);
+        bfly<T>(v[1], v[5]);
+        bfly<T>(v[2], v[6]);
+        bfly<T>(v[3], v[7]);
+        v[5] = cmul(v[5], mk<T>(c, s));
+        v[6] = mul_i<T>(v[6], sign);
+        v[7] = cmul(v[7], mk<T>(-c, s));
+        bfly<T>(v[0], v[2]);
+        bfly<T>(v[1], v[3]);
+        bfly<T>(v[4], v[6]);
+        bfly<T>(v[5], v[7]);
+        v[3] = mul_i<T>(v[3], sign);
+        v[7] = mul_i<T>(v[7], sign);
+        bfly<T>(v[0], v[1]);
+        bfly<T>(v[2], v[3]);
+        bfly<T>(v[4], v[5]);
+        bfly<T>(v[6], v[7]);
+    }
+    static __device__ __forceinline__ constexpr int out(int k)
+    {
+        return ((k & 1) << 2) | (k & 2) | ((k >> 2) & 1);
+    }
+};
+
+template <typename T, int R, int LOGR, int BPT>
+__device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *__restrict__ tw,
+                                              int logNmax)
+{
+    const int NR = (1 << logN) >> LOGR;
+    const int Ns = 1 << logNs;
+    const int tsh = logNmax - logNs - LOGR;
+    cx<T> v[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = b * blockDim.x + threadIdx.x;
+        if (j < NR) {
+            const int k = j & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                cx<T> a = x[j + r * NR];
+                if (r > 0 && k > 0) {
+                    cx<T> w = tw[(k * r) << tsh];
+                    if (sign > 0) w.y = -w.y;
+                    a = cmul(a, w);
+                }
+                v[b][r] = a;
+            }
+            SmallDft<T, R>::run(v[b], sign);
         }
     }
     __syncthreads();
-    for (int s = 1; s <= logN; ++s) {
-        const int half = 1 << (s - 1);
-        const int tsh = logNmax - s;
-        for (int b = threadIdx.x; b < N / 2; b += blockDim.x) {
-            const int pos = b & (half - 1);
-            const int i0 = ((b >> (s - 1)) << s) + pos;
-            const int i1 = i0 + half;
-            cx<T> w = tw[pos << tsh];
-            if (sign > 0) w.y = -w.y;
-            const cx<T> u = x[i0], v = cmul(x[i1], w);
-            x[i0] = cadd(u, v);
-            x[i1] = csub(u, v);
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = b * blockDim.x + threadIdx.x;
+        if (j < NR) {
+            const int k = j & (Ns - 1);
+            const int d = ((j >> logNs) << (logNs + LOGR)) + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[d + SmallDft<T, R>::out(r) * Ns] = v[b][r];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *__restrict__ tw, int logNmax)
+{
+    int logNs = 0;
+    const int head = logN % 3;
+    if (head == 1) {
+        stockham_pass<T, 2, 1, 8>(x, logN, 0, sign, tw, logNmax);
+        logNs = 1;
+    } else if (head == 2) {
+        stockham_pass<T, 4, 2, 4>(x, logN, 0, sign, tw, logNmax);
+        logNs = 2;
+    }
+    while (logNs < logN) {
+        stockham_pass<T, 8, 3, 2>(x, logN, logNs, sign, tw, logNmax);
+        logNs += 3;
     }
 }
 
@@ -194,13 +288,15 @@ struct RingCommon {
     int npairs, lmax, L, logNmax;
     const RingTab *rings;
     long long scr_stride;
+    const double2 *Glow;  // mixed path: FP64-block coefficients for m < lc (or null)
+    int lc, glow_stride;
 };
 
 // ---------------------------------------------------------------------------
 // synthesis side: fold -> inverse ring DFT -> blend (or write the map)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(RING_THREADS) k_ringsyn(RingCommon rc, const cx<T> *__restrict__ roots,
+__global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, const cx<T> *__restrict__ roots,
                                                           const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
                                                           cx<T> *__restrict__ scr, const cx<T> *__restrict__ G,
                                                           int mode, const T *__restrict__ r, const T *__restrict__ nu,
@@ -223,17 +319,27 @@ __global__ void __launch_bounds__(RING_THREADS) k_ringsyn(RingCommon rc, const c
         const cx<T> *g = G + (size_t)pair * (rc.lmax + 1) * 2;
         cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
         const bool south = R.offS >= 0;
+        const double2 *gl = rc.Glow ? rc.Glow + (size_t)pair * rc.glow_stride * 2 : nullptr;
+        auto coef = [&](int m, int h) -> cx<T> {
+            cx<T> v = g[2 * m + h];
+            if (gl && m < rc.lc) {
+                const double2 w = gl[2 * m + h];
+                v.x += (T)w.x;
+                v.y += (T)w.y;
+            }
+            return v;
+        };
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             cx<T> hn = mk<T>(0, 0), hs = mk<T>(0, 0);
             for (int m = k; m <= L; m += n) {
                 const cx<T> ph = root[q ? (m % twon) : 0];
-                hn = cadd(hn, cmul(g[2 * m], ph));
-                hs = cadd(hs, cmul(g[2 * m + 1], ph));
+                hn = cadd(hn, cmul(coef(m, 0), ph));
+                hs = cadd(hs, cmul(coef(m, 1), ph));
             }
             for (int m = (k == 0 ? n : n - k); m <= L; m += n) {
                 const cx<T> ph = root[q ? (m % twon) : 0];
-                hn = cadd(hn, cconj(cmul(g[2 * m], ph)));
-                hs = cadd(hs, cconj(cmul(g[2 * m + 1], ph)));
+                hn = cadd(hn, cconj(cmul(coef(m, 0), ph)));
+                hs = cadd(hs, cconj(cmul(coef(m, 1), ph)));
             }
             if (!south) hs = mk<T>(0, 0);
             in[k] = mk<T>(hn.x - hs.y, hn.y + hs.x);
@@ -274,7 +380,7 @@ __global__ void __launch_bounds__(RING_THREADS) k_ringsyn(RingCommon rc, const c
 // analysis side: pack -> forward ring DFT -> unfold to F_m, m <= L
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(RING_THREADS) k_ringana(RingCommon rc, const cx<T> *__restrict__ roots,
+__global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, const cx<T> *__restrict__ roots,
                                                           const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
                                                           cx<T> *__restrict__ scr, const T *__restrict__ map,
                                                           cx<T> *__restrict__ F)
@@ -315,7 +421,12 @@ template <typename T> struct RingLaunch {
     static wf_status syn(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *omap)
     {
         const HpTables &t = p->tab;
-        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue};
+        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0};
+        if (p->prec != WF_PREC_FP64 && t.lc_mx > 0) {
+            rc.Glow = p->ws.Glow;
+            rc.lc = t.lc_mx;
+            rc.glow_stride = t.glow_cap;
+        }
         const size_t sm = (size_t)t.bmax * sizeof(cx<T>);
         WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
@@ -328,7 +439,7 @@ template <typename T> struct RingLaunch {
     static wf_status ana(wf_plan p, int L, const void *map)
     {
         const HpTables &t = p->tab;
-        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue};
+        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0};
         const size_t sm = (size_t)t.bmax * sizeof(cx<T>);
         WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_ringana<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
@@ -440,7 +551,8 @@ wf_status hp_build_ring_tables(wf_plan p)
         }
     }
     const int logNmax = ilog2(nmaxF);
-    std::vector<double2> tw((size_t)1 << (logNmax - 1));
+    if (bmax > 8192) return set_error(WF_EUNSUPPORTED, "ring FFT longer than 8192 (nside > 2048)");
+    std::vector<double2> tw((size_t)1 << logNmax);
     for (size_t t = 0; t < tw.size(); ++t) {
         const double a = -2.0 * M_PI * (double)t / (double)(1LL << logNmax);
         tw[t] = make_double2(std::cos(a), std::sin(a));

@@ -1,0 +1,92 @@
+"""Mixed-precision path (FP32 Legendre/ring kernels, FP64 seeds, a_lm,
+reductions and low-l block) against the oracle and the FP64 GPU path."""
+import numpy as np
+import pytest
+
+import oracle
+import wf_inputs as gen
+from gpu_util import T, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    import torch
+
+    import paper_1210_4931_gb300 as w
+
+    w.load()
+    torch.cuda.set_device(0)
+    return w
+
+
+@pytest.mark.parametrize("nside,lmax", [(16, 32), (64, 128), (128, 256)])
+def test_mixed_basis_change_accuracy(wf, nside, lmax):
+    """FP32 transforms of a CMB-like a_lm: within 2e-5 of the oracle (max norm,
+    relative to the map's max) -- the FP32 recurrence's error budget."""
+    import torch
+
+    rng = np.random.default_rng(nside)
+    cl = gen.cmb_like_cl(lmax, 4 * 3438.0 / lmax)
+    a = gen.alm_unit_gaussian(rng, lmax) * np.sqrt(cl[gen.alm_ell(lmax)])
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed")
+    m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    wf.wf_alm2map(plan, T(a), lmax, m)
+    assert rel(m.cpu().numpy(), oracle.synthesis(nside, lmax, lmax, a)) < 2e-5
+    f = oracle.synthesis(nside, lmax, lmax, a) + 0.1 * rng.standard_normal(plan.npix)
+    out = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+    wf.wf_map2alm_adjoint(plan, T(f), lmax, out)
+    assert rel(out.cpu().numpy(), oracle.adjoint_synthesis(nside, lmax, lmax, f)) < 2e-5
+    plan.close()
+
+
+def _hard_case(nside, lmax, seed):
+    # noise dynamic range 1e4 and a galactic cut: S_l / tau_h reaches ~1e6 at low l
+    P = gen.healpix_problem(nside, lmax, seed, fwhm_arcmin=5.0 * 2048 / nside, noise_range=1e4, b_cut_deg=15.0,
+                            n_disks=20, disk_radius_deg=min(8.0, 0.3 * 2048 / nside))
+    basis = oracle.HealpixBasis(nside, lmax)
+    d = basis.synth(P["a_signal"]) + P["noise"]
+    return P, basis, d
+
+
+def test_mixed_solve_is_stable_and_matches_fp64(wf):
+    """The mixed iteration stays contractive where S / tau_h is large (FP64
+    low-l block) and its result matches the FP64 GPU path replaying the same
+    schedule; the true residual of the mixed result, evaluated with the
+    oracle's FP64 operator, is within 1e-5 of the FP64 one."""
+    import torch
+
+    nside, lmax = 32, 64
+    P, basis, d = _hard_case(nside, lmax, gen.seed_for(3, 50))
+    obs = P["mask"] > 0
+    nu = np.where(obs, 1.0 / P["noise_var"], 0.0)
+    tau = float(P["noise_var"][obs].min())
+    S = basis.per_mode(P["c_ell"])
+    out = {}
+    for prec in ("mixed", "fp64"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+        wf.wf_set_options(plan, maxiter=3000)
+        if prec == "fp64":
+            wf.wf_set_schedule(plan, out["mixed"][0]["lambda_trace"], out["mixed"][0]["L_trace"])
+        s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        alm = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+        rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-5, s, alm,
+                          trace_cap=3100)
+        out[prec] = (rep, alm.cpu().numpy(), s.cpu().numpy())
+        plan.close()
+    rm, rf = out["mixed"][0], out["fp64"][0]
+    assert rm["mixed_lc"] > 2  # the FP64 low-l block is in use on this problem
+    res = rm["resid_trace"][~np.isnan(rm["resid_trace"])]
+    res64 = rf["resid_trace"][~np.isnan(rf["resid_trace"])]
+    # contractive like the FP64 path: no growth, and the same residual to within the FP32 floor
+    n = len(res)
+    assert res[-1] < res[n // 2] < res[n // 8]
+    assert abs(res[-1] - res64[-1]) < 0.05 * res64[-1] + 1e-5
+    # true residual of both results with the oracle's FP64 operator (one step at lambda = 1)
+    true = {}
+    for prec in ("mixed", "fp64"):
+        r1 = oracle.messenger_solve(basis, nu * d, nu, S, tau, replay=[(1.0, lmax)], a0=out[prec][1])
+        true[prec] = r1["resid"][0]
+    assert abs(true["mixed"] - true["fp64"]) < 1e-5
+    assert rel(out["mixed"][2], out["fp64"][2]) < 1e-3
