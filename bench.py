@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--full-band-iters", type=int, default=0,
+                    help="replay this many lambda = 1, L = lmax iterations instead of the cooling schedule "
+                         "(steady-state timing and profiling)")
     return ap.parse_args()
 
 
@@ -243,7 +246,9 @@ def run_ours(args):
     s_out = torch.empty(plan.npix, dtype=torch.float64, device=dev)
     alm_out = torch.empty(plan.nalm, dtype=torch.complex128, device=dev)
     wf.wf_set_options(plan, profile=1, maxiter=args.maxiter)
-    cap = args.maxiter + 16
+    if args.full_band_iters > 0:
+        wf.wf_set_schedule(plan, [1.0] * args.full_band_iters, [lmax] * args.full_band_iters)
+    cap = max(args.maxiter, args.full_band_iters) + 16
 
     def solve():
         return wf.wf_solve(plan, d, nv, mask, cl, args.tol, s_out, alm_out, trace_cap=cap)

@@ -34,6 +34,7 @@ wf_status set_error(wf_status s, const char *fmt, ...)
 
 wf_status cuda_check(cudaError_t e, const char *what)
 {
+    (void)cudaGetLastError();  // do not leave a non-sticky error behind for the caller's next CUDA call
     if (e == cudaErrorMemoryAllocation) return set_error(WF_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
     return set_error(WF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }

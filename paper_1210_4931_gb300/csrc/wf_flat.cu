@@ -473,7 +473,14 @@ wf_status flat_create(wf_plan p)
     if ((st = plan_alloc(p, (void **)&f->levels, 64 * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&f->status, sizeof(FlatStatus))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&p->ws.redu, 16 * 8)) != WF_OK) return st;
-    WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->smem));
+    // the attribute is per function, shared by every plan: set it for the largest grid
+    // (n = FLAT_MAXN) so that a smaller plan never lowers it under a larger one
+    {
+        const int nm = FLAT_MAXN, nhm = nm / 2 + 1, Pm = (nhm + FLAT_CS - 1) / FLAT_CS, RPm = nm / FLAT_CS;
+        const size_t smax = (size_t)(nm / 2) * 16 + (size_t)Pm * nm * 16 * 2 + (size_t)RPm * nhm * 16 +
+                            (size_t)FLAT_WARPS * nm * 16 + (size_t)Pm * nm * 8 + (size_t)RPm * nm * 8 * 2;
+        WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    }
     return WF_OK;
 }
 

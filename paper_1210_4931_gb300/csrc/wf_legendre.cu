@@ -41,7 +41,7 @@ namespace {
 
 constexpr double SEED_LOG2_THRESHOLD = -80.0;
 constexpr int MXP = 4;               // ring pairs per thread in the mixed synthesis
-constexpr int MXPA = 8;              // ring pairs per lane in the mixed analysis
+constexpr int MXPA = 4;              // ring pairs per lane in the mixed analysis
 constexpr float X_DIFFERENCE_FORM = 0.4f;
 constexpr int BIG = INT_MAX / 2;
 
@@ -271,9 +271,10 @@ __device__ __forceinline__ void block_reduce2(double &a, double &b, double (*red
 
 // Eq. (4) epilogue shared by both precisions: t_hat = Omega (c acc + low),
 // a_new = S/(S + lam tau_h) t_hat, chi^2 of a_old, lambda = 1 residual.
+template <typename ACC>
 __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long base, int mode, double omega,
                                                const BlendArgs &ba, const double *__restrict__ c64,
-                                               const double2 *acc, const double2 *__restrict__ low, int low_lim,
+                                               const ACC *acc, const double2 *__restrict__ low, int low_lim,
                                                const double2 *__restrict__ a_old, double2 *__restrict__ out,
                                                double *__restrict__ part, double (*red)[LEG_THREADS / 32])
 {
@@ -284,8 +285,8 @@ __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long
         const long long idx = base + j;
         double2 b = make_double2(0.0, 0.0);
         if (l <= L) {
-            b.x = c64[idx] * acc[j].x;
-            b.y = c64[idx] * acc[j].y;
+            b.x = c64[idx] * (double)acc[j].x;
+            b.y = c64[idx] * (double)acc[j].y;
             if (low && l < low_lim) {
                 const double2 q = low[idx];
                 b.x += q.x;
@@ -624,7 +625,7 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L,
                                            const float *__restrict__ sA, const float *__restrict__ sB,
                                            const float2 (&FEr)[MXPA / 2], const float2 (&FEi)[MXPA / 2],
                                            const float2 (&FOr)[MXPA / 2], const float2 (&FOi)[MXPA / 2],
-                                           double2 *acc, int lane)
+                                           float2 *acc, int lane)
 {
     constexpr int NPK = MXPA / 2;
     float2 Sa[NPK], Sb[NPK], V0[NPK], V1[NPK];
@@ -661,8 +662,8 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L,
         if ((lane & 1) == 0) {
             const int l = l0 + (lane >> 1);
             if (l <= L) {
-                atomicAdd(&acc[l - m].x, (double)vr[0]);
-                atomicAdd(&acc[l - m].y, (double)vi[0]);
+                atomicAdd(&acc[l - m].x, vr[0]);
+                atomicAdd(&acc[l - m].y, vi[0]);
             }
         }
     }
@@ -682,24 +683,33 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana_mx(int lmax, int L, int 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[2][LEG_THREADS / 32];
+    __shared__ int next_group;
     const int m = blockIdx.x;
     const int nl = L - m + 1;
     const int nlp = nl + MX_CH + 2;
     const long long base = mbase(lmax, m);
-    double2 *acc = reinterpret_cast<double2 *>(smem_raw);
+    // FP32 accumulators: each entry sums one 32-lane reduce-scatter result per
+    // group of 128 ring pairs; the epilogue converts to FP64
+    float2 *acc = reinterpret_cast<float2 *>(smem_raw);
     float *sA = reinterpret_cast<float *>(acc + nlp);
     float *sB = sA + nlp;
     for (int i = threadIdx.x; i < nlp; i += blockDim.x) {
-        acc[i] = make_double2(0.0, 0.0);
+        acc[i] = make_float2(0.f, 0.f);
         sA[i] = (i < nl) ? A[base + i] : 0.f;
         sB[i] = (i < nl) ? B[base + i] : 0.f;
     }
+    if (threadIdx.x == 0) next_group = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int per_group = 32 * MXPA;
     const int ngroups = (npairs + per_group - 1) / per_group;
     const size_t pstride = (size_t)(lmax + 1) * 2;
-    for (int grp = warp; grp < ngroups; grp += nwarps) {
+    for (;;) {
+        // warps take groups of ring pairs dynamically (their work differs with latitude)
+        int grp = 0;
+        if (lane == 0) grp = atomicAdd(&next_group, 1);
+        grp = __shfl_sync(0xffffffffu, grp, 0);
+        if (grp >= ngroups) break;
         const int p0 = grp * per_group + lane * MXPA;
         MxPairs<MXPA> P;
         mx_load_pairs<MXPA>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
@@ -746,7 +756,7 @@ template <typename T, int CH>
 size_t ana_smem(int L) { return (size_t)(L + 1 + CH + 2) * (sizeof(double2) + sizeof(T)) + 16; }
 
 size_t syn_mx_smem(int L) { return (size_t)((L + 2) / 2 + 2) * 2 * sizeof(float4) + 16; }
-size_t ana_mx_smem(int L) { return (size_t)(L + 1 + MX_CH + 2) * (sizeof(double2) + 2 * sizeof(float)) + 16; }
+size_t ana_mx_smem(int L) { return (size_t)(L + 1 + MX_CH + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32; }
 
 wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *G, int gstride)
 {

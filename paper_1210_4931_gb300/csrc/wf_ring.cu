@@ -290,7 +290,18 @@ struct RingCommon {
     long long scr_stride;
     const double2 *Glow;  // mixed path: FP64-block coefficients for m < lc (or null)
     int lc, glow_stride;
+    int bmax;             // shared FFT buffer length
+    int zsmem;            // 1: Bluestein input/output buffers follow the FFT buffer in shared memory
 };
+
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// prefetch a byte range into L2, one 128-byte line per thread and step
+__device__ __forceinline__ void prefetch_range(const void *base, size_t bytes)
+{
+    const char *b = reinterpret_cast<const char *>(base);
+    for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128) prefetch_l2(b + off);
+}
 
 // ---------------------------------------------------------------------------
 // synthesis side: fold -> inverse ring DFT -> blend (or write the map)
@@ -306,12 +317,13 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[RING_THREADS / 32];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *zin = scr + (size_t)blockIdx.x * rc.scr_stride;
+    cx<T> *zin = rc.zsmem ? buf + rc.bmax : scr + (size_t)blockIdx.x * rc.scr_stride;
     cx<T> *zout = zin + rc.scr_stride / 2;
     const int L = rc.L;
     const T lt = lam * tau, lm1t = (lam - (T)1) * tau;
     double chi = 0.0;
     for (int it = blockIdx.x; it < rc.npairs; it += gridDim.x) {
+        T chi_pair = 0;  // per-thread partial of this pair in the working precision
         const int pair = rc.npairs - 1 - it;
         const RingTab R = rc.rings[pair];
         const int n = R.n, q = R.q, twon = 2 * n;
@@ -319,6 +331,19 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
         const cx<T> *g = G + (size_t)pair * (rc.lmax + 1) * 2;
         cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
         const bool south = R.offS >= 0;
+        if (it + (int)gridDim.x < rc.npairs) {  // next pair of this CTA: pull its rows into L2
+            const int nxt = rc.npairs - 1 - (it + (int)gridDim.x);
+            const RingTab Rn = rc.rings[nxt];
+            prefetch_range(G + (size_t)nxt * (rc.lmax + 1) * 2, (size_t)(L + 1) * 2 * sizeof(cx<T>));
+            if (mode == RS_BLEND) {
+                prefetch_range(r + Rn.offN, (size_t)Rn.n * sizeof(T));
+                prefetch_range(nu + Rn.offN, (size_t)Rn.n * sizeof(T));
+                if (Rn.offS >= 0) {
+                    prefetch_range(r + Rn.offS, (size_t)Rn.n * sizeof(T));
+                    prefetch_range(nu + Rn.offS, (size_t)Rn.n * sizeof(T));
+                }
+            }
+        }
         const double2 *gl = rc.Glow ? rc.Glow + (size_t)pair * rc.glow_stride * 2 : nullptr;
         auto coef = [&](int m, int h) -> cx<T> {
             cx<T> v = g[2 * m + h];
@@ -357,17 +382,18 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
                     const T s = zz.x, nv = nu[iN], rv = r[iN];
                     const T den = (T)1 + lm1t * nv;
                     tmap[iN] = s + lt * (rv - nv * s) / den;
-                    chi += (double)((nv * s * s - (T)2 * rv * s) / den);
+                    chi_pair += (nv * s * s - (T)2 * rv * s) / den;
                 }
                 if (south) {
                     const long long iS = R.offS + j;
                     const T s = zz.y, nv = nu[iS], rv = r[iS];
                     const T den = (T)1 + lm1t * nv;
                     tmap[iS] = s + lt * (rv - nv * s) / den;
-                    chi += (double)((nv * s * s - (T)2 * rv * s) / den);
+                    chi_pair += (nv * s * s - (T)2 * rv * s) / den;
                 }
             }
         }
+        chi += (double)chi_pair;
         __syncthreads();
     }
     if (mode == RS_BLEND) {
@@ -387,7 +413,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *zin = scr + (size_t)blockIdx.x * rc.scr_stride;
+    cx<T> *zin = rc.zsmem ? buf + rc.bmax : scr + (size_t)blockIdx.x * rc.scr_stride;
     cx<T> *zout = zin + rc.scr_stride / 2;
     const int L = rc.L;
     for (int it = blockIdx.x; it < rc.npairs; it += gridDim.x) {
@@ -397,6 +423,11 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
         const cx<T> *root = roots + R.rootOff;
         cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
         const bool south = R.offS >= 0;
+        if (it + (int)gridDim.x < rc.npairs) {
+            const RingTab Rn = rc.rings[rc.npairs - 1 - (it + (int)gridDim.x)];
+            prefetch_range(map + Rn.offN, (size_t)Rn.n * sizeof(T));
+            if (Rn.offS >= 0) prefetch_range(map + Rn.offS, (size_t)Rn.n * sizeof(T));
+        }
         for (int j = threadIdx.x; j < n; j += blockDim.x)
             in[j] = mk<T>(map[R.offN + j], south ? map[R.offS + j] : (T)0);
         __syncthreads();
@@ -421,13 +452,13 @@ template <typename T> struct RingLaunch {
     static wf_status syn(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *omap)
     {
         const HpTables &t = p->tab;
-        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0};
+        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0, t.bmax, zsmem()};
         if (p->prec != WF_PREC_FP64 && t.lc_mx > 0) {
             rc.Glow = p->ws.Glow;
             rc.lc = t.lc_mx;
             rc.glow_stride = t.glow_cap;
         }
-        const size_t sm = (size_t)t.bmax * sizeof(cx<T>);
+        const size_t sm = smem_bytes(t);
         WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
             rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
@@ -439,8 +470,8 @@ template <typename T> struct RingLaunch {
     static wf_status ana(wf_plan p, int L, const void *map)
     {
         const HpTables &t = p->tab;
-        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0};
-        const size_t sm = (size_t)t.bmax * sizeof(cx<T>);
+        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0, t.bmax, zsmem()};
+        const size_t sm = smem_bytes(t);
         WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_ringana<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
                                                                   (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
@@ -448,9 +479,16 @@ template <typename T> struct RingLaunch {
         WF_CUDA(cudaGetLastError());
         return WF_OK;
     }
+    // FP32: the Bluestein buffers fit next to the FFT buffer (the kernel runs one CTA
+    // per SM anyway, bounded by registers); FP64 keeps them in per-CTA global scratch
+    static int zsmem() { return sizeof(T) == 4 ? 1 : 0; }
+    static size_t smem_bytes(const HpTables &t)
+    {
+        return ((size_t)t.bmax + (zsmem() ? 2 * (size_t)t.maxBlue : 0)) * sizeof(cx<T>);
+    }
     static wf_status grid(wf_plan p, int *out)
     {
-        const size_t sm = (size_t)p->tab.bmax * sizeof(cx<T>);
+        const size_t sm = smem_bytes(p->tab);
         WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         int b1 = 0, b2 = 0;

@@ -198,3 +198,19 @@ def test_host_entry_point_matches_device(wf):
     assert rep["converged"]
     assert rel(sh, s.cpu().numpy()) < 1e-13
     plan.close()
+
+
+def test_flat_plans_of_different_sizes_coexist(wf):
+    """A small flat plan created after a large one must not break the large
+    one (per-function launch attributes are shared by all plans)."""
+    import torch
+
+    big = wf.wf_plan_create("flat", n=128)
+    small = wf.wf_plan_create("flat", n=16)
+    P = gen.flat_problem(128, seed=gen.seed_for(1, 55))
+    d = oracle.FlatBasis(128, 128).synth(P["a_signal"]) + P["noise"]
+    s = torch.empty(128 * 128, dtype=torch.float64, device="cuda")
+    rep = wf.wf_solve(big, T(d.ravel()), T(P["noise_var"].ravel()), T(P["mask"].ravel()), T(P["S"].ravel()), 1e-6, s)
+    assert rep["converged"]
+    small.close()
+    big.close()
