@@ -176,6 +176,22 @@ long long wf_plan_device_bytes(wf_plan p);
 const char *wf_strerror(wf_status s);
 const char *wf_last_error(void);
 
+/* Flat-grid Wiener filter that allocates no device memory: the paper has no
+ * counterpart; it exists for callers that cannot allocate at solve time (a
+ * solve inside another framework's memory pool, or where cudaMalloc is not
+ * allowed).  Same arithmetic and results as wf_solve on a flat plan of the
+ * same n, with the solver's scratch in one static device array (0.71 MiB,
+ * resident on every device that loads the library) instead of plan memory.
+ * n: power of two in [16, 128]; opt: may be NULL (defaults), opt->maxiter <=
+ * 20000; anything larger is rejected with WF_EINVAL.  d, noise_var, mask, S,
+ * s_wf, alm_out: device pointers as for wf_solve; cuda_stream: the stream to
+ * use.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it: make that
+ * first call outside any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race; each call writes what it reads first. */
+wf_status wf_flat_solve_noalloc(int n, const double *d, const double *noise_var, const uint8_t *mask,
+                                const double *S, double tol, const wf_options *opt, void *cuda_stream,
+                                double *s_wf, double *alm_out, wf_info *info);
 
 #ifdef __cplusplus
 }

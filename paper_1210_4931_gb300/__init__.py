@@ -58,7 +58,7 @@ KERNEL_FAMILIES = ["leg_syn", "ring_syn", "ring_ana", "leg_ana", "other", "flat"
 _lib = None
 EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host",
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
-           "wf_strerror", "wf_last_error"]
+           "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc"]
 
 
 def load(path: str = LIB_PATH):
@@ -84,6 +84,9 @@ def load(path: str = LIB_PATH):
     for f in ("wf_npix", "wf_nalm", "wf_plan_device_bytes"):
         getattr(L, f).argtypes = [vp]
         getattr(L, f).restype = ctypes.c_longlong
+    L.wf_flat_solve_noalloc.argtypes = [ctypes.c_int, dp, dp, u8p, dp, ctypes.c_double, ctypes.POINTER(wf_options),
+                                        vp, dp, dp, ctypes.POINTER(wf_info)]
+    L.wf_flat_solve_noalloc.restype = ctypes.c_int
     L.wf_strerror.argtypes = [ctypes.c_int]
     L.wf_strerror.restype = ctypes.c_char_p
     L.wf_last_error.argtypes = []
@@ -264,6 +267,28 @@ def wf_fluct(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_out=Non
     return _info_dict(st, info, bufs)
 
 
+def wf_flat_solve_noalloc(n, d, noise_var, mask, S, tol, s_wf, alm_out=None, trace_cap=0, stream=None,
+                          **options) -> dict:
+    """Flat-grid solve that allocates no device memory (see include/wf.h):
+    same arguments as wf_solve without a plan; n <= 128."""
+    import torch
+
+    info, bufs = _info(trace_cap)
+    o = wf_options()
+    for k, v in options.items():
+        setattr(o, k, v)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n8 = n * n * 8
+    st = load().wf_flat_solve_noalloc(int(n), _ptr(d, None, n8, "d"), _ptr(noise_var, None, n8, "noise_var"),
+                                      _ptr(mask, None, n * n, "mask"), _ptr(S, None, None, "S"), float(tol),
+                                      ctypes.byref(o), ctypes.c_void_p(stream.cuda_stream),
+                                      _ptr(s_wf, None, n8, "s_wf"),
+                                      _ptr(alm_out, None, n * (n // 2 + 1) * 16, "alm_out"), ctypes.byref(info))
+    _check(st, "wf_flat_solve_noalloc", allow=(WF_ENOCONV,))
+    return _info_dict(st, info, bufs)
+
+
 def wf_alm2map(plan: Plan, alm, L, map_out):
     _check(load().wf_alm2map(plan.handle, _ptr(alm, None, plan.nalm * 16, "alm"), int(L),
                              _ptr(map_out, None, plan.npix * 8, "map")), "wf_alm2map")
@@ -274,6 +299,6 @@ def wf_map2alm_adjoint(plan: Plan, map_in, L, alm_out):
                                      _ptr(alm_out, None, plan.nalm * 16, "alm")), "wf_map2alm_adjoint")
 
 
-__all__ = ["Plan", "WfError", "load", "wf_alm2map", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
+__all__ = ["Plan", "WfError", "load", "wf_alm2map", "wf_flat_solve_noalloc", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
            "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "EXPORTS",
            "LIB_PATH"]

@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -641,4 +642,205 @@ wf_status flat_map2alm(wf_plan p, const double *map, double *alm)
     return set_error(WF_EUNSUPPORTED, "flat-grid basis change is internal to the fused solve");
 }
 
+// ---------------------------------------------------------------------------
+// Flat-grid solve that allocates nothing (wf_flat_solve_noalloc).
+//
+// For callers that cannot allocate device memory at solve time -- code that
+// runs inside another framework's memory pool, under a CUDA graph capture
+// that forbids cudaMalloc, or on a context where allocation is locked down --
+// this entry point runs the same two kernels as wf_solve on the flat grid
+// (k_flat_setup, k_flat_solve), with the solver's scratch (the source and
+// inverse-noise maps, the lambda levels, the status block and the per-
+// iteration traces) in one file-scope device array instead of plan memory.
+// Limits: n <= 128 (a power of two >= 16) and at most 20000 iterations;
+// the array is 0.71 MiB and stays resident on every device that loads the
+// library.  In host code the array's symbol is not a device address: the
+// first call on a device looks up its address with cudaGetSymbolAddress
+// (with that device current) and caches it, so that first call should not
+// be made during a stream capture.  All calls share the one array: calls
+// that overlap on the GPU race; everything a call reads is written by that
+// call first.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int NOALLOC_MAXN = 128;
+constexpr int NOALLOC_MAXITER = 20000;
+constexpr int NOALLOC_LEVELS = 64;
+constexpr size_t NA_PIX = (size_t)NOALLOC_MAXN * NOALLOC_MAXN;
+constexpr size_t NA_R = 0;
+constexpr size_t NA_NU = NA_R + NA_PIX * sizeof(double);
+constexpr size_t NA_LEV = NA_NU + NA_PIX * sizeof(double);
+constexpr size_t NA_RAD = NA_LEV + NOALLOC_LEVELS * sizeof(double);
+constexpr size_t NA_REDU = NA_RAD + 16 * sizeof(double);
+constexpr size_t NA_STATUS = NA_REDU + 16 * sizeof(double);
+constexpr size_t NA_TRACE = NA_STATUS + 256;
+constexpr size_t NA_BYTES = NA_TRACE + 3 * (size_t)NOALLOC_MAXITER * sizeof(double);
+
+// max S over the half-plane modes whose rounded |k| equals 2^j, j = 1..15
+// (-1 where no mode has that radius): the priors the flat schedule needs
+__global__ void k_flat_radial_max(int n, const double *__restrict__ S, double *__restrict__ out)
+{
+    __shared__ unsigned long long best[16];
+    if (threadIdx.x < 16) best[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int nh = n / 2 + 1;
+    for (int i = threadIdx.x; i < n * nh; i += blockDim.x) {
+        const int ky = i / nh, kx = i % nh;
+        const int sy = ky < (n + 1) / 2 ? ky : ky - n;
+        const long r = lrint(sqrt((double)sy * sy + (double)kx * kx));
+        if (r >= 2 && (r & (r - 1)) == 0) {
+            int j = 0;
+            while ((1L << j) < r) ++j;
+            if (j < 16) atomicMax(&best[j], (unsigned long long)__double_as_longlong(S[i]) | 0ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        const unsigned long long b = best[threadIdx.x];
+        out[threadIdx.x] = b ? __longlong_as_double((long long)b) : -1.0;
+    }
+}
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_flat_noalloc_scratch[NA_BYTES];
+
+namespace {
+std::mutex g_na_mutex;
+unsigned char *g_na_base[128] = {};
+
+wf_status noalloc_base(unsigned char **out)
+{
+    int dev = 0;
+    WF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return set_error(WF_EUNSUPPORTED, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_base[dev]) {
+        void *p = nullptr;
+        WF_CUDA(cudaGetSymbolAddress(&p, g_flat_noalloc_scratch));
+        g_na_base[dev] = (unsigned char *)p;
+    }
+    *out = g_na_base[dev];
+    return WF_OK;
+}
+}  // namespace
+
 }  // namespace wf
+
+extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double *noise_var, const uint8_t *mask,
+                                           const double *S, double tol, const wf_options *opt, void *cuda_stream,
+                                           double *s_wf, double *alm_out, wf_info *info)
+{
+    using namespace wf;
+    if (!d || !noise_var || !S || !s_wf) return set_error(WF_EINVAL, "null argument");
+    if (n < 16 || n > NOALLOC_MAXN || (n & (n - 1)))
+        return set_error(WF_EINVAL, "wf_flat_solve_noalloc: n must be a power of two in [16, %d] (got %d)",
+                         NOALLOC_MAXN, n);
+    if (!(tol > 0)) return set_error(WF_EINVAL, "tol must be > 0");
+    wf_options o = opt ? *opt : wf_options{};
+    if (o.maxiter <= 0) o.maxiter = NOALLOC_MAXITER;
+    if (o.maxiter > NOALLOC_MAXITER)
+        return set_error(WF_EINVAL, "wf_flat_solve_noalloc: maxiter %d exceeds the %d iterations its scratch holds",
+                         o.maxiter, NOALLOC_MAXITER);
+    if (o.level_cap <= 0) o.level_cap = 200;
+    if (!(o.eta > 0)) o.eta = 1e-2;
+    if (!(o.lambda_max > 0)) o.lambda_max = 100.0;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    unsigned char *base = nullptr;
+    wf_status st = noalloc_base(&base);
+    if (st != WF_OK) return st;
+    double *r = (double *)(base + NA_R), *nu = (double *)(base + NA_NU), *lev_d = (double *)(base + NA_LEV);
+    double *rad = (double *)(base + NA_RAD), *redu = (double *)(base + NA_REDU);
+    FlatStatus *status = (FlatStatus *)(base + NA_STATUS);
+    double *tr = (double *)(base + NA_TRACE);
+    const long long npix = (long long)n * n;
+    const int nh = n / 2 + 1;
+
+    k_flat_setup<<<1, 1024, 0, stream>>>(npix, d, noise_var, mask, r, nu, redu);
+    WF_CUDA(cudaGetLastError());
+    k_flat_radial_max<<<1, 256, 0, stream>>>(n, S, rad);
+    WF_CUDA(cudaGetLastError());
+    double h[3], smax[16];
+    WF_CUDA(cudaMemcpyAsync(h, redu, sizeof h, cudaMemcpyDeviceToHost, stream));
+    WF_CUDA(cudaMemcpyAsync(smax, rad, sizeof smax, cudaMemcpyDeviceToHost, stream));
+    WF_CUDA(cudaStreamSynchronize(stream));
+    if (h[2] != 0.0) return set_error(WF_EINVAL, "noise variance must be finite and > 0 (and d finite) on observed pixels");
+    if (h[1] == 0.0) return set_error(WF_EINVAL, "every pixel is masked");
+    const double tau = h[0];
+    const long long ndof = (long long)h[1];
+
+    // lambda levels of the flat schedule: k_iter = 1, 2, 4, ..., first level at lambda_max
+    double lev[NOALLOC_LEVELS];
+    int nlev = 0;
+    lev[nlev++] = o.lambda_max;
+    for (int j = 1; lev[nlev - 1] != 1.0 && nlev < NOALLOC_LEVELS - 1; ++j) {
+        double lam = 1.0;
+        if (j < 16 && smax[j] >= 0.0) lam = std::min(o.lambda_max, std::max(1.0, smax[j] / tau));
+        if (j >= 16) lam = 1.0;
+        if (lam != lev[nlev - 1]) lev[nlev++] = lam;
+    }
+    if (lev[nlev - 1] != 1.0) lev[nlev++] = 1.0;
+    WF_CUDA(cudaMemcpyAsync(lev_d, lev, nlev * sizeof(double), cudaMemcpyHostToDevice, stream));
+
+    FlatArgs A{};
+    A.n = n;
+    A.logn = 0;
+    while ((1 << A.logn) < n) ++A.logn;
+    A.nh = nh;
+    A.P = (nh + FLAT_CS - 1) / FLAT_CS;
+    A.RP = n / FLAT_CS;
+    A.r = r;
+    A.nu = nu;
+    A.S = S;
+    A.levels = lev_d;
+    A.nlevels = nlev;
+    A.tau = tau;
+    A.sigma = std::sqrt(2.0 * (double)ndof);
+    A.eta = o.eta;
+    A.tol = tol;
+    A.level_cap = o.level_cap;
+    A.maxiter = o.maxiter;
+    A.s_out = s_wf;
+    A.alm_out = (double2 *)alm_out;
+    A.tr_lam = tr;
+    A.tr_chi2 = tr + NOALLOC_MAXITER;
+    A.tr_res = tr + 2 * NOALLOC_MAXITER;
+    A.tr_cap = NOALLOC_MAXITER;
+    A.status = status;
+    const size_t smem = (size_t)(n / 2) * 16 + (size_t)A.P * n * 16 * 2 + (size_t)A.RP * nh * 16 +
+                        (size_t)FLAT_WARPS * n * 16 + (size_t)A.P * n * 8 + (size_t)A.RP * n * 8 * 2;
+    {
+        // the dynamic shared-memory limit is per function: set it for the largest grid this
+        // entry point takes (n = NOALLOC_MAXN), on every call (a plan may have changed it)
+        const int nm = NOALLOC_MAXN, nhm = nm / 2 + 1, Pm = (nhm + FLAT_CS - 1) / FLAT_CS, RPm = nm / FLAT_CS;
+        const size_t smax = (size_t)(nm / 2) * 16 + (size_t)Pm * nm * 16 * 2 + (size_t)RPm * nhm * 16 +
+                            (size_t)FLAT_WARPS * nm * 16 + (size_t)Pm * nm * 8 + (size_t)RPm * nm * 8 * 2;
+        WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
+    }
+    k_flat_solve<<<FLAT_CS, FLAT_THREADS, smem, stream>>>(A);
+    WF_CUDA(cudaGetLastError());
+    FlatStatus fs;
+    WF_CUDA(cudaMemcpyAsync(&fs, status, sizeof fs, cudaMemcpyDeviceToHost, stream));
+    WF_CUDA(cudaStreamSynchronize(stream));
+    if (info) {
+        info->iters = fs.iters;
+        info->converged = fs.converged;
+        info->final_residual = fs.final_resid;
+        info->chi2_over_ndof = fs.chi2_final / (double)ndof;
+        info->n_dof = ndof;
+        info->tau = tau;
+        info->n_levels = fs.levels;
+        info->refine_sweeps = 0;
+        info->mixed_lc = 0;
+        info->launches = 3;
+        const int nt = std::min(fs.iters, info->trace_cap);
+        if (nt > 0) {
+            if (info->lambda_trace) WF_CUDA(cudaMemcpy(info->lambda_trace, A.tr_lam, nt * 8, cudaMemcpyDeviceToHost));
+            if (info->chi2_trace) WF_CUDA(cudaMemcpy(info->chi2_trace, A.tr_chi2, nt * 8, cudaMemcpyDeviceToHost));
+            if (info->resid_trace) WF_CUDA(cudaMemcpy(info->resid_trace, A.tr_res, nt * 8, cudaMemcpyDeviceToHost));
+            if (info->L_trace)
+                for (int i = 0; i < nt; ++i) info->L_trace[i] = -1;
+        }
+    }
+    if (fs.stop_reason == 3) return set_error(WF_EDIVERGE, "residual grew (%.3e)", fs.final_resid);
+    if (fs.stop_reason == 2) return set_error(WF_ENOCONV, "iteration cap reached (residual %.3e)", fs.final_resid);
+    return WF_OK;
+}
