@@ -81,7 +81,7 @@ typedef struct {
     int ell_step_max;   /* HEALPix: largest increase of l_iter per level (500) */
     int band_margin;    /* HEALPix: transform band limit L = l_iter + margin (100) */
     double lambda_max;  /* flat: first lambda level (100) */
-    int refine_sweeps;  /* mixed precision: max FP64 correction sweeps (3) */
+    int refine_sweeps;  /* mixed precision: FP64 lambda = 1 sweeps from the mixed result, stopping at tol (0) */
     int profile;        /* nonzero: time every kernel family with CUDA events (fills wf_info.kernel_ms) */
     double mixed_kappa; /* mixed precision: modes with S_l / (tau Omega) >= kappa run in FP64 (3e4) */
     int mixed_lc;       /* mixed precision: > 0 forces the FP64 block l < mixed_lc, < 0 disables it, 0 = auto */
@@ -166,6 +166,16 @@ wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, cons
  * without the pixel area, Omega Y^T being the HEALPix analysis). */
 wf_status wf_alm2map(wf_plan p, const double *alm, int L, double *map);
 wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm);
+
+/* Template marginalisation before the solve (Sect. 3, Eq. 12): the sigma ->
+ * infinity limit of (1 + sigma V V^T)^-1 d_raw by the Woodbury identity,
+ *     d_out = d_raw - V (V^T V)^-1 V^T d_raw,
+ * with V the monopole and the three dipole templates (1, sin th cos ph,
+ * sin th sin ph, cos th) on the observed pixels (mask != 0; NULL = all).
+ * Masked pixels are copied unchanged.  HEALPix plans only.  d_raw, mask,
+ * d_out: device; d_out may equal d_raw.  coef: optional HOST array of 4,
+ * receives the removed template amplitudes.  Synchronises the stream. */
+wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mask, double *d_out, double *coef);
 
 /* Sizes of the plan's arrays. */
 long long wf_npix(wf_plan p);

@@ -20,6 +20,7 @@ Functions and the paper passage each follows:
                                Eqs. (3)-(4), the chi^2 of Eq. (6), the cooling
                                schedule of Sect. 3 and the fluctuation source
                                of Eq. (9).
+* ``marginalize_templates`` -- monopole/dipole projection of Eq. (12).
 
 Parity status: every function here is pinned by tests in
 ``tests/test_oracle_*.py`` except the heuristic schedule's plateau constant
@@ -223,6 +224,7 @@ from .messenger import (  # noqa: E402
     messenger_solve,
     wnorm,
 )
+from .templates import marginalize_templates, template_matrix  # noqa: E402
 
 __all__ = [
     "FlatBasis",
@@ -233,11 +235,13 @@ __all__ = [
     "fluct_source",
     "healpix_rings",
     "legendre",
+    "marginalize_templates",
     "messenger_solve",
     "nalm",
     "npix",
     "num_threads",
     "pixel_angles",
     "synthesis",
+    "template_matrix",
     "wnorm",
 ]

@@ -58,7 +58,7 @@ KERNEL_FAMILIES = ["leg_syn", "ring_syn", "ring_ana", "leg_ana", "other", "flat"
 _lib = None
 EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host",
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
-           "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc"]
+           "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates"]
 
 
 def load(path: str = LIB_PATH):
@@ -87,6 +87,8 @@ def load(path: str = LIB_PATH):
     L.wf_flat_solve_noalloc.argtypes = [ctypes.c_int, dp, dp, u8p, dp, ctypes.c_double, ctypes.POINTER(wf_options),
                                         vp, dp, dp, ctypes.POINTER(wf_info)]
     L.wf_flat_solve_noalloc.restype = ctypes.c_int
+    L.wf_remove_templates.argtypes = [vp, dp, u8p, dp, ctypes.POINTER(ctypes.c_double)]
+    L.wf_remove_templates.restype = ctypes.c_int
     L.wf_strerror.argtypes = [ctypes.c_int]
     L.wf_strerror.restype = ctypes.c_char_p
     L.wf_last_error.argtypes = []
@@ -289,6 +291,16 @@ def wf_flat_solve_noalloc(n, d, noise_var, mask, S, tol, s_wf, alm_out=None, tra
     return _info_dict(st, info, bufs)
 
 
+def wf_remove_templates(plan: Plan, d_raw, mask, d_out):
+    """Monopole/dipole marginalisation of Eq. (12); returns the 4 removed
+    template amplitudes (monopole, dipole x, y, z)."""
+    coef = (ctypes.c_double * 4)()
+    n8 = plan.npix * 8
+    _check(load().wf_remove_templates(plan.handle, _ptr(d_raw, None, n8, "d_raw"), _ptr(mask, None, plan.npix, "mask"),
+                                      _ptr(d_out, None, n8, "d_out"), coef), "wf_remove_templates")
+    return np.array(list(coef))
+
+
 def wf_alm2map(plan: Plan, alm, L, map_out):
     _check(load().wf_alm2map(plan.handle, _ptr(alm, None, plan.nalm * 16, "alm"), int(L),
                              _ptr(map_out, None, plan.npix * 8, "map")), "wf_alm2map")
@@ -299,6 +311,6 @@ def wf_map2alm_adjoint(plan: Plan, map_in, L, alm_out):
                                      _ptr(alm_out, None, plan.nalm * 16, "alm")), "wf_map2alm_adjoint")
 
 
-__all__ = ["Plan", "WfError", "load", "wf_alm2map", "wf_flat_solve_noalloc", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
+__all__ = ["Plan", "WfError", "load", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
            "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "EXPORTS",
            "LIB_PATH"]

@@ -256,6 +256,117 @@ __global__ void k_map_to_T(long long n, const double *__restrict__ in, T *__rest
         out[i] = (T)in[i];
 }
 
+
+// Template marginalisation (Sect. 3, Eq. 12): d = d_raw - V (V^T V)^-1 V^T d_raw,
+// V = masked monopole and dipole templates (1, sin th cos ph, sin th sin ph, cos th).
+// Pass 1: per-CTA partial sums of V^T d (4) and the upper triangle of V^T V (10).
+__device__ __forceinline__ void pixel_templates(double x, int n, int q, int j, bool south, double v[4])
+{
+    double s, c;
+    sincospi((double)(2 * j + q) / (double)n, &s, &c);
+    const double st = sqrt((1.0 - x) * (1.0 + x));
+    v[0] = 1.0;
+    v[1] = st * c;
+    v[2] = st * s;
+    v[3] = south ? -x : x;
+}
+
+__global__ void k_template_sums(int npairs, const RingTab *__restrict__ rings, const double *__restrict__ xp,
+                                const double *__restrict__ d, const uint8_t *__restrict__ mask,
+                                double *__restrict__ part /* [14][gridDim.x] */)
+{
+    __shared__ double red[14][32];
+    double acc[14];
+#pragma unroll
+    for (int k = 0; k < 14; ++k) acc[k] = 0.0;
+    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const RingTab R = rings[pr];
+        const double x = xp[pr];
+        for (int h = 0; h < 2; ++h) {
+            const long long off = h ? R.offS : R.offN;
+            if (off < 0) continue;
+            for (int j = threadIdx.x; j < R.n; j += blockDim.x) {
+                const long long i = off + j;
+                if (mask && !mask[i]) continue;
+                double v[4];
+                pixel_templates(x, R.n, R.q, j, h == 1, v);
+                const double dv = d[i];
+                int t = 4;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[a] += v[a] * dv;
+#pragma unroll
+                    for (int b = a; b < 4; ++b) acc[t++] += v[a] * v[b];
+                }
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 14; ++k) {
+        double s = acc[k];
+        for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[k][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 14) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+__global__ void k_template_apply(int npairs, const RingTab *__restrict__ rings, const double *__restrict__ xp,
+                                 const double *__restrict__ d, const uint8_t *__restrict__ mask, double c0,
+                                 double c1, double c2, double c3, double *__restrict__ out)
+{
+    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
+        const RingTab R = rings[pr];
+        const double x = xp[pr];
+        for (int h = 0; h < 2; ++h) {
+            const long long off = h ? R.offS : R.offN;
+            if (off < 0) continue;
+            for (int j = threadIdx.x; j < R.n; j += blockDim.x) {
+                const long long i = off + j;
+                double r = d[i];
+                if (!mask || mask[i]) {
+                    double v[4];
+                    pixel_templates(x, R.n, R.q, j, h == 1, v);
+                    r -= c0 * v[0] + c1 * v[1] + c2 * v[2] + c3 * v[3];
+                }
+                out[i] = r;
+            }
+        }
+    }
+}
+
+// solve the symmetric 4x4 system G c = b by Gaussian elimination with partial pivoting
+bool solve4(double G[4][4], double b[4], double c[4])
+{
+    double A[4][5];
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) A[i][j] = G[i][j];
+        A[i][4] = b[i];
+    }
+    for (int k = 0; k < 4; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < 4; ++i)
+            if (std::fabs(A[i][k]) > std::fabs(A[piv][k])) piv = i;
+        if (A[piv][k] == 0.0) return false;
+        for (int j = 0; j < 5; ++j) std::swap(A[k][j], A[piv][j]);
+        for (int i = k + 1; i < 4; ++i) {
+            const double f = A[i][k] / A[k][k];
+            for (int j = k; j < 5; ++j) A[i][j] -= f * A[k][j];
+        }
+    }
+    for (int i = 3; i >= 0; --i) {
+        double s = A[i][4];
+        for (int j = i + 1; j < 4; ++j) s -= A[i][j] * c[j];
+        c[i] = s / A[i][i];
+    }
+    return true;
+}
+
 int grid_for(long long n, int nsm) { return (int)std::min<long long>((n + 255) / 256, (long long)nsm * 8); }
 
 wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
@@ -303,7 +414,7 @@ wf_options defaults(wf_options o)
     if (o.ell_step_max <= 0) o.ell_step_max = 500;
     if (o.band_margin <= 0) o.band_margin = 100;
     if (!(o.lambda_max > 0)) o.lambda_max = 100.0;
-    if (o.refine_sweeps <= 0) o.refine_sweeps = 3;
+    if (o.refine_sweeps < 0) o.refine_sweeps = 0;
     if (!(o.mixed_kappa > 0)) o.mixed_kappa = 3e4;
     return o;
 }
@@ -366,7 +477,8 @@ wf_status hp_adjoint_T(wf_plan p, const void *map_T, int L, double2 *out)
 }
 
 wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *mask, const double *C_ell, double tol,
-                   bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out, wf_info *info)
+                   bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out, wf_info *info,
+                   const double2 *a_init = nullptr)
 {
     const wf_options o = defaults(p->opt);
     const int lmax = p->lmax;
@@ -432,7 +544,10 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     sch.ell_iter = std::min(o.ell0, lmax);
     sch.level();
 
-    WF_CUDA(cudaMemsetAsync(p->ws.a, 0, p->nalm * sizeof(double2), p->stream));
+    if (a_init)
+        WF_CUDA(cudaMemcpyAsync(p->ws.a, a_init, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    else
+        WF_CUDA(cudaMemsetAsync(p->ws.a, 0, p->nalm * sizeof(double2), p->stream));
     WF_CUDA(cudaMemsetAsync(p->ws.a_new, 0, p->nalm * sizeof(double2), p->stream));
     const bool replay = !p->replay_lambda.empty();
     const int nrep = (int)p->replay_lambda.size();
@@ -497,7 +612,10 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         }
         if (!std::isfinite(chi2)) { result = WF_EDIVERGE; break; }
         if (replay) {
-            if (full && resid < tol) converged = true;
+            if (full && resid < tol) {
+                converged = true;
+                if (a_init) break;  // correction sweeps stop at the tolerance
+            }
             continue;
         }
         if (sch.final_level()) {
@@ -515,6 +633,55 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         }
         prev_chi2 = chi2;
         have_prev = true;
+    }
+    // Mixed precision, row a9: FP64 correction sweeps.  Up to refine_sweeps
+    // messenger iterations at lambda = 1 on the full band run in FP64 from the
+    // mixed-precision iterate (an FP64 sub-plan of the same geometry); their
+    // residual is the FP64 operator's, and the output map is synthesised in FP64.
+    if (p->prec != WF_PREC_FP64 && o.refine_sweeps > 0 && result != WF_EDIVERGE) {
+        if (!p->sub) {
+            wf_plan sub = nullptr;
+            if ((st = wf_plan_create(&p->g, lmax, WF_PREC_FP64, (void *)p->stream, &sub)) != WF_OK) return st;
+            p->sub = sub;
+        }
+        wf_plan sub = p->sub;
+        sub->opt = p->opt;
+        sub->opt.profile = o.profile;
+        sub->opt.refine_sweeps = 0;
+        sub->replay_lambda.assign(o.refine_sweeps, 1.0);
+        sub->replay_L.assign(o.refine_sweeps, lmax);
+        wf_info si{};
+        std::vector<double> tl(o.refine_sweeps), tc(o.refine_sweeps), tr(o.refine_sweeps), tm(o.refine_sweeps);
+        std::vector<int> tL(o.refine_sweeps);
+        si.lambda_trace = tl.data();
+        si.L_trace = tL.data();
+        si.chi2_trace = tc.data();
+        si.resid_trace = tr.data();
+        si.iter_ms_trace = tm.data();
+        si.trace_cap = o.refine_sweeps;
+        st = hp_solve(sub, d, nv, mask, C_ell, tol, fluct, g1, g2, s_out, alm_out, &si, p->ws.a);
+        if (st != WF_OK) return st;
+        for (int i = 0; i < si.iters; ++i) record(info, k + i, tl[i], tL[i], tc[i], tr[i], tm[i]);
+        for (int f = 0; f < WF_NK; ++f) {
+            pr.ms[f] += si.kernel_ms[f];
+            pr.cnt[f] += si.kernel_launches[f];
+        }
+        pr.launches += si.launches;
+        pr.finish();
+        if (info) {
+            info->iters = k + si.iters;
+            info->converged = (converged || si.converged) ? 1 : 0;
+            info->final_residual = si.final_residual;
+            info->chi2_over_ndof = si.chi2_over_ndof;
+            info->n_dof = ndof;
+            info->tau = tau;
+            info->n_levels = levels;
+            info->refine_sweeps = si.iters;
+            info->mixed_lc = lc;
+        }
+        if (si.converged) return WF_OK;
+        set_error(WF_ENOCONV, "not converged after %d FP64 sweeps (residual %.3e)", si.iters, si.final_residual);
+        return replay ? WF_OK : WF_ENOCONV;
     }
     if ((st = hp_alm2map(p, p->ws.a, lmax, s_out)) != WF_OK) return st;
     pr.count(WF_K_LEG_SYN);
@@ -679,6 +846,7 @@ void wf_plan_destroy(wf_plan p)
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
     if (p->flat) flat_destroy(p);
+    if (p->sub) wf_plan_destroy(p->sub);
     if (p->events_ready)
         for (auto &e : p->ev) cudaEventDestroy(e);
     for (void *a : p->allocations) cudaFree(a);
@@ -756,6 +924,40 @@ wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, con
     if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nh * 8, cudaMemcpyDeviceToHost, s));
     WF_CUDA(cudaStreamSynchronize(s));
     return st;
+}
+
+wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mask, double *d_out, double *coef)
+{
+    if (!p || !d_raw || !d_out) return set_error(WF_EINVAL, "null argument");
+    if (p->g.kind != WF_GEOM_HEALPIX) return set_error(WF_EUNSUPPORTED, "template marginalisation needs a HEALPix plan");
+    const int grid = std::min(p->npairs, 4 * p->nsm);
+    const size_t need = (size_t)14 * grid * sizeof(double);
+    if (!p->ws.redu) {
+        wf_status st = plan_alloc(p, (void **)&p->ws.redu, (size_t)14 * 4 * p->nsm * sizeof(double));
+        if (st != WF_OK) return st;
+    }
+    k_template_sums<<<grid, 256, 0, p->stream>>>(p->npairs, p->tab.rings, p->tab.x64, d_raw, mask, p->ws.redu);
+    WF_CUDA(cudaGetLastError());
+    std::vector<double> part((size_t)14 * grid);
+    WF_CUDA(cudaMemcpyAsync(part.data(), p->ws.redu, need, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    double s[14] = {};
+    for (int k = 0; k < 14; ++k)
+        for (int b = 0; b < grid; ++b) s[k] += part[(size_t)k * grid + b];
+    double G[4][4], b[4], c[4];
+    int t = 4;
+    for (int i = 0; i < 4; ++i) {
+        b[i] = s[i];
+        for (int j = i; j < 4; ++j) G[i][j] = G[j][i] = s[t++];
+    }
+    if (!solve4(G, b, c)) return set_error(WF_EINVAL, "templates are degenerate on the observed pixels");
+    k_template_apply<<<grid, 256, 0, p->stream>>>(p->npairs, p->tab.rings, p->tab.x64, d_raw, mask, c[0], c[1], c[2],
+                                                  c[3], d_out);
+    WF_CUDA(cudaGetLastError());
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    if (coef)
+        for (int i = 0; i < 4; ++i) coef[i] = c[i];
+    return WF_OK;
 }
 
 wf_status wf_alm2map(wf_plan p, const double *alm, int L, double *map)

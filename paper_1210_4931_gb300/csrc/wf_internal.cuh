@@ -132,6 +132,7 @@ struct wf_plan_s {
     long long device_bytes = 0;
     std::vector<void *> allocations;
     cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
+    wf_plan sub = nullptr;    // mixed precision: FP64 plan of the same geometry for the correction sweeps
     bool events_ready = false;
 };
 

@@ -214,3 +214,19 @@ def test_flat_plans_of_different_sizes_coexist(wf):
     assert rep["converged"]
     small.close()
     big.close()
+
+
+@pytest.mark.parametrize("nside", [8, 64])
+def test_template_marginalisation_matches_oracle(wf, nside):
+    import torch
+
+    P, basis, d, nu, tau = healpix_case(nside, 2 * nside, gen.seed_for(2, 400 + nside))
+    th, ph = oracle.pixel_angles(nside)
+    d_raw = d + 5.0 + 0.7 * np.sin(th) * np.cos(ph) - 1.3 * np.cos(th)  # residual monopole + dipole
+    ref, cref = oracle.marginalize_templates(nside, d_raw, P["mask"])
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=2 * nside, precision="fp64")
+    out = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    c = wf.wf_remove_templates(plan, T(d_raw), T(P["mask"]), out)
+    assert rel(out.cpu().numpy(), ref) < 1e-10
+    np.testing.assert_allclose(c, cref, rtol=1e-9, atol=1e-9)
+    plan.close()
