@@ -108,6 +108,41 @@ class FlatSchedule:
                 return
 
 
+class RigorousSchedule:
+    """Cooling that keeps the chi^2 bound (Sect. 2.2): with b = n_dof -
+    m sigma_chi2, lambda starts where chi^2(lambda, 0) = d^T (N + (lambda-1)
+    T)^-1 d = b; after every iteration lambda is lowered until chi^2(lambda,
+    x) = b again; when lambda stops falling (x has converged to s(lambda) at
+    lambda > 1) b is raised to b' = chi2_min(lambda) + (lambda - 1) tau x^T
+    S^-2 x, the first-order estimate of chi2_min(1) from below; lambda = 1
+    is taken once lambda - 1 < lam_floor.  Written with u = (lambda - 1) tau:
+    chi^2(u, x) = x^T S^-1 x + sum (d - x)^2 / (N + u) over observed pixels.
+    Readings (the paper gives none): m = 5, "stops falling" = relative change
+    of lambda - 1 below stall_tol over one iteration."""
+
+    def __init__(self, n_dof, m_sigma=5.0, stall_tol=1e-7, lam_floor=1e-9):
+        self.b = n_dof - m_sigma * np.sqrt(2.0 * n_dof)
+        self.stall_tol = stall_tol
+        self.lam_floor = lam_floor
+        self.u = None
+        self.b_updates = 0
+
+    @staticmethod
+    def _root(f, hi):
+        """Largest-accuracy root of the decreasing function f on [0, hi]
+        (returns 0 when f(0) <= 0)."""
+        from scipy.optimize import brentq
+
+        if f(0.0) <= 0.0:
+            return 0.0
+        if f(hi) >= 0.0:
+            return hi
+        return brentq(f, 0.0, hi, xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=500)
+
+    def lam(self, tau):
+        return 1.0 + self.u / tau
+
+
 def fluct_source(basis, nu, S, g1, g2):
     """Pixel source of Eq. (9): r = nu^1/2 g1 + Omega Y (S^-1/2 g2); modes
     with S = 0 get no draw (pseudo-inverse)."""
@@ -149,6 +184,9 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
     n_dof = int(np.count_nonzero(nu > 0))
     sigma = float(np.sqrt(2.0 * n_dof))
 
+    rigorous = isinstance(schedule, RigorousSchedule)
+    if rigorous and d is None:
+        raise ValueError("the chi^2-bound schedule needs the data d")
     if replay is None and schedule is None:
         if basis.kind == "flat":
             schedule = FlatSchedule(S, basis.kabs(), tau)
@@ -156,7 +194,7 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
             raise ValueError("a HealpixSchedule (built from C_ell) is required")
 
     a = np.zeros(b.shape, dtype=np.complex128) if a0 is None else np.array(a0, dtype=np.complex128)
-    trace, chi2s, resids = [], [], []
+    trace, chi2s, resids, bounds = [], [], [], []
     converged = False
     prev_chi2 = None
     level_iters = 0
@@ -167,6 +205,37 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
                 break
             lam, L = replay[k]
             L = None if L is None or basis.kind == "flat" else int(L)
+        elif rigorous:
+            if k >= maxiter:
+                break
+            L = full_L
+            s = basis.synth(a, full_L)
+            obs = nu > 0
+            e2 = np.where(obs, (d - s) ** 2, 0.0)
+            N = np.where(obs, 1.0 / np.where(obs, nu, 1.0), 1.0)
+            h = float(np.sum(basis.w * np.abs(a) ** 2 * inv_S))
+
+            def g(u):
+                return h + float(np.sum(np.where(obs, e2 / (N + u), 0.0))) - schedule.b
+
+            if schedule.u is None:  # initial lambda: chi^2(lambda, 0) = b
+                hi = 1.0
+                while g(hi) > 0.0 and hi < 1e300:
+                    hi *= 4.0
+                schedule.u = schedule._root(g, hi)
+            else:
+                u_prev = schedule.u
+                u_new = schedule._root(g, u_prev) if u_prev > 0.0 else 0.0
+                if u_new > 0.0 and (u_prev - u_new) <= schedule.stall_tol * u_new:
+                    # converged at lambda > 1: raise b towards chi2_min(1)
+                    q = float(np.sum(basis.w * np.abs(a) ** 2 * inv_S ** 2))
+                    schedule.b = (h + float(np.sum(np.where(obs, e2 / (N + u_new), 0.0)))) + u_new * omega * q
+                    schedule.b_updates += 1
+                    u_new = schedule._root(g, u_prev)
+                schedule.u = u_new
+            if schedule.u / tau < schedule.lam_floor:
+                schedule.u = 0.0
+            lam = schedule.lam(tau)
         else:
             if k >= maxiter:
                 break
@@ -175,7 +244,8 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
         Lb = full_L if L is None else L
 
         # Eq. (3): pixel blend
-        s = basis.synth(a, Lb)
+        if not rigorous or replay is not None:
+            s = basis.synth(a, Lb)
         den = 1.0 + (lam - 1.0) * tau * nu
         t = s + lam * tau * (r - nu * s) / den
         # Eq. (4): harmonic blend
@@ -188,6 +258,8 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
         if lam == 1.0 and full:
             resid = wnorm(basis.w, (inv_S + 1.0 / tau_h) * (a - a_new), active) / bnorm
         trace.append((float(lam), None if basis.kind == "flat" else int(Lb)))
+        if rigorous and replay is None:
+            bounds.append(schedule.b)
         chi2s.append(chi2)
         resids.append(resid)
         a = a_new
@@ -195,6 +267,11 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
         if callback is not None:
             callback(k, a)
 
+        if replay is None and rigorous:
+            if lam == 1.0 and resid < tol:
+                converged = True
+                break
+            continue
         if replay is None:
             if schedule.final:
                 if resid < tol:
@@ -222,6 +299,7 @@ def messenger_solve(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000,
         "converged": converged,
         "n_dof": n_dof,
         "bnorm": bnorm,
+        "bound": np.array(bounds),
     }
     if d is not None:
         s = out["s"]

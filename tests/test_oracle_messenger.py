@@ -358,3 +358,60 @@ def test_healpix_schedule_follows_paper(oracle):
         assert lam == pytest.approx(max(1.0, c[e] / tau_h))
         assert L == min(4096, e + 100)
     assert seen[-1][1] == 1.0 and seen[-1][2] == 4096
+
+
+# ---------------------------------------------------------------------------
+# chi^2-bound cooling (Sect. 2.2)
+# ---------------------------------------------------------------------------
+
+
+def test_rigorous_schedule_keeps_the_chi2_bound(oracle):
+    """Each lambda > 1 is chosen so that chi^2(lambda, x) = b for the current
+    iterate (dense chi^2 of Eq. 6, including its x-independent part); b stays
+    below chi2_min(1) = d^T (S + N)^-1 d and approaches it; the result is the
+    Wiener filter of Eq. (2)."""
+    from oracle.messenger import RigorousSchedule
+
+    P = _problem()
+    B, d, nu, tau = _setup(oracle, P)
+    D = DenseFlat(P)
+    obs = (nu > 0).ravel()
+    dv = d.ravel()
+    chi2_min1 = dv[obs] @ np.linalg.solve(D.S[np.ix_(obs, obs)] + np.diag(P["noise_var"].ravel()[obs]), dv[obs])
+    sch = RigorousSchedule(int(obs.sum()))
+    b0 = sch.b
+    xs = [np.zeros(d.size)]
+    res = oracle.messenger_solve(B, nu * d, nu, P["S"], tau, schedule=sch, tol=1e-11, d=d,
+                                 callback=lambda k, a: xs.append(B.synth(a).ravel()))
+    assert res["converged"]
+    lams = np.array([t[0] for t in res["trace"]])
+    assert lams[0] > 1.0 and np.all(np.diff(lams) <= 0) and lams[-1] == 1.0
+    W = lambda lam: (nu / (1.0 + (lam - 1.0) * tau * nu)).ravel()
+    checked = 0
+    for k, (lam, bk) in enumerate(zip(lams, res["bound"])):
+        if lam <= 1.0:
+            break
+        x = xs[k]
+        chi2 = x @ D.Sinv @ x + np.sum(W(lam) * (dv - x) ** 2)
+        assert chi2 == pytest.approx(bk, rel=1e-9)
+        checked += 1
+    assert checked > 5
+    assert res["bound"].max() <= chi2_min1 * (1 + 1e-10)  # b approaches chi2_min(1) from below up to rounding
+    assert b0 < res["bound"].max() and (chi2_min1 - res["bound"].max()) < 0.1 * (chi2_min1 - b0)
+    s_ref = np.linalg.solve(D.Sinv + np.diag(nu.ravel()), (nu * d).ravel())
+    assert np.max(np.abs(res["s"].ravel() - s_ref)) / np.max(np.abs(s_ref)) < 1e-8
+
+
+def test_rigorous_initial_lambda(oracle):
+    """The first lambda solves d^T (N + (lambda - 1) T)^-1 d = b (Sect. 2.2)."""
+    from oracle.messenger import RigorousSchedule
+
+    P = _problem(seed=9)
+    B, d, nu, tau = _setup(oracle, P)
+    obs = nu > 0
+    sch = RigorousSchedule(int(obs.sum()))
+    b = sch.b
+    res = oracle.messenger_solve(B, nu * d, nu, P["S"], tau, schedule=sch, tol=1e-6, d=d, maxiter=1)
+    lam = res["trace"][0][0]
+    N = P["noise_var"][obs]
+    assert np.sum(d[obs] ** 2 / (N + (lam - 1.0) * tau)) == pytest.approx(b, rel=1e-10)
