@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--maxiter", type=int, default=1000, help="iteration cap of one solve (one step)")
     ap.add_argument("--refine-sweeps", type=int, default=2,
                     help="FP64 lambda = 1 correction sweeps after the mixed iteration (0: none)")
+    ap.add_argument("--schedule", default="heuristic", choices=["heuristic", "bound"],
+                    help="cooling: the heuristic of Sect. 3 (default) or the chi^2 bound of Sect. 2.2")
     ap.add_argument("--nside", type=int, default=CFG["nside"])
     ap.add_argument("--lmax", type=int, default=CFG["lmax"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
@@ -247,7 +249,8 @@ def run_ours(args):
     nv, mask, cl = T(P["noise_var"]), T(P["mask"]), T(P["c_ell"])
     s_out = torch.empty(plan.npix, dtype=torch.float64, device=dev)
     alm_out = torch.empty(plan.nalm, dtype=torch.complex128, device=dev)
-    wf.wf_set_options(plan, profile=1, maxiter=args.maxiter,
+    sched = 1 if args.schedule == "bound" else 0
+    wf.wf_set_options(plan, profile=1, maxiter=args.maxiter, schedule=sched,
                       refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0)
     if args.full_band_iters > 0:
         wf.wf_set_schedule(plan, [1.0] * args.full_band_iters, [lmax] * args.full_band_iters)
@@ -315,7 +318,8 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
-                      "tol": args.tol, "l2": "inputs (1.2 GB) larger than L2", "parallelism": "replicas"},
+                      "tol": args.tol, "schedule": args.schedule, "l2": "inputs (1.2 GB) larger than L2",
+                      "parallelism": "replicas"},
            "time_to_tol_s": t_ms / args.steps / 1e3 if last["converged"] else None,
            "time_to_residual_s": time_to_residual(last), "iters_per_solve": last["iters"],
            "maxiter": args.maxiter, "mixed_lc": last.get("mixed_lc"), "fp64_sweeps": last.get("refine_sweeps"),
@@ -334,7 +338,7 @@ def run_ours(args):
         dh = d.cpu().numpy()
         nvh, mh, clh = P["noise_var"], P["mask"], P["c_ell"]
         sh = np.empty(plan.npix)
-        wf.wf_set_options(plan, profile=0, maxiter=args.maxiter,
+        wf.wf_set_options(plan, profile=0, maxiter=args.maxiter, schedule=sched,
                           refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0)
         wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)  # warm
         t0 = time.perf_counter()

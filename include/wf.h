@@ -85,6 +85,12 @@ typedef struct {
     int profile;        /* nonzero: time every kernel family with CUDA events (fills wf_info.kernel_ms) */
     double mixed_kappa; /* mixed precision: modes with S_l / (tau Omega) >= kappa run in FP64 (3e4) */
     int mixed_lc;       /* mixed precision: > 0 forces the FP64 block l < mixed_lc, < 0 disables it, 0 = auto */
+    int schedule;       /* 0: heuristic cooling of Sect. 3 (default); 1: chi^2-bound cooling of Sect. 2.2
+                           (HEALPix Wiener filter only: lambda such that chi^2(lambda, x) = b every iteration,
+                           b = n_dof - m_sigma sqrt(2 n_dof), raised when lambda stalls; full band) */
+    double m_sigma;     /* chi^2-bound cooling: initial b = n_dof - m_sigma sigma_chi2 (5) */
+    double stall_tol;   /* chi^2-bound cooling: lambda - 1 changing by less than this fraction in one
+                           iteration counts as converged at lambda > 1 and raises b (1e-7) */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one
@@ -108,12 +114,14 @@ typedef struct {
     double chi2_over_ndof;  /* chi^2(s, 1) / n_dof of the result (Wiener filter only) */
     long long n_dof;        /* observed pixels */
     double tau;             /* min noise variance over observed pixels */
-    int n_levels;           /* lambda levels visited */
+    int n_levels;           /* lambda levels visited (chi^2-bound schedule: values the bound b took) */
     int refine_sweeps;      /* FP64 correction sweeps run (mixed precision) */
     int mixed_lc;           /* FP64 block l < mixed_lc used by the mixed-precision transforms */
     double *lambda_trace;   /* optional, lambda_k */
     int *L_trace;           /* optional, band limit L_k (HEALPix; -1 on the flat grid) */
-    double *chi2_trace;     /* optional, chi^2 of the iterate entering iteration k (Eq. 6, x-independent part dropped) */
+    double *chi2_trace;     /* optional, chi^2 of the iterate entering iteration k (Eq. 6, x-independent part
+                               dropped); under the chi^2-bound schedule the full chi^2(lambda_k, x_k), which
+                               equals the bound b while lambda_k > 1 */
     double *resid_trace;    /* optional, relative residual (NaN where lambda > 1 or L < lmax) */
     double *iter_ms_trace;  /* optional, device time of iteration k in ms (CUDA events; HEALPix) */
     int trace_cap;

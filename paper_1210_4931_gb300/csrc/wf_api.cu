@@ -227,9 +227,9 @@ __global__ void k_pix_chi2(long long npix, const double *__restrict__ d, const d
 
 // deterministic fixed-order sums: out[k] = sum_i in[off_k + i * stride_k], i < n_k
 struct SumSpec {
-    const double *in[3];
-    int n[3];
-    int stride[3];
+    const double *in[5];
+    int n[5];
+    int stride[5];
 };
 __global__ void k_sums(SumSpec sp, int nsum, double *__restrict__ out)
 {
@@ -367,6 +367,56 @@ bool solve4(double G[4][4], double b[4], double c[4])
     return true;
 }
 
+
+// chi^2-bound cooling (Sect. 2.2): pixel sums at u = (lambda - 1) tau for the
+// current synthesis s,  A(u) = sum (d - s)^2 / (N + u) = sum (r - nu s)^2 / (nu (1 + u nu)),
+// D(u) = -dA/du = sum (r - nu s)^2 / (1 + u nu)^2, over observed pixels; per-block partials.
+template <typename T>
+__global__ void k_pixsums(long long npix, const T *__restrict__ r, const T *__restrict__ nu, const T *__restrict__ s,
+                          double u, double *__restrict__ part /* [2][gridDim.x] */)
+{
+    __shared__ double red[2][32];
+    double A = 0.0, D = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+        const double nv = (double)nu[i];
+        if (nv > 0.0) {
+            const double e = (double)r[i] - nv * (double)s[i];
+            const double den = 1.0 + u * nv;
+            A += e * e / (nv * den);
+            D += e * e / (den * den);
+        }
+    }
+    for (int o = 16; o >= 1; o >>= 1) {
+        A += __shfl_xor_sync(0xffffffffu, A, o);
+        D += __shfl_xor_sync(0xffffffffu, D, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = A;
+        red[1][threadIdx.x >> 5] = D;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        part[blockIdx.x] = a;
+        part[gridDim.x + blockIdx.x] = b;
+    }
+}
+
+// Eq. (3) blend in place on the synthesised map: t = s + lam tau (r - nu s) / (1 + (lam - 1) tau nu)
+template <typename T>
+__global__ void k_blend(long long npix, const T *__restrict__ r, const T *__restrict__ nu, T *__restrict__ st, T lt,
+                        T lm1t)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += (long long)gridDim.x * blockDim.x) {
+        const T s = st[i], nv = nu[i];
+        st[i] = s + lt * (r[i] - nv * s) / ((T)1 + lm1t * nv);
+    }
+}
+
 int grid_for(long long n, int nsm) { return (int)std::min<long long>((n + 255) / 256, (long long)nsm * 8); }
 
 wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
@@ -376,6 +426,79 @@ wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
     WF_CUDA(cudaGetLastError());
     WF_CUDA(cudaMemcpyAsync(p->ws.h_scal, p->ws.scal, nsum * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     WF_CUDA(cudaStreamSynchronize(p->stream));
+    return WF_OK;
+}
+
+
+// A(u), D(u) of the chi^2-bound schedule for the synthesis currently in ws.t
+wf_status pix_sums(wf_plan p, double u, double *A, double *D, Prof *pr)
+{
+    const int grid = std::min((int)((p->npix + 255) / 256), 2 * p->nsm);
+    if (p->prec == WF_PREC_FP64)
+        k_pixsums<double><<<grid, 256, 0, p->stream>>>(p->npix, (const double *)p->ws.r, (const double *)p->ws.nu,
+                                                       (const double *)p->ws.t, u, p->ws.part_pix);
+    else
+        k_pixsums<float><<<grid, 256, 0, p->stream>>>(p->npix, (const float *)p->ws.r, (const float *)p->ws.nu,
+                                                      (const float *)p->ws.t, u, p->ws.part_pix);
+    WF_CUDA(cudaGetLastError());
+    if (pr) pr->count(WF_K_OTHER);
+    SumSpec sp{};
+    sp.in[0] = p->ws.part_pix;
+    sp.n[0] = grid;
+    sp.stride[0] = 1;
+    sp.in[1] = p->ws.part_pix + grid;
+    sp.n[1] = grid;
+    sp.stride[1] = 1;
+    wf_status st = sums(p, sp, 2, pr);
+    if (st != WF_OK) return st;
+    *A = p->ws.h_scal[0];
+    *D = p->ws.h_scal[1];
+    return WF_OK;
+}
+
+// Root of g(u) = h + A(u) - b on [0, hi] (g decreasing and convex in u):
+// safeguarded Newton inside a shrinking bracket.  Returns 0 when g(0) <= 0;
+// when g(hi) > 0 it widens hi by factors of 4 if `expand` (the first lambda),
+// else returns hi (lambda never rises).
+wf_status bound_root(wf_plan p, double h, double b, double hi, bool expand, double *u_out, double *chi2_out, Prof *pr)
+{
+    double A, D;
+    wf_status st = pix_sums(p, 0.0, &A, &D, pr);
+    if (st != WF_OK) return st;
+    if (h + A - b <= 0.0) {
+        *u_out = 0.0;
+        *chi2_out = h + A;
+        return WF_OK;
+    }
+    double lo = 0.0, u = hi;
+    if ((st = pix_sums(p, u, &A, &D, pr)) != WF_OK) return st;
+    double g = h + A - b;
+    while (expand && g > 0.0 && u < 1e300) {  // bracket from above (the first lambda only)
+        lo = u;
+        u *= 4.0;
+        if ((st = pix_sums(p, u, &A, &D, pr)) != WF_OK) return st;
+        g = h + A - b;
+    }
+    if (g >= 0.0) {
+        *u_out = u;
+        *chi2_out = h + A;
+        return WF_OK;
+    }
+    hi = u;
+    for (int it = 0; it < 100; ++it) {
+        double un = u + g / D;  // Newton: g' = -D
+        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+        if ((st = pix_sums(p, un, &A, &D, pr)) != WF_OK) return st;
+        const double gn = h + A - b;
+        if (gn > 0.0) lo = un;
+        else hi = un;
+        const bool done = std::fabs(un - u) <= 1e-13 * std::max(un, 1e-300) || std::fabs(gn) <= 1e-13 * b;
+        u = un;
+        g = gn;
+        if (done) break;
+    }
+    *u_out = u;
+    *chi2_out = h + A;
     return WF_OK;
 }
 
@@ -416,6 +539,8 @@ wf_options defaults(wf_options o)
     if (!(o.lambda_max > 0)) o.lambda_max = 100.0;
     if (o.refine_sweeps < 0) o.refine_sweeps = 0;
     if (!(o.mixed_kappa > 0)) o.mixed_kappa = 3e4;
+    if (!(o.m_sigma > 0)) o.m_sigma = 5.0;
+    if (!(o.stall_tol > 0)) o.stall_tol = 1e-7;
     return o;
 }
 
@@ -482,6 +607,10 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
 {
     const wf_options o = defaults(p->opt);
     const int lmax = p->lmax;
+    if (o.schedule == 1 && fluct && p->replay_lambda.empty())
+        return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
+    if (o.schedule == 1 && a_init && p->replay_lambda.empty())
+        return set_error(WF_EUNSUPPORTED, "chi^2-bound schedule with a starting iterate");
     Prof pr(p, info, o.profile != 0);
     double tau = 0;
     long long ndof = 0;
@@ -551,8 +680,14 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     WF_CUDA(cudaMemsetAsync(p->ws.a_new, 0, p->nalm * sizeof(double2), p->stream));
     const bool replay = !p->replay_lambda.empty();
     const int nrep = (int)p->replay_lambda.size();
+    const bool rigorous = o.schedule == 1 && !replay;  // a replay overrides the schedule
+    double bound = (double)ndof - o.m_sigma * std::sqrt(2.0 * (double)ndof);
+    if (rigorous && !(bound > 0.0))
+        return set_error(WF_EINVAL, "chi^2 bound n_dof - m sigma = %.3g is not positive (too few observed pixels)", bound);
+    double u_cur = 0.0, h_cur = 0.0, q_cur = 0.0;
+    int bound_updates = 0;
     int k = 0, level_iters = 0, levels = 1;
-    bool have_prev = false, converged = false;
+    bool have_prev = false, converged = false, chi2_bad = false;
     double prev_chi2 = 0, last_resid = NAN, best_resid = INFINITY;
     const double sigma = std::sqrt(2.0 * (double)ndof);
     wf_status result = WF_OK;
@@ -568,14 +703,57 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
             lam = sch.lam;
             L = sch.L;
         }
-        const bool full = (lam == 1.0 && L == lmax);
         pr.iter_begin();
-        pr.begin(WF_K_LEG_SYN);
-        if ((st = hp_legendre_synthesis(p, p->ws.a, L)) != WF_OK) return st;
-        pr.end();
-        pr.begin(WF_K_RING_SYN);
-        if ((st = hp_ring_synthesis(p, L, RS_BLEND, lam, tau, nullptr)) != WF_OK) return st;
-        pr.end();
+        double chi2_bound = NAN;
+        if (rigorous) {
+            // x_k = Y a_k, then lambda_k from chi^2(lambda_k, x_k) = b (Sect. 2.2)
+            L = lmax;
+            pr.begin(WF_K_LEG_SYN);
+            if ((st = hp_legendre_synthesis(p, p->ws.a, L)) != WF_OK) return st;
+            pr.end();
+            pr.begin(WF_K_RING_SYN);
+            if ((st = hp_ring_synthesis(p, L, RS_SYN, 1.0, tau, nullptr)) != WF_OK) return st;
+            pr.end();
+            double u_new = 0.0;
+            if (k == 0) {
+                if ((st = bound_root(p, h_cur, bound, 1.0, true, &u_new, &chi2_bound, &pr)) != WF_OK) return st;
+            } else if (u_cur > 0.0) {
+                if ((st = bound_root(p, h_cur, bound, u_cur, false, &u_new, &chi2_bound, &pr)) != WF_OK) return st;
+                if (u_new > 0.0 && (u_cur - u_new) <= o.stall_tol * u_new) {
+                    // converged at lambda > 1: raise b to chi2_min(lambda) + (lambda - 1) tau_h x^T S^-2 x
+                    bound = chi2_bound + u_new * p->omega * q_cur;
+                    ++bound_updates;
+                    if ((st = bound_root(p, h_cur, bound, u_cur, false, &u_new, &chi2_bound, &pr)) != WF_OK) return st;
+                }
+            }
+            if (u_new / tau < 1e-9) u_new = 0.0;
+            if (u_new == 0.0) {
+                // lambda = 1 (reached or floored): report chi^2(1, x_k)
+                double A, D;
+                if ((st = pix_sums(p, 0.0, &A, &D, &pr)) != WF_OK) return st;
+                chi2_bound = h_cur + A;
+            }
+            u_cur = u_new;
+            lam = 1.0 + u_cur / tau;
+            pr.count(WF_K_OTHER);
+            if (p->prec == WF_PREC_FP64)
+                k_blend<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
+                    p->npix, (const double *)p->ws.r, (const double *)p->ws.nu, (double *)p->ws.t, lam * tau,
+                    (lam - 1.0) * tau);
+            else
+                k_blend<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
+                    p->npix, (const float *)p->ws.r, (const float *)p->ws.nu, (float *)p->ws.t, (float)(lam * tau),
+                    (float)((lam - 1.0) * tau));
+            WF_CUDA(cudaGetLastError());
+        } else {
+            pr.begin(WF_K_LEG_SYN);
+            if ((st = hp_legendre_synthesis(p, p->ws.a, L)) != WF_OK) return st;
+            pr.end();
+            pr.begin(WF_K_RING_SYN);
+            if ((st = hp_ring_synthesis(p, L, RS_BLEND, lam, tau, nullptr)) != WF_OK) return st;
+            pr.end();
+        }
+        const bool full = (lam == 1.0 && L == lmax);
         pr.begin(WF_K_RING_ANA);
         if ((st = hp_ring_analysis(p, L, p->ws.t)) != WF_OK) return st;
         pr.end();
@@ -591,17 +769,18 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         sp.in[0] = p->ws.part_pix;
         sp.n[0] = p->tab.ringGrid;
         sp.stride[0] = 1;
-        sp.in[1] = p->ws.part_harm;
-        sp.n[1] = L + 1;
-        sp.stride[1] = 2;
-        sp.in[2] = p->ws.part_harm + 1;
-        sp.n[2] = L + 1;
-        sp.stride[2] = 2;
-        if ((st = sums(p, sp, 3, &pr)) != WF_OK) return st;
+        for (int q = 0; q < 4; ++q) {
+            sp.in[1 + q] = p->ws.part_harm + q;
+            sp.n[1 + q] = L + 1;
+            sp.stride[1 + q] = 4;
+        }
+        if ((st = sums(p, sp, 5, &pr)) != WF_OK) return st;
         const double ims = pr.iter_end();
         pr.collect();
-        const double chi2 = p->ws.h_scal[0] + p->ws.h_scal[1];
+        const double chi2 = (rigorous) ? chi2_bound : p->ws.h_scal[0] + p->ws.h_scal[1];
         const double resid = full ? std::sqrt(p->ws.h_scal[2]) / bnorm : NAN;
+        h_cur = p->ws.h_scal[3];  // x_{k+1}^T S^-1 x_{k+1} and x^T S^-2 x for the next lambda
+        q_cur = p->ws.h_scal[4];
         record(info, k, lam, L, chi2, resid, ims);
         std::swap(p->ws.a, p->ws.a_new);
         ++k;
@@ -610,7 +789,11 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
             if (!std::isfinite(resid) || (k > 50 && resid > 1e3 * best_resid)) { result = WF_EDIVERGE; break; }
             best_resid = std::min(best_resid, resid);
         }
-        if (!std::isfinite(chi2)) { result = WF_EDIVERGE; break; }
+        if (!std::isfinite(chi2)) { result = WF_EDIVERGE; chi2_bad = true; break; }
+        if (rigorous) {
+            if (full && resid < tol) { converged = true; break; }
+            continue;
+        }
         if (replay) {
             if (full && resid < tol) {
                 converged = true;
@@ -648,6 +831,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         sub->opt = p->opt;
         sub->opt.profile = o.profile;
         sub->opt.refine_sweeps = 0;
+        sub->opt.schedule = 0;
         sub->replay_lambda.assign(o.refine_sweeps, 1.0);
         sub->replay_L.assign(o.refine_sweeps, lmax);
         wf_info si{};
@@ -675,7 +859,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
             info->chi2_over_ndof = si.chi2_over_ndof;
             info->n_dof = ndof;
             info->tau = tau;
-            info->n_levels = levels;
+            info->n_levels = rigorous ? 1 + bound_updates : levels;
             info->refine_sweeps = si.iters;
             info->mixed_lc = lc;
         }
@@ -714,14 +898,16 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         info->chi2_over_ndof = chi2n;
         info->n_dof = ndof;
         info->tau = tau;
-        info->n_levels = levels;
+        info->n_levels = rigorous ? 1 + bound_updates : levels;
         info->refine_sweeps = 0;
         info->mixed_lc = lc;
     }
     pr.finish();
     if (result == WF_OK && !replay && !converged) result = WF_ENOCONV;
     if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", last_resid);
-    if (result == WF_EDIVERGE) set_error(result, "residual grew (%.3e); lmax too large for this nside?", last_resid);
+    if (result == WF_EDIVERGE && chi2_bad) set_error(result, "chi^2 is not finite at iteration %d", k);
+    else if (result == WF_EDIVERGE)
+        set_error(result, "residual grew (%.3e); lmax too large for this nside?", last_resid);
     return result;
 }
 
@@ -762,9 +948,9 @@ wf_status hp_create(wf_plan p)
     if ((st = plan_alloc(p, &p->ws.r, p->npix * es)) != WF_OK) return st;
     if ((st = plan_alloc(p, &p->ws.nu, p->npix * es)) != WF_OK) return st;
     if ((st = plan_alloc(p, &p->ws.t, p->npix * es)) != WF_OK) return st;
-    const int npart = std::max(p->tab.ringGrid, 256);
+    const int npart = std::max(p->tab.ringGrid, std::max(256, 4 * p->nsm));  // also the 2 x (<= 2 nsm) chi^2-bound sums
     if ((st = plan_alloc(p, (void **)&p->ws.part_pix, npart * sizeof(double))) != WF_OK) return st;
-    if ((st = plan_alloc(p, (void **)&p->ws.part_harm, 2 * (p->lmax + 2) * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.part_harm, 4 * (p->lmax + 2) * sizeof(double))) != WF_OK) return st;
     return WF_OK;
 }
 
@@ -857,6 +1043,8 @@ void wf_plan_destroy(wf_plan p)
 wf_status wf_set_options(wf_plan p, const wf_options *opt)
 {
     if (!p) return set_error(WF_EINVAL, "null plan");
+    if (opt && (opt->schedule < 0 || opt->schedule > 1))
+        return set_error(WF_EINVAL, "schedule must be 0 (heuristic) or 1 (chi^2 bound)");
     p->opt = opt ? *opt : wf_options{};
     return WF_OK;
 }
@@ -881,8 +1069,11 @@ wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const ui
 {
     if (!p || !d || !noise_var || !C_ell || !s_wf) return set_error(WF_EINVAL, "null argument");
     if (!(tol > 0)) return set_error(WF_EINVAL, "tol must be > 0");
-    if (p->g.kind == WF_GEOM_FLAT)
+    if (p->g.kind == WF_GEOM_FLAT) {
+        if (p->opt.schedule == 1 && p->replay_lambda.empty())
+            return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule is implemented on the HEALPix sphere only");
         return flat_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
+    }
     return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
 }
 
@@ -891,8 +1082,11 @@ wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, cons
 {
     if (!p || !noise_var || !C_ell || !g1 || !g2 || !f_out) return set_error(WF_EINVAL, "null argument");
     if (!(tol > 0)) return set_error(WF_EINVAL, "tol must be > 0");
-    if (p->g.kind == WF_GEOM_FLAT)
+    if (p->g.kind == WF_GEOM_FLAT) {
+        if (p->opt.schedule == 1 && p->replay_lambda.empty())
+            return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
         return flat_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
+    }
     return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
 }
 

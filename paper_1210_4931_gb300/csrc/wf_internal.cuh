@@ -187,7 +187,7 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
 
 // ring transforms (wf_ring.cu)
 wf_status hp_build_ring_tables(wf_plan p);
-enum RingSynMode { RS_BLEND = 0, RS_MAP = 1 };
+enum RingSynMode { RS_BLEND = 0, RS_MAP = 1, RS_SYN = 2 };
 wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *out_map);
 wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T);
 

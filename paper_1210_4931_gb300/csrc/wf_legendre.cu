@@ -251,21 +251,23 @@ template <int CH> struct Log2;
 template <> struct Log2<16> { static constexpr int v = 4; };
 template <> struct Log2<32> { static constexpr int v = 5; };
 
-__device__ __forceinline__ void block_reduce2(double &a, double &b, double (*red)[LEG_THREADS / 32])
+__device__ __forceinline__ void block_reduce4(double (&v)[4], double (*red)[LEG_THREADS / 32])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0) red[k][warp] = v[k];
     }
-    if (lane == 0) { red[0][warp] = a; red[1][warp] = b; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double x = 0.0, y = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { x += red[0][w]; y += red[1][w]; }
-        a = x;
-        b = y;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            double x = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[k][w];
+            v[k] = x;
+        }
     }
 }
 
@@ -278,7 +280,7 @@ __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long
                                                const double2 *__restrict__ a_old, double2 *__restrict__ out,
                                                double *__restrict__ part, double (*red)[LEG_THREADS / 32])
 {
-    double chi2 = 0.0, res2 = 0.0;
+    double chi2 = 0.0, res2 = 0.0, hnew = 0.0, qnew = 0.0;
     const double wm = (m == 0) ? 1.0 : 2.0;
     for (int j = threadIdx.x; j <= lmax - m; j += blockDim.x) {
         const int l = m + j;
@@ -306,6 +308,9 @@ __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long
             }
             if (S > 0.0) {
                 chi2 += wm * (ao.x * ao.x + ao.y * ao.y) / S;
+                const double an2 = wm * (an.x * an.x + an.y * an.y) / S;
+                hnew += an2;
+                qnew += an2 / S;
                 if (ba.want_resid) {
                     const double k = 1.0 / S + 1.0 / ba.tauh;
                     const double dx = k * (ao.x - an.x), dy = k * (ao.y - an.y);
@@ -316,11 +321,11 @@ __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long
         }
     }
     if (mode == LEG_BLEND) {
-        block_reduce2(chi2, res2, red);
-        if (threadIdx.x == 0) {
-            part[2 * m] = chi2;
-            part[2 * m + 1] = res2;
-        }
+        double v[4] = {chi2, res2, hnew, qnew};
+        block_reduce4(v, red);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) part[4 * m + k] = v[k];
     }
 }
 
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
                                                         double2 *__restrict__ out, double *__restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][LEG_THREADS / 32];
+    __shared__ double red[4][LEG_THREADS / 32];
     const int m = blockIdx.x;
     const int Lm = lcut > 0 ? min(L, lcm_of(lcut, m) - 1) : L;
     const int nl = Lm - m + 1;
@@ -682,7 +687,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana_mx(int lmax, int L, int 
                                                            double2 *__restrict__ out, double *__restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[2][LEG_THREADS / 32];
+    __shared__ double red[4][LEG_THREADS / 32];
     __shared__ int next_group;
     const int m = blockIdx.x;
     const int nl = L - m + 1;

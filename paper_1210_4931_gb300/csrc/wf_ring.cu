@@ -377,6 +377,9 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             if (mode == RS_MAP) {
                 omap[iN] = (double)zz.x;
                 if (south) omap[R.offS + j] = (double)zz.y;
+            } else if (mode == RS_SYN) {
+                tmap[iN] = zz.x;
+                if (south) tmap[R.offS + j] = zz.y;
             } else {
                 {
                     const T s = zz.x, nv = nu[iN], rv = r[iN];

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import wf_inputs as gen
-from gpu_util import T, rel
+from gpu_util import T, healpix_case, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -119,3 +119,34 @@ def test_fp64_correction_sweeps(wf):
     assert r1["resid"][0] <= rep["final_residual"] * 1.01
     assert rep["resid_trace"][-1] == rep["final_residual"]
     plan.close()
+
+
+def test_mixed_chi2_bound_schedule(wf):
+    """Sect. 2.2 cooling with FP32 transforms and FP64 correction sweeps:
+    lambda falls monotonically to 1, the first chi^2 is the bound
+    n_dof - 5 sigma, and the result's true FP64 residual (oracle operator)
+    is at the tolerance (2e-6, above the FP32 floor); the map agrees with the
+    FP64 path's."""
+    import torch
+
+    nside, lmax = 32, 64
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(3, 52))
+    S = basis.per_mode(P["c_ell"])
+    n_dof = int(np.count_nonzero(nu > 0))
+    out = {}
+    for prec in ("mixed", "fp64"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+        wf.wf_set_options(plan, maxiter=20000, schedule=1, refine_sweeps=4 if prec == "mixed" else 0)
+        s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        alm = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+        rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 2e-6, s, alm,
+                          trace_cap=20100)
+        out[prec] = (rep, alm.cpu().numpy(), s.cpu().numpy())
+        plan.close()
+        assert rep["converged"]
+        lam = rep["lambda_trace"]
+        assert lam[0] > 1.0 and np.all(np.diff(lam) <= 0) and lam[-1] == 1.0
+        assert rep["chi2_trace"][0] == pytest.approx(n_dof - 5.0 * np.sqrt(2.0 * n_dof), rel=1e-6)
+    r1 = oracle.messenger_solve(basis, nu * d, nu, S, tau, replay=[(1.0, lmax)], a0=out["mixed"][1])
+    assert r1["resid"][0] < 3e-6
+    assert rel(out["mixed"][2], out["fp64"][2]) < 1e-3

@@ -230,3 +230,77 @@ def test_template_marginalisation_matches_oracle(wf, nside):
     assert rel(out.cpu().numpy(), ref) < 1e-10
     np.testing.assert_allclose(c, cref, rtol=1e-9, atol=1e-9)
     plan.close()
+
+
+@pytest.mark.parametrize("nside", [8, 16])
+def test_chi2_bound_schedule_matches_oracle(wf, nside):
+    """Cooling of Sect. 2.2 on the GPU: lambda solves chi^2(lambda, x_k) = b
+    for every iterate; the result matches the oracle replaying the GPU's
+    lambda trace, the reported chi^2 is the full chi^2 (J-form of the oracle
+    plus its x-independent term), and the lambda decisions match the oracle
+    running the same schedule on its own."""
+    import torch
+
+    from oracle.messenger import RigorousSchedule
+
+    lmax = 2 * nside
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 700 + nside))
+    S = basis.per_mode(P["c_ell"])
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64")
+    wf.wf_set_options(plan, schedule=1)
+    s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    alm = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+    rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-7, s, alm, trace_cap=20000)
+    assert rep["converged"] and rep["final_residual"] < 1e-7
+    lam, chi2 = rep["lambda_trace"], rep["chi2_trace"]
+    assert lam[0] > 1.0 and np.all(np.diff(lam) <= 0) and lam[-1] == 1.0
+    assert np.all(rep["L_trace"] == lmax)
+
+    ref = oracle.messenger_solve(basis, nu * d, nu, S, tau, replay=[(x, lmax) for x in lam], d=d)
+    assert rel(alm.cpu().numpy(), ref["a"]) < 1e-10
+    assert rel(s.cpu().numpy(), ref["s"]) < 1e-10
+    const = np.array([np.sum(nu * d * d / (1.0 + (x - 1.0) * tau * nu)) for x in lam])
+    np.testing.assert_allclose(chi2, ref["chi2"] + const, rtol=1e-9, atol=1e-11 * const.max())
+
+    n_dof = int(np.count_nonzero(nu > 0))
+    b0 = n_dof - 5.0 * np.sqrt(2.0 * n_dof)
+    assert chi2[0] == pytest.approx(b0, rel=1e-12)
+    hot = lam > 1.0
+    assert np.all(np.diff(chi2[hot]) >= -1e-9 * b0)  # b only rises
+
+    sch = RigorousSchedule(n_dof)
+    ind = oracle.messenger_solve(basis, nu * d, nu, S, tau, schedule=sch, tol=1e-7, d=d, maxiter=20000)
+    lam_o = np.array([t[0] for t in ind["trace"]])
+    k = min(50, lam_o.size, lam.size)
+    np.testing.assert_allclose(lam[:k] - 1.0, lam_o[:k] - 1.0, rtol=1e-8, atol=1e-12)
+    np.testing.assert_allclose(chi2[:k][hot[:k]], ind["bound"][:k][hot[:k]], rtol=1e-10)
+    assert abs(ind["iters"] - rep["iters"]) <= 0.02 * ind["iters"] + 2
+    plan.close()
+
+
+def test_chi2_bound_schedule_rejections(wf):
+    import torch
+
+    nside, lmax = 8, 16
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 9))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64")
+    wf.wf_set_options(plan, schedule=1)
+    f = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    g1 = T(np.zeros(plan.npix))
+    g2 = T(np.zeros(plan.nalm, dtype=np.complex128))
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_fluct(plan, T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), g1, g2, 1e-6, f)
+    assert e.value.status == wf.WF_EUNSUPPORTED
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_set_options(plan, schedule=2)
+    assert e.value.status == wf.WF_EINVAL
+    plan.close()
+    flat = wf.wf_plan_create("flat", n=16)
+    wf.wf_set_options(flat, schedule=1)
+    Pf = gen.flat_problem(16, seed=gen.seed_for(1, 9))
+    sf = torch.empty(256, dtype=torch.float64, device="cuda")
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(flat, T(Pf["noise"].ravel()), T(Pf["noise_var"].ravel()), T(Pf["mask"].ravel()),
+                    T(Pf["S"].ravel()), 1e-6, sf)
+    assert e.value.status == wf.WF_EUNSUPPORTED
+    flat.close()
