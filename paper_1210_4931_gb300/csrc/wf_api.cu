@@ -14,7 +14,10 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "wf_internal.cuh"
@@ -39,6 +42,20 @@ wf_status cuda_check(cudaError_t e, const char *what)
     return set_error(WF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+wf_status raise_smem_limit(const void *func, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    WF_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = limit[{dev, func}];
+    if (bytes <= cur) return WF_OK;
+    WF_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return WF_OK;
+}
+
 wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes)
 {
     void *d = nullptr;
@@ -52,6 +69,8 @@ wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes)
 
 Prof::Prof(wf_plan p_, wf_info *i, bool profile) : p(p_), info(i), on(profile)
 {
+    for (int k = 0; k < WF_NK; ++k) k0[k] = p->kcnt[k];
+    p->kfam = WF_K_OTHER;
     if (on && !p->events_ready) {
         for (auto &e : p->ev) cudaEventCreate(&e);
         p->events_ready = true;
@@ -60,7 +79,7 @@ Prof::Prof(wf_plan p_, wf_info *i, bool profile) : p(p_), info(i), on(profile)
 
 void Prof::begin(int family)
 {
-    count(family);
+    p->kfam = family;
     if (!on || nopen >= 16) return;
     fam[nopen] = family;
     cudaEventRecord(p->ev[2 * nopen], p->stream);
@@ -68,6 +87,7 @@ void Prof::begin(int family)
 
 void Prof::end()
 {
+    p->kfam = WF_K_OTHER;
     if (!on || nopen >= 16) return;
     cudaEventRecord(p->ev[2 * nopen + 1], p->stream);
     ++nopen;
@@ -100,6 +120,12 @@ double Prof::iter_end()
 
 void Prof::finish()
 {
+    p->kfam = WF_K_OTHER;
+    for (int k = 0; k < WF_NK; ++k) {
+        cnt[k] += p->kcnt[k] - k0[k];
+        launches += p->kcnt[k] - k0[k];
+        k0[k] = p->kcnt[k];
+    }
     if (!info) return;
     info->launches = launches;
     for (int k = 0; k < WF_NK; ++k) {
@@ -421,8 +447,8 @@ int grid_for(long long n, int nsm) { return (int)std::min<long long>((n + 255) /
 
 wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
 {
-    if (pr) pr->count(WF_K_OTHER);
     k_sums<<<1, 256, 0, p->stream>>>(sp, nsum, p->ws.scal);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     WF_CUDA(cudaMemcpyAsync(p->ws.h_scal, p->ws.scal, nsum * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     WF_CUDA(cudaStreamSynchronize(p->stream));
@@ -440,8 +466,8 @@ wf_status pix_sums(wf_plan p, double u, double *A, double *D, Prof *pr)
     else
         k_pixsums<float><<<grid, 256, 0, p->stream>>>(p->npix, (const float *)p->ws.r, (const float *)p->ws.nu,
                                                       (const float *)p->ws.t, u, p->ws.part_pix);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
-    if (pr) pr->count(WF_K_OTHER);
     SumSpec sp{};
     sp.in[0] = p->ws.part_pix;
     sp.n[0] = grid;
@@ -562,6 +588,7 @@ wf_status hp_setup_T(wf_plan p, const double *d, const double *nv, const uint8_t
     WF_CUDA(cudaMemsetAsync(p->ws.flag, 0, sizeof(int), p->stream));
     k_setup<T><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(p->npix, d, nv, mask, (T *)p->ws.r, (T *)p->ws.nu,
                                                                  p->ws.scal, p->ws.flag);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     int flag = 0;
     double sc[2];
@@ -614,7 +641,6 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     Prof pr(p, info, o.profile != 0);
     double tau = 0;
     long long ndof = 0;
-    pr.count(WF_K_OTHER);
     wf_status st = hp_setup(p, fluct ? nullptr : d, nv, mask, &tau, &ndof);
     if (st != WF_OK) return st;
     const double tau_h = tau * p->omega;
@@ -636,25 +662,22 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     if (fluct) {
         // r = nu^1/2 g1 + Omega Y (S^-1/2 g2), z synthesised into the output map as scratch
         k_isqrt_S<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, (const double2 *)g2, p->ws.a_new);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         if ((st = hp_alm2map(p, p->ws.a_new, lmax, s_out)) != WF_OK) return st;
-        pr.count(WF_K_OTHER, 2);
-        pr.count(WF_K_LEG_SYN);
-        pr.count(WF_K_RING_SYN);
         if (p->prec == WF_PREC_FP64)
             k_fluct_source<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
                 p->npix, (const double *)p->ws.nu, g1, s_out, p->omega, (double *)p->ws.r);
         else
             k_fluct_source<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
                 p->npix, (const float *)p->ws.nu, g1, s_out, p->omega, (float *)p->ws.r);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
     }
     // |b| = |Y^T r| over modes with S > 0
     if ((st = hp_adjoint_T(p, p->ws.r, lmax, p->ws.b)) != WF_OK) return st;
-    pr.count(WF_K_RING_ANA);
-    pr.count(WF_K_LEG_ANA);
-    pr.count(WF_K_OTHER);
     k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, p->ws.b, 0, p->ws.part_harm);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     {
         SumSpec sp{};
@@ -735,7 +758,6 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
             }
             u_cur = u_new;
             lam = 1.0 + u_cur / tau;
-            pr.count(WF_K_OTHER);
             if (p->prec == WF_PREC_FP64)
                 k_blend<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
                     p->npix, (const double *)p->ws.r, (const double *)p->ws.nu, (double *)p->ws.t, lam * tau,
@@ -744,6 +766,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
                 k_blend<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
                     p->npix, (const float *)p->ws.r, (const float *)p->ws.nu, (float *)p->ws.t, (float)(lam * tau),
                     (float)((lam - 1.0) * tau));
+            WF_COUNT_LAUNCH(p);
             WF_CUDA(cudaGetLastError());
         } else {
             pr.begin(WF_K_LEG_SYN);
@@ -767,7 +790,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         pr.end();
         SumSpec sp{};
         sp.in[0] = p->ws.part_pix;
-        sp.n[0] = p->tab.ringGrid;
+        sp.n[0] = p->npairs;
         sp.stride[0] = 1;
         for (int q = 0; q < 4; ++q) {
             sp.in[1 + q] = p->ws.part_harm + q;
@@ -868,15 +891,15 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         return replay ? WF_OK : WF_ENOCONV;
     }
     if ((st = hp_alm2map(p, p->ws.a, lmax, s_out)) != WF_OK) return st;
-    pr.count(WF_K_LEG_SYN);
-    pr.count(WF_K_RING_SYN);
     if (alm_out)
         WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.a, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
     double chi2n = NAN;
     if (!fluct) {
         k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, p->ws.a, 1, p->ws.part_harm);
+        WF_COUNT_LAUNCH(p);
         const int gb = 256;
         k_pix_chi2<<<gb, 256, 0, p->stream>>>(p->npix, d, nv, mask, s_out, p->ws.part_pix);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         SumSpec sp{};
         sp.in[0] = p->ws.part_harm;
@@ -885,7 +908,6 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         sp.in[1] = p->ws.part_pix;
         sp.n[1] = gb;
         sp.stride[1] = 1;
-        pr.count(WF_K_OTHER, 2);
         if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
         chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
     } else {
@@ -948,9 +970,11 @@ wf_status hp_create(wf_plan p)
     if ((st = plan_alloc(p, &p->ws.r, p->npix * es)) != WF_OK) return st;
     if ((st = plan_alloc(p, &p->ws.nu, p->npix * es)) != WF_OK) return st;
     if ((st = plan_alloc(p, &p->ws.t, p->npix * es)) != WF_OK) return st;
-    const int npart = std::max(p->tab.ringGrid, std::max(256, 4 * p->nsm));  // also the 2 x (<= 2 nsm) chi^2-bound sums
+    // per ring pair; also the 2 x (<= 2 nsm) chi^2-bound sums
+    const int npart = std::max(p->npairs, std::max(256, 4 * p->nsm));
     if ((st = plan_alloc(p, (void **)&p->ws.part_pix, npart * sizeof(double))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&p->ws.part_harm, 4 * (p->lmax + 2) * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.epi, (p->lmax + 1) * sizeof(double4))) != WF_OK) return st;
     return WF_OK;
 }
 
@@ -1131,6 +1155,7 @@ wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mas
         if (st != WF_OK) return st;
     }
     k_template_sums<<<grid, 256, 0, p->stream>>>(p->npairs, p->tab.rings, p->tab.x64, d_raw, mask, p->ws.redu);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     std::vector<double> part((size_t)14 * grid);
     WF_CUDA(cudaMemcpyAsync(part.data(), p->ws.redu, need, cudaMemcpyDeviceToHost, p->stream));
@@ -1147,6 +1172,7 @@ wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mas
     if (!solve4(G, b, c)) return set_error(WF_EINVAL, "templates are degenerate on the observed pixels");
     k_template_apply<<<grid, 256, 0, p->stream>>>(p->npairs, p->tab.rings, p->tab.x64, d_raw, mask, c[0], c[1], c[2],
                                                   c[3], d_out);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     WF_CUDA(cudaStreamSynchronize(p->stream));
     if (coef)
@@ -1174,6 +1200,7 @@ wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm)
         WF_CUDA(cudaMemcpyAsync(p->ws.t, map, p->npix * 8, cudaMemcpyDeviceToDevice, p->stream));
     } else {
         k_map_to_T<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(p->npix, map, (float *)p->ws.t);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
     }
     wf_status st = hp_adjoint_T(p, p->ws.t, L, (double2 *)alm);

@@ -518,8 +518,8 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
     }();
     const int n = f->n, nh = f->nh;
     Prof pr(p, info, p->opt.profile != 0);
-    pr.count(WF_K_OTHER);
     k_flat_setup<<<1, 1024, 0, p->stream>>>(p->npix, fluct ? nullptr : d, noise_var, mask, f->r, f->nu, p->ws.redu);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     double h[3];
     WF_CUDA(cudaMemcpyAsync(h, p->ws.redu, sizeof h, cudaMemcpyDeviceToHost, p->stream));
@@ -597,6 +597,7 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
     A.status = f->status;
     pr.begin(WF_K_FLAT);
     k_flat_solve<<<FLAT_CS, FLAT_THREADS, f->smem, p->stream>>>(A);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     pr.end();
     FlatStatus fs;

@@ -79,8 +79,9 @@ struct Workspace {
     void *scr = nullptr;          // per-CTA Bluestein scratch (2 * max Bluestein n complex per CTA)
     double2 *Glow = nullptr;      // mixed: FP64-block synthesis coefficients [pair][glow_cap][hemisphere]
     double2 *b_low = nullptr;     // mixed: FP64-block analysis output (alm layout, m < lc)
-    double *part_pix = nullptr;   // per ring-CTA partial sums
-    double *part_harm = nullptr;  // per m: [chi2_h, resid^2]
+    double *part_pix = nullptr;   // per ring-pair partial sums
+    double *part_harm = nullptr;  // per m: [chi2_h, resid^2, x^T S^-1 x, x^T S^-2 x]
+    double4 *epi = nullptr;       // per l: factors of the harmonic blend (Eq. 4) for the current lambda
     double *scal = nullptr;       // reduced scalars (device)
     double *h_scal = nullptr;     // pinned host mirror
     double *d_in = nullptr, *nv_in = nullptr, *out_map = nullptr, *cl_in = nullptr, *alm_io = nullptr;  // host-API staging
@@ -109,6 +110,8 @@ struct HpTables {
     int bmax = 0;          // smem FFT buffer length (complex entries)
     int maxBlue = 0;       // longest Bluestein ring
     int ringGrid = 0;      // persistent grid of the ring kernels
+    int *order = nullptr;  // ring pairs by decreasing transform cost
+    int *ticket = nullptr; // work counter of the ring kernels (zeroed before each launch)
 };
 
 }  // namespace wf
@@ -134,6 +137,8 @@ struct wf_plan_s {
     cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
     wf_plan sub = nullptr;    // mixed precision: FP64 plan of the same geometry for the correction sweeps
     bool events_ready = false;
+    long long kcnt[WF_NK] = {};  // kernels launched on this plan, by family (WF_K_*)
+    int kfam = WF_K_OTHER;       // family the next launches are counted under
 };
 
 namespace wf {
@@ -147,8 +152,14 @@ wf_status cuda_check(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ::wf::cuda_check(_e, #call);             \
     } while (0)
 
+// every kernel launch of the HEALPix path is counted on its plan, under the
+// family of the stage that is open (Prof::begin) or WF_K_OTHER
+#define WF_COUNT_LAUNCH(p) (++(p)->kcnt[(p)->kfam])
 // device allocation owned by the plan
 wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes);
+// raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it;
+// serialised, so plans used from several host threads cannot undo each other)
+wf_status raise_smem_limit(const void *func, size_t bytes);
 
 // Per-call kernel accounting: launch counts always; device time per kernel
 // family with CUDA events on the plan's stream when profiling is on.
@@ -161,10 +172,10 @@ struct Prof {
     long long launches = 0;
     double ms[WF_NK] = {};
     long long cnt[WF_NK] = {};
+    long long k0[WF_NK] = {};  // plan launch counters when this accounting started
     Prof(wf_plan p_, wf_info *i, bool profile);
-    void begin(int family);  // call before a launch of `family`
-    void end();              // call after it
-    void count(int family, int n = 1) { cnt[family] += n; launches += n; }
+    void begin(int family);  // call before the launches of a stage of `family`
+    void end();              // call after them
     void collect();          // after a stream synchronisation: harvest event times
     void iter_begin();
     double iter_end();       // after a synchronisation: ms since iter_begin (NaN when off)
@@ -178,6 +189,7 @@ struct BlendArgs {
     double lam_tauh = 0;   // lambda tau Omega
     double tauh = 0;       // tau Omega
     const double *S = nullptr;  // C_ell (device)
+    const double4 *epi = nullptr;  // per l: (Omega S/(S + lambda tau_h), 1/S, 1/S + 1/tau_h, S > 0); filled per launch
     int want_resid = 0;
 };
 wf_status hp_set_low_block(wf_plan p, int lc);

@@ -273,6 +273,23 @@ __device__ __forceinline__ void block_reduce4(double (&v)[4], double (*red)[LEG_
 
 // Eq. (4) epilogue shared by both precisions: t_hat = Omega (c acc + low),
 // a_new = S/(S + lam tau_h) t_hat, chi^2 of a_old, lambda = 1 residual.
+// per-l factors of the harmonic blend (Eq. 4) and of the chi^2 / residual sums
+__global__ void k_epi_table(int lmax, const double *__restrict__ S, double omega, double lam_tauh, double tauh,
+                            double4 *__restrict__ epi)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l > lmax) return;
+    const double s = S[l];
+    double4 e = make_double4(0.0, 0.0, 0.0, 0.0);
+    if (s > 0.0) {
+        e.x = omega * s / (s + lam_tauh);
+        e.y = 1.0 / s;
+        e.z = 1.0 / s + 1.0 / tauh;
+        e.w = 1.0;
+    }
+    epi[l] = e;
+}
+
 template <typename ACC>
 __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long base, int mode, double omega,
                                                const BlendArgs &ba, const double *__restrict__ c64,
@@ -298,22 +315,21 @@ __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long
         if (mode == LEG_ADJOINT) {
             out[idx] = b;
         } else {
-            const double S = ba.S[l];
+            // per-l factors tabulated once per launch (no FP64 division per a_lm)
+            const double4 e = ba.epi[l];
             const double2 ao = a_old[idx];
             double2 an = make_double2(0.0, 0.0);
-            if (l <= L && S > 0.0) {
-                const double f = omega * S / (S + ba.lam_tauh);
-                an.x = f * b.x;
-                an.y = f * b.y;
+            if (l <= L && e.w > 0.0) {
+                an.x = e.x * b.x;
+                an.y = e.x * b.y;
             }
-            if (S > 0.0) {
-                chi2 += wm * (ao.x * ao.x + ao.y * ao.y) / S;
-                const double an2 = wm * (an.x * an.x + an.y * an.y) / S;
+            if (e.w > 0.0) {
+                chi2 += wm * (ao.x * ao.x + ao.y * ao.y) * e.y;
+                const double an2 = wm * (an.x * an.x + an.y * an.y) * e.y;
                 hnew += an2;
-                qnew += an2 / S;
+                qnew += an2 * e.y;
                 if (ba.want_resid) {
-                    const double k = 1.0 / S + 1.0 / ba.tauh;
-                    const double dx = k * (ao.x - an.x), dy = k * (ao.y - an.y);
+                    const double dx = e.z * (ao.x - an.x), dy = e.z * (ao.y - an.y);
                     res2 += wm * (dx * dx + dy * dy);
                 }
             }
@@ -771,9 +787,10 @@ wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *
     const int gx = (p->npairs + 4 * LEG_THREADS - 1) / (4 * LEG_THREADS);
     dim3 grid(gx, Lgrid + 1);
     const size_t sm = syn_smem<double>(lcut > 0 ? std::min(L, lcut + 1) : L);
-    WF_CUDA(cudaFuncSetAttribute(k_legsyn<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (wf_status st = raise_smem_limit((const void *)k_legsyn<double>, sm)) return st;
     k_legsyn<double><<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, lcut, alm, t.A64, t.c64, t.ls,
                                                             t.s0_64, t.s1_64, t.x64, G, gstride);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
 }
@@ -787,10 +804,11 @@ wf_status launch_ana64(wf_plan p, int L, int lcut, const void *F, LegMode mode, 
     const int Lgrid = lcut > 0 ? std::min(L, lcut - 1) : L;
     if (Lgrid < 0) return WF_OK;
     const size_t sm = ana_smem<double, CH>(lcut > 0 ? std::min(L, lcut + 1) : L);
-    WF_CUDA(cudaFuncSetAttribute(k_legana<double, TF, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (wf_status st = raise_smem_limit((const void *)k_legana<double, TF, CH>, sm)) return st;
     k_legana<double, TF, CH><<<Lgrid + 1, LEG_THREADS, sm, p->stream>>>(
         p->lmax, L, p->npairs, lcut, (const cx<TF> *)F, t.A64, t.ls, t.s0_64, t.s1_64, t.x64, t.c64, (int)mode,
         p->omega, ba, a_old, out, p->ws.part_harm);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
 }
@@ -855,6 +873,7 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
         const long long nb = (ns + th - 1) / th;
         k_seeds<<<(unsigned)nb, th, 0, p->stream>>>(lmax, np, t.x64, dst64, dlog2c, t.A64, t.c64, t.ls, t.s0_64,
                                                      t.s1_64);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
     }
     if (f32) {
@@ -900,6 +919,7 @@ wf_status hp_set_low_block(wf_plan p, int lc)
     const int th = 256;
     k_restart_seeds<<<(unsigned)((ns + th - 1) / th), th, 0, p->stream>>>(p->lmax, p->npairs, lc, t.x64, t.A64, t.ls,
                                                                         t.s0_64, t.s1_64, t.ls_mx, t.s0_mx, t.s1_mx);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     if (lc > 0 && lc > t.glow_cap) {
         wf_status st = plan_alloc(p, (void **)&p->ws.Glow, (size_t)p->npairs * lc * 2 * sizeof(double2));
@@ -917,17 +937,27 @@ wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
     const int gx = (p->npairs + MXP * LEG_THREADS - 1) / (MXP * LEG_THREADS);
     dim3 grid(gx, L + 1);
     const size_t sm = syn_mx_smem(L);
-    WF_CUDA(cudaFuncSetAttribute(k_legsyn_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (wf_status st = raise_smem_limit((const void *)k_legsyn_mx, sm)) return st;
     k_legsyn_mx<<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, t.A32, t.B32, t.c64, t.ls_mx,
                                                        t.s0_mx, t.s1_mx, t.x32, t.w32, (float2 *)p->ws.G);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     if (t.lc_mx > 0) return launch_syn64(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap);
     return WF_OK;
 }
 
-wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old, double2 *out)
+wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba_in, const double2 *a_old,
+                               double2 *out)
 {
     const HpTables &t = p->tab;
+    BlendArgs ba = ba_in;
+    if (mode == LEG_BLEND) {
+        k_epi_table<<<(p->lmax + 256) / 256, 256, 0, p->stream>>>(p->lmax, ba.S, p->omega, ba.lam_tauh, ba.tauh,
+                                                                  p->ws.epi);
+        WF_COUNT_LAUNCH(p);
+        WF_CUDA(cudaGetLastError());
+        ba.epi = p->ws.epi;
+    }
     if (p->prec == WF_PREC_FP64) return launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out);
     const double2 *low = nullptr;
     if (t.lc_mx > 0) {
@@ -937,10 +967,11 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
         low = p->ws.b_low;
     }
     const size_t sm = ana_mx_smem(L);
-    WF_CUDA(cudaFuncSetAttribute(k_legana_mx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (wf_status st = raise_smem_limit((const void *)k_legana_mx, sm)) return st;
     k_legana_mx<<<L + 1, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, t.lc_mx, (const float2 *)p->ws.F,
                                                         t.A32, t.B32, t.ls_mx, t.s0_mx, t.s1_mx, t.x32, t.w32, t.c64,
                                                         (int)mode, p->omega, ba, low, a_old, out, p->ws.part_harm);
+    WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
 }

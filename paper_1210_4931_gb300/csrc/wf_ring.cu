@@ -26,6 +26,7 @@
 //     t = s + lambda tau (r - nu s) / (1 + (lambda - 1) tau nu)
 // and the pixel term of chi^2 (Eq. 6, x-independent part dropped):
 //     sum (nu s^2 - 2 r s) / (1 + (lambda - 1) tau nu).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -144,6 +145,12 @@ template <typename T> struct SmallDft<T, 8> {
     }
 };
 
+// Shared-memory FFT buffers are padded by one entry per 16: the Stockham
+// writes at small strides (8 Ns entries apart) would otherwise fall on one
+// or two banks for the whole warp.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+inline size_t padded_len(int n) { return (size_t)n + (size_t)n / 16 + 1; }
+
 template <typename T, int R, int LOGR, int BPT>
 __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *__restrict__ tw,
                                               int logNmax)
@@ -157,15 +164,17 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
         const int j = b * blockDim.x + threadIdx.x;
         if (j < NR) {
             const int k = j & (Ns - 1);
+            // twiddles w^r, r < R, from one table entry w = e^{-+2 pi i k / (R Ns)} by products
+            // (the full table does not stay in L1 next to the large FFT buffers)
+            cx<T> w1 = tw[k << tsh];
+            if (sign > 0) w1.y = -w1.y;
+            cx<T> wr = w1;
+            v[b][0] = x[pidx(j)];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                cx<T> a = x[j + r * NR];
-                if (r > 0 && k > 0) {
-                    cx<T> w = tw[(k * r) << tsh];
-                    if (sign > 0) w.y = -w.y;
-                    a = cmul(a, w);
-                }
-                v[b][r] = a;
+            for (int r = 1; r < R; ++r) {
+                const cx<T> a = x[pidx(j + r * NR)];
+                v[b][r] = cmul(a, wr);
+                if (r + 1 < R) wr = cmul(wr, w1);
             }
             SmallDft<T, R>::run(v[b], sign);
         }
@@ -178,7 +187,7 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
             const int k = j & (Ns - 1);
             const int d = ((j >> logNs) << (logNs + LOGR)) + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[d + SmallDft<T, R>::out(r) * Ns] = v[b][r];
+            for (int r = 0; r < R; ++r) x[pidx(d + SmallDft<T, R>::out(r) * Ns)] = v[b][r];
         }
     }
     __syncthreads();
@@ -202,36 +211,42 @@ __device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> 
     }
 }
 
-// DFT of one ring pair.  Input: in smem buf (naive / pow2) or in zin (Bluestein).
-// Returns a pointer to the n outputs.
+// The n outputs of a ring DFT: in the padded FFT buffer (power-of-two rings)
+// or in the plain zout buffer (direct and Bluestein rings).
+template <typename T> struct RingOut {
+    const cx<T> *p;
+    int padded;
+    __device__ __forceinline__ cx<T> operator[](int j) const { return p[padded ? pidx(j) : j]; }
+};
+
+// DFT of one ring pair.  Input: padded buf (direct / pow2) or plain zin (Bluestein).
 template <typename T>
-__device__ cx<T> *ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout, int sign,
-                           const cx<T> *__restrict__ roots, const cx<T> *__restrict__ V,
-                           const cx<T> *__restrict__ tw, int logNmax)
+__device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout, int sign,
+                               const cx<T> *__restrict__ roots, const cx<T> *__restrict__ V,
+                               const cx<T> *__restrict__ tw, int logNmax)
 {
     const int n = R.n;
-    const int twon = 2 * n;
+    const unsigned twon = 2u * (unsigned)n;
     const cx<T> *root = roots + R.rootOff;
     if (R.kind == RING_NAIVE) {
-        cx<T> *out = buf + n;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             cx<T> acc = mk<T>(0, 0);
             for (int k = 0; k < n; ++k) {
-                cx<T> w = root[(2LL * j * k) % twon];
+                cx<T> w = root[(2u * (unsigned)(j * k)) % twon];
                 if (sign < 0) w.y = -w.y;
-                acc = cadd(acc, cmul(buf[k], w));
+                acc = cadd(acc, cmul(buf[pidx(k)], w));
             }
-            out[j] = acc;
+            zout[j] = acc;
         }
         __syncthreads();
-        return out;
+        return RingOut<T>{zout, 0};
     }
     if (R.kind == RING_POW2) {
         fft_pow2<T>(buf, R.logF, sign, tw, logNmax);
-        return buf;
+        return RingOut<T>{buf, 1};
     }
-    // Bluestein, two half-length passes
-    const int H = 1 << R.logF;           // M / 2
+    // Bluestein, two half-length passes (indices j^2 < 2^26: 32-bit arithmetic)
+    const int H = 1 << R.logF;                 // M / 2
     const int mstep = logNmax - (R.logF + 1);  // index step of w_M in tw
     const cx<T> *Vh = V + R.vOff;
     for (int h = 0; h < 2; ++h) {
@@ -240,34 +255,34 @@ __device__ cx<T> *ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout
             if (j < n) {
                 cx<T> u = zin[j];
                 if (sign > 0) u.y = -u.y;
-                cx<T> c = root[((long long)j * j) % twon];
+                cx<T> c = root[((unsigned)j * (unsigned)j) % twon];
                 c.y = -c.y;  // e^{-i pi j^2 / n}
                 v = cmul(u, c);
-                if (h) v = cmul(v, tw[(long long)j << mstep]);
+                if (h) v = cmul(v, tw[j << mstep]);
             }
-            buf[j] = v;
+            buf[pidx(j)] = v;
         }
         __syncthreads();
         fft_pow2<T>(buf, R.logF, -1, tw, logNmax);
-        for (int k = threadIdx.x; k < H; k += blockDim.x) buf[k] = cmul(buf[k], Vh[h * H + k]);
+        for (int k = threadIdx.x; k < H; k += blockDim.x) buf[pidx(k)] = cmul(buf[pidx(k)], Vh[h * H + k]);
         __syncthreads();
         fft_pow2<T>(buf, R.logF, +1, tw, logNmax);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             if (h == 0) {
-                zout[k] = buf[k];
+                zout[k] = buf[pidx(k)];
             } else {
-                cx<T> w = tw[(long long)k << mstep];
+                cx<T> w = tw[k << mstep];
                 w.y = -w.y;  // w_M^{-k}
-                cx<T> c = root[((long long)k * k) % twon];
+                cx<T> c = root[((unsigned)k * (unsigned)k) % twon];
                 c.y = -c.y;
-                cx<T> y = cmul(cadd(zout[k], cmul(buf[k], w)), c);
+                cx<T> y = cmul(cadd(zout[k], cmul(buf[pidx(k)], w)), c);
                 if (sign > 0) y.y = -y.y;
                 zout[k] = y;
             }
         }
         __syncthreads();
     }
-    return zout;
+    return RingOut<T>{zout, 0};
 }
 
 template <typename T>
@@ -281,17 +296,20 @@ __device__ __forceinline__ double block_sum(double v, double *red)
     double s = 0.0;
     if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();  // red is reused by the next call
     return s;
 }
 
 struct RingCommon {
     int npairs, lmax, L, logNmax;
     const RingTab *rings;
+    const int *order;     // ring pairs by decreasing cost
+    int *ticket;          // work counter (zeroed before the launch)
     long long scr_stride;
     const double2 *Glow;  // mixed path: FP64-block coefficients for m < lc (or null)
     int lc, glow_stride;
-    int bmax;             // shared FFT buffer length
-    int zsmem;            // 1: Bluestein input/output buffers follow the FFT buffer in shared memory
+    int bpad;             // padded shared FFT buffer length
+    int zsmem;            // 1: Bluestein / direct buffers follow the FFT buffer in shared memory
 };
 
 __device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -303,9 +321,26 @@ __device__ __forceinline__ void prefetch_range(const void *base, size_t bytes)
     for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128) prefetch_l2(b + off);
 }
 
+// Work distribution: CTAs take ring pairs from a global counter in order of
+// decreasing cost (Bluestein rings first), one ticket ahead so that the next
+// pair's rows can be prefetched while this one is transformed.
+__device__ __forceinline__ int take_ticket(int *ticket, int *s_tick)
+{
+    if (threadIdx.x == 0) *s_tick = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = *s_tick;
+    __syncthreads();
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // synthesis side: fold -> inverse ring DFT -> blend (or write the map)
 // ---------------------------------------------------------------------------
+// Fold H_k = sum_{m = k mod n} G_m e^{i pi m q / n} + conj terms of -m, for
+// the packed north/south pair.  Each bin is summed by S sub-lanes of one warp
+// (S = n > 256 ? 1 : up to 32), each taking every S-th alias of the bin, and
+// the S partial sums are combined by shuffles in a fixed order: small polar
+// rings, whose bins collect up to 2L/n aliases, no longer serialise the CTA.
 template <typename T>
 __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, const cx<T> *__restrict__ roots,
                                                           const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
@@ -316,25 +351,29 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[RING_THREADS / 32];
+    __shared__ int s_tick;
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *zin = rc.zsmem ? buf + rc.bmax : scr + (size_t)blockIdx.x * rc.scr_stride;
+    cx<T> *zin = rc.zsmem ? buf + rc.bpad : scr + (size_t)blockIdx.x * rc.scr_stride;
     cx<T> *zout = zin + rc.scr_stride / 2;
     const int L = rc.L;
     const T lt = lam * tau, lm1t = (lam - (T)1) * tau;
-    double chi = 0.0;
-    for (int it = blockIdx.x; it < rc.npairs; it += gridDim.x) {
-        T chi_pair = 0;  // per-thread partial of this pair in the working precision
-        const int pair = rc.npairs - 1 - it;
+    int cur = take_ticket(rc.ticket, &s_tick);
+    while (cur < rc.npairs) {
+        if (threadIdx.x == 0) s_tick = atomicAdd(rc.ticket, 1);
+        __syncthreads();
+        const int nxt = s_tick;
+        const int pair = rc.order[cur];
         const RingTab R = rc.rings[pair];
-        const int n = R.n, q = R.q, twon = 2 * n;
+        const int n = R.n, q = R.q;
+        const unsigned twon = 2u * (unsigned)n;
         const cx<T> *root = roots + R.rootOff;
         const cx<T> *g = G + (size_t)pair * (rc.lmax + 1) * 2;
-        cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
+        const bool blue = R.kind == RING_BLUESTEIN;
         const bool south = R.offS >= 0;
-        if (it + (int)gridDim.x < rc.npairs) {  // next pair of this CTA: pull its rows into L2
-            const int nxt = rc.npairs - 1 - (it + (int)gridDim.x);
-            const RingTab Rn = rc.rings[nxt];
-            prefetch_range(G + (size_t)nxt * (rc.lmax + 1) * 2, (size_t)(L + 1) * 2 * sizeof(cx<T>));
+        if (nxt < rc.npairs) {  // next pair of this CTA: pull its rows into L2
+            const int pn = rc.order[nxt];
+            const RingTab Rn = rc.rings[pn];
+            prefetch_range(G + (size_t)pn * (rc.lmax + 1) * 2, (size_t)(L + 1) * 2 * sizeof(cx<T>));
             if (mode == RS_BLEND) {
                 prefetch_range(r + Rn.offN, (size_t)Rn.n * sizeof(T));
                 prefetch_range(nu + Rn.offN, (size_t)Rn.n * sizeof(T));
@@ -354,23 +393,41 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             }
             return v;
         };
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        int S = 1;
+        while (S < 32 && 2 * S * n <= (int)blockDim.x) S *= 2;
+        const int sub = threadIdx.x & (S - 1);
+        const int nb = blockDim.x / S;
+        for (int base = 0; base < n; base += nb) {
+            const int k = base + threadIdx.x / S;
             cx<T> hn = mk<T>(0, 0), hs = mk<T>(0, 0);
-            for (int m = k; m <= L; m += n) {
-                const cx<T> ph = root[q ? (m % twon) : 0];
-                hn = cadd(hn, cmul(coef(m, 0), ph));
-                hs = cadd(hs, cmul(coef(m, 1), ph));
+            if (k < n) {
+                for (int m = k + sub * n; m <= L; m += S * n) {
+                    const cx<T> ph = root[q ? (unsigned)m % twon : 0u];
+                    hn = cadd(hn, cmul(coef(m, 0), ph));
+                    hs = cadd(hs, cmul(coef(m, 1), ph));
+                }
+                for (int m = (k == 0 ? n : n - k) + sub * n; m <= L; m += S * n) {
+                    const cx<T> ph = root[q ? (unsigned)m % twon : 0u];
+                    hn = cadd(hn, cconj(cmul(coef(m, 0), ph)));
+                    hs = cadd(hs, cconj(cmul(coef(m, 1), ph)));
+                }
             }
-            for (int m = (k == 0 ? n : n - k); m <= L; m += n) {
-                const cx<T> ph = root[q ? (m % twon) : 0];
-                hn = cadd(hn, cconj(cmul(coef(m, 0), ph)));
-                hs = cadd(hs, cconj(cmul(coef(m, 1), ph)));
+            for (int o = S >> 1; o >= 1; o >>= 1) {
+                hn.x += __shfl_xor_sync(0xffffffffu, hn.x, o);
+                hn.y += __shfl_xor_sync(0xffffffffu, hn.y, o);
+                hs.x += __shfl_xor_sync(0xffffffffu, hs.x, o);
+                hs.y += __shfl_xor_sync(0xffffffffu, hs.y, o);
             }
-            if (!south) hs = mk<T>(0, 0);
-            in[k] = mk<T>(hn.x - hs.y, hn.y + hs.x);
+            if (k < n && sub == 0) {
+                if (!south) hs = mk<T>(0, 0);
+                const cx<T> z = mk<T>(hn.x - hs.y, hn.y + hs.x);
+                if (blue) zin[k] = z;
+                else buf[pidx(k)] = z;
+            }
         }
         __syncthreads();
-        const cx<T> *z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax);
+        T chi_pair = 0;  // per-thread partial of this pair in the working precision
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             const cx<T> zz = z[j];
             const long long iN = R.offN + j;
@@ -396,12 +453,13 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
                 }
             }
         }
-        chi += (double)chi_pair;
-        __syncthreads();
-    }
-    if (mode == RS_BLEND) {
-        const double s = block_sum<T>(chi, red);
-        if (threadIdx.x == 0) part[blockIdx.x] = s;
+        if (mode == RS_BLEND) {  // per-pair partial: the reduction order does not depend on the schedule
+            const double s = block_sum<T>((double)chi_pair, red);
+            if (threadIdx.x == 0) part[pair] = s;
+        } else {
+            __syncthreads();
+        }
+        cur = nxt;
     }
 }
 
@@ -415,26 +473,35 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
                                                           cx<T> *__restrict__ F)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_tick;
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
-    cx<T> *zin = rc.zsmem ? buf + rc.bmax : scr + (size_t)blockIdx.x * rc.scr_stride;
+    cx<T> *zin = rc.zsmem ? buf + rc.bpad : scr + (size_t)blockIdx.x * rc.scr_stride;
     cx<T> *zout = zin + rc.scr_stride / 2;
     const int L = rc.L;
-    for (int it = blockIdx.x; it < rc.npairs; it += gridDim.x) {
-        const int pair = rc.npairs - 1 - it;
+    int cur = take_ticket(rc.ticket, &s_tick);
+    while (cur < rc.npairs) {
+        if (threadIdx.x == 0) s_tick = atomicAdd(rc.ticket, 1);
+        __syncthreads();
+        const int nxt = s_tick;
+        const int pair = rc.order[cur];
         const RingTab R = rc.rings[pair];
-        const int n = R.n, q = R.q, twon = 2 * n;
+        const int n = R.n, q = R.q;
+        const unsigned twon = 2u * (unsigned)n;
         const cx<T> *root = roots + R.rootOff;
-        cx<T> *in = (R.kind == RING_BLUESTEIN) ? zin : buf;
+        const bool blue = R.kind == RING_BLUESTEIN;
         const bool south = R.offS >= 0;
-        if (it + (int)gridDim.x < rc.npairs) {
-            const RingTab Rn = rc.rings[rc.npairs - 1 - (it + (int)gridDim.x)];
+        if (nxt < rc.npairs) {
+            const RingTab Rn = rc.rings[rc.order[nxt]];
             prefetch_range(map + Rn.offN, (size_t)Rn.n * sizeof(T));
             if (Rn.offS >= 0) prefetch_range(map + Rn.offS, (size_t)Rn.n * sizeof(T));
         }
-        for (int j = threadIdx.x; j < n; j += blockDim.x)
-            in[j] = mk<T>(map[R.offN + j], south ? map[R.offS + j] : (T)0);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const cx<T> v = mk<T>(map[R.offN + j], south ? map[R.offS + j] : (T)0);
+            if (blue) zin[j] = v;
+            else buf[pidx(j)] = v;
+        }
         __syncthreads();
-        const cx<T> *z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax);
         cx<T> *f = F + (size_t)pair * (rc.lmax + 1) * 2;
         for (int m = threadIdx.x; m <= L; m += blockDim.x) {
             const int k = m % n;
@@ -442,58 +509,83 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
             const cx<T> zk = z[k], znk = z[nk];
             const cx<T> tn = mk<T>((T)0.5 * (zk.x + znk.x), (T)0.5 * (zk.y - znk.y));
             const cx<T> ts = mk<T>((T)0.5 * (zk.y + znk.y), (T)-0.5 * (zk.x - znk.x));
-            cx<T> ph = root[q ? (m % twon) : 0];
+            cx<T> ph = root[q ? (unsigned)m % twon : 0u];
             ph.y = -ph.y;
             f[2 * m] = cmul(ph, tn);
             f[2 * m + 1] = south ? cmul(ph, ts) : mk<T>(0, 0);
         }
         __syncthreads();
+        cur = nxt;
     }
 }
 
 template <typename T> struct RingLaunch {
+    static RingCommon common(wf_plan p, int L)
+    {
+        const HpTables &t = p->tab;
+        RingCommon rc{};
+        rc.npairs = p->npairs;
+        rc.lmax = p->lmax;
+        rc.L = L;
+        rc.logNmax = t.logNmax;
+        rc.rings = t.rings;
+        rc.order = t.order;
+        rc.ticket = t.ticket;
+        rc.scr_stride = 2LL * zlen(t);
+        rc.bpad = (int)padded_len(t.bmax);
+        rc.zsmem = zsmem();
+        return rc;
+    }
     static wf_status syn(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *omap)
     {
         const HpTables &t = p->tab;
-        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0, t.bmax, zsmem()};
+        RingCommon rc = common(p, L);
         if (p->prec != WF_PREC_FP64 && t.lc_mx > 0) {
             rc.Glow = p->ws.Glow;
             rc.lc = t.lc_mx;
             rc.glow_stride = t.glow_cap;
         }
         const size_t sm = smem_bytes(t);
-        WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
         k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
             rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
             (const cx<T> *)p->ws.G, (int)mode, (const T *)p->ws.r, (const T *)p->ws.nu, (T)lam, (T)tau,
             (T *)p->ws.t, omap, p->ws.part_pix);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         return WF_OK;
     }
     static wf_status ana(wf_plan p, int L, const void *map)
     {
         const HpTables &t = p->tab;
-        RingCommon rc{p->npairs, p->lmax, L, t.logNmax, t.rings, 2LL * t.maxBlue, nullptr, 0, 0, t.bmax, zsmem()};
+        RingCommon rc = common(p, L);
         const size_t sm = smem_bytes(t);
-        WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
         k_ringana<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
                                                                   (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
                                                                   (const T *)map, (cx<T> *)p->ws.F);
+        WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         return WF_OK;
     }
-    // FP32: the Bluestein buffers fit next to the FFT buffer (the kernel runs one CTA
-    // per SM anyway, bounded by registers); FP64 keeps them in per-CTA global scratch
+    // FP32: the Bluestein / direct buffers fit next to the FFT buffer (the kernel
+    // runs one CTA per SM anyway, bounded by registers); FP64 keeps them in
+    // per-CTA global scratch
     static int zsmem() { return sizeof(T) == 4 ? 1 : 0; }
+    static long long zlen(const HpTables &t) { return t.maxBlue > NAIVE_MAX ? t.maxBlue : NAIVE_MAX; }
     static size_t smem_bytes(const HpTables &t)
     {
-        return ((size_t)t.bmax + (zsmem() ? 2 * (size_t)t.maxBlue : 0)) * sizeof(cx<T>);
+        return (padded_len(t.bmax) + (zsmem() ? 2 * (size_t)zlen(t) : 0)) * sizeof(cx<T>);
     }
+    // The dynamic shared-memory limit is raised once per kernel and size, before
+    // any launch that needs it, and never lowered: plans of several sizes may
+    // launch concurrently from different host threads.
     static wf_status grid(wf_plan p, int *out)
     {
         const size_t sm = smem_bytes(p->tab);
-        WF_CUDA(cudaFuncSetAttribute(k_ringsyn<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        WF_CUDA(cudaFuncSetAttribute(k_ringana<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        wf_status st;
+        if ((st = raise_smem_limit((const void *)k_ringsyn<T>, sm)) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_ringana<T>, sm)) != WF_OK) return st;
         int b1 = 0, b2 = 0;
         WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_ringsyn<T>, RING_THREADS, sm));
         WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_ringana<T>, RING_THREADS, sm));
@@ -617,8 +709,23 @@ wf_status hp_build_ring_tables(wf_plan p)
         if ((st = upload_cx<double>(p, &p->tab.tw, tw)) != WF_OK) return st;
         if ((st = RingLaunch<double>::grid(p, &p->tab.ringGrid)) != WF_OK) return st;
     }
+    // pairs by decreasing cost: Bluestein (four half-length FFTs), then the rest by length
+    std::vector<int> order(np);
+    std::vector<double> cost(np);
+    for (int i = 0; i < np; ++i) {
+        order[i] = i;
+        const RingTab &t = rt[i];
+        const double F = (double)(1LL << t.logF);
+        cost[i] = t.kind == RING_BLUESTEIN ? 4.0 * F * (t.logF + 2) : t.kind == RING_POW2 ? F * t.logF : (double)t.n * t.n / 8;
+        cost[i] += 2.0 * p->lmax / 64.0;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    if ((st = plan_alloc(p, (void **)&p->tab.order, np * sizeof(int))) != WF_OK) return st;
+    WF_CUDA(cudaMemcpy(p->tab.order, order.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+    if ((st = plan_alloc(p, (void **)&p->tab.ticket, 16)) != WF_OK) return st;
     const size_t es = f32 ? sizeof(float2) : sizeof(double2);
-    return plan_alloc(p, &p->ws.scr, (size_t)p->tab.ringGrid * 2 * maxBlue * es + 16);
+    const long long zl = maxBlue > NAIVE_MAX ? maxBlue : NAIVE_MAX;
+    return plan_alloc(p, &p->ws.scr, (size_t)p->tab.ringGrid * 2 * zl * es + 16);
 }
 
 wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *out_map)
