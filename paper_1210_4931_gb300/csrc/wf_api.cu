@@ -954,6 +954,11 @@ wf_status hp_create(wf_plan p)
             stp[pr] = std::sqrt((1.0 - z) * (1.0 + z));
         }
     }
+    if (p->prec != WF_PREC_FP64) {
+        WF_CUDA(cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking));
+        WF_CUDA(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
+        WF_CUDA(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
+    }
     wf_status st;
     if ((st = hp_build_legendre_tables(p, xp, stp)) != WF_OK) return st;
     if ((st = hp_build_ring_tables(p)) != WF_OK) return st;
@@ -1055,8 +1060,12 @@ void wf_plan_destroy(wf_plan p)
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
+    if (p->aux) cudaStreamSynchronize(p->aux);
     if (p->flat) flat_destroy(p);
     if (p->sub) wf_plan_destroy(p->sub);
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->join_ev) cudaEventDestroy(p->join_ev);
     if (p->events_ready)
         for (auto &e : p->ev) cudaEventDestroy(e);
     for (void *a : p->allocations) cudaFree(a);

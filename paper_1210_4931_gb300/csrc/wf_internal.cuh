@@ -137,6 +137,8 @@ struct wf_plan_s {
     cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
     wf_plan sub = nullptr;    // mixed precision: FP64 plan of the same geometry for the correction sweeps
     bool events_ready = false;
+    cudaStream_t aux = nullptr;      // mixed precision: stream of the FP64 low-l block
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     long long kcnt[WF_NK] = {};  // kernels launched on this plan, by family (WF_K_*)
     int kfam = WF_K_OTHER;       // family the next launches are counted under
 };

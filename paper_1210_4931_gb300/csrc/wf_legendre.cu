@@ -17,7 +17,8 @@
 // Two precisions:
 //   FP64     k_legsyn<double>, k_legana<double,...>: one ring pair per thread.
 //   mixed    k_legsyn_mx, k_legana_mx: FP32 recurrence and contraction, four
-//            ring pairs per thread in two packed f32x2 lanes (__ffma2_rn).
+//            (synthesis) or eight (analysis) ring pairs per thread in packed
+//            f32x2 lanes (__ffma2_rn).
 //            Near the poles the plain recurrence mu_l = A x mu_{l-1} - mu_{l-2}
 //            loses ~1/sin(theta) digits (its two characteristic roots merge
 //            at x = 1), so rings with x > 0.4 run the same recurrence in
@@ -41,7 +42,7 @@ namespace {
 
 constexpr double SEED_LOG2_THRESHOLD = -80.0;
 constexpr int MXP = 4;               // ring pairs per thread in the mixed synthesis
-constexpr int MXPA = 4;              // ring pairs per lane in the mixed analysis
+constexpr int MXPA = 8;              // ring pairs per lane in the mixed analysis
 constexpr float X_DIFFERENCE_FORM = 0.4f;
 constexpr int BIG = INT_MAX / 2;
 
@@ -248,6 +249,7 @@ __device__ __forceinline__ void warp_reduce_scatter(T (&vr)[CH], T (&vi)[CH], in
 }
 
 template <int CH> struct Log2;
+template <> struct Log2<8> { static constexpr int v = 3; };
 template <> struct Log2<16> { static constexpr int v = 4; };
 template <> struct Log2<32> { static constexpr int v = 5; };
 
@@ -351,7 +353,7 @@ __device__ __forceinline__ void blend_epilogue(int lmax, int L, int m, long long
 // TF is the storage type of F (FP64 plans: double; FP64 block of the mixed
 // path: float).
 // ---------------------------------------------------------------------------
-template <typename T, typename TF, int CH>
+template <typename T, typename TF, int CH, bool SPLIT>
 __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npairs, int lcut,
                                                         const cx<TF> *__restrict__ F, const T *__restrict__ A,
                                                         const int *__restrict__ ls_tab, const T *__restrict__ s0_tab,
@@ -377,7 +379,11 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int ngroups = (npairs + 31) / 32;
-    for (int grp = warp; grp < ngroups; grp += nwarps) {
+    // SPLIT: the ring pairs of one m are shared by gridDim.y CTAs
+    const int gpc = SPLIT ? (ngroups + gridDim.y - 1) / gridDim.y : ngroups;
+    const int g0 = SPLIT ? blockIdx.y * gpc : 0;
+    const int g1 = min(ngroups, g0 + gpc);
+    for (int grp = g0 + warp; grp < g1; grp += nwarps) {
         const int p = grp * 32 + lane;
         const size_t sidx = (size_t)m * npairs + p;
         int ls = (p < npairs) ? ls_tab[sidx] : BIG;
@@ -423,6 +429,14 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
         }
     }
     __syncthreads();
+    if (SPLIT) {  // adjoint only: add this CTA's share into the (zeroed) output
+        for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+            const double cc = c64[base + j];
+            atomicAdd(&out[base + j].x, cc * acc[j].x);
+            atomicAdd(&out[base + j].y, cc * acc[j].y);
+        }
+        return;
+    }
     blend_epilogue(lmax, Lm, m, base, mode, omega, ba, c64, acc, nullptr, 0, a_old, out, part, red);
 }
 
@@ -636,10 +650,12 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
     }
 }
 
-// analysis: CTA per m; a warp covers 32 lanes x 4 pairs; chunks of 16 values
-// of l accumulate both packs in f32x2 registers, then are summed over the
-// pack lanes and reduced across the warp.
-constexpr int MX_CH = 16;
+// analysis: CTA per m; a warp covers 32 lanes x MXPA pairs; chunks of MX_CH
+// values of l accumulate the packs in f32x2 registers, then are summed over
+// the pack lanes and reduced across the warp.  Eight pairs per lane halve the
+// cross-lane reduction per (l, m, pair) against four; two CTAs per SM (128
+// registers) measured faster than one CTA with no spills.
+constexpr int MX_CH = 8;
 
 template <bool DIFF>
 __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L, int lmin_w,
@@ -680,8 +696,9 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L,
             vi[i] = AI[i].x + AI[i].y;
         }
         warp_reduce_scatter<float, MX_CH>(vr, vi, lane);
-        if ((lane & 1) == 0) {
-            const int l = l0 + (lane >> 1);
+        constexpr int sh = 5 - Log2<MX_CH>::v;  // each l ends in 2^sh lanes
+        if ((lane & ((1 << sh) - 1)) == 0) {
+            const int l = l0 + (lane >> sh);
             if (l <= L) {
                 atomicAdd(&acc[l - m].x, vr[0]);
                 atomicAdd(&acc[l - m].y, vi[0]);
@@ -690,7 +707,7 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L,
     }
 }
 
-__global__ void __launch_bounds__(LEG_THREADS) k_legana_mx(int lmax, int L, int npairs, int lc,
+__global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, int npairs, int lc,
                                                            const float2 *__restrict__ F, const float *__restrict__ A,
                                                            const float *__restrict__ B,
                                                            const int *__restrict__ ls_tab,
@@ -779,7 +796,7 @@ size_t ana_smem(int L) { return (size_t)(L + 1 + CH + 2) * (sizeof(double2) + si
 size_t syn_mx_smem(int L) { return (size_t)((L + 2) / 2 + 2) * 2 * sizeof(float4) + 16; }
 size_t ana_mx_smem(int L) { return (size_t)(L + 1 + MX_CH + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32; }
 
-wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *G, int gstride)
+wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *G, int gstride, cudaStream_t s)
 {
     const HpTables &t = p->tab;
     const int Lgrid = lcut > 0 ? std::min(L, lcut - 1) : L;
@@ -788,7 +805,7 @@ wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *
     dim3 grid(gx, Lgrid + 1);
     const size_t sm = syn_smem<double>(lcut > 0 ? std::min(L, lcut + 1) : L);
     if (wf_status st = raise_smem_limit((const void *)k_legsyn<double>, sm)) return st;
-    k_legsyn<double><<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, lcut, alm, t.A64, t.c64, t.ls,
+    k_legsyn<double><<<grid, LEG_THREADS, sm, s>>>(p->lmax, L, p->npairs, lcut, alm, t.A64, t.c64, t.ls,
                                                             t.s0_64, t.s1_64, t.x64, G, gstride);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
@@ -797,17 +814,39 @@ wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *
 
 template <typename TF>
 wf_status launch_ana64(wf_plan p, int L, int lcut, const void *F, LegMode mode, const BlendArgs &ba,
-                       const double2 *a_old, double2 *out)
+                       const double2 *a_old, double2 *out, cudaStream_t s)
 {
     constexpr int CH = 16;
     const HpTables &t = p->tab;
     const int Lgrid = lcut > 0 ? std::min(L, lcut - 1) : L;
     if (Lgrid < 0) return WF_OK;
     const size_t sm = ana_smem<double, CH>(lcut > 0 ? std::min(L, lcut + 1) : L);
-    if (wf_status st = raise_smem_limit((const void *)k_legana<double, TF, CH>, sm)) return st;
-    k_legana<double, TF, CH><<<Lgrid + 1, LEG_THREADS, sm, p->stream>>>(
+    if (wf_status st = raise_smem_limit((const void *)k_legana<double, TF, CH, false>, sm)) return st;
+    k_legana<double, TF, CH, false><<<Lgrid + 1, LEG_THREADS, sm, s>>>(
         p->lmax, L, p->npairs, lcut, (const cx<TF> *)F, t.A64, t.ls, t.s0_64, t.s1_64, t.x64, t.c64, (int)mode,
         p->omega, ba, a_old, out, p->ws.part_harm);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+// FP64 block of the mixed analysis (adjoint, l < lcm(lcut, m)): the block is
+// triangular in m, so one CTA per m would leave m = 0 as the critical path;
+// each m is split over ring-pair chunks whose shares are added atomically.
+wf_status launch_ana64_low(wf_plan p, int L, int lcut, const float2 *F, double2 *out, cudaStream_t s)
+{
+    constexpr int CH = 16;
+    const HpTables &t = p->tab;
+    const int nm = std::min(L, lcut - 1) + 1;
+    if (nm <= 0) return WF_OK;
+    WF_CUDA(cudaMemsetAsync(out, 0, (size_t)mbase(p->lmax, nm) * sizeof(double2), s));
+    const size_t sm = ana_smem<double, CH>(std::min(L, lcut + 1));
+    if (wf_status st = raise_smem_limit((const void *)k_legana<double, float, CH, true>, sm)) return st;
+    const int nchunk = std::max(1, std::min(16, p->npairs / 512));
+    BlendArgs none;
+    k_legana<double, float, CH, true><<<dim3(nm, nchunk), LEG_THREADS, sm, s>>>(
+        p->lmax, L, p->npairs, lcut, F, t.A64, t.ls, t.s0_64, t.s1_64, t.x64, t.c64, (int)LEG_ADJOINT, p->omega, none,
+        nullptr, out, nullptr);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
@@ -930,21 +969,60 @@ wf_status hp_set_low_block(wf_plan p, int lc)
     return WF_OK;
 }
 
+// Mixed precision: the FP64 low-l block (FP64 pipe, few CTAs) runs on the
+// plan's auxiliary stream next to the FP32 kernels (FMA pipes); the two write
+// disjoint buffers and are joined before their results are combined.
+wf_status fork_aux(wf_plan p)
+{
+    WF_CUDA(cudaEventRecord(p->fork_ev, p->stream));
+    WF_CUDA(cudaStreamWaitEvent(p->aux, p->fork_ev, 0));
+    return WF_OK;
+}
+
+wf_status join_aux(wf_plan p)
+{
+    WF_CUDA(cudaEventRecord(p->join_ev, p->aux));
+    WF_CUDA(cudaStreamWaitEvent(p->stream, p->join_ev, 0));
+    return WF_OK;
+}
+
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
 {
     const HpTables &t = p->tab;
-    if (p->prec == WF_PREC_FP64) return launch_syn64(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1);
+    if (p->prec == WF_PREC_FP64) return launch_syn64(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1, p->stream);
+    wf_status st;
+    const bool low = t.lc_mx > 0;
+    if (low) {
+        if ((st = fork_aux(p)) != WF_OK) return st;
+        if ((st = launch_syn64(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux)) != WF_OK) return st;
+    }
     const int gx = (p->npairs + MXP * LEG_THREADS - 1) / (MXP * LEG_THREADS);
     dim3 grid(gx, L + 1);
     const size_t sm = syn_mx_smem(L);
-    if (wf_status st = raise_smem_limit((const void *)k_legsyn_mx, sm)) return st;
+    if ((st = raise_smem_limit((const void *)k_legsyn_mx, sm)) != WF_OK) return st;
     k_legsyn_mx<<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, t.A32, t.B32, t.c64, t.ls_mx,
                                                        t.s0_mx, t.s1_mx, t.x32, t.w32, (float2 *)p->ws.G);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
-    if (t.lc_mx > 0) return launch_syn64(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap);
+    if (low) return join_aux(p);
     return WF_OK;
 }
+
+namespace {
+wf_status launch_ana_mx(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *low, const double2 *a_old,
+                        double2 *out)
+{
+    const HpTables &t = p->tab;
+    const size_t sm = ana_mx_smem(L);
+    if (wf_status st = raise_smem_limit((const void *)k_legana_mx, sm)) return st;
+    k_legana_mx<<<L + 1, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, t.lc_mx, (const float2 *)p->ws.F,
+                                                        t.A32, t.B32, t.ls_mx, t.s0_mx, t.s1_mx, t.x32, t.w32, t.c64,
+                                                        (int)mode, p->omega, ba, low, a_old, out, p->ws.part_harm);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+}  // namespace
 
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba_in, const double2 *a_old,
                                double2 *out)
@@ -958,22 +1036,13 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
         WF_CUDA(cudaGetLastError());
         ba.epi = p->ws.epi;
     }
-    if (p->prec == WF_PREC_FP64) return launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out);
-    const double2 *low = nullptr;
-    if (t.lc_mx > 0) {
-        BlendArgs none;
-        wf_status st = launch_ana64<float>(p, L, t.lc_mx, p->ws.F, LEG_ADJOINT, none, nullptr, p->ws.b_low);
-        if (st != WF_OK) return st;
-        low = p->ws.b_low;
-    }
-    const size_t sm = ana_mx_smem(L);
-    if (wf_status st = raise_smem_limit((const void *)k_legana_mx, sm)) return st;
-    k_legana_mx<<<L + 1, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, t.lc_mx, (const float2 *)p->ws.F,
-                                                        t.A32, t.B32, t.ls_mx, t.s0_mx, t.s1_mx, t.x32, t.w32, t.c64,
-                                                        (int)mode, p->omega, ba, low, a_old, out, p->ws.part_harm);
-    WF_COUNT_LAUNCH(p);
-    WF_CUDA(cudaGetLastError());
-    return WF_OK;
+    if (p->prec == WF_PREC_FP64) return launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out, p->stream);
+    const int lc = t.lc_mx;
+    if (lc <= 0) return launch_ana_mx(p, L, mode, ba, nullptr, a_old, out);
+    // sequential: the FP64 block measured slower running beside the FP32 kernel
+    wf_status st = launch_ana64_low(p, L, lc, (const float2 *)p->ws.F, p->ws.b_low, p->stream);
+    if (st != WF_OK) return st;
+    return launch_ana_mx(p, L, mode, ba, p->ws.b_low, a_old, out);
 }
 
 }  // namespace wf
