@@ -188,8 +188,19 @@ wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mas
 /* Sizes of the plan's arrays. */
 long long wf_npix(wf_plan p);
 long long wf_nalm(wf_plan p); /* complex entries */
-/* Device bytes the plan holds (tables + workspace). */
+/* Device bytes the plan holds (tables + workspace, including the FP64
+ * sub-plan of the correction sweeps once created). */
 long long wf_plan_device_bytes(wf_plan p);
+/* Device bytes a plan of this geometry will hold, computed without creating
+ * it (upper estimate; with_host_staging adds the buffers of the *_host entry
+ * points).  -1 for an invalid geometry. */
+long long wf_plan_estimate_bytes(const wf_geometry *g, int lmax, wf_precision prec, int with_host_staging);
+/* Move the plan to another CUDA stream (waits for work queued on the old one). */
+wf_status wf_plan_set_stream(wf_plan p, void *cuda_stream);
+/* wf_fluct with HOST buffers (copies in, solves, copies the map out). */
+wf_status wf_fluct_host(wf_plan p, const double *noise_var, const uint8_t *mask, const double *C_ell,
+                        const double *g1, const double *g2, double tol, double *f_out, double *alm_out,
+                        wf_info *info);
 
 const char *wf_strerror(wf_status s);
 const char *wf_last_error(void);
@@ -210,6 +221,83 @@ const char *wf_last_error(void);
 wf_status wf_flat_solve_noalloc(int n, const double *d, const double *noise_var, const uint8_t *mask,
                                 const double *S, double tol, const wf_options *opt, void *cuda_stream,
                                 double *s_wf, double *alm_out, wf_info *info);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop over many HEALPix solves of mixed size.
+ *
+ * The paper solves one map at a time; this engine runs many Wiener-filter
+ * (Sect. 2.1), fluctuation (Eq. 9) and constrained-realization (Sect. 2.3:
+ * s_WF + f) requests concurrently on one GPU.  Requests carry HOST buffers
+ * and wait in a FIFO queue.  Each of `slots` worker threads owns a CUDA
+ * stream and takes the next request that can be admitted:
+ *   - a plan (tables + workspace) of the request's (nside, lmax, precision) is
+ *     taken from the pool of idle plans, or created if the plans' device bytes
+ *     stay within `mem_budget` after it (estimate from wf_plan_estimate_bytes),
+ *     evicting least recently used idle plans for the queue head if needed;
+ *   - the head of the queue has priority; a request behind it is admitted
+ *     before it only into memory that is free without evicting anything.
+ * Plans stay resident between requests, so a geometry's Legendre tables are
+ * built once; the solves of different slots run on different streams and
+ * overlap on the device.  Every result is that of the corresponding direct
+ * call (wf_solve_host / wf_fluct_host) on a plan of the same geometry. */
+typedef struct wf_server_s *wf_server;
+
+typedef enum { WF_REQ_WF = 0, WF_REQ_FLUCT = 1, WF_REQ_CR = 2 } wf_request_kind;
+
+typedef struct {
+    unsigned long long tag;   /* caller's identifier, returned in the result */
+    int kind;                 /* wf_request_kind */
+    int nside, lmax;          /* HEALPix geometry, 2 <= lmax <= 2 nside */
+    wf_precision precision;
+    double tol;
+    wf_options opt;           /* per-request options (zero-filled: defaults) */
+    /* host buffers, owned by the caller, valid until the result is returned */
+    const double *d;          /* WF, CR: npix */
+    const double *noise_var;  /* npix */
+    const uint8_t *mask;      /* npix or NULL */
+    const double *C_ell;      /* lmax + 1 */
+    const double *g1, *g2;    /* FLUCT, CR: npix real and n_alm complex draws of Eq. (9) */
+    double *s_out;            /* npix: s_WF (WF), f (FLUCT), s_WF + f (CR) */
+    double *f_out;            /* CR only, optional: npix, the fluctuation map f */
+} wf_request;
+
+typedef struct {
+    unsigned long long tag;
+    wf_status status;         /* of the solve (WF_ENOCONV: the last iterate is written) */
+    int iters;                /* messenger iterations (CR: both solves) */
+    int converged;
+    double final_residual;
+    double chi2_over_ndof;    /* WF and CR */
+    double t_submit, t_start, t_done;  /* seconds since wf_server_create */
+    int slot;                 /* worker that ran it */
+    int plan_reused;          /* 1 if an existing plan served it */
+} wf_result;
+
+typedef struct {
+    long long pending, active, completed, rejected;
+    long long bytes_in_use;   /* device bytes of all pooled plans (busy and idle) */
+    long long peak_bytes;     /* maximum of bytes_in_use */
+    long long budget;
+    int plans, max_active;    /* pooled plans; most solves in flight at once */
+    long long plans_created, plans_evicted;
+} wf_server_stats;
+
+/* device: CUDA device index; mem_budget: bytes of device memory for plans;
+ * slots: concurrent solves (1..64). */
+wf_status wf_server_create(int device, long long mem_budget, int slots, wf_server *out);
+/* Queue a request (the struct is copied; the arrays are not).  A request that
+ * can never fit the budget, or is invalid, completes at once with an error
+ * status in its result. */
+wf_status wf_server_submit(wf_server s, const wf_request *req);
+/* Completed results, oldest first: up to cap are moved to out.  poll returns
+ * at once; wait blocks until at least one is available or timeout_s passes.
+ * Return value: the number written. */
+int wf_server_poll(wf_server s, wf_result *out, int cap);
+int wf_server_wait(wf_server s, wf_result *out, int cap, double timeout_s);
+wf_status wf_server_get_stats(wf_server s, wf_server_stats *st);
+/* Stops the workers after the solves in flight; queued requests are dropped
+ * (their buffers are no longer touched).  Destroys the pooled plans. */
+void wf_server_destroy(wf_server s);
 
 #ifdef __cplusplus
 }

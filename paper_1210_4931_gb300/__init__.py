@@ -55,11 +55,39 @@ class wf_info(ctypes.Structure):
 
 KERNEL_FAMILIES = ["leg_syn", "ring_syn", "ring_ana", "leg_ana", "other", "flat"]
 
+WF_REQ_WF, WF_REQ_FLUCT, WF_REQ_CR = 0, 1, 2
+REQUEST_KINDS = {"wf": WF_REQ_WF, "fluct": WF_REQ_FLUCT, "cr": WF_REQ_CR}
+
+
+class wf_request(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_ulonglong), ("kind", ctypes.c_int), ("nside", ctypes.c_int), ("lmax", ctypes.c_int),
+                ("precision", ctypes.c_int), ("tol", ctypes.c_double), ("opt", wf_options),
+                ("d", ctypes.c_void_p), ("noise_var", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("C_ell", ctypes.c_void_p), ("g1", ctypes.c_void_p), ("g2", ctypes.c_void_p),
+                ("s_out", ctypes.c_void_p), ("f_out", ctypes.c_void_p)]
+
+
+class wf_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_ulonglong), ("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("converged", ctypes.c_int), ("final_residual", ctypes.c_double),
+                ("chi2_over_ndof", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("slot", ctypes.c_int), ("plan_reused", ctypes.c_int)]
+
+
+class wf_server_stats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_longlong), ("active", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("rejected", ctypes.c_longlong), ("bytes_in_use", ctypes.c_longlong),
+                ("peak_bytes", ctypes.c_longlong), ("budget", ctypes.c_longlong), ("plans", ctypes.c_int),
+                ("max_active", ctypes.c_int), ("plans_created", ctypes.c_longlong),
+                ("plans_evicted", ctypes.c_longlong)]
+
 
 _lib = None
 EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host",
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
-           "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates"]
+           "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
+           "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
+           "wf_server_wait", "wf_server_get_stats", "wf_server_destroy"]
 
 
 def load(path: str = LIB_PATH):
@@ -90,6 +118,24 @@ def load(path: str = LIB_PATH):
     L.wf_flat_solve_noalloc.restype = ctypes.c_int
     L.wf_remove_templates.argtypes = [vp, dp, u8p, dp, ctypes.POINTER(ctypes.c_double)]
     L.wf_remove_templates.restype = ctypes.c_int
+    L.wf_fluct_host.argtypes = [vp, dp, u8p, dp, dp, dp, ctypes.c_double, dp, dp, ctypes.POINTER(wf_info)]
+    L.wf_fluct_host.restype = ctypes.c_int
+    L.wf_plan_estimate_bytes.argtypes = [ctypes.POINTER(wf_geometry), ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.wf_plan_estimate_bytes.restype = ctypes.c_longlong
+    L.wf_plan_set_stream.argtypes = [vp, vp]
+    L.wf_plan_set_stream.restype = ctypes.c_int
+    L.wf_server_create.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(vp)]
+    L.wf_server_create.restype = ctypes.c_int
+    L.wf_server_submit.argtypes = [vp, ctypes.POINTER(wf_request)]
+    L.wf_server_submit.restype = ctypes.c_int
+    L.wf_server_poll.argtypes = [vp, ctypes.POINTER(wf_result), ctypes.c_int]
+    L.wf_server_poll.restype = ctypes.c_int
+    L.wf_server_wait.argtypes = [vp, ctypes.POINTER(wf_result), ctypes.c_int, ctypes.c_double]
+    L.wf_server_wait.restype = ctypes.c_int
+    L.wf_server_get_stats.argtypes = [vp, ctypes.POINTER(wf_server_stats)]
+    L.wf_server_get_stats.restype = ctypes.c_int
+    L.wf_server_destroy.argtypes = [vp]
+    L.wf_server_destroy.restype = None
     L.wf_strerror.argtypes = [ctypes.c_int]
     L.wf_strerror.restype = ctypes.c_char_p
     L.wf_last_error.argtypes = []
@@ -292,6 +338,107 @@ def wf_flat_solve_noalloc(n, d, noise_var, mask, S, tol, s_wf, alm_out=None, tra
     return _info_dict(st, info, bufs)
 
 
+def wf_fluct_host(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_out=None, trace_cap=0) -> dict:
+    """wf_fluct with numpy (host) arrays; copies are made inside the call."""
+    info, bufs = _info(trace_cap)
+
+    def hp(a, dt):
+        if a is None:
+            return None
+        assert a.dtype == dt and a.flags.c_contiguous
+        return ctypes.c_void_p(a.ctypes.data)
+
+    st = load().wf_fluct_host(plan.handle, hp(noise_var, np.float64), hp(mask, np.uint8), hp(C_ell, np.float64),
+                              hp(g1, np.float64), hp(g2, np.complex128), float(tol), hp(f_out, np.float64),
+                              hp(alm_out, np.complex128), ctypes.byref(info))
+    _check(st, "wf_fluct_host", allow=(WF_ENOCONV,))
+    return _info_dict(st, info, bufs)
+
+
+def wf_plan_estimate_bytes(kind: str, *, nside: int = 0, lmax: int = 0, n: int = 0, precision: str = "fp64",
+                           host_staging: bool = True) -> int:
+    g = wf_geometry()
+    if kind == "healpix":
+        g.kind, g.nside, g.ncomp = WF_GEOM_HEALPIX, nside, 1
+    else:
+        g.kind, g.nx, g.ny, g.ncomp = WF_GEOM_FLAT, n, n, 1
+    return int(load().wf_plan_estimate_bytes(ctypes.byref(g), int(lmax), PRECISIONS[precision], int(host_staging)))
+
+
+class Server:
+    """The request loop of include/wf.h (wf_server_*): host numpy buffers in,
+    results with timings out.  Buffers are held here until their result has
+    been collected."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 8 << 30, slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(load().wf_server_create(int(device), int(mem_budget), int(slots), ctypes.byref(h)), "wf_server_create")
+        self.handle = h
+        self._held = {}
+        self._next = 1
+
+    def submit(self, kind: str, *, nside: int, lmax: int, noise_var, C_ell, s_out, d=None, mask=None, g1=None,
+               g2=None, f_out=None, precision: str = "mixed", tol: float = 1e-6, tag=None, **options) -> int:
+        def hp(a, dt):
+            if a is None:
+                return None
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise TypeError("request buffers must be C-contiguous %s arrays" % np.dtype(dt).name)
+            return a.ctypes.data
+
+        r = wf_request()
+        if tag is None:
+            tag = self._next
+            self._next += 1
+        r.tag, r.kind, r.nside, r.lmax = int(tag), REQUEST_KINDS[kind], int(nside), int(lmax)
+        r.precision, r.tol = PRECISIONS[precision], float(tol)
+        for k, v in options.items():
+            setattr(r.opt, k, v)
+        r.d, r.noise_var, r.mask = hp(d, np.float64), hp(noise_var, np.float64), hp(mask, np.uint8)
+        r.C_ell, r.g1, r.g2 = hp(C_ell, np.float64), hp(g1, np.float64), hp(g2, np.complex128)
+        r.s_out, r.f_out = hp(s_out, np.float64), hp(f_out, np.float64)
+        self._held[int(tag)] = (d, noise_var, mask, C_ell, g1, g2, s_out, f_out)
+        _check(load().wf_server_submit(self.handle, ctypes.byref(r)), "wf_server_submit")
+        return int(tag)
+
+    def _collect(self, arr, n):
+        out = []
+        for i in range(n):
+            x = arr[i]
+            self._held.pop(int(x.tag), None)
+            out.append({"tag": int(x.tag), "status": int(x.status), "iters": int(x.iters),
+                        "converged": bool(x.converged), "final_residual": float(x.final_residual),
+                        "chi2_over_ndof": float(x.chi2_over_ndof), "t_submit": float(x.t_submit),
+                        "t_start": float(x.t_start), "t_done": float(x.t_done), "slot": int(x.slot),
+                        "plan_reused": bool(x.plan_reused)})
+        return out
+
+    def poll(self, cap: int = 256) -> list:
+        arr = (wf_result * cap)()
+        return self._collect(arr, load().wf_server_poll(self.handle, arr, cap))
+
+    def wait(self, cap: int = 256, timeout: float = 1.0) -> list:
+        arr = (wf_result * cap)()
+        return self._collect(arr, load().wf_server_wait(self.handle, arr, cap, float(timeout)))
+
+    def stats(self) -> dict:
+        s = wf_server_stats()
+        _check(load().wf_server_get_stats(self.handle, ctypes.byref(s)), "wf_server_get_stats")
+        return {f: int(getattr(s, f)) for f, _ in s._fields_}
+
+    def close(self):
+        if self.handle:
+            load().wf_server_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def wf_remove_templates(plan: Plan, d_raw, mask, d_out):
     """Monopole/dipole marginalisation of Eq. (12); returns the 4 removed
     template amplitudes (monopole, dipole x, y, z)."""
@@ -312,6 +459,6 @@ def wf_map2alm_adjoint(plan: Plan, map_in, L, alm_out):
                                      _ptr(alm_out, None, plan.nalm * 16, "alm")), "wf_map2alm_adjoint")
 
 
-__all__ = ["Plan", "WfError", "load", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
+__all__ = ["Plan", "Server", "WfError", "load", "wf_fluct_host", "wf_plan_estimate_bytes", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
            "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "EXPORTS",
            "LIB_PATH"]

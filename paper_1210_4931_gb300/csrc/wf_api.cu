@@ -56,6 +56,19 @@ wf_status raise_smem_limit(const void *func, size_t bytes)
     return WF_OK;
 }
 
+wf_status to_device(wf_plan p, void *dst, const void *src, size_t bytes)
+{
+    WF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, p->stream));
+    return WF_OK;
+}
+
+wf_status to_host(wf_plan p, void *dst, const void *src, size_t bytes)
+{
+    WF_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    return WF_OK;
+}
+
 wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes)
 {
     void *d = nullptr;
@@ -646,7 +659,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     const double tau_h = tau * p->omega;
     HpSchedule sch;
     sch.c.resize(lmax + 1);
-    WF_CUDA(cudaMemcpy(sch.c.data(), C_ell, (lmax + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    if ((st = to_host(p, sch.c.data(), C_ell, (lmax + 1) * sizeof(double))) != WF_OK) return st;
     // Mixed precision: the messenger iteration contracts a mode by about
     // tau_h / S_l per iteration where the mask leaves it unconstrained, so a
     // systematic operator error larger than that margin makes the iteration
@@ -985,6 +998,47 @@ wf_status hp_create(wf_plan p)
 
 }  // namespace
 
+// Device bytes a HEALPix plan allocates (tables, workspace, host-API staging),
+// mirroring hp_create and the table builders; the mixed path's FP64-block
+// buffer is counted for l_c = (lmax + 1) / 8 (it grows with l_c on demand).
+long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging)
+{
+    const bool f32 = prec != WF_PREC_FP64;
+    const long long np = 2LL * nside, npix = 12LL * nside * nside;
+    const long long nalm = (long long)(lmax + 1) * (lmax + 2) / 2, ns = (long long)(lmax + 1) * np;
+    const long long es = f32 ? 4 : 8, ec = 2 * es;
+    long long b = 0;
+    b += nalm * 16 + np * 16 + (lmax + 1) * 8 + ns * (4 + 16);  // A64, c64, x, st, log2 c, seeds
+    if (f32) b += nalm * 8 + np * 8 + ns * 12;                   // A32, B32, x32, w32, FP32 seeds
+    // ring tables: roots per distinct length, Bluestein filters, twiddles, scratch
+    long long roots = 0, V = 0, nmaxF = 2, maxBlue = 1;
+    for (int k = 1; k <= nside; ++k) {
+        const long long n = 4LL * k;
+        roots += 2 * n;
+        if (n <= 32) continue;
+        if ((n & (n - 1)) == 0) {
+            nmaxF = std::max(nmaxF, n);
+        } else {
+            long long M = 1;
+            while (M < 2 * n - 1) M <<= 1;
+            V += M;
+            nmaxF = std::max(nmaxF, M);
+            maxBlue = std::max(maxBlue, n);
+        }
+    }
+    const long long zl = std::max(maxBlue, 32LL);
+    b += (roots + V + nmaxF) * ec + np * (48 + 4) + 64;
+    b += std::min<long long>(np, 8LL * 152) * 2 * zl * ec;
+    // workspace
+    b += nalm * 16 * (f32 ? 4 : 3);                              // a, a_new, b (+ b_low)
+    b += 2 * np * (lmax + 1) * 2 * ec;                           // G, F
+    b += 3 * npix * es;                                          // r, nu, t
+    b += std::max(np, 1024LL) * 8 + 4LL * (lmax + 2) * 8 + (lmax + 1) * 32 + 256;
+    if (f32) b += np * ((lmax + 1) / 8 + 1) * 2 * 16;            // FP64-block coefficients
+    if (staging) b += npix * (3 * 8 + 1) + (lmax + 1) * 8 + nalm * 16 * 2 + npix * 8;
+    return b + (1LL << 20);
+}
+
 }  // namespace wf
 
 using namespace wf;
@@ -1095,7 +1149,32 @@ wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n)
 
 long long wf_npix(wf_plan p) { return p ? p->npix : 0; }
 long long wf_nalm(wf_plan p) { return p ? p->nalm : 0; }
-long long wf_plan_device_bytes(wf_plan p) { return p ? p->device_bytes : 0; }
+long long wf_plan_device_bytes(wf_plan p)
+{
+    if (!p) return 0;
+    return p->device_bytes + (p->sub ? wf_plan_device_bytes(p->sub) : 0);
+}
+
+long long wf_plan_estimate_bytes(const wf_geometry *g, int lmax, wf_precision prec, int with_host_staging)
+{
+    if (!g) return -1;
+    if (g->kind == WF_GEOM_FLAT) return 8LL << 20;  // n <= 128: a few hundred KB of maps and traces
+    if (g->kind != WF_GEOM_HEALPIX || g->nside < 1 || lmax < 2 || lmax > 2 * g->nside) return -1;
+    return wf::hp_estimate_bytes(g->nside, lmax, prec, with_host_staging != 0);
+}
+
+wf_status wf_plan_set_stream(wf_plan p, void *cuda_stream)
+{
+    if (!p) return set_error(WF_EINVAL, "null plan");
+    if (p->stream != (cudaStream_t)cuda_stream) {
+        // work queued on the old stream finishes before the new one is used
+        if (p->stream) WF_CUDA(cudaStreamSynchronize(p->stream));
+        else WF_CUDA(cudaDeviceSynchronize());
+    }
+    p->stream = (cudaStream_t)cuda_stream;
+    if (p->sub) return wf_plan_set_stream(p->sub, cuda_stream);
+    return WF_OK;
+}
 
 wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask, const double *C_ell,
                    double tol, double *s_wf, double *alm_out, wf_info *info)
@@ -1123,6 +1202,28 @@ wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, cons
     return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
 }
 
+}  // extern "C"
+
+namespace wf {
+// device staging of the host-buffer entry points (allocated on first use)
+wf_status host_staging(wf_plan p)
+{
+    if (p->ws.d_in) return WF_OK;
+    const size_t npx = (size_t)p->npix;
+    const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
+    const size_t nh = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) * 2 : (size_t)p->nalm * 2;
+    wf_status st;
+    if ((st = plan_alloc(p, (void **)&p->ws.d_in, npx * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.nv_in, npx * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.mask_in, npx)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.out_map, npx * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.cl_in, nS * 8)) != WF_OK) return st;
+    return plan_alloc(p, (void **)&p->ws.alm_io, nh * 8);
+}
+}  // namespace wf
+
+extern "C" {
+
 wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask, const double *C_ell,
                         double tol, double *s_wf, double *alm_out, wf_info *info)
 {
@@ -1131,14 +1232,7 @@ wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, con
     const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
     const size_t nh = (size_t)p->nalm * 2;
     wf_status st;
-    if (!p->ws.d_in) {
-        if ((st = plan_alloc(p, (void **)&p->ws.d_in, npx * 8)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.nv_in, npx * 8)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.mask_in, npx)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.out_map, npx * 8)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.cl_in, nS * 8)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.alm_io, nh * 8)) != WF_OK) return st;
-    }
+    if ((st = host_staging(p)) != WF_OK) return st;
     cudaStream_t s = p->stream;
     WF_CUDA(cudaMemcpyAsync(p->ws.d_in, d, npx * 8, cudaMemcpyHostToDevice, s));
     WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, npx * 8, cudaMemcpyHostToDevice, s));
@@ -1148,6 +1242,34 @@ wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, con
                   alm_out ? p->ws.alm_io : nullptr, info);
     if (st != WF_OK && st != WF_ENOCONV) return st;
     WF_CUDA(cudaMemcpyAsync(s_wf, p->ws.out_map, npx * 8, cudaMemcpyDeviceToHost, s));
+    if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nh * 8, cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+wf_status wf_fluct_host(wf_plan p, const double *noise_var, const uint8_t *mask, const double *C_ell, const double *g1,
+                        const double *g2, double tol, double *f_out, double *alm_out, wf_info *info)
+{
+    if (!p || !noise_var || !C_ell || !g1 || !g2 || !f_out) return set_error(WF_EINVAL, "null argument");
+    const size_t npx = (size_t)p->npix;
+    const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
+    const size_t nh = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) * 2 : (size_t)p->nalm * 2;
+    wf_status st;
+    if ((st = host_staging(p)) != WF_OK) return st;
+    if (!p->ws.g1_in) {
+        if ((st = plan_alloc(p, (void **)&p->ws.g1_in, npx * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.g2_in, nh * 8)) != WF_OK) return st;
+    }
+    cudaStream_t s = p->stream;
+    WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, npx * 8, cudaMemcpyHostToDevice, s));
+    if (mask) WF_CUDA(cudaMemcpyAsync(p->ws.mask_in, mask, npx, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.cl_in, C_ell, nS * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.g1_in, g1, npx * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.g2_in, g2, nh * 8, cudaMemcpyHostToDevice, s));
+    st = wf_fluct(p, p->ws.nv_in, mask ? p->ws.mask_in : nullptr, p->ws.cl_in, p->ws.g1_in, p->ws.g2_in, tol,
+                  p->ws.out_map, alm_out ? p->ws.alm_io : nullptr, info);
+    if (st != WF_OK && st != WF_ENOCONV) return st;
+    WF_CUDA(cudaMemcpyAsync(f_out, p->ws.out_map, npx * 8, cudaMemcpyDeviceToHost, s));
     if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nh * 8, cudaMemcpyDeviceToHost, s));
     WF_CUDA(cudaStreamSynchronize(s));
     return st;

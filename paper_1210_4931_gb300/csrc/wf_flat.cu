@@ -531,7 +531,8 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
 
     // lambda levels: k_iter = 1, 2, 4, ...; lambda = clip(max S on |k| = k_iter / tau, 1, lambda_max)
     std::vector<double> Sh((size_t)n * nh);
-    WF_CUDA(cudaMemcpy(Sh.data(), S, Sh.size() * 8, cudaMemcpyDeviceToHost));
+    wf_status st = to_host(p, Sh.data(), S, Sh.size() * 8);
+    if (st != WF_OK) return st;
     std::vector<double> lev{o.lambda_max};
     int kmax = 0;
     std::vector<int> kr(Sh.size());
@@ -564,7 +565,7 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
     if (replay)
         WF_CUDA(cudaMemcpyAsync(f->replay, p->replay_lambda.data(), nrep * 8, cudaMemcpyHostToDevice, p->stream));
     const int cap = replay ? nrep : o.maxiter;
-    wf_status st = ensure_trace(p, std::max(cap, 1));
+    st = ensure_trace(p, std::max(cap, 1));
     if (st != WF_OK) return st;
 
     FlatArgs A{};
@@ -617,9 +618,9 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
         const int nt = std::min(fs.iters, info->trace_cap);
         if (nt > 0) {
             std::vector<double> tl(nt), tc(nt), trs(nt);
-            WF_CUDA(cudaMemcpy(tl.data(), f->tr_lam, nt * 8, cudaMemcpyDeviceToHost));
-            WF_CUDA(cudaMemcpy(tc.data(), f->tr_chi2, nt * 8, cudaMemcpyDeviceToHost));
-            WF_CUDA(cudaMemcpy(trs.data(), f->tr_res, nt * 8, cudaMemcpyDeviceToHost));
+            if ((st = to_host(p, tl.data(), f->tr_lam, nt * 8)) != WF_OK) return st;
+            if ((st = to_host(p, tc.data(), f->tr_chi2, nt * 8)) != WF_OK) return st;
+            if ((st = to_host(p, trs.data(), f->tr_res, nt * 8)) != WF_OK) return st;
             for (int i = 0; i < nt; ++i) {
                 if (info->lambda_trace) info->lambda_trace[i] = tl[i];
                 if (info->L_trace) info->L_trace[i] = -1;

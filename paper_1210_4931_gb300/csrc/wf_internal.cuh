@@ -159,6 +159,12 @@ wf_status cuda_check(cudaError_t e, const char *what);
 #define WF_COUNT_LAUNCH(p) (++(p)->kcnt[(p)->kfam])
 // device allocation owned by the plan
 wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes);
+wf_status host_staging(wf_plan p);
+long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging);
+// copies ordered on the plan's stream (no legacy-default-stream copies: the
+// plan may run on a non-blocking stream beside other plans); to_host waits
+wf_status to_device(wf_plan p, void *dst, const void *src, size_t bytes);
+wf_status to_host(wf_plan p, void *dst, const void *src, size_t bytes);
 // raise a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it;
 // serialised, so plans used from several host threads cannot undo each other)
 wf_status raise_smem_limit(const void *func, size_t bytes);

@@ -896,17 +896,17 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
     if ((st = plan_alloc(p, (void **)&t.c64, nalm * sizeof(double))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&t.A64, nalm * sizeof(double))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&t.x64, np * sizeof(double))) != WF_OK) return st;
-    WF_CUDA(cudaMalloc(&dst64, np * sizeof(double)));
-    WF_CUDA(cudaMalloc(&dlog2c, (lmax + 1) * sizeof(double)));
+    if ((st = plan_alloc(p, (void **)&dst64, np * sizeof(double))) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&dlog2c, (lmax + 1) * sizeof(double))) != WF_OK) return st;
     const long long ns = (long long)(lmax + 1) * np;
     if ((st = plan_alloc(p, (void **)&t.ls, ns * sizeof(int))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&t.s0_64, ns * sizeof(double))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&t.s1_64, ns * sizeof(double))) != WF_OK) return st;
-    WF_CUDA(cudaMemcpy(t.A64, A.data(), nalm * sizeof(double), cudaMemcpyHostToDevice));
-    WF_CUDA(cudaMemcpy(t.c64, c.data(), nalm * sizeof(double), cudaMemcpyHostToDevice));
-    WF_CUDA(cudaMemcpy(t.x64, xpair.data(), np * sizeof(double), cudaMemcpyHostToDevice));
-    WF_CUDA(cudaMemcpy(dst64, stpair.data(), np * sizeof(double), cudaMemcpyHostToDevice));
-    WF_CUDA(cudaMemcpy(dlog2c, log2c.data(), (lmax + 1) * sizeof(double), cudaMemcpyHostToDevice));
+    if ((st = to_device(p, t.A64, A.data(), nalm * sizeof(double))) != WF_OK) return st;
+    if ((st = to_device(p, t.c64, c.data(), nalm * sizeof(double))) != WF_OK) return st;
+    if ((st = to_device(p, t.x64, xpair.data(), np * sizeof(double))) != WF_OK) return st;
+    if ((st = to_device(p, dst64, stpair.data(), np * sizeof(double))) != WF_OK) return st;
+    if ((st = to_device(p, dlog2c, log2c.data(), (lmax + 1) * sizeof(double))) != WF_OK) return st;
     {
         const int th = 256;
         const long long nb = (ns + th - 1) / th;
@@ -932,16 +932,14 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
             xf[i] = (float)xpair[i];
             wf[i] = (float)wpair[i];
         }
-        WF_CUDA(cudaMemcpy(t.A32, Af.data(), nalm * sizeof(float), cudaMemcpyHostToDevice));
-        WF_CUDA(cudaMemcpy(t.B32, Bf.data(), nalm * sizeof(float), cudaMemcpyHostToDevice));
-        WF_CUDA(cudaMemcpy(t.x32, xf.data(), np * sizeof(float), cudaMemcpyHostToDevice));
-        WF_CUDA(cudaMemcpy(t.w32, wf.data(), np * sizeof(float), cudaMemcpyHostToDevice));
+        if ((st = to_device(p, t.A32, Af.data(), nalm * sizeof(float))) != WF_OK) return st;
+        if ((st = to_device(p, t.B32, Bf.data(), nalm * sizeof(float))) != WF_OK) return st;
+        if ((st = to_device(p, t.x32, xf.data(), np * sizeof(float))) != WF_OK) return st;
+        if ((st = to_device(p, t.w32, wf.data(), np * sizeof(float))) != WF_OK) return st;
         t.lc_mx = -1;
         if ((st = hp_set_low_block(p, 0)) != WF_OK) return st;
     }
     WF_CUDA(cudaStreamSynchronize(p->stream));
-    cudaFree(dst64);
-    cudaFree(dlog2c);
     return WF_OK;
 }
 

@@ -605,7 +605,7 @@ wf_status upload_cx(wf_plan p, void **dst, const std::vector<double2> &src)
     if (st != WF_OK) return st;
     std::vector<cx<T>> tmp(src.size());
     for (size_t i = 0; i < src.size(); ++i) tmp[i] = mk<T>((T)src[i].x, (T)src[i].y);
-    WF_CUDA(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(cx<T>), cudaMemcpyHostToDevice));
+    if ((st = to_device(p, *dst, tmp.data(), tmp.size() * sizeof(cx<T>))) != WF_OK) return st;
     return WF_OK;
 }
 
@@ -696,7 +696,7 @@ wf_status hp_build_ring_tables(wf_plan p)
     p->tab.maxBlue = maxBlue;
     wf_status st;
     if ((st = plan_alloc(p, (void **)&p->tab.rings, rt.size() * sizeof(RingTab))) != WF_OK) return st;
-    WF_CUDA(cudaMemcpy(p->tab.rings, rt.data(), rt.size() * sizeof(RingTab), cudaMemcpyHostToDevice));
+    if ((st = to_device(p, p->tab.rings, rt.data(), rt.size() * sizeof(RingTab))) != WF_OK) return st;
     const bool f32 = p->prec != WF_PREC_FP64;
     if (f32) {
         if ((st = upload_cx<float>(p, &p->tab.roots, roots)) != WF_OK) return st;
@@ -721,7 +721,7 @@ wf_status hp_build_ring_tables(wf_plan p)
     }
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     if ((st = plan_alloc(p, (void **)&p->tab.order, np * sizeof(int))) != WF_OK) return st;
-    WF_CUDA(cudaMemcpy(p->tab.order, order.data(), np * sizeof(int), cudaMemcpyHostToDevice));
+    if ((st = to_device(p, p->tab.order, order.data(), np * sizeof(int))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&p->tab.ticket, 16)) != WF_OK) return st;
     const size_t es = f32 ? sizeof(float2) : sizeof(double2);
     const long long zl = maxBlue > NAIVE_MAX ? maxBlue : NAIVE_MAX;

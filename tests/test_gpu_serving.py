@@ -1,0 +1,171 @@
+"""Request loop (wf_server_*): many Wiener-filter, fluctuation and
+constrained-realization requests of mixed size, admitted by device memory and
+run concurrently.  Each result must equal the same request run alone through
+the direct host entry points (wf_solve_host / wf_fluct_host) on a fresh plan:
+to 1e-10 relative in FP64 (the analysis sums use atomics, so runs may differ
+in the last bits), and for mixed precision to within the solve tolerance
+(relative map difference below 1e-3 with both residuals below tol)."""
+import numpy as np
+import pytest
+
+import wf_inputs as gen
+from gpu_util import healpix_case, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    import torch
+
+    import paper_1210_4931_gb300 as w
+
+    w.load()
+    torch.cuda.set_device(0)
+    return w
+
+
+CASES = [  # nside, lmax, precision, kind, tol
+    (16, 32, "fp64", "wf", 1e-8),
+    (32, 64, "mixed", "wf", 1e-5),
+    (16, 32, "mixed", "fluct", 1e-5),
+    (32, 64, "fp64", "cr", 1e-7),
+    (64, 128, "mixed", "wf", 1e-5),
+    (16, 32, "fp64", "fluct", 1e-8),
+    (32, 64, "mixed", "cr", 1e-5),
+    (64, 128, "fp64", "wf", 1e-7),
+]
+
+
+def _request(i, nside, lmax, kind):
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(5, i))
+    rng = np.random.default_rng(1000 + i)
+    g1 = rng.standard_normal(d.size)
+    g2 = np.ascontiguousarray(gen.alm_unit_gaussian(rng, lmax), dtype=np.complex128)
+    return dict(d=np.ascontiguousarray(d), noise_var=np.ascontiguousarray(P["noise_var"]),
+                mask=np.ascontiguousarray(P["mask"]), C_ell=np.ascontiguousarray(P["c_ell"]), g1=g1, g2=g2)
+
+
+def _alone(w, nside, lmax, prec, kind, tol, R):
+    plan = w.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+    s = np.empty(R["d"].size)
+    if kind in ("wf", "cr"):
+        rep = w.wf_solve_host(plan, R["d"], R["noise_var"], R["mask"], R["C_ell"], tol, s)
+    if kind in ("fluct", "cr"):
+        f = np.empty(R["d"].size)
+        rep = w.wf_fluct_host(plan, R["noise_var"], R["mask"], R["C_ell"], R["g1"], R["g2"], tol, f)
+        s = f if kind == "fluct" else s + f
+    plan.close()
+    return s, rep
+
+
+def test_results_in_the_mix_equal_results_alone(wf):
+    reqs = [_request(i, n, l, k) for i, (n, l, p, k, t) in enumerate(CASES)]
+    alone = [_alone(wf, n, l, p, k, t, R) for (n, l, p, k, t), R in zip(CASES, reqs)]
+    srv = wf.Server(mem_budget=4 << 30, slots=4)
+    outs = {}
+    for rep_round in range(2):  # twice: the second round reuses the pooled plans
+        for i, ((n, l, p, k, t), R) in enumerate(zip(CASES, reqs)):
+            out = np.full(R["d"].size, np.nan)
+            tag = 100 * rep_round + i
+            outs[tag] = out
+            srv.submit(k, nside=n, lmax=l, precision=p, tol=t, s_out=out, tag=tag,
+                       **{key: R[key] for key in ("d", "noise_var", "mask", "C_ell", "g1", "g2")})
+    results = {}
+    while len(results) < 2 * len(CASES):
+        for r in srv.wait(timeout=60.0):
+            results[r["tag"]] = r
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 2 * len(CASES) and st["rejected"] == 0
+    assert st["plans_created"] <= len({(n, l, p) for n, l, p, k, t in CASES}) * 4
+    for tag, r in results.items():
+        i = tag % 100
+        n, l, p, k, t = CASES[i]
+        assert r["status"] == wf.WF_OK, (tag, r)
+        s_alone, rep = alone[i]
+        if p == "fp64":
+            assert rel(outs[tag], s_alone) < 1e-10, (tag, rel(outs[tag], s_alone))
+        else:
+            assert r["final_residual"] < t and rep["final_residual"] < t
+            assert rel(outs[tag], s_alone) < 1e-3, (tag, rel(outs[tag], s_alone))
+        assert r["t_submit"] <= r["t_start"] <= r["t_done"]
+    assert any(r["plan_reused"] for r in results.values())
+
+
+def test_plan_size_estimate_bounds_the_measured_size(wf):
+    for nside, prec in ((16, "fp64"), (64, "mixed"), (128, "mixed"), (128, "fp64")):
+        lmax = 2 * nside
+        R = _request(50 + nside, nside, lmax, "wf")
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+        s = np.empty(R["d"].size)
+        wf.wf_solve_host(plan, R["d"], R["noise_var"], R["mask"], R["C_ell"], 1e-5, s)
+        f = np.empty(R["d"].size)
+        wf.wf_fluct_host(plan, R["noise_var"], R["mask"], R["C_ell"], R["g1"], R["g2"], 1e-5, f)
+        actual = plan.device_bytes
+        est = wf.wf_plan_estimate_bytes("healpix", nside=nside, lmax=lmax, precision=prec)
+        plan.close()
+        assert actual <= est <= 1.6 * actual + (4 << 20), (nside, prec, actual, est)
+
+
+def test_admission_keeps_the_memory_budget(wf):
+    # two keys of nearly equal size and a budget that holds one plan: every
+    # change of key must evict the idle plan of the other
+    geoms = [(64, 128), (64, 126)] * 3
+    budget = max(wf.wf_plan_estimate_bytes("healpix", nside=n, lmax=l, precision="mixed") for n, l in geoms[:2])
+    budget += 1 << 20
+    srv = wf.Server(mem_budget=budget, slots=3)
+    reqs = [_request(60 + i, n, l, "wf") for i, (n, l) in enumerate(geoms)]
+    outs = []
+    for i, ((n, l), R) in enumerate(zip(geoms, reqs)):
+        out = np.empty(R["d"].size)
+        outs.append(out)
+        srv.submit("wf", nside=n, lmax=l, precision="mixed", tol=1e-4, s_out=out, tag=i, d=R["d"],
+                   noise_var=R["noise_var"], mask=R["mask"], C_ell=R["C_ell"])
+    got = []
+    while len(got) < len(geoms):
+        got += srv.wait(timeout=60.0)
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == wf.WF_OK for r in got), got
+    assert st["peak_bytes"] <= budget
+    assert st["plans_evicted"] >= 1 and st["max_active"] == 1
+
+
+def test_requests_overlap_on_the_device(wf):
+    srv = wf.Server(mem_budget=4 << 30, slots=4)
+    reqs = [_request(70 + i, 64, 128, "wf") for i in range(8)]
+    outs = []
+    for i, R in enumerate(reqs):
+        out = np.empty(R["d"].size)
+        outs.append(out)
+        srv.submit("wf", nside=64, lmax=128, precision="mixed", tol=1e-5, s_out=out, tag=i, d=R["d"],
+                   noise_var=R["noise_var"], mask=R["mask"], C_ell=R["C_ell"])
+    got = []
+    while len(got) < len(reqs):
+        got += srv.wait(timeout=60.0)
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == wf.WF_OK for r in got)
+    assert st["max_active"] >= 2
+    spans = sorted((r["t_start"], r["t_done"]) for r in got)
+    assert any(b[0] < a[1] for a, b in zip(spans, spans[1:]))  # some solves ran at the same time
+
+
+def test_invalid_and_oversized_requests_are_rejected(wf):
+    srv = wf.Server(mem_budget=64 << 20, slots=2)
+    R = _request(80, 16, 32, "wf")
+    out = np.empty(R["d"].size)
+    srv.submit("wf", nside=16, lmax=40, precision="fp64", tol=1e-6, s_out=out, tag=1, d=R["d"],
+               noise_var=R["noise_var"], C_ell=R["C_ell"])
+    big = np.empty(12 * 1024 * 1024)
+    srv.submit("wf", nside=1024, lmax=2048, precision="mixed", tol=1e-6, s_out=big, tag=2, d=big,
+               noise_var=big, C_ell=np.ones(2049))
+    got = {}
+    while len(got) < 2:
+        for r in srv.wait(timeout=10.0):
+            got[r["tag"]] = r
+    st = srv.stats()
+    srv.close()
+    assert got[1]["status"] == wf.WF_EINVAL and got[2]["status"] == wf.WF_ENOMEM
+    assert st["rejected"] == 2 and st["plans_created"] == 0
