@@ -62,6 +62,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving workload instead: Poisson stream of mixed-size requests through wf_server_*")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="offered requests per second")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-maxiter", type=int, default=3000)
     ap.add_argument("--full-band-iters", type=int, default=0,
                     help="replay this many lambda = 1, L = lmax iterations instead of the cooling schedule "
                          "(steady-state timing and profiling)")
@@ -380,10 +387,124 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# serving workload: Poisson stream of Wiener-filter requests of mixed size
+# --------------------------------------------------------------------------
+SERVE_NSIDES = [64, 128, 256, 512, 1024]
+SERVE_WEIGHTS = [0.3, 0.3, 0.2, 0.15, 0.05]
+SERVE_POOL = {64: 6, 128: 6, 256: 4, 512: 3, 1024: 2}  # distinct seeded problems per nside
+
+
+def serve_problems(wf, dev):
+    """Seeded problems per nside: power-law C_l = l^-n (n ~ U(2, 3)), hit
+    pattern with its own jitter, |b| < U(10, 25) deg plus U{0..1000} disks of
+    0.3 deg; data = signal synthesised by the library + noise."""
+    import torch
+
+    pool = {}
+    for ns in SERVE_NSIDES:
+        lmax = 2 * ns
+        plan = wf.wf_plan_create("healpix", nside=ns, lmax=lmax, precision="fp64")
+        items = []
+        for k in range(SERVE_POOL[ns]):
+            rng = np.random.default_rng(gen.seed_for(5, 100 * ns + k))
+            cl = gen.power_law_cl(lmax, float(rng.uniform(2.0, 3.0)))
+            P = gen.healpix_problem(ns, lmax, gen.seed_for(5, 100 * ns + 50 + k), cl=cl,
+                                    b_cut_deg=float(rng.uniform(10.0, 25.0)), n_disks=int(rng.integers(0, 1001)),
+                                    disk_radius_deg=0.3)
+            s = torch.empty(plan.npix, dtype=torch.float64, device=dev)
+            wf.wf_alm2map(plan, torch.from_numpy(P["a_signal"]).to(dev), lmax, s)
+            d = s.cpu().numpy() + P["noise"]
+            items.append({"d": np.ascontiguousarray(d), "noise_var": np.ascontiguousarray(P["noise_var"]),
+                          "mask": np.ascontiguousarray(P["mask"]), "C_ell": np.ascontiguousarray(cl)})
+        plan.close()
+        pool[ns] = items
+    return pool
+
+
+def run_serve(args):
+    import torch
+
+    import paper_1210_4931_gb300 as wf
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wf.load()
+    pool = serve_problems(wf, dev)
+    rng = np.random.default_rng(gen.seed_for(5, 7))
+    n = args.serve_requests
+    gaps = rng.exponential(1.0 / args.serve_rate, n)
+    arrive = np.cumsum(gaps) - gaps[0]
+    ns_of = rng.choice(SERVE_NSIDES, size=n, p=SERVE_WEIGHTS)
+    prob_of = [int(rng.integers(0, SERVE_POOL[int(x)])) for x in ns_of]
+    tol_of = rng.choice([1e-4, 1e-6], size=n)
+    free = {ns: [] for ns in SERVE_NSIDES}  # recycled output maps
+    srv = wf.Server(device=local, mem_budget=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
+    outs, results = {}, {}
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    i = 0
+    while len(results) < n:
+        now = time.perf_counter() - t0
+        while i < n and arrive[i] <= now:
+            ns = int(ns_of[i])
+            R = pool[ns][prob_of[i]]
+            out = free[ns].pop() if free[ns] else np.empty(12 * ns * ns)
+            outs[i] = (ns, out)
+            srv.submit("wf", nside=ns, lmax=2 * ns, precision="mixed", tol=float(tol_of[i]), s_out=out, tag=i,
+                       d=R["d"], noise_var=R["noise_var"], mask=R["mask"], C_ell=R["C_ell"],
+                       maxiter=args.serve_maxiter)
+            i += 1
+        wait = (arrive[i] - (time.perf_counter() - t0)) if i < n else 0.5
+        for r in srv.wait(timeout=max(0.0, min(wait, 0.5))):
+            results[r["tag"]] = r
+            ns, out = outs.pop(r["tag"])
+            free[ns].append(out)
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in results.values()])
+    qwait = np.array([r["t_start"] - r["t_submit"] for r in results.values()])
+    t_first = min(r["t_submit"] for r in results.values())
+    t_last = max(r["t_done"] for r in results.values())
+    per = {}
+    for ns in SERVE_NSIDES:
+        sel = [r for r in results.values() if int(ns_of[r["tag"]]) == ns]
+        if sel:
+            l_ns = np.array([r["t_done"] - r["t_submit"] for r in sel])
+            per[str(ns)] = {"n": len(sel), "p50_ms": float(np.percentile(l_ns, 50) * 1e3),
+                            "p99_ms": float(np.percentile(l_ns, 99) * 1e3),
+                            "iters_mean": float(np.mean([r["iters"] for r in sel])),
+                            "converged": float(np.mean([r["converged"] for r in sel]))}
+    ok = sum(1 for r in results.values() if r["status"] in (wf.WF_OK, wf.WF_ENOCONV))
+    out = {"metric": "serving: Wiener-filter solves per second, Poisson arrivals, mixed nside 64-1024",
+           "value": n / (t_last - t_first), "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+           "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                          "mean": float(lat.mean() * 1e3)},
+           "queue_wait_ms": {"p50": float(np.percentile(qwait, 50) * 1e3),
+                             "p99": float(np.percentile(qwait, 99) * 1e3)},
+           "offered_rate": args.serve_rate, "achieved_rate": n / (t_last - t_first), "requests": n,
+           "ok": ok, "converged_fraction": float(np.mean([r["converged"] for r in results.values()])),
+           "per_nside": per, "wall_s": wall, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "serving_T_nside64-1024_poisson", "slots": args.serve_slots,
+                      "budget_gb": args.serve_budget_gb, "maxiter": args.serve_maxiter,
+                      "tol": "1e-4 or 1e-6 (equiprobable)", "precision": "mixed",
+                      "inputs": "seeded pool of %s problems per nside" % SERVE_POOL},
+           "server": st, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 
