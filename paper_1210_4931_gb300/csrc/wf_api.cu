@@ -1034,7 +1034,7 @@ long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging
     b += 2 * np * (lmax + 1) * 2 * ec;                           // G, F
     b += 3 * npix * es;                                          // r, nu, t
     b += std::max(np, 1024LL) * 8 + 4LL * (lmax + 2) * 8 + (lmax + 1) * 32 + 256;
-    if (f32) b += np * ((lmax + 1) / 8 + 1) * 2 * 16;            // FP64-block coefficients
+    if (f32) b += np * ((lmax + 1) / 8 + 1) * 2 * 8;             // FP64-block coefficients (stored FP32)
     if (staging) b += npix * (3 * 8 + 1) + (lmax + 1) * 8 + nalm * 16 * 2 + npix * 8;
     return b + (1LL << 20);
 }

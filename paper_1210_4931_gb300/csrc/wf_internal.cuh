@@ -77,7 +77,7 @@ struct Workspace {
     void *G = nullptr, *F = nullptr;
     void *r = nullptr, *nu = nullptr, *t = nullptr;
     void *scr = nullptr;          // per-CTA Bluestein scratch (2 * max Bluestein n complex per CTA)
-    double2 *Glow = nullptr;      // mixed: FP64-block synthesis coefficients [pair][glow_cap][hemisphere]
+    float2 *Glow = nullptr;       // mixed: FP64-block synthesis coefficients, rounded to FP32 [pair][glow_cap][hemisphere]
     double2 *b_low = nullptr;     // mixed: FP64-block analysis output (alm layout, m < lc)
     double *part_pix = nullptr;   // per ring-pair partial sums
     double *part_harm = nullptr;  // per m: [chi2_h, resid^2, x^T S^-1 x, x^T S^-2 x]

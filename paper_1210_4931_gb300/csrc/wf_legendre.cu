@@ -161,13 +161,16 @@ __global__ void k_to_T(const double *__restrict__ in, T *__restrict__ out, long 
 // lcut > 0: the FP64 block of the mixed path, l < lcm_of(lcut, m), output
 // into Gout with row stride gstride.
 // ---------------------------------------------------------------------------
-template <typename T>
+// TG: element type of the output (FP32 for the FP64 block of the mixed path,
+// whose ring pass adds it to the FP32 coefficients in FP32 anyway: converting
+// here keeps the 1/64-rate conversions off the ring kernel).
+template <typename T, typename TG>
 __global__ void __launch_bounds__(LEG_THREADS) k_legsyn(int lmax, int L, int npairs, int lcut,
                                                         const double2 *__restrict__ alm, const T *__restrict__ A,
                                                         const double *__restrict__ c64,
                                                         const int *__restrict__ ls_tab, const T *__restrict__ s0_tab,
                                                         const T *__restrict__ s1_tab, const T *__restrict__ xp,
-                                                        cx<T> *__restrict__ G, int gstride)
+                                                        cx<TG> *__restrict__ G, int gstride)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.y;
@@ -212,9 +215,9 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn(int lmax, int L, int npa
                 oi = fma(a1.y, mu1, oi);
             }
         }
-        cx<T> *g = G + ((size_t)p * gstride + m) * 2;
-        g[0] = mk<T>(er + orr, ei + oi);
-        g[1] = mk<T>(er - orr, ei - oi);
+        cx<TG> *g = G + ((size_t)p * gstride + m) * 2;
+        g[0] = mk<TG>((TG)(er + orr), (TG)(ei + oi));
+        g[1] = mk<TG>((TG)(er - orr), (TG)(ei - oi));
     }
 }
 
@@ -553,18 +556,19 @@ __device__ __forceinline__ void mx_step(const MxPairs<NP> &P, int l, float A0, f
 
 template <bool DIFF>
 __device__ __forceinline__ void mx_syn_run(const MxPairs<MXP> &P, int m, int L, const float4 *__restrict__ sAB,
-                                           const float4 *__restrict__ sac, float2 (&ER)[2], float2 (&EI)[2],
-                                           float2 (&OR)[2], float2 (&OI)[2])
+                                           const float4 *__restrict__ sac, float2 (&ER)[MXP / 2],
+                                           float2 (&EI)[MXP / 2], float2 (&OR)[MXP / 2], float2 (&OI)[MXP / 2])
 {
-    float2 Sa[2] = {dup(0.f), dup(0.f)}, Sb[2] = {dup(0.f), dup(0.f)};
-    float2 V0[2], V1[2];
+    float2 Sa[MXP / 2], Sb[MXP / 2], V0[MXP / 2], V1[MXP / 2];
+#pragma unroll
+    for (int pk = 0; pk < MXP / 2; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
     int l = P.lmin;
     for (; l <= L && l <= P.lmaxs; l += 2) {
         const int j = (l - m) >> 1;
         const float4 ab = sAB[j], ac = sac[j];
         mx_step<DIFF, true, MXP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
 #pragma unroll
-        for (int pk = 0; pk < 2; ++pk) {
+        for (int pk = 0; pk < MXP / 2; ++pk) {
             ER[pk] = __ffma2_rn(dup(ac.x), V0[pk], ER[pk]);
             EI[pk] = __ffma2_rn(dup(ac.y), V0[pk], EI[pk]);
             OR[pk] = __ffma2_rn(dup(ac.z), V1[pk], OR[pk]);
@@ -576,7 +580,7 @@ __device__ __forceinline__ void mx_syn_run(const MxPairs<MXP> &P, int m, int L, 
         const float4 ab = sAB[j], ac = sac[j];
         mx_step<DIFF, false, MXP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
 #pragma unroll
-        for (int pk = 0; pk < 2; ++pk) {
+        for (int pk = 0; pk < MXP / 2; ++pk) {
             ER[pk] = __ffma2_rn(dup(ac.x), V0[pk], ER[pk]);
             EI[pk] = __ffma2_rn(dup(ac.y), V0[pk], EI[pk]);
             OR[pk] = __ffma2_rn(dup(ac.z), V1[pk], OR[pk]);
@@ -631,8 +635,9 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
     for (int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * MXP; p0 < npairs; p0 += gridDim.x * blockDim.x * MXP) {
         MxPairs<MXP> P;
         mx_load_pairs<MXP>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
-        float2 ER[2] = {dup(0.f), dup(0.f)}, EI[2] = {dup(0.f), dup(0.f)};
-        float2 OR[2] = {dup(0.f), dup(0.f)}, OI[2] = {dup(0.f), dup(0.f)};
+        float2 ER[MXP / 2], EI[MXP / 2], OR[MXP / 2], OI[MXP / 2];
+#pragma unroll
+        for (int pk = 0; pk < MXP / 2; ++pk) ER[pk] = EI[pk] = OR[pk] = OI[pk] = dup(0.f);
         if (P.lmin <= L) {
             if (P.diff) mx_syn_run<true>(P, m, L, sAB, sac, ER, EI, OR, OI);
             else mx_syn_run<false>(P, m, L, sAB, sac, ER, EI, OR, OI);
@@ -796,7 +801,8 @@ size_t ana_smem(int L) { return (size_t)(L + 1 + CH + 2) * (sizeof(double2) + si
 size_t syn_mx_smem(int L) { return (size_t)((L + 2) / 2 + 2) * 2 * sizeof(float4) + 16; }
 size_t ana_mx_smem(int L) { return (size_t)(L + 1 + MX_CH + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32; }
 
-wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *G, int gstride, cudaStream_t s)
+template <typename TG>
+wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, cx<TG> *G, int gstride, cudaStream_t s)
 {
     const HpTables &t = p->tab;
     const int Lgrid = lcut > 0 ? std::min(L, lcut - 1) : L;
@@ -804,8 +810,8 @@ wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, double2 *
     const int gx = (p->npairs + 4 * LEG_THREADS - 1) / (4 * LEG_THREADS);
     dim3 grid(gx, Lgrid + 1);
     const size_t sm = syn_smem<double>(lcut > 0 ? std::min(L, lcut + 1) : L);
-    if (wf_status st = raise_smem_limit((const void *)k_legsyn<double>, sm)) return st;
-    k_legsyn<double><<<grid, LEG_THREADS, sm, s>>>(p->lmax, L, p->npairs, lcut, alm, t.A64, t.c64, t.ls,
+    if (wf_status st = raise_smem_limit((const void *)k_legsyn<double, TG>, sm)) return st;
+    k_legsyn<double, TG><<<grid, LEG_THREADS, sm, s>>>(p->lmax, L, p->npairs, lcut, alm, t.A64, t.c64, t.ls,
                                                             t.s0_64, t.s1_64, t.x64, G, gstride);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
@@ -959,7 +965,7 @@ wf_status hp_set_low_block(wf_plan p, int lc)
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     if (lc > 0 && lc > t.glow_cap) {
-        wf_status st = plan_alloc(p, (void **)&p->ws.Glow, (size_t)p->npairs * lc * 2 * sizeof(double2));
+        wf_status st = plan_alloc(p, (void **)&p->ws.Glow, (size_t)p->npairs * lc * 2 * sizeof(float2));
         if (st != WF_OK) return st;
         t.glow_cap = lc;
     }
@@ -987,12 +993,12 @@ wf_status join_aux(wf_plan p)
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
 {
     const HpTables &t = p->tab;
-    if (p->prec == WF_PREC_FP64) return launch_syn64(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1, p->stream);
+    if (p->prec == WF_PREC_FP64) return launch_syn64<double>(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1, p->stream);
     wf_status st;
     const bool low = t.lc_mx > 0;
     if (low) {
         if ((st = fork_aux(p)) != WF_OK) return st;
-        if ((st = launch_syn64(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux)) != WF_OK) return st;
+        if ((st = launch_syn64<float>(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux)) != WF_OK) return st;
     }
     const int gx = (p->npairs + MXP * LEG_THREADS - 1) / (MXP * LEG_THREADS);
     dim3 grid(gx, L + 1);

@@ -306,7 +306,7 @@ struct RingCommon {
     const int *order;     // ring pairs by decreasing cost
     int *ticket;          // work counter (zeroed before the launch)
     long long scr_stride;
-    const double2 *Glow;  // mixed path: FP64-block coefficients for m < lc (or null)
+    const float2 *Glow;   // mixed path: FP64-block coefficients for m < lc, rounded to FP32 (or null)
     int lc, glow_stride;
     int bpad;             // padded shared FFT buffer length
     int zsmem;            // 1: Bluestein / direct buffers follow the FFT buffer in shared memory
@@ -383,11 +383,11 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
                 }
             }
         }
-        const double2 *gl = rc.Glow ? rc.Glow + (size_t)pair * rc.glow_stride * 2 : nullptr;
+        const float2 *gl = rc.Glow ? rc.Glow + (size_t)pair * rc.glow_stride * 2 : nullptr;
         auto coef = [&](int m, int h) -> cx<T> {
             cx<T> v = g[2 * m + h];
             if (gl && m < rc.lc) {
-                const double2 w = gl[2 * m + h];
+                const float2 w = gl[2 * m + h];
                 v.x += (T)w.x;
                 v.y += (T)w.y;
             }
