@@ -222,6 +222,35 @@ wf_status wf_flat_solve_noalloc(int n, const double *d, const double *noise_var,
                                 const double *S, double tol, const wf_options *opt, void *cuda_stream,
                                 double *s_wf, double *alm_out, wf_info *info);
 
+/* Kinds of solve (batch items and serving requests). */
+typedef enum { WF_REQ_WF = 0, WF_REQ_FLUCT = 1, WF_REQ_CR = 2 } wf_request_kind;
+
+/* Batched solves: n HEALPix solves (Wiener filter of Sect. 2.1 or fluctuation
+ * map of Eq. 9; plans of any nside / lmax / precision, one distinct plan per
+ * item) advanced together.  Each step captures one messenger iteration of
+ * every unfinished solve, each on its own stream, in one CUDA graph and
+ * launches it with one call; the host then runs each solve's own cooling
+ * schedule (heuristic of Sect. 3 or a replay).  The graph is replayed while no
+ * solve changes (lambda, L) and updated when one does.  Results equal those
+ * of wf_solve / wf_fluct on the same plan (to rounding).  Items use device
+ * pointers as in wf_solve; info may be NULL.  The chi^2-bound schedule is not
+ * batchable (WF_EUNSUPPORTED).  cuda_stream: stream the graph is launched on;
+ * statuses[i]: the status of item i (WF_OK / WF_ENOCONV / error).  The return
+ * value reports argument and CUDA errors of the batch as a whole. */
+typedef struct {
+    int kind;                 /* WF_REQ_WF or WF_REQ_FLUCT */
+    const double *d;          /* WF: npix */
+    const double *noise_var;  /* npix */
+    const uint8_t *mask;      /* npix or NULL */
+    const double *C_ell;      /* lmax + 1 */
+    const double *g1, *g2;    /* FLUCT: npix real and n_alm complex draws */
+    double tol;
+    double *s_out;            /* npix */
+    double *alm_out;          /* n_alm complex, optional */
+    wf_info *info;            /* optional */
+} wf_batch_item;
+wf_status wf_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, void *cuda_stream, wf_status *statuses);
+
 /* ------------------------------------------------------------------------
  * Serving: a request loop over many HEALPix solves of mixed size.
  *
@@ -241,8 +270,6 @@ wf_status wf_flat_solve_noalloc(int n, const double *d, const double *noise_var,
  * overlap on the device.  Every result is that of the corresponding direct
  * call (wf_solve_host / wf_fluct_host) on a plan of the same geometry. */
 typedef struct wf_server_s *wf_server;
-
-typedef enum { WF_REQ_WF = 0, WF_REQ_FLUCT = 1, WF_REQ_CR = 2 } wf_request_kind;
 
 typedef struct {
     unsigned long long tag;   /* caller's identifier, returned in the result */

@@ -74,6 +74,13 @@ class wf_result(ctypes.Structure):
                 ("t_done", ctypes.c_double), ("slot", ctypes.c_int), ("plan_reused", ctypes.c_int)]
 
 
+class wf_batch_item(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("d", ctypes.c_void_p), ("noise_var", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("C_ell", ctypes.c_void_p), ("g1", ctypes.c_void_p),
+                ("g2", ctypes.c_void_p), ("tol", ctypes.c_double), ("s_out", ctypes.c_void_p),
+                ("alm_out", ctypes.c_void_p), ("info", ctypes.c_void_p)]
+
+
 class wf_server_stats(ctypes.Structure):
     _fields_ = [("pending", ctypes.c_longlong), ("active", ctypes.c_longlong), ("completed", ctypes.c_longlong),
                 ("rejected", ctypes.c_longlong), ("bytes_in_use", ctypes.c_longlong),
@@ -87,7 +94,7 @@ EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedu
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
            "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
            "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
-           "wf_server_wait", "wf_server_get_stats", "wf_server_destroy"]
+           "wf_server_wait", "wf_server_get_stats", "wf_server_destroy", "wf_solve_batch"]
 
 
 def load(path: str = LIB_PATH):
@@ -134,6 +141,9 @@ def load(path: str = LIB_PATH):
     L.wf_server_wait.restype = ctypes.c_int
     L.wf_server_get_stats.argtypes = [vp, ctypes.POINTER(wf_server_stats)]
     L.wf_server_get_stats.restype = ctypes.c_int
+    L.wf_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(wf_batch_item), vp,
+                                 ctypes.POINTER(ctypes.c_int)]
+    L.wf_solve_batch.restype = ctypes.c_int
     L.wf_server_destroy.argtypes = [vp]
     L.wf_server_destroy.restype = None
     L.wf_strerror.argtypes = [ctypes.c_int]
@@ -355,6 +365,45 @@ def wf_fluct_host(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_ou
     return _info_dict(st, info, bufs)
 
 
+def wf_solve_batch(plans, items, trace_cap=0, stream=None) -> list:
+    """Several solves advanced together (one CUDA graph per step).  items:
+    dicts with kind ('wf' or 'fluct'), d / g1 / g2, noise_var, mask, C_ell, tol,
+    s_out and optional alm_out (CUDA tensors).  Returns one report per item
+    (with its 'status'); argument or CUDA errors of the batch raise."""
+    import torch
+
+    n = len(plans)
+    assert len(items) == n
+    arr = (wf_batch_item * n)()
+    hv = (ctypes.c_void_p * n)(*[pl.handle for pl in plans])
+    st = (ctypes.c_int * n)()
+    infos = []
+    for i, (pl, it) in enumerate(zip(plans, items)):
+        info, bufs = _info(trace_cap)
+        infos.append((info, bufs))
+        n8 = pl.npix * 8
+        b = arr[i]
+        b.kind = REQUEST_KINDS[it.get("kind", "wf")]
+        b.d = _ptr(it.get("d"), None, n8, "d")
+        b.noise_var = _ptr(it["noise_var"], None, n8, "noise_var")
+        b.mask = _ptr(it.get("mask"), None, pl.npix, "mask")
+        b.C_ell = _ptr(it["C_ell"], None, None, "C_ell")
+        b.g1 = _ptr(it.get("g1"), None, n8, "g1")
+        b.g2 = _ptr(it.get("g2"), None, pl.nalm * 16, "g2")
+        b.tol = float(it["tol"])
+        b.s_out = _ptr(it["s_out"], None, n8, "s_out")
+        b.alm_out = _ptr(it.get("alm_out"), None, pl.nalm * 16, "alm_out")
+        b.info = ctypes.cast(ctypes.byref(info), ctypes.c_void_p)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().wf_solve_batch(n, hv, arr, ctypes.c_void_p(stream.cuda_stream), st), "wf_solve_batch")
+    out = []
+    for i in range(n):
+        info, bufs = infos[i]
+        out.append(_info_dict(int(st[i]), info, bufs))
+    return out
+
+
 def wf_plan_estimate_bytes(kind: str, *, nside: int = 0, lmax: int = 0, n: int = 0, precision: str = "fp64",
                            host_staging: bool = True) -> int:
     g = wf_geometry()
@@ -459,6 +508,6 @@ def wf_map2alm_adjoint(plan: Plan, map_in, L, alm_out):
                                      _ptr(alm_out, None, plan.nalm * 16, "alm")), "wf_map2alm_adjoint")
 
 
-__all__ = ["Plan", "Server", "WfError", "load", "wf_fluct_host", "wf_plan_estimate_bytes", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
+__all__ = ["Plan", "Server", "WfError", "load", "wf_fluct_host", "wf_plan_estimate_bytes", "wf_solve_batch", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
            "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "EXPORTS",
            "LIB_PATH"]

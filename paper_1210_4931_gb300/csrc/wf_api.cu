@@ -15,6 +15,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <array>
 #include <mutex>
 #include <new>
 #include <utility>
@@ -80,8 +81,11 @@ wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes)
     return WF_OK;
 }
 
-Prof::Prof(wf_plan p_, wf_info *i, bool profile) : p(p_), info(i), on(profile)
+void Prof::init(wf_plan p_, wf_info *i, bool profile)
 {
+    p = p_;
+    info = i;
+    on = profile;
     for (int k = 0; k < WF_NK; ++k) k0[k] = p->kcnt[k];
     p->kfam = WF_K_OTHER;
     if (on && !p->events_ready) {
@@ -458,12 +462,21 @@ __global__ void k_blend(long long npix, const T *__restrict__ r, const T *__rest
 
 int grid_for(long long n, int nsm) { return (int)std::min<long long>((n + 255) / 256, (long long)nsm * 8); }
 
-wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
+// reduce the partial sums in a fixed order into ws.scal and copy them to the
+// pinned host mirror ws.h_scal (enqueued only: valid after the stream syncs)
+wf_status sums_enqueue(wf_plan p, SumSpec sp, int nsum)
 {
     k_sums<<<1, 256, 0, p->stream>>>(sp, nsum, p->ws.scal);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     WF_CUDA(cudaMemcpyAsync(p->ws.h_scal, p->ws.scal, nsum * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    return WF_OK;
+}
+
+wf_status sums(wf_plan p, SumSpec sp, int nsum, Prof *pr = nullptr)
+{
+    wf_status st = sums_enqueue(p, sp, nsum);
+    if (st != WF_OK) return st;
     WF_CUDA(cudaStreamSynchronize(p->stream));
     return WF_OK;
 }
@@ -641,55 +654,87 @@ wf_status hp_adjoint_T(wf_plan p, const void *map_T, int L, double2 *out)
     return hp_legendre_analysis(p, L, LEG_ADJOINT, ba, nullptr, out);
 }
 
-wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *mask, const double *C_ell, double tol,
-                   bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out, wf_info *info,
-                   const double2 *a_init = nullptr)
-{
-    const wf_options o = defaults(p->opt);
-    const int lmax = p->lmax;
-    if (o.schedule == 1 && fluct && p->replay_lambda.empty())
-        return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
-    if (o.schedule == 1 && a_init && p->replay_lambda.empty())
-        return set_error(WF_EUNSUPPORTED, "chi^2-bound schedule with a starting iterate");
-    Prof pr(p, info, o.profile != 0);
-    double tau = 0;
+// Resumable state of one HEALPix solve.  hp_solve runs
+//   begin -> { pick -> launch -> (stream sync) -> absorb } -> end
+// on the plan's stream; the batch solver runs the same phases for several
+// plans, with the launches of one step of all of them captured in one graph.
+struct HpRun {
+    wf_plan p = nullptr;
+    const double *d = nullptr, *nv = nullptr, *C_ell = nullptr, *g1 = nullptr, *g2 = nullptr;
+    const uint8_t *mask = nullptr;
+    double tol = 0;
+    bool fluct = false;
+    double *s_out = nullptr, *alm_out = nullptr;
+    wf_info *info = nullptr;
+    const double2 *a_init = nullptr;
+    bool copy_back = false;  // a <- a_new by a device copy in the iteration (pointers fixed for graphs)
+    bool graph = false;      // the launches are being captured: no profiling events
+    wf_options o{};
+    int lmax = 0;
+    double tau = 0, tau_h = 0, bnorm = 0, sigma = 0;
     long long ndof = 0;
-    wf_status st = hp_setup(p, fluct ? nullptr : d, nv, mask, &tau, &ndof);
-    if (st != WF_OK) return st;
-    const double tau_h = tau * p->omega;
+    int lc = 0;
     HpSchedule sch;
+    bool replay = false, rigorous = false;
+    int nrep = 0;
+    double bound = 0, u_cur = 0, h_cur = 0, q_cur = 0;
+    int bound_updates = 0;
+    int k = 0, level_iters = 0, levels = 1;
+    bool have_prev = false, converged = false, chi2_bad = false;
+    double prev_chi2 = 0, last_resid = NAN, best_resid = INFINITY;
+    wf_status result = WF_OK;
+    double lam = 1.0, chi2_bound = NAN;  // the current iteration
+    int L = 0;
+    Prof pr;
+};
+
+wf_status hp_begin(HpRun &R)
+{
+    wf_plan p = R.p;
+    R.o = defaults(p->opt);
+    const wf_options &o = R.o;
+    const int lmax = R.lmax = p->lmax;
+    if (o.schedule == 1 && R.fluct && p->replay_lambda.empty())
+        return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
+    if (o.schedule == 1 && R.a_init && p->replay_lambda.empty())
+        return set_error(WF_EUNSUPPORTED, "chi^2-bound schedule with a starting iterate");
+    R.pr.init(p, R.info, o.profile != 0 && !R.graph);
+    wf_status st = hp_setup(p, R.fluct ? nullptr : R.d, R.nv, R.mask, &R.tau, &R.ndof);
+    if (st != WF_OK) return st;
+    const double tau_h = R.tau_h = R.tau * p->omega;
+    HpSchedule &sch = R.sch;
     sch.c.resize(lmax + 1);
-    if ((st = to_host(p, sch.c.data(), C_ell, (lmax + 1) * sizeof(double))) != WF_OK) return st;
+    if ((st = to_host(p, sch.c.data(), R.C_ell, (lmax + 1) * sizeof(double))) != WF_OK) return st;
     // Mixed precision: the messenger iteration contracts a mode by about
     // tau_h / S_l per iteration where the mask leaves it unconstrained, so a
     // systematic operator error larger than that margin makes the iteration
     // grow.  Modes with S_l / tau_h >= kappa take the FP64 block.
-    int lc = 0;
+    R.lc = 0;
     if (p->prec != WF_PREC_FP64) {
-        if (o.mixed_lc > 0) lc = std::min(o.mixed_lc, lmax + 1);
+        if (o.mixed_lc > 0) R.lc = std::min(o.mixed_lc, lmax + 1);
         else if (o.mixed_lc == 0)
             for (int l = lmax; l >= 0; --l)
-                if (sch.c[l] / tau_h >= o.mixed_kappa) { lc = l + 1; break; }
-        if ((st = hp_set_low_block(p, lc)) != WF_OK) return st;
+                if (sch.c[l] / tau_h >= o.mixed_kappa) { R.lc = l + 1; break; }
+        if ((st = hp_set_low_block(p, R.lc)) != WF_OK) return st;
     }
-    if (fluct) {
+    if (R.fluct) {
         // r = nu^1/2 g1 + Omega Y (S^-1/2 g2), z synthesised into the output map as scratch
-        k_isqrt_S<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, (const double2 *)g2, p->ws.a_new);
+        k_isqrt_S<<<lmax + 1, 256, 0, p->stream>>>(lmax, R.C_ell, (const double2 *)R.g2, p->ws.a_new);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
-        if ((st = hp_alm2map(p, p->ws.a_new, lmax, s_out)) != WF_OK) return st;
+        if ((st = hp_alm2map(p, p->ws.a_new, lmax, R.s_out)) != WF_OK) return st;
         if (p->prec == WF_PREC_FP64)
             k_fluct_source<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
-                p->npix, (const double *)p->ws.nu, g1, s_out, p->omega, (double *)p->ws.r);
+                p->npix, (const double *)p->ws.nu, R.g1, R.s_out, p->omega, (double *)p->ws.r);
         else
             k_fluct_source<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
-                p->npix, (const float *)p->ws.nu, g1, s_out, p->omega, (float *)p->ws.r);
+                p->npix, (const float *)p->ws.nu, R.g1, R.s_out, p->omega, (float *)p->ws.r);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
     }
     // |b| = |Y^T r| over modes with S > 0
     if ((st = hp_adjoint_T(p, p->ws.r, lmax, p->ws.b)) != WF_OK) return st;
-    k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, p->ws.b, 0, p->ws.part_harm);
+    k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, R.C_ell, p->ws.b, 0, p->ws.part_harm);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     {
@@ -697,10 +742,10 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         sp.in[0] = p->ws.part_harm;
         sp.n[0] = lmax + 1;
         sp.stride[0] = 1;
-        if ((st = sums(p, sp, 1, &pr)) != WF_OK) return st;
+        if ((st = sums(p, sp, 1, &R.pr)) != WF_OK) return st;
     }
-    const double bnorm = std::sqrt(p->ws.h_scal[0]);
-    if (!(bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
+    R.bnorm = std::sqrt(p->ws.h_scal[0]);
+    if (!(R.bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
 
     sch.tau_h = tau_h;
     sch.lmax = lmax;
@@ -709,161 +754,218 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     sch.ell_iter = std::min(o.ell0, lmax);
     sch.level();
 
-    if (a_init)
-        WF_CUDA(cudaMemcpyAsync(p->ws.a, a_init, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    if (R.a_init)
+        WF_CUDA(cudaMemcpyAsync(p->ws.a, R.a_init, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
     else
         WF_CUDA(cudaMemsetAsync(p->ws.a, 0, p->nalm * sizeof(double2), p->stream));
     WF_CUDA(cudaMemsetAsync(p->ws.a_new, 0, p->nalm * sizeof(double2), p->stream));
-    const bool replay = !p->replay_lambda.empty();
-    const int nrep = (int)p->replay_lambda.size();
-    const bool rigorous = o.schedule == 1 && !replay;  // a replay overrides the schedule
-    double bound = (double)ndof - o.m_sigma * std::sqrt(2.0 * (double)ndof);
-    if (rigorous && !(bound > 0.0))
-        return set_error(WF_EINVAL, "chi^2 bound n_dof - m sigma = %.3g is not positive (too few observed pixels)", bound);
-    double u_cur = 0.0, h_cur = 0.0, q_cur = 0.0;
-    int bound_updates = 0;
-    int k = 0, level_iters = 0, levels = 1;
-    bool have_prev = false, converged = false, chi2_bad = false;
-    double prev_chi2 = 0, last_resid = NAN, best_resid = INFINITY;
-    const double sigma = std::sqrt(2.0 * (double)ndof);
-    wf_status result = WF_OK;
-    for (;;) {
-        double lam;
-        int L;
-        if (replay) {
-            if (k >= nrep) break;
-            lam = p->replay_lambda[k];
-            L = std::min(std::max(p->replay_L[k], 0), lmax);
-        } else {
-            if (k >= o.maxiter) { result = WF_ENOCONV; break; }
-            lam = sch.lam;
-            L = sch.L;
+    R.replay = !p->replay_lambda.empty();
+    R.nrep = (int)p->replay_lambda.size();
+    R.rigorous = o.schedule == 1 && !R.replay;  // a replay overrides the schedule
+    R.bound = (double)R.ndof - o.m_sigma * std::sqrt(2.0 * (double)R.ndof);
+    if (R.rigorous && !(R.bound > 0.0))
+        return set_error(WF_EINVAL, "chi^2 bound n_dof - m sigma = %.3g is not positive (too few observed pixels)",
+                         R.bound);
+    R.sigma = std::sqrt(2.0 * (double)R.ndof);
+    return WF_OK;
+}
+
+// (lambda, L) of iteration R.k; false when the loop is over (R.result set)
+bool hp_pick(HpRun &R)
+{
+    wf_plan p = R.p;
+    if (R.replay) {
+        if (R.k >= R.nrep) return false;
+        R.lam = p->replay_lambda[R.k];
+        R.L = std::min(std::max(p->replay_L[R.k], 0), R.lmax);
+    } else {
+        if (R.k >= R.o.maxiter) {
+            R.result = WF_ENOCONV;
+            return false;
         }
-        pr.iter_begin();
-        double chi2_bound = NAN;
-        if (rigorous) {
-            // x_k = Y a_k, then lambda_k from chi^2(lambda_k, x_k) = b (Sect. 2.2)
-            L = lmax;
-            pr.begin(WF_K_LEG_SYN);
-            if ((st = hp_legendre_synthesis(p, p->ws.a, L)) != WF_OK) return st;
-            pr.end();
-            pr.begin(WF_K_RING_SYN);
-            if ((st = hp_ring_synthesis(p, L, RS_SYN, 1.0, tau, nullptr)) != WF_OK) return st;
-            pr.end();
-            double u_new = 0.0;
-            if (k == 0) {
-                if ((st = bound_root(p, h_cur, bound, 1.0, true, &u_new, &chi2_bound, &pr)) != WF_OK) return st;
-            } else if (u_cur > 0.0) {
-                if ((st = bound_root(p, h_cur, bound, u_cur, false, &u_new, &chi2_bound, &pr)) != WF_OK) return st;
-                if (u_new > 0.0 && (u_cur - u_new) <= o.stall_tol * u_new) {
-                    // converged at lambda > 1: raise b to chi2_min(lambda) + (lambda - 1) tau_h x^T S^-2 x
-                    bound = chi2_bound + u_new * p->omega * q_cur;
-                    ++bound_updates;
-                    if ((st = bound_root(p, h_cur, bound, u_cur, false, &u_new, &chi2_bound, &pr)) != WF_OK) return st;
-                }
-            }
-            if (u_new / tau < 1e-9) u_new = 0.0;
-            if (u_new == 0.0) {
-                // lambda = 1 (reached or floored): report chi^2(1, x_k)
-                double A, D;
-                if ((st = pix_sums(p, 0.0, &A, &D, &pr)) != WF_OK) return st;
-                chi2_bound = h_cur + A;
-            }
-            u_cur = u_new;
-            lam = 1.0 + u_cur / tau;
-            if (p->prec == WF_PREC_FP64)
-                k_blend<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
-                    p->npix, (const double *)p->ws.r, (const double *)p->ws.nu, (double *)p->ws.t, lam * tau,
-                    (lam - 1.0) * tau);
-            else
-                k_blend<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
-                    p->npix, (const float *)p->ws.r, (const float *)p->ws.nu, (float *)p->ws.t, (float)(lam * tau),
-                    (float)((lam - 1.0) * tau));
-            WF_COUNT_LAUNCH(p);
-            WF_CUDA(cudaGetLastError());
-        } else {
-            pr.begin(WF_K_LEG_SYN);
-            if ((st = hp_legendre_synthesis(p, p->ws.a, L)) != WF_OK) return st;
-            pr.end();
-            pr.begin(WF_K_RING_SYN);
-            if ((st = hp_ring_synthesis(p, L, RS_BLEND, lam, tau, nullptr)) != WF_OK) return st;
-            pr.end();
-        }
-        const bool full = (lam == 1.0 && L == lmax);
-        pr.begin(WF_K_RING_ANA);
-        if ((st = hp_ring_analysis(p, L, p->ws.t)) != WF_OK) return st;
-        pr.end();
-        BlendArgs ba;
-        ba.lam_tauh = lam * tau_h;
-        ba.tauh = tau_h;
-        ba.S = C_ell;
-        ba.want_resid = full ? 1 : 0;
-        pr.begin(WF_K_LEG_ANA);
-        if ((st = hp_legendre_analysis(p, L, LEG_BLEND, ba, p->ws.a, p->ws.a_new)) != WF_OK) return st;
-        pr.end();
-        SumSpec sp{};
-        sp.in[0] = p->ws.part_pix;
-        sp.n[0] = p->npairs;
-        sp.stride[0] = 1;
-        for (int q = 0; q < 4; ++q) {
-            sp.in[1 + q] = p->ws.part_harm + q;
-            sp.n[1 + q] = L + 1;
-            sp.stride[1 + q] = 4;
-        }
-        if ((st = sums(p, sp, 5, &pr)) != WF_OK) return st;
-        const double ims = pr.iter_end();
-        pr.collect();
-        const double chi2 = (rigorous) ? chi2_bound : p->ws.h_scal[0] + p->ws.h_scal[1];
-        const double resid = full ? std::sqrt(p->ws.h_scal[2]) / bnorm : NAN;
-        h_cur = p->ws.h_scal[3];  // x_{k+1}^T S^-1 x_{k+1} and x^T S^-2 x for the next lambda
-        q_cur = p->ws.h_scal[4];
-        record(info, k, lam, L, chi2, resid, ims);
-        std::swap(p->ws.a, p->ws.a_new);
-        ++k;
-        if (full) {
-            last_resid = resid;
-            if (!std::isfinite(resid) || (k > 50 && resid > 1e3 * best_resid)) { result = WF_EDIVERGE; break; }
-            best_resid = std::min(best_resid, resid);
-        }
-        if (!std::isfinite(chi2)) { result = WF_EDIVERGE; chi2_bad = true; break; }
-        if (rigorous) {
-            if (full && resid < tol) { converged = true; break; }
-            continue;
-        }
-        if (replay) {
-            if (full && resid < tol) {
-                converged = true;
-                if (a_init) break;  // correction sweeps stop at the tolerance
-            }
-            continue;
-        }
-        if (sch.final_level()) {
-            if (resid < tol) { converged = true; break; }
-        } else {
-            ++level_iters;
-            const bool plateau = have_prev && std::fabs(chi2 - prev_chi2) < o.eta * sigma;
-            if (plateau || level_iters >= o.level_cap) {
-                sch.advance();
-                ++levels;
-                have_prev = false;
-                level_iters = 0;
-                continue;
-            }
-        }
-        prev_chi2 = chi2;
-        have_prev = true;
+        R.lam = R.sch.lam;
+        R.L = R.sch.L;
     }
+    return true;
+}
+
+// one messenger iteration (Eqs. 3-4) and its sums, enqueued on the plan's
+// stream; the chi^2-bound schedule synchronises inside to find lambda
+wf_status hp_launch(HpRun &R)
+{
+    wf_plan p = R.p;
+    Prof &pr = R.pr;
+    const wf_options &o = R.o;
+    const double tau = R.tau;
+    wf_status st;
+    pr.iter_begin();
+    R.chi2_bound = NAN;
+    if (R.rigorous) {
+        // x_k = Y a_k, then lambda_k from chi^2(lambda_k, x_k) = b (Sect. 2.2)
+        R.L = R.lmax;
+        pr.begin(WF_K_LEG_SYN);
+        if ((st = hp_legendre_synthesis(p, p->ws.a, R.L)) != WF_OK) return st;
+        pr.end();
+        pr.begin(WF_K_RING_SYN);
+        if ((st = hp_ring_synthesis(p, R.L, RS_SYN, 1.0, tau, nullptr)) != WF_OK) return st;
+        pr.end();
+        double u_new = 0.0;
+        if (R.k == 0) {
+            if ((st = bound_root(p, R.h_cur, R.bound, 1.0, true, &u_new, &R.chi2_bound, &pr)) != WF_OK) return st;
+        } else if (R.u_cur > 0.0) {
+            if ((st = bound_root(p, R.h_cur, R.bound, R.u_cur, false, &u_new, &R.chi2_bound, &pr)) != WF_OK) return st;
+            if (u_new > 0.0 && (R.u_cur - u_new) <= o.stall_tol * u_new) {
+                // converged at lambda > 1: raise b to chi2_min(lambda) + (lambda - 1) tau_h x^T S^-2 x
+                R.bound = R.chi2_bound + u_new * p->omega * R.q_cur;
+                ++R.bound_updates;
+                if ((st = bound_root(p, R.h_cur, R.bound, R.u_cur, false, &u_new, &R.chi2_bound, &pr)) != WF_OK)
+                    return st;
+            }
+        }
+        if (u_new / tau < 1e-9) u_new = 0.0;
+        if (u_new == 0.0) {
+            // lambda = 1 (reached or floored): report chi^2(1, x_k)
+            double A, D;
+            if ((st = pix_sums(p, 0.0, &A, &D, &pr)) != WF_OK) return st;
+            R.chi2_bound = R.h_cur + A;
+        }
+        R.u_cur = u_new;
+        R.lam = 1.0 + R.u_cur / tau;
+        const double lam = R.lam;
+        if (p->prec == WF_PREC_FP64)
+            k_blend<double><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
+                p->npix, (const double *)p->ws.r, (const double *)p->ws.nu, (double *)p->ws.t, lam * tau,
+                (lam - 1.0) * tau);
+        else
+            k_blend<float><<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(
+                p->npix, (const float *)p->ws.r, (const float *)p->ws.nu, (float *)p->ws.t, (float)(lam * tau),
+                (float)((lam - 1.0) * tau));
+        WF_COUNT_LAUNCH(p);
+        WF_CUDA(cudaGetLastError());
+    } else {
+        pr.begin(WF_K_LEG_SYN);
+        if ((st = hp_legendre_synthesis(p, p->ws.a, R.L)) != WF_OK) return st;
+        pr.end();
+        pr.begin(WF_K_RING_SYN);
+        if ((st = hp_ring_synthesis(p, R.L, RS_BLEND, R.lam, tau, nullptr)) != WF_OK) return st;
+        pr.end();
+    }
+    const int L = R.L;
+    const bool full = (R.lam == 1.0 && L == R.lmax);
+    pr.begin(WF_K_RING_ANA);
+    if ((st = hp_ring_analysis(p, L, p->ws.t)) != WF_OK) return st;
+    pr.end();
+    BlendArgs ba;
+    ba.lam_tauh = R.lam * R.tau_h;
+    ba.tauh = R.tau_h;
+    ba.S = R.C_ell;
+    ba.want_resid = full ? 1 : 0;
+    pr.begin(WF_K_LEG_ANA);
+    if ((st = hp_legendre_analysis(p, L, LEG_BLEND, ba, p->ws.a, p->ws.a_new)) != WF_OK) return st;
+    pr.end();
+    SumSpec sp{};
+    sp.in[0] = p->ws.part_pix;
+    sp.n[0] = p->npairs;
+    sp.stride[0] = 1;
+    for (int q = 0; q < 4; ++q) {
+        sp.in[1 + q] = p->ws.part_harm + q;
+        sp.n[1 + q] = L + 1;
+        sp.stride[1 + q] = 4;
+    }
+    if ((st = sums_enqueue(p, sp, 5)) != WF_OK) return st;
+    if (R.copy_back)
+        WF_CUDA(cudaMemcpyAsync(p->ws.a, p->ws.a_new, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    return WF_OK;
+}
+
+// after the iteration's sums reached the host: trace, residual, schedule;
+// false when the loop is over
+bool hp_absorb(HpRun &R)
+{
+    wf_plan p = R.p;
+    const double ims = R.pr.iter_end();
+    R.pr.collect();
+    const bool full = (R.lam == 1.0 && R.L == R.lmax);
+    const double chi2 = R.rigorous ? R.chi2_bound : p->ws.h_scal[0] + p->ws.h_scal[1];
+    const double resid = full ? std::sqrt(p->ws.h_scal[2]) / R.bnorm : NAN;
+    R.h_cur = p->ws.h_scal[3];  // x_{k+1}^T S^-1 x_{k+1} and x^T S^-2 x for the next lambda
+    R.q_cur = p->ws.h_scal[4];
+    record(R.info, R.k, R.lam, R.L, chi2, resid, ims);
+    if (!R.copy_back) std::swap(p->ws.a, p->ws.a_new);
+    ++R.k;
+    if (full) {
+        R.last_resid = resid;
+        if (!std::isfinite(resid) || (R.k > 50 && resid > 1e3 * R.best_resid)) {
+            R.result = WF_EDIVERGE;
+            return false;
+        }
+        R.best_resid = std::min(R.best_resid, resid);
+    }
+    if (!std::isfinite(chi2)) {
+        R.result = WF_EDIVERGE;
+        R.chi2_bad = true;
+        return false;
+    }
+    if (R.rigorous) {
+        if (full && resid < R.tol) {
+            R.converged = true;
+            return false;
+        }
+        return true;
+    }
+    if (R.replay) {
+        if (full && resid < R.tol) {
+            R.converged = true;
+            if (R.a_init) return false;  // correction sweeps stop at the tolerance
+        }
+        return true;
+    }
+    HpSchedule &sch = R.sch;
+    if (sch.final_level()) {
+        if (resid < R.tol) {
+            R.converged = true;
+            return false;
+        }
+    } else {
+        ++R.level_iters;
+        const bool plateau = R.have_prev && std::fabs(chi2 - R.prev_chi2) < R.o.eta * R.sigma;
+        if (plateau || R.level_iters >= R.o.level_cap) {
+            sch.advance();
+            ++R.levels;
+            R.have_prev = false;
+            R.level_iters = 0;
+            return true;
+        }
+    }
+    R.prev_chi2 = chi2;
+    R.have_prev = true;
+    return true;
+}
+
+wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *mask, const double *C_ell, double tol,
+                   bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out, wf_info *info,
+                   const double2 *a_init = nullptr);
+
+// refinement sweeps (mixed precision), output map, chi^2 of the result, report
+wf_status hp_end(HpRun &R)
+{
+    wf_plan p = R.p;
+    const wf_options &o = R.o;
+    const int lmax = R.lmax;
+    Prof &pr = R.pr;
+    wf_status st;
     // Mixed precision, row a9: FP64 correction sweeps.  Up to refine_sweeps
     // messenger iterations at lambda = 1 on the full band run in FP64 from the
     // mixed-precision iterate (an FP64 sub-plan of the same geometry); their
     // residual is the FP64 operator's, and the output map is synthesised in FP64.
-    if (p->prec != WF_PREC_FP64 && o.refine_sweeps > 0 && result != WF_EDIVERGE) {
+    if (p->prec != WF_PREC_FP64 && o.refine_sweeps > 0 && R.result != WF_EDIVERGE) {
         if (!p->sub) {
             wf_plan sub = nullptr;
             if ((st = wf_plan_create(&p->g, lmax, WF_PREC_FP64, (void *)p->stream, &sub)) != WF_OK) return st;
             p->sub = sub;
         }
         wf_plan sub = p->sub;
+        sub->stream = p->stream;
         sub->opt = p->opt;
         sub->opt.profile = o.profile;
         sub->opt.refine_sweeps = 0;
@@ -879,39 +981,40 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         si.resid_trace = tr.data();
         si.iter_ms_trace = tm.data();
         si.trace_cap = o.refine_sweeps;
-        st = hp_solve(sub, d, nv, mask, C_ell, tol, fluct, g1, g2, s_out, alm_out, &si, p->ws.a);
+        st = hp_solve(sub, R.d, R.nv, R.mask, R.C_ell, R.tol, R.fluct, R.g1, R.g2, R.s_out, R.alm_out, &si, p->ws.a);
         if (st != WF_OK) return st;
-        for (int i = 0; i < si.iters; ++i) record(info, k + i, tl[i], tL[i], tc[i], tr[i], tm[i]);
+        for (int i = 0; i < si.iters; ++i) record(R.info, R.k + i, tl[i], tL[i], tc[i], tr[i], tm[i]);
         for (int f = 0; f < WF_NK; ++f) {
             pr.ms[f] += si.kernel_ms[f];
             pr.cnt[f] += si.kernel_launches[f];
         }
         pr.launches += si.launches;
         pr.finish();
-        if (info) {
-            info->iters = k + si.iters;
-            info->converged = (converged || si.converged) ? 1 : 0;
+        if (R.info) {
+            wf_info *info = R.info;
+            info->iters = R.k + si.iters;
+            info->converged = (R.converged || si.converged) ? 1 : 0;
             info->final_residual = si.final_residual;
             info->chi2_over_ndof = si.chi2_over_ndof;
-            info->n_dof = ndof;
-            info->tau = tau;
-            info->n_levels = rigorous ? 1 + bound_updates : levels;
+            info->n_dof = R.ndof;
+            info->tau = R.tau;
+            info->n_levels = R.rigorous ? 1 + R.bound_updates : R.levels;
             info->refine_sweeps = si.iters;
-            info->mixed_lc = lc;
+            info->mixed_lc = R.lc;
         }
         if (si.converged) return WF_OK;
         set_error(WF_ENOCONV, "not converged after %d FP64 sweeps (residual %.3e)", si.iters, si.final_residual);
-        return replay ? WF_OK : WF_ENOCONV;
+        return R.replay ? WF_OK : WF_ENOCONV;
     }
-    if ((st = hp_alm2map(p, p->ws.a, lmax, s_out)) != WF_OK) return st;
-    if (alm_out)
-        WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.a, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    if ((st = hp_alm2map(p, p->ws.a, lmax, R.s_out)) != WF_OK) return st;
+    if (R.alm_out)
+        WF_CUDA(cudaMemcpyAsync(R.alm_out, p->ws.a, p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
     double chi2n = NAN;
-    if (!fluct) {
-        k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, C_ell, p->ws.a, 1, p->ws.part_harm);
+    if (!R.fluct) {
+        k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, R.C_ell, p->ws.a, 1, p->ws.part_harm);
         WF_COUNT_LAUNCH(p);
         const int gb = 256;
-        k_pix_chi2<<<gb, 256, 0, p->stream>>>(p->npix, d, nv, mask, s_out, p->ws.part_pix);
+        k_pix_chi2<<<gb, 256, 0, p->stream>>>(p->npix, R.d, R.nv, R.mask, R.s_out, p->ws.part_pix);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         SumSpec sp{};
@@ -922,28 +1025,218 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
         sp.n[1] = gb;
         sp.stride[1] = 1;
         if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
-        chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
+        chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)R.ndof;
     } else {
         WF_CUDA(cudaStreamSynchronize(p->stream));
     }
-    if (info) {
-        info->iters = k;
-        info->converged = converged ? 1 : 0;
-        info->final_residual = last_resid;
+    if (R.info) {
+        wf_info *info = R.info;
+        info->iters = R.k;
+        info->converged = R.converged ? 1 : 0;
+        info->final_residual = R.last_resid;
         info->chi2_over_ndof = chi2n;
-        info->n_dof = ndof;
-        info->tau = tau;
-        info->n_levels = rigorous ? 1 + bound_updates : levels;
+        info->n_dof = R.ndof;
+        info->tau = R.tau;
+        info->n_levels = R.rigorous ? 1 + R.bound_updates : R.levels;
         info->refine_sweeps = 0;
-        info->mixed_lc = lc;
+        info->mixed_lc = R.lc;
     }
     pr.finish();
-    if (result == WF_OK && !replay && !converged) result = WF_ENOCONV;
-    if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", last_resid);
-    if (result == WF_EDIVERGE && chi2_bad) set_error(result, "chi^2 is not finite at iteration %d", k);
+    wf_status result = R.result;
+    if (result == WF_OK && !R.replay && !R.converged) result = WF_ENOCONV;
+    if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", R.last_resid);
+    if (result == WF_EDIVERGE && R.chi2_bad) set_error(result, "chi^2 is not finite at iteration %d", R.k);
     else if (result == WF_EDIVERGE)
-        set_error(result, "residual grew (%.3e); lmax too large for this nside?", last_resid);
+        set_error(result, "residual grew (%.3e); lmax too large for this nside?", R.last_resid);
     return result;
+}
+
+wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *mask, const double *C_ell, double tol,
+                   bool fluct, const double *g1, const double *g2, double *s_out, double *alm_out, wf_info *info,
+                   const double2 *a_init)
+{
+    HpRun R;
+    R.p = p;
+    R.d = d;
+    R.nv = nv;
+    R.mask = mask;
+    R.C_ell = C_ell;
+    R.tol = tol;
+    R.fluct = fluct;
+    R.g1 = g1;
+    R.g2 = g2;
+    R.s_out = s_out;
+    R.alm_out = alm_out;
+    R.info = info;
+    R.a_init = a_init;
+    wf_status st = hp_begin(R);
+    if (st != WF_OK) return st;
+    while (hp_pick(R)) {
+        if ((st = hp_launch(R)) != WF_OK) return st;
+        WF_CUDA(cudaStreamSynchronize(p->stream));
+        if (!hp_absorb(R)) break;
+    }
+    return hp_end(R);
+}
+
+// Several HEALPix solves advanced together: one step of every active solve
+// (its iteration's kernels on its own branch stream) is captured in one CUDA
+// graph and launched at once; the host then reads every solve's sums and runs
+// its schedule.  The graph is replayed while every solve keeps its (lambda,
+// L), and updated in place (or re-instantiated) when one changes or a solve
+// leaves the batch.  The iterate is copied a <- a_new inside the step, so the
+// captured pointers stay valid from one step to the next.
+wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cudaStream_t user,
+                         wf_status *statuses)
+{
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || plans[i]->g.kind != WF_GEOM_HEALPIX)
+            return set_error(WF_EINVAL, "batch item %d: needs a HEALPix plan", i);
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return set_error(WF_EINVAL, "batch items %d and %d share a plan", j, i);
+        const wf_batch_item &it = items[i];
+        if (it.kind != WF_REQ_WF && it.kind != WF_REQ_FLUCT)
+            return set_error(WF_EINVAL, "batch item %d: kind must be WF_REQ_WF or WF_REQ_FLUCT", i);
+        if (!it.noise_var || !it.C_ell || !it.s_out || (it.kind == WF_REQ_WF && !it.d) ||
+            (it.kind == WF_REQ_FLUCT && (!it.g1 || !it.g2)) || !(it.tol > 0))
+            return set_error(WF_EINVAL, "batch item %d: missing buffer or bad tol", i);
+        if (defaults(plans[i]->opt).schedule == 1 && plans[i]->replay_lambda.empty())
+            return set_error(WF_EUNSUPPORTED, "batch item %d: the chi^2-bound schedule synchronises inside an "
+                                              "iteration and cannot be batched", i);
+    }
+    auto ck = [](cudaError_t e, const char *what) { return e == cudaSuccess ? WF_OK : cuda_check(e, what); };
+    std::vector<cudaStream_t> saved(n), branch(n, nullptr);
+    std::vector<cudaEvent_t> join(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaStream_t origin = nullptr;  // capture stream (the caller's may be the legacy one, which cannot be captured)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<HpRun> R(n);
+    std::vector<char> active(n, 0);
+    std::vector<std::array<long long, WF_NK>> per_step(n);
+    wf_status st = WF_OK;
+    auto bind = [](wf_plan p, cudaStream_t s) {
+        for (; p; p = p->sub) p->stream = s;
+    };
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (int i = 0; i < n; ++i) {
+            if (branch[i]) {
+                cudaStreamSynchronize(branch[i]);
+                bind(plans[i], saved[i]);
+                cudaStreamDestroy(branch[i]);
+            }
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (origin) {
+            cudaStreamSynchronize(origin);
+            cudaStreamDestroy(origin);
+        }
+    };
+    // work queued on the plans' own streams finishes before their branch streams take over
+    for (int i = 0; i < n; ++i) {
+        saved[i] = plans[i]->stream;
+        if (saved[i]) WF_CUDA(cudaStreamSynchronize(saved[i]));
+    }
+    WF_CUDA(cudaStreamSynchronize(user));
+    if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
+        cleanup();
+        return set_error(WF_ECUDA, "cudaEventCreate failed");
+    }
+    for (int i = 0; i < n; ++i) {
+        if (cudaStreamCreateWithFlags(&branch[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return set_error(WF_ECUDA, "batch stream or event creation failed");
+        }
+        bind(plans[i], branch[i]);
+    }
+    for (int i = 0; i < n; ++i) {
+        const wf_batch_item &it = items[i];
+        HpRun &r = R[i];
+        r.p = plans[i];
+        r.fluct = it.kind == WF_REQ_FLUCT;
+        r.d = it.d;
+        r.nv = it.noise_var;
+        r.mask = it.mask;
+        r.C_ell = it.C_ell;
+        r.g1 = it.g1;
+        r.g2 = it.g2;
+        r.tol = it.tol;
+        r.s_out = it.s_out;
+        r.alm_out = it.alm_out;
+        r.info = it.info;
+        r.copy_back = true;
+        r.graph = true;
+        statuses[i] = hp_begin(r);
+        active[i] = statuses[i] == WF_OK;
+    }
+    std::vector<std::pair<int, std::pair<double, int>>> cfg, cur;
+    for (;;) {
+        cfg.clear();
+        for (int i = 0; i < n; ++i)
+            if (active[i]) {
+                if (!hp_pick(R[i])) active[i] = 0;
+                else cfg.push_back({i, {R[i].lam, R[i].L}});
+            }
+        if (cfg.empty()) break;
+        if (!exec || cfg != cur) {
+            cudaGraph_t ng = nullptr;
+            if ((st = ck(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal), "capture"))) break;
+            cudaEventRecord(fork, origin);
+            for (auto &c : cfg) {
+                const int i = c.first;
+                wf_plan p = plans[i];
+                cudaStreamWaitEvent(branch[i], fork, 0);
+                long long k0[WF_NK];
+                for (int f = 0; f < WF_NK; ++f) k0[f] = p->kcnt[f];
+                st = hp_launch(R[i]);
+                for (int f = 0; f < WF_NK; ++f) {
+                    per_step[i][f] = p->kcnt[f] - k0[f];
+                    p->kcnt[f] = k0[f];  // counted when the graph runs
+                }
+                if (st != WF_OK) break;
+                cudaEventRecord(join[i], branch[i]);
+                cudaStreamWaitEvent(origin, join[i], 0);
+            }
+            cudaError_t ce = cudaStreamEndCapture(origin, &ng);
+            if (st == WF_OK) st = ck(ce, "cudaStreamEndCapture");
+            if (st != WF_OK) {
+                if (ng) cudaGraphDestroy(ng);
+                break;
+            }
+            if (exec) {
+                cudaGraphExecUpdateResultInfo ui;
+                if (cudaGraphExecUpdate(exec, ng, &ui) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(exec);
+                    exec = nullptr;
+                }
+            }
+            if (!exec && (st = ck(cudaGraphInstantiate(&exec, ng, 0), "cudaGraphInstantiate")) != WF_OK) {
+                cudaGraphDestroy(ng);
+                break;
+            }
+            if (graph) cudaGraphDestroy(graph);
+            graph = ng;
+            cur = cfg;
+        }
+        if ((st = ck(cudaGraphLaunch(exec, origin), "cudaGraphLaunch")) != WF_OK) break;
+        if ((st = ck(cudaStreamSynchronize(origin), "batch step")) != WF_OK) break;
+        for (auto &c : cfg) {
+            const int i = c.first;
+            for (int f = 0; f < WF_NK; ++f) plans[i]->kcnt[f] += per_step[i][f];
+            if (!hp_absorb(R[i])) active[i] = 0;
+        }
+    }
+    if (st == WF_OK)
+        for (int i = 0; i < n; ++i)
+            if (statuses[i] == WF_OK) statuses[i] = hp_end(R[i]);
+    cleanup();
+    return st;
 }
 
 wf_status hp_create(wf_plan p)
@@ -1187,6 +1480,14 @@ wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const ui
         return flat_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
     }
     return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
+}
+
+wf_status wf_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, void *cuda_stream, wf_status *statuses)
+{
+    if (n < 0 || (n > 0 && (!plans || !items || !statuses))) return set_error(WF_EINVAL, "null argument");
+    if (n == 0) return WF_OK;
+    for (int i = 0; i < n; ++i) statuses[i] = WF_EINVAL;
+    return hp_solve_batch(n, plans, items, (cudaStream_t)cuda_stream, statuses);
 }
 
 wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, const double *C_ell, const double *g1,

@@ -172,16 +172,18 @@ wf_status raise_smem_limit(const void *func, size_t bytes);
 // Per-call kernel accounting: launch counts always; device time per kernel
 // family with CUDA events on the plan's stream when profiling is on.
 struct Prof {
-    wf_plan p;
-    wf_info *info;
-    bool on;
+    wf_plan p = nullptr;
+    wf_info *info = nullptr;
+    bool on = false;
     int nopen = 0;
     int fam[16];
     long long launches = 0;
     double ms[WF_NK] = {};
     long long cnt[WF_NK] = {};
     long long k0[WF_NK] = {};  // plan launch counters when this accounting started
-    Prof(wf_plan p_, wf_info *i, bool profile);
+    Prof() = default;
+    Prof(wf_plan p_, wf_info *i, bool profile) { init(p_, i, profile); }
+    void init(wf_plan p_, wf_info *i, bool profile);
     void begin(int family);  // call before the launches of a stage of `family`
     void end();              // call after them
     void collect();          // after a stream synchronisation: harvest event times

@@ -945,6 +945,23 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
         t.lc_mx = -1;
         if ((st = hp_set_low_block(p, 0)) != WF_OK) return st;
     }
+    // raise the shared-memory limits of every Legendre kernel this plan can launch to
+    // their lmax sizes now, so that no launch (e.g. inside a graph capture) needs to
+    if (f32) {
+        if ((st = raise_smem_limit((const void *)k_legsyn_mx, syn_mx_smem(lmax))) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_legana_mx, ana_mx_smem(lmax))) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_legsyn<double, float>, syn_smem<double>(lmax))) != WF_OK)
+            return st;
+        if ((st = raise_smem_limit((const void *)k_legana<double, float, 16, true>, ana_smem<double, 16>(lmax))) !=
+            WF_OK)
+            return st;
+    } else {
+        if ((st = raise_smem_limit((const void *)k_legsyn<double, double>, syn_smem<double>(lmax))) != WF_OK)
+            return st;
+        if ((st = raise_smem_limit((const void *)k_legana<double, double, 16, false>, ana_smem<double, 16>(lmax))) !=
+            WF_OK)
+            return st;
+    }
     WF_CUDA(cudaStreamSynchronize(p->stream));
     return WF_OK;
 }
