@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-maxiter", type=int, default=3000)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default Legendre tiles")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="batching workload instead: this many solves of mixed nside (64-256), "
+                         "run one by one and as one wf_solve_batch")
     ap.add_argument("--full-band-iters", type=int, default=0,
                     help="replay this many lambda = 1, L = lmax iterations instead of the cooling schedule "
                          "(steady-state timing and profiling)")
@@ -247,6 +251,7 @@ def run_ours(args):
     P = make_problem(nside, lmax, rank)
     stream = torch.cuda.current_stream()
     plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=args.precision)
+    tiles = wf.wf_plan_tiles(plan) if args.no_autotune else wf.wf_plan_autotune(plan)
     T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     # data = signal (synthesised by the library's own basis change) + noise
     a_sig = T(P["a_signal"])
@@ -325,7 +330,8 @@ def run_ours(args):
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
-                      "tol": args.tol, "schedule": args.schedule, "l2": "inputs (1.2 GB) larger than L2",
+                      "tol": args.tol, "schedule": args.schedule, "legendre_tiles": list(tiles),
+                      "l2": "inputs (1.2 GB) larger than L2",
                       "parallelism": "replicas"},
            "time_to_tol_s": t_ms / args.steps / 1e3 if last["converged"] else None,
            "time_to_residual_s": time_to_residual(last), "iters_per_solve": last["iters"],
@@ -499,12 +505,86 @@ def run_serve(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# batching workload: many small solves, one by one vs one wf_solve_batch call
+# --------------------------------------------------------------------------
+def run_batch(args):
+    import torch
+
+    import paper_1210_4931_gb300 as wf
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wf.load()
+    rng = np.random.default_rng(gen.seed_for(4, 0))
+    n = args.batch
+    nsides = rng.choice([64, 128, 256], size=n)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    items, geo = [], []
+    for i, ns in enumerate(nsides):
+        ns = int(ns)
+        lmax = 2 * ns
+        P = gen.healpix_problem(ns, lmax, gen.seed_for(4, 10 + i), cl=gen.cmb_like_cl(lmax, 5.0 * 2048 / ns),
+                                b_cut_deg=20.0, n_disks=100, disk_radius_deg=1.0)
+        helper = wf.wf_plan_create("healpix", nside=ns, lmax=lmax, precision="fp64")
+        s = torch.empty(helper.npix, dtype=torch.float64, device=dev)
+        wf.wf_alm2map(helper, T(P["a_signal"]), lmax, s)
+        helper.close()
+        items.append({"kind": "wf", "d": s + T(P["noise"]), "noise_var": T(P["noise_var"]), "mask": T(P["mask"]),
+                      "C_ell": T(P["c_ell"]), "tol": 1e-5, "s_out": torch.empty_like(s)})
+        geo.append((ns, lmax))
+    plans = [wf.wf_plan_create("healpix", nside=ns, lmax=l, precision="mixed") for ns, l in geo]
+    for pl in plans:
+        wf.wf_plan_autotune(pl, reps=2)
+    stream = torch.cuda.current_stream()
+
+    def one_by_one():
+        reps = []
+        for pl, it in zip(plans, items):
+            reps.append(wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], it["tol"], it["s_out"]))
+        return reps
+
+    def batched():
+        return wf.wf_solve_batch(plans, items)
+
+    out = {}
+    for name, fn in (("one_by_one", one_by_one), ("batched", batched)):
+        fn()  # warm: graphs, pooled tables
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            e0.record(stream)
+            reps = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        iters = sum(r["iters"] for r in reps)
+        out[name] = {"ms": float(np.median(ts)), "iters": iters, "solves_per_s": n / (np.median(ts) / 1e3),
+                     "iters_per_s": iters / (np.median(ts) / 1e3),
+                     "converged": int(sum(r["converged"] for r in reps))}
+    res = {"metric": "batched solves: Wiener filters of mixed nside 64-256 per second", "unit": "solves/s",
+           "value": out["batched"]["solves_per_s"], "n_gpus": 1, "higher_is_better": True, "batch": n,
+           "nsides": [int(x) for x in nsides], "one_by_one": out["one_by_one"], "batched": out["batched"],
+           "speedup": out["one_by_one"]["ms"] / out["batched"]["ms"], "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "batch_T_nside64-256", "precision": "mixed", "tol": 1e-5,
+                      "timing": "CUDA events around the whole call, median of --steps runs"}}
+    for pl in plans:
+        pl.close()
+    if rank == 0:
+        print(json.dumps(res))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.batch > 0:
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -195,6 +195,14 @@ long long wf_plan_device_bytes(wf_plan p);
  * it (upper estimate; with_host_staging adds the buffers of the *_host entry
  * points).  -1 for an invalid geometry. */
 long long wf_plan_estimate_bytes(const wf_geometry *g, int lmax, wf_precision prec, int with_host_staging);
+/* Autotuner of the mixed-precision Legendre tiles: times each variant (2, 4
+ * or 8 ring pairs per thread in the synthesis, per lane in the analysis) on
+ * this plan's own buffers at the full band and keeps the fastest; reps timed
+ * launches per variant (<= 0: 3).  FP64 and flat plans: no effect.  Overwrites
+ * the plan's iterate buffers (call it between solves).  wf_plan_tiles reports
+ * the current choice (defaults 4 and 8). */
+wf_status wf_plan_autotune(wf_plan p, int reps);
+wf_status wf_plan_tiles(wf_plan p, int *syn_pairs, int *ana_pairs);
 /* Move the plan to another CUDA stream (waits for work queued on the old one). */
 wf_status wf_plan_set_stream(wf_plan p, void *cuda_stream);
 /* wf_fluct with HOST buffers (copies in, solves, copies the map out). */

@@ -94,7 +94,8 @@ EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedu
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
            "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
            "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
-           "wf_server_wait", "wf_server_get_stats", "wf_server_destroy", "wf_solve_batch"]
+           "wf_server_wait", "wf_server_get_stats", "wf_server_destroy", "wf_solve_batch", "wf_plan_autotune",
+           "wf_plan_tiles"]
 
 
 def load(path: str = LIB_PATH):
@@ -141,6 +142,10 @@ def load(path: str = LIB_PATH):
     L.wf_server_wait.restype = ctypes.c_int
     L.wf_server_get_stats.argtypes = [vp, ctypes.POINTER(wf_server_stats)]
     L.wf_server_get_stats.restype = ctypes.c_int
+    L.wf_plan_autotune.argtypes = [vp, ctypes.c_int]
+    L.wf_plan_autotune.restype = ctypes.c_int
+    L.wf_plan_tiles.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.wf_plan_tiles.restype = ctypes.c_int
     L.wf_solve_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(wf_batch_item), vp,
                                  ctypes.POINTER(ctypes.c_int)]
     L.wf_solve_batch.restype = ctypes.c_int
@@ -365,6 +370,19 @@ def wf_fluct_host(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_ou
     return _info_dict(st, info, bufs)
 
 
+def wf_plan_autotune(plan: Plan, reps: int = 3) -> tuple:
+    """Time the mixed Legendre tile variants on this plan and keep the fastest;
+    returns (synthesis pairs per thread, analysis pairs per lane)."""
+    _check(load().wf_plan_autotune(plan.handle, int(reps)), "wf_plan_autotune")
+    return wf_plan_tiles(plan)
+
+
+def wf_plan_tiles(plan: Plan) -> tuple:
+    s, a = ctypes.c_int(), ctypes.c_int()
+    _check(load().wf_plan_tiles(plan.handle, ctypes.byref(s), ctypes.byref(a)), "wf_plan_tiles")
+    return int(s.value), int(a.value)
+
+
 def wf_solve_batch(plans, items, trace_cap=0, stream=None) -> list:
     """Several solves advanced together (one CUDA graph per step).  items:
     dicts with kind ('wf' or 'fluct'), d / g1 / g2, noise_var, mask, C_ell, tol,
@@ -508,6 +526,6 @@ def wf_map2alm_adjoint(plan: Plan, map_in, L, alm_out):
                                      _ptr(alm_out, None, plan.nalm * 16, "alm")), "wf_map2alm_adjoint")
 
 
-__all__ = ["Plan", "Server", "WfError", "load", "wf_fluct_host", "wf_plan_estimate_bytes", "wf_solve_batch", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
+__all__ = ["Plan", "Server", "WfError", "load", "wf_fluct_host", "wf_plan_estimate_bytes", "wf_solve_batch", "wf_plan_autotune", "wf_plan_tiles", "wf_alm2map", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct", "wf_map2alm_adjoint", "wf_plan_create",
            "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "EXPORTS",
            "LIB_PATH"]

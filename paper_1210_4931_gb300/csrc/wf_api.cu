@@ -1456,6 +1456,24 @@ long long wf_plan_estimate_bytes(const wf_geometry *g, int lmax, wf_precision pr
     return wf::hp_estimate_bytes(g->nside, lmax, prec, with_host_staging != 0);
 }
 
+wf_status wf_plan_autotune(wf_plan p, int reps)
+{
+    if (!p) return set_error(WF_EINVAL, "null plan");
+    if (p->g.kind != WF_GEOM_HEALPIX) return WF_OK;
+    wf_status st = hp_autotune(p, reps);
+    if (st != WF_OK) return st;
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    return WF_OK;
+}
+
+wf_status wf_plan_tiles(wf_plan p, int *syn_pairs, int *ana_pairs)
+{
+    if (!p) return set_error(WF_EINVAL, "null plan");
+    if (syn_pairs) *syn_pairs = p->tile_syn;
+    if (ana_pairs) *ana_pairs = p->tile_ana;
+    return WF_OK;
+}
+
 wf_status wf_plan_set_stream(wf_plan p, void *cuda_stream)
 {
     if (!p) return set_error(WF_EINVAL, "null plan");

@@ -137,6 +137,7 @@ struct wf_plan_s {
     cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
     wf_plan sub = nullptr;    // mixed precision: FP64 plan of the same geometry for the correction sweeps
     bool events_ready = false;
+    int tile_syn = 4, tile_ana = 8;  // mixed Legendre tiles: ring pairs per thread / per lane
     cudaStream_t aux = nullptr;      // mixed precision: stream of the FP64 low-l block
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     long long kcnt[WF_NK] = {};  // kernels launched on this plan, by family (WF_K_*)
@@ -203,6 +204,7 @@ struct BlendArgs {
     int want_resid = 0;
 };
 wf_status hp_set_low_block(wf_plan p, int lc);
+wf_status hp_autotune(wf_plan p, int reps);
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L);
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old,
                                double2 *out);

@@ -16,9 +16,10 @@
 //
 // Two precisions:
 //   FP64     k_legsyn<double>, k_legana<double,...>: one ring pair per thread.
-//   mixed    k_legsyn_mx, k_legana_mx: FP32 recurrence and contraction, four
-//            (synthesis) or eight (analysis) ring pairs per thread in packed
-//            f32x2 lanes (__ffma2_rn).
+//   mixed    k_legsyn_mx<NP>, k_legana_mx<NP, CH>: FP32 recurrence and
+//            contraction, NP ring pairs per thread (synthesis) or per lane
+//            (analysis) in packed f32x2 lanes (__ffma2_rn); NP is the plan's
+//            tile choice (4 and 8 by default, or what wf_plan_autotune timed).
 //            Near the poles the plain recurrence mu_l = A x mu_{l-1} - mu_{l-2}
 //            loses ~1/sin(theta) digits (its two characteristic roots merge
 //            at x = 1), so rings with x > 0.4 run the same recurrence in
@@ -41,8 +42,8 @@ namespace wf {
 namespace {
 
 constexpr double SEED_LOG2_THRESHOLD = -80.0;
-constexpr int MXP = 4;               // ring pairs per thread in the mixed synthesis
-constexpr int MXPA = 8;              // ring pairs per lane in the mixed analysis
+// ring pairs per thread (mixed synthesis) and per lane (mixed analysis): the
+// plan's tile choice, 4 and 8 unless wf_plan_autotune measured better
 constexpr float X_DIFFERENCE_FORM = 0.4f;
 constexpr int BIG = INT_MAX / 2;
 
@@ -554,21 +555,21 @@ __device__ __forceinline__ void mx_step(const MxPairs<NP> &P, int l, float A0, f
     }
 }
 
-template <bool DIFF>
-__device__ __forceinline__ void mx_syn_run(const MxPairs<MXP> &P, int m, int L, const float4 *__restrict__ sAB,
-                                           const float4 *__restrict__ sac, float2 (&ER)[MXP / 2],
-                                           float2 (&EI)[MXP / 2], float2 (&OR)[MXP / 2], float2 (&OI)[MXP / 2])
+template <bool DIFF, int NP>
+__device__ __forceinline__ void mx_syn_run(const MxPairs<NP> &P, int m, int L, const float4 *__restrict__ sAB,
+                                           const float4 *__restrict__ sac, float2 (&ER)[NP / 2],
+                                           float2 (&EI)[NP / 2], float2 (&OR)[NP / 2], float2 (&OI)[NP / 2])
 {
-    float2 Sa[MXP / 2], Sb[MXP / 2], V0[MXP / 2], V1[MXP / 2];
+    float2 Sa[NP / 2], Sb[NP / 2], V0[NP / 2], V1[NP / 2];
 #pragma unroll
-    for (int pk = 0; pk < MXP / 2; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
+    for (int pk = 0; pk < NP / 2; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
     int l = P.lmin;
     for (; l <= L && l <= P.lmaxs; l += 2) {
         const int j = (l - m) >> 1;
         const float4 ab = sAB[j], ac = sac[j];
-        mx_step<DIFF, true, MXP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
+        mx_step<DIFF, true, NP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
 #pragma unroll
-        for (int pk = 0; pk < MXP / 2; ++pk) {
+        for (int pk = 0; pk < NP / 2; ++pk) {
             ER[pk] = __ffma2_rn(dup(ac.x), V0[pk], ER[pk]);
             EI[pk] = __ffma2_rn(dup(ac.y), V0[pk], EI[pk]);
             OR[pk] = __ffma2_rn(dup(ac.z), V1[pk], OR[pk]);
@@ -578,9 +579,9 @@ __device__ __forceinline__ void mx_syn_run(const MxPairs<MXP> &P, int m, int L, 
     for (; l <= L; l += 2) {
         const int j = (l - m) >> 1;
         const float4 ab = sAB[j], ac = sac[j];
-        mx_step<DIFF, false, MXP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
+        mx_step<DIFF, false, NP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
 #pragma unroll
-        for (int pk = 0; pk < MXP / 2; ++pk) {
+        for (int pk = 0; pk < NP / 2; ++pk) {
             ER[pk] = __ffma2_rn(dup(ac.x), V0[pk], ER[pk]);
             EI[pk] = __ffma2_rn(dup(ac.y), V0[pk], EI[pk]);
             OR[pk] = __ffma2_rn(dup(ac.z), V1[pk], OR[pk]);
@@ -591,6 +592,7 @@ __device__ __forceinline__ void mx_syn_run(const MxPairs<MXP> &P, int m, int L, 
 
 // shared-memory staging: per pair of l (l = m + 2j, l + 1):
 //   sAB[j] = (A_l, B_l, A_{l+1}, B_{l+1}),  sac[j] = (Re a'_l, Im a'_l, Re a'_{l+1}, Im a'_{l+1})
+template <int NP>
 __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int npairs,
                                                            const double2 *__restrict__ alm,
                                                            const float *__restrict__ A, const float *__restrict__ B,
@@ -632,18 +634,18 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
     }
     __syncthreads();
     const size_t pstride = (size_t)(lmax + 1) * 2;
-    for (int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * MXP; p0 < npairs; p0 += gridDim.x * blockDim.x * MXP) {
-        MxPairs<MXP> P;
-        mx_load_pairs<MXP>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
-        float2 ER[MXP / 2], EI[MXP / 2], OR[MXP / 2], OI[MXP / 2];
+    for (int p0 = (blockIdx.x * blockDim.x + threadIdx.x) * NP; p0 < npairs; p0 += gridDim.x * blockDim.x * NP) {
+        MxPairs<NP> P;
+        mx_load_pairs<NP>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
+        float2 ER[NP / 2], EI[NP / 2], OR[NP / 2], OI[NP / 2];
 #pragma unroll
-        for (int pk = 0; pk < MXP / 2; ++pk) ER[pk] = EI[pk] = OR[pk] = OI[pk] = dup(0.f);
+        for (int pk = 0; pk < NP / 2; ++pk) ER[pk] = EI[pk] = OR[pk] = OI[pk] = dup(0.f);
         if (P.lmin <= L) {
-            if (P.diff) mx_syn_run<true>(P, m, L, sAB, sac, ER, EI, OR, OI);
-            else mx_syn_run<false>(P, m, L, sAB, sac, ER, EI, OR, OI);
+            if (P.diff) mx_syn_run<true, NP>(P, m, L, sAB, sac, ER, EI, OR, OI);
+            else mx_syn_run<false, NP>(P, m, L, sAB, sac, ER, EI, OR, OI);
         }
 #pragma unroll
-        for (int k = 0; k < MXP; ++k) {
+        for (int k = 0; k < NP; ++k) {
             const int p = p0 + k;
             if (p >= npairs) break;
             const int pk = k >> 1, h = k & 1;
@@ -655,33 +657,32 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
     }
 }
 
-// analysis: CTA per m; a warp covers 32 lanes x MXPA pairs; chunks of MX_CH
+// analysis: CTA per m; a warp covers 32 lanes x NP pairs; chunks of CH
 // values of l accumulate the packs in f32x2 registers, then are summed over
 // the pack lanes and reduced across the warp.  Eight pairs per lane halve the
 // cross-lane reduction per (l, m, pair) against four; two CTAs per SM (128
 // registers) measured faster than one CTA with no spills.
-constexpr int MX_CH = 8;
 
-template <bool DIFF>
-__device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L, int lmin_w,
+template <bool DIFF, int NP, int CH>
+__device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, int lmin_w,
                                            const float *__restrict__ sA, const float *__restrict__ sB,
-                                           const float2 (&FEr)[MXPA / 2], const float2 (&FEi)[MXPA / 2],
-                                           const float2 (&FOr)[MXPA / 2], const float2 (&FOi)[MXPA / 2],
+                                           const float2 (&FEr)[NP / 2], const float2 (&FEi)[NP / 2],
+                                           const float2 (&FOr)[NP / 2], const float2 (&FOi)[NP / 2],
                                            float2 *acc, int lane)
 {
-    constexpr int NPK = MXPA / 2;
+    constexpr int NPK = NP / 2;
     float2 Sa[NPK], Sb[NPK], V0[NPK], V1[NPK];
 #pragma unroll
     for (int pk = 0; pk < NPK; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
-    for (int l0 = lmin_w; l0 <= L; l0 += MX_CH) {
-        float2 AR[MX_CH], AI[MX_CH];
+    for (int l0 = lmin_w; l0 <= L; l0 += CH) {
+        float2 AR[CH], AI[CH];
         const bool inj = l0 <= P.lmaxs;
 #pragma unroll
-        for (int i = 0; i < MX_CH; i += 2) {
+        for (int i = 0; i < CH; i += 2) {
             const int j = l0 - m + i;
             const float A0 = sA[j], B0 = sB[j], A1 = sA[j + 1], B1 = sB[j + 1];
-            if (inj) mx_step<DIFF, true, MXPA>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
-            else mx_step<DIFF, false, MXPA>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
+            if (inj) mx_step<DIFF, true, NP>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
+            else mx_step<DIFF, false, NP>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
             AR[i] = __fmul2_rn(FEr[0], V0[0]);
             AI[i] = __fmul2_rn(FEi[0], V0[0]);
             AR[i + 1] = __fmul2_rn(FOr[0], V1[0]);
@@ -694,14 +695,14 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L,
                 AI[i + 1] = __ffma2_rn(FOi[pk], V1[pk], AI[i + 1]);
             }
         }
-        float vr[MX_CH], vi[MX_CH];
+        float vr[CH], vi[CH];
 #pragma unroll
-        for (int i = 0; i < MX_CH; ++i) {
+        for (int i = 0; i < CH; ++i) {
             vr[i] = AR[i].x + AR[i].y;
             vi[i] = AI[i].x + AI[i].y;
         }
-        warp_reduce_scatter<float, MX_CH>(vr, vi, lane);
-        constexpr int sh = 5 - Log2<MX_CH>::v;  // each l ends in 2^sh lanes
+        warp_reduce_scatter<float, CH>(vr, vi, lane);
+        constexpr int sh = 5 - Log2<CH>::v;  // each l ends in 2^sh lanes
         if ((lane & ((1 << sh) - 1)) == 0) {
             const int l = l0 + (lane >> sh);
             if (l <= L) {
@@ -712,6 +713,7 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<MXPA> &P, int m, int L,
     }
 }
 
+template <int NP, int CH>
 __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, int npairs, int lc,
                                                            const float2 *__restrict__ F, const float *__restrict__ A,
                                                            const float *__restrict__ B,
@@ -729,7 +731,7 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
     __shared__ int next_group;
     const int m = blockIdx.x;
     const int nl = L - m + 1;
-    const int nlp = nl + MX_CH + 2;
+    const int nlp = nl + CH + 2;
     const long long base = mbase(lmax, m);
     // FP32 accumulators: each entry sums one 32-lane reduce-scatter result per
     // group of 128 ring pairs; the epilogue converts to FP64
@@ -744,7 +746,7 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
     if (threadIdx.x == 0) next_group = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int per_group = 32 * MXPA;
+    const int per_group = 32 * NP;
     const int ngroups = (npairs + per_group - 1) / per_group;
     const size_t pstride = (size_t)(lmax + 1) * 2;
     for (;;) {
@@ -753,16 +755,16 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
         if (lane == 0) grp = atomicAdd(&next_group, 1);
         grp = __shfl_sync(0xffffffffu, grp, 0);
         if (grp >= ngroups) break;
-        const int p0 = grp * per_group + lane * MXPA;
-        MxPairs<MXPA> P;
-        mx_load_pairs<MXPA>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
+        const int p0 = grp * per_group + lane * NP;
+        MxPairs<NP> P;
+        mx_load_pairs<NP>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
         // one recurrence form per warp: the shuffles below need warp-uniform control flow
         P.diff = __shfl_sync(0xffffffffu, P.diff ? 1 : 0, 0) != 0;
         const int lmin_w = __reduce_min_sync(0xffffffffu, P.lmin);
         if (lmin_w > L) continue;
-        float fer[MXPA], fei[MXPA], forr[MXPA], foi[MXPA];
+        float fer[NP], fei[NP], forr[NP], foi[NP];
 #pragma unroll
-        for (int k = 0; k < MXPA; ++k) {
+        for (int k = 0; k < NP; ++k) {
             fer[k] = fei[k] = forr[k] = foi[k] = 0.f;
             if (P.ls[k] != BIG) {
                 const float2 *f = F + (size_t)(p0 + k) * pstride + 2 * (size_t)m;
@@ -773,16 +775,16 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
                 foi[k] = fn.y - fs.y;
             }
         }
-        float2 FEr[MXPA / 2], FEi[MXPA / 2], FOr[MXPA / 2], FOi[MXPA / 2];
+        float2 FEr[NP / 2], FEi[NP / 2], FOr[NP / 2], FOi[NP / 2];
 #pragma unroll
-        for (int pk = 0; pk < MXPA / 2; ++pk) {
+        for (int pk = 0; pk < NP / 2; ++pk) {
             FEr[pk] = make_float2(fer[2 * pk], fer[2 * pk + 1]);
             FEi[pk] = make_float2(fei[2 * pk], fei[2 * pk + 1]);
             FOr[pk] = make_float2(forr[2 * pk], forr[2 * pk + 1]);
             FOi[pk] = make_float2(foi[2 * pk], foi[2 * pk + 1]);
         }
-        if (P.diff) mx_ana_run<true>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
-        else mx_ana_run<false>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+        if (P.diff) mx_ana_run<true, NP, CH>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+        else mx_ana_run<false, NP, CH>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
     }
     __syncthreads();
     const int low_lim = (low && m < lc) ? lcm_of(lc, m) : 0;
@@ -799,7 +801,7 @@ template <typename T, int CH>
 size_t ana_smem(int L) { return (size_t)(L + 1 + CH + 2) * (sizeof(double2) + sizeof(T)) + 16; }
 
 size_t syn_mx_smem(int L) { return (size_t)((L + 2) / 2 + 2) * 2 * sizeof(float4) + 16; }
-size_t ana_mx_smem(int L) { return (size_t)(L + 1 + MX_CH + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32; }
+size_t ana_mx_smem(int L, int ch) { return (size_t)(L + 1 + ch + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32; }
 
 template <typename TG>
 wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, cx<TG> *G, int gstride, cudaStream_t s)
@@ -948,8 +950,12 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
     // raise the shared-memory limits of every Legendre kernel this plan can launch to
     // their lmax sizes now, so that no launch (e.g. inside a graph capture) needs to
     if (f32) {
-        if ((st = raise_smem_limit((const void *)k_legsyn_mx, syn_mx_smem(lmax))) != WF_OK) return st;
-        if ((st = raise_smem_limit((const void *)k_legana_mx, ana_mx_smem(lmax))) != WF_OK) return st;
+        const void *syn[] = {(const void *)k_legsyn_mx<2>, (const void *)k_legsyn_mx<4>, (const void *)k_legsyn_mx<8>};
+        for (const void *f : syn)
+            if ((st = raise_smem_limit(f, syn_mx_smem(lmax))) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_legana_mx<2, 16>, ana_mx_smem(lmax, 16))) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_legana_mx<4, 16>, ana_mx_smem(lmax, 16))) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_legana_mx<8, 8>, ana_mx_smem(lmax, 8))) != WF_OK) return st;
         if ((st = raise_smem_limit((const void *)k_legsyn<double, float>, syn_smem<double>(lmax))) != WF_OK)
             return st;
         if ((st = raise_smem_limit((const void *)k_legana<double, float, 16, true>, ana_smem<double, 16>(lmax))) !=
@@ -1007,6 +1013,21 @@ wf_status join_aux(wf_plan p)
     return WF_OK;
 }
 
+template <int NP>
+wf_status launch_syn_mx(wf_plan p, const double2 *alm, int L)
+{
+    const HpTables &t = p->tab;
+    const int gx = (p->npairs + NP * LEG_THREADS - 1) / (NP * LEG_THREADS);
+    dim3 grid(gx, L + 1);
+    const size_t sm = syn_mx_smem(L);
+    if (wf_status st = raise_smem_limit((const void *)k_legsyn_mx<NP>, sm)) return st;
+    k_legsyn_mx<NP><<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, t.A32, t.B32, t.c64, t.ls_mx,
+                                                           t.s0_mx, t.s1_mx, t.x32, t.w32, (float2 *)p->ws.G);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
 {
     const HpTables &t = p->tab;
@@ -1017,33 +1038,89 @@ wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
         if ((st = fork_aux(p)) != WF_OK) return st;
         if ((st = launch_syn64<float>(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux)) != WF_OK) return st;
     }
-    const int gx = (p->npairs + MXP * LEG_THREADS - 1) / (MXP * LEG_THREADS);
-    dim3 grid(gx, L + 1);
-    const size_t sm = syn_mx_smem(L);
-    if ((st = raise_smem_limit((const void *)k_legsyn_mx, sm)) != WF_OK) return st;
-    k_legsyn_mx<<<grid, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, t.A32, t.B32, t.c64, t.ls_mx,
-                                                       t.s0_mx, t.s1_mx, t.x32, t.w32, (float2 *)p->ws.G);
-    WF_COUNT_LAUNCH(p);
-    WF_CUDA(cudaGetLastError());
+    switch (p->tile_syn) {
+    case 2: st = launch_syn_mx<2>(p, alm, L); break;
+    case 8: st = launch_syn_mx<8>(p, alm, L); break;
+    default: st = launch_syn_mx<4>(p, alm, L); break;
+    }
+    if (st != WF_OK) return st;
     if (low) return join_aux(p);
     return WF_OK;
 }
 
 namespace {
-wf_status launch_ana_mx(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *low, const double2 *a_old,
-                        double2 *out)
+template <int NP, int CH>
+wf_status launch_ana_mx_t(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *low,
+                          const double2 *a_old, double2 *out)
 {
     const HpTables &t = p->tab;
-    const size_t sm = ana_mx_smem(L);
-    if (wf_status st = raise_smem_limit((const void *)k_legana_mx, sm)) return st;
-    k_legana_mx<<<L + 1, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, t.lc_mx, (const float2 *)p->ws.F,
-                                                        t.A32, t.B32, t.ls_mx, t.s0_mx, t.s1_mx, t.x32, t.w32, t.c64,
-                                                        (int)mode, p->omega, ba, low, a_old, out, p->ws.part_harm);
+    const size_t sm = ana_mx_smem(L, CH);
+    if (wf_status st = raise_smem_limit((const void *)k_legana_mx<NP, CH>, sm)) return st;
+    k_legana_mx<NP, CH><<<L + 1, LEG_THREADS, sm, p->stream>>>(
+        p->lmax, L, p->npairs, t.lc_mx, (const float2 *)p->ws.F, t.A32, t.B32, t.ls_mx, t.s0_mx, t.s1_mx, t.x32,
+        t.w32, t.c64, (int)mode, p->omega, ba, low, a_old, out, p->ws.part_harm);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
 }
+
+wf_status launch_ana_mx(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *low, const double2 *a_old,
+                        double2 *out)
+{
+    switch (p->tile_ana) {
+    case 2: return launch_ana_mx_t<2, 16>(p, L, mode, ba, low, a_old, out);
+    case 4: return launch_ana_mx_t<4, 16>(p, L, mode, ba, low, a_old, out);
+    default: return launch_ana_mx_t<8, 8>(p, L, mode, ba, low, a_old, out);
+    }
+}
 }  // namespace
+
+// Autotuner of the mixed Legendre tiles: each variant of the synthesis (2, 4
+// or 8 ring pairs per thread) and of the analysis (2, 4 or 8 pairs per lane)
+// runs on this plan's own buffers at the full band; the fastest is kept.
+wf_status hp_autotune(wf_plan p, int reps)
+{
+    if (p->prec == WF_PREC_FP64) return WF_OK;
+    if (reps <= 0) reps = 3;
+    const int L = p->lmax;
+    WF_CUDA(cudaMemsetAsync(p->ws.a, 0, p->nalm * sizeof(double2), p->stream));
+    WF_CUDA(cudaMemsetAsync(p->ws.F, 0, (size_t)p->npairs * (L + 1) * 2 * sizeof(float2), p->stream));
+    cudaEvent_t e0, e1;
+    WF_CUDA(cudaEventCreate(&e0));
+    WF_CUDA(cudaEventCreate(&e1));
+    const int saved_syn = p->tile_syn, saved_ana = p->tile_ana;
+    const int np[3] = {2, 4, 8};
+    float best_syn = 1e30f, best_ana = 1e30f;
+    int pick_syn = saved_syn, pick_ana = saved_ana;
+    wf_status st = WF_OK;
+    BlendArgs none;
+    for (int v = 0; v < 3 && st == WF_OK; ++v) {
+        p->tile_syn = np[v];
+        p->tile_ana = np[v];
+        float ms[2] = {0.f, 0.f};
+        for (int which = 0; which < 2 && st == WF_OK; ++which) {
+            for (int r = -1; r < reps && st == WF_OK; ++r) {  // r = -1: untimed warm-up
+                if (r == 0) cudaEventRecord(e0, p->stream);
+                if (which == 0)
+                    st = np[v] == 2 ? launch_syn_mx<2>(p, p->ws.a, L)
+                                    : np[v] == 8 ? launch_syn_mx<8>(p, p->ws.a, L) : launch_syn_mx<4>(p, p->ws.a, L);
+                else
+                    st = launch_ana_mx(p, L, LEG_ADJOINT, none, nullptr, nullptr, p->ws.b);
+            }
+            cudaEventRecord(e1, p->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms[which], e0, e1);
+        }
+        if (st != WF_OK) break;
+        if (ms[0] < best_syn) { best_syn = ms[0]; pick_syn = np[v]; }
+        if (ms[1] < best_ana) { best_ana = ms[1]; pick_ana = np[v]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->tile_syn = st == WF_OK ? pick_syn : saved_syn;
+    p->tile_ana = st == WF_OK ? pick_ana : saved_ana;
+    return st;
+}
 
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba_in, const double2 *a_old,
                                double2 *out)

@@ -109,3 +109,26 @@ def test_batch_rejections(wf):
         wf.wf_solve_batch([plan], [it])
     assert e.value.status == wf.WF_EUNSUPPORTED
     plan.close()
+
+
+def test_autotuned_tiles_keep_the_results(wf):
+    """The autotuner picks one of the tile variants (2, 4 or 8 ring pairs) and
+    the solve on the tuned plan matches the default-tile solve within the
+    mixed-precision tolerance; FP64 plans are left alone."""
+    import torch
+
+    n, l, p, k, t = 64, 128, "mixed", "wf", 1e-5
+    it = _item(40, n, l, k, t)
+    ref, rep_ref = _alone(wf, n, l, p, it)
+    plan = wf.wf_plan_create("healpix", nside=n, lmax=l, precision=p)
+    assert wf.wf_plan_tiles(plan) == (4, 8)
+    tiles = wf.wf_plan_autotune(plan, reps=2)
+    assert tiles[0] in (2, 4, 8) and tiles[1] in (2, 4, 8)
+    s = torch.empty_like(it["s_out"])
+    rep = wf.wf_solve(plan, it["d"], it["noise_var"], it["mask"], it["C_ell"], t, s)
+    assert rep["final_residual"] < t
+    assert rel(s.cpu().numpy(), ref) < 1e-3
+    plan.close()
+    p64 = wf.wf_plan_create("healpix", nside=16, lmax=32, precision="fp64")
+    assert wf.wf_plan_autotune(p64) == (4, 8)
+    p64.close()
