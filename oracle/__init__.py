@@ -16,6 +16,10 @@ Functions and the paper passage each follows:
 * ``synthesis`` / ``adjoint_synthesis`` -- the basis change between pixel
                                space (where N is diagonal) and harmonic space
                                (where S is diagonal), Sect. 2.1.
+* ``spin_legendre``, ``synthesis_pol`` / ``adjoint_pol`` -- the spin-2 basis
+                               change of the polarised maps (I, Q, U) that
+                               Eqs. (10)-(11) act on, written from the
+                               definition (Q + iU) = sum 2a_lm 2Y_lm over all m.
 * ``FlatBasis`` / ``HealpixBasis`` -- the two bases; ``messenger.py`` runs
                                Eqs. (3)-(4), the chi^2 of Eq. (6), the cooling
                                schedule of Sect. 3 and the fluctuation source
@@ -52,6 +56,13 @@ def _lib():
         lib.or_synthesis.restype = None
         lib.or_adjoint_synthesis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int]
         lib.or_adjoint_synthesis.restype = None
+        lib.or_spin_legendre.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp]
+        lib.or_spin_legendre.restype = None
+        lib.or_synthesis_pol.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ctypes.c_int,
+                                         ctypes.c_int]
+        lib.or_synthesis_pol.restype = None
+        lib.or_adjoint_pol.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        lib.or_adjoint_pol.restype = None
         lib.or_num_threads.argtypes = []
         lib.or_num_threads.restype = ctypes.c_int
         _LIB = lib
@@ -154,6 +165,41 @@ def adjoint_synthesis(nside: int, lmax: int, L: int, f: np.ndarray, ms=None) -> 
     return res
 
 
+def spin_legendre(lmax: int, m: int, s: int, x: float) -> np.ndarray:
+    """slambda_lm(theta) = sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta), l = 0..lmax
+    (zero below max(|m|, |s|)); any sign of m and s.  s = 0 is lambda_lm."""
+    out = np.zeros(lmax + 1)
+    st = float(np.sqrt((1.0 - x) * (1.0 + x)))
+    _lib().or_spin_legendre(lmax, m, s, float(x), st, _dp(out))
+    return out
+
+
+def synthesis_pol(nside: int, lmax: int, L: int, E, B, rings=None):
+    """(Q, U) maps of (Q + iU) = sum_{l>=2, |m|<=l} 2a_lm 2Y_lm, 2a = -(E + iB),
+    l <= L; E, B stored like a_lm (m >= 0).  ``rings`` = (lo, hi) computes
+    only those rings (other pixels NaN)."""
+    e = np.ascontiguousarray(np.asarray(E, dtype=np.complex128)).view(np.float64)
+    b = np.ascontiguousarray(np.asarray(B, dtype=np.complex128)).view(np.float64)
+    assert e.size == b.size == 2 * nalm(lmax)
+    Q = np.full(npix(nside), np.nan)
+    U = np.full(npix(nside), np.nan)
+    lo, hi = (0, 4 * nside - 1) if rings is None else rings
+    _lib().or_synthesis_pol(nside, lmax, L, _dp(e), _dp(b), _dp(Q), _dp(U), lo, hi)
+    return Q, U
+
+
+def adjoint_pol(nside: int, lmax: int, L: int, Q, U):
+    """Adjoint of synthesis_pol: (E, B) with E_lm = -(t_lm + (-1)^m conj t_{l,-m})/2,
+    B_lm = (i/2)(t_lm - (-1)^m conj t_{l,-m}), t_lm = sum_p (Q + iU)_p conj 2Y_lm(p)."""
+    q = np.ascontiguousarray(np.asarray(Q, dtype=np.float64))
+    u = np.ascontiguousarray(np.asarray(U, dtype=np.float64))
+    assert q.size == u.size == npix(nside)
+    e = np.zeros(2 * nalm(lmax))
+    b = np.zeros(2 * nalm(lmax))
+    _lib().or_adjoint_pol(nside, lmax, L, _dp(q), _dp(u), _dp(e), _dp(b))
+    return e.view(np.complex128).copy(), b.view(np.complex128).copy()
+
+
 # --------------------------------------------------------------------------
 # The two bases of Sect. 2.1: pixel space (N diagonal) and harmonic space
 # (S diagonal).  ``synth`` maps harmonic -> pixel; ``adjoint`` is its adjoint
@@ -229,6 +275,7 @@ from .templates import marginalize_templates, template_matrix  # noqa: E402
 __all__ = [
     "FlatBasis",
     "HealpixBasis",
+    "adjoint_pol",
     "adjoint_synthesis",
     "alm_index",
     "alm_lm",
@@ -241,7 +288,9 @@ __all__ = [
     "npix",
     "num_threads",
     "pixel_angles",
+    "spin_legendre",
     "synthesis",
+    "synthesis_pol",
     "template_matrix",
     "wnorm",
 ]

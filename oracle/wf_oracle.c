@@ -273,6 +273,237 @@ void or_adjoint_synthesis(int nside, int lmax, int L, const double *map,
     free(z); free(st); free(p0); free(nr); free(off);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Spin-weighted harmonics (polarisation, Eqs. 10-11 of the paper work on     */
+/* I, Q, U maps).  Convention:                                                */
+/*   sY_lm(theta, phi) = slambda_lm(theta) e^{i m phi},                       */
+/*   slambda_lm(theta) = sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta),               */
+/* with Wigner's small d (explicit sum below); for s = 0 this is the          */
+/* Condon-Shortley Y_lm above.  Polarisation:                                 */
+/*   (Q + iU)(n) = sum_{l >= 2} sum_{m=-l..l} 2a_lm 2Y_lm(n),                 */
+/*   2a_lm = -(E_lm + i B_lm), E_{l,-m} = (-1)^m conj(E_lm) (B alike),        */
+/* E, B stored like a_lm (m >= 0).                                            */
+/* d^j_{ab}(beta) = sum_k (-1)^(a-b+k) sqrt((j+a)!(j-a)!(j+b)!(j-b)!)         */
+/*                  c^(2j+b-a-2k) s^(a-b+2k) / ((j+b-k)! k! (a-b+k)! (j-a-k)!)*/
+/* with c = cos(beta/2), s = sin(beta/2); at j = max(|a|, |b|) exactly one k  */
+/* is allowed, which gives the seed.  Upward in l (a, b fixed):               */
+/*   d^l = l(2l-1)/sqrt((l^2-a^2)(l^2-b^2)) (x - ab/(l(l-1))) d^{l-1}         */
+/*       - l sqrt(((l-1)^2-a^2)((l-1)^2-b^2)) / ((l-1) sqrt((l^2-a^2)(l^2-b^2))) d^{l-2}. */
+/* ------------------------------------------------------------------------- */
+static double lfact(int n) { return lgamma((double)n + 1.0); }
+
+/* slambda_lm(theta) for l = l0 .. lmax, l0 = max(|m|, |s|); out[l - l0].      */
+/* ch = cos(theta/2), sh = sin(theta/2), x = cos(theta).  Returns l0.          */
+static int spin_column(int lmax, int m, int s, double x, double ch, double sh, double *out)
+{
+    const int a = m, b = -s;
+    const int l0 = abs(a) > abs(b) ? abs(a) : abs(b);
+    if (l0 > lmax) return l0;
+    /* seed: the single k of the explicit sum at j = l0 */
+    const int j = l0;
+    int kk = 0;
+    if (a == j) kk = 0;
+    else if (a == -j) kk = j + b;
+    else if (b == j) kk = j - a;
+    else kk = 0; /* b == -j */
+    const int ec = 2 * j + b - a - 2 * kk, es = a - b + 2 * kk;
+    double lg = 0.5 * (lfact(j + a) + lfact(j - a) + lfact(j + b) + lfact(j - b)) -
+                (lfact(j + b - kk) + lfact(kk) + lfact(a - b + kk) + lfact(j - a - kk));
+    const int sign = ((a - b + kk) & 1) ? -1 : 1;
+    if ((ec > 0 && ch == 0.0) || (es > 0 && sh == 0.0)) {
+        for (int l = l0; l <= lmax; ++l) out[l - l0] = 0.0;
+        return l0;
+    }
+    if (ec > 0) lg += ec * log(ch);
+    if (es > 0) lg += es * log(sh);
+    const double ln2 = log(2.0);
+    int E = (int)floor(lg / ln2);
+    double v1 = sign * exp(lg - E * ln2), v0 = 0.0; /* d^{l0} and d^{l0-1} = 0, as v * 2^E */
+    out[0] = ldexp(v1, E) * sqrt((2.0 * l0 + 1.0) / (4.0 * M_PI));
+    for (int l = l0 + 1; l <= lmax; ++l) {
+        const double ll = l, d1 = sqrt((ll * ll - (double)a * a) * (ll * ll - (double)b * b));
+        double v2;
+        if (l == 1) {
+            v2 = x * v1; /* a = b = 0: d^1_00 = cos(theta) */
+        } else {
+            const double c1 = ll * (2.0 * ll - 1.0) / d1 * (x - (double)a * b / (ll * (ll - 1.0)));
+            const double lm1 = ll - 1.0;
+            const double c2 = ll * sqrt((lm1 * lm1 - (double)a * a) * (lm1 * lm1 - (double)b * b)) / (lm1 * d1);
+            v2 = c1 * v1 - c2 * v0;
+        }
+        v0 = v1;
+        v1 = v2;
+        if (fabs(v1) > 0x1p+300) {
+            v0 = ldexp(v0, -300);
+            v1 = ldexp(v1, -300);
+            E += 300;
+        }
+        out[l - l0] = ldexp(v1, E) * sqrt((2.0 * ll + 1.0) / (4.0 * M_PI));
+    }
+    return l0;
+}
+
+static void half_angles(double x, double st, double *ch, double *sh)
+{
+    if (x >= 0.0) {
+        *ch = sqrt(0.5 * (1.0 + x));
+        *sh = st / (2.0 * *ch);
+    } else {
+        *sh = sqrt(0.5 * (1.0 - x));
+        *ch = st / (2.0 * *sh);
+    }
+}
+
+/* slambda_lm(theta) for l = 0 .. lmax (zero below max(|m|, |s|)). */
+void or_spin_legendre(int lmax, int m, int s, double x, double sintheta, double *out)
+{
+    double ch, sh;
+    half_angles(x, sintheta, &ch, &sh);
+    double *col = malloc(sizeof(double) * (lmax + 1));
+    for (int l = 0; l <= lmax; ++l) out[l] = 0.0;
+    const int l0 = spin_column(lmax, m, s, x, ch, sh, col);
+    for (int l = l0; l <= lmax; ++l) out[l] = col[l - l0];
+    free(col);
+}
+
+/* 2a_lm for any m from E, B stored for m >= 0 (re, im interleaved). */
+static inline void two_a(int lmax, const double *E, const double *B, int l, int m, double *re, double *im)
+{
+    const int am = abs(m);
+    const int64_t k = alm_index(lmax, l, am);
+    double er = E[2 * k], ei = E[2 * k + 1], br = B[2 * k], bi = B[2 * k + 1];
+    if (m < 0) { /* E_{l,-m} = (-1)^m conj(E_lm), B alike */
+        const double sg = (am & 1) ? -1.0 : 1.0;
+        er *= sg; ei *= -sg; br *= sg; bi *= -sg;
+    }
+    /* -(E + i B) */
+    *re = -(er - bi);
+    *im = -(ei + br);
+}
+
+/* Polarisation synthesis (Q, U) from (E, B), l <= L, rings [ring_lo, ring_hi):
+ *   P_m(theta_r) = sum_l 2a_lm 2lambda_lm(theta_r),  m = -L..L,
+ *   (Q + iU)_j = sum_m P_m e^{i m phi_j},  evaluated term by term. */
+void or_synthesis_pol(int nside, int lmax, int L, const double *E, const double *B, double *Q, double *U,
+                      int ring_lo, int ring_hi)
+{
+    const int R = 4 * nside - 1;
+    double *z = malloc(sizeof(double) * R), *st = malloc(sizeof(double) * R);
+    double *p0 = malloc(sizeof(double) * R);
+    int64_t *nr = malloc(sizeof(int64_t) * R), *off = malloc(sizeof(int64_t) * R);
+    or_healpix_rings(nside, z, st, p0, nr, off);
+    if (ring_lo < 0) ring_lo = 0;
+    if (ring_hi > R) ring_hi = R;
+#pragma omp parallel
+    {
+        double *col = malloc(sizeof(double) * (L + 1));
+        double *Pr = malloc(sizeof(double) * (2 * L + 1)), *Pi = malloc(sizeof(double) * (2 * L + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int r = ring_lo; r < ring_hi; ++r) {
+            double ch, sh;
+            half_angles(z[r], st[r], &ch, &sh);
+            for (int m = -L; m <= L; ++m) {
+                double sr = 0.0, si = 0.0;
+                const int l0 = spin_column(L, m, 2, z[r], ch, sh, col);
+                for (int l = l0; l <= L; ++l) {
+                    double ar, ai;
+                    two_a(lmax, E, B, l, m, &ar, &ai);
+                    sr += ar * col[l - l0];
+                    si += ai * col[l - l0];
+                }
+                Pr[m + L] = sr;
+                Pi[m + L] = si;
+            }
+            const int64_t n = nr[r];
+            const int64_t q = p0[r] != 0.0;
+            for (int64_t j = 0; j < n; ++j) {
+                double fr = 0.0, fi = 0.0;
+                for (int m = -L; m <= L; ++m) {
+                    const int64_t pp = ((((int64_t)m * (2 * j + q)) % (2 * n)) + 2 * n) % (2 * n);
+                    const double ang = M_PI * (double)pp / (double)n, c = cos(ang), s = sin(ang);
+                    fr += Pr[m + L] * c - Pi[m + L] * s;
+                    fi += Pr[m + L] * s + Pi[m + L] * c;
+                }
+                Q[off[r] + j] = fr;
+                U[off[r] + j] = fi;
+            }
+        }
+        free(col);
+        free(Pr);
+        free(Pi);
+    }
+    free(z); free(st); free(p0); free(nr); free(off);
+}
+
+/* Adjoint of or_synthesis_pol under sum_p (Q Q' + U U') and
+ * Re sum_{l, all m} (conj(E) E' + conj(B) B'):
+ *   2t_lm = sum_p (Q + iU)_p conj(2Y_lm(p))                 (m = -L..L)
+ *   E_lm = -(2t_lm + (-1)^m conj(2t_{l,-m})) / 2
+ *   B_lm = (i/2) (2t_lm - (-1)^m conj(2t_{l,-m}))            (m >= 0, 2 <= l <= L)
+ * E, B: all entries written (zero outside 2 <= l <= L). */
+void or_adjoint_pol(int nside, int lmax, int L, const double *Q, const double *U, double *E, double *B)
+{
+    const int R = 4 * nside - 1;
+    double *z = malloc(sizeof(double) * R), *st = malloc(sizeof(double) * R);
+    double *p0 = malloc(sizeof(double) * R);
+    int64_t *nr = malloc(sizeof(int64_t) * R), *off = malloc(sizeof(int64_t) * R);
+    or_healpix_rings(nside, z, st, p0, nr, off);
+    const int64_t na = or_nalm(lmax);
+    for (int64_t i = 0; i < 2 * na; ++i) E[i] = B[i] = 0.0;
+    /* t[m + L][l] for m = -L..L, l = 0..L (complex) */
+    double *tr = calloc((size_t)(2 * L + 1) * (L + 1), sizeof(double));
+    double *ti = calloc((size_t)(2 * L + 1) * (L + 1), sizeof(double));
+#pragma omp parallel
+    {
+        double *col = malloc(sizeof(double) * (L + 1));
+        double *Fr = malloc(sizeof(double) * R), *Fi = malloc(sizeof(double) * R);
+        double *chs = malloc(sizeof(double) * R), *shs = malloc(sizeof(double) * R);
+        for (int r = 0; r < R; ++r) half_angles(z[r], st[r], &chs[r], &shs[r]);
+#pragma omp for schedule(dynamic, 1)
+        for (int m = -L; m <= L; ++m) {
+            for (int r = 0; r < R; ++r) {
+                const int64_t n = nr[r];
+                const int64_t q = p0[r] != 0.0;
+                double sr = 0.0, si = 0.0;
+                for (int64_t j = 0; j < n; ++j) {
+                    const int64_t pp = ((((int64_t)m * (2 * j + q)) % (2 * n)) + 2 * n) % (2 * n);
+                    const double ang = M_PI * (double)pp / (double)n, c = cos(ang), s = sin(ang);
+                    const double qr = Q[off[r] + j], ui = U[off[r] + j];
+                    /* (Q + iU) e^{-i ang} */
+                    sr += qr * c + ui * s;
+                    si += ui * c - qr * s;
+                }
+                Fr[r] = sr;
+                Fi[r] = si;
+            }
+            double *rowr = tr + (size_t)(m + L) * (L + 1), *rowi = ti + (size_t)(m + L) * (L + 1);
+            for (int r = 0; r < R; ++r) {
+                const int l0 = spin_column(L, m, 2, z[r], chs[r], shs[r], col);
+                for (int l = l0; l <= L; ++l) {
+                    rowr[l] += col[l - l0] * Fr[r];
+                    rowi[l] += col[l - l0] * Fi[r];
+                }
+            }
+        }
+        free(col); free(Fr); free(Fi); free(chs); free(shs);
+    }
+    for (int m = 0; m <= L; ++m) {
+        const double sg = (m & 1) ? -1.0 : 1.0;
+        for (int l = (m > 2 ? m : 2); l <= L; ++l) {
+            const double ar = tr[(size_t)(m + L) * (L + 1) + l], ai = ti[(size_t)(m + L) * (L + 1) + l];
+            const double cr = sg * tr[(size_t)(-m + L) * (L + 1) + l], ci = -sg * ti[(size_t)(-m + L) * (L + 1) + l];
+            const int64_t k = alm_index(lmax, l, m);
+            E[2 * k] = -0.5 * (ar + cr);
+            E[2 * k + 1] = -0.5 * (ai + ci);
+            /* (i/2)(t - c) */
+            B[2 * k] = -0.5 * (ai - ci);
+            B[2 * k + 1] = 0.5 * (ar - cr);
+        }
+    }
+    free(tr); free(ti);
+    free(z); free(st); free(p0); free(nr); free(off);
+}
+
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int or_num_threads(void)
 {

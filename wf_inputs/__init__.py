@@ -256,6 +256,56 @@ def healpix_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float = 13
     return out
 
 
+def healpix_pol_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float = 13.0, corr: float = 0.1,
+                        pol_noise_factor: float = 2.0, bb_ratio: float = 0.0, draws: bool = True, **kw) -> dict:
+    """Polarised (I, Q, U) workload.  Spectra: TT CMB-like, EE = 0.05 TT in
+    shape, TE = 0.5 sqrt(TT EE), BB = bb_ratio EE; columns (TT, EE, BB, TE).
+    Noise per pixel: diag(s_I^2, s_Q^2, s_U^2) with s_I^2 from the temperature
+    hit model (healpix_problem, same keywords), s_Q^2 = s_U^2 =
+    pol_noise_factor s_I^2, and I-Q, I-U, Q-U correlation coefficients drawn
+    in [-corr, corr], redrawn until the block is positive definite.  Draws:
+    signal (T, E, B) from the prior blocks, noise from the pixel blocks,
+    fluctuation draws g1 (3, npix) and g2 (3, n_alm).  The mask is shared by
+    I, Q and U."""
+    base = healpix_problem(nside, lmax, seed, fwhm_arcmin=fwhm_arcmin, draws=False, **kw)
+    rng = np.random.default_rng(seed + 7919)
+    npix = 12 * nside * nside
+    tt = base["c_ell"]
+    ee = 0.05 * tt
+    cl = np.stack([tt, ee, bb_ratio * ee, 0.5 * np.sqrt(tt * ee)], axis=1)
+    sI = base["noise_var"]
+    var = np.stack([sI, pol_noise_factor * sI, pol_noise_factor * sI], axis=1)
+    rho = rng.uniform(-corr, corr, size=(npix, 3))
+    N = np.zeros((npix, 3, 3))
+    for _ in range(100):
+        sd = np.sqrt(var)
+        N[:, 0, 0], N[:, 1, 1], N[:, 2, 2] = var[:, 0], var[:, 1], var[:, 2]
+        N[:, 0, 1] = N[:, 1, 0] = rho[:, 0] * sd[:, 0] * sd[:, 1]
+        N[:, 0, 2] = N[:, 2, 0] = rho[:, 1] * sd[:, 0] * sd[:, 2]
+        N[:, 1, 2] = N[:, 2, 1] = rho[:, 2] * sd[:, 1] * sd[:, 2]
+        bad = np.linalg.eigvalsh(N).min(axis=1) <= 0
+        if not bad.any():
+            break
+        rho[bad] = rng.uniform(-corr, corr, size=(int(bad.sum()), 3))
+    out = {"kind": "healpix_pol", "nside": nside, "lmax": lmax, "c_ell": cl, "noise_cov": N, "mask": base["mask"]}
+    if draws:
+        ell = alm_ell(lmax)
+        g = np.stack([alm_unit_gaussian(rng, lmax) for _ in range(3)])
+        a = np.zeros_like(g)
+        # T, E correlated through TE (Cholesky of the 2x2 block), B alone
+        a[0] = np.sqrt(tt[ell]) * g[0]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            c = np.where(tt[ell] > 0, cl[ell, 3] / np.sqrt(np.where(tt[ell] > 0, tt[ell], 1.0)), 0.0)
+        a[1] = c * g[0] + np.sqrt(np.maximum(ee[ell] - c * c, 0.0)) * g[1]
+        a[2] = np.sqrt(cl[ell, 2]) * g[2]
+        out["a_signal"] = a
+        Lc = np.linalg.cholesky(N)
+        out["noise"] = np.einsum("nij,jn->in", Lc, rng.standard_normal((3, npix)))
+        out["g1"] = rng.standard_normal((3, npix))
+        out["g2"] = np.stack([alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    return out
+
+
 # ---------------------------------------------------------------------------
 # named workloads
 # ---------------------------------------------------------------------------
