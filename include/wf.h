@@ -68,7 +68,7 @@ typedef struct {
     wf_geom_kind kind;
     int nx, ny;  /* flat only: powers of two, 16 <= n <= 256 */
     int nside;   /* HEALPix only */
-    int ncomp;   /* 1 (temperature); polarisation is not supported in this version */
+    int ncomp;   /* 1 (temperature) or 3 (polarised I, Q, U: HEALPix, FP64) */
 } wf_geometry;
 
 /* Options of the cooling schedule and stopping rule (Sect. 3).  Zero-filled
@@ -150,7 +150,16 @@ wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n);
  * conventions).  tol: relative residual |(S^-1 + N^-1) s - N^-1 d| / |N^-1 d|
  * in harmonic coordinates at which to stop.  s_wf: n_pix FP64 output.
  * alm_out: optional harmonic output.  info: optional report.
- * Noise variance must be finite and > 0 on observed pixels (WF_EINVAL). */
+ * Noise variance must be finite and > 0 on observed pixels (WF_EINVAL).
+ * Polarised plans (ncomp = 3; Eqs. 10-11, heuristic cooling or replay): d and
+ * s_wf are 3 x n_pix (I, Q, U, component-major); noise_var is the 3x3 noise
+ * covariance per pixel as 6 x n_pix (II, QQ, UU, IQ, IU, QU), positive definite
+ * on observed pixels; the mask is shared by I, Q, U; C_ell is 4 x (lmax + 1)
+ * (TT, EE, BB, TE), each block [[TT, TE, 0], [TE, EE, 0], [0, 0, BB]] positive
+ * semi-definite (singular blocks act through their pseudo-inverse); alm_out is
+ * 3 x n_alm (T, E, B).  Spin-2 convention: (Q + iU) = sum_{l >= 2, |m| <= l}
+ * 2a_lm 2Y_lm, 2a = -(E + iB), sY_lm = sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta)
+ * e^{i m phi}.  tau is the smallest eigenvalue of any observed noise block. */
 wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const uint8_t *mask,
                    const double *C_ell, double tol, double *s_wf, double *alm_out, wf_info *info);
 

@@ -217,21 +217,22 @@ def _check(st, what, allow=()):
 
 
 def wf_plan_create(kind: str, *, nside: int = 0, lmax: int = 0, n: int = 0, precision: str = "fp64",
-                   stream=None) -> Plan:
-    """kind 'healpix' (nside, lmax) or 'flat' (n x n).  stream: torch
-    CUDA stream (default: the current stream)."""
+                   stream=None, ncomp: int = 1) -> Plan:
+    """kind 'healpix' (nside, lmax) or 'flat' (n x n); ncomp 3 for polarised
+    (I, Q, U) HEALPix plans (FP64).  stream: torch CUDA stream (default: the
+    current stream)."""
     import torch
 
     L = load()
     g = wf_geometry()
     g.kind = WF_GEOM_HEALPIX if kind == "healpix" else WF_GEOM_FLAT
-    g.nside, g.nx, g.ny, g.ncomp = nside, n, n, 1
+    g.nside, g.nx, g.ny, g.ncomp = nside, n, n, int(ncomp)
     if stream is None:
         stream = torch.cuda.current_stream()
     h = ctypes.c_void_p()
     _check(L.wf_plan_create(ctypes.byref(g), lmax, PRECISIONS[precision], ctypes.c_void_p(stream.cuda_stream),
                             ctypes.byref(h)), "wf_plan_create")
-    return Plan(h, {"kind": kind, "nside": nside, "n": n}, lmax, precision)
+    return Plan(h, {"kind": kind, "nside": nside, "n": n, "ncomp": int(ncomp)}, lmax, precision)
 
 
 def wf_plan_destroy(plan: Plan):

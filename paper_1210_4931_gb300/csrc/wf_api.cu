@@ -1079,6 +1079,195 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
     return hp_end(R);
 }
 
+// (T, E, B) -> (I, Q, U) maps: FP64 map out (omap, 3 x npix) or the plan's
+// working maps (tmap) when omap is null; l <= L
+wf_status pol_synthesis(wf_plan p, const double2 *a3, int L, double *omap, double *tmap)
+{
+    PolState *P = p->pol;
+    const long long nalm = p->nalm, npix = p->npix;
+    const RingSynMode mode = omap ? RS_MAP : RS_SYN;
+    wf_status st;
+    if ((st = hp_legendre_synthesis_buf(p, a3, L, (double2 *)p->ws.G)) != WF_OK) return st;
+    if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, p->ws.G, tmap, omap)) != WF_OK) return st;
+    if ((st = hp_pol_legendre_synthesis(p, a3 + nalm, a3 + 2 * nalm, L)) != WF_OK) return st;
+    if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, P->GQ, tmap ? tmap + npix : nullptr,
+                                    omap ? omap + npix : nullptr)) != WF_OK)
+        return st;
+    return hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, P->GU, tmap ? tmap + 2 * npix : nullptr,
+                                 omap ? omap + 2 * npix : nullptr);
+}
+
+// adjoint: (I, Q, U) maps (FP64, 3 x npix) -> (T, E, B) = Y^T map, l <= L
+wf_status pol_adjoint(wf_plan p, const double *map3, int L, double2 *out3)
+{
+    PolState *P = p->pol;
+    const long long nalm = p->nalm, npix = p->npix;
+    wf_status st;
+    if ((st = hp_ring_analysis_buf(p, L, map3, p->ws.F)) != WF_OK) return st;
+    if ((st = hp_legendre_adjoint_buf(p, L, (const double2 *)p->ws.F, out3)) != WF_OK) return st;
+    if ((st = hp_ring_analysis_buf(p, L, map3 + npix, P->FQ)) != WF_OK) return st;
+    if ((st = hp_ring_analysis_buf(p, L, map3 + 2 * npix, P->FU)) != WF_OK) return st;
+    return hp_pol_legendre_analysis(p, L, out3 + nalm, out3 + 2 * nalm);
+}
+
+// Polarised Wiener filter (Eqs. 10-11), FP64, with the heuristic cooling of
+// Sect. 3 on the largest eigenvalue of each l's prior block (or a replay).
+// d: 3 x npix (I, Q, U); N6: 6 x npix noise covariance (II, QQ, UU, IQ, IU, QU);
+// C4: 4 x (lmax + 1) spectra (TT, EE, BB, TE); s_out 3 x npix; alm_out 3 x n_alm.
+wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8_t *mask, const double *C4,
+                       double tol, double *s_out, double *alm_out, wf_info *info)
+{
+    const wf_options o = defaults(p->opt);
+    if (o.schedule == 1 && p->replay_lambda.empty())
+        return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule is built for temperature maps only");
+    PolState *P = p->pol;
+    const int lmax = p->lmax;
+    const long long nalm = p->nalm, npix = p->npix;
+    Prof pr(p, info, o.profile != 0);
+    wf_status st;
+    std::vector<double> C((size_t)4 * (lmax + 1));
+    if ((st = to_host(p, C.data(), C4, C.size() * sizeof(double))) != WF_OK) return st;
+    HpSchedule sch;
+    sch.c.resize(lmax + 1);
+    for (int l = 0; l <= lmax; ++l) {
+        const double tt = C[l], ee = C[lmax + 1 + l], bb = C[2 * (lmax + 1) + l], te = C[3 * (lmax + 1) + l];
+        if (!(std::isfinite(tt) && std::isfinite(ee) && std::isfinite(bb) && std::isfinite(te)) || tt < 0 ||
+            ee < 0 || bb < 0 || te * te > tt * ee * (1.0 + 1e-12))
+            return set_error(WF_EINVAL, "prior block of l = %d is not positive semi-definite", l);
+        const double h = 0.5 * (tt - ee);
+        sch.c[l] = std::max(0.5 * (tt + ee) + std::sqrt(h * h + te * te), bb);
+    }
+    double tau = 0;
+    long long ndof = 0;
+    if ((st = hp_pol_setup(p, d, N6, mask, &tau, &ndof)) != WF_OK) return st;
+    const double tau_h = tau * p->omega;
+    if ((st = pol_adjoint(p, P->r, lmax, P->b)) != WF_OK) return st;
+    if ((st = hp_pol_alm_norm(p, C4, P->b, 1)) != WF_OK) return st;
+    {
+        SumSpec sp{};
+        sp.in[0] = P->part2;
+        sp.n[0] = lmax + 1;
+        sp.stride[0] = 1;
+        if ((st = sums(p, sp, 1, &pr)) != WF_OK) return st;
+    }
+    const double bnorm = std::sqrt(p->ws.h_scal[0]);
+    if (!(bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
+    sch.tau_h = tau_h;
+    sch.lmax = lmax;
+    sch.step_max = o.ell_step_max;
+    sch.margin = o.band_margin;
+    sch.ell_iter = std::min(o.ell0, lmax);
+    sch.level();
+    WF_CUDA(cudaMemsetAsync(P->a, 0, 3 * nalm * sizeof(double2), p->stream));
+    WF_CUDA(cudaMemsetAsync(P->a_new, 0, 3 * nalm * sizeof(double2), p->stream));
+    const bool replay = !p->replay_lambda.empty();
+    const int nrep = (int)p->replay_lambda.size();
+    const double sigma = std::sqrt(2.0 * (double)ndof);
+    int k = 0, level_iters = 0, levels = 1;
+    bool have_prev = false, converged = false;
+    double prev_chi2 = 0, last_resid = NAN, best_resid = INFINITY;
+    wf_status result = WF_OK;
+    for (;;) {
+        double lam;
+        int L;
+        if (replay) {
+            if (k >= nrep) break;
+            lam = p->replay_lambda[k];
+            L = std::min(std::max(p->replay_L[k], 0), lmax);
+        } else {
+            if (k >= o.maxiter) { result = WF_ENOCONV; break; }
+            lam = sch.lam;
+            L = sch.L;
+        }
+        const bool full = (lam == 1.0 && L == lmax);
+        pr.iter_begin();
+        pr.begin(WF_K_LEG_SYN);
+        if ((st = pol_synthesis(p, P->a, L, nullptr, P->t)) != WF_OK) return st;
+        pr.end();
+        int nb = 0;
+        if ((st = hp_pol_blend(p, lam, tau, &nb)) != WF_OK) return st;
+        pr.begin(WF_K_LEG_ANA);
+        if ((st = pol_adjoint(p, P->t, L, P->b)) != WF_OK) return st;
+        if ((st = hp_pol_hblend(p, L, C4, lam * tau_h, tau_h, full ? 1 : 0)) != WF_OK) return st;
+        pr.end();
+        SumSpec sp{};
+        sp.in[0] = P->part;
+        sp.n[0] = nb;
+        sp.stride[0] = 1;
+        sp.in[1] = P->part2;
+        sp.n[1] = lmax + 1;
+        sp.stride[1] = 2;
+        sp.in[2] = P->part2 + 1;
+        sp.n[2] = lmax + 1;
+        sp.stride[2] = 2;
+        if ((st = sums(p, sp, 3, &pr)) != WF_OK) return st;
+        const double ims = pr.iter_end();
+        pr.collect();
+        const double chi2 = p->ws.h_scal[0] + p->ws.h_scal[1];
+        const double resid = full ? std::sqrt(p->ws.h_scal[2]) / bnorm : NAN;
+        record(info, k, lam, L, chi2, resid, ims);
+        std::swap(P->a, P->a_new);
+        ++k;
+        if (full) {
+            last_resid = resid;
+            if (!std::isfinite(resid) || (k > 50 && resid > 1e3 * best_resid)) { result = WF_EDIVERGE; break; }
+            best_resid = std::min(best_resid, resid);
+        }
+        if (!std::isfinite(chi2)) { result = WF_EDIVERGE; break; }
+        if (replay) {
+            if (full && resid < tol) converged = true;
+            continue;
+        }
+        if (sch.final_level()) {
+            if (resid < tol) { converged = true; break; }
+        } else {
+            ++level_iters;
+            const bool plateau = have_prev && std::fabs(chi2 - prev_chi2) < o.eta * sigma;
+            if (plateau || level_iters >= o.level_cap) {
+                sch.advance();
+                ++levels;
+                have_prev = false;
+                level_iters = 0;
+                continue;
+            }
+        }
+        prev_chi2 = chi2;
+        have_prev = true;
+    }
+    if ((st = pol_synthesis(p, P->a, lmax, s_out, nullptr)) != WF_OK) return st;
+    if (alm_out)
+        WF_CUDA(cudaMemcpyAsync(alm_out, P->a, 3 * nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    int nb = 0;
+    if ((st = hp_pol_alm_norm(p, C4, P->a, 0)) != WF_OK) return st;
+    if ((st = hp_pol_pix_chi2(p, d, s_out, &nb)) != WF_OK) return st;
+    SumSpec sp{};
+    sp.in[0] = P->part2;
+    sp.n[0] = lmax + 1;
+    sp.stride[0] = 1;
+    sp.in[1] = P->part;
+    sp.n[1] = nb;
+    sp.stride[1] = 1;
+    if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
+    const double chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
+    if (info) {
+        info->iters = k;
+        info->converged = converged ? 1 : 0;
+        info->final_residual = last_resid;
+        info->chi2_over_ndof = chi2n;
+        info->n_dof = ndof;
+        info->tau = tau;
+        info->n_levels = levels;
+        info->refine_sweeps = 0;
+        info->mixed_lc = 0;
+    }
+    pr.finish();
+    if (result == WF_OK && !replay && !converged) result = WF_ENOCONV;
+    if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", last_resid);
+    if (result == WF_EDIVERGE) set_error(result, "residual grew (%.3e)", last_resid);
+    (void)npix;
+    return result;
+}
+
 // Several HEALPix solves advanced together: one step of every active solve
 // (its iteration's kernels on its own branch stream) is captured in one CUDA
 // graph and launched at once; the host then reads every solve's sums and runs
@@ -1092,6 +1281,7 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
     for (int i = 0; i < n; ++i) {
         if (!plans[i] || plans[i]->g.kind != WF_GEOM_HEALPIX)
             return set_error(WF_EINVAL, "batch item %d: needs a HEALPix plan", i);
+        if (plans[i]->pol) return set_error(WF_EUNSUPPORTED, "batch item %d: polarised plans are not batched", i);
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return set_error(WF_EINVAL, "batch items %d and %d share a plan", j, i);
         const wf_batch_item &it = items[i];
@@ -1359,7 +1549,10 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
 {
     if (!g || !out) return set_error(WF_EINVAL, "null argument");
     *out = nullptr;
-    if (g->ncomp != 0 && g->ncomp != 1) return set_error(WF_EUNSUPPORTED, "only ncomp = 1 (temperature) is supported");
+    if (g->ncomp != 0 && g->ncomp != 1 && g->ncomp != 3)
+        return set_error(WF_EUNSUPPORTED, "ncomp must be 1 (temperature) or 3 (I, Q, U)");
+    if (g->ncomp == 3 && (g->kind != WF_GEOM_HEALPIX || prec != WF_PREC_FP64))
+        return set_error(WF_EUNSUPPORTED, "polarised plans (ncomp = 3) are HEALPix and FP64 in this version");
     if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32) return set_error(WF_EINVAL, "unknown precision");
     wf_plan p = new (std::nothrow) wf_plan_s();
     if (!p) return set_error(WF_ENOMEM, "host allocation");
@@ -1380,6 +1573,7 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
             p->nside = g->nside;
             p->lmax = lmax;
             st = hp_create(p);
+            if (st == WF_OK && g->ncomp == 3) st = hp_pol_create(p, p->tab.x64, p->tab.st64);
         }
     } else if (g->kind == WF_GEOM_FLAT) {
         p->lmax = 0;
@@ -1409,6 +1603,7 @@ void wf_plan_destroy(wf_plan p)
     else cudaDeviceSynchronize();
     if (p->aux) cudaStreamSynchronize(p->aux);
     if (p->flat) flat_destroy(p);
+    if (p->pol) hp_pol_destroy(p);
     if (p->sub) wf_plan_destroy(p->sub);
     if (p->aux) cudaStreamDestroy(p->aux);
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
@@ -1497,6 +1692,7 @@ wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const ui
             return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule is implemented on the HEALPix sphere only");
         return flat_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
     }
+    if (p->pol) return hp_solve_pol(p, d, noise_var, mask, C_ell, tol, s_wf, alm_out, info);
     return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
 }
 
@@ -1518,6 +1714,7 @@ wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, cons
             return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
         return flat_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
     }
+    if (p->pol) return set_error(WF_EUNSUPPORTED, "the polarised fluctuation solve is not built in this version");
     return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
 }
 
@@ -1531,13 +1728,14 @@ wf_status host_staging(wf_plan p)
     const size_t npx = (size_t)p->npix;
     const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
     const size_t nh = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) * 2 : (size_t)p->nalm * 2;
+    const size_t nc = p->pol ? 3 : 1;  // maps and harmonic vectors per solve
     wf_status st;
-    if ((st = plan_alloc(p, (void **)&p->ws.d_in, npx * 8)) != WF_OK) return st;
-    if ((st = plan_alloc(p, (void **)&p->ws.nv_in, npx * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.d_in, nc * npx * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.nv_in, (p->pol ? 6 : 1) * npx * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&p->ws.mask_in, npx)) != WF_OK) return st;
-    if ((st = plan_alloc(p, (void **)&p->ws.out_map, npx * 8)) != WF_OK) return st;
-    if ((st = plan_alloc(p, (void **)&p->ws.cl_in, nS * 8)) != WF_OK) return st;
-    return plan_alloc(p, (void **)&p->ws.alm_io, nh * 8);
+    if ((st = plan_alloc(p, (void **)&p->ws.out_map, nc * npx * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&p->ws.cl_in, (p->pol ? 4 : 1) * nS * 8)) != WF_OK) return st;
+    return plan_alloc(p, (void **)&p->ws.alm_io, nc * nh * 8);
 }
 }  // namespace wf
 
@@ -1550,18 +1748,19 @@ wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, con
     const size_t npx = (size_t)p->npix;
     const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
     const size_t nh = (size_t)p->nalm * 2;
+    const size_t nc = p->pol ? 3 : 1, nn = p->pol ? 6 : 1, ncl = p->pol ? 4 : 1;  // components per array
     wf_status st;
     if ((st = host_staging(p)) != WF_OK) return st;
     cudaStream_t s = p->stream;
-    WF_CUDA(cudaMemcpyAsync(p->ws.d_in, d, npx * 8, cudaMemcpyHostToDevice, s));
-    WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, npx * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.d_in, d, nc * npx * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, nn * npx * 8, cudaMemcpyHostToDevice, s));
     if (mask) WF_CUDA(cudaMemcpyAsync(p->ws.mask_in, mask, npx, cudaMemcpyHostToDevice, s));
-    WF_CUDA(cudaMemcpyAsync(p->ws.cl_in, C_ell, nS * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.cl_in, C_ell, ncl * nS * 8, cudaMemcpyHostToDevice, s));
     st = wf_solve(p, p->ws.d_in, p->ws.nv_in, mask ? p->ws.mask_in : nullptr, p->ws.cl_in, tol, p->ws.out_map,
                   alm_out ? p->ws.alm_io : nullptr, info);
     if (st != WF_OK && st != WF_ENOCONV) return st;
-    WF_CUDA(cudaMemcpyAsync(s_wf, p->ws.out_map, npx * 8, cudaMemcpyDeviceToHost, s));
-    if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nh * 8, cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaMemcpyAsync(s_wf, p->ws.out_map, nc * npx * 8, cudaMemcpyDeviceToHost, s));
+    if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nc * nh * 8, cudaMemcpyDeviceToHost, s));
     WF_CUDA(cudaStreamSynchronize(s));
     return st;
 }
@@ -1598,6 +1797,7 @@ wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mas
 {
     if (!p || !d_raw || !d_out) return set_error(WF_EINVAL, "null argument");
     if (p->g.kind != WF_GEOM_HEALPIX) return set_error(WF_EUNSUPPORTED, "template marginalisation needs a HEALPix plan");
+    // on a polarised plan the monopole / dipole of Eq. (12) are removed from the I map (the first npix values)
     const int grid = std::min(p->npairs, 4 * p->nsm);
     const size_t need = (size_t)14 * grid * sizeof(double);
     if (!p->ws.redu) {
@@ -1635,7 +1835,8 @@ wf_status wf_alm2map(wf_plan p, const double *alm, int L, double *map)
     if (!p || !alm || !map) return set_error(WF_EINVAL, "null argument");
     if (p->g.kind == WF_GEOM_FLAT) return flat_alm2map(p, alm, map);
     if (L < 0 || L > p->lmax) L = p->lmax;
-    wf_status st = hp_alm2map(p, (const double2 *)alm, L, map);
+    wf_status st = p->pol ? pol_synthesis(p, (const double2 *)alm, L, map, nullptr)
+                          : hp_alm2map(p, (const double2 *)alm, L, map);
     if (st != WF_OK) return st;
     WF_CUDA(cudaStreamSynchronize(p->stream));
     return WF_OK;
@@ -1646,6 +1847,12 @@ wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm)
     if (!p || !alm || !map) return set_error(WF_EINVAL, "null argument");
     if (p->g.kind == WF_GEOM_FLAT) return flat_map2alm(p, map, alm);
     if (L < 0 || L > p->lmax) L = p->lmax;
+    if (p->pol) {
+        wf_status st = pol_adjoint(p, map, L, (double2 *)alm);
+        if (st != WF_OK) return st;
+        WF_CUDA(cudaStreamSynchronize(p->stream));
+        return WF_OK;
+    }
     if (p->prec == WF_PREC_FP64) {
         WF_CUDA(cudaMemcpyAsync(p->ws.t, map, p->npix * 8, cudaMemcpyDeviceToDevice, p->stream));
     } else {

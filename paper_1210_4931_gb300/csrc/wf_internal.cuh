@@ -70,6 +70,17 @@ constexpr int RING_THREADS = 512;
 // plan
 // ---------------------------------------------------------------------------
 struct FlatPlan;  // flat-grid state (wf_flat.cu)
+// Polarisation (ncomp = 3, FP64): spin-2 tables and the (I, Q, U) / (T, E, B) workspace
+struct PolState {
+    double *al = nullptr, *be = nullptr, *ga = nullptr;  // per alm: spin -+2 recurrence coefficients
+    int *ls = nullptr;                                   // per (m, pair): first kept l
+    double *p0 = nullptr, *p1 = nullptr, *m0 = nullptr, *m1 = nullptr;  // 2lambda/2, -2lambda/2 at ls and ls + 1
+    double2 *a = nullptr, *a_new = nullptr, *b = nullptr;  // 3 x n_alm each: T, E, B
+    double2 *GQ = nullptr, *GU = nullptr, *FQ = nullptr, *FU = nullptr;  // ring coefficients of Q and U
+    double *r = nullptr, *t = nullptr;  // 3 x npix: source nu d and the messenger field
+    double *nu = nullptr;               // 6 x npix: inverse noise blocks (II, QQ, UU, IQ, IU, QU)
+    double *part = nullptr, *part2 = nullptr;  // pixel and harmonic partial sums
+};
 
 struct Workspace {
     // HEALPix working buffers; T-typed ones are void* and cast per precision
@@ -99,6 +110,7 @@ struct HpTables {
     int *ls = nullptr;
     double *s0_64 = nullptr, *s1_64 = nullptr;
     double *x64 = nullptr;
+    double *st64 = nullptr;  // sin(theta) per pair
     // mixed precision: FP32 A and B = A - 2 per alm, x and w = 1 - x per pair,
     // and the FP32 seeds that start the recurrence at max(l_s, l_c) (m < l_c)
     float *A32 = nullptr, *B32 = nullptr, *x32 = nullptr, *w32 = nullptr;
@@ -129,6 +141,7 @@ struct wf_plan_s {
     wf::HpTables tab;
     wf::Workspace ws;
     wf::FlatPlan *flat = nullptr;
+    wf::PolState *pol = nullptr;  // polarised plans (ncomp = 3)
     wf_options opt{};
     std::vector<double> replay_lambda;
     std::vector<int> replay_L;
@@ -214,6 +227,23 @@ wf_status hp_build_ring_tables(wf_plan p);
 enum RingSynMode { RS_BLEND = 0, RS_MAP = 1, RS_SYN = 2 };
 wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *out_map);
 wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T);
+// the same passes on explicit buffers (G / F in the working precision, maps T-typed or FP64 out)
+wf_status hp_ring_synthesis_buf(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
+                                void *tmap, double *out_map);
+wf_status hp_ring_analysis_buf(wf_plan p, int L, const void *map_T, void *F);
+// FP64 temperature Legendre transforms on explicit buffers (FP64 plans)
+wf_status hp_legendre_synthesis_buf(wf_plan p, const double2 *alm, int L, double2 *G);
+wf_status hp_legendre_adjoint_buf(wf_plan p, int L, const double2 *F, double2 *out);
+// polarisation (wf_spin.cu)
+wf_status hp_pol_create(wf_plan p, const double *xpair_dev, const double *stpair_dev);
+void hp_pol_destroy(wf_plan p);
+wf_status hp_pol_legendre_synthesis(wf_plan p, const double2 *E, const double2 *B, int L);
+wf_status hp_pol_legendre_analysis(wf_plan p, int L, double2 *E, double2 *B);
+wf_status hp_pol_setup(wf_plan p, const double *d, const double *N6, const uint8_t *mask, double *tau, long long *ndof);
+wf_status hp_pol_blend(wf_plan p, double lam, double tau, int *nblocks);
+wf_status hp_pol_hblend(wf_plan p, int L, const double *C, double lam_tauh, double tauh, int want_resid);
+wf_status hp_pol_alm_norm(wf_plan p, const double *C, const double2 *a, int mode);
+wf_status hp_pol_pix_chi2(wf_plan p, const double *d, const double *s_map, int *nblocks);
 
 // flat grid (wf_flat.cu)
 wf_status flat_create(wf_plan p);

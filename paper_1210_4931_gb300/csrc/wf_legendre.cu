@@ -905,6 +905,7 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
     if ((st = plan_alloc(p, (void **)&t.A64, nalm * sizeof(double))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&t.x64, np * sizeof(double))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&dst64, np * sizeof(double))) != WF_OK) return st;
+    t.st64 = dst64;
     if ((st = plan_alloc(p, (void **)&dlog2c, (lmax + 1) * sizeof(double))) != WF_OK) return st;
     const long long ns = (long long)(lmax + 1) * np;
     if ((st = plan_alloc(p, (void **)&t.ls, ns * sizeof(int))) != WF_OK) return st;
@@ -994,6 +995,20 @@ wf_status hp_set_low_block(wf_plan p, int lc)
     }
     t.lc_mx = lc;
     return WF_OK;
+}
+
+wf_status hp_legendre_synthesis_buf(wf_plan p, const double2 *alm, int L, double2 *G)
+{
+    if (p->prec != WF_PREC_FP64) return set_error(WF_EUNSUPPORTED, "explicit-buffer transforms need an FP64 plan");
+    return launch_syn64<double>(p, alm, L, 0, G, p->lmax + 1, p->stream);
+}
+
+wf_status hp_legendre_adjoint_buf(wf_plan p, int L, const double2 *F, double2 *out)
+{
+    if (p->prec != WF_PREC_FP64) return set_error(WF_EUNSUPPORTED, "explicit-buffer transforms need an FP64 plan");
+    WF_CUDA(cudaMemsetAsync(out, 0, p->nalm * sizeof(double2), p->stream));
+    BlendArgs none;
+    return launch_ana64<double>(p, L, 0, F, LEG_ADJOINT, none, nullptr, out, p->stream);
 }
 
 // Mixed precision: the FP64 low-l block (FP64 pipe, few CTAs) runs on the

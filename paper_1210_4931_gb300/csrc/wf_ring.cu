@@ -538,6 +538,11 @@ template <typename T> struct RingLaunch {
     }
     static wf_status syn(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *omap)
     {
+        return syn_buf(p, L, mode, lam, tau, p->ws.G, p->ws.t, omap);
+    }
+    static wf_status syn_buf(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G, void *tmap,
+                             double *omap)
+    {
         const HpTables &t = p->tab;
         RingCommon rc = common(p, L);
         if (p->prec != WF_PREC_FP64 && t.lc_mx > 0) {
@@ -549,13 +554,14 @@ template <typename T> struct RingLaunch {
         WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
         k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
             rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
-            (const cx<T> *)p->ws.G, (int)mode, (const T *)p->ws.r, (const T *)p->ws.nu, (T)lam, (T)tau,
-            (T *)p->ws.t, omap, p->ws.part_pix);
+            (const cx<T> *)G, (int)mode, (const T *)p->ws.r, (const T *)p->ws.nu, (T)lam, (T)tau,
+            (T *)tmap, omap, p->ws.part_pix);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         return WF_OK;
     }
-    static wf_status ana(wf_plan p, int L, const void *map)
+    static wf_status ana(wf_plan p, int L, const void *map) { return ana_buf(p, L, map, p->ws.F); }
+    static wf_status ana_buf(wf_plan p, int L, const void *map, void *F)
     {
         const HpTables &t = p->tab;
         RingCommon rc = common(p, L);
@@ -563,7 +569,7 @@ template <typename T> struct RingLaunch {
         WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
         k_ringana<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
                                                                   (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
-                                                                  (const T *)map, (cx<T> *)p->ws.F);
+                                                                  (const T *)map, (cx<T> *)F);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         return WF_OK;
@@ -732,6 +738,19 @@ wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, doub
 {
     return p->prec == WF_PREC_FP64 ? RingLaunch<double>::syn(p, L, mode, lam, tau, out_map)
                                    : RingLaunch<float>::syn(p, L, mode, lam, tau, out_map);
+}
+
+wf_status hp_ring_synthesis_buf(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
+                                void *tmap, double *out_map)
+{
+    return p->prec == WF_PREC_FP64 ? RingLaunch<double>::syn_buf(p, L, mode, lam, tau, G, tmap, out_map)
+                                   : RingLaunch<float>::syn_buf(p, L, mode, lam, tau, G, tmap, out_map);
+}
+
+wf_status hp_ring_analysis_buf(wf_plan p, int L, const void *map_T, void *F)
+{
+    return p->prec == WF_PREC_FP64 ? RingLaunch<double>::ana_buf(p, L, map_T, F)
+                                   : RingLaunch<float>::ana_buf(p, L, map_T, F);
 }
 
 wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T)

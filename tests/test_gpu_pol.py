@@ -1,0 +1,132 @@
+"""Polarised (I, Q, U) path on the GPU against the oracle: the spin-2 basis
+change (synthesis and its adjoint) to 1e-12, and the polarised messenger
+solve of Eqs. 10-11 (FP64) to 1e-10 against the oracle replaying the GPU's
+own (lambda, L) trace."""
+import numpy as np
+import pytest
+
+import oracle
+import wf_inputs as gen
+from gpu_util import T, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    import torch
+
+    import paper_1210_4931_gb300 as w
+
+    w.load()
+    torch.cuda.set_device(0)
+    return w
+
+
+def _rand_teb(rng, lmax):
+    l, m = oracle.alm_lm(lmax)
+    a = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    a[1:, l < 2] = 0.0
+    return a
+
+
+@pytest.mark.parametrize("nside,lmax", [(2, 4), (4, 8), (8, 16), (16, 32), (32, 64), (64, 100)])
+def test_pol_basis_change_matches_oracle(wf, nside, lmax):
+    import torch
+
+    rng = np.random.default_rng(500 + nside)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3)
+    npx = 12 * nside * nside
+    a = _rand_teb(rng, lmax)
+    m = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    for L in (lmax, lmax // 2 + 1):
+        wf.wf_alm2map(plan, T(a.ravel()), L, m)
+        got = m.cpu().numpy().reshape(3, npx)
+        I = oracle.synthesis(nside, lmax, L, a[0])
+        Q, U = oracle.synthesis_pol(nside, lmax, L, a[1], a[2])
+        ref = np.stack([I, Q, U])
+        assert rel(got, ref) < 1e-12, (L, rel(got[0], I), rel(got[1], Q), rel(got[2], U))
+    f = rng.standard_normal((3, npx))
+    out = torch.empty(3 * plan.nalm, dtype=torch.complex128, device="cuda")
+    for L in (lmax, lmax // 2 + 1):
+        wf.wf_map2alm_adjoint(plan, T(f.ravel()), L, out)
+        got = out.cpu().numpy().reshape(3, plan.nalm)
+        Tt = oracle.adjoint_synthesis(nside, lmax, L, f[0])
+        Et, Bt = oracle.adjoint_pol(nside, lmax, L, f[1], f[2])
+        assert rel(got, np.stack([Tt, Et, Bt])) < 1e-12, (L, rel(got[1], Et), rel(got[2], Bt))
+    plan.close()
+
+
+def _pol_case(nside, lmax, seed):
+    from oracle.messenger_pol import HealpixPolBasis
+
+    P = gen.healpix_pol_problem(nside, lmax, seed, fwhm_arcmin=4 * 3438.0 / lmax, n_disks=6,
+                                disk_radius_deg=6.0, corr=0.1)
+    basis = HealpixPolBasis(nside, lmax)
+    d = basis.synth(P["a_signal"]) + P["noise"]
+    obs = P["mask"] > 0
+    nu = np.zeros_like(P["noise_cov"])
+    nu[obs] = np.linalg.inv(P["noise_cov"][obs])
+    N6 = np.stack([P["noise_cov"][:, 0, 0], P["noise_cov"][:, 1, 1], P["noise_cov"][:, 2, 2],
+                   P["noise_cov"][:, 0, 1], P["noise_cov"][:, 0, 2], P["noise_cov"][:, 1, 2]])
+    C4 = np.ascontiguousarray(P["c_ell"].T)
+    return P, basis, d, nu, obs, N6, C4
+
+
+@pytest.mark.parametrize("nside,lmax", [(8, 16), (16, 32)])
+def test_pol_solve_fp64_matches_oracle_replay(wf, nside, lmax):
+    import torch
+
+    from oracle.messenger_pol import messenger_solve_pol, pol_tau
+
+    P, basis, d, nu, obs, N6, C4 = _pol_case(nside, lmax, gen.seed_for(4, nside))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3)
+    npx = 12 * nside * nside
+    s = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    alm = torch.empty(3 * plan.nalm, dtype=torch.complex128, device="cuda")
+    rep = wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(C4.ravel()), 1e-7, s, alm, trace_cap=20000)
+    assert rep["converged"] and rep["final_residual"] < 1e-7
+    tau = pol_tau(P["noise_cov"], obs)
+    assert rep["tau"] == pytest.approx(tau, rel=1e-12)
+    lam = rep["lambda_trace"]
+    assert lam[-1] == 1.0 and np.all(np.diff(lam) <= 0)
+    S = basis.per_mode(P["c_ell"])
+    r = np.einsum("nij,jn->in", nu, d)
+    ref = messenger_solve_pol(basis, r, nu, S, tau, replay=list(zip(lam, rep["L_trace"])))
+    assert rel(alm.cpu().numpy().reshape(3, -1), ref["a"]) < 1e-10
+    assert rel(s.cpu().numpy().reshape(3, npx), ref["s"]) < 1e-10
+    np.testing.assert_allclose(rep["chi2_trace"], ref["chi2"], rtol=1e-10, atol=1e-10 * np.max(np.abs(ref["chi2"])))
+    fin = ~np.isnan(ref["resid"])
+    np.testing.assert_allclose(rep["resid_trace"][fin], ref["resid"][fin], rtol=1e-7)
+    assert rep["n_dof"] == ref["n_dof"]
+    plan.close()
+
+
+def test_pol_rejections(wf):
+    import torch
+
+    nside, lmax = 8, 16
+    P, basis, d, nu, obs, N6, C4 = _pol_case(nside, lmax, gen.seed_for(4, 99))
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed", ncomp=3)
+    assert e.value.status == wf.WF_EUNSUPPORTED
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3)
+    npx = 12 * nside * nside
+    s = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    bad = N6.copy()
+    k = np.nonzero(P["mask"])[0][5]
+    bad[3, k] = 2.0 * np.sqrt(bad[0, k] * bad[1, k])  # |rho_IQ| > 1: not positive definite
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(bad.ravel()), T(P["mask"]), T(C4.ravel()), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    badC = C4.copy()
+    badC[3, 10] = 2.0 * np.sqrt(badC[0, 10] * badC[1, 10])
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(badC.ravel()), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    g1 = T(np.zeros(3 * npx))
+    g2 = T(np.zeros(3 * plan.nalm, dtype=np.complex128))
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_fluct(plan, T(N6.ravel()), T(P["mask"]), T(C4.ravel()), g1, g2, 1e-6, s)
+    assert e.value.status == wf.WF_EUNSUPPORTED
+    plan.close()
