@@ -151,3 +151,65 @@ def test_pol_converges_to_dense_fixed_point(oracle, bb):
         rr = M @ xk - rhs
         true = math.sqrt(np.sum(Wa * rr ** 2)) / math.sqrt(np.sum(Wa * rhs ** 2))
         assert rep == pytest.approx(true, rel=1e-9)
+
+
+def test_pol_fluct_source_matches_dense_construction(oracle):
+    """Eq. (9) for (I, Q, U): r = nu^1/2 g1 + Omega Y (S^+1/2 g2), built here
+    from scipy's matrix square root per pixel and per l (pseudo-inverse of the
+    root) and from the explicitly evaluated basis functions, against the
+    oracle's source."""
+    import scipy.linalg as sl
+
+    from oracle.messenger_pol import fluct_source_pol
+
+    nside, lmax = 2, 4
+    P, basis, d, nu, obs = _pol_case(oracle, nside, lmax, 47, corr=0.1, fwhm_arcmin=600.0, b_cut_deg=10.0,
+                                     n_disks=1, disk_radius_deg=20.0, noise_level_ell=lmax)
+    S = basis.per_mode(P["c_ell"])
+    rng = np.random.default_rng(48)
+    npx = 12 * nside * nside
+    g1 = rng.standard_normal((3, npx))
+    g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    r = fluct_source_pol(basis, nu, S, g1, g2)
+
+    pix = np.stack([sl.sqrtm(nu[p]).real @ g1[:, p] if obs[p] else np.zeros(3) for p in range(npx)], axis=1)
+    def pinv_root(B):  # scipy's root of the nonsingular sub-block on the active components, inverted
+        act = np.diag(B) > 0
+        out = np.zeros((3, 3))
+        out[np.ix_(act, act)] = np.linalg.inv(sl.sqrtm(B[np.ix_(act, act)]).real)
+        return out
+
+    h = np.stack([pinv_root(S[k]) @ g2[:, k] for k in range(basis.ell.size)], axis=1)
+    Y, W, modes = _dense_pol(oracle, nside, lmax)
+    z = (Y @ _to_x(h, modes)).reshape(3, npx)
+    ref = pix + basis.omega * z
+    np.testing.assert_allclose(r, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    assert np.all(r[:, ~obs] == pytest.approx(basis.omega * z[:, ~obs], rel=1e-12, abs=1e-14))
+
+
+def test_pol_fluct_source_decoupled_limit(oracle):
+    """Diagonal noise and TE = 0: the I part of the polarised source is the
+    temperature source of the same draws, and Q, U get g1 / sigma in each
+    observed pixel plus the spin-2 synthesis of (E, B) / sqrt(C_l)."""
+    from oracle.messenger_pol import fluct_source_pol
+
+    nside, lmax = 8, 16
+    P, basis, d, nu, obs = _pol_case(oracle, nside, lmax, 49, corr=0.0, fwhm_arcmin=120.0, n_disks=4,
+                                     disk_radius_deg=10.0)
+    cl = P["c_ell"].copy()
+    cl[:, 3] = 0.0
+    S = basis.per_mode(cl)
+    rng = np.random.default_rng(50)
+    npx = 12 * nside * nside
+    g1 = rng.standard_normal((3, npx))
+    g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    r = fluct_source_pol(basis, nu, S, g1, g2)
+    b0 = oracle.HealpixBasis(nside, lmax)
+    rT = oracle.fluct_source(b0, nu[:, 0, 0], b0.per_mode(cl[:, 0]), g1[0], g2[0])
+    np.testing.assert_allclose(r[0], rT, rtol=0, atol=1e-12 * np.max(np.abs(rT)))
+    e = np.where(cl[basis.ell, 1] > 0, g2[1] / np.sqrt(np.where(cl[basis.ell, 1] > 0, cl[basis.ell, 1], 1.0)), 0.0)
+    b = np.where(cl[basis.ell, 2] > 0, g2[2] / np.sqrt(np.where(cl[basis.ell, 2] > 0, cl[basis.ell, 2], 1.0)), 0.0)
+    Q, U = oracle.synthesis_pol(nside, lmax, lmax, e, b)
+    for c, z in ((1, Q), (2, U)):
+        ref = np.sqrt(nu[:, c, c]) * g1[c] + basis.omega * z
+        np.testing.assert_allclose(r[c], ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
