@@ -156,7 +156,8 @@ wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n);
  * covariance per pixel as 6 x n_pix (II, QQ, UU, IQ, IU, QU), positive definite
  * on observed pixels; the mask is shared by I, Q, U; C_ell is 4 x (lmax + 1)
  * (TT, EE, BB, TE), each block [[TT, TE, 0], [TE, EE, 0], [0, 0, BB]] positive
- * semi-definite (singular blocks act through their pseudo-inverse); alm_out is
+ * semi-definite with TE^2 < TT EE wherever TE != 0 (WF_EINVAL otherwise); zero
+ * entries act through the pseudo-inverse (e.g. BB = 0, or l < 2); alm_out is
  * 3 x n_alm (T, E, B).  Spin-2 convention: (Q + iU) = sum_{l >= 2, |m| <= l}
  * 2a_lm 2Y_lm, 2a = -(E + iB), sY_lm = sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta)
  * e^{i m phi}.  tau is the smallest eigenvalue of any observed noise block. */
@@ -172,7 +173,12 @@ wf_status wf_solve_host(wf_plan p, const double *d, const double *noise_var, con
  * source N^-1/2 g1 + S^-1/2 g2 (g1: n_pix FP64 unit normal draws; g2: unit
  * complex normal harmonic draws in the harmonic layout, m = 0 / kx-Hermitian
  * entries real).  f_out: n_pix FP64 with covariance (S^-1 + N^-1)^-1.
- * A constrained realisation is s_WF + f_out. */
+ * A constrained realisation is s_WF + f_out.
+ * Polarised plans (ncomp = 3): g1 3 x n_pix (I, Q, U), g2 3 x n_alm (T, E,
+ * B), f_out 3 x n_pix, noise and C_ell as for wf_solve; N^-1/2 is the
+ * symmetric square root of each pixel's inverse noise block and S^-1/2 the
+ * pseudo-inverse square root of each l's prior block.  chi2_over_ndof of the
+ * report is NaN (it needs data). */
 wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, const double *C_ell,
                    const double *g1, const double *g2, double tol, double *f_out, double *alm_out,
                    wf_info *info);

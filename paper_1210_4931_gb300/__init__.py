@@ -193,6 +193,14 @@ class Plan:
         self.precision = precision
         self.npix = int(load().wf_npix(handle))
         self.nalm = int(load().wf_nalm(handle))
+        self.ncomp = int(geometry.get("ncomp", 1))
+
+    @property
+    def sizes(self):
+        """Bytes of (a map argument, the noise argument, a harmonic argument):
+        polarised plans take 3 maps, 6 noise maps and 3 harmonic vectors."""
+        nc = self.ncomp
+        return nc * self.npix * 8, (6 if nc == 3 else 1) * self.npix * 8, nc * self.nalm * 16
 
     @property
     def device_bytes(self):
@@ -295,10 +303,10 @@ def wf_solve(plan: Plan, d, noise_var, mask, C_ell, tol, s_wf, alm_out=None, tra
     """Wiener filter; returns the report as a dict (status WF_OK or
     WF_ENOCONV; other statuses raise)."""
     info, bufs = _info(trace_cap)
-    n8 = plan.npix * 8
-    st = load().wf_solve(plan.handle, _ptr(d, _f64(d), n8, "d"), _ptr(noise_var, _f64(d), n8, "noise_var"),
+    n8, nn, nh = plan.sizes
+    st = load().wf_solve(plan.handle, _ptr(d, _f64(d), n8, "d"), _ptr(noise_var, _f64(d), nn, "noise_var"),
                          _ptr(mask, None, plan.npix, "mask"), _ptr(C_ell, _f64(d), None, "C_ell"), float(tol),
-                         _ptr(s_wf, _f64(d), n8, "s_wf"), _ptr(alm_out, _f64(d), plan.nalm * 16, "alm_out"),
+                         _ptr(s_wf, _f64(d), n8, "s_wf"), _ptr(alm_out, _f64(d), nh, "alm_out"),
                          ctypes.byref(info))
     _check(st, "wf_solve", allow=(WF_ENOCONV,))
     return _info_dict(st, info, bufs)
@@ -308,26 +316,30 @@ def wf_solve_host(plan: Plan, d, noise_var, mask, C_ell, tol, s_wf, alm_out=None
     """wf_solve on host numpy arrays; the library copies in and out."""
     info, bufs = _info(trace_cap)
 
-    def hp(a, dt):
+    def hp(a, dt, n=None):
         if a is None:
             return None
         assert a.dtype == dt and a.flags.c_contiguous
+        if n is not None and a.nbytes < n:
+            raise ValueError("host array too small (%d bytes, need %d)" % (a.nbytes, n))
         return ctypes.c_void_p(a.ctypes.data)
 
-    st = load().wf_solve_host(plan.handle, hp(d, np.float64), hp(noise_var, np.float64), hp(mask, np.uint8),
-                              hp(C_ell, np.float64), float(tol), hp(s_wf, np.float64),
-                              hp(alm_out, np.complex128), ctypes.byref(info))
+    n8, nn, nh = plan.sizes
+
+    st = load().wf_solve_host(plan.handle, hp(d, np.float64, n8), hp(noise_var, np.float64, nn),
+                              hp(mask, np.uint8, plan.npix), hp(C_ell, np.float64), float(tol),
+                              hp(s_wf, np.float64, n8), hp(alm_out, np.complex128, nh), ctypes.byref(info))
     _check(st, "wf_solve_host", allow=(WF_ENOCONV,))
     return _info_dict(st, info, bufs)
 
 
 def wf_fluct(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_out=None, trace_cap=0) -> dict:
     info, bufs = _info(trace_cap)
-    n8 = plan.npix * 8
-    st = load().wf_fluct(plan.handle, _ptr(noise_var, None, n8, "noise_var"), _ptr(mask, None, plan.npix, "mask"),
+    n8, nn, nh = plan.sizes
+    st = load().wf_fluct(plan.handle, _ptr(noise_var, None, nn, "noise_var"), _ptr(mask, None, plan.npix, "mask"),
                          _ptr(C_ell, None, None, "C_ell"), _ptr(g1, None, n8, "g1"),
-                         _ptr(g2, None, plan.nalm * 16, "g2"), float(tol), _ptr(f_out, None, n8, "f_out"),
-                         _ptr(alm_out, None, plan.nalm * 16, "alm_out"), ctypes.byref(info))
+                         _ptr(g2, None, nh, "g2"), float(tol), _ptr(f_out, None, n8, "f_out"),
+                         _ptr(alm_out, None, nh, "alm_out"), ctypes.byref(info))
     _check(st, "wf_fluct", allow=(WF_ENOCONV,))
     return _info_dict(st, info, bufs)
 
@@ -358,15 +370,19 @@ def wf_fluct_host(plan: Plan, noise_var, mask, C_ell, g1, g2, tol, f_out, alm_ou
     """wf_fluct with numpy (host) arrays; copies are made inside the call."""
     info, bufs = _info(trace_cap)
 
-    def hp(a, dt):
+    def hp(a, dt, n=None):
         if a is None:
             return None
         assert a.dtype == dt and a.flags.c_contiguous
+        if n is not None and a.nbytes < n:
+            raise ValueError("host array too small (%d bytes, need %d)" % (a.nbytes, n))
         return ctypes.c_void_p(a.ctypes.data)
 
-    st = load().wf_fluct_host(plan.handle, hp(noise_var, np.float64), hp(mask, np.uint8), hp(C_ell, np.float64),
-                              hp(g1, np.float64), hp(g2, np.complex128), float(tol), hp(f_out, np.float64),
-                              hp(alm_out, np.complex128), ctypes.byref(info))
+    n8, nn, nh = plan.sizes
+
+    st = load().wf_fluct_host(plan.handle, hp(noise_var, np.float64, nn), hp(mask, np.uint8, plan.npix),
+                              hp(C_ell, np.float64), hp(g1, np.float64, n8), hp(g2, np.complex128, nh), float(tol),
+                              hp(f_out, np.float64, n8), hp(alm_out, np.complex128, nh), ctypes.byref(info))
     _check(st, "wf_fluct_host", allow=(WF_ENOCONV,))
     return _info_dict(st, info, bufs)
 

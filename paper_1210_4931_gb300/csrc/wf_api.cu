@@ -1114,8 +1114,11 @@ wf_status pol_adjoint(wf_plan p, const double *map3, int L, double2 *out3)
 // Sect. 3 on the largest eigenvalue of each l's prior block (or a replay).
 // d: 3 x npix (I, Q, U); N6: 6 x npix noise covariance (II, QQ, UU, IQ, IU, QU);
 // C4: 4 x (lmax + 1) spectra (TT, EE, BB, TE); s_out 3 x npix; alm_out 3 x n_alm.
+// fluct: the fluctuation solve of Eq. (9) instead, source r = nu^1/2 g1 +
+// Omega Y (S^+1/2 g2) from g1 (3 x npix) and g2 (3 x n_alm), d unused.
 wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8_t *mask, const double *C4,
-                       double tol, double *s_out, double *alm_out, wf_info *info)
+                       double tol, bool fluct, const double *g1, const double2 *g2, double *s_out, double *alm_out,
+                       wf_info *info)
 {
     const wf_options o = defaults(p->opt);
     if (o.schedule == 1 && p->replay_lambda.empty())
@@ -1131,16 +1134,25 @@ wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8
     sch.c.resize(lmax + 1);
     for (int l = 0; l <= lmax; ++l) {
         const double tt = C[l], ee = C[lmax + 1 + l], bb = C[2 * (lmax + 1) + l], te = C[3 * (lmax + 1) + l];
+        // a TE correlation must be below 1 in magnitude (the pseudo-inverse of a
+        // singular TE block with TE != 0 is left undefined)
         if (!(std::isfinite(tt) && std::isfinite(ee) && std::isfinite(bb) && std::isfinite(te)) || tt < 0 ||
-            ee < 0 || bb < 0 || te * te > tt * ee * (1.0 + 1e-12))
-            return set_error(WF_EINVAL, "prior block of l = %d is not positive semi-definite", l);
+            ee < 0 || bb < 0 || (te != 0.0 && !(te * te < tt * ee)))
+            return set_error(WF_EINVAL, "prior block of l = %d is not positive semi-definite with |TE| < "
+                                        "sqrt(TT EE)", l);
         const double h = 0.5 * (tt - ee);
         sch.c[l] = std::max(0.5 * (tt + ee) + std::sqrt(h * h + te * te), bb);
     }
     double tau = 0;
     long long ndof = 0;
-    if ((st = hp_pol_setup(p, d, N6, mask, &tau, &ndof)) != WF_OK) return st;
+    if ((st = hp_pol_setup(p, fluct ? nullptr : d, N6, mask, &tau, &ndof)) != WF_OK) return st;
     const double tau_h = tau * p->omega;
+    if (fluct) {
+        // z = Y (S^+1/2 g2) into the output maps as scratch, then r = nu^1/2 g1 + Omega z
+        if ((st = hp_pol_isqrt_prior(p, C4, g2, P->a_new)) != WF_OK) return st;
+        if ((st = pol_synthesis(p, P->a_new, lmax, s_out, nullptr)) != WF_OK) return st;
+        if ((st = hp_pol_fluct_source(p, g1, s_out)) != WF_OK) return st;
+    }
     if ((st = pol_adjoint(p, P->r, lmax, P->b)) != WF_OK) return st;
     if ((st = hp_pol_alm_norm(p, C4, P->b, 1)) != WF_OK) return st;
     {
@@ -1237,18 +1249,23 @@ wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8
     if ((st = pol_synthesis(p, P->a, lmax, s_out, nullptr)) != WF_OK) return st;
     if (alm_out)
         WF_CUDA(cudaMemcpyAsync(alm_out, P->a, 3 * nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
-    int nb = 0;
-    if ((st = hp_pol_alm_norm(p, C4, P->a, 0)) != WF_OK) return st;
-    if ((st = hp_pol_pix_chi2(p, d, s_out, &nb)) != WF_OK) return st;
-    SumSpec sp{};
-    sp.in[0] = P->part2;
-    sp.n[0] = lmax + 1;
-    sp.stride[0] = 1;
-    sp.in[1] = P->part;
-    sp.n[1] = nb;
-    sp.stride[1] = 1;
-    if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
-    const double chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
+    double chi2n = NAN;  // chi^2 of the result needs data: not defined for the fluctuation solve
+    if (!fluct) {
+        int nb = 0;
+        if ((st = hp_pol_alm_norm(p, C4, P->a, 0)) != WF_OK) return st;
+        if ((st = hp_pol_pix_chi2(p, d, s_out, &nb)) != WF_OK) return st;
+        SumSpec sp{};
+        sp.in[0] = P->part2;
+        sp.n[0] = lmax + 1;
+        sp.stride[0] = 1;
+        sp.in[1] = P->part;
+        sp.n[1] = nb;
+        sp.stride[1] = 1;
+        if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
+        chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
+    } else {
+        WF_CUDA(cudaStreamSynchronize(p->stream));
+    }
     if (info) {
         info->iters = k;
         info->converged = converged ? 1 : 0;
@@ -1692,7 +1709,7 @@ wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const ui
             return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule is implemented on the HEALPix sphere only");
         return flat_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
     }
-    if (p->pol) return hp_solve_pol(p, d, noise_var, mask, C_ell, tol, s_wf, alm_out, info);
+    if (p->pol) return hp_solve_pol(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
     return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
 }
 
@@ -1714,7 +1731,9 @@ wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, cons
             return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
         return flat_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
     }
-    if (p->pol) return set_error(WF_EUNSUPPORTED, "the polarised fluctuation solve is not built in this version");
+    if (p->pol)
+        return hp_solve_pol(p, nullptr, noise_var, mask, C_ell, tol, true, g1, (const double2 *)g2, f_out, alm_out,
+                            info);
     return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
 }
 
@@ -1772,23 +1791,24 @@ wf_status wf_fluct_host(wf_plan p, const double *noise_var, const uint8_t *mask,
     const size_t npx = (size_t)p->npix;
     const size_t nS = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) : (size_t)p->lmax + 1;
     const size_t nh = p->g.kind == WF_GEOM_FLAT ? (size_t)p->g.ny * (p->g.nx / 2 + 1) * 2 : (size_t)p->nalm * 2;
+    const size_t nc = p->pol ? 3 : 1, nn = p->pol ? 6 : 1, ncl = p->pol ? 4 : 1;  // components per array
     wf_status st;
     if ((st = host_staging(p)) != WF_OK) return st;
     if (!p->ws.g1_in) {
-        if ((st = plan_alloc(p, (void **)&p->ws.g1_in, npx * 8)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.g2_in, nh * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.g1_in, nc * npx * 8)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.g2_in, nc * nh * 8)) != WF_OK) return st;
     }
     cudaStream_t s = p->stream;
-    WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, npx * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.nv_in, noise_var, nn * npx * 8, cudaMemcpyHostToDevice, s));
     if (mask) WF_CUDA(cudaMemcpyAsync(p->ws.mask_in, mask, npx, cudaMemcpyHostToDevice, s));
-    WF_CUDA(cudaMemcpyAsync(p->ws.cl_in, C_ell, nS * 8, cudaMemcpyHostToDevice, s));
-    WF_CUDA(cudaMemcpyAsync(p->ws.g1_in, g1, npx * 8, cudaMemcpyHostToDevice, s));
-    WF_CUDA(cudaMemcpyAsync(p->ws.g2_in, g2, nh * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.cl_in, C_ell, ncl * nS * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.g1_in, g1, nc * npx * 8, cudaMemcpyHostToDevice, s));
+    WF_CUDA(cudaMemcpyAsync(p->ws.g2_in, g2, nc * nh * 8, cudaMemcpyHostToDevice, s));
     st = wf_fluct(p, p->ws.nv_in, mask ? p->ws.mask_in : nullptr, p->ws.cl_in, p->ws.g1_in, p->ws.g2_in, tol,
                   p->ws.out_map, alm_out ? p->ws.alm_io : nullptr, info);
     if (st != WF_OK && st != WF_ENOCONV) return st;
-    WF_CUDA(cudaMemcpyAsync(f_out, p->ws.out_map, npx * 8, cudaMemcpyDeviceToHost, s));
-    if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nh * 8, cudaMemcpyDeviceToHost, s));
+    WF_CUDA(cudaMemcpyAsync(f_out, p->ws.out_map, nc * npx * 8, cudaMemcpyDeviceToHost, s));
+    if (alm_out) WF_CUDA(cudaMemcpyAsync(alm_out, p->ws.alm_io, nc * nh * 8, cudaMemcpyDeviceToHost, s));
     WF_CUDA(cudaStreamSynchronize(s));
     return st;
 }

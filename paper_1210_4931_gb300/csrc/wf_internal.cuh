@@ -244,6 +244,8 @@ wf_status hp_pol_blend(wf_plan p, double lam, double tau, int *nblocks);
 wf_status hp_pol_hblend(wf_plan p, int L, const double *C, double lam_tauh, double tauh, int want_resid);
 wf_status hp_pol_alm_norm(wf_plan p, const double *C, const double2 *a, int mode);
 wf_status hp_pol_pix_chi2(wf_plan p, const double *d, const double *s_map, int *nblocks);
+wf_status hp_pol_isqrt_prior(wf_plan p, const double *C, const double2 *g2, double2 *out);  // S^+1/2 g2
+wf_status hp_pol_fluct_source(wf_plan p, const double *g1, const double *z);  // r = nu^1/2 g1 + Omega z
 
 // flat grid (wf_flat.cu)
 wf_status flat_create(wf_plan p);

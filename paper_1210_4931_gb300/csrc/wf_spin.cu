@@ -416,6 +416,59 @@ __device__ double eigmin3(const Sym3 &s)
     return q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
 }
 
+// all three eigenvalues, descending (same trigonometric solution)
+__device__ void eig3(const Sym3 &s, double (&l)[3])
+{
+    const double p1 = s.d * s.d + s.e * s.e + s.f * s.f;
+    if (p1 == 0.0) {
+        l[0] = s.a;
+        l[1] = s.b;
+        l[2] = s.c;
+        return;
+    }
+    const double q = (s.a + s.b + s.c) / 3.0;
+    const double p2 = (s.a - q) * (s.a - q) + (s.b - q) * (s.b - q) + (s.c - q) * (s.c - q) + 2.0 * p1;
+    const double pp = sqrt(p2 / 6.0);
+    const Sym3 Bm{(s.a - q) / pp, (s.b - q) / pp, (s.c - q) / pp, s.d / pp, s.e / pp, s.f / pp};
+    const double r = fmin(1.0, fmax(-1.0, det3(Bm) / 2.0));
+    const double phi = acos(r) / 3.0;
+    l[0] = q + 2.0 * pp * cos(phi);
+    l[2] = q + 2.0 * pp * cos(phi + 2.0 * M_PI / 3.0);
+    l[1] = 3.0 * q - l[0] - l[2];
+}
+
+// X Y for symmetric X, Y that commute (so X Y is symmetric), symmetrised
+__device__ __forceinline__ Sym3 symmul(const Sym3 &X, const Sym3 &Y)
+{
+    const double p00 = X.a * Y.a + X.d * Y.d + X.e * Y.e, p11 = X.d * Y.d + X.b * Y.b + X.f * Y.f;
+    const double p22 = X.e * Y.e + X.f * Y.f + X.c * Y.c;
+    const double p01 = X.a * Y.d + X.d * Y.b + X.e * Y.f, p10 = X.d * Y.a + X.b * Y.d + X.f * Y.e;
+    const double p02 = X.a * Y.e + X.d * Y.f + X.e * Y.c, p20 = X.e * Y.a + X.f * Y.d + X.c * Y.e;
+    const double p12 = X.d * Y.e + X.b * Y.f + X.f * Y.c, p21 = X.e * Y.d + X.f * Y.b + X.c * Y.f;
+    return Sym3{p00, p11, p22, 0.5 * (p01 + p10), 0.5 * (p02 + p20), 0.5 * (p12 + p21)};
+}
+
+// symmetric square root of a symmetric positive definite 3x3 block.  With
+// mu_i = sqrt(lambda_i) and I1, I2, I3 the invariants of U = A^1/2, the
+// Cayley-Hamilton theorem for U (U^3 - I1 U^2 + I2 U - I3 = 0, U^2 = A) gives
+// U = (A + I2)^-1 (I1 A + I3); the invariants are symmetric in the eigenvalues,
+// so a close pair (where the trigonometric roots lose half their digits) costs
+// only second order.  One Newton step U <- (U + A U^-1) / 2 then restores full
+// accuracy for ill-conditioned blocks.
+__device__ Sym3 sqrt3(const Sym3 &A)
+{
+    double l[3];
+    eig3(A, l);
+    const double m0 = sqrt(fmax(l[0], 0.0)), m1 = sqrt(fmax(l[1], 0.0)), m2 = sqrt(fmax(l[2], 0.0));
+    const double I1 = m0 + m1 + m2, I2 = m0 * m1 + m0 * m2 + m1 * m2, I3 = m0 * m1 * m2;
+    const Sym3 K{A.a + I2, A.b + I2, A.c + I2, A.d, A.e, A.f};
+    const Sym3 R{I1 * A.a + I3, I1 * A.b + I3, I1 * A.c + I3, I1 * A.d, I1 * A.e, I1 * A.f};
+    const Sym3 U = symmul(inv3(K), R);
+    const Sym3 AUi = symmul(A, inv3(U));
+    return Sym3{0.5 * (U.a + AUi.a), 0.5 * (U.b + AUi.b), 0.5 * (U.c + AUi.c),
+                0.5 * (U.d + AUi.d), 0.5 * (U.e + AUi.e), 0.5 * (U.f + AUi.f)};
+}
+
 __device__ __forceinline__ void atomic_min_posd(double *addr, double v)
 {
     atomicMin(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
@@ -640,6 +693,57 @@ __global__ void k_hblend_pol(int lmax, int L, long long nalm, const double *__re
     }
 }
 
+// fluctuation source of Eq. (9) for (I, Q, U) maps: r = nu^1/2 g1 + Omega z,
+// z the synthesised S^+1/2 g2 (nu = 0 in masked pixels, where r = Omega z)
+__global__ void k_fluct_source_pol(long long npix, const double *__restrict__ nu6, const double *__restrict__ g1,
+                                   const double *__restrict__ z, double omega, double *__restrict__ r)
+{
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (long long)gridDim.x * blockDim.x) {
+        const Sym3 nu = load6(nu6, npix, p);
+        double o[3] = {0.0, 0.0, 0.0};
+        if (nu.a != 0.0 || nu.b != 0.0 || nu.c != 0.0) {
+            const double g[3] = {g1[p], g1[npix + p], g1[2 * npix + p]};
+            mv3(sqrt3(nu), g, o);
+        }
+        r[p] = o[0] + omega * z[p];
+        r[npix + p] = o[1] + omega * z[npix + p];
+        r[2 * npix + p] = o[2] + omega * z[2 * npix + p];
+    }
+}
+
+// S^+1/2 g2 per (l, m): the pseudo-inverse square root of the prior block.  A
+// TE block with TE != 0 is positive definite (checked on the host) and its
+// inverse square root is closed-form: with s = det^1/2 and t = (TT + EE + 2 s)^1/2,
+// [[TT, TE], [TE, EE]]^-1/2 = [[EE + s, -TE], [-TE, TT + s]] / (s t).
+__global__ void k_isqrt_S_pol(int lmax, long long nalm, const double *__restrict__ C, const double2 *__restrict__ g2,
+                              double2 *__restrict__ out)
+{
+    const int m = blockIdx.x;
+    const long long base = pmbase(lmax, m);
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+        const long long k = base + (l - m);
+        const Prior S = prior(C, lmax, l);
+        double jt, je, jx;
+        if (S.te != 0.0) {
+            const double sd = sqrt(S.tt * S.ee - S.te * S.te), t = sqrt(S.tt + S.ee + 2.0 * sd);
+            const double q = 1.0 / (sd * t);
+            jt = (S.ee + sd) * q;
+            je = (S.tt + sd) * q;
+            jx = -S.te * q;
+        } else {
+            jt = S.tt > 0.0 ? 1.0 / sqrt(S.tt) : 0.0;
+            je = S.ee > 0.0 ? 1.0 / sqrt(S.ee) : 0.0;
+            jx = 0.0;
+        }
+        const double jb = S.bb > 0.0 ? 1.0 / sqrt(S.bb) : 0.0;
+        const double2 gT = g2[k], gE = g2[nalm + k], gB = g2[2 * nalm + k];
+        out[k] = make_double2(jt * gT.x + jx * gE.x, jt * gT.y + jx * gE.y);
+        out[nalm + k] = make_double2(jx * gT.x + je * gE.x, jx * gT.y + je * gE.y);
+        out[2 * nalm + k] = make_double2(jb * gB.x, jb * gB.y);
+    }
+}
+
 // sum over observed pixels of (d - s)^T nu (d - s) (chi^2 of the result), per-block partials
 __global__ void k_pix_chi2_pol(long long npix, const double *__restrict__ d, const double *__restrict__ nu6,
                                const double *__restrict__ s, double *__restrict__ part)
@@ -797,6 +901,23 @@ wf_status hp_pol_hblend(wf_plan p, int L, const double *C, double lam_tauh, doub
 wf_status hp_pol_alm_norm(wf_plan p, const double *C, const double2 *a, int mode)
 {
     k_pol_alm_norm<<<p->lmax + 1, 256, 0, p->stream>>>(p->lmax, C, a, p->nalm, mode, p->pol->part2);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+wf_status hp_pol_isqrt_prior(wf_plan p, const double *C, const double2 *g2, double2 *out)
+{
+    k_isqrt_S_pol<<<p->lmax + 1, 256, 0, p->stream>>>(p->lmax, p->nalm, C, g2, out);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+wf_status hp_pol_fluct_source(wf_plan p, const double *g1, const double *z)
+{
+    const int grid = (int)std::min<long long>((p->npix + 255) / 256, 2LL * p->nsm);
+    k_fluct_source_pol<<<grid, 256, 0, p->stream>>>(p->npix, p->pol->nu, g1, z, p->omega, p->pol->r);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;

@@ -1,7 +1,7 @@
 """Polarised (I, Q, U) path on the GPU against the oracle: the spin-2 basis
 change (synthesis and its adjoint) to 1e-12, and the polarised messenger
-solve of Eqs. 10-11 (FP64) to 1e-10 against the oracle replaying the GPU's
-own (lambda, L) trace."""
+solve of Eqs. 10-11 and its fluctuation variant (Eq. 9), FP64, to 1e-10
+against the oracle replaying the GPU's own (lambda, L) trace."""
 import numpy as np
 import pytest
 
@@ -57,11 +57,11 @@ def test_pol_basis_change_matches_oracle(wf, nside, lmax):
     plan.close()
 
 
-def _pol_case(nside, lmax, seed):
+def _pol_case(nside, lmax, seed, corr=0.1):
     from oracle.messenger_pol import HealpixPolBasis
 
     P = gen.healpix_pol_problem(nside, lmax, seed, fwhm_arcmin=4 * 3438.0 / lmax, n_disks=6,
-                                disk_radius_deg=6.0, corr=0.1)
+                                disk_radius_deg=6.0, corr=corr)
     basis = HealpixPolBasis(nside, lmax)
     d = basis.synth(P["a_signal"]) + P["noise"]
     obs = P["mask"] > 0
@@ -124,9 +124,54 @@ def test_pol_rejections(wf):
     with pytest.raises(wf.WfError) as e:
         wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(badC.ravel()), 1e-6, s)
     assert e.value.status == wf.WF_EINVAL
+    badC = C4.copy()
+    badC[3, 12] = 1.0000001 * np.sqrt(badC[0, 12] * badC[1, 12])  # |rho_TE| just above 1
     g1 = T(np.zeros(3 * npx))
     g2 = T(np.zeros(3 * plan.nalm, dtype=np.complex128))
     with pytest.raises(wf.WfError) as e:
-        wf.wf_fluct(plan, T(N6.ravel()), T(P["mask"]), T(C4.ravel()), g1, g2, 1e-6, s)
+        wf.wf_fluct(plan, T(N6.ravel()), T(P["mask"]), T(badC.ravel()), g1, g2, 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    wf.wf_set_options(plan, schedule=1)
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(C4.ravel()), 1e-6, s)
     assert e.value.status == wf.WF_EUNSUPPORTED
+    plan.close()
+
+
+@pytest.mark.parametrize("nside,lmax,corr", [(8, 16, 0.1), (16, 32, 0.1), (8, 16, 0.0)])
+def test_pol_fluct_fp64_matches_oracle_replay(wf, nside, lmax, corr):
+    """Fluctuation solve of Eq. (9) on (I, Q, U): the source nu^1/2 g1 +
+    Omega Y (S^+1/2 g2) and the iteration against the oracle replaying the
+    GPU's trace; corr = 0 gives noise blocks with equal Q and U variances
+    (a repeated eigenvalue in the square root)."""
+    import torch
+
+    from oracle.messenger_pol import fluct_source_pol, messenger_solve_pol, pol_tau
+
+    P, basis, d, nu, obs, N6, C4 = _pol_case(nside, lmax, gen.seed_for(4, 200 + nside), corr=corr)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3)
+    npx = 12 * nside * nside
+    rng = np.random.default_rng(700 + nside)
+    g1 = rng.standard_normal((3, npx))
+    g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    f = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    alm = torch.empty(3 * plan.nalm, dtype=torch.complex128, device="cuda")
+    rep = wf.wf_fluct(plan, T(N6.ravel()), T(P["mask"]), T(C4.ravel()), T(g1.ravel()), T(g2.ravel()), 1e-7, f, alm,
+                      trace_cap=20000)
+    assert rep["converged"] and rep["final_residual"] < 1e-7
+    assert np.isnan(rep["chi2_over_ndof"])
+    tau = pol_tau(P["noise_cov"], obs)
+    S = basis.per_mode(P["c_ell"])
+    r = fluct_source_pol(basis, nu, S, g1, g2)
+    ref = messenger_solve_pol(basis, r, nu, S, tau, replay=list(zip(rep["lambda_trace"], rep["L_trace"])))
+    assert rel(alm.cpu().numpy().reshape(3, -1), ref["a"]) < 1e-10
+    assert rel(f.cpu().numpy().reshape(3, npx), ref["s"]) < 1e-10
+    np.testing.assert_allclose(rep["chi2_trace"], ref["chi2"], rtol=1e-10, atol=1e-10 * np.max(np.abs(ref["chi2"])))
+    # the host entry point gives the same map
+    fh = np.empty(3 * npx)
+    rep_h = wf.wf_fluct_host(plan, np.ascontiguousarray(N6.ravel()), np.ascontiguousarray(P["mask"]),
+                             np.ascontiguousarray(C4.ravel()), np.ascontiguousarray(g1.ravel()),
+                             np.ascontiguousarray(g2.ravel()), 1e-7, fh)
+    assert rep_h["iters"] == rep["iters"]
+    assert rel(fh, f.cpu().numpy()) < 1e-12
     plan.close()
