@@ -256,8 +256,11 @@ typedef enum { WF_REQ_WF = 0, WF_REQ_FLUCT = 1, WF_REQ_CR = 2 } wf_request_kind;
  * schedule (heuristic of Sect. 3 or a replay).  The graph is replayed while no
  * solve changes (lambda, L) and updated when one does.  Results equal those
  * of wf_solve / wf_fluct on the same plan (to rounding).  Items use device
- * pointers as in wf_solve; info may be NULL.  The chi^2-bound schedule is not
- * batchable (WF_EUNSUPPORTED).  cuda_stream: stream the graph is launched on;
+ * pointers as in wf_solve; info may be NULL.  Polarised plans (ncomp = 3)
+ * may be mixed with temperature plans; their items take the three-component
+ * layouts of wf_solve / wf_fluct (per-item sizes below are for ncomp = 1).
+ * The chi^2-bound schedule is not batchable (WF_EUNSUPPORTED).  cuda_stream:
+ * stream the graph is launched on;
  * statuses[i]: the status of item i (WF_OK / WF_ENOCONV / error).  The return
  * value reports argument and CUDA errors of the batch as a whole. */
 typedef struct {

@@ -403,8 +403,9 @@ def wf_plan_tiles(plan: Plan) -> tuple:
 def wf_solve_batch(plans, items, trace_cap=0, stream=None) -> list:
     """Several solves advanced together (one CUDA graph per step).  items:
     dicts with kind ('wf' or 'fluct'), d / g1 / g2, noise_var, mask, C_ell, tol,
-    s_out and optional alm_out (CUDA tensors).  Returns one report per item
-    (with its 'status'); argument or CUDA errors of the batch raise."""
+    s_out and optional alm_out (CUDA tensors; polarised plans take the
+    three-component layouts of wf_solve / wf_fluct).  Returns one report per
+    item (with its 'status'); argument or CUDA errors of the batch raise."""
     import torch
 
     n = len(plans)
@@ -416,18 +417,18 @@ def wf_solve_batch(plans, items, trace_cap=0, stream=None) -> list:
     for i, (pl, it) in enumerate(zip(plans, items)):
         info, bufs = _info(trace_cap)
         infos.append((info, bufs))
-        n8 = pl.npix * 8
+        n8, nn, nh = pl.sizes
         b = arr[i]
         b.kind = REQUEST_KINDS[it.get("kind", "wf")]
         b.d = _ptr(it.get("d"), None, n8, "d")
-        b.noise_var = _ptr(it["noise_var"], None, n8, "noise_var")
+        b.noise_var = _ptr(it["noise_var"], None, nn, "noise_var")
         b.mask = _ptr(it.get("mask"), None, pl.npix, "mask")
         b.C_ell = _ptr(it["C_ell"], None, None, "C_ell")
         b.g1 = _ptr(it.get("g1"), None, n8, "g1")
-        b.g2 = _ptr(it.get("g2"), None, pl.nalm * 16, "g2")
+        b.g2 = _ptr(it.get("g2"), None, nh, "g2")
         b.tol = float(it["tol"])
         b.s_out = _ptr(it["s_out"], None, n8, "s_out")
-        b.alm_out = _ptr(it.get("alm_out"), None, pl.nalm * 16, "alm_out")
+        b.alm_out = _ptr(it.get("alm_out"), None, nh, "alm_out")
         b.info = ctypes.cast(ctypes.byref(info), ctypes.c_void_p)
     if stream is None:
         stream = torch.cuda.current_stream()

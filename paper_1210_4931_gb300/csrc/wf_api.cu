@@ -688,12 +688,17 @@ struct HpRun {
     Prof pr;
 };
 
+wf_status hp_begin_pol(HpRun &R);
+wf_status hp_launch_pol(HpRun &R);
+wf_status hp_end_pol(HpRun &R);
+
 wf_status hp_begin(HpRun &R)
 {
     wf_plan p = R.p;
     R.o = defaults(p->opt);
     const wf_options &o = R.o;
     const int lmax = R.lmax = p->lmax;
+    if (p->pol) return hp_begin_pol(R);
     if (o.schedule == 1 && R.fluct && p->replay_lambda.empty())
         return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
     if (o.schedule == 1 && R.a_init && p->replay_lambda.empty())
@@ -794,6 +799,7 @@ bool hp_pick(HpRun &R)
 wf_status hp_launch(HpRun &R)
 {
     wf_plan p = R.p;
+    if (p->pol) return hp_launch_pol(R);
     Prof &pr = R.pr;
     const wf_options &o = R.o;
     const double tau = R.tau;
@@ -891,7 +897,10 @@ bool hp_absorb(HpRun &R)
     R.h_cur = p->ws.h_scal[3];  // x_{k+1}^T S^-1 x_{k+1} and x^T S^-2 x for the next lambda
     R.q_cur = p->ws.h_scal[4];
     record(R.info, R.k, R.lam, R.L, chi2, resid, ims);
-    if (!R.copy_back) std::swap(p->ws.a, p->ws.a_new);
+    if (!R.copy_back) {
+        if (p->pol) std::swap(p->pol->a, p->pol->a_new);
+        else std::swap(p->ws.a, p->ws.a_new);
+    }
     ++R.k;
     if (full) {
         R.last_resid = resid;
@@ -950,6 +959,7 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
 wf_status hp_end(HpRun &R)
 {
     wf_plan p = R.p;
+    if (p->pol) return hp_end_pol(R);
     const wf_options &o = R.o;
     const int lmax = R.lmax;
     Prof &pr = R.pr;
@@ -1114,23 +1124,24 @@ wf_status pol_adjoint(wf_plan p, const double *map3, int L, double2 *out3)
 // Sect. 3 on the largest eigenvalue of each l's prior block (or a replay).
 // d: 3 x npix (I, Q, U); N6: 6 x npix noise covariance (II, QQ, UU, IQ, IU, QU);
 // C4: 4 x (lmax + 1) spectra (TT, EE, BB, TE); s_out 3 x npix; alm_out 3 x n_alm.
-// fluct: the fluctuation solve of Eq. (9) instead, source r = nu^1/2 g1 +
+// R.fluct: the fluctuation solve of Eq. (9) instead, source r = nu^1/2 g1 +
 // Omega Y (S^+1/2 g2) from g1 (3 x npix) and g2 (3 x n_alm), d unused.
-wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8_t *mask, const double *C4,
-                       double tol, bool fluct, const double *g1, const double2 *g2, double *s_out, double *alm_out,
-                       wf_info *info)
+// The phases mirror the temperature ones (hp_begin / hp_launch / hp_end), so
+// the batched solver runs polarised items too.
+wf_status hp_begin_pol(HpRun &R)
 {
-    const wf_options o = defaults(p->opt);
+    wf_plan p = R.p;
+    const wf_options &o = R.o;
     if (o.schedule == 1 && p->replay_lambda.empty())
         return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule is built for temperature maps only");
     PolState *P = p->pol;
-    const int lmax = p->lmax;
-    const long long nalm = p->nalm, npix = p->npix;
-    Prof pr(p, info, o.profile != 0);
+    const int lmax = R.lmax;
+    const long long nalm = p->nalm;
+    R.pr.init(p, R.info, o.profile != 0 && !R.graph);
     wf_status st;
     std::vector<double> C((size_t)4 * (lmax + 1));
-    if ((st = to_host(p, C.data(), C4, C.size() * sizeof(double))) != WF_OK) return st;
-    HpSchedule sch;
+    if ((st = to_host(p, C.data(), R.C_ell, C.size() * sizeof(double))) != WF_OK) return st;
+    HpSchedule &sch = R.sch;
     sch.c.resize(lmax + 1);
     for (int l = 0; l <= lmax; ++l) {
         const double tt = C[l], ee = C[lmax + 1 + l], bb = C[2 * (lmax + 1) + l], te = C[3 * (lmax + 1) + l];
@@ -1143,28 +1154,26 @@ wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8
         const double h = 0.5 * (tt - ee);
         sch.c[l] = std::max(0.5 * (tt + ee) + std::sqrt(h * h + te * te), bb);
     }
-    double tau = 0;
-    long long ndof = 0;
-    if ((st = hp_pol_setup(p, fluct ? nullptr : d, N6, mask, &tau, &ndof)) != WF_OK) return st;
-    const double tau_h = tau * p->omega;
-    if (fluct) {
+    if ((st = hp_pol_setup(p, R.fluct ? nullptr : R.d, R.nv, R.mask, &R.tau, &R.ndof)) != WF_OK) return st;
+    R.tau_h = R.tau * p->omega;
+    if (R.fluct) {
         // z = Y (S^+1/2 g2) into the output maps as scratch, then r = nu^1/2 g1 + Omega z
-        if ((st = hp_pol_isqrt_prior(p, C4, g2, P->a_new)) != WF_OK) return st;
-        if ((st = pol_synthesis(p, P->a_new, lmax, s_out, nullptr)) != WF_OK) return st;
-        if ((st = hp_pol_fluct_source(p, g1, s_out)) != WF_OK) return st;
+        if ((st = hp_pol_isqrt_prior(p, R.C_ell, (const double2 *)R.g2, P->a_new)) != WF_OK) return st;
+        if ((st = pol_synthesis(p, P->a_new, lmax, R.s_out, nullptr)) != WF_OK) return st;
+        if ((st = hp_pol_fluct_source(p, R.g1, R.s_out)) != WF_OK) return st;
     }
     if ((st = pol_adjoint(p, P->r, lmax, P->b)) != WF_OK) return st;
-    if ((st = hp_pol_alm_norm(p, C4, P->b, 1)) != WF_OK) return st;
+    if ((st = hp_pol_alm_norm(p, R.C_ell, P->b, 1)) != WF_OK) return st;
     {
         SumSpec sp{};
         sp.in[0] = P->part2;
         sp.n[0] = lmax + 1;
         sp.stride[0] = 1;
-        if ((st = sums(p, sp, 1, &pr)) != WF_OK) return st;
+        if ((st = sums(p, sp, 1, &R.pr)) != WF_OK) return st;
     }
-    const double bnorm = std::sqrt(p->ws.h_scal[0]);
-    if (!(bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
-    sch.tau_h = tau_h;
+    R.bnorm = std::sqrt(p->ws.h_scal[0]);
+    if (!(R.bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
+    sch.tau_h = R.tau_h;
     sch.lmax = lmax;
     sch.step_max = o.ell_step_max;
     sch.margin = o.band_margin;
@@ -1172,88 +1181,66 @@ wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8
     sch.level();
     WF_CUDA(cudaMemsetAsync(P->a, 0, 3 * nalm * sizeof(double2), p->stream));
     WF_CUDA(cudaMemsetAsync(P->a_new, 0, 3 * nalm * sizeof(double2), p->stream));
-    const bool replay = !p->replay_lambda.empty();
-    const int nrep = (int)p->replay_lambda.size();
-    const double sigma = std::sqrt(2.0 * (double)ndof);
-    int k = 0, level_iters = 0, levels = 1;
-    bool have_prev = false, converged = false;
-    double prev_chi2 = 0, last_resid = NAN, best_resid = INFINITY;
-    wf_status result = WF_OK;
-    for (;;) {
-        double lam;
-        int L;
-        if (replay) {
-            if (k >= nrep) break;
-            lam = p->replay_lambda[k];
-            L = std::min(std::max(p->replay_L[k], 0), lmax);
-        } else {
-            if (k >= o.maxiter) { result = WF_ENOCONV; break; }
-            lam = sch.lam;
-            L = sch.L;
-        }
-        const bool full = (lam == 1.0 && L == lmax);
-        pr.iter_begin();
-        pr.begin(WF_K_LEG_SYN);
-        if ((st = pol_synthesis(p, P->a, L, nullptr, P->t)) != WF_OK) return st;
-        pr.end();
-        int nb = 0;
-        if ((st = hp_pol_blend(p, lam, tau, &nb)) != WF_OK) return st;
-        pr.begin(WF_K_LEG_ANA);
-        if ((st = pol_adjoint(p, P->t, L, P->b)) != WF_OK) return st;
-        if ((st = hp_pol_hblend(p, L, C4, lam * tau_h, tau_h, full ? 1 : 0)) != WF_OK) return st;
-        pr.end();
-        SumSpec sp{};
-        sp.in[0] = P->part;
-        sp.n[0] = nb;
-        sp.stride[0] = 1;
-        sp.in[1] = P->part2;
-        sp.n[1] = lmax + 1;
-        sp.stride[1] = 2;
-        sp.in[2] = P->part2 + 1;
-        sp.n[2] = lmax + 1;
-        sp.stride[2] = 2;
-        if ((st = sums(p, sp, 3, &pr)) != WF_OK) return st;
-        const double ims = pr.iter_end();
-        pr.collect();
-        const double chi2 = p->ws.h_scal[0] + p->ws.h_scal[1];
-        const double resid = full ? std::sqrt(p->ws.h_scal[2]) / bnorm : NAN;
-        record(info, k, lam, L, chi2, resid, ims);
-        std::swap(P->a, P->a_new);
-        ++k;
-        if (full) {
-            last_resid = resid;
-            if (!std::isfinite(resid) || (k > 50 && resid > 1e3 * best_resid)) { result = WF_EDIVERGE; break; }
-            best_resid = std::min(best_resid, resid);
-        }
-        if (!std::isfinite(chi2)) { result = WF_EDIVERGE; break; }
-        if (replay) {
-            if (full && resid < tol) converged = true;
-            continue;
-        }
-        if (sch.final_level()) {
-            if (resid < tol) { converged = true; break; }
-        } else {
-            ++level_iters;
-            const bool plateau = have_prev && std::fabs(chi2 - prev_chi2) < o.eta * sigma;
-            if (plateau || level_iters >= o.level_cap) {
-                sch.advance();
-                ++levels;
-                have_prev = false;
-                level_iters = 0;
-                continue;
-            }
-        }
-        prev_chi2 = chi2;
-        have_prev = true;
-    }
-    if ((st = pol_synthesis(p, P->a, lmax, s_out, nullptr)) != WF_OK) return st;
-    if (alm_out)
-        WF_CUDA(cudaMemcpyAsync(alm_out, P->a, 3 * nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    R.replay = !p->replay_lambda.empty();
+    R.nrep = (int)p->replay_lambda.size();
+    R.rigorous = false;
+    R.sigma = std::sqrt(2.0 * (double)R.ndof);
+    return WF_OK;
+}
+
+// one polarised messenger iteration (Eqs. 10-11) and its sums [chi^2 pixel
+// term, chi^2 harmonic term, residual^2], enqueued on the plan's stream
+wf_status hp_launch_pol(HpRun &R)
+{
+    wf_plan p = R.p;
+    PolState *P = p->pol;
+    Prof &pr = R.pr;
+    const int L = R.L;
+    const bool full = (R.lam == 1.0 && L == R.lmax);
+    wf_status st;
+    pr.iter_begin();
+    R.chi2_bound = NAN;
+    pr.begin(WF_K_LEG_SYN);
+    if ((st = pol_synthesis(p, P->a, L, nullptr, P->t)) != WF_OK) return st;
+    pr.end();
+    int nb = 0;
+    if ((st = hp_pol_blend(p, R.lam, R.tau, &nb)) != WF_OK) return st;
+    pr.begin(WF_K_LEG_ANA);
+    if ((st = pol_adjoint(p, P->t, L, P->b)) != WF_OK) return st;
+    if ((st = hp_pol_hblend(p, L, R.C_ell, R.lam * R.tau_h, R.tau_h, full ? 1 : 0)) != WF_OK) return st;
+    pr.end();
+    SumSpec sp{};
+    sp.in[0] = P->part;
+    sp.n[0] = nb;
+    sp.stride[0] = 1;
+    sp.in[1] = P->part2;
+    sp.n[1] = R.lmax + 1;
+    sp.stride[1] = 2;
+    sp.in[2] = P->part2 + 1;
+    sp.n[2] = R.lmax + 1;
+    sp.stride[2] = 2;
+    if ((st = sums_enqueue(p, sp, 3)) != WF_OK) return st;
+    if (R.copy_back)
+        WF_CUDA(cudaMemcpyAsync(P->a, P->a_new, 3 * p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    return WF_OK;
+}
+
+// output maps, chi^2 of the result (Wiener filter), report
+wf_status hp_end_pol(HpRun &R)
+{
+    wf_plan p = R.p;
+    PolState *P = p->pol;
+    const int lmax = R.lmax;
+    wf_status st;
+    if ((st = pol_synthesis(p, P->a, lmax, R.s_out, nullptr)) != WF_OK) return st;
+    if (R.alm_out)
+        WF_CUDA(cudaMemcpyAsync(R.alm_out, P->a, 3 * p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                p->stream));
     double chi2n = NAN;  // chi^2 of the result needs data: not defined for the fluctuation solve
-    if (!fluct) {
+    if (!R.fluct) {
         int nb = 0;
-        if ((st = hp_pol_alm_norm(p, C4, P->a, 0)) != WF_OK) return st;
-        if ((st = hp_pol_pix_chi2(p, d, s_out, &nb)) != WF_OK) return st;
+        if ((st = hp_pol_alm_norm(p, R.C_ell, P->a, 0)) != WF_OK) return st;
+        if ((st = hp_pol_pix_chi2(p, R.d, R.s_out, &nb)) != WF_OK) return st;
         SumSpec sp{};
         sp.in[0] = P->part2;
         sp.n[0] = lmax + 1;
@@ -1261,28 +1248,57 @@ wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8
         sp.in[1] = P->part;
         sp.n[1] = nb;
         sp.stride[1] = 1;
-        if ((st = sums(p, sp, 2, &pr)) != WF_OK) return st;
-        chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)ndof;
+        if ((st = sums(p, sp, 2, &R.pr)) != WF_OK) return st;
+        chi2n = (p->ws.h_scal[0] + p->ws.h_scal[1]) / (double)R.ndof;
     } else {
         WF_CUDA(cudaStreamSynchronize(p->stream));
     }
-    if (info) {
-        info->iters = k;
-        info->converged = converged ? 1 : 0;
-        info->final_residual = last_resid;
+    if (R.info) {
+        wf_info *info = R.info;
+        info->iters = R.k;
+        info->converged = R.converged ? 1 : 0;
+        info->final_residual = R.last_resid;
         info->chi2_over_ndof = chi2n;
-        info->n_dof = ndof;
-        info->tau = tau;
-        info->n_levels = levels;
+        info->n_dof = R.ndof;
+        info->tau = R.tau;
+        info->n_levels = R.levels;
         info->refine_sweeps = 0;
         info->mixed_lc = 0;
     }
-    pr.finish();
-    if (result == WF_OK && !replay && !converged) result = WF_ENOCONV;
-    if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", last_resid);
-    if (result == WF_EDIVERGE) set_error(result, "residual grew (%.3e)", last_resid);
-    (void)npix;
+    R.pr.finish();
+    wf_status result = R.result;
+    if (result == WF_OK && !R.replay && !R.converged) result = WF_ENOCONV;
+    if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", R.last_resid);
+    if (result == WF_EDIVERGE && R.chi2_bad) set_error(result, "chi^2 is not finite at iteration %d", R.k);
+    else if (result == WF_EDIVERGE) set_error(result, "residual grew (%.3e)", R.last_resid);
     return result;
+}
+
+wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8_t *mask, const double *C4,
+                       double tol, bool fluct, const double *g1, const double2 *g2, double *s_out, double *alm_out,
+                       wf_info *info)
+{
+    HpRun R;
+    R.p = p;
+    R.d = d;
+    R.nv = N6;
+    R.mask = mask;
+    R.C_ell = C4;
+    R.tol = tol;
+    R.fluct = fluct;
+    R.g1 = g1;
+    R.g2 = (const double *)g2;
+    R.s_out = s_out;
+    R.alm_out = alm_out;
+    R.info = info;
+    wf_status st = hp_begin(R);
+    if (st != WF_OK) return st;
+    while (hp_pick(R)) {
+        if ((st = hp_launch(R)) != WF_OK) return st;
+        WF_CUDA(cudaStreamSynchronize(p->stream));
+        if (!hp_absorb(R)) break;
+    }
+    return hp_end(R);
 }
 
 // Several HEALPix solves advanced together: one step of every active solve
@@ -1298,7 +1314,6 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
     for (int i = 0; i < n; ++i) {
         if (!plans[i] || plans[i]->g.kind != WF_GEOM_HEALPIX)
             return set_error(WF_EINVAL, "batch item %d: needs a HEALPix plan", i);
-        if (plans[i]->pol) return set_error(WF_EUNSUPPORTED, "batch item %d: polarised plans are not batched", i);
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return set_error(WF_EINVAL, "batch items %d and %d share a plan", j, i);
         const wf_batch_item &it = items[i];

@@ -31,6 +31,27 @@ def healpix_case(nside, lmax, seed, **kw):
     return P, basis, d, nu, tau
 
 
+def healpix_pol_case(nside, lmax, seed, corr=0.1, **kw):
+    """Polarised problem + (I, Q, U) data made with the oracle's synthesis, the
+    inverse noise blocks, and the device layouts: N6 (6 x npix: II, QQ, UU,
+    IQ, IU, QU) and C4 (4 x (lmax + 1): TT, EE, BB, TE)."""
+    from oracle.messenger_pol import HealpixPolBasis
+
+    kw.setdefault("fwhm_arcmin", 4 * 3438.0 / lmax)
+    kw.setdefault("n_disks", 6)
+    kw.setdefault("disk_radius_deg", 6.0)
+    P = gen.healpix_pol_problem(nside, lmax, seed, corr=corr, **kw)
+    basis = HealpixPolBasis(nside, lmax)
+    d = basis.synth(P["a_signal"]) + P["noise"]
+    obs = P["mask"] > 0
+    nu = np.zeros_like(P["noise_cov"])
+    nu[obs] = np.linalg.inv(P["noise_cov"][obs])
+    Nc = P["noise_cov"]
+    N6 = np.stack([Nc[:, 0, 0], Nc[:, 1, 1], Nc[:, 2, 2], Nc[:, 0, 1], Nc[:, 0, 2], Nc[:, 1, 2]])
+    C4 = np.ascontiguousarray(P["c_ell"].T)
+    return P, basis, d, nu, obs, N6, C4
+
+
 def rel(a, b):
     a = np.asarray(a)
     b = np.asarray(b)

@@ -132,3 +132,55 @@ def test_autotuned_tiles_keep_the_results(wf):
     p64 = wf.wf_plan_create("healpix", nside=16, lmax=32, precision="fp64")
     assert wf.wf_plan_autotune(p64) == (4, 8)
     p64.close()
+
+
+def test_batch_of_polarised_constrained_realisations(wf):
+    """(I, Q, U) Wiener-filter and fluctuation solves of mixed nside, paired
+    per map (a constrained realisation is s_WF + f), in one batch beside a
+    temperature solve: each item equals the same solve run alone (FP64, to
+    1e-10, same iterations and launch count)."""
+    import torch
+
+    from gpu_util import healpix_pol_case
+
+    geoms = [(8, 16), (16, 32), (32, 64)]
+    plans, items, alone = [], [], []
+    for j, (nside, lmax) in enumerate(geoms):
+        P, basis, d, nu, obs, N6, C4 = healpix_pol_case(nside, lmax, gen.seed_for(4, 300 + j))
+        rng = np.random.default_rng(3000 + j)
+        npx = 12 * nside * nside
+        g1 = rng.standard_normal((3, npx))
+        g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+        for kind in ("wf", "fluct"):
+            it = {"kind": kind, "noise_var": T(N6.ravel()), "mask": T(P["mask"]), "C_ell": T(C4.ravel()), "tol": 1e-7,
+                  "s_out": torch.full((3 * npx,), float("nan"), dtype=torch.float64, device="cuda")}
+            if kind == "wf":
+                it["d"] = T(d.ravel())
+            else:
+                it["g1"] = T(g1.ravel())
+                it["g2"] = T(g2.ravel())
+            pl = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3)
+            s = torch.empty_like(it["s_out"])
+            if kind == "wf":
+                rep = wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], 1e-7, s, trace_cap=20000)
+            else:
+                rep = wf.wf_fluct(pl, it["noise_var"], it["mask"], it["C_ell"], it["g1"], it["g2"], 1e-7, s,
+                                  trace_cap=20000)
+            pl.close()
+            alone.append((s.cpu().numpy(), rep))
+            plans.append(wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3))
+            items.append(it)
+    n, l, p, k, t = CASES[0]
+    it = _item(0, n, l, k, t)
+    alone.append(_alone(wf, n, l, p, it))
+    plans.append(wf.wf_plan_create("healpix", nside=n, lmax=l, precision=p))
+    items.append(it)
+    reps = wf.wf_solve_batch(plans, items, trace_cap=20000)
+    for i, (it, rep, (s_alone, rep_alone)) in enumerate(zip(items, reps, alone)):
+        assert rep["status"] == wf.WF_OK, (i, rep["status"])
+        assert rel(it["s_out"].cpu().numpy(), s_alone) < 1e-10, (i, rel(it["s_out"].cpu().numpy(), s_alone))
+        assert rep["iters"] == rep_alone["iters"]
+        np.testing.assert_array_equal(rep["lambda_trace"], rep_alone["lambda_trace"])
+        assert rep["launches"] == rep_alone["launches"] > 0
+    for pl in plans:
+        pl.close()

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import wf_inputs as gen
-from gpu_util import T, rel
+from gpu_util import T, healpix_pol_case, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -58,19 +58,7 @@ def test_pol_basis_change_matches_oracle(wf, nside, lmax):
 
 
 def _pol_case(nside, lmax, seed, corr=0.1):
-    from oracle.messenger_pol import HealpixPolBasis
-
-    P = gen.healpix_pol_problem(nside, lmax, seed, fwhm_arcmin=4 * 3438.0 / lmax, n_disks=6,
-                                disk_radius_deg=6.0, corr=corr)
-    basis = HealpixPolBasis(nside, lmax)
-    d = basis.synth(P["a_signal"]) + P["noise"]
-    obs = P["mask"] > 0
-    nu = np.zeros_like(P["noise_cov"])
-    nu[obs] = np.linalg.inv(P["noise_cov"][obs])
-    N6 = np.stack([P["noise_cov"][:, 0, 0], P["noise_cov"][:, 1, 1], P["noise_cov"][:, 2, 2],
-                   P["noise_cov"][:, 0, 1], P["noise_cov"][:, 0, 2], P["noise_cov"][:, 1, 2]])
-    C4 = np.ascontiguousarray(P["c_ell"].T)
-    return P, basis, d, nu, obs, N6, C4
+    return healpix_pol_case(nside, lmax, seed, corr=corr)
 
 
 @pytest.mark.parametrize("nside,lmax", [(8, 16), (16, 32)])
