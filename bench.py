@@ -70,6 +70,11 @@ def parse():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-maxiter", type=int, default=3000)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default Legendre tiles")
+    ap.add_argument("--pol-batch", type=int, default=0,
+                    help="batched polarised constrained realisations of this many (I, Q, U) maps")
+    ap.add_argument("--pol-nsides", default="32,64,128", help="nside choices of the polarised maps (lmax = 2 nside)")
+    ap.add_argument("--pol-tol", type=float, default=1e-4)
+    ap.add_argument("--pol-maxiter", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=0,
                     help="batching workload instead: this many solves of mixed nside (64-256), "
                          "run one by one and as one wf_solve_batch")
@@ -577,6 +582,104 @@ def run_batch(args):
     return 0
 
 
+def run_pol_batch(args):
+    """Batched polarised constrained realisations: each (I, Q, U) map is a
+    Wiener-filter solve plus a fluctuation solve (s_CR = s_WF + f), the pairs of
+    all maps advanced together by wf_solve_batch; against the same solves one
+    by one.  Also the per-iteration kernel-family times of one full-band
+    polarised iteration at the largest nside."""
+    import torch
+
+    import paper_1210_4931_gb300 as wf
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wf.load()
+    rng = np.random.default_rng(gen.seed_for(4, 1))
+    n = args.pol_batch
+    choices = [int(x) for x in args.pol_nsides.split(",")]
+    nsides = rng.choice(choices, size=n)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    items, geo = [], []
+    for i, ns in enumerate(nsides):
+        ns = int(ns)
+        lmax = 2 * ns
+        P = gen.healpix_pol_problem(ns, lmax, gen.seed_for(4, 100 + i), fwhm_arcmin=5.0 * 2048 / ns, corr=0.1,
+                                    b_cut_deg=20.0, n_disks=100, disk_radius_deg=1.0)
+        helper = wf.wf_plan_create("healpix", nside=ns, lmax=lmax, precision="fp64", ncomp=3)
+        sig = torch.empty(3 * helper.npix, dtype=torch.float64, device=dev)
+        wf.wf_alm2map(helper, T(P["a_signal"].ravel()), lmax, sig)
+        helper.close()
+        Nc = P["noise_cov"]
+        N6 = np.stack([Nc[:, 0, 0], Nc[:, 1, 1], Nc[:, 2, 2], Nc[:, 0, 1], Nc[:, 0, 2], Nc[:, 1, 2]])
+        common = {"noise_var": T(N6.ravel()), "mask": T(P["mask"]), "C_ell": T(P["c_ell"].T.ravel()),
+                  "tol": args.pol_tol}
+        items.append(dict(common, kind="wf", d=sig + T(P["noise"].ravel()), s_out=torch.empty_like(sig)))
+        items.append(dict(common, kind="fluct", g1=T(P["g1"].ravel()), g2=T(P["g2"].ravel()),
+                          s_out=torch.empty_like(sig)))
+        geo += [(ns, lmax)] * 2
+    plans = [wf.wf_plan_create("healpix", nside=ns, lmax=l, precision="fp64", ncomp=3) for ns, l in geo]
+    for pl in plans:
+        wf.wf_set_options(pl, maxiter=args.pol_maxiter)
+    stream = torch.cuda.current_stream()
+
+    def one_by_one():
+        reps = []
+        for pl, it in zip(plans, items):
+            if it["kind"] == "wf":
+                reps.append(wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], it["tol"], it["s_out"]))
+            else:
+                reps.append(wf.wf_fluct(pl, it["noise_var"], it["mask"], it["C_ell"], it["g1"], it["g2"], it["tol"],
+                                        it["s_out"]))
+        return reps
+
+    def batched():
+        return wf.wf_solve_batch(plans, items)
+
+    out = {}
+    for name, fn in (("one_by_one", one_by_one), ("batched", batched)):
+        fn()  # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            e0.record(stream)
+            reps = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        iters = sum(r["iters"] for r in reps)
+        ms = float(np.median(ts))
+        out[name] = {"ms": ms, "iters": iters, "crs_per_s": n / (ms / 1e3), "iters_per_s": iters / (ms / 1e3),
+                     "converged": int(sum(r["converged"] for r in reps)), "launches": int(sum(r["launches"] for r in reps))}
+    # kernel families of one full-band polarised iteration at the largest nside (profiled replay)
+    nb = int(max(nsides))
+    it = items[int(np.argmax(nsides)) * 2]
+    pl = wf.wf_plan_create("healpix", nside=nb, lmax=2 * nb, precision="fp64", ncomp=3)
+    wf.wf_set_options(pl, profile=1)
+    k = 6
+    wf.wf_set_schedule(pl, [1.0] * k, [2 * nb] * k)
+    rep = wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], 1e-30, it["s_out"], trace_cap=k)
+    fam = {kname: v / k for kname, v in rep["kernel_ms"].items() if v > 0}
+    iter_ms = float(np.median(rep["iter_ms_trace"][1:]))
+    pl.close()
+    res = {"metric": "batched polarised constrained realisations (WF + fluctuation pairs) per second",
+           "unit": "CR/s", "value": out["batched"]["crs_per_s"], "n_gpus": 1, "higher_is_better": True,
+           "maps": n, "nsides": [int(x) for x in nsides], "one_by_one": out["one_by_one"],
+           "batched": out["batched"], "speedup": out["one_by_one"]["ms"] / out["batched"]["ms"],
+           "full_band_iteration": {"nside": nb, "lmax": 2 * nb, "ms": iter_ms, "families_ms": fam},
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "batch_IQU_CR_nside" + "-".join(str(c) for c in choices), "precision": "fp64",
+                      "tol": args.pol_tol, "maxiter": args.pol_maxiter,
+                      "timing": "CUDA events around the whole call, median of --steps runs"}}
+    for p_ in plans:
+        p_.close()
+    if rank == 0:
+        print(json.dumps(res))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -585,6 +688,8 @@ def main():
         return run_serve(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.pol_batch > 0:
+        return run_pol_batch(args)
     return run_ours(args)
 
 
