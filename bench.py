@@ -75,6 +75,7 @@ def parse():
     ap.add_argument("--pol-nsides", default="32,64,128", help="nside choices of the polarised maps (lmax = 2 nside)")
     ap.add_argument("--pol-tol", type=float, default=1e-4)
     ap.add_argument("--pol-maxiter", type=int, default=3000)
+    ap.add_argument("--pol-precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--batch", type=int, default=0,
                     help="batching workload instead: this many solves of mixed nside (64-256), "
                          "run one by one and as one wf_solve_batch")
@@ -619,7 +620,8 @@ def run_pol_batch(args):
         items.append(dict(common, kind="fluct", g1=T(P["g1"].ravel()), g2=T(P["g2"].ravel()),
                           s_out=torch.empty_like(sig)))
         geo += [(ns, lmax)] * 2
-    plans = [wf.wf_plan_create("healpix", nside=ns, lmax=l, precision="fp64", ncomp=3) for ns, l in geo]
+    prec = args.pol_precision
+    plans = [wf.wf_plan_create("healpix", nside=ns, lmax=l, precision=prec, ncomp=3) for ns, l in geo]
     for pl in plans:
         wf.wf_set_options(pl, maxiter=args.pol_maxiter)
     stream = torch.cuda.current_stream()
@@ -656,8 +658,8 @@ def run_pol_batch(args):
     # kernel families of one full-band polarised iteration at the largest nside (profiled replay)
     nb = int(max(nsides))
     it = items[int(np.argmax(nsides)) * 2]
-    pl = wf.wf_plan_create("healpix", nside=nb, lmax=2 * nb, precision="fp64", ncomp=3)
-    wf.wf_set_options(pl, profile=1)
+    pl = wf.wf_plan_create("healpix", nside=nb, lmax=2 * nb, precision=prec, ncomp=3)
+    wf.wf_set_options(pl, profile=1, refine_sweeps=0)
     k = 6
     wf.wf_set_schedule(pl, [1.0] * k, [2 * nb] * k)
     rep = wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], 1e-30, it["s_out"], trace_cap=k)
@@ -669,8 +671,8 @@ def run_pol_batch(args):
            "maps": n, "nsides": [int(x) for x in nsides], "one_by_one": out["one_by_one"],
            "batched": out["batched"], "speedup": out["one_by_one"]["ms"] / out["batched"]["ms"],
            "full_band_iteration": {"nside": nb, "lmax": 2 * nb, "ms": iter_ms, "families_ms": fam},
-           "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "batch_IQU_CR_nside" + "-".join(str(c) for c in choices), "precision": "fp64",
+           "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
+           "config": {"workload": "batch_IQU_CR_nside" + "-".join(str(c) for c in choices), "precision": prec,
                       "tol": args.pol_tol, "maxiter": args.pol_maxiter,
                       "timing": "CUDA events around the whole call, median of --steps runs"}}
     for p_ in plans:

@@ -1091,33 +1091,65 @@ wf_status hp_solve(wf_plan p, const double *d, const double *nv, const uint8_t *
 
 // (T, E, B) -> (I, Q, U) maps: FP64 map out (omap, 3 x npix) or the plan's
 // working maps (tmap) when omap is null; l <= L
-wf_status pol_synthesis(wf_plan p, const double2 *a3, int L, double *omap, double *tmap)
+wf_status pol_synthesis(wf_plan p, const double2 *a3, int L, double *omap, void *tmap)
 {
     PolState *P = p->pol;
     const long long nalm = p->nalm, npix = p->npix;
     const RingSynMode mode = omap ? RS_MAP : RS_SYN;
+    const size_t es = p->prec == WF_PREC_FP64 ? sizeof(double) : sizeof(float);
+    auto tm = [&](int c) -> void * { return tmap ? (void *)((char *)tmap + (size_t)c * npix * es) : nullptr; };
+    auto om = [&](int c) -> double * { return omap ? omap + (size_t)c * npix : nullptr; };
     wf_status st;
-    if ((st = hp_legendre_synthesis_buf(p, a3, L, (double2 *)p->ws.G)) != WF_OK) return st;
-    if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, p->ws.G, tmap, omap)) != WF_OK) return st;
-    if ((st = hp_pol_legendre_synthesis(p, a3 + nalm, a3 + 2 * nalm, L)) != WF_OK) return st;
-    if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, P->GQ, tmap ? tmap + npix : nullptr,
-                                    omap ? omap + npix : nullptr)) != WF_OK)
+    if (p->prec == WF_PREC_FP64) {
+        if ((st = hp_legendre_synthesis_buf(p, a3, L, (double2 *)p->ws.G)) != WF_OK) return st;
+        if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, p->ws.G, tm(0), om(0))) != WF_OK) return st;
+        if ((st = hp_pol_legendre_synthesis(p, a3 + nalm, a3 + 2 * nalm, L)) != WF_OK) return st;
+        if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, P->GQ, tm(1), om(1))) != WF_OK) return st;
+        return hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, P->GU, tm(2), om(2));
+    }
+    // mixed: T through the temperature kernels (with their FP64 block), E, B
+    // through the FP32 spin-2 kernels, whose FP64 block the ring pass adds
+    if ((st = hp_legendre_synthesis(p, a3, L)) != WF_OK) return st;
+    if ((st = hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, p->ws.G, tm(0), om(0))) != WF_OK) return st;
+    if ((st = hp_pol_legendre_synthesis_mx(p, a3 + nalm, a3 + 2 * nalm, L)) != WF_OK) return st;
+    const bool low = P->lc > 0;
+    if ((st = hp_ring_synthesis_buf_low(p, L, mode, 1.0, 0.0, P->GQ, low ? P->GQlow : nullptr, P->lc, P->low_cap,
+                                        tm(1), om(1))) != WF_OK)
         return st;
-    return hp_ring_synthesis_buf(p, L, mode, 1.0, 0.0, P->GU, tmap ? tmap + 2 * npix : nullptr,
-                                 omap ? omap + 2 * npix : nullptr);
+    return hp_ring_synthesis_buf_low(p, L, mode, 1.0, 0.0, P->GU, low ? P->GUlow : nullptr, P->lc, P->low_cap,
+                                     tm(2), om(2));
 }
 
-// adjoint: (I, Q, U) maps (FP64, 3 x npix) -> (T, E, B) = Y^T map, l <= L
-wf_status pol_adjoint(wf_plan p, const double *map3, int L, double2 *out3)
+// adjoint: (I, Q, U) maps in the working precision (3 x npix) -> (T, E, B) = Y^T map, l <= L
+wf_status pol_adjoint(wf_plan p, const void *map3, int L, double2 *out3)
 {
     PolState *P = p->pol;
     const long long nalm = p->nalm, npix = p->npix;
     wf_status st;
-    if ((st = hp_ring_analysis_buf(p, L, map3, p->ws.F)) != WF_OK) return st;
-    if ((st = hp_legendre_adjoint_buf(p, L, (const double2 *)p->ws.F, out3)) != WF_OK) return st;
-    if ((st = hp_ring_analysis_buf(p, L, map3 + npix, P->FQ)) != WF_OK) return st;
-    if ((st = hp_ring_analysis_buf(p, L, map3 + 2 * npix, P->FU)) != WF_OK) return st;
-    return hp_pol_legendre_analysis(p, L, out3 + nalm, out3 + 2 * nalm);
+    if (p->prec == WF_PREC_FP64) {
+        const double *m = (const double *)map3;
+        if ((st = hp_ring_analysis_buf(p, L, m, p->ws.F)) != WF_OK) return st;
+        if ((st = hp_legendre_adjoint_buf(p, L, (const double2 *)p->ws.F, out3)) != WF_OK) return st;
+        if ((st = hp_ring_analysis_buf(p, L, m + npix, P->FQ)) != WF_OK) return st;
+        if ((st = hp_ring_analysis_buf(p, L, m + 2 * npix, P->FU)) != WF_OK) return st;
+        return hp_pol_legendre_analysis(p, L, out3 + nalm, out3 + 2 * nalm);
+    }
+    const float *m = (const float *)map3;
+    if ((st = hp_adjoint_T(p, m, L, out3)) != WF_OK) return st;
+    if ((st = hp_ring_analysis_buf(p, L, m + npix, P->FQ)) != WF_OK) return st;
+    if ((st = hp_ring_analysis_buf(p, L, m + 2 * npix, P->FU)) != WF_OK) return st;
+    return hp_pol_legendre_analysis_mx(p, L, out3 + nalm, out3 + 2 * nalm);
+}
+
+// Y^T of FP64 maps (3 x npix): mixed plans round them into the working maps first
+wf_status pol_adjoint_f64(wf_plan p, const double *map3, int L, double2 *out3)
+{
+    if (p->prec == WF_PREC_FP64) return pol_adjoint(p, map3, L, out3);
+    const long long n = 3 * p->npix;
+    k_map_to_T<float><<<grid_for(n, p->nsm), 256, 0, p->stream>>>(n, map3, (float *)p->pol->t);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return pol_adjoint(p, p->pol->t, L, out3);
 }
 
 // Polarised Wiener filter (Eqs. 10-11), FP64, with the heuristic cooling of
@@ -1156,13 +1188,25 @@ wf_status hp_begin_pol(HpRun &R)
     }
     if ((st = hp_pol_setup(p, R.fluct ? nullptr : R.d, R.nv, R.mask, &R.tau, &R.ndof)) != WF_OK) return st;
     R.tau_h = R.tau * p->omega;
+    // mixed precision: modes whose prior block's largest eigenvalue reaches
+    // kappa tau_h take the FP64 blocks of both the temperature and the spin-2
+    // kernels (the same reading as for temperature plans)
+    R.lc = 0;
+    if (p->prec != WF_PREC_FP64) {
+        if (o.mixed_lc > 0) R.lc = std::min(o.mixed_lc, lmax + 1);
+        else if (o.mixed_lc == 0)
+            for (int l = lmax; l >= 0; --l)
+                if (sch.c[l] / R.tau_h >= o.mixed_kappa) { R.lc = l + 1; break; }
+        if ((st = hp_set_low_block(p, R.lc)) != WF_OK) return st;
+        if ((st = hp_pol_set_low_block(p, R.lc)) != WF_OK) return st;
+    }
     if (R.fluct) {
         // z = Y (S^+1/2 g2) into the output maps as scratch, then r = nu^1/2 g1 + Omega z
         if ((st = hp_pol_isqrt_prior(p, R.C_ell, (const double2 *)R.g2, P->a_new)) != WF_OK) return st;
         if ((st = pol_synthesis(p, P->a_new, lmax, R.s_out, nullptr)) != WF_OK) return st;
         if ((st = hp_pol_fluct_source(p, R.g1, R.s_out)) != WF_OK) return st;
     }
-    if ((st = pol_adjoint(p, P->r, lmax, P->b)) != WF_OK) return st;
+    if ((st = pol_adjoint_f64(p, P->r, lmax, P->b)) != WF_OK) return st;
     if ((st = hp_pol_alm_norm(p, R.C_ell, P->b, 1)) != WF_OK) return st;
     {
         SumSpec sp{};
@@ -1179,7 +1223,10 @@ wf_status hp_begin_pol(HpRun &R)
     sch.margin = o.band_margin;
     sch.ell_iter = std::min(o.ell0, lmax);
     sch.level();
-    WF_CUDA(cudaMemsetAsync(P->a, 0, 3 * nalm * sizeof(double2), p->stream));
+    if (R.a_init)
+        WF_CUDA(cudaMemcpyAsync(P->a, R.a_init, 3 * nalm * sizeof(double2), cudaMemcpyDeviceToDevice, p->stream));
+    else
+        WF_CUDA(cudaMemsetAsync(P->a, 0, 3 * nalm * sizeof(double2), p->stream));
     WF_CUDA(cudaMemsetAsync(P->a_new, 0, 3 * nalm * sizeof(double2), p->stream));
     R.replay = !p->replay_lambda.empty();
     R.nrep = (int)p->replay_lambda.size();
@@ -1225,13 +1272,69 @@ wf_status hp_launch_pol(HpRun &R)
     return WF_OK;
 }
 
-// output maps, chi^2 of the result (Wiener filter), report
+wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8_t *mask, const double *C4,
+                       double tol, bool fluct, const double *g1, const double2 *g2, double *s_out, double *alm_out,
+                       wf_info *info, const double2 *a_init = nullptr);
+
+// FP64 correction sweeps of a mixed polarised solve (as for temperature plans:
+// lambda = 1 iterations on an FP64 sub-plan from the mixed iterate, whose
+// residual is the FP64 operator's), output maps, chi^2 of the result, report
 wf_status hp_end_pol(HpRun &R)
 {
     wf_plan p = R.p;
     PolState *P = p->pol;
     const int lmax = R.lmax;
+    const wf_options &o = R.o;
     wf_status st;
+    if (p->prec != WF_PREC_FP64 && o.refine_sweeps > 0 && R.result != WF_EDIVERGE) {
+        if (!p->sub) {
+            wf_plan sub = nullptr;
+            if ((st = wf_plan_create(&p->g, lmax, WF_PREC_FP64, (void *)p->stream, &sub)) != WF_OK) return st;
+            p->sub = sub;
+        }
+        wf_plan sub = p->sub;
+        sub->stream = p->stream;
+        sub->opt = p->opt;
+        sub->opt.profile = o.profile;
+        sub->opt.refine_sweeps = 0;
+        sub->opt.schedule = 0;
+        sub->replay_lambda.assign(o.refine_sweeps, 1.0);
+        sub->replay_L.assign(o.refine_sweeps, lmax);
+        wf_info si{};
+        std::vector<double> tl(o.refine_sweeps), tc(o.refine_sweeps), tr(o.refine_sweeps), tm(o.refine_sweeps);
+        std::vector<int> tL(o.refine_sweeps);
+        si.lambda_trace = tl.data();
+        si.L_trace = tL.data();
+        si.chi2_trace = tc.data();
+        si.resid_trace = tr.data();
+        si.iter_ms_trace = tm.data();
+        si.trace_cap = o.refine_sweeps;
+        st = hp_solve_pol(sub, R.d, R.nv, R.mask, R.C_ell, R.tol, R.fluct, R.g1, (const double2 *)R.g2, R.s_out,
+                          R.alm_out, &si, P->a);
+        if (st != WF_OK) return st;
+        for (int i = 0; i < si.iters; ++i) record(R.info, R.k + i, tl[i], tL[i], tc[i], tr[i], tm[i]);
+        for (int f = 0; f < WF_NK; ++f) {
+            R.pr.ms[f] += si.kernel_ms[f];
+            R.pr.cnt[f] += si.kernel_launches[f];
+        }
+        R.pr.launches += si.launches;
+        R.pr.finish();
+        if (R.info) {
+            wf_info *info = R.info;
+            info->iters = R.k + si.iters;
+            info->converged = (R.converged || si.converged) ? 1 : 0;
+            info->final_residual = si.final_residual;
+            info->chi2_over_ndof = si.chi2_over_ndof;
+            info->n_dof = R.ndof;
+            info->tau = R.tau;
+            info->n_levels = R.levels;
+            info->refine_sweeps = si.iters;
+            info->mixed_lc = R.lc;
+        }
+        if (si.converged) return WF_OK;
+        set_error(WF_ENOCONV, "not converged after %d FP64 sweeps (residual %.3e)", si.iters, si.final_residual);
+        return R.replay ? WF_OK : WF_ENOCONV;
+    }
     if ((st = pol_synthesis(p, P->a, lmax, R.s_out, nullptr)) != WF_OK) return st;
     if (R.alm_out)
         WF_CUDA(cudaMemcpyAsync(R.alm_out, P->a, 3 * p->nalm * sizeof(double2), cudaMemcpyDeviceToDevice,
@@ -1263,7 +1366,7 @@ wf_status hp_end_pol(HpRun &R)
         info->tau = R.tau;
         info->n_levels = R.levels;
         info->refine_sweeps = 0;
-        info->mixed_lc = 0;
+        info->mixed_lc = R.lc;
     }
     R.pr.finish();
     wf_status result = R.result;
@@ -1276,9 +1379,10 @@ wf_status hp_end_pol(HpRun &R)
 
 wf_status hp_solve_pol(wf_plan p, const double *d, const double *N6, const uint8_t *mask, const double *C4,
                        double tol, bool fluct, const double *g1, const double2 *g2, double *s_out, double *alm_out,
-                       wf_info *info)
+                       wf_info *info, const double2 *a_init)
 {
     HpRun R;
+    R.a_init = a_init;
     R.p = p;
     R.d = d;
     R.nv = N6;
@@ -1583,8 +1687,8 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
     *out = nullptr;
     if (g->ncomp != 0 && g->ncomp != 1 && g->ncomp != 3)
         return set_error(WF_EUNSUPPORTED, "ncomp must be 1 (temperature) or 3 (I, Q, U)");
-    if (g->ncomp == 3 && (g->kind != WF_GEOM_HEALPIX || prec != WF_PREC_FP64))
-        return set_error(WF_EUNSUPPORTED, "polarised plans (ncomp = 3) are HEALPix and FP64 in this version");
+    if (g->ncomp == 3 && g->kind != WF_GEOM_HEALPIX)
+        return set_error(WF_EUNSUPPORTED, "polarised plans (ncomp = 3) are HEALPix");
     if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32) return set_error(WF_EINVAL, "unknown precision");
     wf_plan p = new (std::nothrow) wf_plan_s();
     if (!p) return set_error(WF_ENOMEM, "host allocation");
@@ -1883,7 +1987,7 @@ wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm)
     if (p->g.kind == WF_GEOM_FLAT) return flat_map2alm(p, map, alm);
     if (L < 0 || L > p->lmax) L = p->lmax;
     if (p->pol) {
-        wf_status st = pol_adjoint(p, map, L, (double2 *)alm);
+        wf_status st = pol_adjoint_f64(p, map, L, (double2 *)alm);
         if (st != WF_OK) return st;
         WF_CUDA(cudaStreamSynchronize(p->stream));
         return WF_OK;

@@ -70,16 +70,25 @@ constexpr int RING_THREADS = 512;
 // plan
 // ---------------------------------------------------------------------------
 struct FlatPlan;  // flat-grid state (wf_flat.cu)
-// Polarisation (ncomp = 3, FP64): spin-2 tables and the (I, Q, U) / (T, E, B) workspace
+// Polarisation (ncomp = 3): spin-2 tables and the (I, Q, U) / (T, E, B) workspace
 struct PolState {
     double *al = nullptr, *be = nullptr, *ga = nullptr;  // per alm: spin -+2 recurrence coefficients
     int *ls = nullptr;                                   // per (m, pair): first kept l
     double *p0 = nullptr, *p1 = nullptr, *m0 = nullptr, *m1 = nullptr;  // 2lambda/2, -2lambda/2 at ls and ls + 1
     double2 *a = nullptr, *a_new = nullptr, *b = nullptr;  // 3 x n_alm each: T, E, B
-    double2 *GQ = nullptr, *GU = nullptr, *FQ = nullptr, *FU = nullptr;  // ring coefficients of Q and U
-    double *r = nullptr, *t = nullptr;  // 3 x npix: source nu d and the messenger field
+    void *GQ = nullptr, *GU = nullptr, *FQ = nullptr, *FU = nullptr;  // ring coefficients of Q, U (working precision)
+    double *r = nullptr;  // 3 x npix: source nu d
+    void *t = nullptr;    // 3 x npix: the messenger field (working precision)
     double *nu = nullptr;               // 6 x npix: inverse noise blocks (II, QQ, UU, IQ, IU, QU)
     double *part = nullptr, *part2 = nullptr;  // pixel and harmonic partial sums
+    // mixed precision: FP32 spin-2 kernels in mu form (lambda = c mu), FP64 block l < lcm(lc, m)
+    float4 *tab = nullptr;     // per alm: (A, A be, A (1 + be) - 2, A (1 - be) - 2)
+    double *c = nullptr;       // per alm
+    int *ls_mx = nullptr;      // per (m, pair): first l of the FP32 recurrence
+    float4 *seed = nullptr;    // per (m, pair): mu+ at ls_mx, ls_mx + 1; mu- at ls_mx, ls_mx + 1
+    float2 *GQlow = nullptr, *GUlow = nullptr;  // FP64 block's ring coefficients [pair][m < lc][hemisphere]
+    double2 *Elow = nullptr, *Blow = nullptr;   // FP64 block's (E, B)
+    int lc = -1, low_cap = 0;
 };
 
 struct Workspace {
@@ -231,6 +240,9 @@ wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T);
 wf_status hp_ring_synthesis_buf(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
                                 void *tmap, double *out_map);
 wf_status hp_ring_analysis_buf(wf_plan p, int L, const void *map_T, void *F);
+// mixed plans: the FP32 synthesis pass with an explicit FP64-block buffer (m < lc)
+wf_status hp_ring_synthesis_buf_low(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
+                                    const float2 *glow, int lc, int glow_stride, void *tmap, double *out_map);
 // FP64 temperature Legendre transforms on explicit buffers (FP64 plans)
 wf_status hp_legendre_synthesis_buf(wf_plan p, const double2 *alm, int L, double2 *G);
 wf_status hp_legendre_adjoint_buf(wf_plan p, int L, const double2 *F, double2 *out);
@@ -245,6 +257,17 @@ wf_status hp_pol_hblend(wf_plan p, int L, const double *C, double lam_tauh, doub
 wf_status hp_pol_alm_norm(wf_plan p, const double *C, const double2 *a, int mode);
 wf_status hp_pol_pix_chi2(wf_plan p, const double *d, const double *s_map, int *nblocks);
 wf_status hp_pol_isqrt_prior(wf_plan p, const double *C, const double2 *g2, double2 *out);  // S^+1/2 g2
+// the FP64 block of the mixed spin-2 transforms (m < lc, l < lcm(lc, m)): synthesis into FP32 ring
+// coefficients with stride lc, analysis from the FP32 ring coefficients
+wf_status hp_pol_legendre_synthesis_low(wf_plan p, const double2 *E, const double2 *B, int L, int lc, float2 *GQ,
+                                        float2 *GU);
+wf_status hp_pol_legendre_analysis_low(wf_plan p, int L, int lc, const float2 *FQ, const float2 *FU, double2 *E,
+                                       double2 *B);
+// mixed precision (wf_spin_mx.cu)
+wf_status hp_pol_create_mx(wf_plan p);
+wf_status hp_pol_set_low_block(wf_plan p, int lc);
+wf_status hp_pol_legendre_synthesis_mx(wf_plan p, const double2 *E, const double2 *B, int L);
+wf_status hp_pol_legendre_analysis_mx(wf_plan p, int L, double2 *E, double2 *B);
 wf_status hp_pol_fluct_source(wf_plan p, const double *g1, const double *z);  // r = nu^1/2 g1 + Omega z
 
 // flat grid (wf_flat.cu)

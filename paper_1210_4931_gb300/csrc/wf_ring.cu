@@ -544,11 +544,21 @@ template <typename T> struct RingLaunch {
                              double *omap)
     {
         const HpTables &t = p->tab;
+        if (p->prec != WF_PREC_FP64 && t.lc_mx > 0)
+            return syn_buf_low(p, L, mode, lam, tau, G, p->ws.Glow, t.lc_mx, t.glow_cap, tmap, omap);
+        return syn_buf_low(p, L, mode, lam, tau, G, nullptr, 0, 0, tmap, omap);
+    }
+    // with the FP64 block's coefficients (m < lc, [pair][m][hemisphere] with
+    // glow_stride columns per pair) added to G, or none (glow null)
+    static wf_status syn_buf_low(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
+                                 const float2 *glow, int lc, int glow_stride, void *tmap, double *omap)
+    {
+        const HpTables &t = p->tab;
         RingCommon rc = common(p, L);
-        if (p->prec != WF_PREC_FP64 && t.lc_mx > 0) {
-            rc.Glow = p->ws.Glow;
-            rc.lc = t.lc_mx;
-            rc.glow_stride = t.glow_cap;
+        if (glow && lc > 0) {
+            rc.Glow = glow;
+            rc.lc = lc;
+            rc.glow_stride = glow_stride;
         }
         const size_t sm = smem_bytes(t);
         WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
@@ -745,6 +755,13 @@ wf_status hp_ring_synthesis_buf(wf_plan p, int L, RingSynMode mode, double lam, 
 {
     return p->prec == WF_PREC_FP64 ? RingLaunch<double>::syn_buf(p, L, mode, lam, tau, G, tmap, out_map)
                                    : RingLaunch<float>::syn_buf(p, L, mode, lam, tau, G, tmap, out_map);
+}
+
+wf_status hp_ring_synthesis_buf_low(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
+                                    const float2 *glow, int lc, int glow_stride, void *tmap, double *out_map)
+{
+    if (p->prec == WF_PREC_FP64) return set_error(WF_EINVAL, "FP64 plans have no FP64 block");
+    return RingLaunch<float>::syn_buf_low(p, L, mode, lam, tau, G, glow, lc, glow_stride, tmap, out_map);
 }
 
 wf_status hp_ring_analysis_buf(wf_plan p, int L, const void *map_T, void *F)

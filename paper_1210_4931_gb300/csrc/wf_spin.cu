@@ -164,8 +164,16 @@ __global__ void k_seeds_pol(int lmax, int npairs, const double *__restrict__ xp,
     m1[idx] = M1;
 }
 
-// synthesis: (E, B) -> ring coefficients (Q_m, U_m) of both rings of each pair
-__global__ void __launch_bounds__(POL_THREADS) k_legsyn_pol(int lmax, int L, int npairs,
+// first l of the FP32 range for m < lc (mixed plans): lc rounded up to the
+// parity of m, as for the temperature kernels; the FP64 kernels then cover
+// l < lcm_of(lc, m) for those m
+__host__ __device__ inline int lcm_of(int lc, int m) { return m + 2 * ((lc - m + 1) / 2); }
+
+// synthesis: (E, B) -> ring coefficients (Q_m, U_m) of both rings of each pair,
+// l <= L (and l < lcm_of(lcut, m) when lcut > 0: the FP64 block of a mixed
+// plan); output [pair][m][hemisphere] with gstride columns per pair, in TG
+template <typename TG>
+__global__ void __launch_bounds__(POL_THREADS) k_legsyn_pol(int lmax, int L, int lcut, int gstride, int npairs,
                                                             const double2 *__restrict__ E,
                                                             const double2 *__restrict__ B,
                                                             const double *__restrict__ al,
@@ -176,8 +184,8 @@ __global__ void __launch_bounds__(POL_THREADS) k_legsyn_pol(int lmax, int L, int
                                                             const double *__restrict__ p1t,
                                                             const double *__restrict__ m0t,
                                                             const double *__restrict__ m1t,
-                                                            const double *__restrict__ xp, double2 *__restrict__ GQ,
-                                                            double2 *__restrict__ GU)
+                                                            const double *__restrict__ xp, cx<TG> *__restrict__ GQ,
+                                                            cx<TG> *__restrict__ GU)
 {
     const int m = blockIdx.y;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,6 +193,7 @@ __global__ void __launch_bounds__(POL_THREADS) k_legsyn_pol(int lmax, int L, int
     const long long base = pmbase(lmax, m);
     const size_t sidx = (size_t)m * npairs + p;
     const int ls = ls_tab[sidx];
+    if (lcut > 0) L = min(L, lcm_of(lcut, m) - 1);
     const double2 z = make_double2(0.0, 0.0);
     double2 EWe = z, EWo = z, BXe = z, BXo = z, BWe = z, BWo = z, EXe = z, EXo = z;
     if (ls <= L) {
@@ -222,11 +231,11 @@ __global__ void __launch_bounds__(POL_THREADS) k_legsyn_pol(int lmax, int L, int
     const double2 QS = dneg(dsub(dsub(EWe, EWo), times_i(dsub(BXe, BXo))));
     const double2 UN = dneg(dsub(dadd(BWe, BWo), times_i(dadd(EXe, EXo))));
     const double2 US = dneg(dadd(dsub(BWe, BWo), times_i(dsub(EXe, EXo))));
-    const size_t o = ((size_t)p * (lmax + 1) + m) * 2;
-    GQ[o] = QN;
-    GQ[o + 1] = QS;
-    GU[o] = UN;
-    GU[o + 1] = US;
+    const size_t o = ((size_t)p * gstride + m) * 2;
+    GQ[o] = mk<TG>((TG)QN.x, (TG)QN.y);
+    GQ[o + 1] = mk<TG>((TG)QS.x, (TG)QS.y);
+    GU[o] = mk<TG>((TG)UN.x, (TG)UN.y);
+    GU[o + 1] = mk<TG>((TG)US.x, (TG)US.y);
 }
 
 // warp reduce-scatter (same pattern as the temperature analysis)
@@ -257,10 +266,12 @@ __device__ __forceinline__ void rscatter(double (&vr)[CH], double (&vi)[CH], int
 }
 
 // analysis (the adjoint of k_legsyn_pol): ring coefficients FQ, FU of both
-// rings of each pair -> (E, B);  E = -sum_r (W FQ + i X FU), B = -sum_r (W FU - i X FQ)
-__global__ void __launch_bounds__(POL_THREADS) k_legana_pol(int lmax, int L, int npairs,
-                                                            const double2 *__restrict__ FQ,
-                                                            const double2 *__restrict__ FU,
+// rings of each pair -> (E, B);  E = -sum_r (W FQ + i X FU), B = -sum_r (W FU - i X FQ);
+// l <= L (and l < lcm_of(lcut, m) when lcut > 0); ring coefficients in TF
+template <typename TF>
+__global__ void __launch_bounds__(POL_THREADS) k_legana_pol(int lmax, int L, int lcut, int npairs,
+                                                            const cx<TF> *__restrict__ FQ,
+                                                            const cx<TF> *__restrict__ FU,
                                                             const double *__restrict__ al,
                                                             const double *__restrict__ be,
                                                             const double *__restrict__ ga,
@@ -274,7 +285,8 @@ __global__ void __launch_bounds__(POL_THREADS) k_legana_pol(int lmax, int L, int
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int m = blockIdx.x;
-    const int nl = L - m + 1;
+    if (lcut > 0) L = min(L, lcm_of(lcut, m) - 1);
+    const int nl = max(L - m + 1, 0);
     const long long base = pmbase(lmax, m);
     double2 *accE = reinterpret_cast<double2 *>(smem_raw);
     double2 *accB = accE + (nl + POL_CH + 2);
@@ -293,7 +305,9 @@ __global__ void __launch_bounds__(POL_THREADS) k_legana_pol(int lmax, int L, int
         double x = 0.0, P0 = 0.0, P1 = 0.0, M0 = 0.0, M1 = 0.0;
         if (ls <= L) {
             const size_t o = ((size_t)p * (lmax + 1) + m) * 2;
-            const double2 qn = FQ[o], qs = FQ[o + 1], un = FU[o], us = FU[o + 1];
+            const cx<TF> fq0 = FQ[o], fq1 = FQ[o + 1], fu0 = FU[o], fu1 = FU[o + 1];
+            const double2 qn = make_double2(fq0.x, fq0.y), qs = make_double2(fq1.x, fq1.y);
+            const double2 un = make_double2(fu0.x, fu0.y), us = make_double2(fu1.x, fu1.y);
             Pq = dadd(qn, qs);
             Mq = dsub(qn, qs);
             Pu = dadd(un, us);
@@ -530,8 +544,9 @@ __global__ void k_setup_pol(long long npix, const double *__restrict__ d, const 
 // Eq. (10): t = s + lam tau (1 + (lam - 1) tau nu)^-1 (r - nu s), in place on
 // the synthesised maps, and the pixel term of chi^2,
 // sum (nu s) . u - 2 r . u with u = (1 + (lam - 1) tau nu)^-1 s; per-block partials
+template <typename TM>
 __global__ void k_blend_pol(long long npix, const double *__restrict__ r, const double *__restrict__ nu6,
-                            double *__restrict__ t, double lt, double lm1t, double *__restrict__ part)
+                            TM *__restrict__ t, double lt, double lm1t, double *__restrict__ part)
 {
     __shared__ double red[32];
     double chi = 0.0;
@@ -548,9 +563,9 @@ __global__ void k_blend_pol(long long npix, const double *__restrict__ r, const 
         double y[3], u[3];
         mv3(Mi, res, y);
         mv3(Mi, s, u);
-        t[p] = s[0] + lt * y[0];
-        t[npix + p] = s[1] + lt * y[1];
-        t[2 * npix + p] = s[2] + lt * y[2];
+        t[p] = (TM)(s[0] + lt * y[0]);
+        t[npix + p] = (TM)(s[1] + lt * y[1]);
+        t[2 * npix + p] = (TM)(s[2] + lt * y[2]);
         chi += (ns[0] - 2.0 * rv[0]) * u[0] + (ns[1] - 2.0 * rv[1]) * u[1] + (ns[2] - 2.0 * rv[2]) * u[2];
     }
     for (int o = 16; o >= 1; o >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, o);
@@ -780,7 +795,8 @@ wf_status hp_pol_create(wf_plan p, const double *xpair_dev, const double *stpair
     p->pol = s;
     const int lmax = p->lmax, np = p->npairs;
     const long long nalm = p->nalm, ns = (long long)(lmax + 1) * np, npix = p->npix;
-    const size_t gsz = (size_t)np * (lmax + 1) * 2 * sizeof(double2);
+    const bool f64 = p->prec == WF_PREC_FP64;
+    const size_t gsz = (size_t)np * (lmax + 1) * 2 * (f64 ? sizeof(double2) : sizeof(float2));
     wf_status st;
     if ((st = plan_alloc(p, (void **)&s->al, nalm * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->be, nalm * 8)) != WF_OK) return st;
@@ -798,7 +814,7 @@ wf_status hp_pol_create(wf_plan p, const double *xpair_dev, const double *stpair
     if ((st = plan_alloc(p, (void **)&s->FQ, gsz)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->FU, gsz)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->r, 3 * npix * 8)) != WF_OK) return st;
-    if ((st = plan_alloc(p, (void **)&s->t, 3 * npix * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&s->t, 3 * npix * (f64 ? 8 : 4))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->nu, 6 * npix * 8)) != WF_OK) return st;
     const int npart = std::max(2 * (lmax + 2), std::max(256, 4 * p->nsm));
     if ((st = plan_alloc(p, (void **)&s->part, (size_t)npart * 8)) != WF_OK) return st;
@@ -811,6 +827,12 @@ wf_status hp_pol_create(wf_plan p, const double *xpair_dev, const double *stpair
                                                                      s->ga, s->ls, s->p0, s->p1, s->m0, s->m1);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
+    // shared-memory limits at their lmax sizes now, so no launch (e.g. inside a graph capture) needs to
+    const size_t sm_ana = (size_t)2 * (lmax + 1 + POL_CH + 2) * sizeof(double2) + 16;
+    if ((st = raise_smem_limit((const void *)(f64 ? (const void *)k_legana_pol<double>
+                                                  : (const void *)k_legana_pol<float>), sm_ana)) != WF_OK)
+        return st;
+    if (!f64 && (st = hp_pol_create_mx(p)) != WF_OK) return st;
     WF_CUDA(cudaStreamSynchronize(p->stream));
     return WF_OK;
 }
@@ -826,8 +848,9 @@ wf_status hp_pol_legendre_synthesis(wf_plan p, const double2 *E, const double2 *
 {
     const PolState *s = p->pol;
     dim3 grid((p->npairs + POL_THREADS - 1) / POL_THREADS, L + 1);
-    k_legsyn_pol<<<grid, POL_THREADS, 0, p->stream>>>(p->lmax, L, p->npairs, E, B, s->al, s->be, s->ga, s->ls,
-                                                       s->p0, s->p1, s->m0, s->m1, p->tab.x64, s->GQ, s->GU);
+    k_legsyn_pol<double><<<grid, POL_THREADS, 0, p->stream>>>(p->lmax, L, 0, p->lmax + 1, p->npairs, E, B, s->al,
+                                                               s->be, s->ga, s->ls, s->p0, s->p1, s->m0, s->m1,
+                                                               p->tab.x64, (double2 *)s->GQ, (double2 *)s->GU);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
@@ -838,9 +861,10 @@ wf_status hp_pol_legendre_analysis(wf_plan p, int L, double2 *E, double2 *B)
 {
     const PolState *s = p->pol;
     const size_t sm = (size_t)2 * (L + 1 + POL_CH + 2) * sizeof(double2) + 16;
-    if (wf_status st = raise_smem_limit((const void *)k_legana_pol, sm)) return st;
-    k_legana_pol<<<L + 1, POL_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, s->FQ, s->FU, s->al, s->be, s->ga,
-                                                         s->ls, s->p0, s->p1, s->m0, s->m1, p->tab.x64, E, B);
+    if (wf_status st = raise_smem_limit((const void *)k_legana_pol<double>, sm)) return st;
+    k_legana_pol<double><<<L + 1, POL_THREADS, sm, p->stream>>>(p->lmax, L, 0, p->npairs, (const double2 *)s->FQ,
+                                                                 (const double2 *)s->FU, s->al, s->be, s->ga, s->ls,
+                                                                 s->p0, s->p1, s->m0, s->m1, p->tab.x64, E, B);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     if (L < p->lmax) {  // columns m > L are not visited: zero them
@@ -848,6 +872,37 @@ wf_status hp_pol_legendre_analysis(wf_plan p, int L, double2 *E, double2 *B)
         WF_CUDA(cudaMemsetAsync(E + from, 0, (p->nalm - from) * sizeof(double2), p->stream));
         WF_CUDA(cudaMemsetAsync(B + from, 0, (p->nalm - from) * sizeof(double2), p->stream));
     }
+    return WF_OK;
+}
+
+wf_status hp_pol_legendre_synthesis_low(wf_plan p, const double2 *E, const double2 *B, int L, int lc, float2 *GQ,
+                                        float2 *GU)
+{
+    const PolState *s = p->pol;
+    const int nm = std::min(lc, L + 1);
+    if (nm <= 0) return WF_OK;
+    dim3 grid((p->npairs + POL_THREADS - 1) / POL_THREADS, nm);
+    k_legsyn_pol<float><<<grid, POL_THREADS, 0, p->stream>>>(p->lmax, L, lc, s->low_cap, p->npairs, E, B, s->al, s->be,
+                                                              s->ga, s->ls, s->p0, s->p1, s->m0, s->m1, p->tab.x64, GQ,
+                                                              GU);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+wf_status hp_pol_legendre_analysis_low(wf_plan p, int L, int lc, const float2 *FQ, const float2 *FU, double2 *E,
+                                       double2 *B)
+{
+    const PolState *s = p->pol;
+    const int nm = std::min(lc, L + 1);
+    if (nm <= 0) return WF_OK;
+    const int Lb = std::min(L, lc + 1);
+    const size_t sm = (size_t)2 * (Lb + 1 + POL_CH + 2) * sizeof(double2) + 16;
+    if (wf_status st = raise_smem_limit((const void *)k_legana_pol<float>, sm)) return st;
+    k_legana_pol<float><<<nm, POL_THREADS, sm, p->stream>>>(p->lmax, L, lc, p->npairs, FQ, FU, s->al, s->be, s->ga,
+                                                             s->ls, s->p0, s->p1, s->m0, s->m1, p->tab.x64, E, B);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
     return WF_OK;
 }
 
@@ -881,7 +936,12 @@ wf_status hp_pol_blend(wf_plan p, double lam, double tau, int *nblocks)
 {
     PolState *s = p->pol;
     const int grid = (int)std::min<long long>((p->npix + 255) / 256, 2LL * p->nsm);
-    k_blend_pol<<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, s->t, lam * tau, (lam - 1.0) * tau, s->part);
+    if (p->prec == WF_PREC_FP64)
+        k_blend_pol<double><<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, (double *)s->t, lam * tau,
+                                                         (lam - 1.0) * tau, s->part);
+    else
+        k_blend_pol<float><<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, (float *)s->t, lam * tau,
+                                                        (lam - 1.0) * tau, s->part);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     *nblocks = grid;

@@ -1,0 +1,157 @@
+"""Mixed-precision polarised path (FP32 spin-2 Legendre kernels in mu form,
+difference form near the poles, FP64 seeds, low-l block and correction
+sweeps) against the oracle and the FP64 GPU path."""
+import numpy as np
+import pytest
+
+import oracle
+import wf_inputs as gen
+from gpu_util import T, healpix_pol_case, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    import torch
+
+    import paper_1210_4931_gb300 as w
+
+    w.load()
+    torch.cuda.set_device(0)
+    return w
+
+
+def _cmb_teb(rng, lmax):
+    """(T, E, B) draws with the polarised workload's spectra (TT CMB-like,
+    EE = 0.05 TT, TE = 0.5 sqrt(TT EE)) and BB = 0.1 EE so B is exercised."""
+    ell = gen.alm_ell(lmax)
+    tt = gen.cmb_like_cl(lmax, 4 * 3438.0 / lmax)
+    ee = 0.05 * tt
+    te = 0.5 * np.sqrt(tt * ee)
+    g = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    a = np.zeros_like(g)
+    a[0] = np.sqrt(tt[ell]) * g[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = np.where(tt[ell] > 0, te[ell] / np.sqrt(np.where(tt[ell] > 0, tt[ell], 1.0)), 0.0)
+    a[1] = c * g[0] + np.sqrt(np.maximum(ee[ell] - c * c, 0.0)) * g[1]
+    a[2] = np.sqrt(0.1 * ee[ell]) * g[2]
+    a[1:, ell < 2] = 0.0
+    return a
+
+
+@pytest.mark.parametrize("nside,lmax", [(16, 32), (64, 128), (128, 256)])
+def test_pol_mixed_basis_change_accuracy(wf, nside, lmax):
+    """FP32 spin-0 and spin-2 transforms of CMB-like (T, E, B): each of I, Q, U
+    (and T, E, B for the adjoint) within 5e-5 of the oracle, relative to that
+    component's largest value."""
+    import torch
+
+    rng = np.random.default_rng(900 + nside)
+    a = _cmb_teb(rng, lmax)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed", ncomp=3)
+    npx = plan.npix
+    m = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    wf.wf_alm2map(plan, T(a.ravel()), lmax, m)
+    got = m.cpu().numpy().reshape(3, npx)
+    I = oracle.synthesis(nside, lmax, lmax, a[0])
+    Q, U = oracle.synthesis_pol(nside, lmax, lmax, a[1], a[2])
+    for c, ref in enumerate((I, Q, U)):
+        assert rel(got[c], ref) < 5e-5, (c, rel(got[c], ref))
+    f = np.stack([I, Q, U]) + 0.1 * np.std(Q) * rng.standard_normal((3, npx))
+    out = torch.empty(3 * plan.nalm, dtype=torch.complex128, device="cuda")
+    wf.wf_map2alm_adjoint(plan, T(f.ravel()), lmax, out)
+    got = out.cpu().numpy().reshape(3, plan.nalm)
+    Tt = oracle.adjoint_synthesis(nside, lmax, lmax, f[0])
+    Et, Bt = oracle.adjoint_pol(nside, lmax, lmax, f[1], f[2])
+    for c, ref in enumerate((Tt, Et, Bt)):
+        assert rel(got[c], ref) < 5e-5, (c, rel(got[c], ref))
+    plan.close()
+
+
+def _hard_pol(nside, lmax, seed):
+    # noise dynamic range 1e4 and a galactic cut: the largest prior eigenvalue
+    # over tau_h reaches ~1e6 at low l, so the FP64 low-l block is in use
+    return healpix_pol_case(nside, lmax, seed, noise_range=1e4, b_cut_deg=15.0, n_disks=20,
+                            disk_radius_deg=min(8.0, 0.3 * 2048 / nside), fwhm_arcmin=5.0 * 2048 / nside)
+
+
+@pytest.mark.parametrize("kind", ["wf", "fluct"])
+def test_pol_mixed_solve_matches_fp64(wf, kind):
+    """The mixed polarised iteration stays contractive where the prior's
+    largest eigenvalue over tau_h is large (FP64 low-l block in use), ends (after
+    FP64 correction sweeps) on the residual of the FP64 GPU path replaying the
+    same schedule, and its map matches that path's."""
+    import torch
+
+    nside, lmax = 32, 64
+    P, basis, d, nu, obs, N6, C4 = _hard_pol(nside, lmax, gen.seed_for(4, 400))
+    rng = np.random.default_rng(401)
+    g1 = rng.standard_normal((3, 12 * nside * nside))
+    g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    out = {}
+    for prec in ("mixed", "fp64"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3)
+        wf.wf_set_options(plan, maxiter=3000, refine_sweeps=3)
+        if prec == "fp64":
+            wf.wf_set_schedule(plan, out["mixed"][0]["lambda_trace"], out["mixed"][0]["L_trace"])
+        s = torch.empty(3 * plan.npix, dtype=torch.float64, device="cuda")
+        if kind == "wf":
+            rep = wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(C4.ravel()), 1e-5, s,
+                              trace_cap=5000)
+        else:
+            rep = wf.wf_fluct(plan, T(N6.ravel()), T(P["mask"]), T(C4.ravel()), T(g1.ravel()), T(g2.ravel()),
+                              1e-5, s, trace_cap=5000)
+        out[prec] = (rep, s.cpu().numpy())
+        plan.close()
+    rm, rf = out["mixed"][0], out["fp64"][0]
+    res = rm["resid_trace"][~np.isnan(rm["resid_trace"])]
+    res64 = rf["resid_trace"][~np.isnan(rf["resid_trace"])]
+    info = (rm["iters"], rm["refine_sweeps"], rm["mixed_lc"], res[-1], res64[-1])
+    assert rm["mixed_lc"] > 2, info  # the FP64 low-l block is in use on this problem
+    assert rm["refine_sweeps"] == 3, info
+    # contractive like the FP64 path, and the same residual to within the FP32 floor (the
+    # last three entries are the FP64 sweeps, so both traces end on FP64 residuals)
+    n = len(res)
+    assert n > 8 and res[-1] < res[n // 2] < res[n // 8], info
+    assert abs(res[-1] - res64[-1]) < 0.05 * res64[-1] + 1e-5, info
+    assert rel(out["mixed"][1], out["fp64"][1]) < 1e-3, rel(out["mixed"][1], out["fp64"][1])
+
+
+def test_pol_mixed_batch(wf):
+    """Mixed polarised WF + fluctuation items in one batch give the results of
+    the same solves run alone, within the solve tolerance."""
+    import torch
+
+    items, plans, alone = [], [], []
+    for j, (nside, lmax) in enumerate([(16, 32), (32, 64)]):
+        P, basis, d, nu, obs, N6, C4 = healpix_pol_case(nside, lmax, gen.seed_for(4, 500 + j))
+        rng = np.random.default_rng(5000 + j)
+        npx = 12 * nside * nside
+        g1 = rng.standard_normal((3, npx))
+        g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+        for kind in ("wf", "fluct"):
+            it = {"kind": kind, "noise_var": T(N6.ravel()), "mask": T(P["mask"]), "C_ell": T(C4.ravel()), "tol": 1e-5,
+                  "s_out": torch.full((3 * npx,), float("nan"), dtype=torch.float64, device="cuda")}
+            if kind == "wf":
+                it["d"] = T(d.ravel())
+            else:
+                it["g1"] = T(g1.ravel())
+                it["g2"] = T(g2.ravel())
+            pl = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed", ncomp=3)
+            s = torch.empty_like(it["s_out"])
+            if kind == "wf":
+                rep = wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], 1e-5, s)
+            else:
+                rep = wf.wf_fluct(pl, it["noise_var"], it["mask"], it["C_ell"], it["g1"], it["g2"], 1e-5, s)
+            pl.close()
+            alone.append((s.cpu().numpy(), rep))
+            plans.append(wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed", ncomp=3))
+            items.append(it)
+    reps = wf.wf_solve_batch(plans, items)
+    for i, (it, rep, (s_alone, rep_alone)) in enumerate(zip(items, reps, alone)):
+        assert rep["status"] == wf.WF_OK, (i, rep["status"])
+        assert rep["final_residual"] < 1e-5 and rep_alone["final_residual"] < 1e-5
+        assert rel(it["s_out"].cpu().numpy(), s_alone) < 1e-3, (i, rel(it["s_out"].cpu().numpy(), s_alone))
+    for pl in plans:
+        pl.close()
