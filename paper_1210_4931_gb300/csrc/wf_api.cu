@@ -1206,6 +1206,7 @@ wf_status hp_begin_pol(HpRun &R)
         if ((st = pol_synthesis(p, P->a_new, lmax, R.s_out, nullptr)) != WF_OK) return st;
         if ((st = hp_pol_fluct_source(p, R.g1, R.s_out)) != WF_OK) return st;
     }
+    if ((st = hp_pol_round_pixels(p)) != WF_OK) return st;
     if ((st = pol_adjoint_f64(p, P->r, lmax, P->b)) != WF_OK) return st;
     if ((st = hp_pol_alm_norm(p, R.C_ell, P->b, 1)) != WF_OK) return st;
     {

@@ -80,6 +80,8 @@ struct PolState {
     double *r = nullptr;  // 3 x npix: source nu d
     void *t = nullptr;    // 3 x npix: the messenger field (working precision)
     double *nu = nullptr;               // 6 x npix: inverse noise blocks (II, QQ, UU, IQ, IU, QU)
+    float *r32 = nullptr, *nu32 = nullptr;  // mixed plans: FP32 copies of r and nu for the blend
+    double4 *hbt = nullptr;  // 3 x (lmax + 1): per-l factors of the harmonic blend
     double *part = nullptr, *part2 = nullptr;  // pixel and harmonic partial sums
     // mixed precision: FP32 spin-2 kernels in mu form (lambda = c mu), FP64 block l < lcm(lc, m)
     float4 *tab = nullptr;     // per alm: (A, A be, A (1 + be) - 2, A (1 - be) - 2)
@@ -269,6 +271,7 @@ wf_status hp_pol_set_low_block(wf_plan p, int lc);
 wf_status hp_pol_legendre_synthesis_mx(wf_plan p, const double2 *E, const double2 *B, int L);
 wf_status hp_pol_legendre_analysis_mx(wf_plan p, int L, double2 *E, double2 *B);
 wf_status hp_pol_fluct_source(wf_plan p, const double *g1, const double *z);  // r = nu^1/2 g1 + Omega z
+wf_status hp_pol_round_pixels(wf_plan p);  // mixed plans: FP32 copies of r and nu
 
 // flat grid (wf_flat.cu)
 wf_status flat_create(wf_plan p);

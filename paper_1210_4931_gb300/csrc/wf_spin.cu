@@ -294,7 +294,10 @@ __global__ void __launch_bounds__(POL_THREADS) k_legana_pol(int lmax, int L, int
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int ngroups = (npairs + 31) / 32;
-    for (int grp = warp; grp < ngroups; grp += nwarps) {
+    // gridDim.y > 1 splits the ring pairs of each m over CTAs (the FP64 block of
+    // mixed plans: its few m would otherwise leave most SMs idle); they add
+    // their sums into pre-zeroed outputs
+    for (int grp = warp + nwarps * blockIdx.y; grp < ngroups; grp += nwarps * gridDim.y) {
         const int p = grp * 32 + lane;
         const size_t sidx = (size_t)m * npairs + p;
         int ls = (p < npairs) ? ls_tab[sidx] : lmax + 1;
@@ -371,6 +374,16 @@ __global__ void __launch_bounds__(POL_THREADS) k_legana_pol(int lmax, int L, int
         }
     }
     __syncthreads();
+    if (gridDim.y > 1) {
+        for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+            if (m + j < 2) continue;
+            atomicAdd(&Eo[base + j].x, accE[j].x);
+            atomicAdd(&Eo[base + j].y, accE[j].y);
+            atomicAdd(&Bo[base + j].x, accB[j].x);
+            atomicAdd(&Bo[base + j].y, accB[j].y);
+        }
+        return;
+    }
     for (int j = threadIdx.x; j <= lmax - m; j += blockDim.x) {
         const int l = m + j;
         const bool in = l <= L && l >= 2;
@@ -578,6 +591,57 @@ __global__ void k_blend_pol(long long npix, const double *__restrict__ r, const 
     }
 }
 
+// Eq. (10) for mixed plans: the same step on FP32 copies of r and nu, in
+// FP32 arithmetic (1 + (lam - 1) tau nu has eigenvalues in [1, lam], so its
+// cofactor inverse is well conditioned), chi^2 partials accumulated in FP64
+__global__ void k_blend_pol_f32(long long npix, const float *__restrict__ r, const float *__restrict__ nu6,
+                                float *__restrict__ t, float lt, float lm1t, double *__restrict__ part)
+{
+    __shared__ double red[32];
+    double chi = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (long long)gridDim.x * blockDim.x) {
+        const float na = nu6[p], nb = nu6[npix + p], nc = nu6[2 * npix + p];
+        const float nd = nu6[3 * npix + p], ne = nu6[4 * npix + p], nf = nu6[5 * npix + p];
+        const float s0 = t[p], s1 = t[npix + p], s2 = t[2 * npix + p];
+        const float r0 = r[p], r1 = r[npix + p], r2 = r[2 * npix + p];
+        const float ns0 = na * s0 + nd * s1 + ne * s2;
+        const float ns1 = nd * s0 + nb * s1 + nf * s2;
+        const float ns2 = ne * s0 + nf * s1 + nc * s2;
+        // M = 1 + lm1t nu, inverse by cofactors
+        const float a = 1.f + lm1t * na, b = 1.f + lm1t * nb, c = 1.f + lm1t * nc;
+        const float d = lm1t * nd, e = lm1t * ne, f = lm1t * nf;
+        const float c00 = b * c - f * f, c11 = a * c - e * e, c22 = a * b - d * d;
+        const float c01 = e * f - d * c, c02 = d * f - b * e, c12 = d * e - a * f;
+        const float id = 1.f / (a * c00 + d * c01 + e * c02);
+        const float q0 = r0 - ns0, q1 = r1 - ns1, q2 = r2 - ns2;
+        const float y0 = (c00 * q0 + c01 * q1 + c02 * q2) * id;
+        const float y1 = (c01 * q0 + c11 * q1 + c12 * q2) * id;
+        const float y2 = (c02 * q0 + c12 * q1 + c22 * q2) * id;
+        const float u0 = (c00 * s0 + c01 * s1 + c02 * s2) * id;
+        const float u1 = (c01 * s0 + c11 * s1 + c12 * s2) * id;
+        const float u2 = (c02 * s0 + c12 * s1 + c22 * s2) * id;
+        t[p] = s0 + lt * y0;
+        t[npix + p] = s1 + lt * y1;
+        t[2 * npix + p] = s2 + lt * y2;
+        chi += (double)((ns0 - 2.f * r0) * u0 + (ns1 - 2.f * r1) * u1 + (ns2 - 2.f * r2) * u2);
+    }
+    for (int o = 16; o >= 1; o >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = chi;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        part[blockIdx.x] = sum;
+    }
+}
+
+__global__ void k_to_f32(long long n, const double *__restrict__ in, float *__restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
 // prior block of one l: TE block [[TT, TE], [TE, EE]] and BB
 struct Prior {
     double tt, ee, bb, te;
@@ -638,12 +702,37 @@ __global__ void k_pol_alm_norm(int lmax, const double *__restrict__ C, const dou
     }
 }
 
+// per-l factors of Eq. (11) for one launch (the a_lm kernel then does no
+// divisions): T0 = Omega S (S + lam tau_h)^-1 on the TE block (f00, f01, f10,
+// f11); T1 = (Omega BB / (BB + lam tau_h), S^+ entries it, ie, ix); T2 = (ib,
+// and the residual multipliers S^+ + P / tau_h on the TE block diagonal and BB)
+__global__ void k_hblend_table(int lmax, const double *__restrict__ C, double omega, double lam_tauh, double tauh,
+                               double4 *__restrict__ tab)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l > lmax) return;
+    const Prior S = prior(C, lmax, l);
+    const double c = lam_tauh;
+    const double m00 = S.tt + c, m11 = S.ee + c, m01 = S.te;
+    const double det = m00 * m11 - m01 * m01;
+    const double i00 = m11 / det, i11 = m00 / det, i01 = -m01 / det;
+    const double f00 = S.tt * i00 + S.te * i01, f01 = S.tt * i01 + S.te * i11;
+    const double f10 = S.te * i00 + S.ee * i01, f11 = S.te * i01 + S.ee * i11;
+    const double fb = S.bb > 0.0 ? S.bb / (S.bb + c) : 0.0;
+    double it, ie, ix, ib;
+    pinv_te(S, it, ie, ix, ib);
+    const double ih = 1.0 / tauh;
+    tab[3 * l] = make_double4(omega * f00, omega * f01, omega * f10, omega * f11);
+    tab[3 * l + 1] = make_double4(omega * fb, it, ie, ix);
+    tab[3 * l + 2] = make_double4(ib, it + (S.tt > 0.0 ? ih : 0.0), ie + (S.ee > 0.0 ? ih : 0.0),
+                                  ib + (S.bb > 0.0 ? ih : 0.0));
+}
+
 // Eq. (11): a_new = S (S + lam tau_h)^-1 Omega b for l <= L (0 above), and per-m
 // partial sums [chi2_h(a_old), |(S^+ + 1/tau_h)(a_old - a_new)|^2]
-__global__ void k_hblend_pol(int lmax, int L, long long nalm, const double *__restrict__ C, double omega,
-                             double lam_tauh, double tauh, int want_resid, const double2 *__restrict__ b,
-                             const double2 *__restrict__ a_old, double2 *__restrict__ a_new,
-                             double *__restrict__ part)
+__global__ void k_hblend_pol(int lmax, int L, long long nalm, const double4 *__restrict__ tab, int want_resid,
+                             const double2 *__restrict__ b, const double2 *__restrict__ a_old,
+                             double2 *__restrict__ a_new, double *__restrict__ part)
 {
     __shared__ double red[2][32];
     const int m = blockIdx.x;
@@ -652,36 +741,23 @@ __global__ void k_hblend_pol(int lmax, int L, long long nalm, const double *__re
     double chi = 0.0, res = 0.0;
     for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
         const long long k = base + (l - m);
-        const Prior S = prior(C, lmax, l);
+        const double4 T0 = tab[3 * l], T1 = tab[3 * l + 1], T2 = tab[3 * l + 2];
         double2 nT = make_double2(0, 0), nE = nT, nB = nT;
         if (l <= L) {
             const double2 tT = b[k], tE = b[nalm + k], tB = b[2 * nalm + k];
-            // F = S (S + c)^-1 on the TE block, BB / (BB + c)
-            const double c = lam_tauh;
-            const double m00 = S.tt + c, m11 = S.ee + c, m01 = S.te;
-            const double det = m00 * m11 - m01 * m01;
-            const double i00 = m11 / det, i11 = m00 / det, i01 = -m01 / det;
-            const double f00 = S.tt * i00 + S.te * i01, f01 = S.tt * i01 + S.te * i11;
-            const double f10 = S.te * i00 + S.ee * i01, f11 = S.te * i01 + S.ee * i11;
-            const double fb = S.bb > 0.0 ? S.bb / (S.bb + c) : 0.0;
-            nT = make_double2(omega * (f00 * tT.x + f01 * tE.x), omega * (f00 * tT.y + f01 * tE.y));
-            nE = make_double2(omega * (f10 * tT.x + f11 * tE.x), omega * (f10 * tT.y + f11 * tE.y));
-            nB = make_double2(omega * fb * tB.x, omega * fb * tB.y);
+            nT = make_double2(T0.x * tT.x + T0.y * tE.x, T0.x * tT.y + T0.y * tE.y);
+            nE = make_double2(T0.z * tT.x + T0.w * tE.x, T0.z * tT.y + T0.w * tE.y);
+            nB = make_double2(T1.x * tB.x, T1.x * tB.y);
         }
         const double2 oT = a_old[k], oE = a_old[nalm + k], oB = a_old[2 * nalm + k];
-        double it, ie, ix, ib;
-        pinv_te(S, it, ie, ix, ib);
+        const double it = T1.y, ie = T1.z, ix = T1.w, ib = T2.x;
         chi += wm * (it * (oT.x * oT.x + oT.y * oT.y) + ie * (oE.x * oE.x + oE.y * oE.y) +
                      2.0 * ix * (oT.x * oE.x + oT.y * oE.y) + ib * (oB.x * oB.x + oB.y * oB.y));
         if (want_resid) {
             const double2 dT = dsub(oT, nT), dE = dsub(oE, nE), dB = dsub(oB, nB);
-            const bool t = S.tt > 0.0, e = S.ee > 0.0, bb = S.bb > 0.0;
-            const double ih = 1.0 / tauh;
-            const double2 rT = make_double2(it * dT.x + ix * dE.x + (t ? ih * dT.x : 0.0),
-                                            it * dT.y + ix * dE.y + (t ? ih * dT.y : 0.0));
-            const double2 rE = make_double2(ix * dT.x + ie * dE.x + (e ? ih * dE.x : 0.0),
-                                            ix * dT.y + ie * dE.y + (e ? ih * dE.y : 0.0));
-            const double2 rB = make_double2((ib + (bb ? ih : 0.0)) * dB.x, (ib + (bb ? ih : 0.0)) * dB.y);
+            const double2 rT = make_double2(T2.y * dT.x + ix * dE.x, T2.y * dT.y + ix * dE.y);
+            const double2 rE = make_double2(ix * dT.x + T2.z * dE.x, ix * dT.y + T2.z * dE.y);
+            const double2 rB = make_double2(T2.w * dB.x, T2.w * dB.y);
             res += wm * (rT.x * rT.x + rT.y * rT.y + rE.x * rE.x + rE.y * rE.y + rB.x * rB.x + rB.y * rB.y);
         }
         a_new[k] = nT;
@@ -816,6 +892,11 @@ wf_status hp_pol_create(wf_plan p, const double *xpair_dev, const double *stpair
     if ((st = plan_alloc(p, (void **)&s->r, 3 * npix * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->t, 3 * npix * (f64 ? 8 : 4))) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->nu, 6 * npix * 8)) != WF_OK) return st;
+    if ((st = plan_alloc(p, (void **)&s->hbt, (size_t)3 * (lmax + 1) * sizeof(double4))) != WF_OK) return st;
+    if (!f64) {
+        if ((st = plan_alloc(p, (void **)&s->r32, 3 * npix * 4)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&s->nu32, 6 * npix * 4)) != WF_OK) return st;
+    }
     const int npart = std::max(2 * (lmax + 2), std::max(256, 4 * p->nsm));
     if ((st = plan_alloc(p, (void **)&s->part, (size_t)npart * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&s->part2, (size_t)npart * 8)) != WF_OK) return st;
@@ -899,8 +980,15 @@ wf_status hp_pol_legendre_analysis_low(wf_plan p, int L, int lc, const float2 *F
     const int Lb = std::min(L, lc + 1);
     const size_t sm = (size_t)2 * (Lb + 1 + POL_CH + 2) * sizeof(double2) + 16;
     if (wf_status st = raise_smem_limit((const void *)k_legana_pol<float>, sm)) return st;
-    k_legana_pol<float><<<nm, POL_THREADS, sm, p->stream>>>(p->lmax, L, lc, p->npairs, FQ, FU, s->al, s->be, s->ga,
-                                                             s->ls, s->p0, s->p1, s->m0, s->m1, p->tab.x64, E, B);
+    // about four CTAs per SM: each m's ring pairs split over CTAs that add into zeroed outputs
+    const int ngroups = (p->npairs + 31) / 32, per_cta = POL_THREADS / 32;
+    const int split = std::max(1, std::min((4 * p->nsm + nm - 1) / nm, (ngroups + per_cta - 1) / per_cta));
+    const long long nz = pmbase(p->lmax, nm);
+    WF_CUDA(cudaMemsetAsync(E, 0, nz * sizeof(double2), p->stream));
+    WF_CUDA(cudaMemsetAsync(B, 0, nz * sizeof(double2), p->stream));
+    k_legana_pol<float><<<dim3(nm, split), POL_THREADS, sm, p->stream>>>(p->lmax, L, lc, p->npairs, FQ, FU, s->al,
+                                                                          s->be, s->ga, s->ls, s->p0, s->p1, s->m0,
+                                                                          s->m1, p->tab.x64, E, B);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
@@ -940,8 +1028,8 @@ wf_status hp_pol_blend(wf_plan p, double lam, double tau, int *nblocks)
         k_blend_pol<double><<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, (double *)s->t, lam * tau,
                                                          (lam - 1.0) * tau, s->part);
     else
-        k_blend_pol<float><<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, (float *)s->t, lam * tau,
-                                                        (lam - 1.0) * tau, s->part);
+        k_blend_pol_f32<<<grid, 256, 0, p->stream>>>(p->npix, s->r32, s->nu32, (float *)s->t, (float)(lam * tau),
+                                                     (float)((lam - 1.0) * tau), s->part);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     *nblocks = grid;
@@ -951,8 +1039,10 @@ wf_status hp_pol_blend(wf_plan p, double lam, double tau, int *nblocks)
 wf_status hp_pol_hblend(wf_plan p, int L, const double *C, double lam_tauh, double tauh, int want_resid)
 {
     PolState *s = p->pol;
-    k_hblend_pol<<<p->lmax + 1, 256, 0, p->stream>>>(p->lmax, L, p->nalm, C, p->omega, lam_tauh, tauh, want_resid,
-                                                      s->b, s->a, s->a_new, s->part2);
+    k_hblend_table<<<(p->lmax + 256) / 256, 256, 0, p->stream>>>(p->lmax, C, p->omega, lam_tauh, tauh, s->hbt);
+    WF_COUNT_LAUNCH(p);
+    k_hblend_pol<<<p->lmax + 1, 256, 0, p->stream>>>(p->lmax, L, p->nalm, s->hbt, want_resid, s->b, s->a, s->a_new,
+                                                      s->part2);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
@@ -969,6 +1059,21 @@ wf_status hp_pol_alm_norm(wf_plan p, const double *C, const double2 *a, int mode
 wf_status hp_pol_isqrt_prior(wf_plan p, const double *C, const double2 *g2, double2 *out)
 {
     k_isqrt_S_pol<<<p->lmax + 1, 256, 0, p->stream>>>(p->lmax, p->nalm, C, g2, out);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+// mixed plans: FP32 copies of the source and the inverse-noise blocks for the blend
+wf_status hp_pol_round_pixels(wf_plan p)
+{
+    PolState *s = p->pol;
+    if (p->prec == WF_PREC_FP64) return WF_OK;
+    const long long n3 = 3 * p->npix, n6 = 6 * p->npix;
+    const int grid = (int)std::min<long long>((n6 + 255) / 256, 4LL * p->nsm);
+    k_to_f32<<<grid, 256, 0, p->stream>>>(n3, s->r, s->r32);
+    WF_COUNT_LAUNCH(p);
+    k_to_f32<<<grid, 256, 0, p->stream>>>(n6, s->nu, s->nu32);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;
