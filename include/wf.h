@@ -68,7 +68,7 @@ typedef struct {
     wf_geom_kind kind;
     int nx, ny;  /* flat only: powers of two, 16 <= n <= 256 */
     int nside;   /* HEALPix only */
-    int ncomp;   /* 1 (temperature) or 3 (polarised I, Q, U: HEALPix, FP64) */
+    int ncomp;   /* 1 (temperature) or 3 (polarised I, Q, U: HEALPix, FP64 or mixed) */
 } wf_geometry;
 
 /* Options of the cooling schedule and stopping rule (Sect. 3).  Zero-filled
@@ -83,7 +83,8 @@ typedef struct {
     double lambda_max;  /* flat: first lambda level (100) */
     int refine_sweeps;  /* mixed precision: FP64 lambda = 1 sweeps from the mixed result, stopping at tol (0) */
     int profile;        /* nonzero: time every kernel family with CUDA events (fills wf_info.kernel_ms) */
-    double mixed_kappa; /* mixed precision: modes with S_l / (tau Omega) >= kappa run in FP64 (3e4) */
+    double mixed_kappa; /* mixed precision: modes with S_l / (tau Omega) >= kappa run in FP64 (3e4); polarised
+                           plans use the largest eigenvalue of each l's prior block for S_l */
     int mixed_lc;       /* mixed precision: > 0 forces the FP64 block l < mixed_lc, < 0 disables it, 0 = auto */
     int schedule;       /* 0: heuristic cooling of Sect. 3 (default); 1: chi^2-bound cooling of Sect. 2.2
                            (HEALPix Wiener filter only: lambda such that chi^2(lambda, x) = b every iteration,
