@@ -755,7 +755,10 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
         if (lane == 0) grp = atomicAdd(&next_group, 1);
         grp = __shfl_sync(0xffffffffu, grp, 0);
         if (grp >= ngroups) break;
-        const int p0 = grp * per_group + lane * NP;
+        // equator first: the work per pair grows towards the equator (more l above the
+        // first kept one), so handing out the largest groups first shortens the tail at the
+        // barrier before the epilogue
+        const int p0 = (ngroups - 1 - grp) * per_group + lane * NP;
         MxPairs<NP> P;
         mx_load_pairs<NP>(P, m, L, npairs, p0, ls_tab, s0_tab, s1_tab, xp, wp);
         // one recurrence form per warp: the shuffles below need warp-uniform control flow

@@ -492,7 +492,10 @@ __global__ void __launch_bounds__(PM_THREADS, 2) k_legana_pol_mx(int lmax, int L
         if (lane == 0) grp = atomicAdd(&next_group, 1);
         grp = __shfl_sync(0xffffffffu, grp, 0);
         if (grp >= ngroups) break;
-        const int p0 = grp * per_group + lane * NP;
+        // equator first: the work per pair grows towards the equator (more l above the
+        // first kept one), so handing out the largest groups first shortens the tail at the
+        // barrier before the epilogue
+        const int p0 = (ngroups - 1 - grp) * per_group + lane * NP;
         PmPairs<NP> P;
         pm_load_pairs<NP>(P, m, L, npairs, p0, ls_tab, seed, xp, wp);
         // one recurrence form per warp: the shuffles need warp-uniform control flow
