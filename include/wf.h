@@ -286,7 +286,7 @@ wf_status wf_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, void
  * s_WF + f) requests concurrently on one GPU.  Requests carry HOST buffers
  * and wait in a FIFO queue.  Each of `slots` worker threads owns a CUDA
  * stream and takes the next request that can be admitted:
- *   - a plan (tables + workspace) of the request's (nside, lmax, precision) is
+ *   - a plan (tables + workspace) of the request's (nside, lmax, precision, ncomp) is
  *     taken from the pool of idle plans, or created if the plans' device bytes
  *     stay within `mem_budget` after it (estimate from wf_plan_estimate_bytes),
  *     evicting least recently used idle plans for the queue head if needed;
@@ -313,6 +313,8 @@ typedef struct {
     const double *g1, *g2;    /* FLUCT, CR: npix real and n_alm complex draws of Eq. (9) */
     double *s_out;            /* npix: s_WF (WF), f (FLUCT), s_WF + f (CR) */
     double *f_out;            /* CR only, optional: npix, the fluctuation map f */
+    int ncomp;                /* 0 or 1: temperature; 3: polarised (I, Q, U), every array in the
+                                 three-component layouts of wf_solve / wf_fluct */
 } wf_request;
 
 typedef struct {

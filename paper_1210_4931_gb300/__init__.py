@@ -64,7 +64,7 @@ class wf_request(ctypes.Structure):
                 ("precision", ctypes.c_int), ("tol", ctypes.c_double), ("opt", wf_options),
                 ("d", ctypes.c_void_p), ("noise_var", ctypes.c_void_p), ("mask", ctypes.c_void_p),
                 ("C_ell", ctypes.c_void_p), ("g1", ctypes.c_void_p), ("g2", ctypes.c_void_p),
-                ("s_out", ctypes.c_void_p), ("f_out", ctypes.c_void_p)]
+                ("s_out", ctypes.c_void_p), ("f_out", ctypes.c_void_p), ("ncomp", ctypes.c_int)]
 
 
 class wf_result(ctypes.Structure):
@@ -441,10 +441,10 @@ def wf_solve_batch(plans, items, trace_cap=0, stream=None) -> list:
 
 
 def wf_plan_estimate_bytes(kind: str, *, nside: int = 0, lmax: int = 0, n: int = 0, precision: str = "fp64",
-                           host_staging: bool = True) -> int:
+                           host_staging: bool = True, ncomp: int = 1) -> int:
     g = wf_geometry()
     if kind == "healpix":
-        g.kind, g.nside, g.ncomp = WF_GEOM_HEALPIX, nside, 1
+        g.kind, g.nside, g.ncomp = WF_GEOM_HEALPIX, nside, int(ncomp)
     else:
         g.kind, g.nx, g.ny, g.ncomp = WF_GEOM_FLAT, n, n, 1
     return int(load().wf_plan_estimate_bytes(ctypes.byref(g), int(lmax), PRECISIONS[precision], int(host_staging)))
@@ -463,7 +463,8 @@ class Server:
         self._next = 1
 
     def submit(self, kind: str, *, nside: int, lmax: int, noise_var, C_ell, s_out, d=None, mask=None, g1=None,
-               g2=None, f_out=None, precision: str = "mixed", tol: float = 1e-6, tag=None, **options) -> int:
+               g2=None, f_out=None, precision: str = "mixed", tol: float = 1e-6, tag=None, ncomp: int = 1,
+               **options) -> int:
         def hp(a, dt):
             if a is None:
                 return None
@@ -476,7 +477,7 @@ class Server:
             tag = self._next
             self._next += 1
         r.tag, r.kind, r.nside, r.lmax = int(tag), REQUEST_KINDS[kind], int(nside), int(lmax)
-        r.precision, r.tol = PRECISIONS[precision], float(tol)
+        r.precision, r.tol, r.ncomp = PRECISIONS[precision], float(tol), int(ncomp)
         for k, v in options.items():
             setattr(r.opt, k, v)
         r.d, r.noise_var, r.mask = hp(d, np.float64), hp(noise_var, np.float64), hp(mask, np.uint8)

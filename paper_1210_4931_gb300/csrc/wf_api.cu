@@ -1621,7 +1621,7 @@ wf_status hp_create(wf_plan p)
 // Device bytes a HEALPix plan allocates (tables, workspace, host-API staging),
 // mirroring hp_create and the table builders; the mixed path's FP64-block
 // buffer is counted for l_c = (lmax + 1) / 8 (it grows with l_c on demand).
-long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging)
+long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging, int ncomp)
 {
     const bool f32 = prec != WF_PREC_FP64;
     const long long np = 2LL * nside, npix = 12LL * nside * nside;
@@ -1656,6 +1656,21 @@ long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging
     b += std::max(np, 1024LL) * 8 + 4LL * (lmax + 2) * 8 + (lmax + 1) * 32 + 256;
     if (f32) b += np * ((lmax + 1) / 8 + 1) * 2 * 8;             // FP64-block coefficients (stored FP32)
     if (staging) b += npix * (3 * 8 + 1) + (lmax + 1) * 8 + nalm * 16 * 2 + npix * 8;
+    if (ncomp == 3) {  // polarisation (PolState)
+        const long long lcap = (lmax + 1) / 8 + 1;                  // FP64-block allowance, as above
+        b += nalm * 8 * 3 + ns * (4 + 32);                           // al, be, ga; ls and the four seeds
+        b += 3 * 3 * nalm * 16;                                      // a, a_new, b for T, E, B
+        b += 4 * np * (lmax + 1) * 2 * ec;                           // GQ, GU, FQ, FU
+        b += 3 * npix * 8 + 3 * npix * es + 6 * npix * 8;            // r, t, nu
+        b += 3 * (lmax + 1) * 32 + 2 * std::max(2LL * (lmax + 2), 8LL * 152) * 8;  // blend table, partials
+        if (f32) {
+            b += 9 * npix * 4;                                       // FP32 r, nu
+            b += nalm * (8 + 16 + 2 * 16);                           // c, mu-form table, FP64-block (E, B)
+            b += ns * (4 + 16);                                      // FP32 seeds
+            b += 2 * np * lcap * 2 * 8;                              // FP64-block ring coefficients
+        }
+        if (staging) b += npix * 8 * (2 + 5 + 2 + 2) + 3 * (lmax + 1) * 8 + 4 * nalm * 16;  // 3-component buffers
+    }
     return b + (1LL << 20);
 }
 
@@ -1785,7 +1800,8 @@ long long wf_plan_estimate_bytes(const wf_geometry *g, int lmax, wf_precision pr
     if (!g) return -1;
     if (g->kind == WF_GEOM_FLAT) return 8LL << 20;  // n <= 128: a few hundred KB of maps and traces
     if (g->kind != WF_GEOM_HEALPIX || g->nside < 1 || lmax < 2 || lmax > 2 * g->nside) return -1;
-    return wf::hp_estimate_bytes(g->nside, lmax, prec, with_host_staging != 0);
+    if (g->ncomp != 0 && g->ncomp != 1 && g->ncomp != 3) return -1;
+    return wf::hp_estimate_bytes(g->nside, lmax, prec, with_host_staging != 0, g->ncomp == 3 ? 3 : 1);
 }
 
 wf_status wf_plan_autotune(wf_plan p, int reps)

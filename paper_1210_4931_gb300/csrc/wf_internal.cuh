@@ -185,7 +185,7 @@ wf_status cuda_check(cudaError_t e, const char *what);
 // device allocation owned by the plan
 wf_status plan_alloc(wf_plan p, void **ptr, size_t bytes);
 wf_status host_staging(wf_plan p);
-long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging);
+long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging, int ncomp);
 // copies ordered on the plan's stream (no legacy-default-stream copies: the
 // plan may run on a non-blocking stream beside other plans); to_host waits
 wf_status to_device(wf_plan p, void *dst, const void *src, size_t bytes);

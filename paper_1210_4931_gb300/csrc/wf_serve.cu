@@ -6,7 +6,7 @@
 //   * `slots` worker threads, each with its own non-blocking CUDA stream; a
 //     worker runs one solve at a time through the host-buffer entry points,
 //     so the solves of different workers overlap on the device;
-//   * a pool of plans keyed by (nside, lmax, precision): a plan holds the
+//   * a pool of plans keyed by (nside, lmax, precision, ncomp): a plan holds the
 //     geometry's Legendre and ring tables and the workspace, and is reused by
 //     later requests of the same key (a key's tables are built once for each
 //     of its solves that run at the same time, not once per request);
@@ -30,7 +30,7 @@ namespace {
 
 struct PooledPlan {
     wf_plan p = nullptr;
-    int nside = 0, lmax = 0;
+    int nside = 0, lmax = 0, ncomp = 1;
     wf_precision prec = WF_PREC_FP64;
     long long bytes = 0;
     bool busy = false;
@@ -50,12 +50,14 @@ struct Admit {
     std::vector<PooledPlan *> evict;   // idle plans to destroy first
 };
 
+int ncomp_of(const wf_request &r) { return r.ncomp == 3 ? 3 : 1; }
+
 long long request_bytes(const wf_request &r)
 {
     wf_geometry g{};
     g.kind = WF_GEOM_HEALPIX;
     g.nside = r.nside;
-    g.ncomp = 1;
+    g.ncomp = ncomp_of(r);
     long long b = wf_plan_estimate_bytes(&g, r.lmax, r.precision, 1);
     if (b < 0) return b;
     if (r.precision != WF_PREC_FP64 && r.opt.refine_sweeps > 0)  // FP64 sub-plan of the correction sweeps
@@ -76,6 +78,7 @@ const char *request_error(const wf_request &r)
     if (r.kind < WF_REQ_WF || r.kind > WF_REQ_CR) return "unknown request kind";
     if (r.nside < 1 || r.lmax < 2 || r.lmax > 2 * r.nside) return "need 2 <= lmax <= 2 nside";
     if (r.precision != WF_PREC_FP64 && r.precision != WF_PREC_MIXED_FP32) return "unknown precision";
+    if (r.ncomp != 0 && r.ncomp != 1 && r.ncomp != 3) return "ncomp must be 0, 1 or 3";
     if (!(r.tol > 0)) return "tol must be > 0";
     if (!r.noise_var || !r.C_ell || !r.s_out) return "noise_var, C_ell and s_out are required";
     if (r.kind != WF_REQ_FLUCT && !r.d) return "d is required";
@@ -113,7 +116,8 @@ struct wf_server_s {
         for (size_t i = 0; i < look; ++i) {
             const wf_request &r = pending[i].r;
             for (PooledPlan *pp : pool)
-                if (!pp->busy && pp->nside == r.nside && pp->lmax == r.lmax && pp->prec == r.precision) {
+                if (!pp->busy && pp->nside == r.nside && pp->lmax == r.lmax && pp->prec == r.precision &&
+                    pp->ncomp == ncomp_of(r)) {
                     a.ok = true;
                     a.idx = i;
                     a.pp = pp;
@@ -168,7 +172,7 @@ void run_request(wf_plan p, const wf_request &r, wf_result &res)
 {
     wf_set_options(p, &r.opt);
     wf_info info{};
-    const long long npix = wf_npix(p);
+    const long long nmap = wf_npix(p) * ncomp_of(r);  // values per map argument
     if (r.kind == WF_REQ_WF) {
         res.status = wf_solve_host(p, r.d, r.noise_var, r.mask, r.C_ell, r.tol, r.s_out, nullptr, &info);
         res.iters = info.iters;
@@ -198,7 +202,7 @@ void run_request(wf_plan p, const wf_request &r, wf_result &res)
     std::vector<double> tmp;
     double *f = r.f_out;
     if (!f) {
-        tmp.resize((size_t)npix);
+        tmp.resize((size_t)nmap);
         f = tmp.data();
     }
     wf_info fi{};
@@ -210,7 +214,7 @@ void run_request(wf_plan p, const wf_request &r, wf_result &res)
         res.status = s2;
         return;
     }
-    for (long long i = 0; i < npix; ++i) r.s_out[i] += f[i];
+    for (long long i = 0; i < nmap; ++i) r.s_out[i] += f[i];
     res.status = (s1 == WF_OK && s2 == WF_OK) ? WF_OK : WF_ENOCONV;
 }
 
@@ -265,7 +269,7 @@ void wf_server_s::worker(int slot)
             wf_geometry g{};
             g.kind = WF_GEOM_HEALPIX;
             g.nside = job.r.nside;
-            g.ncomp = 1;
+            g.ncomp = ncomp_of(job.r);
             wf_plan p = nullptr;
             cs = wf_plan_create(&g, job.r.lmax, job.r.precision, (void *)st, &p);
             if (cs == WF_OK) {
@@ -273,6 +277,7 @@ void wf_server_s::worker(int slot)
                 pp->p = p;
                 pp->nside = job.r.nside;
                 pp->lmax = job.r.lmax;
+                pp->ncomp = ncomp_of(job.r);
                 pp->prec = job.r.precision;
                 pp->bytes = ad.reserve;
                 pp->busy = true;

@@ -169,3 +169,87 @@ def test_invalid_and_oversized_requests_are_rejected(wf):
     srv.close()
     assert got[1]["status"] == wf.WF_EINVAL and got[2]["status"] == wf.WF_ENOMEM
     assert st["rejected"] == 2 and st["plans_created"] == 0
+
+
+def _pol_request(i, nside, lmax):
+    from gpu_util import healpix_pol_case
+
+    P, basis, d, nu, obs, N6, C4 = healpix_pol_case(nside, lmax, gen.seed_for(5, 200 + i))
+    rng = np.random.default_rng(3000 + i)
+    npx = 12 * nside * nside
+    g1 = rng.standard_normal((3, npx))
+    g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    return dict(d=np.ascontiguousarray(d.ravel()), noise_var=np.ascontiguousarray(N6.ravel()),
+                mask=np.ascontiguousarray(P["mask"]), C_ell=np.ascontiguousarray(C4.ravel()),
+                g1=np.ascontiguousarray(g1.ravel()), g2=np.ascontiguousarray(g2.ravel()))
+
+
+POL_CASES = [  # nside, lmax, precision, kind, tol
+    (8, 16, "fp64", "wf", 1e-8),
+    (16, 32, "fp64", "cr", 1e-7),
+    (16, 32, "mixed", "fluct", 1e-5),
+    (32, 64, "mixed", "cr", 1e-5),
+]
+
+
+def test_polarised_requests_in_the_mix(wf):
+    """(I, Q, U) Wiener-filter, fluctuation and constrained-realization
+    requests (ncomp = 3) beside temperature ones: each result equals the same
+    request run alone through the direct host entry points on a fresh plan."""
+    reqs = [_pol_request(i, n, l) for i, (n, l, p, k, t) in enumerate(POL_CASES)]
+    alone = []
+    for (n, l, p, k, t), R in zip(POL_CASES, reqs):
+        plan = wf.wf_plan_create("healpix", nside=n, lmax=l, precision=p, ncomp=3)
+        s = np.empty(R["d"].size)
+        if k in ("wf", "cr"):
+            rep = wf.wf_solve_host(plan, R["d"], R["noise_var"], R["mask"], R["C_ell"], t, s)
+        if k in ("fluct", "cr"):
+            f = np.empty(R["d"].size)
+            rep = wf.wf_fluct_host(plan, R["noise_var"], R["mask"], R["C_ell"], R["g1"], R["g2"], t, f)
+            s = f if k == "fluct" else s + f
+        plan.close()
+        alone.append((s, rep))
+    T_req = _request(90, 32, 64, "wf")
+    srv = wf.Server(mem_budget=4 << 30, slots=3)
+    outs = {}
+    for i, ((n, l, p, k, t), R) in enumerate(zip(POL_CASES, reqs)):
+        outs[i] = np.full(R["d"].size, np.nan)
+        srv.submit(k, nside=n, lmax=l, precision=p, tol=t, s_out=outs[i], tag=i, ncomp=3,
+                   **{key: R[key] for key in ("d", "noise_var", "mask", "C_ell", "g1", "g2")})
+    outT = np.full(T_req["d"].size, np.nan)
+    srv.submit("wf", nside=32, lmax=64, precision="mixed", tol=1e-5, s_out=outT, tag=99, d=T_req["d"],
+               noise_var=T_req["noise_var"], mask=T_req["mask"], C_ell=T_req["C_ell"])
+    got = {}
+    while len(got) < len(POL_CASES) + 1:
+        for r in srv.wait(timeout=60.0):
+            got[r["tag"]] = r
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(POL_CASES) + 1 and st["rejected"] == 0
+    assert got[99]["status"] == wf.WF_OK
+    for i, (n, l, p, k, t) in enumerate(POL_CASES):
+        r = got[i]
+        assert r["status"] == wf.WF_OK, (i, r)
+        s_alone, rep = alone[i]
+        if p == "fp64":
+            assert rel(outs[i], s_alone) < 1e-10, (i, rel(outs[i], s_alone))
+        else:
+            assert r["final_residual"] < t and rep["final_residual"] < t
+            assert rel(outs[i], s_alone) < 1e-3, (i, rel(outs[i], s_alone))
+
+
+def test_polarised_plan_size_estimate(wf):
+    """The estimate bounds the measured size of polarised plans after a Wiener
+    filter and a fluctuation solve through the host entry points."""
+    for nside, prec in ((16, "fp64"), (64, "mixed"), (64, "fp64")):
+        lmax = 2 * nside
+        R = _pol_request(300 + nside, nside, lmax)
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3)
+        s = np.empty(R["d"].size)
+        wf.wf_solve_host(plan, R["d"], R["noise_var"], R["mask"], R["C_ell"], 1e-4, s)
+        f = np.empty(R["d"].size)
+        wf.wf_fluct_host(plan, R["noise_var"], R["mask"], R["C_ell"], R["g1"], R["g2"], 1e-4, f)
+        actual = plan.device_bytes
+        est = wf.wf_plan_estimate_bytes("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3)
+        plan.close()
+        assert actual <= est <= 1.6 * actual + (4 << 20), (nside, prec, actual, est)
