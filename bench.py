@@ -603,12 +603,16 @@ def run_pol_batch(args):
     choices = [int(x) for x in args.pol_nsides.split(",")]
     nsides = rng.choice(choices, size=n)
     T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
-    items, geo = [], []
+    items, geo, base = [], [], {}
     for i, ns in enumerate(nsides):
         ns = int(ns)
         lmax = 2 * ns
-        P = gen.healpix_pol_problem(ns, lmax, gen.seed_for(4, 100 + i), fwhm_arcmin=5.0 * 2048 / ns, corr=0.1,
-                                    b_cut_deg=20.0, n_disks=100, disk_radius_deg=1.0)
+        # one noise model and mask per nside, own signal, noise and fluctuation draws per map
+        if ns not in base:
+            base[ns] = gen.healpix_pol_problem(ns, lmax, gen.seed_for(4, 100 + ns), fwhm_arcmin=5.0 * 2048 / ns,
+                                               corr=0.1, b_cut_deg=20.0, n_disks=100, disk_radius_deg=1.0,
+                                               draws=False)
+        P = dict(base[ns], **gen.healpix_pol_draws(base[ns], gen.seed_for(4, 1000 + i)))
         helper = wf.wf_plan_create("healpix", nside=ns, lmax=lmax, precision="fp64", ncomp=3)
         sig = torch.empty(3 * helper.npix, dtype=torch.float64, device=dev)
         wf.wf_alm2map(helper, T(P["a_signal"].ravel()), lmax, sig)

@@ -160,3 +160,58 @@ def test_pol_fluct_fp64_matches_oracle_replay(wf, nside, lmax, corr):
     assert rep_h["iters"] == rep["iters"]
     assert rel(fh, f.cpu().numpy()) < 1e-12
     plan.close()
+
+
+def test_pol_solve_with_b_modes_matches_oracle_replay(wf):
+    """A prior with BB > 0 (B modes filtered too) and a TE block of full rank:
+    the FP64 polarised solve against the oracle replaying its trace."""
+    import torch
+
+    from oracle.messenger_pol import messenger_solve_pol, pol_tau
+
+    nside, lmax = 8, 16
+    P, basis, d, nu, obs, N6, C4 = healpix_pol_case(nside, lmax, gen.seed_for(4, 77), bb_ratio=0.3)
+    assert np.all(C4[2, 2:] > 0)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=3)
+    npx = 12 * nside * nside
+    s = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    alm = torch.empty(3 * plan.nalm, dtype=torch.complex128, device="cuda")
+    rep = wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(C4.ravel()), 1e-8, s, alm, trace_cap=20000)
+    assert rep["converged"]
+    S = basis.per_mode(P["c_ell"])
+    tau = pol_tau(P["noise_cov"], obs)
+    r = np.einsum("nij,jn->in", nu, d)
+    ref = messenger_solve_pol(basis, r, nu, S, tau, replay=list(zip(rep["lambda_trace"], rep["L_trace"])))
+    got = alm.cpu().numpy().reshape(3, -1)
+    assert np.max(np.abs(got[2])) > 1e-3 * np.max(np.abs(got[1]))  # B is not held at zero
+    assert rel(got, ref["a"]) < 1e-10
+    assert rel(s.cpu().numpy().reshape(3, npx), ref["s"]) < 1e-10
+    plan.close()
+
+
+@pytest.mark.parametrize("nside,lmax,L", [(16, 32, 17), (32, 64, 40)])
+def test_pol_mixed_band_limited_transforms(wf, nside, lmax, L):
+    """Mixed-precision (I, Q, U) transforms restricted to l <= L < lmax (the
+    band limits of the cooling schedule) against the oracle."""
+    import torch
+
+    rng = np.random.default_rng(600 + L)
+    a = _rand_teb(rng, lmax)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed", ncomp=3)
+    npx = 12 * nside * nside
+    m = torch.empty(3 * npx, dtype=torch.float64, device="cuda")
+    wf.wf_alm2map(plan, T(a.ravel()), L, m)
+    got = m.cpu().numpy().reshape(3, npx)
+    I = oracle.synthesis(nside, lmax, L, a[0])
+    Q, U = oracle.synthesis_pol(nside, lmax, L, a[1], a[2])
+    for c, ref in enumerate((I, Q, U)):
+        assert rel(got[c], ref) < 5e-5, (c, rel(got[c], ref))
+    f = rng.standard_normal((3, npx))
+    out = torch.empty(3 * plan.nalm, dtype=torch.complex128, device="cuda")
+    wf.wf_map2alm_adjoint(plan, T(f.ravel()), L, out)
+    got = out.cpu().numpy().reshape(3, plan.nalm)
+    Tt = oracle.adjoint_synthesis(nside, lmax, L, f[0])
+    Et, Bt = oracle.adjoint_pol(nside, lmax, L, f[1], f[2])
+    for c, ref in enumerate((Tt, Et, Bt)):
+        assert rel(got[c], ref) < 5e-5, (c, rel(got[c], ref))
+    plan.close()

@@ -289,21 +289,35 @@ def healpix_pol_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float 
         rho[bad] = rng.uniform(-corr, corr, size=(int(bad.sum()), 3))
     out = {"kind": "healpix_pol", "nside": nside, "lmax": lmax, "c_ell": cl, "noise_cov": N, "mask": base["mask"]}
     if draws:
-        ell = alm_ell(lmax)
-        g = np.stack([alm_unit_gaussian(rng, lmax) for _ in range(3)])
-        a = np.zeros_like(g)
-        # T, E correlated through TE (Cholesky of the 2x2 block), B alone
-        a[0] = np.sqrt(tt[ell]) * g[0]
-        with np.errstate(divide="ignore", invalid="ignore"):
-            c = np.where(tt[ell] > 0, cl[ell, 3] / np.sqrt(np.where(tt[ell] > 0, tt[ell], 1.0)), 0.0)
-        a[1] = c * g[0] + np.sqrt(np.maximum(ee[ell] - c * c, 0.0)) * g[1]
-        a[2] = np.sqrt(cl[ell, 2]) * g[2]
-        out["a_signal"] = a
-        Lc = np.linalg.cholesky(N)
-        out["noise"] = np.einsum("nij,jn->in", Lc, rng.standard_normal((3, npix)))
-        out["g1"] = rng.standard_normal((3, npix))
-        out["g2"] = np.stack([alm_unit_gaussian(rng, lmax) for _ in range(3)])
+        out.update(_pol_draws(rng, out))
     return out
+
+
+def _pol_draws(rng, P: dict) -> dict:
+    lmax, npix = P["lmax"], 12 * P["nside"] ** 2
+    cl = P["c_ell"]
+    tt, ee = cl[:, 0], cl[:, 1]
+    ell = alm_ell(lmax)
+    g = np.stack([alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    a = np.zeros_like(g)
+    # T, E correlated through TE (Cholesky of the 2x2 block), B alone
+    a[0] = np.sqrt(tt[ell]) * g[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = np.where(tt[ell] > 0, cl[ell, 3] / np.sqrt(np.where(tt[ell] > 0, tt[ell], 1.0)), 0.0)
+    a[1] = c * g[0] + np.sqrt(np.maximum(ee[ell] - c * c, 0.0)) * g[1]
+    a[2] = np.sqrt(cl[ell, 2]) * g[2]
+    Lc = np.linalg.cholesky(P["noise_cov"])
+    noise = np.einsum("nij,jn->in", Lc, rng.standard_normal((3, npix)))
+    g1 = rng.standard_normal((3, npix))
+    g2 = np.stack([alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    return {"a_signal": a, "noise": noise, "g1": g1, "g2": g2}
+
+
+def healpix_pol_draws(P: dict, seed: int) -> dict:
+    """Another set of draws (signal a_signal, noise, fluctuation g1 and g2)
+    for an existing polarised problem P (its spectra and noise blocks), from
+    seed: many maps of one geometry without rebuilding its noise model."""
+    return _pol_draws(np.random.default_rng(seed), P)
 
 
 # ---------------------------------------------------------------------------
