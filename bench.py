@@ -327,9 +327,16 @@ def run_ours(args):
     achieved = LEG_FLOPS_PER_TRIPLE * leg_triples / (leg_ms / 1e3) / 1e12
     sm_mhz = ck.get("sm_mhz") or 2070.0
     peak = peak_fp32_tflops(2070.0)
+    # DRAM bytes (read + write) of one full-band k_legsyn_mx<8> + k_legana_mx<8, 8> pair at nside 2048,
+    # lmax 4096, from a one-pass ncu capture of these kernels (659.9 + 739.9 MB); other sizes or tiles
+    # were not captured
+    traffic = 1399823104 if (nside, lmax, tuple(tiles), args.precision) == (2048, 4096, (8, 8), "mixed") else None
     roof = {"bound": "alu", "kernel": "legendre synthesis + analysis (k_legsyn, k_legana)",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, see design notes)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_basis": "DRAM bytes of one full-band synthesis + analysis pair (ncu dram__bytes_read.sum + "
+                             "dram__bytes_write.sum)" if traffic else None,
+            "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (from the unit counts and the "
+                          "maximum SM clock; no measured FP32 peak exists for this pool)",
             "flops_per_triple": LEG_FLOPS_PER_TRIPLE, "kernel_ms": leg_ms,
             "share_of_step": leg_ms / max(1e-9, sum(kms.values()))}
 

@@ -51,7 +51,8 @@ typedef enum {
     WF_ENOMEM = 2,    /* device or host allocation failed */
     WF_ECUDA = 3,     /* a CUDA call failed; see wf_last_error() */
     WF_ENOCONV = 4,   /* iteration cap reached; the last iterate is still written */
-    WF_EDIVERGE = 5,  /* residual grew without bound (see the design notes on HEALPix quadrature) */
+    WF_EDIVERGE = 5,  /* residual grew without bound (e.g. lmax far above 2 nside, where the HEALPix
+                         analysis Omega Y^T is too far from the inverse of the synthesis to contract) */
     WF_ETIMEOUT = 6,  /* a bounded device wait gave up */
     WF_EUNSUPPORTED = 7
 } wf_status;

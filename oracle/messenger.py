@@ -30,7 +30,7 @@ Paper passages followed, in order of use:
   identity in masked pixels; in the r form above this is
   r = nu^1/2 g1 + Omega Y (S^-1/2 g2).
 
-Readings where the paper is silent (also listed in the design notes): the
+Readings where the paper is silent: the
 plateau test |chi2_k - chi2_{k-1}| < eta sigma_chi2 with eta = 1e-2 and
 sigma_chi2 = sqrt(2 n_dof); a cap of ``level_cap`` iterations per level; on
 the flat grid the levels are k_iter = 1, 2, 4, ... with
