@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE (see the package docstring).  Maps are (I, Q, U) per
 pixel, harmonic coefficients (T, E, B) per mode; the noise is a symmetric
-positive definite 3x3 block per observed pixel (inverse nu = N^-1, zero in
-masked pixels), the prior a 3x3 block per l,
+positive definite 3x3 block per pixel on its observed components (inverse
+nu = N^-1 there, zero rows and columns for masked components, see
+pol_inverse_noise), the prior a 3x3 block per l,
 
     S_l = [[TT, TE, 0], [TE, EE, 0], [0, 0, BB]],
 
@@ -91,9 +92,47 @@ def sym_sqrt(M, inverse=False):
     return np.einsum("nij,nj,nkj->nik", V, f, V)
 
 
+def observed_components(mask):
+    """(npix, 3) booleans: which of I, Q, U each pixel observes.  ``mask`` is
+    either booleans (all three or none) or the codes 0 (none), 1 (I, Q, U),
+    2 (I only: polarisation masked) and 3 (Q, U only: temperature masked)."""
+    m = np.asarray(mask)
+    if m.dtype == bool:
+        return np.repeat(m[:, None], 3, axis=1)
+    out = np.zeros((m.size, 3), dtype=bool)
+    out[m == 1] = True
+    out[m == 2, 0] = True
+    out[m == 3, 1:] = True
+    return out
+
+
+def _patterns(comp):
+    for pattern in np.unique(comp, axis=0):
+        K = np.nonzero(pattern)[0]
+        if K.size:
+            yield np.all(comp == pattern, axis=1), K
+
+
+def pol_inverse_noise(N, mask):
+    """nu per pixel: the inverse of the noise block restricted to the observed
+    components, zero in the rows and columns of the others -- the limit of
+    N^-1 as the variance of an unobserved component goes to infinity (the
+    masked pixels of Sect. 2.1, N^-1 = 0, component by component)."""
+    comp = observed_components(mask)
+    nu = np.zeros_like(N)
+    for sel, K in _patterns(comp):
+        idx = np.nonzero(sel)[0]
+        sub = N[np.ix_(idx, K, K)]
+        nu[np.ix_(idx, K, K)] = np.linalg.inv(sub)
+    return nu
+
+
 def pol_tau(N, obs):
-    """tau = smallest eigenvalue of the noise blocks over observed pixels."""
-    return float(np.linalg.eigvalsh(N[obs]).min())
+    """tau = smallest eigenvalue of the noise blocks over the observed
+    components (the observed sub-block of each pixel), so that N - tau stays
+    positive semi-definite where there is data."""
+    comp = observed_components(obs)
+    return float(min(np.linalg.eigvalsh(N[np.ix_(np.nonzero(sel)[0], K, K)]).min() for sel, K in _patterns(comp)))
 
 
 def fluct_source_pol(basis, nu, S, g1, g2):
@@ -118,8 +157,7 @@ def messenger_solve_pol(basis, r, nu, S, tau, *, tol=1e-6, maxiter=20000, replay
     w = basis.w
     b = basis.adjoint(r, lmax)
     bnorm = float(np.sqrt(np.sum(w * np.sum(np.abs(_apply(Pr, b)) ** 2, axis=0))))
-    obs = np.any(nu != 0.0, axis=(1, 2))
-    n_dof = 3 * int(np.count_nonzero(obs))
+    n_dof = int(np.count_nonzero(np.diagonal(nu, axis1=1, axis2=2) > 0.0))  # observed components
     sigma = float(np.sqrt(2.0 * n_dof))
     schedule = None
     if replay is None:

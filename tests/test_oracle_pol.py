@@ -18,16 +18,23 @@ def oracle():
     return o
 
 
-def _pol_case(oracle, nside, lmax, seed, **kw):
-    from oracle.messenger_pol import HealpixPolBasis
+def _pol_case(oracle, nside, lmax, seed, partial=False, **kw):
+    from oracle.messenger_pol import HealpixPolBasis, pol_inverse_noise
 
     P = gen.healpix_pol_problem(nside, lmax, seed, **kw)
     basis = HealpixPolBasis(nside, lmax)
     d = basis.synth(P["a_signal"]) + P["noise"]
     obs = P["mask"] > 0
-    nu = np.zeros_like(P["noise_cov"])
-    nu[obs] = np.linalg.inv(P["noise_cov"][obs])
-    return P, basis, d, nu, obs
+    if not partial:
+        nu = np.zeros_like(P["noise_cov"])
+        nu[obs] = np.linalg.inv(P["noise_cov"][obs])
+        return P, basis, d, nu, obs
+    # separate masks: every fourth observed pixel observes I only, every fifth Q, U only
+    code = obs.astype(np.uint8)
+    k = np.nonzero(obs)[0]
+    code[k[::4]] = 2
+    code[k[1::5]] = 3
+    return P, basis, d, pol_inverse_noise(P["noise_cov"], code), code
 
 
 def test_decoupled_limit_is_the_temperature_iteration(oracle):
@@ -95,16 +102,19 @@ def _to_x(a, modes):
     return np.array([a[c, k].real if p == 0 else a[c, k].imag for c, k, p in modes])
 
 
-@pytest.mark.parametrize("bb", [0.3, 0.0])
-def test_pol_converges_to_dense_fixed_point(oracle, bb):
+@pytest.mark.parametrize("bb,partial", [(0.3, False), (0.0, False), (0.3, True)])
+def test_pol_converges_to_dense_fixed_point(oracle, bb, partial):
     """[S^+ + Y^T nu Y + (1 - Omega Y^T Y) / tau_h] a = Y^T r on the range of S,
     solved densely; the iteration at lambda = 1 contracts (spectral radius < 1)
     and the reported residual is the dense one."""
     from oracle.messenger_pol import messenger_solve_pol, pol_tau
 
     nside, lmax = 2, 4
-    P, basis, d, nu, obs = _pol_case(oracle, nside, lmax, 43, bb_ratio=bb, corr=0.1, fwhm_arcmin=600.0,
-                                     b_cut_deg=10.0, n_disks=1, disk_radius_deg=20.0, noise_level_ell=lmax)
+    P, basis, d, nu, obs = _pol_case(oracle, nside, lmax, 43, partial=partial, bb_ratio=bb, corr=0.1,
+                                     fwhm_arcmin=600.0, b_cut_deg=10.0, n_disks=1, disk_radius_deg=20.0,
+                                     noise_level_ell=lmax)
+    if partial:
+        assert set(np.unique(obs)) == {0, 1, 2, 3}
     tau = pol_tau(P["noise_cov"], obs)
     om = basis.omega
     S = basis.per_mode(P["c_ell"])
@@ -213,3 +223,40 @@ def test_pol_fluct_source_decoupled_limit(oracle):
     for c, z in ((1, Q), (2, U)):
         ref = np.sqrt(nu[:, c, c]) * g1[c] + basis.omega * z
         np.testing.assert_allclose(r[c], ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_partial_mask_inverse_noise_is_the_infinite_variance_limit(oracle):
+    """nu for separate T / P masks equals the inverse of the full block once the
+    unobserved components' variances are made huge (1e12 added on the
+    diagonal), and tau is the smallest eigenvalue of the observed sub-blocks:
+    N - tau (1 - 1e-9) is positive definite on every observed sub-block and
+    N - tau (1 + 1e-9) is not on at least one (Cholesky)."""
+    from oracle.messenger_pol import observed_components, pol_inverse_noise, pol_tau
+
+    rng = np.random.default_rng(52)
+    n = 400
+    X = rng.standard_normal((n, 3, 3))
+    N = np.einsum("nij,nkj->nik", X, X) + 0.3 * np.eye(3)
+    code = rng.integers(0, 4, size=n).astype(np.uint8)
+    nu = pol_inverse_noise(N, code)
+    comp = observed_components(code)
+    big = N + np.einsum("ni,ij->nij", (~comp).astype(float) * 1e12, np.eye(3))
+    lim = np.linalg.inv(big)
+    np.testing.assert_allclose(nu, lim, rtol=0, atol=1e-9 * np.max(np.abs(nu)))
+    assert np.all(nu[~comp[:, 0], 0, :] == 0.0) and np.all(nu[code == 2][:, 1:, :] == 0.0)
+    tau = pol_tau(N, code)
+    ok_below, fails_above = True, False
+    for p in range(n):
+        K = np.nonzero(comp[p])[0]
+        if K.size == 0:
+            continue
+        sub = N[p][np.ix_(K, K)]
+        try:
+            np.linalg.cholesky(sub - tau * (1 - 1e-9) * np.eye(K.size))
+        except np.linalg.LinAlgError:
+            ok_below = False
+        try:
+            np.linalg.cholesky(sub - tau * (1 + 1e-9) * np.eye(K.size))
+        except np.linalg.LinAlgError:
+            fails_above = True
+    assert ok_below and fails_above

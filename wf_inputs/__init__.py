@@ -257,7 +257,8 @@ def healpix_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float = 13
 
 
 def healpix_pol_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float = 13.0, corr: float = 0.1,
-                        pol_noise_factor: float = 2.0, bb_ratio: float = 0.0, draws: bool = True, **kw) -> dict:
+                        pol_noise_factor: float = 2.0, bb_ratio: float = 0.0, p_b_cut_deg=None, draws: bool = True,
+                        **kw) -> dict:
     """Polarised (I, Q, U) workload.  Spectra: TT CMB-like, EE = 0.05 TT in
     shape, TE = 0.5 sqrt(TT EE), BB = bb_ratio EE; columns (TT, EE, BB, TE).
     Noise per pixel: diag(s_I^2, s_Q^2, s_U^2) with s_I^2 from the temperature
@@ -266,7 +267,9 @@ def healpix_pol_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float 
     in [-corr, corr], redrawn until the block is positive definite.  Draws:
     signal (T, E, B) from the prior blocks, noise from the pixel blocks,
     fluctuation draws g1 (3, npix) and g2 (3, n_alm).  The mask is shared by
-    I, Q and U."""
+    I, Q and U (values 0 / 1), unless ``p_b_cut_deg`` adds a polarisation
+    mask |b| < p_b_cut_deg: there observed pixels get the code 2 (I observed,
+    Q and U masked)."""
     base = healpix_problem(nside, lmax, seed, fwhm_arcmin=fwhm_arcmin, draws=False, **kw)
     rng = np.random.default_rng(seed + 7919)
     npix = 12 * nside * nside
@@ -287,7 +290,12 @@ def healpix_pol_problem(nside: int, lmax: int, seed: int, *, fwhm_arcmin: float 
         if not bad.any():
             break
         rho[bad] = rng.uniform(-corr, corr, size=(int(bad.sum()), 3))
-    out = {"kind": "healpix_pol", "nside": nside, "lmax": lmax, "c_ell": cl, "noise_cov": N, "mask": base["mask"]}
+    mask = base["mask"].copy()
+    if p_b_cut_deg is not None:
+        z, _, nr = ring_layout(nside)
+        zp = np.repeat(z, nr)
+        mask[(mask > 0) & (np.abs(zp) < np.sin(np.radians(p_b_cut_deg)))] = 2
+    out = {"kind": "healpix_pol", "nside": nside, "lmax": lmax, "c_ell": cl, "noise_cov": N, "mask": mask}
     if draws:
         out.update(_pol_draws(rng, out))
     return out
