@@ -155,8 +155,13 @@ wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n);
  * Noise variance must be finite and > 0 on observed pixels (WF_EINVAL).
  * Polarised plans (ncomp = 3; Eqs. 10-11, heuristic cooling or replay): d and
  * s_wf are 3 x n_pix (I, Q, U, component-major); noise_var is the 3x3 noise
- * covariance per pixel as 6 x n_pix (II, QQ, UU, IQ, IU, QU), positive definite
- * on observed pixels; the mask is shared by I, Q, U; C_ell is 4 x (lmax + 1)
+ * covariance per pixel as 6 x n_pix (II, QQ, UU, IQ, IU, QU); the mask byte of a
+ * pixel is a code: 0 nothing observed, 1 I, Q and U, 2 I only (polarisation
+ * masked), 3 Q and U only (temperature masked), others WF_EINVAL (NULL: all
+ * observed).  Masking is infinite noise component by component: N^-1 is the
+ * inverse of the observed sub-block, which must be positive definite, tau
+ * the smallest eigenvalue of any observed sub-block and n_dof the number of
+ * observed components; d may hold anything in unobserved components.  C_ell is 4 x (lmax + 1)
  * (TT, EE, BB, TE), each block [[TT, TE, 0], [TE, EE, 0], [0, 0, BB]] positive
  * semi-definite with TE^2 < TT EE wherever TE != 0 (WF_EINVAL otherwise); zero
  * entries act through the pseudo-inverse (e.g. BB = 0, or l < 2); alm_out is

@@ -501,8 +501,14 @@ __device__ __forceinline__ void atomic_min_posd(double *addr, double v)
     atomicMin(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// nu = N^-1 (0 where masked), r = nu d, tau = min eigenvalue of N over observed
-// pixels, observed count, and a flag for invalid inputs
+// Per-pixel mask codes of polarised plans: 0 nothing observed, 1 I, Q, U,
+// 2 I only (polarisation masked), 3 Q, U only (temperature masked).  Masking
+// is infinite noise (N^-1 = 0, Sect. 2.1) component by component: nu is the
+// inverse of the observed sub-block, zero in the other rows and columns (its
+// limit as the unobserved variances grow), r = nu d, and tau is the smallest
+// eigenvalue of any observed sub-block.  Counts observed components (n_dof)
+// and flags invalid inputs: a code above 3, or an observed sub-block that is
+// not finite and positive definite, or observed d not finite.
 __global__ void k_setup_pol(long long npix, const double *__restrict__ d, const double *__restrict__ N6,
                             const uint8_t *__restrict__ mask, double *__restrict__ r, double *__restrict__ nu6,
                             double *__restrict__ scal, int *__restrict__ flag)
@@ -511,38 +517,65 @@ __global__ void k_setup_pol(long long npix, const double *__restrict__ d, const 
     unsigned long long cnt = 0;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (long long)gridDim.x * blockDim.x) {
-        const bool obs = mask ? mask[p] != 0 : true;
-        if (!obs) {
-            store6(nu6, npix, p, Sym3{0, 0, 0, 0, 0, 0});
+        const int code = mask ? mask[p] : 1;
+        const Sym3 zero{0, 0, 0, 0, 0, 0};
+        if (code == 0 || code > 3) {
+            if (code > 3) atomicOr(flag, 1);
+            store6(nu6, npix, p, zero);
             r[p] = r[npix + p] = r[2 * npix + p] = 0.0;
             continue;
         }
+        const bool oI = code != 3, oP = code != 2;
         const Sym3 N = load6(N6, npix, p);
-        const double m2 = N.a * N.b - N.d * N.d, m3 = det3(N);
-        bool ok = isfinite(N.a) && isfinite(N.b) && isfinite(N.c) && isfinite(N.d) && isfinite(N.e) &&
-                  isfinite(N.f) && N.a > 0.0 && m2 > 0.0 && m3 > 0.0;
+        bool ok = true;
         double dv[3] = {0.0, 0.0, 0.0};
         if (d) {
-            dv[0] = d[p];
-            dv[1] = d[npix + p];
-            dv[2] = d[2 * npix + p];
-            ok = ok && isfinite(dv[0]) && isfinite(dv[1]) && isfinite(dv[2]);
+            dv[0] = oI ? d[p] : 0.0;
+            dv[1] = oP ? d[npix + p] : 0.0;
+            dv[2] = oP ? d[2 * npix + p] : 0.0;
+            ok = isfinite(dv[0]) && isfinite(dv[1]) && isfinite(dv[2]);
+        }
+        Sym3 nu = zero;
+        double tl = INFINITY;
+        if (code == 1) {
+            const double m2 = N.a * N.b - N.d * N.d, m3 = det3(N);
+            ok = ok && isfinite(N.a) && isfinite(N.b) && isfinite(N.c) && isfinite(N.d) && isfinite(N.e) &&
+                 isfinite(N.f) && N.a > 0.0 && m2 > 0.0 && m3 > 0.0;
+            if (ok) {
+                nu = inv3(N);
+                tl = eigmin3(N);
+            }
+        } else if (code == 2) {
+            ok = ok && isfinite(N.a) && N.a > 0.0;
+            if (ok) {
+                nu.a = 1.0 / N.a;
+                tl = N.a;
+            }
+        } else {
+            const double det = N.b * N.c - N.f * N.f;
+            ok = ok && isfinite(N.b) && isfinite(N.c) && isfinite(N.f) && N.b > 0.0 && det > 0.0;
+            if (ok) {
+                nu.b = N.c / det;
+                nu.c = N.b / det;
+                nu.f = -N.f / det;
+                const double h = 0.5 * (N.b - N.c);
+                tl = 0.5 * (N.b + N.c) - sqrt(h * h + N.f * N.f);
+            }
         }
         if (!ok) {
             atomicOr(flag, 1);
-            store6(nu6, npix, p, Sym3{0, 0, 0, 0, 0, 0});
+            store6(nu6, npix, p, zero);
             r[p] = r[npix + p] = r[2 * npix + p] = 0.0;
             continue;
         }
-        const Sym3 nu = inv3(N);
         store6(nu6, npix, p, nu);
         double rv[3];
         mv3(nu, dv, rv);
         r[p] = rv[0];
         r[npix + p] = rv[1];
         r[2 * npix + p] = rv[2];
-        tmin = fmin(tmin, eigmin3(N));
-        ++cnt;
+        tmin = fmin(tmin, tl);
+        cnt += code == 1 ? 3 : (code == 2 ? 1 : 2);
     }
     for (int o = 16; o >= 1; o >>= 1) {
         tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
@@ -793,9 +826,16 @@ __global__ void k_fluct_source_pol(long long npix, const double *__restrict__ nu
          p += (long long)gridDim.x * blockDim.x) {
         const Sym3 nu = load6(nu6, npix, p);
         double o[3] = {0.0, 0.0, 0.0};
-        if (nu.a != 0.0 || nu.b != 0.0 || nu.c != 0.0) {
-            const double g[3] = {g1[p], g1[npix + p], g1[2 * npix + p]};
+        const double g[3] = {g1[p], g1[npix + p], g1[2 * npix + p]};
+        const bool hasI = nu.a != 0.0, hasP = nu.b != 0.0 || nu.c != 0.0;
+        if (hasI && hasP) {
             mv3(sqrt3(nu), g, o);
+        } else if (hasI) {  // I only: the block is nu_II alone
+            o[0] = sqrt(nu.a) * g[0];
+        } else if (hasP) {  // Q, U only: sqrt of [[b, f], [f, c]] = ([[b, f], [f, c]] + s) / t, s = det^1/2, t = (b + c + 2 s)^1/2
+            const double sd = sqrt(nu.b * nu.c - nu.f * nu.f), t = sqrt(nu.b + nu.c + 2.0 * sd);
+            o[1] = ((nu.b + sd) * g[1] + nu.f * g[2]) / t;
+            o[2] = (nu.f * g[1] + (nu.c + sd) * g[2]) / t;
         }
         r[p] = o[0] + omega * z[p];
         r[npix + p] = o[1] + omega * z[npix + p];
@@ -844,7 +884,9 @@ __global__ void k_pix_chi2_pol(long long npix, const double *__restrict__ d, con
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (long long)gridDim.x * blockDim.x) {
         const Sym3 nu = load6(nu6, npix, p);
-        const double e[3] = {d[p] - s[p], d[npix + p] - s[npix + p], d[2 * npix + p] - s[2 * npix + p]};
+        // unobserved components (zero rows of nu) may hold anything in d, NaN included
+        const double e[3] = {nu.a != 0.0 ? d[p] - s[p] : 0.0, nu.b != 0.0 ? d[npix + p] - s[npix + p] : 0.0,
+                             nu.c != 0.0 ? d[2 * npix + p] - s[2 * npix + p] : 0.0};
         double ne[3];
         mv3(nu, e, ne);
         acc += e[0] * ne[0] + e[1] * ne[1] + e[2] * ne[2];
@@ -1012,11 +1054,11 @@ wf_status hp_pol_setup(wf_plan p, const double *d, const double *N6, const uint8
     WF_CUDA(cudaStreamSynchronize(p->stream));
     unsigned long long cnt;
     std::memcpy(&cnt, &sc[1], sizeof cnt);
-    if (flag) return set_error(WF_EINVAL, "noise covariance must be finite and positive definite (and d finite) on "
-                                          "observed pixels");
+    if (flag) return set_error(WF_EINVAL, "mask codes must be 0..3, and the noise covariance finite and positive "
+                                          "definite (and d finite) on the observed components");
     if (cnt == 0) return set_error(WF_EINVAL, "every pixel is masked");
     *tau = sc[0];
-    *ndof = 3LL * (long long)cnt;
+    *ndof = (long long)cnt;  // observed components
     return WF_OK;
 }
 
