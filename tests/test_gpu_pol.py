@@ -116,6 +116,32 @@ def test_pol_rejections(wf):
     with pytest.raises(wf.WfError) as e:
         wf.wf_fluct(plan, T(N6.ravel()), T(P["mask"]), T(badC.ravel()), g1, g2, 1e-6, s)
     assert e.value.status == wf.WF_EINVAL
+    # mask codes: 4 is not one; a code-2 pixel (I only) needs N_II > 0 but nothing of Q, U;
+    # a code-3 pixel (Q, U only) needs its 2x2 block positive definite; all masked is rejected
+    m4 = P["mask"].copy()
+    m4[3] = 4
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(m4), T(C4.ravel()), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    k = np.nonzero(P["mask"])[0][7]
+    m2, bad2 = P["mask"].copy(), N6.copy()
+    m2[k] = 2
+    bad2[1, k] = -1.0  # QQ < 0 is not observed at a code-2 pixel: accepted
+    rep = wf.wf_solve(plan, T(d.ravel()), T(bad2.ravel()), T(m2), T(C4.ravel()), 1e-4, s)
+    assert rep["status"] in (wf.WF_OK, wf.WF_ENOCONV)
+    bad2[0, k] = 0.0  # N_II = 0 at an I-only pixel: rejected
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(bad2.ravel()), T(m2), T(C4.ravel()), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    m3, bad3 = P["mask"].copy(), N6.copy()
+    m3[k] = 3
+    bad3[5, k] = 2.0 * np.sqrt(bad3[1, k] * bad3[2, k])  # |rho_QU| > 1
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(bad3.ravel()), T(m3), T(C4.ravel()), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(np.zeros_like(P["mask"])), T(C4.ravel()), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
     wf.wf_set_options(plan, schedule=1)
     with pytest.raises(wf.WfError) as e:
         wf.wf_solve(plan, T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(C4.ravel()), 1e-6, s)
