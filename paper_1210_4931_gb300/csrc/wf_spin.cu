@@ -590,9 +590,8 @@ __global__ void k_setup_pol(long long npix, const double *__restrict__ d, const 
 // Eq. (10): t = s + lam tau (1 + (lam - 1) tau nu)^-1 (r - nu s), in place on
 // the synthesised maps, and the pixel term of chi^2,
 // sum (nu s) . u - 2 r . u with u = (1 + (lam - 1) tau nu)^-1 s; per-block partials
-template <typename TM>
 __global__ void k_blend_pol(long long npix, const double *__restrict__ r, const double *__restrict__ nu6,
-                            TM *__restrict__ t, double lt, double lm1t, double *__restrict__ part)
+                            double *__restrict__ t, double lt, double lm1t, double *__restrict__ part)
 {
     __shared__ double red[32];
     double chi = 0.0;
@@ -609,9 +608,9 @@ __global__ void k_blend_pol(long long npix, const double *__restrict__ r, const 
         double y[3], u[3];
         mv3(Mi, res, y);
         mv3(Mi, s, u);
-        t[p] = (TM)(s[0] + lt * y[0]);
-        t[npix + p] = (TM)(s[1] + lt * y[1]);
-        t[2 * npix + p] = (TM)(s[2] + lt * y[2]);
+        t[p] = s[0] + lt * y[0];
+        t[npix + p] = s[1] + lt * y[1];
+        t[2 * npix + p] = s[2] + lt * y[2];
         chi += (ns[0] - 2.0 * rv[0]) * u[0] + (ns[1] - 2.0 * rv[1]) * u[1] + (ns[2] - 2.0 * rv[2]) * u[2];
     }
     for (int o = 16; o >= 1; o >>= 1) chi += __shfl_xor_sync(0xffffffffu, chi, o);
@@ -1067,8 +1066,8 @@ wf_status hp_pol_blend(wf_plan p, double lam, double tau, int *nblocks)
     PolState *s = p->pol;
     const int grid = (int)std::min<long long>((p->npix + 255) / 256, 2LL * p->nsm);
     if (p->prec == WF_PREC_FP64)
-        k_blend_pol<double><<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, (double *)s->t, lam * tau,
-                                                         (lam - 1.0) * tau, s->part);
+        k_blend_pol<<<grid, 256, 0, p->stream>>>(p->npix, s->r, s->nu, (double *)s->t, lam * tau, (lam - 1.0) * tau,
+                                                 s->part);
     else
         k_blend_pol_f32<<<grid, 256, 0, p->stream>>>(p->npix, s->r32, s->nu32, (float *)s->t, (float)(lam * tau),
                                                      (float)((lam - 1.0) * tau), s->part);
