@@ -93,6 +93,23 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_over_ranks(t_ms, units, device):
+    """Whole-job figures of independent replicas: the slowest rank's time (all
+    ranks start after one barrier and stop before another) and the units of
+    work all ranks processed.  Works on any initialised process group (NCCL on
+    the GPUs, gloo in the CPU tests); one rank returns its own figures."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t_ms), float(units)
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def make_problem(nside, lmax, k):
     kw = dict(fwhm_arcmin=CFG["fwhm_arcmin"], b_cut_deg=CFG["b_cut_deg"], n_disks=CFG["n_disks"],
               disk_radius_deg=CFG["disk_radius_deg"], noise_range=CFG["noise_range"])
@@ -299,12 +316,7 @@ def run_ours(args):
     ck = clocks.stop()
     t_ms = e0.elapsed_time(e1)
     iters = sum(r["iters"] for r in reps)
-    if ws > 1:
-        tt = torch.tensor([t_ms, iters], dtype=torch.float64, device=dev)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt[1:], op=torch.distributed.ReduceOp.SUM)
-        t_ms, iters = float(tmax[0]), float(tt[1])
+    t_ms, iters = aggregate_over_ranks(t_ms, iters, dev)
     value = iters / (t_ms / 1e3)
     last = reps[-1]
 
