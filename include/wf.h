@@ -147,6 +147,19 @@ wf_status wf_set_options(wf_plan p, const wf_options *opt);
  * Host arrays, copied; n = 0 returns to the schedule. */
 wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n);
 
+/* Checkpoint / resume.  The messenger iteration keeps no state but its
+ * iterate a_k and the schedule's (lambda, L): the next solves on this plan
+ * start from alm0 (device, n_alm complex per component, the layout of
+ * alm_out) instead of zero; NULL restores the zero start.  The pointer is kept,
+ * not copied: the array must stay valid while the plan solves.  A run stopped
+ * after k iterations (alm_out and the (lambda, L) trace of its report) and
+ * resumed with wf_set_start(alm_out) and wf_set_schedule(the rest of the
+ * trace) repeats the uninterrupted run (to the atomics' reduction order).
+ * HEALPix plans; not with the chi^2-bound schedule (WF_EUNSUPPORTED at the
+ * solve); in a replay the run stops at the first full-band lambda = 1
+ * iteration whose residual is below tol. */
+wf_status wf_set_start(wf_plan p, const double *alm0);
+
 /* Wiener filter (Eq. 2) by the messenger iteration.  d, noise_var: n_pix
  * FP64; mask: n_pix uint8 (may be NULL: all observed); C_ell: prior (see
  * conventions).  tol: relative residual |(S^-1 + N^-1) s - N^-1 d| / |N^-1 d|

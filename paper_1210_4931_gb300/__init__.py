@@ -90,7 +90,7 @@ class wf_server_stats(ctypes.Structure):
 
 
 _lib = None
-EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host",
+EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_set_start", "wf_solve", "wf_solve_host",
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
            "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
            "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     L.wf_plan_destroy.restype = None
     L.wf_set_options.argtypes = [vp, ctypes.POINTER(wf_options)]
     L.wf_set_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.wf_set_start.argtypes = [vp, dp]
     sig = [vp, dp, dp, u8p, dp, ctypes.c_double, dp, dp, ctypes.POINTER(wf_info)]
     L.wf_solve.argtypes = sig
     L.wf_solve_host.argtypes = sig
@@ -252,6 +253,14 @@ def wf_set_options(plan: Plan, **kw):
     for k, v in kw.items():
         setattr(o, k, v)
     _check(load().wf_set_options(plan.handle, ctypes.byref(o)), "wf_set_options")
+
+
+def wf_set_start(plan: Plan, alm0=None):
+    """Start the next solves on this plan from alm0 (a CUDA complex128 tensor in
+    the alm_out layout, kept referenced here) instead of zero; None clears."""
+    n = plan.nalm * 16 * plan.ncomp
+    _check(load().wf_set_start(plan.handle, _ptr(alm0, None, n, "alm0")), "wf_set_start")
+    plan._start = alm0
 
 
 def wf_set_schedule(plan: Plan, lam, L=None):

@@ -1498,6 +1498,7 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
         r.info = it.info;
         r.copy_back = true;
         r.graph = true;
+        r.a_init = plans[i]->start;
         statuses[i] = hp_begin(r);
         active[i] = statuses[i] == WF_OK;
     }
@@ -1776,6 +1777,14 @@ wf_status wf_set_options(wf_plan p, const wf_options *opt)
     return WF_OK;
 }
 
+wf_status wf_set_start(wf_plan p, const double *alm0)
+{
+    if (!p) return set_error(WF_EINVAL, "null plan");
+    if (p->g.kind != WF_GEOM_HEALPIX && alm0) return set_error(WF_EUNSUPPORTED, "a starting iterate needs a HEALPix plan");
+    p->start = (const double2 *)alm0;
+    return WF_OK;
+}
+
 wf_status wf_set_schedule(wf_plan p, const double *lambda, const int *L, int n)
 {
     if (!p || n < 0 || (n > 0 && !lambda)) return set_error(WF_EINVAL, "bad schedule");
@@ -1845,8 +1854,9 @@ wf_status wf_solve(wf_plan p, const double *d, const double *noise_var, const ui
             return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule is implemented on the HEALPix sphere only");
         return flat_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
     }
-    if (p->pol) return hp_solve_pol(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
-    return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info);
+    if (p->pol)
+        return hp_solve_pol(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info, p->start);
+    return hp_solve(p, d, noise_var, mask, C_ell, tol, false, nullptr, nullptr, s_wf, alm_out, info, p->start);
 }
 
 wf_status wf_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, void *cuda_stream, wf_status *statuses)
@@ -1869,8 +1879,8 @@ wf_status wf_fluct(wf_plan p, const double *noise_var, const uint8_t *mask, cons
     }
     if (p->pol)
         return hp_solve_pol(p, nullptr, noise_var, mask, C_ell, tol, true, g1, (const double2 *)g2, f_out, alm_out,
-                            info);
-    return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info);
+                            info, p->start);
+    return hp_solve(p, nullptr, noise_var, mask, C_ell, tol, true, g1, g2, f_out, alm_out, info, p->start);
 }
 
 }  // extern "C"

@@ -154,6 +154,7 @@ struct wf_plan_s {
     wf::FlatPlan *flat = nullptr;
     wf::PolState *pol = nullptr;  // polarised plans (ncomp = 3)
     wf_options opt{};
+    const double2 *start = nullptr;  // starting iterate of the next solves (wf_set_start), or zero
     std::vector<double> replay_lambda;
     std::vector<int> replay_L;
     long long device_bytes = 0;

@@ -304,3 +304,43 @@ def test_chi2_bound_schedule_rejections(wf):
                     T(Pf["S"].ravel()), 1e-6, sf)
     assert e.value.status == wf.WF_EUNSUPPORTED
     flat.close()
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_checkpoint_resume_repeats_the_uninterrupted_run(wf, ncomp):
+    """A replayed run stopped after k iterations and resumed from its alm_out
+    with the rest of the trace (wf_set_start + wf_set_schedule) ends where the
+    uninterrupted run ends (FP64, to the reduction order of the atomics)."""
+    import torch
+
+    from gpu_util import healpix_pol_case
+
+    nside, lmax = 16, 32
+    if ncomp == 1:
+        P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 77))
+        args = (T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]))
+    else:
+        P, basis, d, nu, obs, N6, C4 = healpix_pol_case(nside, lmax, gen.seed_for(4, 78))
+        args = (T(d.ravel()), T(N6.ravel()), T(P["mask"]), T(C4.ravel()))
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64", ncomp=ncomp)
+    n = ncomp * plan.npix
+    s_full = torch.empty(n, dtype=torch.float64, device="cuda")
+    a_full = torch.empty(ncomp * plan.nalm, dtype=torch.complex128, device="cuda")
+    wf.wf_set_options(plan, maxiter=240)
+    rep = wf.wf_solve(plan, *args, 1e-30, s_full, a_full, trace_cap=400)  # tol below reach: 240 iterations
+    lam, Ls = rep["lambda_trace"], rep["L_trace"]
+    assert rep["iters"] == len(lam) == 240
+    k = len(lam) // 3
+    wf.wf_set_schedule(plan, lam[:k], Ls[:k])
+    s1 = torch.empty_like(s_full)
+    a1 = torch.empty_like(a_full)
+    wf.wf_solve(plan, *args, 1e-30, s1, a1)
+    wf.wf_set_start(plan, a1)
+    wf.wf_set_schedule(plan, lam[k:], Ls[k:])
+    s2 = torch.empty_like(s_full)
+    rep2 = wf.wf_solve(plan, *args, 1e-30, s2, trace_cap=400)
+    assert rep2["iters"] == len(lam) - k
+    assert rel(s2.cpu().numpy(), s_full.cpu().numpy()) < 1e-12
+    wf.wf_set_start(plan, None)
+    wf.wf_set_schedule(plan, [], [])
+    plan.close()
