@@ -255,6 +255,36 @@ def wf_set_options(plan: Plan, **kw):
     _check(load().wf_set_options(plan.handle, ctypes.byref(o)), "wf_set_options")
 
 
+def solve_record(rep: dict, **meta) -> dict:
+    """One solve's metrics as a JSON-ready dict: iterations, per-iteration time
+    p50 / p99 (ms, when the plan profiled), the (lambda, L) trace, chi^2 / n_dof,
+    the final residual, status and launches; ``meta`` (e.g. the geometry, or
+    an error against a reference) is merged in."""
+    ms = rep.get("iter_ms_trace")
+    rec = {"status": int(rep["status"]), "iters": int(rep["iters"]), "converged": bool(rep["converged"]),
+           "final_residual": float(rep["final_residual"]), "chi2_over_ndof": float(rep["chi2_over_ndof"]),
+           "n_dof": int(rep["n_dof"]), "tau": float(rep["tau"]), "launches": int(rep["launches"]),
+           "refine_sweeps": int(rep["refine_sweeps"]), "mixed_lc": int(rep["mixed_lc"])}
+    if ms is not None and len(ms) and np.all(np.isfinite(ms)) and np.any(ms > 0):
+        rec["iter_ms_p50"] = float(np.percentile(ms, 50))
+        rec["iter_ms_p99"] = float(np.percentile(ms, 99))
+    if rep.get("lambda_trace") is not None:
+        rec["lambda_trace"] = [float(x) for x in rep["lambda_trace"]]
+        rec["L_trace"] = [int(x) for x in rep["L_trace"]]
+    rec.update(meta)
+    return rec
+
+
+def append_jsonl(path: str, rep: dict, **meta) -> dict:
+    """Append solve_record(rep, **meta) to a JSON-lines log; returns the record."""
+    import json
+
+    rec = solve_record(rep, **meta)
+    with open(path, "a") as fh:
+        fh.write(json.dumps(rec) + "\n")
+    return rec
+
+
 def wf_set_start(plan: Plan, alm0=None):
     """Start the next solves on this plan from alm0 (a CUDA complex128 tensor in
     the alm_out layout, kept referenced here) instead of zero; None clears."""

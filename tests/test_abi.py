@@ -36,3 +36,25 @@ def test_strerror_without_gpu():
 
     lib = wf.load()
     assert lib.wf_strerror(wf.WF_EDIVERGE) == b"diverged"
+
+
+def test_solve_records_as_json_lines(tmp_path):
+    """Per-solve metrics log: one JSON object per line with the trace, timing
+    percentiles, chi^2 / n_dof and the caller's fields (no GPU needed)."""
+    import json
+
+    import numpy as np
+
+    import paper_1210_4931_gb300 as wf
+
+    rep = {"status": wf.WF_OK, "iters": 3, "converged": True, "final_residual": 5e-7, "chi2_over_ndof": 0.998,
+           "n_dof": 1200, "tau": 0.01, "launches": 24, "refine_sweeps": 0, "mixed_lc": 0,
+           "iter_ms_trace": np.array([1.0, 2.0, 3.0]), "lambda_trace": np.array([4.0, 1.0, 1.0]),
+           "L_trace": np.array([10, 32, 32], dtype=np.int32)}
+    path = tmp_path / "solves.jsonl"
+    wf.append_jsonl(str(path), rep, nside=16, lmax=32)
+    wf.append_jsonl(str(path), dict(rep, iters=4), nside=16, lmax=32, err_vs_oracle=3e-12)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(lines) == 2 and lines[1]["iters"] == 4 and lines[1]["err_vs_oracle"] == 3e-12
+    assert lines[0]["iter_ms_p50"] == 2.0 and lines[0]["lambda_trace"] == [4.0, 1.0, 1.0]
+    assert lines[0]["L_trace"] == [10, 32, 32] and lines[0]["chi2_over_ndof"] == 0.998
