@@ -8,7 +8,9 @@
 //   legendre analysis   F          -> a_{k+1} (Eq. 4)   (wf_legendre.cu)
 //   reduce              chi^2 (Eq. 6) and the lambda = 1 residual
 // with the cooling schedule of Sect. 3 run on the host between iterations
-// (three FP64 scalars cross the PCIe/C2C link per iteration).
+// (three FP64 scalars cross the PCIe/C2C link per iteration).  Polarised
+// plans (ncomp = 3, Eqs. 10-11) run the same phases with the spin-2
+// transforms and 3x3 blends of wf_spin.cu (FP64) and wf_spin_mx.cu (mixed).
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>

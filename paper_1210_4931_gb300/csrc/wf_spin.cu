@@ -1,5 +1,7 @@
 // Polarisation: the spin-2 half of the basis change for (I, Q, U) maps and the
-// 3x3 blends of the polarised messenger iteration (Eqs. 10-11), FP64.
+// 3x3 blends of the polarised messenger iteration (Eqs. 10-11).  The spin-2
+// Legendre kernels here are FP64: the whole transform of FP64 plans, and the
+// low-l block of mixed plans (whose FP32 kernels are in wf_spin_mx.cu).
 //
 // Convention: sY_lm = slambda_lm(theta) e^{i m phi}, slambda_lm =
 // sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) (s = 0: the Condon-Shortley Y_lm of
