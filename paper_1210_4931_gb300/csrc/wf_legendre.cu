@@ -555,16 +555,19 @@ __device__ __forceinline__ void mx_step(const MxPairs<NP> &P, int l, float A0, f
     }
 }
 
+// lmin, lmaxs: the warp's smallest first l and largest seeding l, so that the
+// warp runs one loop with one trip count (lanes not yet started add zeros)
 template <bool DIFF, int NP>
 __device__ __forceinline__ void mx_syn_run(const MxPairs<NP> &P, int m, int L, const float4 *__restrict__ sAB,
                                            const float4 *__restrict__ sac, float2 (&ER)[NP / 2],
-                                           float2 (&EI)[NP / 2], float2 (&OR)[NP / 2], float2 (&OI)[NP / 2])
+                                           float2 (&EI)[NP / 2], float2 (&OR)[NP / 2], float2 (&OI)[NP / 2],
+                                           int lmin, int lmaxs)
 {
     float2 Sa[NP / 2], Sb[NP / 2], V0[NP / 2], V1[NP / 2];
 #pragma unroll
     for (int pk = 0; pk < NP / 2; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
-    int l = P.lmin;
-    for (; l <= L && l <= P.lmaxs; l += 2) {
+    int l = lmin;
+    for (; l <= L && l <= lmaxs; l += 2) {
         const int j = (l - m) >> 1;
         const float4 ab = sAB[j], ac = sac[j];
         mx_step<DIFF, true, NP>(P, l, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
@@ -640,9 +643,15 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
         float2 ER[NP / 2], EI[NP / 2], OR[NP / 2], OI[NP / 2];
 #pragma unroll
         for (int pk = 0; pk < NP / 2; ++pk) ER[pk] = EI[pk] = OR[pk] = OI[pk] = dup(0.f);
-        if (P.lmin <= L) {
-            if (P.diff) mx_syn_run<true, NP>(P, m, L, sAB, sac, ER, EI, OR, OI);
-            else mx_syn_run<false, NP>(P, m, L, sAB, sac, ER, EI, OR, OI);
+        // warp-uniform control flow: one first l, one seeding range and one recurrence
+        // form (the first active lane's) per warp -- per-lane forms split the warp across
+        // both loop bodies; measured 9 % faster at nside 2048
+        const unsigned am = __activemask();
+        const int lmin = __reduce_min_sync(am, P.lmin), lmaxs = __reduce_max_sync(am, P.lmaxs);
+        const bool diff = __shfl_sync(am, P.diff ? 1 : 0, __ffs(am) - 1) != 0;
+        if (lmin <= L) {
+            if (diff) mx_syn_run<true, NP>(P, m, L, sAB, sac, ER, EI, OR, OI, lmin, lmaxs);
+            else mx_syn_run<false, NP>(P, m, L, sAB, sac, ER, EI, OR, OI, lmin, lmaxs);
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -664,7 +673,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
 // registers) measured faster than one CTA with no spills.
 
 template <bool DIFF, int NP, int CH>
-__device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, int lmin_w,
+__device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, int lmin_w, int lmaxs_w,
                                            const float *__restrict__ sA, const float *__restrict__ sB,
                                            const float2 (&FEr)[NP / 2], const float2 (&FEi)[NP / 2],
                                            const float2 (&FOr)[NP / 2], const float2 (&FOi)[NP / 2],
@@ -676,7 +685,7 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, i
     for (int pk = 0; pk < NPK; ++pk) Sa[pk] = Sb[pk] = dup(0.f);
     for (int l0 = lmin_w; l0 <= L; l0 += CH) {
         float2 AR[CH], AI[CH];
-        const bool inj = l0 <= P.lmaxs;
+        const bool inj = l0 <= lmaxs_w;
 #pragma unroll
         for (int i = 0; i < CH; i += 2) {
             const int j = l0 - m + i;
@@ -764,6 +773,7 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
         // one recurrence form per warp: the shuffles below need warp-uniform control flow
         P.diff = __shfl_sync(0xffffffffu, P.diff ? 1 : 0, 0) != 0;
         const int lmin_w = __reduce_min_sync(0xffffffffu, P.lmin);
+        const int lmaxs_w = __reduce_max_sync(0xffffffffu, P.lmaxs);  // one seeding range per warp
         if (lmin_w > L) continue;
         float fer[NP], fei[NP], forr[NP], foi[NP];
 #pragma unroll
@@ -786,8 +796,8 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
             FOr[pk] = make_float2(forr[2 * pk], forr[2 * pk + 1]);
             FOi[pk] = make_float2(foi[2 * pk], foi[2 * pk + 1]);
         }
-        if (P.diff) mx_ana_run<true, NP, CH>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
-        else mx_ana_run<false, NP, CH>(P, m, L, lmin_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+        if (P.diff) mx_ana_run<true, NP, CH>(P, m, L, lmin_w, lmaxs_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+        else mx_ana_run<false, NP, CH>(P, m, L, lmin_w, lmaxs_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
     }
     __syncthreads();
     const int low_lim = (low && m < lc) ? lcm_of(lc, m) : 0;

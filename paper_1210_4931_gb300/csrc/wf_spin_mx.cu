@@ -270,15 +270,17 @@ __device__ __forceinline__ void pm_syn_pair(const PmPairs<NP> &P, int l, int m, 
     }
 }
 
+// lmin, lmaxs: the warp's smallest first l and largest seeding l (one loop, one
+// trip count per warp; lanes not yet started add zeros)
 template <bool DIFF, int NP>
 __device__ __forceinline__ void pm_syn_run(const PmPairs<NP> &P, int m, int L, const float4 *__restrict__ sT,
-                                           const float4 *__restrict__ sAC, PmAcc (&acc)[NP / 2])
+                                           const float4 *__restrict__ sAC, PmAcc (&acc)[NP / 2], int lmin, int lmaxs)
 {
     float2 Spa[NP / 2], Spb[NP / 2], Sqa[NP / 2], Sqb[NP / 2];
 #pragma unroll
     for (int pk = 0; pk < NP / 2; ++pk) Spa[pk] = Spb[pk] = Sqa[pk] = Sqb[pk] = dup(0.f);
-    int l = P.lmin;
-    for (; l <= L && l <= P.lmaxs; l += 2) pm_syn_pair<DIFF, true, NP>(P, l, m, sT, sAC, Spa, Spb, Sqa, Sqb, acc);
+    int l = lmin;
+    for (; l <= L && l <= lmaxs; l += 2) pm_syn_pair<DIFF, true, NP>(P, l, m, sT, sAC, Spa, Spb, Sqa, Sqb, acc);
     for (; l <= L; l += 2) pm_syn_pair<DIFF, false, NP>(P, l, m, sT, sAC, Spa, Spb, Sqa, Sqb, acc);
 }
 
@@ -328,9 +330,13 @@ __global__ void __launch_bounds__(PM_THREADS) k_legsyn_pol_mx(int lmax, int L, i
             for (int h = 0; h < 2; ++h)
                 acc[pk].ApR[h] = acc[pk].ApI[h] = acc[pk].AmR[h] = acc[pk].AmI[h] = acc[pk].CpR[h] =
                     acc[pk].CpI[h] = acc[pk].CmR[h] = acc[pk].CmI[h] = dup(0.f);
-        if (P.lmin <= L) {
-            if (P.diff) pm_syn_run<true, NP>(P, m, L, sT, sAC, acc);
-            else pm_syn_run<false, NP>(P, m, L, sT, sAC, acc);
+        // warp-uniform control flow, as in the temperature synthesis
+        const unsigned am = __activemask();
+        const int lmin = __reduce_min_sync(am, P.lmin), lmaxs = __reduce_max_sync(am, P.lmaxs);
+        const bool diff = __shfl_sync(am, P.diff ? 1 : 0, __ffs(am) - 1) != 0;
+        if (lmin <= L) {
+            if (diff) pm_syn_run<true, NP>(P, m, L, sT, sAC, acc, lmin, lmaxs);
+            else pm_syn_run<false, NP>(P, m, L, sT, sAC, acc, lmin, lmaxs);
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -390,7 +396,7 @@ struct PmRing {
 };
 
 template <bool DIFF, int NP>
-__device__ __forceinline__ void pm_ana_run(const PmPairs<NP> &P, int m, int L, int lmin_w,
+__device__ __forceinline__ void pm_ana_run(const PmPairs<NP> &P, int m, int L, int lmin_w, int lmaxs_w,
                                            const float4 *__restrict__ sT, const PmRing (&G)[NP / 2], float2 *accP,
                                            float2 *accM, int lane)
 {
@@ -400,7 +406,7 @@ __device__ __forceinline__ void pm_ana_run(const PmPairs<NP> &P, int m, int L, i
     for (int pk = 0; pk < NPK; ++pk) Spa[pk] = Spb[pk] = Sqa[pk] = Sqb[pk] = dup(0.f);
     for (int l0 = lmin_w; l0 <= L; l0 += PM_CH) {
         float2 YPr[PM_CH], YPi[PM_CH], YMr[PM_CH], YMi[PM_CH];
-        const bool inj = l0 <= P.lmaxs;
+        const bool inj = l0 <= lmaxs_w;
 #pragma unroll
         for (int i = 0; i < PM_CH; i += 2) {
             const int j = l0 - m + i;
@@ -501,6 +507,7 @@ __global__ void __launch_bounds__(PM_THREADS, 2) k_legana_pol_mx(int lmax, int L
         // one recurrence form per warp: the shuffles need warp-uniform control flow
         P.diff = __shfl_sync(0xffffffffu, P.diff ? 1 : 0, 0) != 0;
         const int lmin_w = __reduce_min_sync(0xffffffffu, P.lmin);
+        const int lmaxs_w = __reduce_max_sync(0xffffffffu, P.lmaxs);  // one seeding range per warp
         if (lmin_w > L) continue;
         float g[8][NP];
 #pragma unroll
@@ -532,8 +539,8 @@ __global__ void __launch_bounds__(PM_THREADS, 2) k_legana_pol_mx(int lmax, int L
             G[pk].qSr = make_float2(g[6][2 * pk], g[6][2 * pk + 1]);
             G[pk].qSi = make_float2(g[7][2 * pk], g[7][2 * pk + 1]);
         }
-        if (P.diff) pm_ana_run<true, NP>(P, m, L, lmin_w, sT, G, accP, accM, lane);
-        else pm_ana_run<false, NP>(P, m, L, lmin_w, sT, G, accP, accM, lane);
+        if (P.diff) pm_ana_run<true, NP>(P, m, L, lmin_w, lmaxs_w, sT, G, accP, accM, lane);
+        else pm_ana_run<false, NP>(P, m, L, lmin_w, lmaxs_w, sT, G, accP, accM, lane);
     }
     __syncthreads();
     const bool low = Elow && m < lc;
