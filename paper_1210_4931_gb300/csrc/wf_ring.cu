@@ -81,7 +81,10 @@ void host_fft(std::vector<double2> &x)
 // pass reads every element once into registers, waits at a barrier, and
 // writes every element once, so shared memory sees 2 log8(N) round trips
 // instead of 2 log2(N) for radix-2.  sign -1: e^{-2 pi i jk/N}; +1:
-// e^{+2 pi i jk/N} (unnormalised).  tw[t] = e^{-2 pi i t / 2^logNmax}, full circle.
+// e^{+2 pi i jk/N} (unnormalised).  stw[u] = e^{-2 pi i u / 2^logB}, u < 2^logB / 8,
+// a shared-memory copy of the first eighth of the circle for the longest FFT of the
+// plan (2^logB <= 8192 entries, so at most 8 KB in FP32): every radix-8 pass reads
+// its twiddle from there instead of a global table.
 // Supports N <= 8192 with RING_THREADS = 512 threads (two radix-8 butterflies per thread).
 template <typename T>
 __device__ __forceinline__ cx<T> mul_i(cx<T> a, int sign)
@@ -152,12 +155,13 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 inline size_t padded_len(int n) { return (size_t)n + (size_t)n / 16 + 1; }
 
 template <typename T, int R, int LOGR, int BPT>
-__device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *__restrict__ tw,
-                                              int logNmax)
+__device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *stw, int logB)
 {
     const int NR = (1 << logN) >> LOGR;
     const int Ns = 1 << logNs;
-    const int tsh = logNmax - logNs - LOGR;
+    // w1 = e^{-2 pi i k / (R Ns)} = stw[k 2^logB / (R Ns)]; the index stays below 2^logB / 8
+    // since radix 2 and 4 run only as the first pass (Ns = 1, k = 0)
+    const int tsh = logB - logNs - LOGR;
     cx<T> v[BPT][R];
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
@@ -165,8 +169,7 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
         if (j < NR) {
             const int k = j & (Ns - 1);
             // twiddles w^r, r < R, from one table entry w = e^{-+2 pi i k / (R Ns)} by products
-            // (the full table does not stay in L1 next to the large FFT buffers)
-            cx<T> w1 = tw[k << tsh];
+            cx<T> w1 = stw[k << tsh];
             if (sign > 0) w1.y = -w1.y;
             cx<T> wr = w1;
             v[b][0] = x[pidx(j)];
@@ -194,19 +197,19 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
 }
 
 template <typename T>
-__device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *__restrict__ tw, int logNmax)
+__device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *stw, int logB)
 {
     int logNs = 0;
     const int head = logN % 3;
     if (head == 1) {
-        stockham_pass<T, 2, 1, 8>(x, logN, 0, sign, tw, logNmax);
+        stockham_pass<T, 2, 1, 8>(x, logN, 0, sign, stw, logB);
         logNs = 1;
     } else if (head == 2) {
-        stockham_pass<T, 4, 2, 4>(x, logN, 0, sign, tw, logNmax);
+        stockham_pass<T, 4, 2, 4>(x, logN, 0, sign, stw, logB);
         logNs = 2;
     }
     while (logNs < logN) {
-        stockham_pass<T, 8, 3, 2>(x, logN, logNs, sign, tw, logNmax);
+        stockham_pass<T, 8, 3, 2>(x, logN, logNs, sign, stw, logB);
         logNs += 3;
     }
 }
@@ -223,7 +226,7 @@ template <typename T> struct RingOut {
 template <typename T>
 __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout, int sign,
                                const cx<T> *__restrict__ roots, const cx<T> *__restrict__ V,
-                               const cx<T> *__restrict__ tw, int logNmax)
+                               const cx<T> *__restrict__ tw, int logNmax, const cx<T> *stw, int logB)
 {
     const int n = R.n;
     const unsigned twon = 2u * (unsigned)n;
@@ -242,7 +245,7 @@ __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *
         return RingOut<T>{zout, 0};
     }
     if (R.kind == RING_POW2) {
-        fft_pow2<T>(buf, R.logF, sign, tw, logNmax);
+        fft_pow2<T>(buf, R.logF, sign, stw, logB);
         return RingOut<T>{buf, 1};
     }
     // Bluestein, two half-length passes (indices j^2 < 2^26: 32-bit arithmetic)
@@ -263,10 +266,10 @@ __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *
             buf[pidx(j)] = v;
         }
         __syncthreads();
-        fft_pow2<T>(buf, R.logF, -1, tw, logNmax);
+        fft_pow2<T>(buf, R.logF, -1, stw, logB);
         for (int k = threadIdx.x; k < H; k += blockDim.x) buf[pidx(k)] = cmul(buf[pidx(k)], Vh[h * H + k]);
         __syncthreads();
-        fft_pow2<T>(buf, R.logF, +1, tw, logNmax);
+        fft_pow2<T>(buf, R.logF, +1, stw, logB);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             if (h == 0) {
                 zout[k] = buf[pidx(k)];
@@ -302,6 +305,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 
 struct RingCommon {
     int npairs, lmax, L, logNmax;
+    int logB;             // log2 of the longest FFT run (the shared twiddle table covers 2^logB / 8)
     const RingTab *rings;
     const int *order;     // ring pairs by decreasing cost
     int *ticket;          // work counter (zeroed before the launch)
@@ -319,6 +323,40 @@ __device__ __forceinline__ void prefetch_range(const void *base, size_t bytes)
 {
     const char *b = reinterpret_cast<const char *>(base);
     for (size_t off = (size_t)threadIdx.x * 128; off < bytes; off += (size_t)blockDim.x * 128) prefetch_l2(b + off);
+}
+
+__device__ __forceinline__ bool aligned16(const void *p) { return ((size_t)p & 15) == 0; }
+
+// Eq. 3 blend of four pixels (float4 lanes), adding their chi^2 pixel terms to chi
+__device__ __forceinline__ float4 blend4(float4 s, float4 r, float4 nu, float lt, float lm1t, float &chi)
+{
+    auto one = [&](float sv, float rv, float nv) {
+        const float den = 1.f + lm1t * nv;
+        chi += (nv * sv * sv - 2.f * rv * sv) / den;
+        return sv + lt * (rv - nv * sv) / den;
+    };
+    return make_float4(one(s.x, r.x, nu.x), one(s.y, r.y, nu.y), one(s.z, r.z, nu.z), one(s.w, r.w, nu.w));
+}
+
+// Shared twiddle table: stw[u] = tw[u 2^(logNmax - logB)] = e^{-2 pi i u / 2^logB}.
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cx<T> *stw, const cx<T> *__restrict__ tw, const RingCommon &rc)
+{
+    const int n = (1 << rc.logB) >> 3, sh = rc.logNmax - rc.logB;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) stw[u] = tw[(size_t)u << sh];
+}
+
+// The next pair's ring tables into L2: e^{i pi p / n} (fold phases and Bluestein chirps)
+// and, for a Bluestein ring, its filter spectrum (M entries).
+template <typename T>
+__device__ __forceinline__ void prefetch_ring_tables(const RingTab &Rn, const cx<T> *roots, const cx<T> *V)
+{
+    if (Rn.kind == RING_BLUESTEIN) {
+        prefetch_range(roots + Rn.rootOff, (size_t)2 * Rn.n * sizeof(cx<T>));
+        prefetch_range(V + Rn.vOff, ((size_t)2 << Rn.logF) * sizeof(cx<T>));
+    } else if (Rn.q) {
+        prefetch_range(roots + Rn.rootOff, (size_t)2 * Rn.n * sizeof(cx<T>));
+    }
 }
 
 // Work distribution: CTAs take ring pairs from a global counter in order of
@@ -355,6 +393,8 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *zin = rc.zsmem ? buf + rc.bpad : scr + (size_t)blockIdx.x * rc.scr_stride;
     cx<T> *zout = zin + rc.scr_stride / 2;
+    cx<T> *stw = buf + rc.bpad + (rc.zsmem ? rc.scr_stride : 0);
+    load_twiddles<T>(stw, tw, rc);
     const int L = rc.L;
     const T lt = lam * tau, lm1t = (lam - (T)1) * tau;
     int cur = take_ticket(rc.ticket, &s_tick);
@@ -374,6 +414,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             const int pn = rc.order[nxt];
             const RingTab Rn = rc.rings[pn];
             prefetch_range(G + (size_t)pn * (rc.lmax + 1) * 2, (size_t)(L + 1) * 2 * sizeof(cx<T>));
+            prefetch_ring_tables<T>(Rn, roots, V);
             if (mode == RS_BLEND) {
                 prefetch_range(r + Rn.offN, (size_t)Rn.n * sizeof(T));
                 prefetch_range(nu + Rn.offN, (size_t)Rn.n * sizeof(T));
@@ -397,7 +438,31 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
         while (S < 32 && 2 * S * n <= (int)blockDim.x) S *= 2;
         const int sub = threadIdx.x & (S - 1);
         const int nb = blockDim.x / S;
-        for (int base = 0; base < n; base += nb) {
+        // rings longer than L: each bin k has at most one alias of each sign (m = k and
+        // m = n - k), so the bins are independent and four of them are loaded at once
+        const bool single = n > L;
+        if (single) {
+#pragma unroll 4
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                cx<T> hn = mk<T>(0, 0), hs = mk<T>(0, 0);
+                if (k <= L) {
+                    const cx<T> ph = root[q ? k : 0];
+                    hn = cmul(coef(k, 0), ph);
+                    hs = cmul(coef(k, 1), ph);
+                }
+                const int mneg = n - k;
+                if (k > 0 && mneg <= L) {
+                    const cx<T> ph = root[q ? mneg : 0];
+                    hn = cadd(hn, cconj(cmul(coef(mneg, 0), ph)));
+                    hs = cadd(hs, cconj(cmul(coef(mneg, 1), ph)));
+                }
+                if (!south) hs = mk<T>(0, 0);
+                const cx<T> z = mk<T>(hn.x - hs.y, hn.y + hs.x);
+                if (blue) zin[k] = z;
+                else buf[pidx(k)] = z;
+            }
+        }
+        for (int base = 0; base < (single ? 0 : n); base += nb) {
             const int k = base + threadIdx.x / S;
             cx<T> hn = mk<T>(0, 0), hs = mk<T>(0, 0);
             if (k < n) {
@@ -426,9 +491,34 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             }
         }
         __syncthreads();
-        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax, stw, rc.logB);
         T chi_pair = 0;  // per-thread partial of this pair in the working precision
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        int j0 = threadIdx.x, jstep = blockDim.x;
+        if constexpr (sizeof(T) == 4) {
+            // four consecutive pixels per thread with 16-byte loads and stores (ring
+            // lengths and offsets are multiples of 4); the scalar loop below takes over
+            // for unaligned map views
+            if (mode != RS_MAP && aligned16(tmap + R.offN) && (!south || aligned16(tmap + R.offS)) &&
+                (mode != RS_BLEND ||
+                 (aligned16(r + R.offN) && aligned16(nu + R.offN) &&
+                  (!south || (aligned16(r + R.offS) && aligned16(nu + R.offS)))))) {
+                for (int j = 4 * threadIdx.x; j < n; j += 4 * blockDim.x) {
+                    const cx<T> z0 = z[j], z1 = z[j + 1], z2 = z[j + 2], z3 = z[j + 3];
+                    float4 sN = make_float4(z0.x, z1.x, z2.x, z3.x), sS = make_float4(z0.y, z1.y, z2.y, z3.y);
+                    if (mode == RS_BLEND) {
+                        sN = blend4(sN, *reinterpret_cast<const float4 *>(r + R.offN + j),
+                                    *reinterpret_cast<const float4 *>(nu + R.offN + j), lt, lm1t, chi_pair);
+                        if (south)
+                            sS = blend4(sS, *reinterpret_cast<const float4 *>(r + R.offS + j),
+                                        *reinterpret_cast<const float4 *>(nu + R.offS + j), lt, lm1t, chi_pair);
+                    }
+                    *reinterpret_cast<float4 *>(tmap + R.offN + j) = sN;
+                    if (south) *reinterpret_cast<float4 *>(tmap + R.offS + j) = sS;
+                }
+                j0 = n;  // done
+            }
+        }
+        for (int j = j0; j < n; j += jstep) {
             const cx<T> zz = z[j];
             const long long iN = R.offN + j;
             if (mode == RS_MAP) {
@@ -477,6 +567,8 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *zin = rc.zsmem ? buf + rc.bpad : scr + (size_t)blockIdx.x * rc.scr_stride;
     cx<T> *zout = zin + rc.scr_stride / 2;
+    cx<T> *stw = buf + rc.bpad + (rc.zsmem ? rc.scr_stride : 0);
+    load_twiddles<T>(stw, tw, rc);
     const int L = rc.L;
     int cur = take_ticket(rc.ticket, &s_tick);
     while (cur < rc.npairs) {
@@ -492,17 +584,43 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
         const bool south = R.offS >= 0;
         if (nxt < rc.npairs) {
             const RingTab Rn = rc.rings[rc.order[nxt]];
+            prefetch_ring_tables<T>(Rn, roots, V);
             prefetch_range(map + Rn.offN, (size_t)Rn.n * sizeof(T));
             if (Rn.offS >= 0) prefetch_range(map + Rn.offS, (size_t)Rn.n * sizeof(T));
         }
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        int j0 = threadIdx.x;
+        if constexpr (sizeof(T) == 4) {
+            // four consecutive pixels per thread with 16-byte loads (aligned map views)
+            if (aligned16(map + R.offN) && (!south || aligned16(map + R.offS))) {
+                for (int j = 4 * threadIdx.x; j < n; j += 4 * blockDim.x) {
+                    const float4 a = *reinterpret_cast<const float4 *>(map + R.offN + j);
+                    const float4 b = south ? *reinterpret_cast<const float4 *>(map + R.offS + j) : make_float4(0, 0, 0, 0);
+                    cx<T> *d = blue ? zin + j : nullptr;
+                    const cx<T> v0 = mk<T>(a.x, b.x), v1 = mk<T>(a.y, b.y), v2 = mk<T>(a.z, b.z), v3 = mk<T>(a.w, b.w);
+                    if (d) {
+                        d[0] = v0;
+                        d[1] = v1;
+                        d[2] = v2;
+                        d[3] = v3;
+                    } else {
+                        buf[pidx(j)] = v0;
+                        buf[pidx(j + 1)] = v1;
+                        buf[pidx(j + 2)] = v2;
+                        buf[pidx(j + 3)] = v3;
+                    }
+                }
+                j0 = n;
+            }
+        }
+        for (int j = j0; j < n; j += blockDim.x) {
             const cx<T> v = mk<T>(map[R.offN + j], south ? map[R.offS + j] : (T)0);
             if (blue) zin[j] = v;
             else buf[pidx(j)] = v;
         }
         __syncthreads();
-        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw, rc.logB);
         cx<T> *f = F + (size_t)pair * (rc.lmax + 1) * 2;
+#pragma unroll 4
         for (int m = threadIdx.x; m <= L; m += blockDim.x) {
             const int k = m % n;
             const int nk = (n - k) % n;
@@ -533,6 +651,7 @@ template <typename T> struct RingLaunch {
         rc.ticket = t.ticket;
         rc.scr_stride = 2LL * zlen(t);
         rc.bpad = (int)padded_len(t.bmax);
+        rc.logB = ilog2(t.bmax);
         rc.zsmem = zsmem();
         return rc;
     }
@@ -591,7 +710,7 @@ template <typename T> struct RingLaunch {
     static long long zlen(const HpTables &t) { return t.maxBlue > NAIVE_MAX ? t.maxBlue : NAIVE_MAX; }
     static size_t smem_bytes(const HpTables &t)
     {
-        return (padded_len(t.bmax) + (zsmem() ? 2 * (size_t)zlen(t) : 0)) * sizeof(cx<T>);
+        return (padded_len(t.bmax) + (zsmem() ? 2 * (size_t)zlen(t) : 0) + (size_t)t.bmax / 8) * sizeof(cx<T>);
     }
     // The dynamic shared-memory limit is raised once per kernel and size, before
     // any launch that needs it, and never lowered: plans of several sizes may
