@@ -93,6 +93,12 @@ typedef struct {
     double m_sigma;     /* chi^2-bound cooling: initial b = n_dof - m_sigma sigma_chi2 (5) */
     double stall_tol;   /* chi^2-bound cooling: lambda - 1 changing by less than this fraction in one
                            iteration counts as converged at lambda > 1 and raises b (1e-7) */
+    long long mixed_table_bytes; /* mixed precision: device-memory cap of the FP64 block's Legendre table
+                                    (lambda_lm for l < l_c, every ring pair, as double-float pairs; 0 = 2 GiB,
+                                    < 0 = no table).  A block whose table fits is contracted from it on the FP32
+                                    pipe in double-float arithmetic; otherwise the FP64 recurrence kernels run.
+                                    A nonzero mixed_lc in these options, or a changed cap, applies at once, so
+                                    the basis-change calls below use that block too. */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one

@@ -39,7 +39,8 @@ class wf_options(ctypes.Structure):
                 ("ell0", ctypes.c_int), ("ell_step_max", ctypes.c_int), ("band_margin", ctypes.c_int),
                 ("lambda_max", ctypes.c_double), ("refine_sweeps", ctypes.c_int), ("profile", ctypes.c_int),
                 ("mixed_kappa", ctypes.c_double), ("mixed_lc", ctypes.c_int), ("schedule", ctypes.c_int),
-                ("m_sigma", ctypes.c_double), ("stall_tol", ctypes.c_double)]
+                ("m_sigma", ctypes.c_double), ("stall_tol", ctypes.c_double),
+                ("mixed_table_bytes", ctypes.c_longlong)]
 
 
 class wf_info(ctypes.Structure):

@@ -1658,6 +1658,7 @@ long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging
     b += 3 * npix * es;                                          // r, nu, t
     b += std::max(np, 1024LL) * 8 + 4LL * (lmax + 2) * 8 + (lmax + 1) * 32 + 256;
     if (f32) b += np * ((lmax + 1) / 8 + 1) * 2 * 8;             // FP64-block coefficients (stored FP32)
+    if (f32) b += std::min(hp_low_table_bytes(lmax, (int)np, (lmax + 1) / 8 + 1), 2LL << 30) + (lmax + 2) * 8;  // its table
     if (staging) b += npix * (3 * 8 + 1) + (lmax + 1) * 8 + nalm * 16 * 2 + npix * 8;
     if (ncomp == 3) {  // polarisation (PolState)
         const long long lcap = (lmax + 1) / 8 + 1;                  // FP64-block allowance, as above
@@ -1775,7 +1776,17 @@ wf_status wf_set_options(wf_plan p, const wf_options *opt)
     if (!p) return set_error(WF_EINVAL, "null plan");
     if (opt && (opt->schedule < 0 || opt->schedule > 1))
         return set_error(WF_EINVAL, "schedule must be 0 (heuristic) or 1 (chi^2 bound)");
+    const long long old_cap = p->opt.mixed_table_bytes;
     p->opt = opt ? *opt : wf_options{};
+    // mixed temperature tables: a forced block (or a changed table cap) takes effect now
+    if (p->g.kind == WF_GEOM_HEALPIX && p->prec != WF_PREC_FP64) {
+        if (p->opt.mixed_table_bytes != old_cap) p->tab.lc_mx = -1;
+        if (p->opt.mixed_lc != 0 || p->tab.lc_mx < 0) {
+            const int lc = p->opt.mixed_lc > 0 ? std::min(p->opt.mixed_lc, p->lmax + 1) : 0;
+            if (wf_status st = hp_set_low_block(p, lc)) return st;
+            WF_CUDA(cudaStreamSynchronize(p->stream));
+        }
+    }
     return WF_OK;
 }
 

@@ -128,6 +128,12 @@ struct HpTables {
     int *ls_mx = nullptr;
     float *s0_mx = nullptr, *s1_mx = nullptr;
     int lc_mx = 0;         // FP64 block l < lc_mx of the mixed path
+    // the block's Legendre table (double-float pairs, rows of np_pad columns) when it fits the
+    // plan's table budget; low_df = 0 runs the FP64 recurrence kernels instead
+    float2 *lowtab = nullptr;
+    long long lowtab_cap = 0;     // float2 entries allocated
+    long long *lowrow = nullptr;  // first row of each m (lmax + 2 entries)
+    int low_df = 0, np_pad = 0;
     int glow_cap = 0;      // row length of the FP64-block ring coefficients
     int logNmax = 0;       // twiddle table is e^{-2 pi i t / 2^logNmax}, t < 2^logNmax
     int bmax = 0;          // smem FFT buffer length (complex entries)
@@ -229,6 +235,7 @@ struct BlendArgs {
     int want_resid = 0;
 };
 wf_status hp_set_low_block(wf_plan p, int lc);
+long long hp_low_table_bytes(int lmax, int npairs, int lc);
 wf_status hp_autotune(wf_plan p, int reps);
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L);
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old,

@@ -445,6 +445,212 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legana(int lmax, int L, int npa
 }
 
 // ---------------------------------------------------------------------------
+// FP64 block of the mixed path from a table.  The block (m < l_c,
+// m <= l < lcm(l_c, m)) holds few (l, m) but every ring pair, and GB300 runs
+// FP64 at 1/64 of the FP32 rate, so the FP64 recurrence kernels above spend
+// more time on it than the FP32 kernels spend on a far larger share of the
+// band.  Here lambda_lm(x_p) is computed once per l_c by the FP64 recurrence
+// and stored as a pair of FP32 numbers (hi, lo) with hi + lo = lambda to 48
+// significant bits; both directions then stream the table and accumulate in
+// double-float arithmetic on the FP32 pipe: products split exactly with an
+// FMA (Dekker's product) and sums with Knuth's two-sum, so each term carries
+// about 2^-46 relative error against 2^-53 in FP64, far below the FP32
+// operator error the block exists to avoid.
+// Layout: row r = rowoff[m] + (l - m), column p (ring pair), row stride
+// np_pad (npairs rounded up to 32; padding columns hold zeros).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (shi, slo) += (xh + xl)(yh + yl), dropping only the xl yl term (2^-48 relative)
+__device__ __forceinline__ void df_fma(float &shi, float &slo, float xh, float xl, float yh, float yl)
+{
+    const float p = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -p);  // xh yh - p exactly
+    e = __fmaf_rn(xh, yl, e);
+    e = __fmaf_rn(xl, yh, e);
+    float s, t;
+    two_sum(shi, p, s, t);
+    shi = s;
+    slo = __fadd_rn(slo, __fadd_rn(t, e));
+}
+
+// (ahi, alo) += (bhi, blo)
+__device__ __forceinline__ void df_add(float &ahi, float &alo, float bhi, float blo)
+{
+    float s, e;
+    two_sum(ahi, bhi, s, e);
+    ahi = s;
+    alo = __fadd_rn(alo, __fadd_rn(e, blo));
+}
+
+// FP64 value split into (hi, lo) floats
+__device__ __forceinline__ float2 df_split(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+__host__ __device__ inline int low_rows(int lmax, int lc, int m) { return min(lcm_of(lc, m), lmax + 1) - m; }
+
+// one thread per (m, column): the FP64 recurrence from the plan's FP64 seeds
+__global__ void k_lowtab_build(int lmax, int npairs, int np_pad, int lc, const long long *__restrict__ rowoff,
+                               const double *__restrict__ A, const double *__restrict__ c,
+                               const int *__restrict__ ls_tab, const double *__restrict__ s0_tab,
+                               const double *__restrict__ s1_tab, const double *__restrict__ xp,
+                               float2 *__restrict__ tab)
+{
+    const int m = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np_pad) return;
+    const int nr = low_rows(lmax, lc, m);
+    const long long base = mbase(lmax, m);
+    const size_t sidx = (size_t)m * npairs + p;
+    const int ls = (p < npairs) ? ls_tab[sidx] : BIG;
+    const double x = (p < npairs) ? xp[p] : 0.0;
+    float2 *col = tab + (size_t)rowoff[m] * np_pad + p;
+    double mu2 = 0.0, mu1 = 0.0;  // mu_{l-2}, mu_{l-1}
+    for (int i = 0; i < nr; ++i) {
+        const int l = m + i;
+        double mu = 0.0;
+        if (l == ls) mu = s0_tab[sidx];
+        else if (l == ls + 1) mu = s1_tab[sidx];
+        else if (l > ls + 1) mu = A[base + i] * x * mu1 - mu2;
+        mu2 = mu1;
+        mu1 = mu;
+        col[(size_t)i * np_pad] = df_split(c[base + i] * mu);
+    }
+}
+
+// synthesis: G_m(theta_p) = sum over the block's l <= L of a_lm lambda_lm, as even and
+// odd partial sums (north = E + O, south = E - O), rounded to FP32 into the block's
+// [pair][m][hemisphere] layout (row stride gstride)
+__global__ void __launch_bounds__(LEG_THREADS) k_lowsyn_df(int lmax, int L, int npairs, int np_pad, int lc,
+                                                           const long long *__restrict__ rowoff,
+                                                           const float2 *__restrict__ tab,
+                                                           const double2 *__restrict__ alm, float2 *__restrict__ G,
+                                                           int gstride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *sa = reinterpret_cast<float4 *>(smem_raw);  // a_lm as (re hi, re lo, im hi, im lo)
+    const int m = blockIdx.y;
+    const int nr = min(low_rows(lmax, lc, m), L - m + 1);
+    const long long base = mbase(lmax, m);
+    for (int i = threadIdx.x; i < nr + 1; i += blockDim.x) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < nr) {
+            const double2 a = alm[base + i];
+            const float2 re = df_split(a.x), im = df_split(a.y);
+            v = make_float4(re.x, re.y, im.x, im.y);
+        }
+        sa[i] = v;
+    }
+    __syncthreads();
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+        const float2 *col = tab + (size_t)rowoff[m] * np_pad + p;
+        float erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f, orh = 0.f, orl = 0.f, oih = 0.f, oil = 0.f;
+        for (int i = 0; i < nr; i += 2) {  // sa[nr] is zero, so an odd nr needs no tail
+            const float2 t0 = col[(size_t)i * np_pad];
+            const float2 t1 = (i + 1 < nr) ? col[(size_t)(i + 1) * np_pad] : make_float2(0.f, 0.f);
+            const float4 a0 = sa[i], a1 = sa[i + 1];
+            df_fma(erh, erl, t0.x, t0.y, a0.x, a0.y);
+            df_fma(eih, eil, t0.x, t0.y, a0.z, a0.w);
+            df_fma(orh, orl, t1.x, t1.y, a1.x, a1.y);
+            df_fma(oih, oil, t1.x, t1.y, a1.z, a1.w);
+        }
+        float nrh = erh, nrl = erl, nih = eih, nil = eil;  // E + O
+        df_add(nrh, nrl, orh, orl);
+        df_add(nih, nil, oih, oil);
+        float srh = erh, srl = erl, sih = eih, sil = eil;  // E - O
+        df_add(srh, srl, -orh, -orl);
+        df_add(sih, sil, -oih, -oil);
+        float2 *g = G + ((size_t)p * gstride + m) * 2;
+        g[0] = make_float2(nrh + nrl, nih + nil);
+        g[1] = make_float2(srh + srl, sih + sil);
+    }
+}
+
+// analysis: b_lm = sum_p lambda_lm(x_p) (F_N +- F_S)(p) for the block's l <= L (sign
+// + for even l - m).  CTA = (rows of one parity of one m, LOWANA_ROWS at most): it
+// stages F_N +- F_S exactly as double-float for every pair in shared memory, each
+// warp then takes LOWANA_RW rows at a time, lanes over pairs, and reduces across
+// the warp.
+constexpr int LOWANA_ROWS = 32, LOWANA_RW = 4;
+
+__global__ void __launch_bounds__(LEG_THREADS) k_lowana_df(int lmax, int L, int npairs, int np_pad, int lc,
+                                                           const long long *__restrict__ rowoff,
+                                                           const float2 *__restrict__ tab,
+                                                           const float2 *__restrict__ F, double2 *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *sf = reinterpret_cast<float4 *>(smem_raw);  // F_N +- F_S as (re hi, re lo, im hi, im lo)
+    const int m = blockIdx.z, parity = blockIdx.y;
+    const int nr = min(low_rows(lmax, lc, m), L - m + 1);
+    const int npar = (nr - parity + 1) / 2;  // rows i = parity + 2 k, k < npar
+    const int k0 = blockIdx.x * LOWANA_ROWS;
+    if (k0 >= npar) return;
+    const int k1 = min(npar, k0 + LOWANA_ROWS);
+    const size_t pstride = (size_t)(lmax + 1) * 2;
+    const float sg = parity ? -1.f : 1.f;
+#pragma unroll 4
+    for (int p = threadIdx.x; p < np_pad; p += blockDim.x) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < npairs) {
+            const float2 *f = F + (size_t)p * pstride + 2 * (size_t)m;
+            const float2 fn = f[0], fs = f[1];
+            float rh, rl, ih, il;
+            two_sum(fn.x, sg * fs.x, rh, rl);
+            two_sum(fn.y, sg * fs.y, ih, il);
+            v = make_float4(rh, rl, ih, il);
+        }
+        sf[p] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const long long base = mbase(lmax, m);
+    const float2 *rows = tab + (size_t)rowoff[m] * np_pad;
+    // LOWANA_RW rows of this parity per warp and pass: one shared F value feeds all of
+    // them, and the unrolled pair loop keeps several table loads in flight per lane
+    for (int k = k0 + LOWANA_RW * warp; k < k1; k += LOWANA_RW * nwarps) {
+        const float2 *r[LOWANA_RW];
+        float acc[LOWANA_RW][4];
+#pragma unroll
+        for (int q = 0; q < LOWANA_RW; ++q) {
+            const int kq = min(k + q, k1 - 1);  // rows past k1 repeat the last one, unwritten
+            r[q] = rows + (size_t)(parity + 2 * kq) * np_pad;
+            acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+        }
+#pragma unroll 4
+        for (int p = lane; p < np_pad; p += 32) {
+            const float4 f = sf[p];
+#pragma unroll
+            for (int q = 0; q < LOWANA_RW; ++q) {
+                const float2 t = r[q][p];
+                df_fma(acc[q][0], acc[q][1], t.x, t.y, f.x, f.y);
+                df_fma(acc[q][2], acc[q][3], t.x, t.y, f.z, f.w);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < LOWANA_RW; ++q) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                const float a = __shfl_xor_sync(0xffffffffu, acc[q][0], o), b = __shfl_xor_sync(0xffffffffu, acc[q][1], o);
+                const float c = __shfl_xor_sync(0xffffffffu, acc[q][2], o), d = __shfl_xor_sync(0xffffffffu, acc[q][3], o);
+                df_add(acc[q][0], acc[q][1], a, b);
+                df_add(acc[q][2], acc[q][3], c, d);
+            }
+            if (lane == 0 && k + q < k1)
+                out[base + parity + 2 * (k + q)] =
+                    make_double2((double)acc[q][0] + (double)acc[q][1], (double)acc[q][2] + (double)acc[q][3]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // mixed precision: FP32 kernels, four ring pairs per thread in two f32x2
 // packs, plain or difference-form recurrence by ring
 // ---------------------------------------------------------------------------
@@ -873,7 +1079,49 @@ wf_status launch_ana64_low(wf_plan p, int L, int lcut, const float2 *F, double2 
     return WF_OK;
 }
 
+// FP64 block from the double-float table: synthesis into the block's FP32 ring
+// coefficients, analysis into the FP64 output that the FP32 analysis epilogue adds
+wf_status launch_lowsyn_df(wf_plan p, const double2 *alm, int L, cudaStream_t s)
+{
+    const HpTables &t = p->tab;
+    const int lc = t.lc_mx, nm = std::min(L, lc - 1) + 1;
+    if (nm <= 0) return WF_OK;
+    const int gx = (p->npairs + LEG_THREADS - 1) / LEG_THREADS;
+    const size_t sm = (size_t)(std::min(low_rows(p->lmax, lc, 0), L + 1) + 1) * sizeof(float4);
+    k_lowsyn_df<<<dim3(gx, nm), LEG_THREADS, sm, s>>>(p->lmax, L, p->npairs, t.np_pad, lc, t.lowrow, t.lowtab, alm,
+                                                       p->ws.Glow, t.glow_cap);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+wf_status launch_lowana_df(wf_plan p, int L, const float2 *F, double2 *out, cudaStream_t s)
+{
+    const HpTables &t = p->tab;
+    const int lc = t.lc_mx, nm = std::min(L, lc - 1) + 1;
+    if (nm <= 0) return WF_OK;
+    const int rows0 = std::min(low_rows(p->lmax, lc, 0), L + 1);
+    const int gx = ((rows0 + 1) / 2 + LOWANA_ROWS - 1) / LOWANA_ROWS;
+    const size_t sm = (size_t)t.np_pad * sizeof(float4);
+    k_lowana_df<<<dim3(gx, 2, nm), LEG_THREADS, sm, s>>>(p->lmax, L, p->npairs, t.np_pad, lc, t.lowrow, t.lowtab, F,
+                                                          out);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+// Device bytes of the block's table for l_c on this plan
+long long low_table_bytes(int lmax, int npairs, int lc)
+{
+    const long long np_pad = (npairs + 31) & ~31;
+    long long rows = 0;
+    for (int m = 0; m < std::min(lc, lmax + 1); ++m) rows += low_rows(lmax, lc, m);
+    return rows * np_pad * (long long)sizeof(float2);
+}
+
 }  // namespace
+
+long long hp_low_table_bytes(int lmax, int npairs, int lc) { return low_table_bytes(lmax, npairs, lc); }
 
 // ---------------------------------------------------------------------------
 // host: recurrence tables and seeds
@@ -975,6 +1223,10 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
         if ((st = raise_smem_limit((const void *)k_legana<double, float, 16, true>, ana_smem<double, 16>(lmax))) !=
             WF_OK)
             return st;
+        if ((st = raise_smem_limit((const void *)k_lowsyn_df, (size_t)(lmax + 2) * sizeof(float4))) != WF_OK)
+            return st;
+        if ((st = raise_smem_limit((const void *)k_lowana_df, (size_t)((np + 31) & ~31) * sizeof(float4))) != WF_OK)
+            return st;
     } else {
         if ((st = raise_smem_limit((const void *)k_legsyn<double, double>, syn_smem<double>(lmax))) != WF_OK)
             return st;
@@ -1005,6 +1257,30 @@ wf_status hp_set_low_block(wf_plan p, int lc)
         wf_status st = plan_alloc(p, (void **)&p->ws.Glow, (size_t)p->npairs * lc * 2 * sizeof(float2));
         if (st != WF_OK) return st;
         t.glow_cap = lc;
+    }
+    // the block's Legendre table, when it fits the budget (wf_options.mixed_table_bytes)
+    t.low_df = 0;
+    const long long budget = p->opt.mixed_table_bytes == 0 ? (2LL << 30) : p->opt.mixed_table_bytes;
+    const long long bytes = lc > 0 ? low_table_bytes(p->lmax, p->npairs, lc) : 0;
+    if (lc > 0 && bytes <= budget) {
+        wf_status st;
+        const int np_pad = (p->npairs + 31) & ~31, nm = std::min(lc, p->lmax + 1);
+        const long long entries = bytes / (long long)sizeof(float2);
+        if (entries > t.lowtab_cap) {
+            if ((st = plan_alloc(p, (void **)&t.lowtab, (size_t)bytes)) != WF_OK) return st;
+            t.lowtab_cap = entries;
+        }
+        if (!t.lowrow && (st = plan_alloc(p, (void **)&t.lowrow, (size_t)(p->lmax + 2) * sizeof(long long))) != WF_OK)
+            return st;
+        std::vector<long long> off(nm + 1, 0);
+        for (int m = 0; m < nm; ++m) off[m + 1] = off[m] + low_rows(p->lmax, lc, m);
+        if ((st = to_device(p, t.lowrow, off.data(), off.size() * sizeof(long long))) != WF_OK) return st;
+        k_lowtab_build<<<dim3((np_pad + 255) / 256, nm), 256, 0, p->stream>>>(
+            p->lmax, p->npairs, np_pad, lc, t.lowrow, t.A64, t.c64, t.ls, t.s0_64, t.s1_64, t.x64, t.lowtab);
+        WF_COUNT_LAUNCH(p);
+        WF_CUDA(cudaGetLastError());
+        t.np_pad = np_pad;
+        t.low_df = 1;
     }
     t.lc_mx = lc;
     return WF_OK;
@@ -1064,7 +1340,9 @@ wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
     const bool low = t.lc_mx > 0;
     if (low) {
         if ((st = fork_aux(p)) != WF_OK) return st;
-        if ((st = launch_syn64<float>(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux)) != WF_OK) return st;
+        st = t.low_df ? launch_lowsyn_df(p, alm, L, p->aux)
+                      : launch_syn64<float>(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux);
+        if (st != WF_OK) return st;
     }
     switch (p->tile_syn) {
     case 2: st = launch_syn_mx<2>(p, alm, L); break;
@@ -1165,8 +1443,9 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
     if (p->prec == WF_PREC_FP64) return launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out, p->stream);
     const int lc = t.lc_mx;
     if (lc <= 0) return launch_ana_mx(p, L, mode, ba, nullptr, a_old, out);
-    // sequential: the FP64 block measured slower running beside the FP32 kernel
-    wf_status st = launch_ana64_low(p, L, lc, (const float2 *)p->ws.F, p->ws.b_low, p->stream);
+    // sequential: the FP32 epilogue of m < lc reads the block's result
+    wf_status st = t.low_df ? launch_lowana_df(p, L, (const float2 *)p->ws.F, p->ws.b_low, p->stream)
+                            : launch_ana64_low(p, L, lc, (const float2 *)p->ws.F, p->ws.b_low, p->stream);
     if (st != WF_OK) return st;
     return launch_ana_mx(p, L, mode, ba, p->ws.b_low, a_old, out);
 }

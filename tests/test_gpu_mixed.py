@@ -41,6 +41,45 @@ def test_mixed_basis_change_accuracy(wf, nside, lmax):
     plan.close()
 
 
+def _lcm(lc, m):
+    return m + 2 * ((lc - m + 1) // 2)
+
+
+@pytest.mark.parametrize("nside,lmax,lc", [(32, 64, 30), (32, 64, 65), (64, 128, 41)])
+def test_low_block_table_matches_fp64_kernels(wf, nside, lmax, lc):
+    """The FP64 block l < lcm(l_c, m) of the mixed transforms, contracted in
+    double-float from its Legendre table, equals the FP64 recurrence kernels'
+    result on the same ring coefficients to 1e-12 (adjoint; the FP32 remainder
+    of the band is excluded since its shared-memory sums are order-dependent),
+    and the maps agree to the FP32 rounding of the block's ring coefficients.
+    With the whole band in the block (l_c = lmax + 1) both directions are
+    within 2e-6 of the oracle: only the FP32 ring FFTs remain."""
+    import torch
+
+    rng = np.random.default_rng(700 + lc)
+    cl = gen.cmb_like_cl(lmax, 4 * 3438.0 / lmax)
+    a = gen.alm_unit_gaussian(rng, lmax) * np.sqrt(cl[gen.alm_ell(lmax)])
+    f = oracle.synthesis(nside, lmax, lmax, a) + 0.1 * rng.standard_normal(12 * nside * nside)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed")
+    res = {}
+    for kind, cap in (("table", 0), ("fp64", -1)):
+        wf.wf_set_options(plan, mixed_lc=lc, mixed_table_bytes=cap)
+        m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        wf.wf_alm2map(plan, T(a), lmax, m)
+        out = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+        wf.wf_map2alm_adjoint(plan, T(f), lmax, out)
+        res[kind] = (m.cpu().numpy(), out.cpu().numpy())
+    plan.close()
+    block = np.array([l < _lcm(lc, m) for m in range(lmax + 1) for l in range(m, lmax + 1)])
+    assert block.sum() > 0
+    b_tab, b_64 = res["table"][1][block], res["fp64"][1][block]
+    assert rel(b_tab, b_64) < 1e-12, rel(b_tab, b_64)
+    assert rel(res["table"][0], res["fp64"][0]) < 1e-6, rel(res["table"][0], res["fp64"][0])
+    if lc == lmax + 1:
+        assert rel(res["table"][0], oracle.synthesis(nside, lmax, lmax, a)) < 2e-6
+        assert rel(res["table"][1], oracle.adjoint_synthesis(nside, lmax, lmax, f)) < 2e-6
+
+
 def _hard_case(nside, lmax, seed):
     # noise dynamic range 1e4 and a galactic cut: S_l / tau_h reaches ~1e6 at low l
     P = gen.healpix_problem(nside, lmax, seed, fwhm_arcmin=5.0 * 2048 / nside, noise_range=1e4, b_cut_deg=15.0,
