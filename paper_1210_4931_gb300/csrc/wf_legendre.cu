@@ -878,12 +878,26 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
 // cross-lane reduction per (l, m, pair) against four; two CTAs per SM (128
 // registers) measured faster than one CTA with no spills.
 
+// Cross-lane sum of one chunk (CH = 8) through shared memory: lane w stores its
+// (AR.x, AR.y, AI.x, AI.y) for each row i of the chunk; lane (i, q) = (lane / 4,
+// lane % 4) then adds the eight stores of lanes 8q..8q+7 for row i, and two shuffles
+// combine the four quarters.  Per chunk that is 8 stores, 8 loads, 16 packed adds
+// and 4 shuffles per lane against 16 adds, 18 shuffles, 18 adds and 28 selects for
+// the shuffle reduce-scatter.  Slots are XOR-swizzled so that both the stores (8
+// lanes of one q) and the loads (8 lanes over two rows and four q) of each
+// 128-byte phase hit distinct bank groups.
+__device__ __forceinline__ int stage_slot(int i, int w)
+{
+    const int q = w >> 3, j = w & 7;
+    return 32 * i + 8 * q + (j ^ (q + 4 * (i & 1)));
+}
+
 template <bool DIFF, int NP, int CH>
 __device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, int lmin_w, int lmaxs_w,
-                                           const float *__restrict__ sA, const float *__restrict__ sB,
+                                           const float4 *__restrict__ sAB,
                                            const float2 (&FEr)[NP / 2], const float2 (&FEi)[NP / 2],
                                            const float2 (&FOr)[NP / 2], const float2 (&FOi)[NP / 2],
-                                           float2 *acc, int lane)
+                                           float2 *acc, float4 *stage, int lane)
 {
     constexpr int NPK = NP / 2;
     float2 Sa[NPK], Sb[NPK], V0[NPK], V1[NPK];
@@ -894,10 +908,9 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, i
         const bool inj = l0 <= lmaxs_w;
 #pragma unroll
         for (int i = 0; i < CH; i += 2) {
-            const int j = l0 - m + i;
-            const float A0 = sA[j], B0 = sB[j], A1 = sA[j + 1], B1 = sB[j + 1];
-            if (inj) mx_step<DIFF, true, NP>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
-            else mx_step<DIFF, false, NP>(P, l0 + i, A0, B0, A1, B1, Sa, Sb, V0, V1);
+            const float4 ab = sAB[(l0 - m + i) >> 1];  // l0 - m is even
+            if (inj) mx_step<DIFF, true, NP>(P, l0 + i, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
+            else mx_step<DIFF, false, NP>(P, l0 + i, ab.x, ab.y, ab.z, ab.w, Sa, Sb, V0, V1);
             AR[i] = __fmul2_rn(FEr[0], V0[0]);
             AI[i] = __fmul2_rn(FEi[0], V0[0]);
             AR[i + 1] = __fmul2_rn(FOr[0], V1[0]);
@@ -909,20 +922,52 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, i
                 AR[i + 1] = __ffma2_rn(FOr[pk], V1[pk], AR[i + 1]);
                 AI[i + 1] = __ffma2_rn(FOi[pk], V1[pk], AI[i + 1]);
             }
+            if constexpr (CH == 8) {
+                stage[stage_slot(i, lane)] = make_float4(AR[i].x, AR[i].y, AI[i].x, AI[i].y);
+                stage[stage_slot(i + 1, lane)] = make_float4(AR[i + 1].x, AR[i + 1].y, AI[i + 1].x, AI[i + 1].y);
+            }
         }
-        float vr[CH], vi[CH];
+        if constexpr (CH == 8) {
+            __syncwarp();
+            const int i = lane >> 2, q = lane & 3;
+            const float4 *row = stage + 32 * i + 8 * q;
+            const int c = q + 4 * (i & 1);
+            float4 v = row[c];
+            float2 sr = make_float2(v.x, v.y), si = make_float2(v.z, v.w);
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            vr[i] = AR[i].x + AR[i].y;
-            vi[i] = AI[i].x + AI[i].y;
-        }
-        warp_reduce_scatter<float, CH>(vr, vi, lane);
-        constexpr int sh = 5 - Log2<CH>::v;  // each l ends in 2^sh lanes
-        if ((lane & ((1 << sh) - 1)) == 0) {
-            const int l = l0 + (lane >> sh);
-            if (l <= L) {
-                atomicAdd(&acc[l - m].x, vr[0]);
-                atomicAdd(&acc[l - m].y, vi[0]);
+            for (int j = 1; j < 8; ++j) {
+                v = row[j ^ c];
+                sr = __fadd2_rn(sr, make_float2(v.x, v.y));
+                si = __fadd2_rn(si, make_float2(v.z, v.w));
+            }
+            float vr = sr.x + sr.y, vi = si.x + si.y;
+            vr += __shfl_xor_sync(0xffffffffu, vr, 1);
+            vi += __shfl_xor_sync(0xffffffffu, vi, 1);
+            vr += __shfl_xor_sync(0xffffffffu, vr, 2);
+            vi += __shfl_xor_sync(0xffffffffu, vi, 2);
+            if (q == 0) {
+                const int l = l0 + i;
+                if (l <= L) {
+                    atomicAdd(&acc[l - m].x, vr);
+                    atomicAdd(&acc[l - m].y, vi);
+                }
+            }
+            __syncwarp();  // the next chunk rewrites the stage
+        } else {
+            float vr[CH], vi[CH];
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                vr[i] = AR[i].x + AR[i].y;
+                vi[i] = AI[i].x + AI[i].y;
+            }
+            warp_reduce_scatter<float, CH>(vr, vi, lane);
+            constexpr int sh = 5 - Log2<CH>::v;  // each l ends in 2^sh lanes
+            if ((lane & ((1 << sh) - 1)) == 0) {
+                const int l = l0 + (lane >> sh);
+                if (l <= L) {
+                    atomicAdd(&acc[l - m].x, vr[0]);
+                    atomicAdd(&acc[l - m].y, vi[0]);
+                }
             }
         }
     }
@@ -948,16 +993,19 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
     const int nl = L - m + 1;
     const int nlp = nl + CH + 2;
     const long long base = mbase(lmax, m);
-    // FP32 accumulators: each entry sums one 32-lane reduce-scatter result per
-    // group of 128 ring pairs; the epilogue converts to FP64
-    float2 *acc = reinterpret_cast<float2 *>(smem_raw);
-    float *sA = reinterpret_cast<float *>(acc + nlp);
-    float *sB = sA + nlp;
-    for (int i = threadIdx.x; i < nlp; i += blockDim.x) {
-        acc[i] = make_float2(0.f, 0.f);
-        sA[i] = (i < nl) ? A[base + i] : 0.f;
-        sB[i] = (i < nl) ? B[base + i] : 0.f;
+    // (A_l, B_l, A_l+1, B_l+1) per pair of l from l - m = 0; for CH = 8 the per-warp
+    // stages of the cross-lane sum; FP32 accumulators (each entry sums one cross-lane
+    // result per group of ring pairs; the epilogue converts to FP64)
+    const int nab = (nlp + 1) / 2;
+    float4 *sAB = reinterpret_cast<float4 *>(smem_raw);
+    float4 *stage = sAB + nab;
+    float2 *acc = reinterpret_cast<float2 *>(stage + (CH == 8 ? LEG_THREADS * 8 : 0));
+    for (int i = threadIdx.x; i < nab; i += blockDim.x) {
+        const int j = 2 * i;
+        sAB[i] = make_float4(j < nl ? A[base + j] : 0.f, j < nl ? B[base + j] : 0.f,
+                             j + 1 < nl ? A[base + j + 1] : 0.f, j + 1 < nl ? B[base + j + 1] : 0.f);
     }
+    for (int i = threadIdx.x; i < nlp; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
     if (threadIdx.x == 0) next_group = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -1002,8 +1050,9 @@ __global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_mx(int lmax, int L, i
             FOr[pk] = make_float2(forr[2 * pk], forr[2 * pk + 1]);
             FOi[pk] = make_float2(foi[2 * pk], foi[2 * pk + 1]);
         }
-        if (P.diff) mx_ana_run<true, NP, CH>(P, m, L, lmin_w, lmaxs_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
-        else mx_ana_run<false, NP, CH>(P, m, L, lmin_w, lmaxs_w, sA, sB, FEr, FEi, FOr, FOi, acc, lane);
+        float4 *wstage = stage + (threadIdx.x >> 5) * 256;
+        if (P.diff) mx_ana_run<true, NP, CH>(P, m, L, lmin_w, lmaxs_w, sAB, FEr, FEi, FOr, FOi, acc, wstage, lane);
+        else mx_ana_run<false, NP, CH>(P, m, L, lmin_w, lmaxs_w, sAB, FEr, FEi, FOr, FOi, acc, wstage, lane);
     }
     __syncthreads();
     const int low_lim = (low && m < lc) ? lcm_of(lc, m) : 0;
@@ -1020,7 +1069,11 @@ template <typename T, int CH>
 size_t ana_smem(int L) { return (size_t)(L + 1 + CH + 2) * (sizeof(double2) + sizeof(T)) + 16; }
 
 size_t syn_mx_smem(int L) { return (size_t)((L + 2) / 2 + 2) * 2 * sizeof(float4) + 16; }
-size_t ana_mx_smem(int L, int ch) { return (size_t)(L + 1 + ch + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32; }
+size_t ana_mx_smem(int L, int ch)
+{
+    return (size_t)(L + 1 + ch + 2) * (sizeof(float2) + 2 * sizeof(float)) + 32 +
+           (ch == 8 ? (size_t)LEG_THREADS * 8 * sizeof(float4) : 0);
+}
 
 template <typename TG>
 wf_status launch_syn64(wf_plan p, const double2 *alm, int L, int lcut, cx<TG> *G, int gstride, cudaStream_t s)
