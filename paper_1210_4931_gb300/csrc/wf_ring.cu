@@ -81,10 +81,12 @@ void host_fft(std::vector<double2> &x)
 // pass reads every element once into registers, waits at a barrier, and
 // writes every element once, so shared memory sees 2 log8(N) round trips
 // instead of 2 log2(N) for radix-2.  sign -1: e^{-2 pi i jk/N}; +1:
-// e^{+2 pi i jk/N} (unnormalised).  stw[u] = e^{-2 pi i u / 2^logB}, u < 2^logB / 8,
-// a shared-memory copy of the first eighth of the circle for the longest FFT of the
-// plan (2^logB <= 8192 entries, so at most 8 KB in FP32): every radix-8 pass reads
-// its twiddle from there instead of a global table.
+// e^{+2 pi i jk/N} (unnormalised).  Twiddles come from a shared-memory table laid out
+// by pass: stw[Ns + k] = e^{-2 pi i k / (8 Ns)}, k < Ns, for every power of two
+// Ns <= 2^logB / 8 (2^logB / 4 entries: 16 KB in FP32 for the 8192-point rings).
+// A warp of one pass reads consecutive entries (Ns >= 32) or a few broadcast ones;
+// one table of the circle indexed k 2^logB / (8 Ns) put the lanes of the middle
+// passes on one bank.
 // Supports N <= 8192 with RING_THREADS = 512 threads (two radix-8 butterflies per thread).
 template <typename T>
 __device__ __forceinline__ cx<T> mul_i(cx<T> a, int sign)
@@ -155,13 +157,12 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
 inline size_t padded_len(int n) { return (size_t)n + (size_t)n / 16 + 1; }
 
 template <typename T, int R, int LOGR, int BPT>
-__device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *stw, int logB)
+__device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *stw)
 {
     const int NR = (1 << logN) >> LOGR;
     const int Ns = 1 << logNs;
-    // w1 = e^{-2 pi i k / (R Ns)} = stw[k 2^logB / (R Ns)]; the index stays below 2^logB / 8
-    // since radix 2 and 4 run only as the first pass (Ns = 1, k = 0)
-    const int tsh = logB - logNs - LOGR;
+    // w1 = e^{-2 pi i k / (R Ns)} = stw[Ns + k]: radix 2 and 4 run only as the first pass
+    // (Ns = 1, k = 0, w1 = 1), so the table of R = 8 serves every pass
     cx<T> v[BPT][R];
 #pragma unroll
     for (int b = 0; b < BPT; ++b) {
@@ -169,7 +170,7 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
         if (j < NR) {
             const int k = j & (Ns - 1);
             // twiddles w^r, r < R, from one table entry w = e^{-+2 pi i k / (R Ns)} by products
-            cx<T> w1 = stw[k << tsh];
+            cx<T> w1 = stw[Ns + k];
             if (sign > 0) w1.y = -w1.y;
             cx<T> wr = w1;
             v[b][0] = x[pidx(j)];
@@ -197,19 +198,19 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
 }
 
 template <typename T>
-__device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *stw, int logB)
+__device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *stw)
 {
     int logNs = 0;
     const int head = logN % 3;
     if (head == 1) {
-        stockham_pass<T, 2, 1, 8>(x, logN, 0, sign, stw, logB);
+        stockham_pass<T, 2, 1, 8>(x, logN, 0, sign, stw);
         logNs = 1;
     } else if (head == 2) {
-        stockham_pass<T, 4, 2, 4>(x, logN, 0, sign, stw, logB);
+        stockham_pass<T, 4, 2, 4>(x, logN, 0, sign, stw);
         logNs = 2;
     }
     while (logNs < logN) {
-        stockham_pass<T, 8, 3, 2>(x, logN, logNs, sign, stw, logB);
+        stockham_pass<T, 8, 3, 2>(x, logN, logNs, sign, stw);
         logNs += 3;
     }
 }
@@ -226,7 +227,7 @@ template <typename T> struct RingOut {
 template <typename T>
 __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout, int sign,
                                const cx<T> *__restrict__ roots, const cx<T> *__restrict__ V,
-                               const cx<T> *__restrict__ tw, int logNmax, const cx<T> *stw, int logB)
+                               const cx<T> *__restrict__ tw, int logNmax, const cx<T> *stw)
 {
     const int n = R.n;
     const unsigned twon = 2u * (unsigned)n;
@@ -245,7 +246,7 @@ __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *
         return RingOut<T>{zout, 0};
     }
     if (R.kind == RING_POW2) {
-        fft_pow2<T>(buf, R.logF, sign, stw, logB);
+        fft_pow2<T>(buf, R.logF, sign, stw);
         return RingOut<T>{buf, 1};
     }
     // Bluestein, two half-length passes (indices j^2 < 2^26: 32-bit arithmetic)
@@ -266,10 +267,10 @@ __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *
             buf[pidx(j)] = v;
         }
         __syncthreads();
-        fft_pow2<T>(buf, R.logF, -1, stw, logB);
+        fft_pow2<T>(buf, R.logF, -1, stw);
         for (int k = threadIdx.x; k < H; k += blockDim.x) buf[pidx(k)] = cmul(buf[pidx(k)], Vh[h * H + k]);
         __syncthreads();
-        fft_pow2<T>(buf, R.logF, +1, stw, logB);
+        fft_pow2<T>(buf, R.logF, +1, stw);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             if (h == 0) {
                 zout[k] = buf[pidx(k)];
@@ -305,7 +306,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 
 struct RingCommon {
     int npairs, lmax, L, logNmax;
-    int logB;             // log2 of the longest FFT run (the shared twiddle table covers 2^logB / 8)
+    int logB;             // log2 of the longest FFT run (the shared twiddle table has 2^logB / 4 entries)
     const RingTab *rings;
     const int *order;     // ring pairs by decreasing cost
     int *ticket;          // work counter (zeroed before the launch)
@@ -338,12 +339,17 @@ __device__ __forceinline__ float4 blend4(float4 s, float4 r, float4 nu, float lt
     return make_float4(one(s.x, r.x, nu.x), one(s.y, r.y, nu.y), one(s.z, r.z, nu.z), one(s.w, r.w, nu.w));
 }
 
-// Shared twiddle table: stw[u] = tw[u 2^(logNmax - logB)] = e^{-2 pi i u / 2^logB}.
+// Shared twiddle table by pass: stw[Ns + k] = e^{-2 pi i k / (8 Ns)} = tw[k 2^logNmax / (8 Ns)]
+// for the powers of two Ns <= 2^logB / 8 (entry 0 unused).
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cx<T> *stw, const cx<T> *__restrict__ tw, const RingCommon &rc)
 {
-    const int n = (1 << rc.logB) >> 3, sh = rc.logNmax - rc.logB;
-    for (int u = threadIdx.x; u < n; u += blockDim.x) stw[u] = tw[(size_t)u << sh];
+    const int n = (1 << rc.logB) >> 2;
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        if (u == 0) continue;
+        const int logNs = 31 - __clz(u), k = u - (1 << logNs);
+        stw[u] = tw[(size_t)k << (rc.logNmax - 3 - logNs)];
+    }
 }
 
 // The next pair's ring tables into L2: e^{i pi p / n} (fold phases and Bluestein chirps)
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             }
         }
         __syncthreads();
-        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax, stw, rc.logB);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax, stw);
         T chi_pair = 0;  // per-thread partial of this pair in the working precision
         int j0 = threadIdx.x, jstep = blockDim.x;
         if constexpr (sizeof(T) == 4) {
@@ -618,7 +624,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
             else buf[pidx(j)] = v;
         }
         __syncthreads();
-        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw, rc.logB);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw);
         cx<T> *f = F + (size_t)pair * (rc.lmax + 1) * 2;
 #pragma unroll 4
         for (int m = threadIdx.x; m <= L; m += blockDim.x) {
@@ -710,7 +716,7 @@ template <typename T> struct RingLaunch {
     static long long zlen(const HpTables &t) { return t.maxBlue > NAIVE_MAX ? t.maxBlue : NAIVE_MAX; }
     static size_t smem_bytes(const HpTables &t)
     {
-        return (padded_len(t.bmax) + (zsmem() ? 2 * (size_t)zlen(t) : 0) + (size_t)t.bmax / 8) * sizeof(cx<T>);
+        return (padded_len(t.bmax) + (zsmem() ? 2 * (size_t)zlen(t) : 0) + (size_t)t.bmax / 4) * sizeof(cx<T>);
     }
     // The dynamic shared-memory limit is raised once per kernel and size, before
     // any launch that needs it, and never lowered: plans of several sizes may
