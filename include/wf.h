@@ -99,6 +99,11 @@ typedef struct {
                                     pipe in double-float arithmetic; otherwise the FP64 recurrence kernels run.
                                     A nonzero mixed_lc in these options, or a changed cap, applies at once, so
                                     the basis-change calls below use that block too. */
+    int fp64_emulation; /* FP64 temperature plans: nonzero runs the Legendre transforms in double-float
+                           arithmetic on the FP32 pipe (pairs of FP32 numbers, about 48 significant bits;
+                           error-free products and sums), several times faster than the FP64 pipe on GPUs
+                           whose FP64 rate is a small fraction of FP32.  The FP64 correction sweeps of mixed
+                           plans always run this way. */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one

@@ -974,6 +974,9 @@ wf_status hp_end(HpRun &R)
         if (!p->sub) {
             wf_plan sub = nullptr;
             if ((st = wf_plan_create(&p->g, lmax, WF_PREC_FP64, (void *)p->stream, &sub)) != WF_OK) return st;
+            // its Legendre transforms run in double-float on the FP32 pipe (48-bit
+            // significands; FP64 runs at 1/64 of the FP32 rate on this GPU)
+            sub->df_legendre = true;
             p->sub = sub;
         }
         wf_plan sub = p->sub;
@@ -1778,6 +1781,8 @@ wf_status wf_set_options(wf_plan p, const wf_options *opt)
         return set_error(WF_EINVAL, "schedule must be 0 (heuristic) or 1 (chi^2 bound)");
     const long long old_cap = p->opt.mixed_table_bytes;
     p->opt = opt ? *opt : wf_options{};
+    if (p->g.kind == WF_GEOM_HEALPIX && p->prec == WF_PREC_FP64 && p->g.ncomp == 1)
+        p->df_legendre = p->opt.fp64_emulation != 0;
     // mixed temperature tables: a forced block (or a changed table cap) takes effect now
     if (p->g.kind == WF_GEOM_HEALPIX && p->prec != WF_PREC_FP64) {
         if (p->opt.mixed_table_bytes != old_cap) p->tab.lc_mx = -1;

@@ -167,6 +167,7 @@ struct wf_plan_s {
     std::vector<void *> allocations;
     cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
     wf_plan sub = nullptr;    // mixed precision: FP64 plan of the same geometry for the correction sweeps
+    bool df_legendre = false; // FP64 plan whose Legendre transforms run in double-float (the sweeps' sub-plan)
     bool events_ready = false;
     int tile_syn = 4, tile_ana = 8;  // mixed Legendre tiles: ring pairs per thread / per lane
     cudaStream_t aux = nullptr;      // mixed precision: stream of the FP64 low-l block

@@ -651,6 +651,269 @@ __global__ void __launch_bounds__(LEG_THREADS) k_lowana_df(int lmax, int L, int 
 }
 
 // ---------------------------------------------------------------------------
+// Double-float transforms for the FP64 correction sweeps of mixed plans.  The
+// sweeps' FP64 plan ran these transforms at the FP64 rate (1/64 of FP32 on
+// GB300): three FP64 synthesis/analysis pairs per solve cost about a tenth of
+// a 1000-iteration benchmark solve.  Here the recurrence, the seeds, x, A and
+// c a_lm are (hi, lo) float pairs and every product and sum is an error-free
+// FP32 transformation (Dekker's product via FMA, Knuth's two-sum): about 48
+// significant bits, against the 24 of the mixed kernels that the sweeps
+// correct.  Near the poles the plain recurrence loses ~log2(1/sin theta) bits
+// in any precision (12 at nside 2048), so the sweeps stay ~10 digits accurate.
+// ---------------------------------------------------------------------------
+// Cross-lane sum of one chunk (CH = 8) through shared memory: lane w stores its
+// (AR.x, AR.y, AI.x, AI.y) for each row i of the chunk; lane (i, q) = (lane / 4,
+// lane % 4) then adds the eight stores of lanes 8q..8q+7 for row i, and two shuffles
+// combine the four quarters.  Per chunk that is 8 stores, 8 loads, 16 packed adds
+// and 4 shuffles per lane against 16 adds, 18 shuffles, 18 adds and 28 selects for
+// the shuffle reduce-scatter.  Slots are XOR-swizzled so that both the stores (8
+// lanes of one q) and the loads (8 lanes over two rows and four q) of each
+// 128-byte phase hit distinct bank groups.
+__device__ __forceinline__ int stage_slot(int i, int w)
+{
+    const int q = w >> 3, j = w & 7;
+    return 32 * i + 8 * q + (j ^ (q + 4 * (i & 1)));
+}
+
+// (ph, pl) ~ (ah + al)(bh + bl), unnormalised (|pl| ~ 2^-23 |ph|)
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl)
+{
+    ph = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -ph);
+    e = __fmaf_rn(ah, bl, e);
+    pl = __fmaf_rn(al, bh, e);
+}
+
+// (sh, sl) = (ah + al) - (bh + bl), normalised
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    e = __fadd_rn(e, __fsub_rn(al, bl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+
+// one recurrence step mu_l = A_l x mu_{l-1} - mu_{l-2} in double-float
+__device__ __forceinline__ void df_step(float2 Al, float xh, float xl, float m1h, float m1l, float &m0h, float &m0l)
+{
+    float th, tl, uh, ul;
+    df_mul(Al.x, Al.y, xh, xl, th, tl);
+    df_mul(th, tl, m1h, m1l, uh, ul);
+    df_sub(uh, ul, m0h, m0l, m0h, m0l);
+}
+
+__device__ __forceinline__ double df_val(float h, float l) { return (double)h + (double)l; }
+
+// synthesis: CTA per (m, block of pairs), thread per pair, as the FP64 kernel
+__global__ void __launch_bounds__(LEG_THREADS) k_legsyn_df(int lmax, int L, int npairs,
+                                                           const double2 *__restrict__ alm, const double *__restrict__ A,
+                                                           const double *__restrict__ c64,
+                                                           const int *__restrict__ ls_tab,
+                                                           const double *__restrict__ s0_tab,
+                                                           const double *__restrict__ s1_tab,
+                                                           const double *__restrict__ xp, double2 *__restrict__ G)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int m = blockIdx.y;
+    const int nl = L - m + 1;
+    const long long base = mbase(lmax, m);
+    float4 *sac = reinterpret_cast<float4 *>(smem_raw);  // c a_lm as (re hi, re lo, im hi, im lo)
+    float2 *sA = reinterpret_cast<float2 *>(sac + (nl + 2));
+    for (int i = threadIdx.x; i < nl + 2; i += blockDim.x) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 a = make_float2(0.f, 0.f);
+        if (i < nl) {
+            const double2 q = alm[base + i];
+            const double cc = c64[base + i];
+            const float2 re = df_split(q.x * cc), im = df_split(q.y * cc);
+            v = make_float4(re.x, re.y, im.x, im.y);
+            a = df_split(A[base + i]);
+        }
+        sac[i] = v;
+        sA[i] = a;
+    }
+    __syncthreads();
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+        const size_t sidx = (size_t)m * npairs + p;
+        const int ls = ls_tab[sidx];
+        float erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f, orh = 0.f, orl = 0.f, oih = 0.f, oil = 0.f;
+        if (ls <= L) {
+            const float2 x = df_split(xp[p]), s0 = df_split(s0_tab[sidx]), s1 = df_split(s1_tab[sidx]);
+            float m0h = s0.x, m0l = s0.y, m1h = s1.x, m1l = s1.y;
+            int i = ls - m;
+            float4 a0 = sac[i], a1 = sac[i + 1];
+            df_fma(erh, erl, a0.x, a0.y, m0h, m0l);
+            df_fma(eih, eil, a0.z, a0.w, m0h, m0l);
+            df_fma(orh, orl, a1.x, a1.y, m1h, m1l);
+            df_fma(oih, oil, a1.z, a1.w, m1h, m1l);
+            for (i += 2; i < nl; i += 2) {
+                df_step(sA[i], x.x, x.y, m1h, m1l, m0h, m0l);
+                a0 = sac[i];
+                df_fma(erh, erl, a0.x, a0.y, m0h, m0l);
+                df_fma(eih, eil, a0.z, a0.w, m0h, m0l);
+                df_step(sA[i + 1], x.x, x.y, m0h, m0l, m1h, m1l);
+                a1 = sac[i + 1];
+                df_fma(orh, orl, a1.x, a1.y, m1h, m1l);
+                df_fma(oih, oil, a1.z, a1.w, m1h, m1l);
+            }
+        }
+        const double er = df_val(erh, erl), ei = df_val(eih, eil), orr = df_val(orh, orl), oi = df_val(oih, oil);
+        double2 *g = G + ((size_t)p * (lmax + 1) + m) * 2;
+        g[0] = make_double2(er + orr, ei + oi);
+        g[1] = make_double2(er - orr, ei - oi);
+    }
+}
+
+// analysis: CTA per m; a warp covers 32 lanes x DFP ring pairs taken dynamically,
+// equator first; chunks of 8 values of l are summed over the lane's pairs in
+// double-float, across the warp through a swizzled shared stage (as in the mixed
+// analysis, with (hi, lo) of the real and imaginary parts per slot and double-float
+// additions), and added into FP64 shared accumulators.
+constexpr int DFP = 4;
+
+template <bool INJ>
+__device__ __forceinline__ void df_ana_pair_step(int l, const int (&ls)[DFP], const float2 (&s0)[DFP],
+                                                 const float2 (&s1)[DFP], const float2 (&x)[DFP], float2 A0, float2 A1,
+                                                 float2 (&m0)[DFP], float2 (&m1)[DFP])
+{
+#pragma unroll
+    for (int k = 0; k < DFP; ++k) {
+        df_step(A0, x[k].x, x[k].y, m1[k].x, m1[k].y, m0[k].x, m0[k].y);
+        df_step(A1, x[k].x, x[k].y, m0[k].x, m0[k].y, m1[k].x, m1[k].y);
+        if (INJ && l == ls[k]) {
+            m0[k] = s0[k];
+            m1[k] = s1[k];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(LEG_THREADS, 2) k_legana_df(int lmax, int L, int npairs,
+                                                           const double2 *__restrict__ F, const double *__restrict__ A,
+                                                           const int *__restrict__ ls_tab,
+                                                           const double *__restrict__ s0_tab,
+                                                           const double *__restrict__ s1_tab,
+                                                           const double *__restrict__ xp,
+                                                           const double *__restrict__ c64, int mode, double omega,
+                                                           BlendArgs ba, const double2 *__restrict__ a_old,
+                                                           double2 *__restrict__ out, double *__restrict__ part)
+{
+    constexpr int CH = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[4][LEG_THREADS / 32];
+    __shared__ int next_group;
+    const int m = blockIdx.x;
+    const int nl = L - m + 1;
+    const int nlp = nl + CH + 2;
+    const long long base = mbase(lmax, m);
+    double2 *acc = reinterpret_cast<double2 *>(smem_raw);
+    float4 *sAA = reinterpret_cast<float4 *>(acc + nlp);   // (A_l hi, lo, A_l+1 hi, lo) from l - m = 0, even
+    float4 *stage = sAA + (nlp + 1) / 2;                      // per warp: 8 rows x 32 lanes of (re hi, lo, im hi, lo)
+    for (int i = threadIdx.x; i < nlp; i += blockDim.x) acc[i] = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < (nlp + 1) / 2; i += blockDim.x) {
+        const int j = 2 * i;
+        const float2 a0 = j < nl ? df_split(A[base + j]) : make_float2(0.f, 0.f);
+        const float2 a1 = j + 1 < nl ? df_split(A[base + j + 1]) : make_float2(0.f, 0.f);
+        sAA[i] = make_float4(a0.x, a0.y, a1.x, a1.y);
+    }
+    if (threadIdx.x == 0) next_group = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    float4 *wst = stage + (threadIdx.x >> 5) * 256;
+    const int per_group = 32 * DFP;
+    const int ngroups = (npairs + per_group - 1) / per_group;
+    const size_t pstride = (size_t)(lmax + 1) * 2;
+    for (;;) {
+        int grp = 0;
+        if (lane == 0) grp = atomicAdd(&next_group, 1);
+        grp = __shfl_sync(0xffffffffu, grp, 0);
+        if (grp >= ngroups) break;
+        const int p0 = (ngroups - 1 - grp) * per_group + lane * DFP;
+        int ls[DFP];
+        float2 s0[DFP], s1[DFP], x[DFP], m0[DFP], m1[DFP], fer[DFP], fei[DFP], forr[DFP], foi[DFP];
+        int lmin = BIG, lmaxs = -1;
+#pragma unroll
+        for (int k = 0; k < DFP; ++k) {
+            const int p = p0 + k;
+            ls[k] = BIG;
+            s0[k] = s1[k] = x[k] = m0[k] = m1[k] = make_float2(0.f, 0.f);
+            fer[k] = fei[k] = forr[k] = foi[k] = make_float2(0.f, 0.f);
+            if (p < npairs) {
+                const size_t sidx = (size_t)m * npairs + p;
+                const int l0 = ls_tab[sidx];
+                if (l0 <= L) {
+                    ls[k] = l0;
+                    s0[k] = df_split(s0_tab[sidx]);
+                    s1[k] = df_split(s1_tab[sidx]);
+                    x[k] = df_split(xp[p]);
+                    const double2 *f = F + (size_t)p * pstride + 2 * (size_t)m;
+                    const double2 fn = f[0], fs = f[1];
+                    fer[k] = df_split(fn.x + fs.x);
+                    fei[k] = df_split(fn.y + fs.y);
+                    forr[k] = df_split(fn.x - fs.x);
+                    foi[k] = df_split(fn.y - fs.y);
+                    lmin = min(lmin, l0);
+                    lmaxs = max(lmaxs, l0);
+                }
+            }
+        }
+        const int lmin_w = __reduce_min_sync(0xffffffffu, lmin);
+        const int lmaxs_w = __reduce_max_sync(0xffffffffu, lmaxs);
+        if (lmin_w > L) continue;
+        for (int l0 = lmin_w; l0 <= L; l0 += CH) {
+            const bool inj = l0 <= lmaxs_w;
+#pragma unroll
+            for (int i = 0; i < CH; i += 2) {
+                const float4 aa = sAA[(l0 - m + i) >> 1];  // l0 - m is even
+                if (inj) df_ana_pair_step<true>(l0 + i, ls, s0, s1, x, make_float2(aa.x, aa.y), make_float2(aa.z, aa.w), m0, m1);
+                else df_ana_pair_step<false>(l0 + i, ls, s0, s1, x, make_float2(aa.x, aa.y), make_float2(aa.z, aa.w), m0, m1);
+                float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
+#pragma unroll
+                for (int k = 0; k < DFP; ++k) {
+                    df_fma(r0h, r0l, fer[k].x, fer[k].y, m0[k].x, m0[k].y);
+                    df_fma(i0h, i0l, fei[k].x, fei[k].y, m0[k].x, m0[k].y);
+                    df_fma(r1h, r1l, forr[k].x, forr[k].y, m1[k].x, m1[k].y);
+                    df_fma(i1h, i1l, foi[k].x, foi[k].y, m1[k].x, m1[k].y);
+                }
+                wst[stage_slot(i, lane)] = make_float4(r0h, r0l, i0h, i0l);
+                wst[stage_slot(i + 1, lane)] = make_float4(r1h, r1l, i1h, i1l);
+            }
+            __syncwarp();
+            {
+                const int i = lane >> 2, q = lane & 3;
+                const float4 *row = wst + 32 * i + 8 * q;
+                const int c = q + 4 * (i & 1);
+                float4 v = row[c];
+                float rh = v.x, rl = v.y, ih = v.z, il = v.w;
+#pragma unroll
+                for (int j = 1; j < 8; ++j) {
+                    v = row[j ^ c];
+                    df_add(rh, rl, v.x, v.y);
+                    df_add(ih, il, v.z, v.w);
+                }
+#pragma unroll
+                for (int o = 1; o <= 2; o <<= 1) {
+                    const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
+                    const float cc = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
+                    df_add(rh, rl, a, b);
+                    df_add(ih, il, cc, d);
+                }
+                if (q == 0) {
+                    const int l = l0 + i;
+                    if (l <= L) {
+                        atomicAdd(&acc[l - m].x, df_val(rh, rl));
+                        atomicAdd(&acc[l - m].y, df_val(ih, il));
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    blend_epilogue(lmax, L, m, base, mode, omega, ba, c64, acc, nullptr, 0, a_old, out, part, red);
+}
+
+// ---------------------------------------------------------------------------
 // mixed precision: FP32 kernels, four ring pairs per thread in two f32x2
 // packs, plain or difference-form recurrence by ring
 // ---------------------------------------------------------------------------
@@ -878,19 +1141,6 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
 // cross-lane reduction per (l, m, pair) against four; two CTAs per SM (128
 // registers) measured faster than one CTA with no spills.
 
-// Cross-lane sum of one chunk (CH = 8) through shared memory: lane w stores its
-// (AR.x, AR.y, AI.x, AI.y) for each row i of the chunk; lane (i, q) = (lane / 4,
-// lane % 4) then adds the eight stores of lanes 8q..8q+7 for row i, and two shuffles
-// combine the four quarters.  Per chunk that is 8 stores, 8 loads, 16 packed adds
-// and 4 shuffles per lane against 16 adds, 18 shuffles, 18 adds and 28 selects for
-// the shuffle reduce-scatter.  Slots are XOR-swizzled so that both the stores (8
-// lanes of one q) and the loads (8 lanes over two rows and four q) of each
-// 128-byte phase hit distinct bank groups.
-__device__ __forceinline__ int stage_slot(int i, int w)
-{
-    const int q = w >> 3, j = w & 7;
-    return 32 * i + 8 * q + (j ^ (q + 4 * (i & 1)));
-}
 
 template <bool DIFF, int NP, int CH>
 __device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, int lmin_w, int lmaxs_w,
@@ -1163,6 +1413,38 @@ wf_status launch_lowana_df(wf_plan p, int L, const float2 *F, double2 *out, cuda
     return WF_OK;
 }
 
+// double-float transforms of a sweep sub-plan (FP64 plan, G and F in FP64)
+size_t syn_df_smem(int L) { return (size_t)(L + 3) * (sizeof(float4) + sizeof(float2)) + 16; }
+size_t ana_df_smem(int L)
+{
+    const size_t nlp = (size_t)L + 1 + 8 + 2;
+    return nlp * sizeof(double2) + ((nlp + 1) / 2) * sizeof(float4) + (size_t)LEG_THREADS * 8 * sizeof(float4) + 32;
+}
+
+wf_status launch_syn_df(wf_plan p, const double2 *alm, int L)
+{
+    const HpTables &t = p->tab;
+    const int gx = (p->npairs + 4 * LEG_THREADS - 1) / (4 * LEG_THREADS);
+    const size_t sm = syn_df_smem(L);
+    k_legsyn_df<<<dim3(gx, L + 1), LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, alm, t.A64, t.c64, t.ls, t.s0_64,
+                                                                 t.s1_64, t.x64, (double2 *)p->ws.G);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+wf_status launch_ana_df(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old, double2 *out)
+{
+    const HpTables &t = p->tab;
+    const size_t sm = ana_df_smem(L);
+    k_legana_df<<<L + 1, LEG_THREADS, sm, p->stream>>>(p->lmax, L, p->npairs, (const double2 *)p->ws.F, t.A64, t.ls,
+                                                       t.s0_64, t.s1_64, t.x64, t.c64, (int)mode, p->omega, ba, a_old,
+                                                       out, p->ws.part_harm);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
 // Device bytes of the block's table for l_c on this plan
 long long low_table_bytes(int lmax, int npairs, int lc)
 {
@@ -1281,6 +1563,8 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
         if ((st = raise_smem_limit((const void *)k_lowana_df, (size_t)((np + 31) & ~31) * sizeof(float4))) != WF_OK)
             return st;
     } else {
+        if ((st = raise_smem_limit((const void *)k_legsyn_df, syn_df_smem(lmax))) != WF_OK) return st;
+        if ((st = raise_smem_limit((const void *)k_legana_df, ana_df_smem(lmax))) != WF_OK) return st;
         if ((st = raise_smem_limit((const void *)k_legsyn<double, double>, syn_smem<double>(lmax))) != WF_OK)
             return st;
         if ((st = raise_smem_limit((const void *)k_legana<double, double, 16, false>, ana_smem<double, 16>(lmax))) !=
@@ -1388,7 +1672,9 @@ wf_status launch_syn_mx(wf_plan p, const double2 *alm, int L)
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
 {
     const HpTables &t = p->tab;
-    if (p->prec == WF_PREC_FP64) return launch_syn64<double>(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1, p->stream);
+    if (p->prec == WF_PREC_FP64)
+        return p->df_legendre ? launch_syn_df(p, alm, L)
+                              : launch_syn64<double>(p, alm, L, 0, (double2 *)p->ws.G, p->lmax + 1, p->stream);
     wf_status st;
     const bool low = t.lc_mx > 0;
     if (low) {
@@ -1493,7 +1779,9 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
         WF_CUDA(cudaGetLastError());
         ba.epi = p->ws.epi;
     }
-    if (p->prec == WF_PREC_FP64) return launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out, p->stream);
+    if (p->prec == WF_PREC_FP64)
+        return p->df_legendre ? launch_ana_df(p, L, mode, ba, a_old, out)
+                              : launch_ana64<double>(p, L, 0, p->ws.F, mode, ba, a_old, out, p->stream);
     const int lc = t.lc_mx;
     if (lc <= 0) return launch_ana_mx(p, L, mode, ba, nullptr, a_old, out);
     // sequential: the FP32 epilogue of m < lc reads the block's result
