@@ -739,19 +739,22 @@ wf_status hp_begin(HpRun &R)
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
     }
-    // |b| = |Y^T r| over modes with S > 0
-    if ((st = hp_adjoint_T(p, p->ws.r, lmax, p->ws.b)) != WF_OK) return st;
-    k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, R.C_ell, p->ws.b, 0, p->ws.part_harm);
-    WF_COUNT_LAUNCH(p);
-    WF_CUDA(cudaGetLastError());
-    {
+    // |b| = |Y^T r| over modes with S > 0 (correction sweeps reuse their parent solve's,
+    // which differs from this plan's only by the parent's transform rounding)
+    if (p->bnorm_given > 0) {
+        R.bnorm = p->bnorm_given;
+    } else {
+        if ((st = hp_adjoint_T(p, p->ws.r, lmax, p->ws.b)) != WF_OK) return st;
+        k_alm_norm<<<lmax + 1, 256, 0, p->stream>>>(lmax, R.C_ell, p->ws.b, 0, p->ws.part_harm);
+        WF_COUNT_LAUNCH(p);
+        WF_CUDA(cudaGetLastError());
         SumSpec sp{};
         sp.in[0] = p->ws.part_harm;
         sp.n[0] = lmax + 1;
         sp.stride[0] = 1;
         if ((st = sums(p, sp, 1, &R.pr)) != WF_OK) return st;
+        R.bnorm = std::sqrt(p->ws.h_scal[0]);
     }
-    R.bnorm = std::sqrt(p->ws.h_scal[0]);
     if (!(R.bnorm > 0)) return set_error(WF_EINVAL, "the source has no component on modes with S > 0");
 
     sch.tau_h = tau_h;
@@ -854,15 +857,19 @@ wf_status hp_launch(HpRun &R)
         pr.begin(WF_K_LEG_SYN);
         if ((st = hp_legendre_synthesis(p, p->ws.a, R.L)) != WF_OK) return st;
         pr.end();
+        // one ring kernel: fold, inverse DFT, Eq. 3 and the forward DFT of t, which never
+        // leaves shared memory (its time is reported under the ring synthesis)
         pr.begin(WF_K_RING_SYN);
-        if ((st = hp_ring_synthesis(p, R.L, RS_BLEND, R.lam, tau, nullptr)) != WF_OK) return st;
+        if ((st = hp_ring_synthesis_analysis(p, R.L, R.lam, tau)) != WF_OK) return st;
         pr.end();
     }
     const int L = R.L;
     const bool full = (R.lam == 1.0 && L == R.lmax);
-    pr.begin(WF_K_RING_ANA);
-    if ((st = hp_ring_analysis(p, L, p->ws.t)) != WF_OK) return st;
-    pr.end();
+    if (R.rigorous) {
+        pr.begin(WF_K_RING_ANA);
+        if ((st = hp_ring_analysis(p, L, p->ws.t)) != WF_OK) return st;
+        pr.end();
+    }
     BlendArgs ba;
     ba.lam_tauh = R.lam * R.tau_h;
     ba.tauh = R.tau_h;
@@ -996,7 +1003,9 @@ wf_status hp_end(HpRun &R)
         si.resid_trace = tr.data();
         si.iter_ms_trace = tm.data();
         si.trace_cap = o.refine_sweeps;
+        sub->bnorm_given = R.bnorm;
         st = hp_solve(sub, R.d, R.nv, R.mask, R.C_ell, R.tol, R.fluct, R.g1, R.g2, R.s_out, R.alm_out, &si, p->ws.a);
+        sub->bnorm_given = 0;
         if (st != WF_OK) return st;
         for (int i = 0; i < si.iters; ++i) record(R.info, R.k + i, tl[i], tL[i], tc[i], tr[i], tm[i]);
         for (int f = 0; f < WF_NK; ++f) {

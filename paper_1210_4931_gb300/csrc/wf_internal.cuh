@@ -168,6 +168,7 @@ struct wf_plan_s {
     cudaEvent_t ev[34] = {};  // profiling events: [0..31] kernel pairs, [32..33] iteration
     wf_plan sub = nullptr;    // mixed precision: FP64 plan of the same geometry for the correction sweeps
     bool df_legendre = false; // FP64 plan whose Legendre transforms run in double-float (the sweeps' sub-plan)
+    double bnorm_given = 0;   // > 0: the next solve's residual norm |Y^T r| (the sweeps take their parent's)
     bool events_ready = false;
     int tile_syn = 4, tile_ana = 8;  // mixed Legendre tiles: ring pairs per thread / per lane
     cudaStream_t aux = nullptr;      // mixed precision: stream of the FP64 low-l block
@@ -244,7 +245,8 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
 
 // ring transforms (wf_ring.cu)
 wf_status hp_build_ring_tables(wf_plan p);
-enum RingSynMode { RS_BLEND = 0, RS_MAP = 1, RS_SYN = 2 };
+// RS_BLEND_ANA: the blended ring goes straight into the forward DFT and the unfold to F
+enum RingSynMode { RS_BLEND = 0, RS_MAP = 1, RS_SYN = 2, RS_BLEND_ANA = 3 };
 wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, double tau, double *out_map);
 wf_status hp_ring_analysis(wf_plan p, int L, const void *map_T);
 // the same passes on explicit buffers (G / F in the working precision, maps T-typed or FP64 out)
@@ -252,6 +254,7 @@ wf_status hp_ring_synthesis_buf(wf_plan p, int L, RingSynMode mode, double lam, 
                                 void *tmap, double *out_map);
 wf_status hp_ring_analysis_buf(wf_plan p, int L, const void *map_T, void *F);
 // mixed plans: the FP32 synthesis pass with an explicit FP64-block buffer (m < lc)
+wf_status hp_ring_synthesis_analysis(wf_plan p, int L, double lam, double tau);
 wf_status hp_ring_synthesis_buf_low(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
                                     const float2 *glow, int lc, int glow_stride, void *tmap, double *out_map);
 // FP64 temperature Legendre transforms on explicit buffers (FP64 plans)

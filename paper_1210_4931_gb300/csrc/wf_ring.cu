@@ -377,6 +377,28 @@ __device__ __forceinline__ int take_ticket(int *ticket, int *s_tick)
     return t;
 }
 
+// Unfold a forward ring DFT of the packed pair (z = f_N + i f_S) to
+// F_m = e^{-i pi m q / n} DFT(f)[m mod n] for both rings, m <= L; ends with a barrier.
+template <typename T>
+__device__ __forceinline__ void unfold_ring(const RingTab &R, const RingOut<T> &z, const cx<T> *__restrict__ root, int q,
+                                            unsigned twon, bool south, cx<T> *__restrict__ f, int L)
+{
+    const int n = R.n;
+#pragma unroll 4
+    for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+        const int k = m % n;
+        const int nk = (n - k) % n;
+        const cx<T> zk = z[k], znk = z[nk];
+        const cx<T> tn = mk<T>((T)0.5 * (zk.x + znk.x), (T)0.5 * (zk.y - znk.y));
+        const cx<T> ts = mk<T>((T)0.5 * (zk.y + znk.y), (T)-0.5 * (zk.x - znk.x));
+        cx<T> ph = root[q ? (unsigned)m % twon : 0u];
+        ph.y = -ph.y;
+        f[2 * m] = cmul(ph, tn);
+        f[2 * m + 1] = south ? cmul(ph, ts) : mk<T>(0, 0);
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // synthesis side: fold -> inverse ring DFT -> blend (or write the map)
 // ---------------------------------------------------------------------------
@@ -391,7 +413,8 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
                                                           cx<T> *__restrict__ scr, const cx<T> *__restrict__ G,
                                                           int mode, const T *__restrict__ r, const T *__restrict__ nu,
                                                           T lam, T tau, T *__restrict__ tmap,
-                                                          double *__restrict__ omap, double *__restrict__ part)
+                                                          double *__restrict__ omap, double *__restrict__ part,
+                                                          cx<T> *__restrict__ F)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[RING_THREADS / 32];
@@ -504,22 +527,41 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             // four consecutive pixels per thread with 16-byte loads and stores (ring
             // lengths and offsets are multiples of 4); the scalar loop below takes over
             // for unaligned map views
-            if (mode != RS_MAP && aligned16(tmap + R.offN) && (!south || aligned16(tmap + R.offS)) &&
-                (mode != RS_BLEND ||
+            const bool fused = mode == RS_BLEND_ANA, blend = mode == RS_BLEND || fused;
+            if (mode != RS_MAP && (fused || (aligned16(tmap + R.offN) && (!south || aligned16(tmap + R.offS)))) &&
+                (!blend ||
                  (aligned16(r + R.offN) && aligned16(nu + R.offN) &&
                   (!south || (aligned16(r + R.offS) && aligned16(nu + R.offS)))))) {
                 for (int j = 4 * threadIdx.x; j < n; j += 4 * blockDim.x) {
                     const cx<T> z0 = z[j], z1 = z[j + 1], z2 = z[j + 2], z3 = z[j + 3];
                     float4 sN = make_float4(z0.x, z1.x, z2.x, z3.x), sS = make_float4(z0.y, z1.y, z2.y, z3.y);
-                    if (mode == RS_BLEND) {
+                    if (blend) {
                         sN = blend4(sN, *reinterpret_cast<const float4 *>(r + R.offN + j),
                                     *reinterpret_cast<const float4 *>(nu + R.offN + j), lt, lm1t, chi_pair);
                         if (south)
                             sS = blend4(sS, *reinterpret_cast<const float4 *>(r + R.offS + j),
                                         *reinterpret_cast<const float4 *>(nu + R.offS + j), lt, lm1t, chi_pair);
                     }
-                    *reinterpret_cast<float4 *>(tmap + R.offN + j) = sN;
-                    if (south) *reinterpret_cast<float4 *>(tmap + R.offS + j) = sS;
+                    if (fused) {  // packed north/south input of the forward DFT (same indices as z)
+                        if (!south) sS = make_float4(0.f, 0.f, 0.f, 0.f);
+                        cx<T> *d = blue ? zin + j : nullptr;
+                        const cx<T> v0 = mk<T>(sN.x, sS.x), v1 = mk<T>(sN.y, sS.y), v2 = mk<T>(sN.z, sS.z),
+                                    v3 = mk<T>(sN.w, sS.w);
+                        if (d) {
+                            d[0] = v0;
+                            d[1] = v1;
+                            d[2] = v2;
+                            d[3] = v3;
+                        } else {
+                            buf[pidx(j)] = v0;
+                            buf[pidx(j + 1)] = v1;
+                            buf[pidx(j + 2)] = v2;
+                            buf[pidx(j + 3)] = v3;
+                        }
+                    } else {
+                        *reinterpret_cast<float4 *>(tmap + R.offN + j) = sN;
+                        if (south) *reinterpret_cast<float4 *>(tmap + R.offS + j) = sS;
+                    }
                 }
                 j0 = n;  // done
             }
@@ -534,26 +576,38 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
                 tmap[iN] = zz.x;
                 if (south) tmap[R.offS + j] = zz.y;
             } else {
+                T tN, tS = 0;
                 {
                     const T s = zz.x, nv = nu[iN], rv = r[iN];
                     const T den = (T)1 + lm1t * nv;
-                    tmap[iN] = s + lt * (rv - nv * s) / den;
+                    tN = s + lt * (rv - nv * s) / den;
                     chi_pair += (nv * s * s - (T)2 * rv * s) / den;
                 }
                 if (south) {
                     const long long iS = R.offS + j;
                     const T s = zz.y, nv = nu[iS], rv = r[iS];
                     const T den = (T)1 + lm1t * nv;
-                    tmap[iS] = s + lt * (rv - nv * s) / den;
+                    tS = s + lt * (rv - nv * s) / den;
                     chi_pair += (nv * s * s - (T)2 * rv * s) / den;
+                }
+                if (mode == RS_BLEND_ANA) {  // same index as z: read and written by this thread only
+                    if (blue) zin[j] = mk<T>(tN, tS);
+                    else buf[pidx(j)] = mk<T>(tN, tS);
+                } else {
+                    tmap[iN] = tN;
+                    if (south) tmap[R.offS + j] = tS;
                 }
             }
         }
-        if (mode == RS_BLEND) {  // per-pair partial: the reduction order does not depend on the schedule
+        if (mode == RS_BLEND || mode == RS_BLEND_ANA) {  // per-pair partial: the reduction order does not depend on the schedule
             const double s = block_sum<T>((double)chi_pair, red);
             if (threadIdx.x == 0) part[pair] = s;
         } else {
             __syncthreads();
+        }
+        if (mode == RS_BLEND_ANA) {  // forward DFT of the blended ring and unfold to F_m, m <= L
+            const RingOut<T> zf = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw);
+            unfold_ring<T>(R, zf, root, q, twon, south, F + (size_t)pair * (rc.lmax + 1) * 2, L);
         }
         cur = nxt;
     }
@@ -625,20 +679,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
         }
         __syncthreads();
         const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw);
-        cx<T> *f = F + (size_t)pair * (rc.lmax + 1) * 2;
-#pragma unroll 4
-        for (int m = threadIdx.x; m <= L; m += blockDim.x) {
-            const int k = m % n;
-            const int nk = (n - k) % n;
-            const cx<T> zk = z[k], znk = z[nk];
-            const cx<T> tn = mk<T>((T)0.5 * (zk.x + znk.x), (T)0.5 * (zk.y - znk.y));
-            const cx<T> ts = mk<T>((T)0.5 * (zk.y + znk.y), (T)-0.5 * (zk.x - znk.x));
-            cx<T> ph = root[q ? (unsigned)m % twon : 0u];
-            ph.y = -ph.y;
-            f[2 * m] = cmul(ph, tn);
-            f[2 * m + 1] = south ? cmul(ph, ts) : mk<T>(0, 0);
-        }
-        __syncthreads();
+        unfold_ring<T>(R, z, root, q, twon, south, F + (size_t)pair * (rc.lmax + 1) * 2, L);
         cur = nxt;
     }
 }
@@ -676,7 +717,8 @@ template <typename T> struct RingLaunch {
     // with the FP64 block's coefficients (m < lc, [pair][m][hemisphere] with
     // glow_stride columns per pair) added to G, or none (glow null)
     static wf_status syn_buf_low(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
-                                 const float2 *glow, int lc, int glow_stride, void *tmap, double *omap)
+                                 const float2 *glow, int lc, int glow_stride, void *tmap, double *omap,
+                                 void *F = nullptr)
     {
         const HpTables &t = p->tab;
         RingCommon rc = common(p, L);
@@ -690,10 +732,19 @@ template <typename T> struct RingLaunch {
         k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
             rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
             (const cx<T> *)G, (int)mode, (const T *)p->ws.r, (const T *)p->ws.nu, (T)lam, (T)tau,
-            (T *)tmap, omap, p->ws.part_pix);
+            (T *)tmap, omap, p->ws.part_pix, (cx<T> *)F);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
         return WF_OK;
+    }
+    // messenger step on the rings: fold, inverse DFT, Eq. 3, forward DFT, unfold into F
+    static wf_status syn_ana(wf_plan p, int L, double lam, double tau)
+    {
+        const HpTables &t = p->tab;
+        if (p->prec != WF_PREC_FP64 && t.lc_mx > 0)
+            return syn_buf_low(p, L, RS_BLEND_ANA, lam, tau, p->ws.G, p->ws.Glow, t.lc_mx, t.glow_cap, nullptr,
+                               nullptr, p->ws.F);
+        return syn_buf_low(p, L, RS_BLEND_ANA, lam, tau, p->ws.G, nullptr, 0, 0, nullptr, nullptr, p->ws.F);
     }
     static wf_status ana(wf_plan p, int L, const void *map) { return ana_buf(p, L, map, p->ws.F); }
     static wf_status ana_buf(wf_plan p, int L, const void *map, void *F)
@@ -873,6 +924,12 @@ wf_status hp_ring_synthesis(wf_plan p, int L, RingSynMode mode, double lam, doub
 {
     return p->prec == WF_PREC_FP64 ? RingLaunch<double>::syn(p, L, mode, lam, tau, out_map)
                                    : RingLaunch<float>::syn(p, L, mode, lam, tau, out_map);
+}
+
+wf_status hp_ring_synthesis_analysis(wf_plan p, int L, double lam, double tau)
+{
+    return p->prec == WF_PREC_FP64 ? RingLaunch<double>::syn_ana(p, L, lam, tau)
+                                   : RingLaunch<float>::syn_ana(p, L, lam, tau);
 }
 
 wf_status hp_ring_synthesis_buf(wf_plan p, int L, RingSynMode mode, double lam, double tau, const void *G,
