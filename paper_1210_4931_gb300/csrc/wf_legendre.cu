@@ -1136,10 +1136,11 @@ __global__ void __launch_bounds__(LEG_THREADS) k_legsyn_mx(int lmax, int L, int 
 }
 
 // analysis: CTA per m; a warp covers 32 lanes x NP pairs; chunks of CH
-// values of l accumulate the packs in f32x2 registers, then are summed over
-// the pack lanes and reduced across the warp.  Eight pairs per lane halve the
-// cross-lane reduction per (l, m, pair) against four; two CTAs per SM (128
-// registers) measured faster than one CTA with no spills.
+// values of l accumulate the packs in f32x2 registers, then are summed across
+// the warp (through the swizzled shared stage for CH = 8, by a shuffle
+// reduce-scatter otherwise).  Eight pairs per lane halve the cross-lane sum
+// per (l, m, pair) against four; two CTAs per SM (128 registers) measured
+// faster than one CTA with no spills.
 
 
 template <bool DIFF, int NP, int CH>
