@@ -102,8 +102,9 @@ typedef struct {
     int fp64_emulation; /* FP64 temperature plans: nonzero runs the Legendre transforms in double-float
                            arithmetic on the FP32 pipe (pairs of FP32 numbers, about 48 significant bits;
                            error-free products and sums), several times faster than the FP64 pipe on GPUs
-                           whose FP64 rate is a small fraction of FP32.  The FP64 correction sweeps of mixed
-                           plans always run this way. */
+                           whose FP64 rate is a small fraction of FP32.  Mixed temperature plans: the
+                           correction sweeps' transforms run this way unless it is negative, which runs
+                           them on the FP64 pipe. */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one

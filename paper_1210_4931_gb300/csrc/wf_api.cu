@@ -981,12 +981,12 @@ wf_status hp_end(HpRun &R)
         if (!p->sub) {
             wf_plan sub = nullptr;
             if ((st = wf_plan_create(&p->g, lmax, WF_PREC_FP64, (void *)p->stream, &sub)) != WF_OK) return st;
-            // its Legendre transforms run in double-float on the FP32 pipe (48-bit
-            // significands; FP64 runs at 1/64 of the FP32 rate on this GPU)
-            sub->df_legendre = true;
             p->sub = sub;
         }
         wf_plan sub = p->sub;
+        // its Legendre transforms run in double-float on the FP32 pipe (48-bit significands;
+        // FP64 runs at 1/64 of the FP32 rate on this GPU) unless fp64_emulation < 0
+        sub->df_legendre = o.fp64_emulation >= 0;
         sub->stream = p->stream;
         sub->opt = p->opt;
         sub->opt.profile = o.profile;

@@ -155,11 +155,13 @@ def test_mixed_solve_is_stable_and_matches_fp64(wf):
     assert rel(out["mixed"][2], out["fp64"][2]) < 1e-3
 
 
-def test_fp64_correction_sweeps(wf):
-    """Row a9: after the mixed iteration, FP64 lambda = 1 sweeps run from the
-    mixed iterate.  The sweeps are exact FP64 messenger steps: the returned
-    a_lm and map satisfy the oracle's FP64 synthesis to 1e-10, and the
-    reported residual is the FP64 operator's (checked with the oracle)."""
+@pytest.mark.parametrize("emulation", [0, -1])
+def test_fp64_correction_sweeps(wf, emulation):
+    """Row a9: after the mixed iteration, FP64-grade lambda = 1 sweeps run from
+    the mixed iterate, with double-float Legendre transforms (default) or on
+    the FP64 pipe (fp64_emulation < 0).  Either way the returned a_lm and map
+    satisfy the oracle's FP64 synthesis to 1e-10, and the reported residual is
+    that of the FP64 operator (checked with the oracle)."""
     import torch
 
     nside, lmax = 32, 64
@@ -169,7 +171,7 @@ def test_fp64_correction_sweeps(wf):
     tau = float(P["noise_var"][obs].min())
     S = basis.per_mode(P["c_ell"])
     plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed")
-    wf.wf_set_options(plan, maxiter=400, refine_sweeps=3)
+    wf.wf_set_options(plan, maxiter=400, refine_sweeps=3, fp64_emulation=emulation)
     s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
     alm = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
     rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-12, s, alm, trace_cap=500)
