@@ -1798,6 +1798,8 @@ wf_status wf_set_options(wf_plan p, const wf_options *opt)
         if (p->opt.mixed_lc != 0 || p->tab.lc_mx < 0) {
             const int lc = p->opt.mixed_lc > 0 ? std::min(p->opt.mixed_lc, p->lmax + 1) : 0;
             if (wf_status st = hp_set_low_block(p, lc)) return st;
+            if (p->pol)  // the spin-2 block as a polarised solve sets it
+                if (wf_status st = hp_pol_set_low_block(p, lc)) return st;
             WF_CUDA(cudaStreamSynchronize(p->stream));
         }
     }
