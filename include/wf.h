@@ -67,7 +67,7 @@ typedef enum {
 
 typedef struct {
     wf_geom_kind kind;
-    int nx, ny;  /* flat only: powers of two, 16 <= n <= 256 */
+    int nx, ny;  /* flat only: nx = ny, a power of two, 16 <= n <= 128 */
     int nside;   /* HEALPix only */
     int ncomp;   /* 1 (temperature) or 3 (polarised I, Q, U: HEALPix, FP64 or mixed) */
 } wf_geometry;
@@ -177,7 +177,8 @@ wf_status wf_set_start(wf_plan p, const double *alm0);
  * conventions).  tol: relative residual |(S^-1 + N^-1) s - N^-1 d| / |N^-1 d|
  * in harmonic coordinates at which to stop.  s_wf: n_pix FP64 output.
  * alm_out: optional harmonic output.  info: optional report.
- * Noise variance must be finite and > 0 on observed pixels (WF_EINVAL).
+ * Noise variance must be finite and > 0 on observed pixels, and the prior
+ * (C_ell, or S on the flat grid) finite and >= 0 everywhere (WF_EINVAL).
  * Polarised plans (ncomp = 3; Eqs. 10-11, heuristic cooling or replay): d and
  * s_wf are 3 x n_pix (I, Q, U, component-major); noise_var is the 3x3 noise
  * covariance per pixel as 6 x n_pix (II, QQ, UU, IQ, IU, QU); the mask byte of a
@@ -260,6 +261,14 @@ wf_status wf_fluct_host(wf_plan p, const double *noise_var, const uint8_t *mask,
 const char *wf_strerror(wf_status s);
 const char *wf_last_error(void);
 
+/* Measurement utility; the paper has no counterpart.  Times an FP32 FMA loop
+ * (independent chains, two 512-thread CTAs per SM; packed != 0 issues packed
+ * f32x2 FMAs as the mixed Legendre kernels do) on cuda_stream and writes the
+ * best of three timed launches, in TFLOP/s (2 flops per FMA), to *tflops: the
+ * measured peak of the FP32 pipe that bounds the mixed Legendre transforms.
+ * Synchronises the stream; allocates nothing. */
+wf_status wf_probe_fp32_fma(void *cuda_stream, int packed, double *tflops);
+
 /* Flat-grid Wiener filter that allocates no device memory: the paper has no
  * counterpart; it exists for callers that cannot allocate at solve time (a
  * solve inside another framework's memory pool, or where cudaMalloc is not
@@ -269,10 +278,14 @@ const char *wf_last_error(void);
  * n: power of two in [16, 128]; opt: may be NULL (defaults), opt->maxiter <=
  * 20000; anything larger is rejected with WF_EINVAL.  d, noise_var, mask, S,
  * s_wf, alm_out: device pointers as for wf_solve; cuda_stream: the stream to
- * use.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it: make that
- * first call outside any stream capture.  All calls share the array, so calls
- * that overlap on the GPU race; each call writes what it reads first. */
+ * use.  S must be finite and >= 0 (WF_EINVAL otherwise).  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current) and caches it per device: make that first call before
+ * any stream capture, and do not use this entry point on a device after a
+ * cudaDeviceReset of it (the cached address is then stale).  All calls share
+ * the array, so calls that overlap on the GPU race; each call writes what it
+ * reads first.  Every copy of the call (status, traces) is ordered on
+ * cuda_stream, and the call returns after that stream has synchronised. */
 wf_status wf_flat_solve_noalloc(int n, const double *d, const double *noise_var, const uint8_t *mask,
                                 const double *S, double tol, const wf_options *opt, void *cuda_stream,
                                 double *s_wf, double *alm_out, wf_info *info);

@@ -96,7 +96,7 @@ EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedu
            "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
            "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
            "wf_server_wait", "wf_server_get_stats", "wf_server_destroy", "wf_solve_batch", "wf_plan_autotune",
-           "wf_plan_tiles"]
+           "wf_plan_tiles", "wf_probe_fp32_fma"]
 
 
 def load(path: str = LIB_PATH):
@@ -153,6 +153,8 @@ def load(path: str = LIB_PATH):
     L.wf_solve_batch.restype = ctypes.c_int
     L.wf_server_destroy.argtypes = [vp]
     L.wf_server_destroy.restype = None
+    L.wf_probe_fp32_fma.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.wf_probe_fp32_fma.restype = ctypes.c_int
     L.wf_strerror.argtypes = [ctypes.c_int]
     L.wf_strerror.restype = ctypes.c_char_p
     L.wf_last_error.argtypes = []
@@ -162,6 +164,18 @@ def load(path: str = LIB_PATH):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def wf_probe_fp32_fma(packed: bool = True, stream=None) -> float:
+    """Measured FP32 FMA throughput of this GPU in TFLOP/s (see include/wf.h)."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_double(0.0)
+    _check(load().wf_probe_fp32_fma(ctypes.c_void_p(stream.cuda_stream), int(bool(packed)), ctypes.byref(out)),
+           "wf_probe_fp32_fma")
+    return float(out.value)
 
 
 def last_error() -> str:

@@ -712,6 +712,9 @@ wf_status hp_begin(HpRun &R)
     HpSchedule &sch = R.sch;
     sch.c.resize(lmax + 1);
     if ((st = to_host(p, sch.c.data(), R.C_ell, (lmax + 1) * sizeof(double))) != WF_OK) return st;
+    for (int l = 0; l <= lmax; ++l)
+        if (!(sch.c[l] >= 0.0 && std::isfinite(sch.c[l])))
+            return set_error(WF_EINVAL, "C_ell must be finite and >= 0 (l = %d: %g)", l, sch.c[l]);
     // Mixed precision: the messenger iteration contracts a mode by about
     // tau_h / S_l per iteration where the mask leaves it unconstrained, so a
     // systematic operator error larger than that margin makes the iteration
@@ -2062,3 +2065,80 @@ wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput probe (a measurement utility; the paper has no
+// counterpart).  The Legendre kernels are bound by the FP32 FMA pipe, so
+// their roofline fraction is taken against this measured rate instead of a
+// figure built from unit counts and clocks.  Every thread runs independent
+// FMA chains (16 scalar, or 8 packed f32x2 through __ffma2_rn) that stay
+// bounded (x <- b x + c with b < 1); the result is written only under a
+// condition that never holds, which keeps the chains live.
+// ---------------------------------------------------------------------------
+namespace wf {
+namespace {
+__device__ float g_fma_probe_sink;
+
+template <bool PACKED>
+__global__ void __launch_bounds__(512) k_fma_probe(int iters, float b, float c)
+{
+    float s = 0.0f;
+    if (PACKED) {
+        float2 x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = make_float2(1e-7f * threadIdx.x + i, 1e-7f * blockIdx.x - i);
+        const float2 bb = make_float2(b, b), cc = make_float2(c, c);
+        for (int k = 0; k < iters; ++k) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = __ffma2_rn(x[i], bb, cc);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += x[i].x + x[i].y;
+    } else {
+        float x[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = 1e-7f * threadIdx.x + 1e-7f * blockIdx.x + i;
+        for (int k = 0; k < iters; ++k) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) x[i] = fmaf(x[i], b, c);
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) s += x[i];
+    }
+    if (s == -1.0f) g_fma_probe_sink = s;
+}
+}  // namespace
+}  // namespace wf
+
+extern "C" wf_status wf_probe_fp32_fma(void *cuda_stream, int packed, double *tflops)
+{
+    using namespace wf;
+    if (!tflops) return set_error(WF_EINVAL, "null argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, nsm = 0;
+    WF_CUDA(cudaGetDevice(&dev));
+    WF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = 2 * nsm, threads = 512, iters = 1 << 16;
+    const double flops = (double)blocks * threads * (double)iters * 16.0 * 2.0;
+    cudaEvent_t e0, e1;
+    WF_CUDA(cudaEventCreate(&e0));
+    WF_CUDA(cudaEventCreate(&e1));
+    double best = 0.0;
+    wf_status status = WF_OK;
+    for (int rep = 0; rep < 4 && status == WF_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        if (packed) k_fma_probe<true><<<blocks, threads, 0, st>>>(iters, 0.9999999f, 1e-7f);
+        else k_fma_probe<false><<<blocks, threads, 0, st>>>(iters, 0.9999999f, 1e-7f);
+        cudaEventRecord(e1, st);
+        cudaError_t ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+        if (ce != cudaSuccess) status = set_error(WF_ECUDA, "fma probe: %s", cudaGetErrorString(ce));
+        else if (rep > 0 && ms > 0.0f) best = std::max(best, flops / (ms * 1e-3) / 1e12);  // rep 0 warms up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = best;
+    return status;
+}

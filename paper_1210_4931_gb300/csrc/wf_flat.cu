@@ -533,6 +533,9 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
     std::vector<double> Sh((size_t)n * nh);
     wf_status st = to_host(p, Sh.data(), S, Sh.size() * 8);
     if (st != WF_OK) return st;
+    for (size_t i = 0; i < Sh.size(); ++i)
+        if (!(Sh[i] >= 0.0 && std::isfinite(Sh[i])))
+            return set_error(WF_EINVAL, "the prior S must be finite and >= 0 (mode %zu: %g)", i, Sh[i]);
     std::vector<double> lev{o.lambda_max};
     int kmax = 0;
     std::vector<int> kr(Sh.size());
@@ -648,9 +651,9 @@ wf_status flat_map2alm(wf_plan p, const double *map, double *alm)
 // Flat-grid solve that allocates nothing (wf_flat_solve_noalloc).
 //
 // For callers that cannot allocate device memory at solve time -- code that
-// runs inside another framework's memory pool, under a CUDA graph capture
-// that forbids cudaMalloc, or on a context where allocation is locked down --
-// this entry point runs the same two kernels as wf_solve on the flat grid
+// runs inside another framework's memory pool (a cudaMalloc there would go
+// around the pool's accounting), or on a context where allocation is locked
+// down -- this entry point runs the same two kernels as wf_solve on the flat grid
 // (k_flat_setup, k_flat_solve), with the solver's scratch (the source and
 // inverse-noise maps, the lambda levels, the status block and the per-
 // iteration traces) in one file-scope device array instead of plan memory.
@@ -658,10 +661,13 @@ wf_status flat_map2alm(wf_plan p, const double *map, double *alm)
 // the array is 0.71 MiB and stays resident on every device that loads the
 // library.  In host code the array's symbol is not a device address: the
 // first call on a device looks up its address with cudaGetSymbolAddress
-// (with that device current) and caches it, so that first call should not
-// be made during a stream capture.  All calls share the one array: calls
-// that overlap on the GPU race; everything a call reads is written by that
-// call first.
+// (with that device current) and caches it per device ordinal, so that first
+// call should come before any stream capture; a cudaDeviceReset of the device
+// invalidates the cached address, so the library must not be used on that
+// device afterwards.  All calls share the one array: calls that overlap on the
+// GPU race; everything a call reads is written by that call first.  The prior
+// S must be finite and >= 0 (the largest S per radius is taken as an integer
+// maximum over the bit patterns, an order that holds for S >= 0 only).
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int NOALLOC_MAXN = 128;
@@ -672,20 +678,28 @@ constexpr size_t NA_R = 0;
 constexpr size_t NA_NU = NA_R + NA_PIX * sizeof(double);
 constexpr size_t NA_LEV = NA_NU + NA_PIX * sizeof(double);
 constexpr size_t NA_RAD = NA_LEV + NOALLOC_LEVELS * sizeof(double);
-constexpr size_t NA_REDU = NA_RAD + 16 * sizeof(double);
+constexpr size_t NA_REDU = NA_RAD + 32 * sizeof(double);
 constexpr size_t NA_STATUS = NA_REDU + 16 * sizeof(double);
 constexpr size_t NA_TRACE = NA_STATUS + 256;
 constexpr size_t NA_BYTES = NA_TRACE + 3 * (size_t)NOALLOC_MAXITER * sizeof(double);
 
 // max S over the half-plane modes whose rounded |k| equals 2^j, j = 1..15
-// (-1 where no mode has that radius): the priors the flat schedule needs
+// (-1 where no mode has that radius): the priors the flat schedule needs.
+// out[16] counts the modes whose S is not finite and >= 0 (rejected by the
+// caller: the maximum below compares bit patterns, valid for S >= 0 only).
 __global__ void k_flat_radial_max(int n, const double *__restrict__ S, double *__restrict__ out)
 {
     __shared__ unsigned long long best[16];
+    __shared__ unsigned int bad;
     if (threadIdx.x < 16) best[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) bad = 0u;
     __syncthreads();
     const int nh = n / 2 + 1;
     for (int i = threadIdx.x; i < n * nh; i += blockDim.x) {
+        if (!(S[i] >= 0.0 && isfinite(S[i]))) {
+            atomicAdd(&bad, 1u);
+            continue;
+        }
         const int ky = i / nh, kx = i % nh;
         const int sy = ky < (n + 1) / 2 ? ky : ky - n;
         const long r = lrint(sqrt((double)sy * sy + (double)kx * kx));
@@ -700,6 +714,7 @@ __global__ void k_flat_radial_max(int n, const double *__restrict__ S, double *_
         const unsigned long long b = best[threadIdx.x];
         out[threadIdx.x] = b ? __longlong_as_double((long long)b) : -1.0;
     }
+    if (threadIdx.x == 0) out[16] = (double)bad;
 }
 }  // namespace
 
@@ -760,12 +775,14 @@ extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double 
     WF_CUDA(cudaGetLastError());
     k_flat_radial_max<<<1, 256, 0, stream>>>(n, S, rad);
     WF_CUDA(cudaGetLastError());
-    double h[3], smax[16];
+    double h[3], smax[17];
     WF_CUDA(cudaMemcpyAsync(h, redu, sizeof h, cudaMemcpyDeviceToHost, stream));
     WF_CUDA(cudaMemcpyAsync(smax, rad, sizeof smax, cudaMemcpyDeviceToHost, stream));
     WF_CUDA(cudaStreamSynchronize(stream));
     if (h[2] != 0.0) return set_error(WF_EINVAL, "noise variance must be finite and > 0 (and d finite) on observed pixels");
     if (h[1] == 0.0) return set_error(WF_EINVAL, "every pixel is masked");
+    if (smax[16] != 0.0)
+        return set_error(WF_EINVAL, "the prior S must be finite and >= 0 (%.0f modes are not)", smax[16]);
     const double tau = h[0];
     const long long ndof = (long long)h[1];
 
@@ -835,9 +852,14 @@ extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double 
         info->launches = 3;
         const int nt = std::min(fs.iters, info->trace_cap);
         if (nt > 0) {
-            if (info->lambda_trace) WF_CUDA(cudaMemcpy(info->lambda_trace, A.tr_lam, nt * 8, cudaMemcpyDeviceToHost));
-            if (info->chi2_trace) WF_CUDA(cudaMemcpy(info->chi2_trace, A.tr_chi2, nt * 8, cudaMemcpyDeviceToHost));
-            if (info->resid_trace) WF_CUDA(cudaMemcpy(info->resid_trace, A.tr_res, nt * 8, cudaMemcpyDeviceToHost));
+            // ordered on the caller's stream like every other copy of this call
+            if (info->lambda_trace)
+                WF_CUDA(cudaMemcpyAsync(info->lambda_trace, A.tr_lam, nt * 8, cudaMemcpyDeviceToHost, stream));
+            if (info->chi2_trace)
+                WF_CUDA(cudaMemcpyAsync(info->chi2_trace, A.tr_chi2, nt * 8, cudaMemcpyDeviceToHost, stream));
+            if (info->resid_trace)
+                WF_CUDA(cudaMemcpyAsync(info->resid_trace, A.tr_res, nt * 8, cudaMemcpyDeviceToHost, stream));
+            WF_CUDA(cudaStreamSynchronize(stream));
             if (info->L_trace)
                 for (int i = 0; i < nt; ++i) info->L_trace[i] = -1;
         }

@@ -166,7 +166,34 @@ def test_invalid_inputs_are_rejected(wf):
     assert rep["converged"]
     with pytest.raises(wf.WfError):
         wf.wf_plan_create("healpix", nside=8, lmax=17)
+    # the prior must be finite and >= 0 (C_0 = C_1 = 0 is allowed)
+    for bad_c in (-1e-3, np.nan, np.inf):
+        cl = P["c_ell"].copy()
+        cl[5] = bad_c
+        with pytest.raises(wf.WfError) as e:
+            wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(cl), 1e-6, s)
+        assert e.value.status == wf.WF_EINVAL
     plan.close()
+    pm = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed")
+    cl = P["c_ell"].copy()
+    cl[7] = -cl[7]
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_solve(pm, T(d), T(P["noise_var"]), T(P["mask"]), T(cl), 1e-6, s)
+    assert e.value.status == wf.WF_EINVAL
+    pm.close()
+    # flat grid: S per mode
+    n = 32
+    F = gen.flat_problem(n, seed=gen.seed_for(1, 5))
+    pf = wf.wf_plan_create("flat", n=n)
+    sf = torch.empty(n * n, dtype=torch.float64, device="cuda")
+    for bad_s in (-1.0, np.nan):
+        S = F["S"].copy()
+        S[1, 1] = bad_s
+        with pytest.raises(wf.WfError) as e:
+            wf.wf_solve(pf, T(F["noise"].ravel()), T(F["noise_var"].ravel()), T(F["mask"].ravel()),
+                        T(S.ravel()), 1e-6, sf)
+        assert e.value.status == wf.WF_EINVAL
+    pf.close()
 
 
 def test_no_mask_pointer_means_all_observed(wf):
