@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="batching workload instead: this many solves of mixed nside (64-256), "
                          "run one by one and as one wf_solve_batch")
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
+                    help="1: flat 128x128 FP64 (us per iteration, time to tol); 2: HEALPix nside 512 / lmax 1024 "
+                         "FP64 (time to tol, p50/p99); 3: the nside 2048 headline (default)")
     ap.add_argument("--full-band-iters", type=int, default=0,
                     help="replay this many lambda = 1, L = lmax iterations instead of the cooling schedule "
                          "(steady-state timing and profiling)")
@@ -777,10 +780,154 @@ def run_pol_batch(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# the two smaller workloads: flat 128 x 128 and HEALPix nside 512, FP64
+# --------------------------------------------------------------------------
+def _pcts(x):
+    x = np.asarray(x, dtype=np.float64)
+    return {"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99)), "n": int(x.size)}
+
+
+def run_config1(args):
+    """Flat 128 x 128 periodic grid, FP64, one map: the whole solve (cooling from lambda 100 to 1
+    and lambda = 1 down to tol) is one persistent 8-CTA cluster kernel.  A step is one solve."""
+    import torch
+
+    import paper_1210_4931_gb300 as wf
+
+    wf.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P = gen.config_flat_128(0)
+    n = P["nx"]
+    d_h = np.fft.irfft2(P["a_signal"], s=(n, n), norm="ortho") + P["noise"]  # data: signal map + noise
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    d, nv, mk, S = T(d_h.ravel()), T(P["noise_var"].ravel()), T(P["mask"].ravel()), T(P["S"].ravel())
+    plan = wf.wf_plan_create("flat", n=n)
+    wf.wf_set_options(plan, maxiter=20000)
+    s_out = torch.empty(n * n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        wf.wf_solve(plan, d, nv, mk, S, args.tol, s_out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms, iters = [], []
+    clocks = Clocks(0)
+    clocks.start()
+    for _ in range(args.steps):
+        e0.record(stream)
+        rep = wf.wf_solve(plan, d, nv, mk, S, args.tol, s_out, trace_cap=20000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters.append(rep["iters"])
+    ck = clocks.stop()
+    us_it = [1e3 * t / k for t, k in zip(step_ms, iters)]
+    out = {"metric": "flat 128x128 FP64 Wiener filter: microseconds per messenger iteration and time to tol",
+           "value": float(np.median(us_it)), "unit": "us/iter", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": False,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "flat_128x128_fp64", "tol": args.tol, "l2": "whole problem in shared memory"},
+           "time_to_tol_ms": _pcts(step_ms), "iters_per_solve": int(iters[-1]), "converged": bool(rep["converged"]),
+           "final_residual": float(rep["final_residual"]), "lambda_levels": int(rep["n_levels"]),
+           "gpu_launches_per_solve": int(rep["launches"]), "clocks": ck}
+    if not args.no_cpu:
+        import oracle
+
+        basis = oracle.FlatBasis(n, n)
+        obs = P["mask"] > 0
+        nu = np.where(obs, 1.0 / P["noise_var"], 0.0)
+        tau = float(P["noise_var"][obs].min())
+        t0 = time.perf_counter()
+        ref = oracle.messenger_solve(basis, nu * d_h, nu, P["S"], tau, tol=args.tol, maxiter=20000)
+        t_or = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 1e6 * t_or / ref["iters"], "unit": "us/iter", "cores": 1, "kind": "oracle",
+                               "sample": "one full oracle solve (numpy FFTs, one thread): %d iterations in %.2f s"
+                                         % (ref["iters"], t_or), "time_to_tol_s": t_or}
+        out["err_vs_oracle"] = {"s_wf_max_rel": float(np.max(np.abs(s_out.cpu().numpy() - ref["s"].ravel())) /
+                                                     np.max(np.abs(ref["s"]))),
+                                "note": "GPU and oracle each run their own schedule to tol (no replay)"}
+    plan.close()
+    print(json.dumps(out))
+    return 0
+
+
+def run_config2(args):
+    """HEALPix nside 512 / lmax 1024, 13' beam, |b| < 20 deg plus 500 disks of 0.6 deg, FP64: full
+    solves to tol (a step is one solve), iterations/s, per-iteration p50/p99, and the same solve in
+    mixed precision beside it."""
+    import torch
+
+    import paper_1210_4931_gb300 as wf
+
+    wf.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nside, lmax = 512, 1024
+    P = gen.config_nside512(0)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    out = {"metric": "HEALPix nside 512 / lmax 1024 FP64 Wiener filter: time to tol and messenger iterations/s",
+           "unit": "iter/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "healpix_T_nside512_lmax1024_fp64", "tol": args.tol, "maxiter": args.maxiter,
+                      "l2": "inputs (75 MB) fit in L2"}}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    for prec in ("fp64", "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+        if prec == "mixed":
+            wf.wf_plan_autotune(plan)
+        s_sig = torch.empty(plan.npix, dtype=torch.float64, device=dev)
+        wf.wf_alm2map(plan, T(P["a_signal"]), lmax, s_sig)
+        d = s_sig + T(P["noise"])
+        nv, mk, cl = T(P["noise_var"]), T(P["mask"]), T(P["c_ell"])
+        s_out = torch.empty(plan.npix, dtype=torch.float64, device=dev)
+        wf.wf_set_options(plan, maxiter=args.maxiter, profile=1)
+        steps = args.steps if prec == "fp64" else max(1, args.steps)
+        for _ in range(args.warmup if prec == "fp64" else 1):
+            wf.wf_solve(plan, d, nv, mk, cl, args.tol, s_out)
+        torch.cuda.synchronize()
+        if prec == "fp64":
+            clocks.start()
+        step_ms, reps = [], []
+        for _ in range(steps):
+            e0.record(stream)
+            reps.append(wf.wf_solve(plan, d, nv, mk, cl, args.tol, s_out, trace_cap=args.maxiter + 16))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        if prec == "fp64":
+            out["clocks"] = clocks.stop()
+        last = reps[-1]
+        it_ms = np.concatenate([r["iter_ms_trace"] for r in reps])
+        full = np.concatenate([(r["lambda_trace"] == 1.0) & (r["L_trace"] == lmax) for r in reps])
+        rec = {"iters_per_s": float(sum(r["iters"] for r in reps) / (sum(step_ms) / 1e3)),
+               "time_to_tol_s": _pcts(np.array(step_ms) / 1e3) if last["converged"] else None,
+               "converged": bool(last["converged"]), "iters_per_solve": int(last["iters"]),
+               "final_residual": float(last["final_residual"]), "chi2_over_ndof": float(last["chi2_over_ndof"]),
+               "iter_ms_full_band": _pcts(it_ms[full]) if full.any() else None,
+               "time_to_residual_s": time_to_residual(last), "ms_per_step": float(np.mean(step_ms))}
+        out[prec] = rec
+        plan.close()
+    out["value"] = out["fp64"]["iters_per_s"]
+    out["ms_per_step"] = out["fp64"]["ms_per_step"]
+    if not args.no_cpu:
+        t_it, desc, thr, _ = oracle_iteration_sample(nside, lmax, n_rings=16, n_m=16)
+        out["cpu_baseline"] = {"value": 1.0 / t_it, "unit": "iter/s", "cores": thr, "kind": "oracle", "sample": desc,
+                               "time_to_tol_s_extrapolated": t_it * out["fp64"]["iters_per_solve"]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 1:
+        return run_config1(args)
+    if args.config == 2:
+        return run_config2(args)
     if args.serve:
         return run_serve(args)
     if args.batch > 0:

@@ -233,6 +233,26 @@ wf_status wf_map2alm_adjoint(wf_plan p, const double *map, int L, double *alm);
  * receives the removed template amplitudes.  Synchronises the stream. */
 wf_status wf_remove_templates(wf_plan p, const double *d_raw, const uint8_t *mask, double *d_out, double *coef);
 
+/* Several data sets of one signal with the same beam and pixelisation (the
+ * generalisation the paper's outlook names, Sect. 4).  For data d_k = s + n_k
+ * with noise variance N_k the stacked Wiener-filter equation
+ *     (S^-1 + sum_k N_k^-1) s = sum_k N_k^-1 d_k
+ * is Eq. (2) of one data set with, per pixel over the data sets observing it,
+ *     N^-1 = sum_k N_k^-1,   N^-1 d = sum_k N_k^-1 d_k.
+ * This call forms that data set: d_out = (sum N_k^-1 d_k) / (sum N_k^-1),
+ * noise_var_out = 1 / sum N_k^-1, mask_out = 1 where any data set observes
+ * the pixel (unobserved pixels: d_out = 0, noise_var_out = 1, mask_out = 0);
+ * wf_solve / wf_fluct on the outputs then give the stacked solution.
+ * Data sets with different beams are not reducible this way.
+ * k: 1..16 data sets.  d, noise_var, mask: HOST arrays of k DEVICE pointers
+ * (n_pix FP64 maps; mask may be NULL, or hold NULL entries: all observed).
+ * d_out, noise_var_out (n_pix FP64) and mask_out (n_pix uint8): device.
+ * Temperature plans (ncomp = 1; WF_EUNSUPPORTED otherwise), flat or HEALPix.
+ * Non-finite or non-positive noise, or non-finite data, on an observed
+ * pixel: WF_EINVAL.  Synchronises the plan's stream. */
+wf_status wf_combine_datasets(wf_plan p, int k, const double *const *d, const double *const *noise_var,
+                              const uint8_t *const *mask, double *d_out, double *noise_var_out, uint8_t *mask_out);
+
 /* Sizes of the plan's arrays. */
 long long wf_npix(wf_plan p);
 long long wf_nalm(wf_plan p); /* complex entries */

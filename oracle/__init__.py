@@ -25,6 +25,9 @@ Functions and the paper passage each follows:
                                schedule of Sect. 3 and the fluctuation source
                                of Eq. (9).
 * ``marginalize_templates`` -- monopole/dipole projection of Eq. (12).
+* ``combine_datasets``      -- several data sets of one signal with the same
+                               beam (the outlook of Sect. 4) reduced exactly
+                               to one: N^-1 = sum N_k^-1, N^-1 d = sum N_k^-1 d_k.
 
 Parity status: every function here is pinned by tests in
 ``tests/test_oracle_*.py`` except the heuristic schedule's plateau constant
@@ -271,6 +274,7 @@ from .messenger import (  # noqa: E402
     wnorm,
 )
 from .templates import marginalize_templates, template_matrix  # noqa: E402
+from .datasets import combine_datasets  # noqa: E402
 
 __all__ = [
     "FlatBasis",
@@ -279,6 +283,7 @@ __all__ = [
     "adjoint_synthesis",
     "alm_index",
     "alm_lm",
+    "combine_datasets",
     "fluct_source",
     "healpix_rings",
     "legendre",

@@ -96,7 +96,7 @@ EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedu
            "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
            "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
            "wf_server_wait", "wf_server_get_stats", "wf_server_destroy", "wf_solve_batch", "wf_plan_autotune",
-           "wf_plan_tiles", "wf_probe_fp32_fma"]
+           "wf_plan_tiles", "wf_probe_fp32_fma", "wf_combine_datasets"]
 
 
 def load(path: str = LIB_PATH):
@@ -153,6 +153,9 @@ def load(path: str = LIB_PATH):
     L.wf_solve_batch.restype = ctypes.c_int
     L.wf_server_destroy.argtypes = [vp]
     L.wf_server_destroy.restype = None
+    L.wf_combine_datasets.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                      dp, dp, u8p]
+    L.wf_combine_datasets.restype = ctypes.c_int
     L.wf_probe_fp32_fma.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.wf_probe_fp32_fma.restype = ctypes.c_int
     L.wf_strerror.argtypes = [ctypes.c_int]
@@ -164,6 +167,24 @@ def load(path: str = LIB_PATH):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def wf_combine_datasets(plan, d_list, noise_list, mask_list, d_out, noise_out, mask_out):
+    """Inverse-noise-weighted combination of k data sets of one signal (see
+    include/wf.h); every map is a CUDA tensor of npix entries (masks uint8,
+    None entries: all observed)."""
+    k = len(d_list)
+    if not (len(noise_list) == k and (mask_list is None or len(mask_list) == k)):
+        raise ValueError("d_list, noise_list and mask_list must have the same length")
+    n8 = plan.npix * 8
+    arr = ctypes.c_void_p * k
+    dp_ = arr(*[_ptr(x, None, n8, "d") for x in d_list])
+    np_ = arr(*[_ptr(x, None, n8, "noise_var") for x in noise_list])
+    mp_ = arr(*[_ptr(x, None, plan.npix, "mask") for x in mask_list]) if mask_list is not None else None
+    _check(load().wf_combine_datasets(plan.handle, k, dp_, np_, mp_, _ptr(d_out, None, n8, "d_out"),
+                                      _ptr(noise_out, None, n8, "noise_out"), _ptr(mask_out, None, plan.npix,
+                                                                                    "mask_out")),
+           "wf_combine_datasets")
 
 
 def wf_probe_fp32_fma(packed: bool = True, stream=None) -> float:

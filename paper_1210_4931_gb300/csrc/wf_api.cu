@@ -2142,3 +2142,74 @@ extern "C" wf_status wf_probe_fp32_fma(void *cuda_stream, int packed, double *tf
     *tflops = best;
     return status;
 }
+
+// ---------------------------------------------------------------------------
+// Several data sets of one signal with the same beam and pixelisation (the
+// outlook of Sect. 4): the stacked Wiener-filter equation
+//     (S^-1 + sum_k N_k^-1) s = sum_k N_k^-1 d_k
+// is Eq. (2) of one data set with N^-1 = sum_k N_k^-1 and N^-1 d =
+// sum_k N_k^-1 d_k per pixel, over the data sets that observe the pixel.
+// ---------------------------------------------------------------------------
+namespace wf {
+namespace {
+constexpr int MAX_DATASETS = 16;
+struct DatasetPtrs {
+    const double *d[MAX_DATASETS];
+    const double *nv[MAX_DATASETS];
+    const uint8_t *mask[MAX_DATASETS];
+};
+
+__global__ void k_combine_datasets(long long npix, int k, DatasetPtrs in, double *__restrict__ d_out,
+                                   double *__restrict__ nv_out, uint8_t *__restrict__ mask_out,
+                                   int *__restrict__ flag)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npix;
+         i += (long long)gridDim.x * blockDim.x) {
+        double w = 0.0, wd = 0.0;
+        bool bad = false;
+        for (int j = 0; j < k; ++j) {
+            if (in.mask[j] && in.mask[j][i] == 0) continue;
+            const double n = in.nv[j][i], d = in.d[j][i];
+            if (!(n > 0.0 && isfinite(n) && isfinite(d))) {
+                bad = true;
+                continue;
+            }
+            w += 1.0 / n;
+            wd += d / n;
+        }
+        if (bad) atomicOr(flag, 1);
+        const bool seen = w > 0.0;
+        nv_out[i] = seen ? 1.0 / w : 1.0;
+        d_out[i] = seen ? wd / w : 0.0;
+        mask_out[i] = seen ? 1 : 0;
+    }
+}
+}  // namespace
+}  // namespace wf
+
+extern "C" wf_status wf_combine_datasets(wf_plan p, int k, const double *const *d, const double *const *noise_var,
+                                         const uint8_t *const *mask, double *d_out, double *noise_var_out,
+                                         uint8_t *mask_out)
+{
+    using namespace wf;
+    if (!p || !d || !noise_var || !d_out || !noise_var_out || !mask_out) return set_error(WF_EINVAL, "null argument");
+    if (k < 1 || k > MAX_DATASETS) return set_error(WF_EINVAL, "need 1 <= k <= %d data sets (got %d)", MAX_DATASETS, k);
+    if (p->g.ncomp == 3) return set_error(WF_EUNSUPPORTED, "wf_combine_datasets: temperature plans only");
+    DatasetPtrs in{};
+    for (int j = 0; j < k; ++j) {
+        if (!d[j] || !noise_var[j]) return set_error(WF_EINVAL, "data set %d: null map", j);
+        in.d[j] = d[j];
+        in.nv[j] = noise_var[j];
+        in.mask[j] = mask ? mask[j] : nullptr;
+    }
+    WF_CUDA(cudaMemsetAsync(p->ws.flag, 0, sizeof(int), p->stream));
+    k_combine_datasets<<<grid_for(p->npix, p->nsm), 256, 0, p->stream>>>(p->npix, k, in, d_out, noise_var_out,
+                                                                        mask_out, p->ws.flag);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    int flag = 0;
+    WF_CUDA(cudaMemcpyAsync(&flag, p->ws.flag, sizeof flag, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    if (flag) return set_error(WF_EINVAL, "noise variance must be finite and > 0 (and d finite) where observed");
+    return WF_OK;
+}
