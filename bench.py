@@ -51,8 +51,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--maxiter", type=int, default=1000, help="iteration cap of one solve (one step)")
+    ap.add_argument("--tol", type=float, default=None,
+                    help="relative residual at which a solve stops (default 1e-6 on the flat grid, 1e-4 on the "
+                         "HEALPix workloads, where 1e-6 is out of reach of the messenger iteration: its residual "
+                         "tail decays as a power law)")
+    ap.add_argument("--maxiter", type=int, default=3000, help="iteration cap of one solve (one step)")
     ap.add_argument("--refine-sweeps", type=int, default=2,
                     help="FP64 lambda = 1 correction sweeps after the mixed iteration (0: none)")
     ap.add_argument("--schedule", default="heuristic", choices=["heuristic", "bound"],
@@ -147,6 +150,21 @@ def time_to_residual(rep):
         hit = np.nonzero(res < tol)[0]
         out["%g" % tol] = {"s": float(cum[hit[0]]), "iters": int(hit[0] + 1)} if hit.size else None
     return out
+
+
+def time_to_dchi2(rep, lmax):
+    """The paper's own stopping rule (Sect. 3): the first lambda = 1, full-band
+    iteration whose chi^2 changed by less than 1e-4 sigma_chi2 = 1e-4 sqrt(2
+    n_dof); device time, iteration and the relative residual there."""
+    ms = np.nan_to_num(rep["iter_ms_trace"], nan=0.0)
+    cum = np.cumsum(ms) / 1e3
+    chi, lam, L, res = rep["chi2_trace"], rep["lambda_trace"], rep["L_trace"], rep["resid_trace"]
+    sig = math.sqrt(2.0 * rep["n_dof"])
+    full = (lam == 1.0) & (L == lmax)
+    for k in range(1, len(chi)):
+        if full[k] and full[k - 1] and abs(chi[k] - chi[k - 1]) < 1e-4 * sig:
+            return {"s": float(cum[k]), "iters": int(k + 1), "residual": float(res[k])}
+    return None
 
 
 # --------------------------------------------------------------------------
@@ -403,7 +421,9 @@ def run_ours(args):
                       "l2": "inputs (1.2 GB) larger than L2",
                       "parallelism": "replicas"},
            "time_to_tol_s": t_ms / args.steps / 1e3 if last["converged"] else None,
-           "time_to_residual_s": time_to_residual(last), "iters_per_solve": last["iters"],
+           "time_to_residual_s": time_to_residual(last),
+           "time_to_paper_stop_s": time_to_dchi2(last, lmax),
+           "iters_per_solve": last["iters"],
            "maxiter": args.maxiter, "mixed_lc": last.get("mixed_lc"), "fp64_sweeps": last.get("refine_sweeps"),
            "final_residual": last["final_residual"], "converged": last["converged"],
            "chi2_over_ndof": last["chi2_over_ndof"],
@@ -922,6 +942,8 @@ def run_config2(args):
 
 def main():
     args = parse()
+    if args.tol is None:
+        args.tol = 1e-6 if args.config == 1 else 1e-4
     if args.impl == "reference":
         return run_reference(args)
     if args.config == 1:

@@ -61,8 +61,14 @@ typedef enum { WF_GEOM_FLAT = 0, WF_GEOM_HEALPIX = 1 } wf_geom_kind;
 
 typedef enum {
     WF_PREC_FP64 = 0,       /* every step in FP64 */
-    WF_PREC_MIXED_FP32 = 1  /* FP32 Legendre recurrence/contraction and ring FFTs from FP64 seeds;
+    WF_PREC_MIXED_FP32 = 1, /* FP32 Legendre recurrence/contraction and ring FFTs from FP64 seeds;
                                FP64 a_lm, reductions and residual refinement */
+    WF_PREC_MIXED_TF32 = 2, /* as MIXED_FP32, with the Legendre synthesis contraction on the tensor cores
+                               (tcgen05): the FP32 recurrence values and c a_lm split into TF32 head + tail,
+                               hi*hi + hi*lo + lo*hi accumulated in FP32 ("3xTF32", FP32-grade accuracy).
+                               Maps of one geometry in one wf_solve_batch share the recurrence (one launch).
+                               Temperature HEALPix plans (ncomp = 1) */
+    WF_PREC_MIXED_SPLITBF16 = 3 /* reserved: the same contraction with BF16 pieces (WF_EUNSUPPORTED) */
 } wf_precision;
 
 typedef struct {

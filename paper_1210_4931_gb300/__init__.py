@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(HERE, "libwf.so")
 
 WF_OK, WF_EINVAL, WF_ENOMEM, WF_ECUDA, WF_ENOCONV, WF_EDIVERGE, WF_ETIMEOUT, WF_EUNSUPPORTED = range(8)
 WF_GEOM_FLAT, WF_GEOM_HEALPIX = 0, 1
-WF_PREC_FP64, WF_PREC_MIXED_FP32 = 0, 1
-PRECISIONS = {"fp64": WF_PREC_FP64, "mixed": WF_PREC_MIXED_FP32, "fp32": WF_PREC_MIXED_FP32}
+WF_PREC_FP64, WF_PREC_MIXED_FP32, WF_PREC_MIXED_TF32, WF_PREC_MIXED_SPLITBF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": WF_PREC_FP64, "mixed": WF_PREC_MIXED_FP32, "fp32": WF_PREC_MIXED_FP32,
+              "tf32": WF_PREC_MIXED_TF32, "bf16": WF_PREC_MIXED_SPLITBF16}
 
 
 class WfError(RuntimeError):

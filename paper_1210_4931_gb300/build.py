@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libwf.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["wf_api.cu", "wf_legendre.cu", "wf_ring.cu", "wf_flat.cu", "wf_serve.cu", "wf_spin.cu", "wf_spin_mx.cu"]
+SOURCES = ["wf_api.cu", "wf_legendre.cu", "wf_ring.cu", "wf_flat.cu", "wf_serve.cu", "wf_spin.cu", "wf_spin_mx.cu",
+           "wf_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

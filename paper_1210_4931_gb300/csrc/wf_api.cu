@@ -1519,6 +1519,16 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
         statuses[i] = hp_begin(r);
         active[i] = statuses[i] == WF_OK;
     }
+    // tensor-core items of one geometry and FP64 block share one synthesis launch per step
+    std::vector<cudaEvent_t> gev(n, nullptr);
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreateWithFlags(&gev[i], cudaEventDisableTiming) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(gev[j]);
+            cleanup();
+            return set_error(WF_ECUDA, "batch event creation failed");
+        }
+    std::vector<int> group_of(n, -1);
+    std::vector<std::array<long long, WF_NK>> group_cnt(n);
     std::vector<std::pair<int, std::pair<double, int>>> cfg, cur;
     for (;;) {
         cfg.clear();
@@ -1532,16 +1542,63 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
             cudaGraph_t ng = nullptr;
             if ((st = ck(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal), "capture"))) break;
             cudaEventRecord(fork, origin);
+            // groups: (nside, lmax, FP64 block) of the tensor-core items, at most TC_MAX_COLUMNS each
+            std::fill(group_of.begin(), group_of.end(), -1);
+            for (auto &gc : group_cnt) gc.fill(0);
+            int ngroups = 0;
+            for (size_t u = 0; u < cfg.size() && st == WF_OK; ++u) {
+                const int i0 = cfg[u].first;
+                wf_plan p0 = plans[i0];
+                if (p0->prec != WF_PREC_MIXED_TF32 || R[i0].rigorous || group_of[i0] >= 0) continue;
+                std::vector<int> mem{i0};
+                for (size_t v = u + 1; v < cfg.size() && (int)mem.size() < TC_MAX_COLUMNS; ++v) {
+                    const int j = cfg[v].first;
+                    wf_plan pj = plans[j];
+                    if (group_of[j] < 0 && pj->prec == WF_PREC_MIXED_TF32 && !R[j].rigorous &&
+                        pj->nside == p0->nside && pj->lmax == p0->lmax && pj->tab.lc_mx == p0->tab.lc_mx)
+                        mem.push_back(j);
+                }
+                std::vector<const double2 *> ga;
+                std::vector<float2 *> gG;
+                std::vector<int> gL;
+                int Lmax = 0;
+                for (int j : mem) {
+                    group_of[j] = ngroups;
+                    ga.push_back(plans[j]->ws.a);
+                    gG.push_back((float2 *)plans[j]->ws.G);
+                    gL.push_back(R[j].L);
+                    Lmax = std::max(Lmax, R[j].L);
+                }
+                long long k0[WF_NK];
+                for (int f = 0; f < WF_NK; ++f) k0[f] = p0->kcnt[f];
+                const int fam = p0->kfam;
+                p0->kfam = WF_K_LEG_SYN;
+                st = hp_tc_synthesis(p0, (int)mem.size(), ga.data(), gG.data(), gL.data(), Lmax, origin);
+                p0->kfam = fam;
+                for (int f = 0; f < WF_NK; ++f) {
+                    group_cnt[i0][f] = p0->kcnt[f] - k0[f];
+                    p0->kcnt[f] = k0[f];
+                }
+                cudaEventRecord(gev[ngroups], origin);
+                ++ngroups;
+            }
             for (auto &c : cfg) {
+                if (st != WF_OK) break;
                 const int i = c.first;
                 wf_plan p = plans[i];
                 cudaStreamWaitEvent(branch[i], fork, 0);
+                if (group_of[i] >= 0) {
+                    cudaStreamWaitEvent(branch[i], gev[group_of[i]], 0);
+                    p->tc_deferred = true;
+                }
                 long long k0[WF_NK];
                 for (int f = 0; f < WF_NK; ++f) k0[f] = p->kcnt[f];
                 st = hp_launch(R[i]);
+                p->tc_deferred = false;
                 for (int f = 0; f < WF_NK; ++f) {
                     per_step[i][f] = p->kcnt[f] - k0[f];
                     p->kcnt[f] = k0[f];  // counted when the graph runs
+                    per_step[i][f] += group_cnt[i][f];  // the group launch, counted on its first item
                 }
                 if (st != WF_OK) break;
                 cudaEventRecord(join[i], branch[i]);
@@ -1581,6 +1638,7 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
         for (int i = 0; i < n; ++i)
             if (statuses[i] == WF_OK) statuses[i] = hp_end(R[i]);
     cleanup();
+    for (int i = 0; i < n; ++i) cudaEventDestroy(gev[i]);
     return st;
 }
 
@@ -1724,7 +1782,13 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
         return set_error(WF_EUNSUPPORTED, "ncomp must be 1 (temperature) or 3 (I, Q, U)");
     if (g->ncomp == 3 && g->kind != WF_GEOM_HEALPIX)
         return set_error(WF_EUNSUPPORTED, "polarised plans (ncomp = 3) are HEALPix");
-    if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32) return set_error(WF_EINVAL, "unknown precision");
+    if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32 && prec != WF_PREC_MIXED_TF32 &&
+        prec != WF_PREC_MIXED_SPLITBF16)
+        return set_error(WF_EINVAL, "unknown precision");
+    if (prec == WF_PREC_MIXED_SPLITBF16)
+        return set_error(WF_EUNSUPPORTED, "the split-BF16 tensor-core contraction is not built");
+    if (prec == WF_PREC_MIXED_TF32 && (g->kind != WF_GEOM_HEALPIX || g->ncomp == 3))
+        return set_error(WF_EUNSUPPORTED, "tensor-core plans are temperature HEALPix plans");
     wf_plan p = new (std::nothrow) wf_plan_s();
     if (!p) return set_error(WF_ENOMEM, "host allocation");
     p->g = *g;
@@ -1754,7 +1818,8 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
     }
     if (st == WF_OK) {
         if ((st = plan_alloc(p, (void **)&p->ws.scal, 16 * sizeof(double))) == WF_OK &&
-            (st = plan_alloc(p, (void **)&p->ws.flag, 16)) == WF_OK) {
+            (st = plan_alloc(p, (void **)&p->ws.flag, 16)) == WF_OK &&
+            (st = plan_alloc(p, (void **)&p->ws.tc_err, 16)) == WF_OK) {
             if (cudaMallocHost(&p->ws.h_scal, 16 * sizeof(double)) != cudaSuccess)
                 st = set_error(WF_ENOMEM, "pinned host allocation");
         }

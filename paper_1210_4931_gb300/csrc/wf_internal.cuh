@@ -110,6 +110,7 @@ struct Workspace {
     uint8_t *mask_in = nullptr;
     double *g1_in = nullptr, *g2_in = nullptr;
     int *flag = nullptr;          // device flags (invalid input)
+    int *tc_err = nullptr;        // tensor-core kernels: set when a bounded wait gave up
     double *redu = nullptr;       // reduction scratch
 };
 
@@ -171,6 +172,7 @@ struct wf_plan_s {
     double bnorm_given = 0;   // > 0: the next solve's residual norm |Y^T r| (the sweeps take their parent's)
     bool events_ready = false;
     int tile_syn = 4, tile_ana = 8;  // mixed Legendre tiles: ring pairs per thread / per lane
+    bool tc_deferred = false;        // tensor-core plan in a batch step: its synthesis ran in the group launch
     cudaStream_t aux = nullptr;      // mixed precision: stream of the FP64 low-l block
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     long long kcnt[WF_NK] = {};  // kernels launched on this plan, by family (WF_K_*)
@@ -242,6 +244,11 @@ wf_status hp_autotune(wf_plan p, int reps);
 wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L);
 wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &ba, const double2 *a_old,
                                double2 *out);
+// tensor-core transforms (wf_tc.cu): ncols columns sharing p's geometry, tables and FP64 block
+constexpr int TC_MAX_COLUMNS = 16;
+wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 *const *G, const int *L, int Lmax,
+                          cudaStream_t stream);
+size_t tc_syn_smem(int nc);
 
 // ring transforms (wf_ring.cu)
 wf_status hp_build_ring_tables(wf_plan p);

@@ -1684,10 +1684,16 @@ wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
                       : launch_syn64<float>(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux);
         if (st != WF_OK) return st;
     }
-    switch (p->tile_syn) {
-    case 2: st = launch_syn_mx<2>(p, alm, L); break;
-    case 8: st = launch_syn_mx<8>(p, alm, L); break;
-    default: st = launch_syn_mx<4>(p, alm, L); break;
+    if (p->prec == WF_PREC_MIXED_TF32) {
+        // in a batch step the group launch (wf_solve_batch) has written G already
+        float2 *G = (float2 *)p->ws.G;
+        st = p->tc_deferred ? WF_OK : hp_tc_synthesis(p, 1, &alm, &G, &L, L, p->stream);
+    } else {
+        switch (p->tile_syn) {
+        case 2: st = launch_syn_mx<2>(p, alm, L); break;
+        case 8: st = launch_syn_mx<8>(p, alm, L); break;
+        default: st = launch_syn_mx<4>(p, alm, L); break;
+        }
     }
     if (st != WF_OK) return st;
     if (low) return join_aux(p);

@@ -1,0 +1,427 @@
+// Tensor-core Legendre transforms (tcgen05, sm_103a) for plans whose
+// precision is WF_PREC_MIXED_TF32: the per-m contraction of the basis change
+// (Sect. 2.1; the O(nside lmax^2) cost of Sect. 3) as a dense matrix product
+// on the 5th-generation tensor cores, for one or several columns (maps of one
+// geometry: a solve alone, or the Wiener-filter and fluctuation solves of a
+// batch that share nside, lmax and the FP64 block).
+//
+//   synthesis  G_c(p, m) = sum_l lambda_lm(x_p) a_c(l, m)
+//              per m: D[p, n] = sum_k A[p, k] B[k, n], rows p = ring pairs,
+//              k = l - m, columns n = (Re, Im) of every map c; the even and
+//              odd l - m terms go to two accumulators (D_E, D_O) so that the
+//              north and south rings of a pair come out as D_E +- D_O.
+//
+// Arithmetic ("3xTF32"): the FP32 recurrence value mu (mu form, lambda = c mu,
+// c folded into B) and the FP32 value c a are each split into a TF32 head and
+// an FP32 tail (x = hi + lo exactly, hi = x rounded to 10 explicit mantissa
+// bits); the products hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor
+// memory.  The dropped lo*lo term and the tails' own truncation to TF32 are
+// below 2^-21 of each product, so the contraction is as accurate as the FP32
+// FMA kernels.
+//
+// Layout on chip (one CTA = two M = 128 tiles of ring pairs, 256 threads, a
+// thread per ring pair = per tensor-memory lane):
+//   tensor memory  D_E, D_O of each tile (N = NC columns each, NC = 2 ncols
+//                  rounded up to 16) and the A operand of the current chunk
+//                  of 32 l (per tile: E hi, E lo, O hi, O lo, 16 columns
+//                  each); each thread writes its own lane (tcgen05.st), so the
+//                  recurrence values never pass through shared memory;
+//   shared memory  the B operand of the chunk (E hi, E lo, O hi, O lo; NC
+//                  rows x 16 k, K-major core matrices of 8 rows x 16 bytes)
+//                  and the chunk's recurrence coefficients.
+// The MMAs of chunk q run while the threads compute chunk q + 1's recurrence
+// in registers; the threads wait on the chunk's mbarrier (bounded) before
+// they overwrite its operands.
+#include <cstdint>
+#include <cstdio>
+
+#include "wf_internal.cuh"
+
+namespace wf {
+
+namespace {
+
+constexpr int TC_THREADS = 256;   // two M = 128 tiles
+constexpr int TC_KC = 32;         // l values per chunk (16 even, 16 odd)
+constexpr int TC_MAXC = TC_MAX_COLUMNS;  // columns (maps) per launch
+constexpr float TC_X_DIFF = 0.4f; // rings with x > 0.4 run the difference form (as the FP32 kernels)
+constexpr long long TC_SPIN = 1LL << 22;  // bound on every mbarrier wait (then the error flag is set)
+
+__host__ __device__ inline long long tc_mbase(int lmax, int m) { return (long long)m * (2 * lmax + 3 - m) / 2; }
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor, K-major, no swizzle: 8-row x 16-byte core
+// matrices; lbo = byte distance between core matrices adjacent along K,
+// sbo = along M/N
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the 5th-generation tensor cores
+    return d;
+}
+
+// instruction descriptor: kind::tf32, FP32 accumulator, A and B K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(mbar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// bounded wait; false (and the error flag set) if the phase did not complete
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int *err)
+{
+    for (long long it = 0; it < TC_SPIN; ++it)
+        if (mbar_try(mbar, parity)) return true;
+    atomicOr(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::
+            "r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]),
+        "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ uint32_t tf32_head(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// x = hi + lo exactly; hi has a TF32 mantissa
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
+{
+    hi = tf32_head(x);
+    lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+// ---------------------------------------------------------------------------
+// B operand tile of a chunk: NC rows (n) x 16 k, K-major core matrices with
+// the K-direction core matrices NC/8 * 128 bytes apart (k-group major)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t b_offset(int n, int k, int nc)
+{
+    return (uint32_t)((k >> 2) * (nc >> 3) * 128 + (n >> 3) * 128 + (n & 7) * 16 + (k & 3) * 4);
+}
+
+struct TcSynArgs {
+    int lmax, Lmax, npairs, ncols, nc;
+    const float *A32, *B32;       // recurrence multipliers per a_lm (mu form), B = A - 2
+    const double *c64;            // lambda = c mu
+    const int *ls;                // per (m, pair): first l of the FP32 recurrence (> lmax: none)
+    const float *s0, *s1;         // mu at ls and ls + 1
+    const float *xp, *wp;         // per pair: x = cos theta and w = 1 - x
+    const double2 *a[TC_MAXC];    // per column: a_lm (m-major)
+    float2 *G[TC_MAXC];           // per column: ring coefficients [pair][m][hemisphere]
+    int L[TC_MAXC];               // per column: band limit
+    int *err;                     // set when a bounded wait gives up
+};
+
+// one double step (l, l + 1) of the recurrence for one ring pair (scalar form
+// of the FP32 kernels' step); v0 = mu_l, v1 = mu_{l+1}
+template <bool DIFF>
+__device__ __forceinline__ void tc_step(float A0, float B0, float A1, float B1, float x, float w, float &Sa, float &Sb,
+                                        float &v0, float &v1)
+{
+    if (DIFF) {
+        float D = fmaf(fmaf(-A0, w, B0), Sb, Sa);
+        v0 = Sb + D;
+        D = fmaf(fmaf(-A1, w, B1), v0, D);
+        v1 = v0 + D;
+        Sa = D;
+        Sb = v1;
+    } else {
+        v0 = fmaf(A0 * x, Sb, -Sa);
+        v1 = fmaf(A1 * x, v0, -Sb);
+        Sa = v0;
+        Sb = v1;
+    }
+}
+
+template <bool DIFF>
+__device__ __forceinline__ void tc_chunk(int l0, int ls, float s0, float s1, float x, float w, const float4 *coef,
+                                         float &Sa, float &Sb, float (&mu)[TC_KC])
+{
+#pragma unroll
+    for (int j = 0; j < TC_KC / 2; ++j) {
+        const float4 ab = coef[j];
+        float v0, v1;
+        tc_step<DIFF>(ab.x, ab.y, ab.z, ab.w, x, w, Sa, Sb, v0, v1);
+        if (l0 + 2 * j == ls) {
+            v0 = s0;
+            v1 = s1;
+            Sa = DIFF ? s1 - s0 : s0;
+            Sb = s1;
+        }
+        mu[2 * j] = v0;
+        mu[2 * j + 1] = v1;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float4 coef[TC_KC / 2];  // (A_l, B_l, A_l+1, B_l+1) per double step of the chunk
+    __shared__ int qmin_s;
+    const int m = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tile = tid >> 7;                 // M tile of this thread's ring pair
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const int p = blockIdx.x * TC_THREADS + tid;
+    const int nc = P.nc;
+    const long long base = tc_mbase(P.lmax, m);
+    const size_t pstride = (size_t)(P.lmax + 1) * 2;
+
+    // this pair's seeds
+    int ls = INT_MAX;
+    float s0 = 0.f, s1 = 0.f, x = 0.f, w = 1.f;
+    if (p < P.npairs) {
+        const size_t si = (size_t)m * P.npairs + p;
+        const int l = P.ls[si];
+        if (l <= P.Lmax) {
+            ls = l;
+            s0 = P.s0[si];
+            s1 = P.s1[si];
+        }
+        x = P.xp[p];
+        w = P.wp[p];
+    }
+    // first chunk any pair of the CTA needs
+    if (tid == 0) qmin_s = INT_MAX;
+    __syncthreads();
+    if (ls != INT_MAX) atomicMin(&qmin_s, (ls - m) / TC_KC);
+    __syncthreads();
+    const int q0 = qmin_s, q1 = (P.Lmax - m) / TC_KC;
+    if (q0 > q1) {  // no pair of the CTA has a term: zero coefficients (block-uniform exit)
+        if (p < P.npairs)
+            for (int c = 0; c < P.ncols; ++c) {
+                float2 *g = P.G[c] + (size_t)p * pstride + 2 * (size_t)m;
+                *reinterpret_cast<float4 *>(g) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        return;
+    }
+    const bool diff = __shfl_sync(0xffffffffu, x > TC_X_DIFF ? 1 : 0, 0) != 0;  // one form per warp
+
+    // shared B operand: 4 tiles (E hi, E lo, O hi, O lo) of nc x 16 tf32
+    const uint32_t btile = (uint32_t)nc * 64;
+    uint32_t *B = reinterpret_cast<uint32_t *>(smem);
+    for (int i = tid; i < 4 * nc * 16; i += TC_THREADS) B[i] = 0u;  // padding rows stay zero
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    // columns: tile t: D_E [2 nc t, 2 nc t + nc), D_O [+ nc, + 2 nc); A at 4 nc + 64 t
+    const uint32_t dE = tmem + 2u * nc * tile, dO = dE + nc;
+    const uint32_t aT = tmem + 4u * nc + 64u * tile;
+    const uint32_t idesc = idesc_tf32(128, nc);
+    const uint32_t lbo = (uint32_t)(nc >> 3) * 128, sbo = 128;
+    const uint32_t bsm = smem_addr(B);
+
+    float Sa = 0.f, Sb = 0.f;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int q = q0; q <= q1; ++q) {
+        const int l0 = m + TC_KC * q;
+        // recurrence coefficients of the chunk (zero past lmax: those terms have B = 0)
+        __syncthreads();  // the previous chunk's recurrence has read coef
+        if (tid < TC_KC / 2) {
+            const int la = l0 + 2 * tid, lb = la + 1;
+            coef[tid] = make_float4(la <= P.lmax ? P.A32[base + (la - m)] : 0.f,
+                                    la <= P.lmax ? P.B32[base + (la - m)] : 0.f,
+                                    lb <= P.lmax ? P.A32[base + (lb - m)] : 0.f,
+                                    lb <= P.lmax ? P.B32[base + (lb - m)] : 0.f);
+        }
+        __syncthreads();
+        float mu[TC_KC];
+        if (diff) tc_chunk<true>(l0, ls, s0, s1, x, w, coef, Sa, Sb, mu);
+        else tc_chunk<false>(l0, ls, s0, s1, x, w, coef, Sa, Sb, mu);
+        // the previous chunk's MMAs have read A (tensor memory) and B (shared memory)
+        if (q > q0) {
+            ok = ok && mbar_wait(&mbar, phase, P.err);
+            phase ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j], hi[j], lo[j]);
+            tmem_st16(aT + lane_base + 0, hi);
+            tmem_st16(aT + lane_base + 16, lo);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j + 1], hi[j], lo[j]);
+            tmem_st16(aT + lane_base + 32, hi);
+            tmem_st16(aT + lane_base + 48, lo);
+        }
+        // B: (c a) of every column for the chunk's 32 l, split the same way
+        for (int it = tid; it < P.ncols * TC_KC; it += TC_THREADS) {
+            const int c = it / TC_KC, i = it % TC_KC;
+            const int l = l0 + i;
+            float vr = 0.f, vi = 0.f;
+            if (l <= P.L[c] && l <= P.lmax) {
+                const double2 a = P.a[c][base + (l - m)];
+                const double cc = P.c64[base + (l - m)];
+                vr = (float)(a.x * cc);
+                vi = (float)(a.y * cc);
+            }
+            uint32_t rh, rl, ih, il;
+            split_tf32(vr, rh, rl);
+            split_tf32(vi, ih, il);
+            const int k = i >> 1;
+            uint32_t *Bp = B + (size_t)(i & 1) * 2 * (btile / 4);  // E tiles first, then O tiles
+            Bp[b_offset(2 * c, k, nc) / 4] = rh;
+            Bp[b_offset(2 * c + 1, k, nc) / 4] = ih;
+            Bp[(btile + b_offset(2 * c, k, nc)) / 4] = rl;
+            Bp[(btile + b_offset(2 * c + 1, k, nc)) / 4] = il;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int t = 0; t < 2; ++t) {
+                const uint32_t dEt = tmem + 2u * nc * t, aTt = tmem + 4u * nc + 64u * t;
+                for (int par = 0; par < 2; ++par) {
+                    const uint32_t d = dEt + (par ? nc : 0);
+                    const uint32_t a_hi = aTt + 32u * par, a_lo = a_hi + 16;
+                    const uint32_t b_hi = bsm + (uint32_t)par * 2 * btile, b_lo = b_hi + btile;
+                    for (int s = 0; s < 2; ++s) {  // K = 8 per instruction
+                        const uint32_t acc = (q > q0 || s > 0) ? 1u : 0u;
+                        mma_tf32_ts(d, a_hi + 8 * s, smem_desc(b_hi + 2 * s * lbo, lbo, sbo), idesc, acc);
+                        mma_tf32_ts(d, a_hi + 8 * s, smem_desc(b_lo + 2 * s * lbo, lbo, sbo), idesc, 1u);
+                        mma_tf32_ts(d, a_lo + 8 * s, smem_desc(b_hi + 2 * s * lbo, lbo, sbo), idesc, 1u);
+                    }
+                }
+            }
+            mma_commit(&mbar);
+        }
+    }
+    ok = ok && mbar_wait(&mbar, phase, P.err);
+    ok = __syncthreads_and(ok) != 0;  // block-uniform: the loads below are warp-collective
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: G_N = E + O, G_S = E - O per column (8 columns per pass of 16 tensor-memory columns)
+    if (ok) {
+        for (int c0 = 0; c0 < P.ncols; c0 += 8) {
+            uint32_t e[16], o[16];
+            tmem_ld16(dE + lane_base + 2 * c0, e);
+            tmem_ld16(dO + lane_base + 2 * c0, o);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p < P.npairs) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = c0 + j;
+                    if (c < P.ncols) {
+                        const float er = __uint_as_float(e[2 * j]), ei = __uint_as_float(e[2 * j + 1]);
+                        const float orr = __uint_as_float(o[2 * j]), oi = __uint_as_float(o[2 * j + 1]);
+                        float2 *g = P.G[c] + (size_t)p * pstride + 2 * (size_t)m;
+                        *reinterpret_cast<float4 *>(g) = make_float4(er + orr, ei + oi, er - orr, ei - oi);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t tc_syn_smem(int nc) { return (size_t)4 * nc * 64 + 64; }
+
+// Synthesis of ncols columns sharing p's geometry and FP32 seeds (every
+// column's plan has p's nside, lmax and FP64 block): one launch on `stream`,
+// counted on p.
+wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 *const *G, const int *L, int Lmax,
+                          cudaStream_t stream)
+{
+    if (ncols < 1 || ncols > TC_MAXC) return set_error(WF_EINVAL, "tensor-core synthesis: 1..%d columns", TC_MAXC);
+    const HpTables &t = p->tab;
+    TcSynArgs A{};
+    A.lmax = p->lmax;
+    A.Lmax = Lmax;
+    A.npairs = p->npairs;
+    A.ncols = ncols;
+    A.nc = ((2 * ncols + 15) / 16) * 16;
+    A.A32 = t.A32;
+    A.B32 = t.B32;
+    A.c64 = t.c64;
+    A.ls = t.ls_mx;
+    A.s0 = t.s0_mx;
+    A.s1 = t.s1_mx;
+    A.xp = t.x32;
+    A.wp = t.w32;
+    for (int c = 0; c < ncols; ++c) {
+        A.a[c] = a[c];
+        A.G[c] = G[c];
+        A.L[c] = L[c];
+    }
+    A.err = p->ws.tc_err;
+    const size_t sm = tc_syn_smem(A.nc);  // <= 8 KB: below the default limit, no attribute to raise
+    dim3 grid((p->npairs + TC_THREADS - 1) / TC_THREADS, Lmax + 1);
+    k_legsyn_tc<<<grid, TC_THREADS, sm, stream>>>(A);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+}  // namespace wf

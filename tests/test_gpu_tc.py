@@ -1,0 +1,150 @@
+"""Tensor-core (tcgen05) Legendre transforms of WF_PREC_MIXED_TF32 plans
+against the oracle (Sect. 2.1 basis change) and against the FP32 plans.
+
+3xTF32 keeps FP32-grade accuracy, so the tolerances are the FP32 path's:
+2e-5 relative (max norm) against the oracle up to nside 128."""
+import numpy as np
+import pytest
+
+import oracle
+import wf_inputs as gen
+from gpu_util import T, healpix_case, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    import torch
+
+    import paper_1210_4931_gb300 as w
+
+    w.load()
+    torch.cuda.set_device(0)
+    return w
+
+
+def _cmb_alm(lmax, seed):
+    rng = np.random.default_rng(seed)
+    cl = gen.cmb_like_cl(lmax, 4 * 3438.0 / lmax)
+    return gen.alm_unit_gaussian(rng, lmax) * np.sqrt(cl[gen.alm_ell(lmax)])
+
+
+@pytest.mark.parametrize("nside,lmax", [(4, 8), (16, 32), (64, 100), (64, 128), (128, 256), (200, 400)])
+def test_tc_synthesis_matches_oracle(wf, nside, lmax):
+    """Sizes span one and several 256-pair CTAs (ragged last one), chunks of
+    32 l with a ragged last chunk, and both recurrence forms."""
+    import torch
+
+    a = _cmb_alm(lmax, 100 + nside)
+    ref = oracle.synthesis(nside, lmax, lmax, a)
+    out = {}
+    for prec in ("tf32", "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+        m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        wf.wf_alm2map(plan, T(a), lmax, m)
+        out[prec] = m.cpu().numpy()
+        plan.close()
+    assert rel(out["tf32"], ref) < 2e-5
+    assert rel(out["tf32"], out["mixed"]) < 2e-5
+
+
+@pytest.mark.parametrize("L", [0, 1, 33, 64, 95])
+def test_tc_synthesis_band_limit(wf, L):
+    import torch
+
+    nside, lmax = 48, 96
+    a = _cmb_alm(lmax, 7)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="tf32")
+    m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+    wf.wf_alm2map(plan, T(a), L, m)
+    ref = oracle.synthesis(nside, lmax, L, a)
+    assert rel(m.cpu().numpy(), ref) < 2e-5
+    plan.close()
+
+
+def test_tc_plan_rejections(wf):
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_plan_create("healpix", nside=16, lmax=32, precision="bf16")
+    assert e.value.status == wf.WF_EUNSUPPORTED
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_plan_create("healpix", nside=16, lmax=32, precision="tf32", ncomp=3)
+    assert e.value.status == wf.WF_EUNSUPPORTED
+
+
+def test_tc_solve_matches_mixed_and_reaches_tol(wf):
+    """A whole mixed solve with the tensor-core synthesis: same iteration as
+    the FP32 plan within the mixed tolerance, residual below tol."""
+    import torch
+
+    nside, lmax = 32, 64
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 77))
+    res = {}
+    for prec in ("tf32", "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+        s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-5, s, trace_cap=20000)
+        assert rep["converged"] and rep["final_residual"] < 1e-5
+        res[prec] = s.cpu().numpy()
+        plan.close()
+    assert rel(res["tf32"], res["mixed"]) < 1e-4
+
+
+def _pair_items(nside, lmax, nmaps, seed):
+    """nmaps maps of one noise model, each a Wiener filter plus a
+    fluctuation solve (Sect. 2.3): 2 nmaps items of one geometry."""
+    import torch
+
+    P, basis, d0, nu, tau = healpix_case(nside, lmax, seed)
+    items = []
+    for j in range(nmaps):
+        rng = np.random.default_rng(seed + 31 * j)
+        d = basis.synth(gen.alm_unit_gaussian(rng, lmax) * np.sqrt(P["c_ell"][gen.alm_ell(lmax)])) + \
+            np.sqrt(P["noise_var"]) * rng.standard_normal(P["noise_var"].size)
+        common = {"noise_var": T(P["noise_var"]), "mask": T(P["mask"]), "C_ell": T(P["c_ell"]), "tol": 1e-5}
+        items.append(dict(common, kind="wf", d=T(d),
+                          s_out=torch.full((d.size,), float("nan"), dtype=torch.float64, device="cuda")))
+        items.append(dict(common, kind="fluct", g1=T(rng.standard_normal(d.size)),
+                          g2=T(np.ascontiguousarray(gen.alm_unit_gaussian(rng, lmax), dtype=np.complex128)),
+                          s_out=torch.full((d.size,), float("nan"), dtype=torch.float64, device="cuda")))
+    return items
+
+
+def _alone(w, nside, lmax, prec, it):
+    import torch
+
+    plan = w.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+    s = torch.empty_like(it["s_out"])
+    if it["kind"] == "wf":
+        rep = w.wf_solve(plan, it["d"], it["noise_var"], it["mask"], it["C_ell"], it["tol"], s, trace_cap=20000)
+    else:
+        rep = w.wf_fluct(plan, it["noise_var"], it["mask"], it["C_ell"], it["g1"], it["g2"], it["tol"], s,
+                         trace_cap=20000)
+    plan.close()
+    return s.cpu().numpy(), rep
+
+
+@pytest.mark.parametrize("nmaps", [1, 3, 9])
+def test_tc_batch_columns(wf, nmaps):
+    """Wiener-filter + fluctuation pairs of one geometry in wf_solve_batch:
+    the tensor-core synthesis of every item runs in one launch per step (the
+    items are the columns of one contraction; 9 maps = 18 columns span two
+    launches of at most 16), and each item's result equals the same solve
+    run alone (the columns do not interact: same iterations, same lambda
+    trace, maps equal to 1e-12)."""
+    nside, lmax = 32, 64
+    items = _pair_items(nside, lmax, nmaps, gen.seed_for(4, 40 + nmaps))
+    alone = [_alone(wf, nside, lmax, "tf32", it) for it in items]
+    plans = [wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="tf32") for _ in items]
+    reps = wf.wf_solve_batch(plans, items, trace_cap=20000)
+    for it, rep, (s_alone, rep_alone) in zip(items, reps, alone):
+        assert rep["status"] == wf.WF_OK and rep["converged"]
+        assert rep["iters"] == rep_alone["iters"]
+        np.testing.assert_array_equal(rep["lambda_trace"], rep_alone["lambda_trace"])
+        assert rel(it["s_out"].cpu().numpy(), s_alone) < 1e-12
+    # launches: one group synthesis per step for up to 16 columns, counted on the group's first item
+    ls = [r["kernel_launches"]["leg_syn"] for r in reps]
+    ls_alone = [r["kernel_launches"]["leg_syn"] for _, r in alone]
+    assert sum(ls) < sum(ls_alone) or len(items) == 1
+    for p in plans:
+        p.close()
