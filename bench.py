@@ -86,6 +86,12 @@ def parse():
     ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3],
                     help="1: flat 128x128 FP64 (us per iteration, time to tol); 2: HEALPix nside 512 / lmax 1024 "
                          "FP64 (time to tol, p50/p99); 3: the nside 2048 headline (default)")
+    ap.add_argument("--columns", type=int, default=0,
+                    help="many maps of one geometry: N maps of one noise model, each a Wiener filter plus a "
+                         "fluctuation solve (2N batch columns), tensor-core (tf32) plans against FP32 plans")
+    ap.add_argument("--columns-nside", type=int, default=1024)
+    ap.add_argument("--columns-iters", type=int, default=30,
+                    help="full-band lambda = 1 iterations per timed batch (0: solve every column to --tol)")
     ap.add_argument("--full-band-iters", type=int, default=0,
                     help="replay this many lambda = 1, L = lmax iterations instead of the cooling schedule "
                          "(steady-state timing and profiling)")
@@ -694,6 +700,91 @@ def run_batch(args):
     return 0
 
 
+def run_columns(args):
+    """N maps of one geometry and noise model (the temperature analogue of the batched
+    constrained realisations: each map a Wiener filter plus its fluctuation solve, Sect. 2.3)
+    as 2N columns of one wf_solve_batch.  Tensor-core plans (tf32) share one synthesis launch
+    per step over up to 16 columns; FP32 plans run their own kernels per column.  A step is
+    one batch of --columns-iters full-band lambda = 1 iterations of every column (or, with
+    --columns-iters 0, a solve of every column to --tol)."""
+    import torch
+
+    import paper_1210_4931_gb300 as wf
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    wf.load()
+    nside = args.columns_nside
+    lmax = 2 * nside
+    nm = args.columns
+    P = gen.healpix_problem(nside, lmax, gen.seed_for(4, 1), fwhm_arcmin=13.0, b_cut_deg=20.0, n_disks=500,
+                            disk_radius_deg=0.6)
+    T = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    helper = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="fp64")
+    npix = helper.npix
+    items = []
+    common = {"noise_var": T(P["noise_var"]), "mask": T(P["mask"]), "C_ell": T(P["c_ell"]), "tol": args.tol}
+    for j in range(nm):
+        rng = np.random.default_rng(gen.seed_for(4, 100 + j))
+        a = gen.alm_unit_gaussian(rng, lmax) * np.sqrt(P["c_ell"][gen.alm_ell(lmax)])
+        s = torch.empty(npix, dtype=torch.float64, device=dev)
+        wf.wf_alm2map(helper, T(a), lmax, s)
+        d = s + T(np.sqrt(P["noise_var"]) * rng.standard_normal(npix))
+        items.append(dict(common, kind="wf", d=d, s_out=torch.empty(npix, dtype=torch.float64, device=dev)))
+        items.append(dict(common, kind="fluct", g1=T(rng.standard_normal(npix)),
+                          g2=T(np.ascontiguousarray(gen.alm_unit_gaussian(rng, lmax), dtype=np.complex128)),
+                          s_out=torch.empty(npix, dtype=torch.float64, device=dev)))
+    helper.close()
+    stream = torch.cuda.current_stream()
+    out, maps = {}, {}
+    clocks = Clocks(0)
+    for prec in ("mixed", "tf32"):
+        plans = [wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec) for _ in items]
+        wf.wf_plan_autotune(plans[0], reps=2)
+        t0, t1 = wf.wf_plan_tiles(plans[0])
+        for pl in plans:
+            if args.columns_iters > 0:
+                wf.wf_set_schedule(pl, [1.0] * args.columns_iters, [lmax] * args.columns_iters)
+            else:
+                wf.wf_set_options(pl, maxiter=args.maxiter)
+        for _ in range(max(1, args.warmup)):
+            wf.wf_solve_batch(plans, items)
+        torch.cuda.synchronize()
+        if prec == "tf32":
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts, reps = [], None
+        for _ in range(max(1, args.steps)):
+            e0.record(stream)
+            reps = wf.wf_solve_batch(plans, items)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        if prec == "tf32":
+            out["clocks"] = clocks.stop()
+        iters = sum(r["iters"] for r in reps)
+        t = float(np.median(ts))
+        out[prec] = {"ms_per_batch": t, "column_iters": iters, "column_iters_per_s": iters / (t / 1e3),
+                     "ms_per_column_iteration": t / iters, "launches_per_batch": int(sum(r["launches"] for r in reps)),
+                     "converged": int(sum(r["converged"] for r in reps)), "tiles": [t0, t1]}
+        maps[prec] = [it["s_out"].cpu().numpy() for it in items]
+        for pl in plans:
+            pl.close()
+    diff = max(float(np.max(np.abs(a - b)) / np.max(np.abs(b))) for a, b in zip(maps["tf32"], maps["mixed"]))
+    res = {"metric": "column iterations/s: %d maps x (Wiener filter + fluctuation) of one geometry, nside %d / "
+                     "lmax %d" % (nm, nside, lmax), "unit": "column-iter/s", "value": out["tf32"]["column_iters_per_s"],
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64",
+           "data": "synthetic", "columns": 2 * nm,
+           "config": {"workload": "columns_T_nside%d_%dmaps" % (nside, nm), "iters_per_batch": args.columns_iters,
+                      "tol": args.tol, "recipe": "13' beam, |b| < 20 deg + 500 disks of 0.6 deg, one noise model",
+                      "l2": "inputs (%d MB) larger than L2" % (2 * nm * npix * 8 // (1 << 20))},
+           "tf32_tensor_core": out["tf32"], "fp32_fma": out["mixed"],
+           "speedup_tf32_vs_fp32": out["mixed"]["ms_per_batch"] / out["tf32"]["ms_per_batch"],
+           "max_rel_diff_tf32_vs_fp32_maps": diff, "clocks": out.get("clocks")}
+    print(json.dumps(res))
+    return 0
+
+
 def run_pol_batch(args):
     """Batched polarised constrained realisations: each (I, Q, U) map is a
     Wiener-filter solve plus a fluctuation solve (s_CR = s_WF + f), the pairs of
@@ -954,6 +1045,8 @@ def main():
         return run_serve(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.columns > 0:
+        return run_columns(args)
     if args.pol_batch > 0:
         return run_pol_batch(args)
     return run_ours(args)

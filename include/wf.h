@@ -68,7 +68,9 @@ typedef enum {
                                hi*hi + hi*lo + lo*hi accumulated in FP32 ("3xTF32", FP32-grade accuracy).
                                Maps of one geometry in one wf_solve_batch share the recurrence (one launch).
                                Temperature HEALPix plans (ncomp = 1) */
-    WF_PREC_MIXED_SPLITBF16 = 3 /* reserved: the same contraction with BF16 pieces (WF_EUNSUPPORTED) */
+    WF_PREC_MIXED_SPLITBF16 = 3 /* as MIXED_TF32 with BF16 operands: each value split into three BF16 pieces
+                                   (successive round-to-nearest of the exact remainders, ~24 significant bits)
+                                   and the six products of total order <= 2 accumulated in FP32 */
 } wf_precision;
 
 typedef struct {

@@ -1549,22 +1549,23 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
             for (size_t u = 0; u < cfg.size() && st == WF_OK; ++u) {
                 const int i0 = cfg[u].first;
                 wf_plan p0 = plans[i0];
-                if (p0->prec != WF_PREC_MIXED_TF32 || R[i0].rigorous || group_of[i0] >= 0) continue;
+                if (!tc_prec(p0->prec) || R[i0].rigorous || group_of[i0] >= 0) continue;
                 std::vector<int> mem{i0};
                 for (size_t v = u + 1; v < cfg.size() && (int)mem.size() < TC_MAX_COLUMNS; ++v) {
                     const int j = cfg[v].first;
                     wf_plan pj = plans[j];
-                    if (group_of[j] < 0 && pj->prec == WF_PREC_MIXED_TF32 && !R[j].rigorous &&
+                    if (group_of[j] < 0 && pj->prec == p0->prec && !R[j].rigorous &&
                         pj->nside == p0->nside && pj->lmax == p0->lmax && pj->tab.lc_mx == p0->tab.lc_mx)
                         mem.push_back(j);
                 }
                 std::vector<const double2 *> ga;
-                std::vector<float2 *> gG;
+                std::vector<float2 *> gG, gca;
                 std::vector<int> gL;
                 int Lmax = 0;
                 for (int j : mem) {
                     group_of[j] = ngroups;
                     ga.push_back(plans[j]->ws.a);
+                    gca.push_back(plans[j]->ws.ca32);
                     gG.push_back((float2 *)plans[j]->ws.G);
                     gL.push_back(R[j].L);
                     Lmax = std::max(Lmax, R[j].L);
@@ -1573,7 +1574,7 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
                 for (int f = 0; f < WF_NK; ++f) k0[f] = p0->kcnt[f];
                 const int fam = p0->kfam;
                 p0->kfam = WF_K_LEG_SYN;
-                st = hp_tc_synthesis(p0, (int)mem.size(), ga.data(), gG.data(), gL.data(), Lmax, origin);
+                st = hp_tc_synthesis(p0, (int)mem.size(), ga.data(), gca.data(), gG.data(), gL.data(), Lmax, origin);
                 p0->kfam = fam;
                 for (int f = 0; f < WF_NK; ++f) {
                     group_cnt[i0][f] = p0->kcnt[f] - k0[f];
@@ -1785,9 +1786,7 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
     if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32 && prec != WF_PREC_MIXED_TF32 &&
         prec != WF_PREC_MIXED_SPLITBF16)
         return set_error(WF_EINVAL, "unknown precision");
-    if (prec == WF_PREC_MIXED_SPLITBF16)
-        return set_error(WF_EUNSUPPORTED, "the split-BF16 tensor-core contraction is not built");
-    if (prec == WF_PREC_MIXED_TF32 && (g->kind != WF_GEOM_HEALPIX || g->ncomp == 3))
+    if (tc_prec(prec) && (g->kind != WF_GEOM_HEALPIX || g->ncomp == 3))
         return set_error(WF_EUNSUPPORTED, "tensor-core plans are temperature HEALPix plans");
     wf_plan p = new (std::nothrow) wf_plan_s();
     if (!p) return set_error(WF_ENOMEM, "host allocation");

@@ -101,6 +101,7 @@ struct Workspace {
     void *scr = nullptr;          // per-CTA Bluestein scratch (2 * max Bluestein n complex per CTA)
     float2 *Glow = nullptr;       // mixed: FP64-block synthesis coefficients, rounded to FP32 [pair][glow_cap][hemisphere]
     double2 *b_low = nullptr;     // mixed: FP64-block analysis output (alm layout, m < lc)
+    float2 *ca32 = nullptr;       // tensor-core plans: c a_lm in FP32, the synthesis B operand's source
     double *part_pix = nullptr;   // per ring-pair partial sums
     double *part_harm = nullptr;  // per m: [chi2_h, resid^2, x^T S^-1 x, x^T S^-2 x]
     double4 *epi = nullptr;       // per l: factors of the harmonic blend (Eq. 4) for the current lambda
@@ -246,9 +247,12 @@ wf_status hp_legendre_analysis(wf_plan p, int L, LegMode mode, const BlendArgs &
                                double2 *out);
 // tensor-core transforms (wf_tc.cu): ncols columns sharing p's geometry, tables and FP64 block
 constexpr int TC_MAX_COLUMNS = 16;
-wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 *const *G, const int *L, int Lmax,
-                          cudaStream_t stream);
-size_t tc_syn_smem(int nc);
+// precisions whose Legendre synthesis runs on the tensor cores
+inline bool tc_prec(wf_precision p) { return p == WF_PREC_MIXED_TF32 || p == WF_PREC_MIXED_SPLITBF16; }
+wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 *const *ca, float2 *const *G,
+                          const int *L, int Lmax, cudaStream_t stream);
+size_t tc_syn_smem(int nc, int L);
+wf_status tc_prepare(int lmax);
 
 // ring transforms (wf_ring.cu)
 wf_status hp_build_ring_tables(wf_plan p);

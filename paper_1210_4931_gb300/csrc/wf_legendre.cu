@@ -1563,6 +1563,10 @@ wf_status hp_build_legendre_tables(wf_plan p, const std::vector<double> &xpair, 
             return st;
         if ((st = raise_smem_limit((const void *)k_lowana_df, (size_t)((np + 31) & ~31) * sizeof(float4))) != WF_OK)
             return st;
+        if (tc_prec(p->prec)) {
+            if ((st = tc_prepare(lmax)) != WF_OK) return st;
+            if ((st = plan_alloc(p, (void **)&p->ws.ca32, nalm * sizeof(float2))) != WF_OK) return st;
+        }
     } else {
         if ((st = raise_smem_limit((const void *)k_legsyn_df, syn_df_smem(lmax))) != WF_OK) return st;
         if ((st = raise_smem_limit((const void *)k_legana_df, ana_df_smem(lmax))) != WF_OK) return st;
@@ -1684,10 +1688,10 @@ wf_status hp_legendre_synthesis(wf_plan p, const double2 *alm, int L)
                       : launch_syn64<float>(p, alm, L, t.lc_mx, p->ws.Glow, t.glow_cap, p->aux);
         if (st != WF_OK) return st;
     }
-    if (p->prec == WF_PREC_MIXED_TF32) {
+    if (tc_prec(p->prec)) {
         // in a batch step the group launch (wf_solve_batch) has written G already
         float2 *G = (float2 *)p->ws.G;
-        st = p->tc_deferred ? WF_OK : hp_tc_synthesis(p, 1, &alm, &G, &L, L, p->stream);
+        st = p->tc_deferred ? WF_OK : hp_tc_synthesis(p, 1, &alm, &p->ws.ca32, &G, &L, L, p->stream);
     } else {
         switch (p->tile_syn) {
         case 2: st = launch_syn_mx<2>(p, alm, L); break;

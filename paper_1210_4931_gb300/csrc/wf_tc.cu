@@ -1,5 +1,5 @@
 // Tensor-core Legendre transforms (tcgen05, sm_103a) for plans whose
-// precision is WF_PREC_MIXED_TF32: the per-m contraction of the basis change
+// precision is WF_PREC_MIXED_TF32 or WF_PREC_MIXED_SPLITBF16: the per-m contraction of the basis change
 // (Sect. 2.1; the O(nside lmax^2) cost of Sect. 3) as a dense matrix product
 // on the 5th-generation tensor cores, for one or several columns (maps of one
 // geometry: a solve alone, or the Wiener-filter and fluctuation solves of a
@@ -13,10 +13,10 @@
 //
 // Arithmetic ("3xTF32"): the FP32 recurrence value mu (mu form, lambda = c mu,
 // c folded into B) and the FP32 value c a are each split into a TF32 head and
-// an FP32 tail (x = hi + lo exactly, hi = x rounded to 10 explicit mantissa
+// an FP32 tail (x = hi + lo exactly, hi = x truncated to 10 explicit mantissa
 // bits); the products hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor
 // memory.  The dropped lo*lo term and the tails' own truncation to TF32 are
-// below 2^-21 of each product, so the contraction is as accurate as the FP32
+// below 2^-20 of each product, so the contraction is as accurate as the FP32
 // FMA kernels.
 //
 // Layout on chip (one CTA = two M = 128 tiles of ring pairs, 256 threads, a
@@ -32,6 +32,8 @@
 // The MMAs of chunk q run while the threads compute chunk q + 1's recurrence
 // in registers; the threads wait on the chunk's mbarrier (bounded) before
 // they overwrite its operands.
+#include <cuda_bf16.h>
+
 #include <cstdint>
 #include <cstdio>
 
@@ -66,18 +68,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: kind::tf32, FP32 accumulator, A and B K-major
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
                                             uint32_t accumulate)
 {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -117,6 +123,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 {
     asm volatile(
@@ -126,27 +139,66 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
         : "r"(taddr));
 }
 
-__device__ __forceinline__ uint32_t tf32_head(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// x = hi + lo exactly; hi has a TF32 mantissa
+// x = hi + lo exactly: hi keeps the sign, exponent and top 10 mantissa bits of x
+// (the TF32 head, by truncation: one logical operation), lo = x - hi is exact in
+// FP32 with |lo| < 2^-10 |x|; the tensor core truncates lo to TF32 in turn, an
+// error below 2^-21 |x|
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
 {
-    hi = tf32_head(x);
+    hi = __float_as_uint(x) & 0xFFFFE000u;
     lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
-// ---------------------------------------------------------------------------
-// B operand tile of a chunk: NC rows (n) x 16 k, K-major core matrices with
-// the K-direction core matrices NC/8 * 128 bytes apart (k-group major)
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t b_offset(int n, int k, int nc)
+// x = b0 + b1 + b2 + (below 2^-24 |x|): three BF16 pieces by successive round-
+// to-nearest of the exact FP32 remainders (8 significant bits each)
+__device__ __forceinline__ void split_bf16(float x, uint16_t (&b)[3])
 {
-    return (uint32_t)((k >> 2) * (nc >> 3) * 128 + (n >> 3) * 128 + (n & 7) * 16 + (k & 3) * 4);
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h0);
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(h1);
+    b[0] = __bfloat16_as_ushort(h0);
+    b[1] = __bfloat16_as_ushort(h1);
+    b[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+
+// The two arithmetic variants of the contraction.
+//   KIND 0 (WF_PREC_MIXED_TF32): pieces (hi, lo) in TF32, products hi*hi + hi*lo + lo*hi.
+//   KIND 1 (WF_PREC_MIXED_SPLITBF16): pieces (b0, b1, b2) in BF16, the six products of total
+//     order <= 2 (b0 b0, b0 b1, b1 b0, b0 b2, b1 b1, b2 b0); the dropped terms are below
+//     2^-24 of each product.
+// Both take 32 bytes of K per instruction (8 TF32 or 16 BF16), i.e. 8 tensor-memory columns of
+// the A operand; per chunk of 16 k per parity: 2 (TF32) or 1 (BF16) K steps.
+template <int KIND> struct TcArith;
+template <> struct TcArith<0> {
+    static constexpr int PIECES = 2, EB = 4, KSTEPS = 2, ACOLS = 16, NPROD = 3;
+    // product u: A piece pa(u) times B piece pb(u)
+    __host__ __device__ static constexpr int pa(int u) { return u == 2 ? 1 : 0; }
+    __host__ __device__ static constexpr int pb(int u) { return u == 1 ? 1 : 0; }
+    static constexpr uint32_t FMT = 2u;  // TF32
+};
+template <> struct TcArith<1> {
+    static constexpr int PIECES = 3, EB = 2, KSTEPS = 1, ACOLS = 8, NPROD = 6;
+    __host__ __device__ static constexpr int pa(int u) { return u == 2 ? 1 : u == 4 ? 1 : u == 5 ? 2 : 0; }
+    __host__ __device__ static constexpr int pb(int u) { return u == 1 ? 1 : u == 3 ? 2 : u == 4 ? 1 : 0; }
+    static constexpr uint32_t FMT = 1u;  // BF16
+};
+
+// instruction descriptor: FP32 accumulator, A and B K-major, M x N, operand format fmt
+__host__ __device__ constexpr uint32_t idesc_of(uint32_t fmt, int M, int N)
+{
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// B operand tile of a chunk: NC rows (n) x 16 k, K-major core matrices (8 rows
+// x 16 bytes) with the K-direction core matrices NC/8 * 128 bytes apart
+// (k-group major); eb = bytes per element
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t b_offset(int n, int k, int nc, int eb)
+{
+    const int t = 16 / eb;  // elements per 16 bytes
+    return (uint32_t)((k / t) * (nc >> 3) * 128 + (n >> 3) * 128 + (n & 7) * 16 + (k % t) * eb);
 }
 
 struct TcSynArgs {
@@ -156,7 +208,7 @@ struct TcSynArgs {
     const int *ls;                // per (m, pair): first l of the FP32 recurrence (> lmax: none)
     const float *s0, *s1;         // mu at ls and ls + 1
     const float *xp, *wp;         // per pair: x = cos theta and w = 1 - x
-    const double2 *a[TC_MAXC];    // per column: a_lm (m-major)
+    const float2 *ca[TC_MAXC];    // per column: c a_lm rounded to FP32 (zero above the column's band limit)
     float2 *G[TC_MAXC];           // per column: ring coefficients [pair][m][hemisphere]
     int L[TC_MAXC];               // per column: band limit
     int *err;                     // set when a bounded wait gives up
@@ -183,7 +235,7 @@ __device__ __forceinline__ void tc_step(float A0, float B0, float A1, float B1, 
     }
 }
 
-template <bool DIFF>
+template <bool DIFF, bool INJ>
 __device__ __forceinline__ void tc_chunk(int l0, int ls, float s0, float s1, float x, float w, const float4 *coef,
                                          float &Sa, float &Sb, float (&mu)[TC_KC])
 {
@@ -192,7 +244,7 @@ __device__ __forceinline__ void tc_chunk(int l0, int ls, float s0, float s1, flo
         const float4 ab = coef[j];
         float v0, v1;
         tc_step<DIFF>(ab.x, ab.y, ab.z, ab.w, x, w, Sa, Sb, v0, v1);
-        if (l0 + 2 * j == ls) {
+        if (INJ && l0 + 2 * j == ls) {
             v0 = s0;
             v1 = s1;
             Sa = DIFF ? s1 - s0 : s0;
@@ -203,12 +255,13 @@ __device__ __forceinline__ void tc_chunk(int l0, int ls, float s0, float s1, flo
     }
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
 {
+    using AR = TcArith<KIND>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    __shared__ float4 coef[TC_KC / 2];  // (A_l, B_l, A_l+1, B_l+1) per double step of the chunk
     __shared__ int qmin_s;
     const int m = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -249,10 +302,35 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     }
     const bool diff = __shfl_sync(0xffffffffu, x > TC_X_DIFF ? 1 : 0, 0) != 0;  // one form per warp
 
-    // shared B operand: 4 tiles (E hi, E lo, O hi, O lo) of nc x 16 tf32
-    const uint32_t btile = (uint32_t)nc * 64;
-    uint32_t *B = reinterpret_cast<uint32_t *>(smem);
-    for (int i = tid; i < 4 * nc * 16; i += TC_THREADS) B[i] = 0u;  // padding rows stay zero
+    // shared B operand: 2 PIECES tiles ([parity][piece]) of nc x 16 elements, then the recurrence
+    // coefficients (A_l, B_l, A_l+1, B_l+1) of every double step of the chunks this CTA runs,
+    // indexed by (l - m) / 2 (zero past lmax: those terms have B = 0)
+    const uint32_t btile = (uint32_t)nc * 16 * AR::EB;
+    unsigned char *B = smem;
+    float4 *coef = reinterpret_cast<float4 *>(smem + 2 * AR::PIECES * btile);
+    for (int i = tid; i < (int)(2 * AR::PIECES * btile / 4); i += TC_THREADS)
+        reinterpret_cast<uint32_t *>(B)[i] = 0u;  // padding rows stay zero
+    for (int j = 16 * q0 + tid; j < 16 * (q1 + 1); j += TC_THREADS) {
+        const int la = m + 2 * j, lb = la + 1;
+        coef[j] = make_float4(la <= P.lmax ? P.A32[base + (la - m)] : 0.f, la <= P.lmax ? P.B32[base + (la - m)] : 0.f,
+                              lb <= P.lmax ? P.A32[base + (lb - m)] : 0.f, lb <= P.lmax ? P.B32[base + (lb - m)] : 0.f);
+    }
+    // B values (c a of one column at one l) this thread stages: items tid and tid + 256 of a chunk
+    // (ncols x 32 items), loaded one chunk ahead so that their latency hides behind the recurrence
+    const int nitems = P.ncols * TC_KC;
+    float2 pa[2];
+    auto prefetch = [&](int q) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int it = tid + r * TC_THREADS;
+            pa[r] = make_float2(0.f, 0.f);
+            if (it < nitems && q <= q1) {
+                const int c = it / TC_KC, l = m + TC_KC * q + it % TC_KC;
+                if (l <= P.lmax) pa[r] = P.ca[c][base + (l - m)];
+            }
+        }
+    };
+    prefetch(q0);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -266,87 +344,119 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    // columns: tile t: D_E [2 nc t, 2 nc t + nc), D_O [+ nc, + 2 nc); A at 4 nc + 64 t
+    // columns: tile t: D_E [2 nc t, 2 nc t + nc), D_O [+ nc, + 2 nc); A at 4 nc + 64 t, laid out
+    // [parity][piece] in blocks of ACOLS columns (16 k each)
     const uint32_t dE = tmem + 2u * nc * tile, dO = dE + nc;
     const uint32_t aT = tmem + 4u * nc + 64u * tile;
-    const uint32_t idesc = idesc_tf32(128, nc);
+    const uint32_t idesc = idesc_of(AR::FMT, 128, nc);
     const uint32_t lbo = (uint32_t)(nc >> 3) * 128, sbo = 128;
     const uint32_t bsm = smem_addr(B);
 
+    // B descriptors (loop-invariant: one operand buffer): [parity][piece][k step]
+    uint64_t bdesc[2][AR::PIECES][AR::KSTEPS];
+#pragma unroll
+    for (int par = 0; par < 2; ++par)
+#pragma unroll
+        for (int h = 0; h < AR::PIECES; ++h)
+#pragma unroll
+            for (int s2 = 0; s2 < AR::KSTEPS; ++s2)
+                bdesc[par][h][s2] =
+                    smem_desc(bsm + (uint32_t)(AR::PIECES * par + h) * btile + 2 * s2 * lbo, lbo, sbo);
     float Sa = 0.f, Sb = 0.f;
     bool ok = true;
     uint32_t phase = 0;
     for (int q = q0; q <= q1; ++q) {
         const int l0 = m + TC_KC * q;
-        // recurrence coefficients of the chunk (zero past lmax: those terms have B = 0)
-        __syncthreads();  // the previous chunk's recurrence has read coef
-        if (tid < TC_KC / 2) {
-            const int la = l0 + 2 * tid, lb = la + 1;
-            coef[tid] = make_float4(la <= P.lmax ? P.A32[base + (la - m)] : 0.f,
-                                    la <= P.lmax ? P.B32[base + (la - m)] : 0.f,
-                                    lb <= P.lmax ? P.A32[base + (lb - m)] : 0.f,
-                                    lb <= P.lmax ? P.B32[base + (lb - m)] : 0.f);
-        }
-        __syncthreads();
         float mu[TC_KC];
-        if (diff) tc_chunk<true>(l0, ls, s0, s1, x, w, coef, Sa, Sb, mu);
-        else tc_chunk<false>(l0, ls, s0, s1, x, w, coef, Sa, Sb, mu);
+        // seeds enter only in the chunk holding a lane's first l: one test per warp and chunk
+        const bool inj = __any_sync(0xffffffffu, ls >= l0 && ls < l0 + TC_KC);
+        if (diff) {
+            if (inj) tc_chunk<true, true>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
+            else tc_chunk<true, false>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
+        } else {
+            if (inj) tc_chunk<false, true>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
+            else tc_chunk<false, false>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
+        }
         // the previous chunk's MMAs have read A (tensor memory) and B (shared memory)
         if (q > q0) {
             ok = ok && mbar_wait(&mbar, phase, P.err);
             phase ^= 1u;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        {
-            uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j], hi[j], lo[j]);
-            tmem_st16(aT + lane_base + 0, hi);
-            tmem_st16(aT + lane_base + 16, lo);
+        for (int par = 0; par < 2; ++par) {
+            if constexpr (KIND == 0) {
+                uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j + 1], hi[j], lo[j]);
-            tmem_st16(aT + lane_base + 32, hi);
-            tmem_st16(aT + lane_base + 48, lo);
+                for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j + par], hi[j], lo[j]);
+                tmem_st16(aT + lane_base + 32 * par, hi);
+                tmem_st16(aT + lane_base + 32 * par + 16, lo);
+            } else {
+                uint32_t pk[3][8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    uint16_t e0[3], e1[3];
+                    split_bf16(mu[4 * j + par], e0);      // k = 2 j     (l - l0 = 4 j + par)
+                    split_bf16(mu[4 * j + 2 + par], e1);  // k = 2 j + 1
+#pragma unroll
+                    for (int h = 0; h < 3; ++h) pk[h][j] = (uint32_t)e0[h] | ((uint32_t)e1[h] << 16);
+                }
+#pragma unroll
+                for (int h = 0; h < 3; ++h) tmem_st8(aT + lane_base + 24 * par + 8 * h, pk[h]);
+            }
         }
         // B: (c a) of every column for the chunk's 32 l, split the same way
-        for (int it = tid; it < P.ncols * TC_KC; it += TC_THREADS) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int it = tid + r * TC_THREADS;
+            if (it >= nitems) break;
             const int c = it / TC_KC, i = it % TC_KC;
-            const int l = l0 + i;
-            float vr = 0.f, vi = 0.f;
-            if (l <= P.L[c] && l <= P.lmax) {
-                const double2 a = P.a[c][base + (l - m)];
-                const double cc = P.c64[base + (l - m)];
-                vr = (float)(a.x * cc);
-                vi = (float)(a.y * cc);
+            const int k = i >> 1, par = i & 1;
+            const uint32_t offr = b_offset(2 * c, k, nc, AR::EB), offi = b_offset(2 * c + 1, k, nc, AR::EB);
+            unsigned char *Bp = B + (size_t)(AR::PIECES * par) * btile;
+            if constexpr (KIND == 0) {
+                uint32_t rh, rl, ih, il;
+                split_tf32(pa[r].x, rh, rl);
+                split_tf32(pa[r].y, ih, il);
+                *reinterpret_cast<uint32_t *>(Bp + offr) = rh;
+                *reinterpret_cast<uint32_t *>(Bp + offi) = ih;
+                *reinterpret_cast<uint32_t *>(Bp + btile + offr) = rl;
+                *reinterpret_cast<uint32_t *>(Bp + btile + offi) = il;
+            } else {
+                uint16_t br[3], bi[3];
+                split_bf16(pa[r].x, br);
+                split_bf16(pa[r].y, bi);
+#pragma unroll
+                for (int h = 0; h < 3; ++h) {
+                    *reinterpret_cast<uint16_t *>(Bp + h * btile + offr) = br[h];
+                    *reinterpret_cast<uint16_t *>(Bp + h * btile + offi) = bi[h];
+                }
             }
-            uint32_t rh, rl, ih, il;
-            split_tf32(vr, rh, rl);
-            split_tf32(vi, ih, il);
-            const int k = i >> 1;
-            uint32_t *Bp = B + (size_t)(i & 1) * 2 * (btile / 4);  // E tiles first, then O tiles
-            Bp[b_offset(2 * c, k, nc) / 4] = rh;
-            Bp[b_offset(2 * c + 1, k, nc) / 4] = ih;
-            Bp[(btile + b_offset(2 * c, k, nc)) / 4] = rl;
-            Bp[(btile + b_offset(2 * c + 1, k, nc)) / 4] = il;
         }
+        prefetch(q + 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc0 = q > q0 ? 1u : 0u;
+#pragma unroll
             for (int t = 0; t < 2; ++t) {
                 const uint32_t dEt = tmem + 2u * nc * t, aTt = tmem + 4u * nc + 64u * t;
+#pragma unroll
                 for (int par = 0; par < 2; ++par) {
                     const uint32_t d = dEt + (par ? nc : 0);
-                    const uint32_t a_hi = aTt + 32u * par, a_lo = a_hi + 16;
-                    const uint32_t b_hi = bsm + (uint32_t)par * 2 * btile, b_lo = b_hi + btile;
-                    for (int s = 0; s < 2; ++s) {  // K = 8 per instruction
-                        const uint32_t acc = (q > q0 || s > 0) ? 1u : 0u;
-                        mma_tf32_ts(d, a_hi + 8 * s, smem_desc(b_hi + 2 * s * lbo, lbo, sbo), idesc, acc);
-                        mma_tf32_ts(d, a_hi + 8 * s, smem_desc(b_lo + 2 * s * lbo, lbo, sbo), idesc, 1u);
-                        mma_tf32_ts(d, a_lo + 8 * s, smem_desc(b_hi + 2 * s * lbo, lbo, sbo), idesc, 1u);
-                    }
+                    const uint32_t a0 = aTt + (uint32_t)(AR::PIECES * AR::ACOLS * par);
+#pragma unroll
+                    for (int s = 0; s < AR::KSTEPS; ++s)
+#pragma unroll
+                        for (int u = 0; u < AR::NPROD; ++u) {
+                            const uint32_t a = a0 + AR::ACOLS * AR::pa(u) + 8 * s;
+                            const uint32_t acc = (s == 0 && u == 0) ? acc0 : 1u;
+                            if constexpr (KIND == 0) mma_tf32_ts(d, a, bdesc[par][AR::pb(u)][s], idesc, acc);
+                            else mma_f16_ts(d, a, bdesc[par][AR::pb(u)][s], idesc, acc);
+                        }
                 }
             }
             mma_commit(&mbar);
@@ -384,18 +494,66 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     }
 }
 
+// c a_lm in FP32 for every column (rounded once from FP64; zero above the column's band
+// limit): the B operand's source
+struct TcPrepArgs {
+    const double2 *a[TC_MAXC];
+    float2 *ca[TC_MAXC];
+    int L[TC_MAXC];
+};
+
+__global__ void k_tc_ca(int lmax, int ncols, const double *__restrict__ c64, TcPrepArgs A)
+{
+    const int m = blockIdx.y;
+    const long long base = tc_mbase(lmax, m);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= lmax - m; j += gridDim.x * blockDim.x) {
+        const double cc = c64[base + j];
+        for (int c = 0; c < ncols; ++c) {
+            float2 v = make_float2(0.f, 0.f);
+            if (m + j <= A.L[c]) {
+                const double2 a = A.a[c][base + j];
+                v = make_float2((float)(a.x * cc), (float)(a.y * cc));
+            }
+            A.ca[c][base + j] = v;
+        }
+    }
+}
+
 }  // namespace
 
-size_t tc_syn_smem(int nc) { return (size_t)4 * nc * 64 + 64; }
+// B tiles (the larger of the two variants: 4 x 64 or 6 x 32 bytes per row) plus the coefficient
+// table of up to L / 32 + 1 chunks
+size_t tc_syn_smem(int nc, int L) { return (size_t)4 * nc * 64 + (size_t)16 * 16 * (L / TC_KC + 1) + 64; }
+
+// raise the synthesis kernels' shared-memory limits for plans up to lmax (at plan creation,
+// outside any stream capture)
+wf_status tc_prepare(int lmax)
+{
+    wf_status st = raise_smem_limit((const void *)k_legsyn_tc<0>, tc_syn_smem(32, lmax));
+    if (st == WF_OK) st = raise_smem_limit((const void *)k_legsyn_tc<1>, tc_syn_smem(32, lmax));
+    return st;
+}
 
 // Synthesis of ncols columns sharing p's geometry and FP32 seeds (every
 // column's plan has p's nside, lmax and FP64 block): one launch on `stream`,
 // counted on p.
-wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 *const *G, const int *L, int Lmax,
-                          cudaStream_t stream)
+wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 *const *ca, float2 *const *G,
+                          const int *L, int Lmax, cudaStream_t stream)
 {
     if (ncols < 1 || ncols > TC_MAXC) return set_error(WF_EINVAL, "tensor-core synthesis: 1..%d columns", TC_MAXC);
     const HpTables &t = p->tab;
+    {
+        TcPrepArgs pa{};
+        for (int c = 0; c < ncols; ++c) {
+            pa.a[c] = a[c];
+            pa.ca[c] = ca[c];
+            pa.L[c] = L[c];
+        }
+        dim3 g((Lmax + 256) / 256, Lmax + 1);
+        k_tc_ca<<<g, 256, 0, stream>>>(p->lmax, ncols, t.c64, pa);
+        WF_COUNT_LAUNCH(p);
+        WF_CUDA(cudaGetLastError());
+    }
     TcSynArgs A{};
     A.lmax = p->lmax;
     A.Lmax = Lmax;
@@ -411,14 +569,15 @@ wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 
     A.xp = t.x32;
     A.wp = t.w32;
     for (int c = 0; c < ncols; ++c) {
-        A.a[c] = a[c];
+        A.ca[c] = ca[c];
         A.G[c] = G[c];
         A.L[c] = L[c];
     }
     A.err = p->ws.tc_err;
-    const size_t sm = tc_syn_smem(A.nc);  // <= 8 KB: below the default limit, no attribute to raise
+    const size_t sm = tc_syn_smem(A.nc, Lmax);  // the limit is raised at plan creation (tc_prepare)
     dim3 grid((p->npairs + TC_THREADS - 1) / TC_THREADS, Lmax + 1);
-    k_legsyn_tc<<<grid, TC_THREADS, sm, stream>>>(A);
+    if (p->prec == WF_PREC_MIXED_SPLITBF16) k_legsyn_tc<1><<<grid, TC_THREADS, sm, stream>>>(A);
+    else k_legsyn_tc<0><<<grid, TC_THREADS, sm, stream>>>(A);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;

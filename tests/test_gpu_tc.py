@@ -1,8 +1,10 @@
-"""Tensor-core (tcgen05) Legendre transforms of WF_PREC_MIXED_TF32 plans
-against the oracle (Sect. 2.1 basis change) and against the FP32 plans.
+"""Tensor-core (tcgen05) Legendre synthesis of WF_PREC_MIXED_TF32 and
+WF_PREC_MIXED_SPLITBF16 plans against the oracle (Sect. 2.1 basis change) and
+against the FP32 plans.
 
-3xTF32 keeps FP32-grade accuracy, so the tolerances are the FP32 path's:
-2e-5 relative (max norm) against the oracle up to nside 128."""
+Both splits keep FP32-grade accuracy (3xTF32: dropped terms below 2^-20 of a
+product; three BF16 pieces with six products: below 2^-23), so the
+tolerances are the FP32 path's: 2e-5 relative (max norm) against the oracle."""
 import numpy as np
 import pytest
 
@@ -30,8 +32,9 @@ def _cmb_alm(lmax, seed):
     return gen.alm_unit_gaussian(rng, lmax) * np.sqrt(cl[gen.alm_ell(lmax)])
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
 @pytest.mark.parametrize("nside,lmax", [(4, 8), (16, 32), (64, 100), (64, 128), (128, 256), (200, 400)])
-def test_tc_synthesis_matches_oracle(wf, nside, lmax):
+def test_tc_synthesis_matches_oracle(wf, nside, lmax, prec):
     """Sizes span one and several 256-pair CTAs (ragged last one), chunks of
     32 l with a ragged last chunk, and both recurrence forms."""
     import torch
@@ -39,23 +42,24 @@ def test_tc_synthesis_matches_oracle(wf, nside, lmax):
     a = _cmb_alm(lmax, 100 + nside)
     ref = oracle.synthesis(nside, lmax, lmax, a)
     out = {}
-    for prec in ("tf32", "mixed"):
-        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+    for pr in (prec, "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=pr)
         m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
         wf.wf_alm2map(plan, T(a), lmax, m)
-        out[prec] = m.cpu().numpy()
+        out[pr] = m.cpu().numpy()
         plan.close()
-    assert rel(out["tf32"], ref) < 2e-5
-    assert rel(out["tf32"], out["mixed"]) < 2e-5
+    assert rel(out[prec], ref) < 2e-5
+    assert rel(out[prec], out["mixed"]) < 2e-5
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
 @pytest.mark.parametrize("L", [0, 1, 33, 64, 95])
-def test_tc_synthesis_band_limit(wf, L):
+def test_tc_synthesis_band_limit(wf, L, prec):
     import torch
 
     nside, lmax = 48, 96
-    a = _cmb_alm(lmax, 7)
-    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="tf32")
+    a = gen.alm_unit_gaussian(np.random.default_rng(7), lmax)  # power at every l, l < 2 included
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
     m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
     wf.wf_alm2map(plan, T(a), L, m)
     ref = oracle.synthesis(nside, lmax, L, a)
@@ -64,15 +68,17 @@ def test_tc_synthesis_band_limit(wf, L):
 
 
 def test_tc_plan_rejections(wf):
-    with pytest.raises(wf.WfError) as e:
-        wf.wf_plan_create("healpix", nside=16, lmax=32, precision="bf16")
-    assert e.value.status == wf.WF_EUNSUPPORTED
-    with pytest.raises(wf.WfError) as e:
-        wf.wf_plan_create("healpix", nside=16, lmax=32, precision="tf32", ncomp=3)
-    assert e.value.status == wf.WF_EUNSUPPORTED
+    for prec in ("tf32", "bf16"):
+        with pytest.raises(wf.WfError) as e:
+            wf.wf_plan_create("healpix", nside=16, lmax=32, precision=prec, ncomp=3)
+        assert e.value.status == wf.WF_EUNSUPPORTED
+        with pytest.raises(wf.WfError) as e:
+            wf.wf_plan_create("flat", n=32, precision=prec)
+        assert e.value.status == wf.WF_EUNSUPPORTED
 
 
-def test_tc_solve_matches_mixed_and_reaches_tol(wf):
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tc_solve_matches_mixed_and_reaches_tol(wf, prec):
     """A whole mixed solve with the tensor-core synthesis: same iteration as
     the FP32 plan within the mixed tolerance, residual below tol."""
     import torch
@@ -80,14 +86,14 @@ def test_tc_solve_matches_mixed_and_reaches_tol(wf):
     nside, lmax = 32, 64
     P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 77))
     res = {}
-    for prec in ("tf32", "mixed"):
-        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
+    for pr in (prec, "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=pr)
         s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
         rep = wf.wf_solve(plan, T(d), T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), 1e-5, s, trace_cap=20000)
         assert rep["converged"] and rep["final_residual"] < 1e-5
-        res[prec] = s.cpu().numpy()
+        res[pr] = s.cpu().numpy()
         plan.close()
-    assert rel(res["tf32"], res["mixed"]) < 1e-4
+    assert rel(res[prec], res["mixed"]) < 1e-4
 
 
 def _pair_items(nside, lmax, nmaps, seed):
@@ -124,8 +130,8 @@ def _alone(w, nside, lmax, prec, it):
     return s.cpu().numpy(), rep
 
 
-@pytest.mark.parametrize("nmaps", [1, 3, 9])
-def test_tc_batch_columns(wf, nmaps):
+@pytest.mark.parametrize("prec,nmaps", [("tf32", 1), ("tf32", 3), ("tf32", 9), ("bf16", 3)])
+def test_tc_batch_columns(wf, prec, nmaps):
     """Wiener-filter + fluctuation pairs of one geometry in wf_solve_batch:
     the tensor-core synthesis of every item runs in one launch per step (the
     items are the columns of one contraction; 9 maps = 18 columns span two
@@ -134,8 +140,8 @@ def test_tc_batch_columns(wf, nmaps):
     trace, maps equal to 1e-12)."""
     nside, lmax = 32, 64
     items = _pair_items(nside, lmax, nmaps, gen.seed_for(4, 40 + nmaps))
-    alone = [_alone(wf, nside, lmax, "tf32", it) for it in items]
-    plans = [wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="tf32") for _ in items]
+    alone = [_alone(wf, nside, lmax, prec, it) for it in items]
+    plans = [wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec) for _ in items]
     reps = wf.wf_solve_batch(plans, items, trace_cap=20000)
     for it, rep, (s_alone, rep_alone) in zip(items, reps, alone):
         assert rep["status"] == wf.WF_OK and rep["converged"]
