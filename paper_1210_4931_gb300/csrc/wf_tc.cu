@@ -19,13 +19,15 @@
 // below 2^-20 of each product, so the contraction is as accurate as the FP32
 // FMA kernels.
 //
-// Layout on chip (one CTA = two M = 128 tiles of ring pairs, 256 threads, a
-// thread per ring pair = per tensor-memory lane):
-//   tensor memory  D_E, D_O of each tile (N = NC columns each, NC = 2 ncols
-//                  rounded up to 16) and the A operand of the current chunk
-//                  of 32 l (per tile: E hi, E lo, O hi, O lo, 16 columns
-//                  each); each thread writes its own lane (tcgen05.st), so the
-//                  recurrence values never pass through shared memory;
+// Layout on chip (one CTA = one M = 128 tile of ring pairs, 128 threads, a
+// thread per ring pair = per tensor-memory lane; 128 tensor-memory columns
+// per CTA, so four CTAs share an SM and one CTA's MMA latency hides behind
+// the others' recurrences):
+//   tensor memory  D_E, D_O (N = NC columns each, NC = 2 ncols rounded up to
+//                  16) and the A operand of the current chunk of 32 l (per
+//                  parity and piece 16 TF32 or 8 packed BF16 columns); each
+//                  thread writes its own lane (tcgen05.st), so the recurrence
+//                  values never pass through shared memory;
 //   shared memory  the B operand of the chunk (E hi, E lo, O hi, O lo; NC
 //                  rows x 16 k, K-major core matrices of 8 rows x 16 bytes)
 //                  and the chunk's recurrence coefficients.
@@ -43,7 +45,9 @@ namespace wf {
 
 namespace {
 
-constexpr int TC_THREADS = 256;   // two M = 128 tiles
+constexpr int TC_THREADS = 128;   // one M = 128 tile: a thread per ring pair and tensor-memory lane
+constexpr int TC_BITEMS = 4;      // B items per thread per chunk (16 columns x 32 l / 128 threads)
+constexpr int TC_TMEM_COLS = 128; // D_E, D_O (nc each, nc <= 32) + the A operand (64 columns)
 constexpr int TC_KC = 32;         // l values per chunk (16 even, 16 odd)
 constexpr int TC_MAXC = TC_MAX_COLUMNS;  // columns (maps) per launch
 constexpr float TC_X_DIFF = 0.4f; // rings with x > 0.4 run the difference form (as the FP32 kernels)
@@ -265,8 +269,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     __shared__ int qmin_s;
     const int m = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int tile = tid >> 7;                 // M tile of this thread's ring pair
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const int p = blockIdx.x * TC_THREADS + tid;
     const int nc = P.nc;
     const long long base = tc_mbase(P.lmax, m);
@@ -318,10 +321,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     // B values (c a of one column at one l) this thread stages: items tid and tid + 256 of a chunk
     // (ncols x 32 items), loaded one chunk ahead so that their latency hides behind the recurrence
     const int nitems = P.ncols * TC_KC;
-    float2 pa[2];
+    float2 pa[TC_BITEMS];
     auto prefetch = [&](int q) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < TC_BITEMS; ++r) {
             const int it = tid + r * TC_THREADS;
             pa[r] = make_float2(0.f, 0.f);
             if (it < nitems && q <= q1) {
@@ -336,7 +339,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tmem_base))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "n"(TC_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -344,10 +348,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    // columns: tile t: D_E [2 nc t, 2 nc t + nc), D_O [+ nc, + 2 nc); A at 4 nc + 64 t, laid out
-    // [parity][piece] in blocks of ACOLS columns (16 k each)
-    const uint32_t dE = tmem + 2u * nc * tile, dO = dE + nc;
-    const uint32_t aT = tmem + 4u * nc + 64u * tile;
+    // columns: D_E [0, nc), D_O [nc, 2 nc); A at 2 nc, laid out [parity][piece] in blocks of
+    // ACOLS columns (16 k each)
+    const uint32_t dE = tmem, dO = dE + nc;
+    const uint32_t aT = tmem + 2u * nc;
     const uint32_t idesc = idesc_of(AR::FMT, 128, nc);
     const uint32_t lbo = (uint32_t)(nc >> 3) * 128, sbo = 128;
     const uint32_t bsm = smem_addr(B);
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         }
         // B: (c a) of every column for the chunk's 32 l, split the same way
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < TC_BITEMS; ++r) {
             const int it = tid + r * TC_THREADS;
             if (it >= nitems) break;
             const int c = it / TC_KC, i = it % TC_KC;
@@ -441,13 +445,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc0 = q > q0 ? 1u : 0u;
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const uint32_t dEt = tmem + 2u * nc * t, aTt = tmem + 4u * nc + 64u * t;
+            {
 #pragma unroll
                 for (int par = 0; par < 2; ++par) {
-                    const uint32_t d = dEt + (par ? nc : 0);
-                    const uint32_t a0 = aTt + (uint32_t)(AR::PIECES * AR::ACOLS * par);
+                    const uint32_t d = dE + (par ? nc : 0);
+                    const uint32_t a0 = aT + (uint32_t)(AR::PIECES * AR::ACOLS * par);
 #pragma unroll
                     for (int s = 0; s < AR::KSTEPS; ++s)
 #pragma unroll
@@ -490,7 +492,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TC_TMEM_COLS)
+                     : "memory");
     }
 }
 
