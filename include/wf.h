@@ -113,6 +113,10 @@ typedef struct {
                            whose FP64 rate is a small fraction of FP32.  Mixed temperature plans: the
                            correction sweeps' transforms run this way unless it is negative, which runs
                            them on the FP64 pipe. */
+    int tile_syn;       /* mixed plans: > 0 sets the FP32 Legendre synthesis tile (2, 4 or 8 ring pairs per
+                           thread) in place of the default or autotuned one; 0 keeps it */
+    int tile_ana;       /* mixed plans: > 0 sets the FP32 Legendre analysis tile (2, 4 or 8 ring pairs per
+                           lane); 0 keeps it */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one

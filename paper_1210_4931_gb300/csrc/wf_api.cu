@@ -1070,6 +1070,16 @@ wf_status hp_end(HpRun &R)
     }
     pr.finish();
     wf_status result = R.result;
+    if (tc_prec(p->prec)) {
+        // a bounded wait of a tensor-core kernel that gave up voids the result
+        int tc_err = 0;
+        WF_CUDA(cudaMemcpyAsync(&tc_err, p->ws.tc_err, sizeof tc_err, cudaMemcpyDeviceToHost, p->stream));
+        WF_CUDA(cudaStreamSynchronize(p->stream));
+        if (tc_err) {
+            WF_CUDA(cudaMemsetAsync(p->ws.tc_err, 0, sizeof(int), p->stream));
+            return set_error(WF_ETIMEOUT, "a tensor-core kernel's bounded wait for its MMAs gave up");
+        }
+    }
     if (result == WF_OK && !R.replay && !R.converged) result = WF_ENOCONV;
     if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", R.last_resid);
     if (result == WF_EDIVERGE && R.chi2_bad) set_error(result, "chi^2 is not finite at iteration %d", R.k);
@@ -1818,7 +1828,10 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
     if (st == WF_OK) {
         if ((st = plan_alloc(p, (void **)&p->ws.scal, 16 * sizeof(double))) == WF_OK &&
             (st = plan_alloc(p, (void **)&p->ws.flag, 16)) == WF_OK &&
-            (st = plan_alloc(p, (void **)&p->ws.tc_err, 16)) == WF_OK) {
+            (st = plan_alloc(p, (void **)&p->ws.tc_err, 16)) == WF_OK &&
+            (st = (cudaMemsetAsync(p->ws.tc_err, 0, 16, p->stream) == cudaSuccess
+                       ? WF_OK
+                       : set_error(WF_ECUDA, "cudaMemsetAsync"))) == WF_OK) {
             if (cudaMallocHost(&p->ws.h_scal, 16 * sizeof(double)) != cudaSuccess)
                 st = set_error(WF_ENOMEM, "pinned host allocation");
         }
@@ -1855,8 +1868,13 @@ wf_status wf_set_options(wf_plan p, const wf_options *opt)
     if (!p) return set_error(WF_EINVAL, "null plan");
     if (opt && (opt->schedule < 0 || opt->schedule > 1))
         return set_error(WF_EINVAL, "schedule must be 0 (heuristic) or 1 (chi^2 bound)");
+    if (opt && ((opt->tile_syn != 0 && opt->tile_syn != 2 && opt->tile_syn != 4 && opt->tile_syn != 8) ||
+                (opt->tile_ana != 0 && opt->tile_ana != 2 && opt->tile_ana != 4 && opt->tile_ana != 8)))
+        return set_error(WF_EINVAL, "tile_syn and tile_ana must be 2, 4 or 8 (0: keep)");
     const long long old_cap = p->opt.mixed_table_bytes;
     p->opt = opt ? *opt : wf_options{};
+    if (p->opt.tile_syn > 0) p->tile_syn = p->opt.tile_syn;
+    if (p->opt.tile_ana > 0) p->tile_ana = p->opt.tile_ana;
     if (p->g.kind == WF_GEOM_HEALPIX && p->prec == WF_PREC_FP64 && p->g.ncomp == 1)
         p->df_legendre = p->opt.fp64_emulation != 0;
     // mixed temperature tables: a forced block (or a changed table cap) takes effect now

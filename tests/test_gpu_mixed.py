@@ -215,3 +215,32 @@ def test_mixed_chi2_bound_schedule(wf):
     r1 = oracle.messenger_solve(basis, nu * d, nu, S, tau, replay=[(1.0, lmax)], a0=out["mixed"][1])
     assert r1["resid"][0] < 3e-6
     assert rel(out["mixed"][2], out["fp64"][2]) < 1e-3
+
+
+@pytest.mark.parametrize("nside,lmax", [(16, 32), (64, 128), (100, 200)])
+def test_tile_variants_agree_with_oracle(wf, nside, lmax):
+    """Every FP32 Legendre tile (2, 4, 8 ring pairs per thread in the synthesis,
+    per lane in the analysis), set through the options, gives the oracle's
+    synthesis and adjoint within the FP32 tolerance."""
+    import torch
+
+    rng = np.random.default_rng(3000 + nside)
+    cl = gen.cmb_like_cl(lmax, 4 * 3438.0 / lmax)
+    a = gen.alm_unit_gaussian(rng, lmax) * np.sqrt(cl[gen.alm_ell(lmax)])
+    m_ref = oracle.synthesis(nside, lmax, lmax, a)
+    f = m_ref + 0.1 * rng.standard_normal(12 * nside * nside)
+    ref = oracle.adjoint_synthesis(nside, lmax, lmax, f)
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision="mixed")
+    for v in (2, 4, 8):
+        wf.wf_set_options(plan, tile_syn=v, tile_ana=v)
+        assert wf.wf_plan_tiles(plan) == (v, v)
+        m = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        wf.wf_alm2map(plan, T(a), lmax, m)
+        assert rel(m.cpu().numpy(), m_ref) < 2e-5, v
+        out = torch.empty(plan.nalm, dtype=torch.complex128, device="cuda")
+        wf.wf_map2alm_adjoint(plan, T(f), lmax, out)
+        assert rel(out.cpu().numpy(), ref) < 2e-5, v
+    with pytest.raises(wf.WfError) as e:
+        wf.wf_set_options(plan, tile_ana=16)
+    assert e.value.status == wf.WF_EINVAL
+    plan.close()

@@ -154,3 +154,29 @@ def test_tc_batch_columns(wf, prec, nmaps):
     assert sum(ls) < sum(ls_alone) or len(items) == 1
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_tc_fluct_matches_mixed(wf, prec):
+    """The fluctuation solve (Eq. 9) with the tensor-core synthesis: its source
+    z = Omega Y (S^-1/2 g2) goes through the same synthesis.  Both plans reach
+    the residual tolerance; the maps agree to the accuracy a 1e-6 residual
+    gives."""
+    import torch
+
+    nside, lmax = 32, 64
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(2, 79))
+    rng = np.random.default_rng(5)
+    g1 = rng.standard_normal(d.size)
+    g2 = np.ascontiguousarray(gen.alm_unit_gaussian(rng, lmax), dtype=np.complex128)
+    res = {}
+    for pr in (prec, "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=pr)
+        f = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        rep = wf.wf_fluct(plan, T(P["noise_var"]), T(P["mask"]), T(P["c_ell"]), T(g1), T(g2), 1e-6, f,
+                          trace_cap=20000)
+        assert rep["converged"] and rep["final_residual"] < 1e-6
+        res[pr] = f.cpu().numpy()
+        plan.close()
+    print("fluct rel diff", prec, rel(res[prec], res["mixed"]))
+    assert rel(res[prec], res["mixed"]) < 1e-3
