@@ -609,6 +609,24 @@ def run_serve(args):
                             "iters_mean": float(np.mean([r["iters"] for r in sel])),
                             "converged": float(np.mean([r["converged"] for r in sel]))}
     ok = sum(1 for r in results.values() if r["status"] in (wf.WF_OK, wf.WF_ENOCONV))
+
+    def lat_of(sel):
+        if not sel:
+            return None
+        x = np.array([r["t_done"] - r["t_submit"] for r in sel])
+        s = np.array([r["t_done"] - r["t_start"] for r in sel])
+        return {"n": len(sel), "p50_ms": float(np.percentile(x, 50) * 1e3), "p99_ms": float(np.percentile(x, 99) * 1e3),
+                "service_p50_ms": float(np.percentile(s, 50) * 1e3),
+                "service_p99_ms": float(np.percentile(s, 99) * 1e3),
+                "iters_mean": float(np.mean([r["iters"] for r in sel]))}
+
+    conv = [r for r in results.values() if r["converged"]]
+    unconv = [r for r in results.values() if not r["converged"]]
+    by_tol = {}
+    for t in (1e-4, 1e-6):
+        sel = [r for r in results.values() if tol_of[r["tag"]] == t]
+        by_tol["%g" % t] = {"n": len(sel), "converged_fraction": float(np.mean([r["converged"] for r in sel]))
+                            if sel else None}
     out = {"metric": "serving: Wiener-filter solves per second, Poisson arrivals, mixed nside 64-1024",
            "value": n / (t_last - t_first), "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
@@ -617,6 +635,7 @@ def run_serve(args):
                              "p99": float(np.percentile(qwait, 99) * 1e3)},
            "offered_rate": args.serve_rate, "achieved_rate": n / (t_last - t_first), "requests": n,
            "ok": ok, "converged_fraction": float(np.mean([r["converged"] for r in results.values()])),
+           "latency_converged": lat_of(conv), "latency_not_converged": lat_of(unconv), "by_tol": by_tol,
            "per_nside": per, "wall_s": wall, "dtype": "f32+f64", "data": "synthetic",
            "config": {"workload": "serving_T_nside64-1024_poisson", "slots": args.serve_slots,
                       "budget_gb": args.serve_budget_gb, "maxiter": args.serve_maxiter,

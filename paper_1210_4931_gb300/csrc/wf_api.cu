@@ -1744,6 +1744,7 @@ long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging
     if (f32) b += np * ((lmax + 1) / 8 + 1) * 2 * 8;             // FP64-block coefficients (stored FP32)
     if (f32) b += std::min(hp_low_table_bytes(lmax, (int)np, (lmax + 1) / 8 + 1), 2LL << 30) + (lmax + 2) * 8;  // its table
     if (staging) b += npix * (3 * 8 + 1) + (lmax + 1) * 8 + nalm * 16 * 2 + npix * 8;
+    if (tc_prec(prec)) b += nalm * 8;                            // c a_lm in FP32 (tensor-core synthesis)
     if (ncomp == 3) {  // polarisation (PolState)
         const long long lcap = (lmax + 1) / 8 + 1;                  // FP64-block allowance, as above
         b += nalm * 8 * 3 + ns * (4 + 32);                           // al, be, ga; ls and the four seeds

@@ -253,3 +253,29 @@ def test_polarised_plan_size_estimate(wf):
         est = wf.wf_plan_estimate_bytes("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3)
         plan.close()
         assert actual <= est <= 1.6 * actual + (4 << 20), (nside, prec, actual, est)
+
+
+@pytest.mark.parametrize("prec,tol,bound", [("fp64", 1e-11, 1e-8), ("mixed", 1e-5, 1e-3), ("tf32", 1e-5, 1e-3)])
+def test_served_request_matches_oracle(wf, prec, tol, bound):
+    """A Wiener-filter request served by the request loop against the oracle's
+    own solve of the same data (its heuristic schedule, run to a tighter tol):
+    both converge to the same discrete fixed point, so the maps agree to the
+    tolerance's accuracy."""
+    import oracle
+
+    nside, lmax = 16, 32
+    P, basis, d, nu, tau = healpix_case(nside, lmax, gen.seed_for(5, 90))
+    srv = wf.Server(device=0, mem_budget=1 << 30, slots=2)
+    out = np.empty(d.size)
+    srv.submit("wf", nside=nside, lmax=lmax, precision=prec, tol=tol, s_out=out, tag=1, d=np.ascontiguousarray(d),
+               noise_var=np.ascontiguousarray(P["noise_var"]), mask=np.ascontiguousarray(P["mask"]),
+               C_ell=np.ascontiguousarray(P["c_ell"]))
+    res = []
+    while not res:
+        res = srv.wait(timeout=5.0)
+    srv.close()
+    assert res[0]["status"] == wf.WF_OK and res[0]["converged"]
+    sched = oracle.messenger.HealpixSchedule(P["c_ell"], tau * basis.omega, lmax)
+    ref = oracle.messenger_solve(basis, nu * d, nu, basis.per_mode(P["c_ell"]), tau, schedule=sched, tol=1e-12)
+    assert ref["converged"]
+    assert rel(out, ref["s"]) < bound
