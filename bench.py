@@ -56,6 +56,9 @@ def parse():
                          "HEALPix workloads, where 1e-6 is out of reach of the messenger iteration: its residual "
                          "tail decays as a power law)")
     ap.add_argument("--maxiter", type=int, default=3000, help="iteration cap of one solve (one step)")
+    ap.add_argument("--mixed-tol-factor", type=float, default=0.75,
+                    help="mixed precision: the FP32 iteration stops at tol x factor, then FP64 sweeps check the "
+                         "result against tol under the FP64 operator")
     ap.add_argument("--refine-sweeps", type=int, default=2,
                     help="FP64 lambda = 1 correction sweeps after the mixed iteration (0: none)")
     ap.add_argument("--schedule", default="heuristic", choices=["heuristic", "bound"],
@@ -349,7 +352,8 @@ def run_ours(args):
     alm_out = torch.empty(plan.nalm, dtype=torch.complex128, device=dev)
     sched = 1 if args.schedule == "bound" else 0
     wf.wf_set_options(plan, profile=1, maxiter=args.maxiter, schedule=sched,
-                      refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0)
+                      refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0,
+                      mixed_tol_factor=args.mixed_tol_factor)
     if args.full_band_iters > 0:
         wf.wf_set_schedule(plan, [1.0] * args.full_band_iters, [lmax] * args.full_band_iters)
     cap = max(args.maxiter, args.full_band_iters) + 16
@@ -424,6 +428,9 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
            "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
                       "tol": args.tol, "schedule": args.schedule, "legendre_tiles": list(tiles),
+                      "tol_check": "the result's residual under the FP64 operator (correction sweeps); the FP32 "
+                                   "iteration stops at %g x tol" % args.mixed_tol_factor
+                                   if args.precision == "mixed" and args.refine_sweeps > 0 else "own operator",
                       "l2": "inputs (1.2 GB) larger than L2",
                       "parallelism": "replicas"},
            "time_to_tol_s": t_ms / args.steps / 1e3 if last["converged"] else None,
@@ -447,7 +454,8 @@ def run_ours(args):
         nvh, mh, clh = P["noise_var"], P["mask"], P["c_ell"]
         sh = np.empty(plan.npix)
         wf.wf_set_options(plan, profile=0, maxiter=args.maxiter, schedule=sched,
-                          refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0)
+                          refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0,
+                          mixed_tol_factor=args.mixed_tol_factor)
         wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)  # warm
         t0 = time.perf_counter()
         rep = wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)

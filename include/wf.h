@@ -90,7 +90,8 @@ typedef struct {
     int ell_step_max;   /* HEALPix: largest increase of l_iter per level (500) */
     int band_margin;    /* HEALPix: transform band limit L = l_iter + margin (100) */
     double lambda_max;  /* flat: first lambda level (100) */
-    int refine_sweeps;  /* mixed precision: FP64 lambda = 1 sweeps from the mixed result, stopping at tol (0) */
+    int refine_sweeps;  /* mixed precision: FP64 lambda = 1 sweeps from the mixed result, stopping at tol (0);
+                           with sweeps, wf_info.converged and the status report the FP64 operator's verdict */
     int profile;        /* nonzero: time every kernel family with CUDA events (fills wf_info.kernel_ms) */
     double mixed_kappa; /* mixed precision: modes with S_l / (tau Omega) >= kappa run in FP64 (3e4); polarised
                            plans use the largest eigenvalue of each l's prior block for S_l */
@@ -113,6 +114,11 @@ typedef struct {
                            whose FP64 rate is a small fraction of FP32.  Mixed temperature plans: the
                            correction sweeps' transforms run this way unless it is negative, which runs
                            them on the FP64 pipe. */
+    double mixed_tol_factor; /* mixed plans with refine_sweeps > 0: the FP32 iteration stops at tol x factor
+                                (0 < factor < 1; 0 = 1) before the FP64 sweeps check the result against tol
+                                under the FP64 operator.  The FP32 operator's fixed point differs from the
+                                FP64 one in the slowest modes, so the FP64-operator residual of an FP32
+                                iterate at tol can lie above tol (by ~20 % on the nside 2048 map) */
     int tile_syn;       /* mixed plans: > 0 sets the FP32 Legendre synthesis tile (2, 4 or 8 ring pairs per
                            thread) in place of the default or autotuned one; 0 keeps it */
     int tile_ana;       /* mixed plans: > 0 sets the FP32 Legendre analysis tile (2, 4 or 8 ring pairs per

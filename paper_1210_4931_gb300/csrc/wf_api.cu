@@ -665,6 +665,7 @@ struct HpRun {
     const double *d = nullptr, *nv = nullptr, *C_ell = nullptr, *g1 = nullptr, *g2 = nullptr;
     const uint8_t *mask = nullptr;
     double tol = 0;
+    double tol_stop = 0;  // the mixed phase stops below this (tol, or tol x mixed_tol_factor before FP64 sweeps)
     bool fluct = false;
     double *s_out = nullptr, *alm_out = nullptr;
     wf_info *info = nullptr;
@@ -700,6 +701,11 @@ wf_status hp_begin(HpRun &R)
     R.o = defaults(p->opt);
     const wf_options &o = R.o;
     const int lmax = R.lmax = p->lmax;
+    // mixed precision with FP64 correction sweeps: the FP32 phase may stop below a tighter
+    // tolerance, so that the result's FP64-operator residual, which the sweeps check, is below tol
+    R.tol_stop = R.tol;
+    if (p->prec != WF_PREC_FP64 && o.refine_sweeps > 0 && o.mixed_tol_factor > 0.0 && o.mixed_tol_factor < 1.0)
+        R.tol_stop = R.tol * o.mixed_tol_factor;
     if (p->pol) return hp_begin_pol(R);
     if (o.schedule == 1 && R.fluct && p->replay_lambda.empty())
         return set_error(WF_EUNSUPPORTED, "the chi^2-bound schedule needs data (Wiener filter, not wf_fluct)");
@@ -928,14 +934,14 @@ bool hp_absorb(HpRun &R)
         return false;
     }
     if (R.rigorous) {
-        if (full && resid < R.tol) {
+        if (full && resid < R.tol_stop) {
             R.converged = true;
             return false;
         }
         return true;
     }
     if (R.replay) {
-        if (full && resid < R.tol) {
+        if (full && resid < R.tol_stop) {
             R.converged = true;
             if (R.a_init) return false;  // correction sweeps stop at the tolerance
         }
@@ -943,7 +949,7 @@ bool hp_absorb(HpRun &R)
     }
     HpSchedule &sch = R.sch;
     if (sch.final_level()) {
-        if (resid < R.tol) {
+        if (resid < R.tol_stop) {
             R.converged = true;
             return false;
         }
@@ -1020,7 +1026,7 @@ wf_status hp_end(HpRun &R)
         if (R.info) {
             wf_info *info = R.info;
             info->iters = R.k + si.iters;
-            info->converged = (R.converged || si.converged) ? 1 : 0;
+            info->converged = si.converged ? 1 : 0;  // the FP64 operator's verdict
             info->final_residual = si.final_residual;
             info->chi2_over_ndof = si.chi2_over_ndof;
             info->n_dof = R.ndof;
@@ -1350,7 +1356,7 @@ wf_status hp_end_pol(HpRun &R)
         if (R.info) {
             wf_info *info = R.info;
             info->iters = R.k + si.iters;
-            info->converged = (R.converged || si.converged) ? 1 : 0;
+            info->converged = si.converged ? 1 : 0;  // the FP64 operator's verdict
             info->final_residual = si.final_residual;
             info->chi2_over_ndof = si.chi2_over_ndof;
             info->n_dof = R.ndof;

@@ -79,6 +79,18 @@ def test_batch_equals_solves_run_alone(wf):
         else:
             assert rep["final_residual"] < t and rep_alone["final_residual"] < t
             assert rel(s, s_alone) < 1e-3, (n, k, rel(s, s_alone))
+            # the batched mixed item's a_lm under the oracle's FP64 operator: the FP32 iteration
+            # stops on its own operator's residual, which the FP64 one matches to the FP32
+            # operator error (well below tol here)
+            import oracle as orc
+
+            P, basis, d, nu, tau = healpix_case(n, l, gen.seed_for(6, CASES.index((n, l, p, k, t))))
+            r_src = nu * d if k == "wf" else orc.fluct_source(basis, nu, basis.per_mode(P["c_ell"]),
+                                                                it["g1"].cpu().numpy(), it["g2"].cpu().numpy())
+            r1 = orc.messenger_solve(basis, r_src, nu, basis.per_mode(P["c_ell"]), tau, replay=[(1.0, l)],
+                                     a0=it["alm_out"].cpu().numpy())
+            print("batch item", n, k, "fp64-operator residual", r1["resid"][0], "reported", rep["final_residual"])
+            assert r1["resid"][0] < 1.5 * t
     for pl in plans:
         pl.close()
 
