@@ -19,15 +19,15 @@
 // below 2^-20 of each product, so the contraction is as accurate as the FP32
 // FMA kernels.
 //
-// Layout on chip (one CTA = 256 ring pairs = two M = 128 tiles, 128 threads;
-// thread t runs the recurrences of pairs 2t and 2t + 1 in packed f32x2 lanes
-// and owns lane t of both tiles; 256 tensor-memory columns per CTA, two CTAs
-// per SM):
-//   tensor memory  per tile D_E, D_O (N = NC columns each, NC = 2 ncols
-//                  rounded up to 16) and the A operand of the current chunk
-//                  of 32 l (per parity and piece 16 TF32 or 8 packed BF16
-//                  columns); each thread writes its own lanes (tcgen05.st), so
-//                  the recurrence values never pass through shared memory;
+// Layout on chip (one CTA = one M = 128 tile of ring pairs, 128 threads, a
+// thread per ring pair = per tensor-memory lane; 128 tensor-memory columns
+// per CTA, so four CTAs share an SM and one CTA's MMA latency hides behind
+// the others' recurrences):
+//   tensor memory  D_E, D_O (N = NC columns each, NC = 2 ncols rounded up to
+//                  16) and the A operand of the current chunk of 32 l (per
+//                  parity and piece 16 TF32 or 8 packed BF16 columns); each
+//                  thread writes its own lane (tcgen05.st), so the recurrence
+//                  values never pass through shared memory;
 //   shared memory  the B operand of the chunk (E hi, E lo, O hi, O lo; NC
 //                  rows x 16 k, K-major core matrices of 8 rows x 16 bytes)
 //                  and the chunk's recurrence coefficients.
@@ -45,10 +45,9 @@ namespace wf {
 
 namespace {
 
-constexpr int TC_THREADS = 128;   // two M = 128 tiles: a thread per pair of ring pairs = tensor-memory lane
-constexpr int TC_PAIRS = 256;     // ring pairs per CTA
+constexpr int TC_THREADS = 128;   // one M = 128 tile: a thread per ring pair and tensor-memory lane
 constexpr int TC_BITEMS = 4;      // B items per thread per chunk (16 columns x 32 l / 128 threads)
-constexpr int TC_TMEM_COLS = 256; // per tile D_E, D_O (nc each, nc <= 32) and the A operand (64 columns)
+constexpr int TC_TMEM_COLS = 128; // D_E, D_O (nc each, nc <= 32) + the A operand (64 columns)
 constexpr int TC_KC = 32;         // l values per chunk (16 even, 16 odd)
 constexpr int TC_MAXC = TC_MAX_COLUMNS;  // columns (maps) per launch
 constexpr float TC_X_DIFF = 0.4f; // rings with x > 0.4 run the difference form (as the FP32 kernels)
@@ -221,57 +220,39 @@ struct TcSynArgs {
 
 // one double step (l, l + 1) of the recurrence for one ring pair (scalar form
 // of the FP32 kernels' step); v0 = mu_l, v1 = mu_{l+1}
-__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2f(float2 a) { return make_float2(-a.x, -a.y); }
-
-// one double step (l, l + 1) of the mu-form recurrence for the thread's two ring pairs in packed
-// f32x2 lanes (the scalar step of the FP32 kernels, two pairs per instruction); v0 = mu_l,
-// v1 = mu_{l+1}.  Plain state (Sa, Sb) = (mu_{l-2}, mu_{l-1}); difference state (D_{l-1}, mu_{l-1}).
 template <bool DIFF>
-__device__ __forceinline__ void tc_step2(float A0, float B0, float A1, float B1, float2 X, float2 W, float2 &Sa,
-                                         float2 &Sb, float2 &v0, float2 &v1)
+__device__ __forceinline__ void tc_step(float A0, float B0, float A1, float B1, float x, float w, float &Sa, float &Sb,
+                                        float &v0, float &v1)
 {
     if (DIFF) {
-        float2 D = __ffma2_rn(__ffma2_rn(dup2(-A0), W, dup2(B0)), Sb, Sa);
-        v0 = __fadd2_rn(Sb, D);
-        D = __ffma2_rn(__ffma2_rn(dup2(-A1), W, dup2(B1)), v0, D);
-        v1 = __fadd2_rn(v0, D);
+        float D = fmaf(fmaf(-A0, w, B0), Sb, Sa);
+        v0 = Sb + D;
+        D = fmaf(fmaf(-A1, w, B1), v0, D);
+        v1 = v0 + D;
         Sa = D;
         Sb = v1;
     } else {
-        v0 = __ffma2_rn(__fmul2_rn(dup2(A0), X), Sb, neg2f(Sa));
-        v1 = __ffma2_rn(__fmul2_rn(dup2(A1), X), v0, neg2f(Sb));
+        v0 = fmaf(A0 * x, Sb, -Sa);
+        v1 = fmaf(A1 * x, v0, -Sb);
         Sa = v0;
         Sb = v1;
     }
 }
 
-__device__ __forceinline__ void inject(float2 &v, int h, float a)
-{
-    if (h) v.y = a;
-    else v.x = a;
-}
-
-// one chunk of TC_KC values of l for both pairs; seeds enter at l == ls[h] (lane h of the pack)
 template <bool DIFF, bool INJ>
-__device__ __forceinline__ void tc_chunk2(int l0, const int (&ls)[2], const float (&s0)[2], const float (&s1)[2],
-                                          float2 X, float2 W, const float4 *coef, float2 &Sa, float2 &Sb,
-                                          float2 (&mu)[TC_KC])
+__device__ __forceinline__ void tc_chunk(int l0, int ls, float s0, float s1, float x, float w, const float4 *coef,
+                                         float &Sa, float &Sb, float (&mu)[TC_KC])
 {
 #pragma unroll
     for (int j = 0; j < TC_KC / 2; ++j) {
         const float4 ab = coef[j];
-        float2 v0, v1;
-        tc_step2<DIFF>(ab.x, ab.y, ab.z, ab.w, X, W, Sa, Sb, v0, v1);
-        if (INJ) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (l0 + 2 * j == ls[h]) {
-                    inject(v0, h, s0[h]);
-                    inject(v1, h, s1[h]);
-                    inject(Sa, h, DIFF ? s1[h] - s0[h] : s0[h]);
-                    inject(Sb, h, s1[h]);
-                }
+        float v0, v1;
+        tc_step<DIFF>(ab.x, ab.y, ab.z, ab.w, x, w, Sa, Sb, v0, v1);
+        if (INJ && l0 + 2 * j == ls) {
+            v0 = s0;
+            v1 = s1;
+            Sa = DIFF ? s1 - s0 : s0;
+            Sb = s1;
         }
         mu[2 * j] = v0;
         mu[2 * j + 1] = v1;
@@ -289,47 +270,40 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     const int m = blockIdx.y;
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    // ring pairs 2 tid and 2 tid + 1 of the CTA's 256: lane tid of M tile 0 and of M tile 1
-    const int pp[2] = {blockIdx.x * TC_PAIRS + 2 * tid, blockIdx.x * TC_PAIRS + 2 * tid + 1};
+    const int p = blockIdx.x * TC_THREADS + tid;
     const int nc = P.nc;
     const long long base = tc_mbase(P.lmax, m);
     const size_t pstride = (size_t)(P.lmax + 1) * 2;
 
-    // the two pairs' seeds
-    int ls[2] = {INT_MAX, INT_MAX};
-    float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f}, xs[2] = {0.f, 0.f}, ws[2] = {1.f, 1.f};
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-        if (pp[h] < P.npairs) {
-            const size_t si = (size_t)m * P.npairs + pp[h];
-            const int l = P.ls[si];
-            if (l <= P.Lmax) {
-                ls[h] = l;
-                s0[h] = P.s0[si];
-                s1[h] = P.s1[si];
-            }
-            xs[h] = P.xp[pp[h]];
-            ws[h] = P.wp[pp[h]];
+    // this pair's seeds
+    int ls = INT_MAX;
+    float s0 = 0.f, s1 = 0.f, x = 0.f, w = 1.f;
+    if (p < P.npairs) {
+        const size_t si = (size_t)m * P.npairs + p;
+        const int l = P.ls[si];
+        if (l <= P.Lmax) {
+            ls = l;
+            s0 = P.s0[si];
+            s1 = P.s1[si];
         }
-    const float2 X = make_float2(xs[0], xs[1]), W = make_float2(ws[0], ws[1]);
+        x = P.xp[p];
+        w = P.wp[p];
+    }
     // first chunk any pair of the CTA needs
     if (tid == 0) qmin_s = INT_MAX;
     __syncthreads();
-    const int lmin = min(ls[0], ls[1]);
-    if (lmin != INT_MAX) atomicMin(&qmin_s, (lmin - m) / TC_KC);
+    if (ls != INT_MAX) atomicMin(&qmin_s, (ls - m) / TC_KC);
     __syncthreads();
     const int q0 = qmin_s, q1 = (P.Lmax - m) / TC_KC;
     if (q0 > q1) {  // no pair of the CTA has a term: zero coefficients (block-uniform exit)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (pp[h] < P.npairs)
-                for (int c = 0; c < P.ncols; ++c) {
-                    float2 *g = P.G[c] + (size_t)pp[h] * pstride + 2 * (size_t)m;
-                    *reinterpret_cast<float4 *>(g) = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+        if (p < P.npairs)
+            for (int c = 0; c < P.ncols; ++c) {
+                float2 *g = P.G[c] + (size_t)p * pstride + 2 * (size_t)m;
+                *reinterpret_cast<float4 *>(g) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         return;
     }
-    const bool diff = __shfl_sync(0xffffffffu, xs[0] > TC_X_DIFF ? 1 : 0, 0) != 0;  // one form per warp
+    const bool diff = __shfl_sync(0xffffffffu, x > TC_X_DIFF ? 1 : 0, 0) != 0;  // one form per warp
 
     // shared B operand: 2 PIECES tiles ([parity][piece]) of nc x 16 elements, then the recurrence
     // coefficients (A_l, B_l, A_l+1, B_l+1) of every double step of the chunks this CTA runs,
@@ -344,8 +318,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         coef[j] = make_float4(la <= P.lmax ? P.A32[base + (la - m)] : 0.f, la <= P.lmax ? P.B32[base + (la - m)] : 0.f,
                               lb <= P.lmax ? P.A32[base + (lb - m)] : 0.f, lb <= P.lmax ? P.B32[base + (lb - m)] : 0.f);
     }
-    // B values (c a of one column at one l) this thread stages: items tid + r * TC_THREADS of a
-    // chunk (ncols x 32 items), loaded one chunk ahead so that their latency hides behind the recurrence
+    // B values (c a of one column at one l) this thread stages: items tid and tid + 256 of a chunk
+    // (ncols x 32 items), loaded one chunk ahead so that their latency hides behind the recurrence
     const int nitems = P.ncols * TC_KC;
     float2 pa[TC_BITEMS];
     auto prefetch = [&](int q) {
@@ -374,9 +348,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    // columns: tile t: D_E [2 nc t, 2 nc t + nc), D_O [+ nc, + 2 nc); A of tile t at 4 nc + 64 t,
-    // laid out [parity][piece] in blocks of ACOLS columns (16 k each)
-    const uint32_t aT0 = tmem + 4u * nc;
+    // columns: D_E [0, nc), D_O [nc, 2 nc); A at 2 nc, laid out [parity][piece] in blocks of
+    // ACOLS columns (16 k each)
+    const uint32_t dE = tmem, dO = dE + nc;
+    const uint32_t aT = tmem + 2u * nc;
     const uint32_t idesc = idesc_of(AR::FMT, 128, nc);
     const uint32_t lbo = (uint32_t)(nc >> 3) * 128, sbo = 128;
     const uint32_t bsm = smem_addr(B);
@@ -391,21 +366,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
             for (int s2 = 0; s2 < AR::KSTEPS; ++s2)
                 bdesc[par][h][s2] =
                     smem_desc(bsm + (uint32_t)(AR::PIECES * par + h) * btile + 2 * s2 * lbo, lbo, sbo);
-    float2 Sa = make_float2(0.f, 0.f), Sb = make_float2(0.f, 0.f);
+    float Sa = 0.f, Sb = 0.f;
     bool ok = true;
     uint32_t phase = 0;
     for (int q = q0; q <= q1; ++q) {
         const int l0 = m + TC_KC * q;
-        float2 mu[TC_KC];
-        // seeds enter only in the chunk holding a pair's first l: one test per warp and chunk
-        const bool inj = __any_sync(0xffffffffu, (ls[0] >= l0 && ls[0] < l0 + TC_KC) ||
-                                                     (ls[1] >= l0 && ls[1] < l0 + TC_KC));
+        float mu[TC_KC];
+        // seeds enter only in the chunk holding a lane's first l: one test per warp and chunk
+        const bool inj = __any_sync(0xffffffffu, ls >= l0 && ls < l0 + TC_KC);
         if (diff) {
-            if (inj) tc_chunk2<true, true>(l0, ls, s0, s1, X, W, coef + 16 * q, Sa, Sb, mu);
-            else tc_chunk2<true, false>(l0, ls, s0, s1, X, W, coef + 16 * q, Sa, Sb, mu);
+            if (inj) tc_chunk<true, true>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
+            else tc_chunk<true, false>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
         } else {
-            if (inj) tc_chunk2<false, true>(l0, ls, s0, s1, X, W, coef + 16 * q, Sa, Sb, mu);
-            else tc_chunk2<false, false>(l0, ls, s0, s1, X, W, coef + 16 * q, Sa, Sb, mu);
+            if (inj) tc_chunk<false, true>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
+            else tc_chunk<false, false>(l0, ls, s0, s1, x, w, coef + 16 * q, Sa, Sb, mu);
         }
         // the previous chunk's MMAs have read A (tensor memory) and B (shared memory)
         if (q > q0) {
@@ -414,29 +388,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const uint32_t aT = aT0 + 64u * t + lane_base;
+        for (int par = 0; par < 2; ++par) {
+            if constexpr (KIND == 0) {
+                uint32_t hi[16], lo[16];
 #pragma unroll
-            for (int par = 0; par < 2; ++par) {
-                if constexpr (KIND == 0) {
-                    uint32_t hi[16], lo[16];
+                for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j + par], hi[j], lo[j]);
+                tmem_st16(aT + lane_base + 32 * par, hi);
+                tmem_st16(aT + lane_base + 32 * par + 16, lo);
+            } else {
+                uint32_t pk[3][8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) split_tf32(t ? mu[2 * j + par].y : mu[2 * j + par].x, hi[j], lo[j]);
-                    tmem_st16(aT + 32 * par, hi);
-                    tmem_st16(aT + 32 * par + 16, lo);
-                } else {
-                    uint32_t pk[3][8];
+                for (int j = 0; j < 8; ++j) {
+                    uint16_t e0[3], e1[3];
+                    split_bf16(mu[4 * j + par], e0);      // k = 2 j     (l - l0 = 4 j + par)
+                    split_bf16(mu[4 * j + 2 + par], e1);  // k = 2 j + 1
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        uint16_t e0[3], e1[3];
-                        split_bf16(t ? mu[4 * j + par].y : mu[4 * j + par].x, e0);          // k = 2 j
-                        split_bf16(t ? mu[4 * j + 2 + par].y : mu[4 * j + 2 + par].x, e1);  // k = 2 j + 1
-#pragma unroll
-                        for (int h = 0; h < 3; ++h) pk[h][j] = (uint32_t)e0[h] | ((uint32_t)e1[h] << 16);
-                    }
-#pragma unroll
-                    for (int h = 0; h < 3; ++h) tmem_st8(aT + 24 * par + 8 * h, pk[h]);
+                    for (int h = 0; h < 3; ++h) pk[h][j] = (uint32_t)e0[h] | ((uint32_t)e1[h] << 16);
                 }
+#pragma unroll
+                for (int h = 0; h < 3; ++h) tmem_st8(aT + lane_base + 24 * par + 8 * h, pk[h]);
             }
         }
         // B: (c a) of every column for the chunk's 32 l, split the same way
@@ -475,12 +445,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t acc0 = q > q0 ? 1u : 0u;
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
+            {
 #pragma unroll
                 for (int par = 0; par < 2; ++par) {
-                    const uint32_t d = tmem + 2u * nc * t + (par ? nc : 0);
-                    const uint32_t a0 = aT0 + 64u * t + (uint32_t)(AR::PIECES * AR::ACOLS * par);
+                    const uint32_t d = dE + (par ? nc : 0);
+                    const uint32_t a0 = aT + (uint32_t)(AR::PIECES * AR::ACOLS * par);
 #pragma unroll
                     for (int s = 0; s < AR::KSTEPS; ++s)
 #pragma unroll
@@ -500,24 +469,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // epilogue: G_N = E + O, G_S = E - O per column (8 columns per pass of 16 tensor-memory columns)
     if (ok) {
+        for (int c0 = 0; c0 < P.ncols; c0 += 8) {
+            uint32_t e[16], o[16];
+            tmem_ld16(dE + lane_base + 2 * c0, e);
+            tmem_ld16(dO + lane_base + 2 * c0, o);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p < P.npairs) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const uint32_t dE = tmem + 2u * nc * t, dO = dE + nc;
-            for (int c0 = 0; c0 < P.ncols; c0 += 8) {
-                uint32_t e[16], o[16];
-                tmem_ld16(dE + lane_base + 2 * c0, e);
-                tmem_ld16(dO + lane_base + 2 * c0, o);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (pp[t] < P.npairs) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int c = c0 + j;
-                        if (c < P.ncols) {
-                            const float er = __uint_as_float(e[2 * j]), ei = __uint_as_float(e[2 * j + 1]);
-                            const float orr = __uint_as_float(o[2 * j]), oi = __uint_as_float(o[2 * j + 1]);
-                            float2 *g = P.G[c] + (size_t)pp[t] * pstride + 2 * (size_t)m;
-                            *reinterpret_cast<float4 *>(g) = make_float4(er + orr, ei + oi, er - orr, ei - oi);
-                        }
+                for (int j = 0; j < 8; ++j) {
+                    const int c = c0 + j;
+                    if (c < P.ncols) {
+                        const float er = __uint_as_float(e[2 * j]), ei = __uint_as_float(e[2 * j + 1]);
+                        const float orr = __uint_as_float(o[2 * j]), oi = __uint_as_float(o[2 * j + 1]);
+                        float2 *g = P.G[c] + (size_t)p * pstride + 2 * (size_t)m;
+                        *reinterpret_cast<float4 *>(g) = make_float4(er + orr, ei + oi, er - orr, ei - oi);
                     }
                 }
             }
@@ -613,7 +578,7 @@ wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 
     }
     A.err = p->ws.tc_err;
     const size_t sm = tc_syn_smem(A.nc, Lmax);  // the limit is raised at plan creation (tc_prepare)
-    dim3 grid((p->npairs + TC_PAIRS - 1) / TC_PAIRS, Lmax + 1);
+    dim3 grid((p->npairs + TC_THREADS - 1) / TC_THREADS, Lmax + 1);
     if (p->prec == WF_PREC_MIXED_SPLITBF16) k_legsyn_tc<1><<<grid, TC_THREADS, sm, stream>>>(A);
     else k_legsyn_tc<0><<<grid, TC_THREADS, sm, stream>>>(A);
     WF_COUNT_LAUNCH(p);
