@@ -84,8 +84,8 @@ typedef struct {
  * fields take the defaults shown. */
 typedef struct {
     int maxiter;        /* total iteration cap (default 20000) */
-    int level_cap;      /* iterations at one lambda level before it is left anyway (200) */
-    double eta;         /* plateau: |chi2_k - chi2_{k-1}| < eta sqrt(2 n_dof) (1e-2) */
+    int level_cap;      /* iterations at one lambda level before it is left anyway (HEALPix 3000, flat 200) */
+    double eta;         /* plateau: |chi2_k - chi2_{k-1}| < eta sqrt(2 n_dof) (HEALPix 3e-5, flat 1e-2) */
     int ell0;           /* HEALPix: first l_iter (20) */
     int ell_step_max;   /* HEALPix: largest increase of l_iter per level (500) */
     int band_margin;    /* HEALPix: transform band limit L = l_iter + margin (100) */
