@@ -1741,7 +1741,7 @@ long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging
         } else {
             long long M = 1;
             while (M < 2 * n - 1) M <<= 1;
-            V += M;
+            V += M + n;  // filter and chirp
             nmaxF = std::max(nmaxF, M);
             maxBlue = std::max(maxBlue, n);
         }

@@ -60,6 +60,7 @@ struct RingTab {
     long long offS;    // first pixel of the south ring, -1 for the equator
     long long rootOff; // offset of e^{i pi p / n}, p < 2n, in the roots table
     long long vOff;    // offset of the Bluestein filter (M entries: even half, odd half)
+    long long cOff;    // offset of the Bluestein chirp e^{-i pi j^2 / n}, j < n, in the chirp table
 };
 
 constexpr int NAIVE_MAX = 32;   // rings this short use a direct DFT
@@ -118,6 +119,7 @@ struct Workspace {
 struct HpTables {
     RingTab *rings = nullptr;
     void *roots = nullptr, *V = nullptr, *tw = nullptr;  // T-typed complex
+    void *chirp = nullptr;                               // T-typed complex, per Bluestein length
     // FP64 recurrence (always present): per alm A, c; per (m, pair) first l and seeds; per pair x
     double *A64 = nullptr, *c64 = nullptr;
     int *ls = nullptr;

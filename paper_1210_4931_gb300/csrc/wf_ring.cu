@@ -87,7 +87,8 @@ void host_fft(std::vector<double2> &x)
 // A warp of one pass reads consecutive entries (Ns >= 32) or a few broadcast ones;
 // one table of the circle indexed k 2^logB / (8 Ns) put the lanes of the middle
 // passes on one bank.
-// Supports N <= 8192 with RING_THREADS = 512 threads (two radix-8 butterflies per thread).
+// Supports N <= 8192 with NT = 512 threads (two radix-8 butterflies per thread) or
+// NT = 1024 (one).
 template <typename T>
 __device__ __forceinline__ cx<T> mul_i(cx<T> a, int sign)
 {
@@ -159,6 +160,7 @@ inline size_t padded_len(int n) { return (size_t)n + (size_t)n / 16 + 1; }
 template <typename T, int R, int LOGR, int BPT>
 __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int sign, const cx<T> *stw)
 {
+    static_assert(R == 2 || R == 4 || R == 8, "radix 2, 4 or 8");
     const int NR = (1 << logN) >> LOGR;
     const int Ns = 1 << logNs;
     // w1 = e^{-2 pi i k / (R Ns)} = stw[Ns + k]: radix 2 and 4 run only as the first pass
@@ -170,16 +172,21 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
         if (j < NR) {
             const int k = j & (Ns - 1);
             // twiddles w^r, r < R, from one table entry w = e^{-+2 pi i k / (R Ns)} by products
-            cx<T> w1 = stw[Ns + k];
-            if (sign > 0) w1.y = -w1.y;
-            cx<T> wr = w1;
-            v[b][0] = x[pidx(j)];
+            // in a tree of depth log2 R (w^2 = w w, w^3 = w^2 w, w^4 = w^2 w^2, ...), not a
+            // chain of R - 2 dependent products
+            cx<T> w[R];
+            w[0] = mk<T>(1, 0);
+            w[1] = stw[Ns + k];
+            if (sign > 0) w[1].y = -w[1].y;
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                const cx<T> a = x[pidx(j + r * NR)];
-                v[b][r] = cmul(a, wr);
-                if (r + 1 < R) wr = cmul(wr, w1);
+            for (int r = 2; r < R; ++r) {
+                const int hb = r >= 4 ? 4 : 2;  // highest power of two <= r (R <= 8)
+                w[r] = r == hb ? cmul(w[hb / 2], w[hb / 2]) : cmul(w[hb], w[r - hb]);
             }
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = x[pidx(j + r * NR)];
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
             SmallDft<T, R>::run(v[b], sign);
         }
     }
@@ -197,20 +204,27 @@ __device__ __forceinline__ void stockham_pass(cx<T> *x, int logN, int logNs, int
     __syncthreads();
 }
 
+// Threads of the ring kernels: FP32 plans run 1024 (32 warps per SM, one radix-8
+// butterfly per thread and pass at N = 8192: twice the warps of 512 threads to hide the
+// shared-memory and L2 latencies of one pair's chain of passes), FP64 plans 512 (their
+// butterflies need twice the registers).
+template <typename T> __host__ __device__ constexpr int ring_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+
 template <typename T>
 __device__ __noinline__ void fft_pow2(cx<T> *x, int logN, int sign, const cx<T> *stw)
 {
+    constexpr int NT = ring_threads<T>();
     int logNs = 0;
     const int head = logN % 3;
     if (head == 1) {
-        stockham_pass<T, 2, 1, 8>(x, logN, 0, sign, stw);
+        stockham_pass<T, 2, 1, 4096 / NT>(x, logN, 0, sign, stw);
         logNs = 1;
     } else if (head == 2) {
-        stockham_pass<T, 4, 2, 4>(x, logN, 0, sign, stw);
+        stockham_pass<T, 4, 2, 2048 / NT>(x, logN, 0, sign, stw);
         logNs = 2;
     }
     while (logNs < logN) {
-        stockham_pass<T, 8, 3, 2>(x, logN, logNs, sign, stw);
+        stockham_pass<T, 8, 3, 1024 / NT>(x, logN, logNs, sign, stw);
         logNs += 3;
     }
 }
@@ -227,7 +241,8 @@ template <typename T> struct RingOut {
 template <typename T>
 __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *zout, int sign,
                                const cx<T> *__restrict__ roots, const cx<T> *__restrict__ V,
-                               const cx<T> *__restrict__ tw, int logNmax, const cx<T> *stw)
+                               const cx<T> *__restrict__ chirp, const cx<T> *__restrict__ tw, int logNmax,
+                               const cx<T> *stw)
 {
     const int n = R.n;
     const unsigned twon = 2u * (unsigned)n;
@@ -249,19 +264,20 @@ __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *
         fft_pow2<T>(buf, R.logF, sign, stw);
         return RingOut<T>{buf, 1};
     }
-    // Bluestein, two half-length passes (indices j^2 < 2^26: 32-bit arithmetic)
+    // Bluestein, two half-length passes; the chirp c_j = e^{-i pi j^2 / n} is read
+    // from its own table in order (consecutive lanes, consecutive entries)
     const int H = 1 << R.logF;                 // M / 2
     const int mstep = logNmax - (R.logF + 1);  // index step of w_M in tw
     const cx<T> *Vh = V + R.vOff;
+    const cx<T> *ch = chirp + R.cOff;
     for (int h = 0; h < 2; ++h) {
+#pragma unroll 4
         for (int j = threadIdx.x; j < H; j += blockDim.x) {
             cx<T> v = mk<T>(0, 0);
             if (j < n) {
                 cx<T> u = zin[j];
                 if (sign > 0) u.y = -u.y;
-                cx<T> c = root[((unsigned)j * (unsigned)j) % twon];
-                c.y = -c.y;  // e^{-i pi j^2 / n}
-                v = cmul(u, c);
+                v = cmul(u, ch[j]);
                 if (h) v = cmul(v, tw[j << mstep]);
             }
             buf[pidx(j)] = v;
@@ -271,15 +287,14 @@ __device__ RingOut<T> ring_dft(const RingTab &R, cx<T> *buf, cx<T> *zin, cx<T> *
         for (int k = threadIdx.x; k < H; k += blockDim.x) buf[pidx(k)] = cmul(buf[pidx(k)], Vh[h * H + k]);
         __syncthreads();
         fft_pow2<T>(buf, R.logF, +1, stw);
+#pragma unroll 4
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
             if (h == 0) {
                 zout[k] = buf[pidx(k)];
             } else {
                 cx<T> w = tw[k << mstep];
                 w.y = -w.y;  // w_M^{-k}
-                cx<T> c = root[((unsigned)k * (unsigned)k) % twon];
-                c.y = -c.y;
-                cx<T> y = cmul(cadd(zout[k], cmul(buf[pidx(k)], w)), c);
+                cx<T> y = cmul(cadd(zout[k], cmul(buf[pidx(k)], w)), ch[k]);
                 if (sign > 0) y.y = -y.y;
                 zout[k] = y;
             }
@@ -355,11 +370,13 @@ __device__ __forceinline__ void load_twiddles(cx<T> *stw, const cx<T> *__restric
 // The next pair's ring tables into L2: e^{i pi p / n} (fold phases and Bluestein chirps)
 // and, for a Bluestein ring, its filter spectrum (M entries).
 template <typename T>
-__device__ __forceinline__ void prefetch_ring_tables(const RingTab &Rn, const cx<T> *roots, const cx<T> *V)
+__device__ __forceinline__ void prefetch_ring_tables(const RingTab &Rn, const cx<T> *roots, const cx<T> *V,
+                                                     const cx<T> *chirp)
 {
     if (Rn.kind == RING_BLUESTEIN) {
         prefetch_range(roots + Rn.rootOff, (size_t)2 * Rn.n * sizeof(cx<T>));
         prefetch_range(V + Rn.vOff, ((size_t)2 << Rn.logF) * sizeof(cx<T>));
+        prefetch_range(chirp + Rn.cOff, (size_t)Rn.n * sizeof(cx<T>));
     } else if (Rn.q) {
         prefetch_range(roots + Rn.rootOff, (size_t)2 * Rn.n * sizeof(cx<T>));
     }
@@ -408,8 +425,9 @@ __device__ __forceinline__ void unfold_ring(const RingTab &R, const RingOut<T> &
 // the S partial sums are combined by shuffles in a fixed order: small polar
 // rings, whose bins collect up to 2L/n aliases, no longer serialise the CTA.
 template <typename T>
-__global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, const cx<T> *__restrict__ roots,
-                                                          const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
+__global__ void __launch_bounds__(ring_threads<T>(), 1) k_ringsyn(RingCommon rc, const cx<T> *__restrict__ roots,
+                                                          const cx<T> *__restrict__ V,
+                                                          const cx<T> *__restrict__ chirp, const cx<T> *__restrict__ tw,
                                                           cx<T> *__restrict__ scr, const cx<T> *__restrict__ G,
                                                           int mode, const T *__restrict__ r, const T *__restrict__ nu,
                                                           T lam, T tau, T *__restrict__ tmap,
@@ -417,7 +435,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
                                                           cx<T> *__restrict__ F)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[RING_THREADS / 32];
+    __shared__ double red[32];
     __shared__ int s_tick;
     cx<T> *buf = reinterpret_cast<cx<T> *>(smem_raw);
     cx<T> *zin = rc.zsmem ? buf + rc.bpad : scr + (size_t)blockIdx.x * rc.scr_stride;
@@ -443,7 +461,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             const int pn = rc.order[nxt];
             const RingTab Rn = rc.rings[pn];
             prefetch_range(G + (size_t)pn * (rc.lmax + 1) * 2, (size_t)(L + 1) * 2 * sizeof(cx<T>));
-            prefetch_ring_tables<T>(Rn, roots, V);
+            prefetch_ring_tables<T>(Rn, roots, V, chirp);
             if (mode == RS_BLEND) {
                 prefetch_range(r + Rn.offN, (size_t)Rn.n * sizeof(T));
                 prefetch_range(nu + Rn.offN, (size_t)Rn.n * sizeof(T));
@@ -520,7 +538,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             }
         }
         __syncthreads();
-        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, tw, rc.logNmax, stw);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, +1, roots, V, chirp, tw, rc.logNmax, stw);
         T chi_pair = 0;  // per-thread partial of this pair in the working precision
         int j0 = threadIdx.x, jstep = blockDim.x;
         if constexpr (sizeof(T) == 4) {
@@ -606,7 +624,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
             __syncthreads();
         }
         if (mode == RS_BLEND_ANA) {  // forward DFT of the blended ring and unfold to F_m, m <= L
-            const RingOut<T> zf = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw);
+            const RingOut<T> zf = ring_dft<T>(R, buf, zin, zout, -1, roots, V, chirp, tw, rc.logNmax, stw);
             unfold_ring<T>(R, zf, root, q, twon, south, F + (size_t)pair * (rc.lmax + 1) * 2, L);
         }
         cur = nxt;
@@ -617,8 +635,9 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringsyn(RingCommon rc, cons
 // analysis side: pack -> forward ring DFT -> unfold to F_m, m <= L
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, const cx<T> *__restrict__ roots,
-                                                          const cx<T> *__restrict__ V, const cx<T> *__restrict__ tw,
+__global__ void __launch_bounds__(ring_threads<T>(), 1) k_ringana(RingCommon rc, const cx<T> *__restrict__ roots,
+                                                          const cx<T> *__restrict__ V,
+                                                          const cx<T> *__restrict__ chirp, const cx<T> *__restrict__ tw,
                                                           cx<T> *__restrict__ scr, const T *__restrict__ map,
                                                           cx<T> *__restrict__ F)
 {
@@ -644,7 +663,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
         const bool south = R.offS >= 0;
         if (nxt < rc.npairs) {
             const RingTab Rn = rc.rings[rc.order[nxt]];
-            prefetch_ring_tables<T>(Rn, roots, V);
+            prefetch_ring_tables<T>(Rn, roots, V, chirp);
             prefetch_range(map + Rn.offN, (size_t)Rn.n * sizeof(T));
             if (Rn.offS >= 0) prefetch_range(map + Rn.offS, (size_t)Rn.n * sizeof(T));
         }
@@ -678,7 +697,7 @@ __global__ void __launch_bounds__(RING_THREADS, 1) k_ringana(RingCommon rc, cons
             else buf[pidx(j)] = v;
         }
         __syncthreads();
-        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, tw, rc.logNmax, stw);
+        const RingOut<T> z = ring_dft<T>(R, buf, zin, zout, -1, roots, V, chirp, tw, rc.logNmax, stw);
         unfold_ring<T>(R, z, root, q, twon, south, F + (size_t)pair * (rc.lmax + 1) * 2, L);
         cur = nxt;
     }
@@ -729,8 +748,9 @@ template <typename T> struct RingLaunch {
         }
         const size_t sm = smem_bytes(t);
         WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
-        k_ringsyn<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(
-            rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
+        k_ringsyn<T><<<t.ringGrid, ring_threads<T>(), sm, p->stream>>>(
+            rc, (const cx<T> *)t.roots, (const cx<T> *)t.V, (const cx<T> *)t.chirp, (const cx<T> *)t.tw,
+            (cx<T> *)p->ws.scr,
             (const cx<T> *)G, (int)mode, (const T *)p->ws.r, (const T *)p->ws.nu, (T)lam, (T)tau,
             (T *)tmap, omap, p->ws.part_pix, (cx<T> *)F);
         WF_COUNT_LAUNCH(p);
@@ -753,8 +773,9 @@ template <typename T> struct RingLaunch {
         RingCommon rc = common(p, L);
         const size_t sm = smem_bytes(t);
         WF_CUDA(cudaMemsetAsync(t.ticket, 0, sizeof(int), p->stream));
-        k_ringana<T><<<t.ringGrid, RING_THREADS, sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
-                                                                  (const cx<T> *)t.tw, (cx<T> *)p->ws.scr,
+        k_ringana<T><<<t.ringGrid, ring_threads<T>(), sm, p->stream>>>(rc, (const cx<T> *)t.roots, (const cx<T> *)t.V,
+                                                                  (const cx<T> *)t.chirp, (const cx<T> *)t.tw,
+                                                                  (cx<T> *)p->ws.scr,
                                                                   (const T *)map, (cx<T> *)F);
         WF_COUNT_LAUNCH(p);
         WF_CUDA(cudaGetLastError());
@@ -779,8 +800,8 @@ template <typename T> struct RingLaunch {
         if ((st = raise_smem_limit((const void *)k_ringsyn<T>, sm)) != WF_OK) return st;
         if ((st = raise_smem_limit((const void *)k_ringana<T>, sm)) != WF_OK) return st;
         int b1 = 0, b2 = 0;
-        WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_ringsyn<T>, RING_THREADS, sm));
-        WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_ringana<T>, RING_THREADS, sm));
+        WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_ringsyn<T>, ring_threads<T>(), sm));
+        WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_ringana<T>, ring_threads<T>(), sm));
         int b = b1 < b2 ? b1 : b2;
         if (b < 1) return set_error(WF_EUNSUPPORTED, "ring kernel does not fit on an SM (smem %zu bytes)", sm);
         long long g = (long long)b * p->nsm;
@@ -822,8 +843,8 @@ wf_status hp_build_ring_tables(wf_plan p)
         off[i] = off[i - 1] + nr[i - 1];
     }
     std::vector<RingTab> rt(np);
-    std::map<int, long long> rootOff, vOff;
-    std::vector<double2> roots, Vtab;
+    std::map<int, long long> rootOff, vOff, cOff;
+    std::vector<double2> roots, Vtab, chirp;
     long long nmaxF = 2;  // largest full FFT length (pow2 n or Bluestein M)
     int bmax = 2 * NAIVE_MAX, maxBlue = 1;
     for (int pr = 0; pr < np; ++pr) {
@@ -843,6 +864,7 @@ wf_status hp_build_ring_tables(wf_plan p)
         }
         t.rootOff = rootOff[n];
         t.vOff = 0;
+        t.cOff = 0;
         if (n <= NAIVE_MAX) {
             t.kind = RING_NAIVE;
             t.logF = 0;
@@ -873,6 +895,14 @@ wf_status hp_build_ring_tables(wf_plan p)
                 for (long long k = 0; k < M / 2; ++k) Vtab.push_back(cscale(v[2 * k + 1], 1.0 / (double)M));
             }
             t.vOff = vOff[n];
+            if (!cOff.count(n)) {  // c_j = e^{-i pi j^2 / n}, j^2 reduced mod 2n exactly
+                cOff[n] = (long long)chirp.size();
+                for (long long j = 0; j < n; ++j) {
+                    const double a = -M_PI * (double)((j * j) % (2LL * n)) / (double)n;
+                    chirp.push_back(make_double2(std::cos(a), std::sin(a)));
+                }
+            }
+            t.cOff = cOff[n];
         }
     }
     const int logNmax = ilog2(nmaxF);
@@ -883,6 +913,7 @@ wf_status hp_build_ring_tables(wf_plan p)
         tw[t] = make_double2(std::cos(a), std::sin(a));
     }
     if (Vtab.empty()) Vtab.push_back(make_double2(0, 0));
+    if (chirp.empty()) chirp.push_back(make_double2(0, 0));
     p->tab.logNmax = logNmax;
     p->tab.bmax = bmax;
     p->tab.maxBlue = maxBlue;
@@ -893,11 +924,13 @@ wf_status hp_build_ring_tables(wf_plan p)
     if (f32) {
         if ((st = upload_cx<float>(p, &p->tab.roots, roots)) != WF_OK) return st;
         if ((st = upload_cx<float>(p, &p->tab.V, Vtab)) != WF_OK) return st;
+        if ((st = upload_cx<float>(p, &p->tab.chirp, chirp)) != WF_OK) return st;
         if ((st = upload_cx<float>(p, &p->tab.tw, tw)) != WF_OK) return st;
         if ((st = RingLaunch<float>::grid(p, &p->tab.ringGrid)) != WF_OK) return st;
     } else {
         if ((st = upload_cx<double>(p, &p->tab.roots, roots)) != WF_OK) return st;
         if ((st = upload_cx<double>(p, &p->tab.V, Vtab)) != WF_OK) return st;
+        if ((st = upload_cx<double>(p, &p->tab.chirp, chirp)) != WF_OK) return st;
         if ((st = upload_cx<double>(p, &p->tab.tw, tw)) != WF_OK) return st;
         if ((st = RingLaunch<double>::grid(p, &p->tab.ringGrid)) != WF_OK) return st;
     }
