@@ -849,7 +849,9 @@ def run_pol_batch(args):
         N6 = np.stack([Nc[:, 0, 0], Nc[:, 1, 1], Nc[:, 2, 2], Nc[:, 0, 1], Nc[:, 0, 2], Nc[:, 1, 2]])
         common = {"noise_var": T(N6.ravel()), "mask": T(P["mask"]), "C_ell": T(P["c_ell"].T.ravel()),
                   "tol": args.pol_tol}
-        items.append(dict(common, kind="wf", d=sig + T(P["noise"].ravel()), s_out=torch.empty_like(sig)))
+        nalm3 = 3 * (lmax + 1) * (lmax + 2) // 2
+        items.append(dict(common, kind="wf", d=sig + T(P["noise"].ravel()), s_out=torch.empty_like(sig),
+                          alm_out=torch.empty(nalm3, dtype=torch.complex128, device=dev)))
         items.append(dict(common, kind="fluct", g1=T(P["g1"].ravel()), g2=T(P["g2"].ravel()),
                           s_out=torch.empty_like(sig)))
         geo += [(ns, lmax)] * 2
@@ -890,6 +892,44 @@ def run_pol_batch(args):
         ms = float(np.median(ts))
         out[name] = {"ms": ms, "iters": iters, "crs_per_s": n / (ms / 1e3), "iters_per_s": iters / (ms / 1e3),
                      "converged": int(sum(r["converged"] for r in reps)), "launches": int(sum(r["launches"] for r in reps))}
+    # convergence of the batched solves by nside (the FP64 operator's verdict for mixed plans)
+    by_nside = {}
+    for (ns_, _), r_ in zip(geo, reps):
+        b_ = by_nside.setdefault(str(ns_), {"solves": 0, "converged": 0, "max_final_residual": 0.0, "iters": []})
+        b_["solves"] += 1
+        b_["converged"] += int(bool(r_["converged"]))
+        b_["max_final_residual"] = max(b_["max_final_residual"], float(r_["final_residual"]))
+        b_["iters"].append(int(r_["iters"]))
+    for b_ in by_nside.values():
+        b_["iters"] = {"min": min(b_["iters"]), "max": max(b_["iters"])}
+    err = None
+    if rank == 0 and not args.no_cpu:
+        # error against the FP64 oracle: one Wiener-filter result per nside, its returned
+        # (I, Q, U) map on sampled rings against the oracle's synthesis of its returned
+        # (T, E, B) a_lm (the first ring, the last polar-cap ring, a belt ring, the equator)
+        import oracle
+
+        err = {}
+        for ns_ in sorted(set(int(x) for x in nsides)):
+            i_ = 2 * [int(x) for x in nsides].index(ns_)
+            lm_ = 2 * ns_
+            na_ = (lm_ + 1) * (lm_ + 2) // 2
+            npx = 12 * ns_ * ns_
+            a3 = items[i_]["alm_out"].cpu().numpy().reshape(3, na_)
+            m3 = items[i_]["s_out"].cpu().numpy().reshape(3, npx)
+            rings = [0, ns_ - 1, ns_ + 3, 2 * ns_ - 1]
+            e_ = 0.0
+            for r0 in rings:
+                sl = ring_slices(ns_, [r0])[0]
+                t_ref = oracle.synthesis(ns_, lm_, lm_, a3[0], rings=(r0, r0 + 1))[sl]
+                q_ref, u_ref = oracle.synthesis_pol(ns_, lm_, lm_, a3[1], a3[2], rings=(r0, r0 + 1))
+                for got, ref in ((m3[0][sl], t_ref), (m3[1][sl], q_ref[sl]), (m3[2][sl], u_ref[sl])):
+                    e_ = max(e_, float(np.max(np.abs(got - ref)) / max(float(np.max(np.abs(ref))), 1e-300)))
+            err[str(ns_)] = e_
+        err = {"result_map_vs_oracle_synthesis_of_result_alm": err,
+               "basis": "max |GPU - oracle| / max |oracle| per component on rings 0, nside - 1, nside + 3, "
+                        "2 nside - 1 of one Wiener-filter result per nside: the returned (I, Q, U) map against "
+                        "the oracle's FP64 synthesis of the returned (T, E, B) a_lm"}
     # kernel families of one full-band polarised iteration at the largest nside (profiled replay)
     nb = int(max(nsides))
     it = items[int(np.argmax(nsides)) * 2]
@@ -904,7 +944,7 @@ def run_pol_batch(args):
     res = {"metric": "batched polarised constrained realisations (WF + fluctuation pairs) per second",
            "unit": "CR/s", "value": out["batched"]["crs_per_s"], "n_gpus": 1, "higher_is_better": True,
            "maps": n, "nsides": [int(x) for x in nsides], "one_by_one": out.get("one_by_one"),
-           "batched": out["batched"],
+           "batched": out["batched"], "by_nside": by_nside, "err_vs_oracle": err,
            "speedup": out["one_by_one"]["ms"] / out["batched"]["ms"] if "one_by_one" in out else None,
            "full_band_iteration": {"nside": nb, "lmax": 2 * nb, "ms": iter_ms, "families_ms": fam},
            "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
