@@ -902,6 +902,9 @@ def run_pol_batch(args):
         b_["iters"].append(int(r_["iters"]))
     for b_ in by_nside.values():
         b_["iters"] = {"min": min(b_["iters"]), "max": max(b_["iters"])}
+    per_item = [{"nside": int(ns_), "kind": it_["kind"], "iters": int(r_["iters"]), "converged": bool(r_["converged"]),
+                 "final_residual": float(r_["final_residual"]), "status": int(r_["status"])}
+                for (ns_, _), it_, r_ in zip(geo, items, reps)]
     err = None
     if rank == 0 and not args.no_cpu:
         # error against the FP64 oracle: one Wiener-filter result per nside, its returned
@@ -944,7 +947,7 @@ def run_pol_batch(args):
     res = {"metric": "batched polarised constrained realisations (WF + fluctuation pairs) per second",
            "unit": "CR/s", "value": out["batched"]["crs_per_s"], "n_gpus": 1, "higher_is_better": True,
            "maps": n, "nsides": [int(x) for x in nsides], "one_by_one": out.get("one_by_one"),
-           "batched": out["batched"], "by_nside": by_nside, "err_vs_oracle": err,
+           "batched": out["batched"], "by_nside": by_nside, "per_item": per_item, "err_vs_oracle": err,
            "speedup": out["one_by_one"]["ms"] / out["batched"]["ms"] if "one_by_one" in out else None,
            "full_band_iteration": {"nside": nb, "lmax": 2 * nb, "ms": iter_ms, "families_ms": fam},
            "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",

@@ -84,7 +84,7 @@ typedef struct {
  * fields take the defaults shown. */
 typedef struct {
     int maxiter;        /* total iteration cap (default 20000) */
-    int level_cap;      /* iterations at one lambda level before it is left anyway (HEALPix 3000, flat 200) */
+    int level_cap;      /* iterations at one lambda level before it is left anyway (HEALPix 300, flat 200) */
     double eta;         /* plateau: |chi2_k - chi2_{k-1}| < eta sqrt(2 n_dof) (HEALPix 3e-5, flat 1e-2) */
     int ell0;           /* HEALPix: first l_iter (20) */
     int ell_step_max;   /* HEALPix: largest increase of l_iter per level (500) */

@@ -584,15 +584,18 @@ struct HpSchedule {
 
 // HEALPix defaults.  The plateau constant and level cap decide how long each
 // lambda level of the Sect. 3 cooling runs (the paper gives no values): a
-// strict plateau (eta = 3e-5 of sigma_chi2, at most 3000 iterations per level)
-// removes more of the slow modes' error while lambda > 1, where they converge
-// faster (Eq. 5), and reached 1e-4 three times sooner than eta = 1e-2 / 200 on
-// the nside 512 and 2048 workloads and on the serving problems.  The flat
-// grid keeps its own schedule (flat_solve).
+// strict plateau (eta = 3e-5 of sigma_chi2) removes more of the slow modes'
+// error while lambda > 1, where they converge faster (Eq. 5), and reached 1e-4
+// three times sooner than eta = 1e-2 on the nside 512 and 2048 workloads and on
+// the serving problems.  Fluctuation solves (Eq. 9), whose source excites the
+// masked high-prior modes, rarely meet that plateau: the cap of 300 iterations
+// per level bounds their levels (a 3000 cap took them 2-4x more iterations)
+// and leaves the Wiener-filter solves unchanged (they leave each level on the
+// plateau).  The flat grid keeps its own schedule (flat_solve).
 wf_options defaults(wf_options o)
 {
     if (o.maxiter <= 0) o.maxiter = 20000;
-    if (o.level_cap <= 0) o.level_cap = 3000;
+    if (o.level_cap <= 0) o.level_cap = 300;
     if (!(o.eta > 0)) o.eta = 3e-5;
     if (o.ell0 <= 0) o.ell0 = 20;
     if (o.ell_step_max <= 0) o.ell_step_max = 500;
