@@ -106,6 +106,15 @@ __device__ void warp_fft(double2 *x, int logn, int sign, const double2 *tw /* e^
 
 enum FlatStep { FS_ITER = 0, FS_PROLOGUE = 1, FS_FLUCT_SRC = 2, FS_OUT = 3 };
 
+// dynamic shared memory of k_flat_solve: twiddles; a, column and row buffers; per-warp FFT
+// rows; S, 1/S and S / (S + lam tau) per owned mode; r, nu and 1 / (1 + (lam - 1) tau nu)
+// per owned pixel
+inline size_t flat_smem(int n, int P, int RP, int nh)
+{
+    return (size_t)(n / 2) * 16 + (size_t)P * n * 16 * 2 + (size_t)RP * nh * 16 + (size_t)FLAT_WARPS * n * 16 +
+           (size_t)P * n * 8 * 3 + (size_t)RP * n * 8 * 3;
+}
+
 __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
     k_flat_solve(FlatArgs A)
 {
@@ -114,6 +123,7 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
     const int n = A.n, nh = A.nh, P = A.P, RP = A.RP, logn = A.logn;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int c0 = c * P;
+    const double inv_tau = 1.0 / A.tau;
     const int ncol = max(0, min(nh, c0 + P) - c0);
     const int y0 = c * RP;
     const double sy = rsqrt((double)n), sx = rsqrt((double)n);
@@ -127,6 +137,9 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
     double *Scol = reinterpret_cast<double *>(wscr + (size_t)FLAT_WARPS * n);  // P * n
     double *rpix = Scol + (size_t)P * n;                             // RP * n
     double *nupix = rpix + (size_t)RP * n;                           // RP * n
+    double *invden = nupix + (size_t)RP * n;                         // RP * n: 1 / (1 + (lam - 1) tau nu)
+    double *Sinv = invden + (size_t)RP * n;                          // P * n: 1 / S (0 where S = 0)
+    double *fcol = Sinv + (size_t)P * n;                             // P * n: S / (S + lam tau)
     __shared__ double part[4];   // pix chi2, harm chi2, resid^2, spare
     __shared__ double red[FLAT_WARPS][3];
 
@@ -139,7 +152,9 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
         const int kl = i / n, ky = i % n;
         const int kx = c0 + kl;
         acol[i] = make_double2(0.0, 0.0);
-        Scol[i] = (kl < ncol) ? A.S[(size_t)ky * nh + kx] : 0.0;
+        const double S = (kl < ncol) ? A.S[(size_t)ky * nh + kx] : 0.0;
+        Scol[i] = S;
+        Sinv[i] = S > 0.0 ? 1.0 / S : 0.0;
     }
     for (int i = tid; i < RP * n; i += blockDim.x) {
         const size_t g = (size_t)y0 * n + i;
@@ -147,6 +162,20 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
         nupix[i] = A.nu[g];
     }
     __syncthreads();
+
+    // the per-pixel and per-mode factors of Eqs. (3) and (4) for one lambda (FP64 divisions
+    // once per cooling level, not once per iteration)
+    double cur_lam = NAN;
+    auto set_level = [&](double lam) {
+        const double lm1t = (lam - 1.0) * A.tau, lt = lam * A.tau;
+        for (int i = tid; i < RP * n; i += blockDim.x) invden[i] = 1.0 / (1.0 + lm1t * nupix[i]);
+        for (int i = tid; i < P * n; i += blockDim.x) {
+            const double S = Scol[i];
+            fcol[i] = S > 0.0 ? S / (S + lt) : 0.0;
+        }
+        cur_lam = lam;
+        __syncthreads();
+    };
 
     auto block_reduce3 = [&](double a, double b, double d) {
         for (int o = 16; o >= 1; o >>= 1) {
@@ -177,6 +206,9 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
     };
 
     // ---- step 2: rows: gather, c2r, blend (or other use), r2c into rowbuf ----
+    // Two real rows per complex FFT: the inverse DFT of Xa + i Xb (both Hermitian) is
+    // xa + i xb, and the forward DFT Z of ta + i tb gives Ta = (Z_k + conj Z_-k) / 2 and
+    // Tb = (Z_k - conj Z_-k) / 2i.
     auto step2 = [&](int mode, double lam) -> double {
         for (int i = tid; i < RP * nh; i += blockDim.x) {
             const int yl = i / nh, kx = i % nh;
@@ -185,49 +217,63 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
             rowbuf[(size_t)yl * nh + kx] = rc[(size_t)kl * n + (y0 + yl)];
         }
         __syncthreads();
-        const double lt = lam * A.tau, lm1t = (lam - 1.0) * A.tau;
+        const double lt = lam * A.tau;
         double acc = 0.0;
         double2 *x = wscr + (size_t)warp * n;
-        for (int yl = warp; yl < RP; yl += FLAT_WARPS) {
-            const double2 *b = rowbuf + (size_t)yl * nh;
+        for (int yp = warp; 2 * yp < RP; yp += FLAT_WARPS) {
+            const int ya = 2 * yp;
+            double2 *ba = rowbuf + (size_t)ya * nh, *bb = ba + nh;
             for (int kx = lane; kx < n; kx += 32) {
-                double2 v;
-                if (kx < nh) v = b[kx];
-                else v = cconj(b[n - kx]);
-                x[kx] = v;
+                double2 va, vb;
+                if (kx < nh) {
+                    va = ba[kx];
+                    vb = bb[kx];
+                } else {
+                    va = cconj(ba[n - kx]);
+                    vb = cconj(bb[n - kx]);
+                }
+                x[kx] = make_double2(va.x - vb.y, va.y + vb.x);
             }
             __syncwarp();
-            warp_fft(x, logn, +1, tw);  // real part = c2r
+            warp_fft(x, logn, +1, tw);  // real part: row ya, imaginary part: row ya + 1
             for (int xx = lane; xx < n; xx += 32) {
-                const double s = x[xx].x * sx;
-                const int pi = yl * n + xx;
-                double t = s;
-                if (mode == FS_ITER) {
-                    const double nv = nupix[pi], rv = rpix[pi];
-                    const double den = 1.0 + lm1t * nv;
-                    t = s + lt * (rv - nv * s) / den;
-                    acc += (nv * s * s - 2.0 * rv * s) / den;
-                } else if (mode == FS_PROLOGUE) {
-                    t = rpix[pi];
-                } else if (mode == FS_FLUCT_SRC) {
-                    const double rv = sqrt(nupix[pi]) * A.g1[(size_t)y0 * n + pi] + s;
-                    rpix[pi] = rv;
-                    t = rv;
-                } else {  // FS_OUT
-                    A.s_out[(size_t)y0 * n + pi] = s;
-                    const double nv = nupix[pi];
-                    if (nv > 0.0) {
-                        const double e = rpix[pi] - nv * s;
-                        acc += e * e / nv;  // nu (d - s)^2
+                double tt[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const double s = (h ? x[xx].y : x[xx].x) * sx;
+                    const int pi = (ya + h) * n + xx;
+                    double t = s;
+                    if (mode == FS_ITER) {
+                        const double nv = nupix[pi], rv = rpix[pi], id = invden[pi];
+                        t = s + lt * (rv - nv * s) * id;
+                        acc += (nv * s * s - 2.0 * rv * s) * id;
+                    } else if (mode == FS_PROLOGUE) {
+                        t = rpix[pi];
+                    } else if (mode == FS_FLUCT_SRC) {
+                        const double rv = sqrt(nupix[pi]) * A.g1[(size_t)y0 * n + pi] + s;
+                        rpix[pi] = rv;
+                        t = rv;
+                    } else {  // FS_OUT
+                        A.s_out[(size_t)y0 * n + pi] = s;
+                        const double nv = nupix[pi];
+                        if (nv > 0.0) {
+                            const double e = rpix[pi] - nv * s;
+                            acc += e * e / nv;  // nu (d - s)^2
+                        }
                     }
+                    tt[h] = t;
                 }
-                x[xx] = make_double2(t, 0.0);
+                x[xx] = make_double2(tt[0], tt[1]);
             }
             __syncwarp();
             if (mode == FS_ITER || mode == FS_PROLOGUE) {
                 warp_fft(x, logn, -1, tw);
-                double2 *bo = rowbuf + (size_t)yl * nh;
-                for (int kx = lane; kx < nh; kx += 32) bo[kx] = cscale(x[kx], sx);
+                for (int kx = lane; kx < nh; kx += 32) {
+                    const double2 z = x[kx], zc = cconj(x[(n - kx) & (n - 1)]);
+                    const double2 d = make_double2(0.5 * (z.x - zc.x), 0.5 * (z.y - zc.y));
+                    ba[kx] = cscale(make_double2(0.5 * (z.x + zc.x), 0.5 * (z.y + zc.y)), sx);
+                    bb[kx] = cscale(make_double2(d.y, -d.x), sx);
+                }
             }
             __syncwarp();
         }
@@ -245,7 +291,6 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
             colbuf[i] = rb[(size_t)yl * nh + (c0 + kl)];
         }
         __syncthreads();
-        const double lt = lam * A.tau;
         const bool full = (lam == 1.0);
         for (int kl = warp; kl < ncol; kl += FLAT_WARPS) {
             double2 *x = colbuf + (size_t)kl * n;
@@ -262,11 +307,11 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
                 const double2 ao = acol[(size_t)kl * n + ky];
                 double2 an = make_double2(0.0, 0.0);
                 if (S > 0.0) {
-                    const double f = S / (S + lt);
-                    an = cscale(th, f);
-                    chi2h += w * (ao.x * ao.x + ao.y * ao.y) / S;
+                    const double si = Sinv[(size_t)kl * n + ky];
+                    an = cscale(th, fcol[(size_t)kl * n + ky]);
+                    chi2h += w * (ao.x * ao.x + ao.y * ao.y) * si;
                     if (full) {
-                        const double k = 1.0 / S + 1.0 / A.tau;
+                        const double k = si + inv_tau;
                         const double dx = k * (ao.x - an.x), dy = k * (ao.y - an.y);
                         res2 += w * (dx * dx + dy * dy);
                     }
@@ -330,6 +375,7 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
             if (k >= A.maxiter) { stop_reason = 2; break; }
             lam = A.levels[lev];
         }
+        if (!(lam == cur_lam)) set_level(lam);
         step1();
         cluster.sync();
         const double pc = step2(FS_ITER, lam);
@@ -466,8 +512,7 @@ wf_status flat_create(wf_plan p)
     p->npix = (long long)n * n;
     p->nalm = (long long)n * f->nh;
     p->omega = 1.0;
-    f->smem = (size_t)(n / 2) * 16 + (size_t)f->P * n * 16 * 2 + (size_t)f->RP * f->nh * 16 +
-              (size_t)FLAT_WARPS * n * 16 + (size_t)f->P * n * 8 + (size_t)f->RP * n * 8 * 2;
+    f->smem = flat_smem(n, f->P, f->RP, f->nh);
     wf_status st;
     if ((st = plan_alloc(p, (void **)&f->r, p->npix * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&f->nu, p->npix * 8)) != WF_OK) return st;
@@ -478,8 +523,7 @@ wf_status flat_create(wf_plan p)
     // (n = FLAT_MAXN) so that a smaller plan never lowers it under a larger one
     {
         const int nm = FLAT_MAXN, nhm = nm / 2 + 1, Pm = (nhm + FLAT_CS - 1) / FLAT_CS, RPm = nm / FLAT_CS;
-        const size_t smax = (size_t)(nm / 2) * 16 + (size_t)Pm * nm * 16 * 2 + (size_t)RPm * nhm * 16 +
-                            (size_t)FLAT_WARPS * nm * 16 + (size_t)Pm * nm * 8 + (size_t)RPm * nm * 8 * 2;
+        const size_t smax = flat_smem(nm, Pm, RPm, nhm);
         WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     }
     return WF_OK;
@@ -824,14 +868,12 @@ extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double 
     A.tr_res = tr + 2 * NOALLOC_MAXITER;
     A.tr_cap = NOALLOC_MAXITER;
     A.status = status;
-    const size_t smem = (size_t)(n / 2) * 16 + (size_t)A.P * n * 16 * 2 + (size_t)A.RP * nh * 16 +
-                        (size_t)FLAT_WARPS * n * 16 + (size_t)A.P * n * 8 + (size_t)A.RP * n * 8 * 2;
+    const size_t smem = flat_smem(n, A.P, A.RP, nh);
     {
         // the dynamic shared-memory limit is per function: set it for the largest grid this
         // entry point takes (n = NOALLOC_MAXN), on every call (a plan may have changed it)
         const int nm = NOALLOC_MAXN, nhm = nm / 2 + 1, Pm = (nhm + FLAT_CS - 1) / FLAT_CS, RPm = nm / FLAT_CS;
-        const size_t smax = (size_t)(nm / 2) * 16 + (size_t)Pm * nm * 16 * 2 + (size_t)RPm * nhm * 16 +
-                            (size_t)FLAT_WARPS * nm * 16 + (size_t)Pm * nm * 8 + (size_t)RPm * nm * 8 * 2;
+        const size_t smax = flat_smem(nm, Pm, RPm, nhm);
         WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     }
     k_flat_solve<<<FLAT_CS, FLAT_THREADS, smem, stream>>>(A);
