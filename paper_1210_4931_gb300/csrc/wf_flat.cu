@@ -3,7 +3,8 @@
 //
 // The whole solve -- every iteration of Eqs. (3)-(4), the chi^2 of Eq. (6),
 // the residual and the cooling schedule -- runs in ONE persistent launch of a
-// single thread-block cluster of CS CTAs (CS = 8).  The grid never leaves the
+// single thread-block cluster of CS CTAs (CS = 16 where the device co-schedules
+// that non-portable size, else 8; flat_cluster_size).  The grid never leaves the
 // cluster's shared memory:
 //   CTA c owns pixel rows [c n/CS, (c+1) n/CS) (source r, inverse noise nu)
 //   and spectrum columns kx in [c P, (c+1) P), P = ceil((n/2+1)/CS) (a, S).
@@ -32,7 +33,8 @@ namespace cg = cooperative_groups;
 
 namespace wf {
 
-constexpr int FLAT_CS = 8;
+constexpr int FLAT_CS = 8;      // portable cluster size; the smallest the solve runs on
+constexpr int FLAT_CS_MAX = 16; // non-portable cluster size, used where the device co-schedules it
 constexpr int FLAT_THREADS = 256;
 constexpr int FLAT_WARPS = FLAT_THREADS / 32;
 constexpr int FLAT_MAXN = 128;
@@ -43,7 +45,7 @@ struct FlatStatus {
 };
 
 struct FlatPlan {
-    int n = 0, logn = 0, nh = 0, P = 0, RP = 0;
+    int n = 0, logn = 0, nh = 0, P = 0, RP = 0, cs = 8;
     size_t smem = 0;
     double *r = nullptr, *nu = nullptr;  // device pixel maps
     double *levels = nullptr;            // device lambda levels
@@ -115,8 +117,7 @@ inline size_t flat_smem(int n, int P, int RP, int nh)
            (size_t)P * n * 8 * 3 + (size_t)RP * n * 8 * 3;
 }
 
-__global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
-    k_flat_solve(FlatArgs A)
+__global__ void __launch_bounds__(FLAT_THREADS) k_flat_solve(FlatArgs A)
 {
     cg::cluster_group cluster = cg::this_cluster();
     const int c = (int)cluster.block_rank();
@@ -325,7 +326,7 @@ __global__ void __cluster_dims__(FLAT_CS, 1, 1) __launch_bounds__(FLAT_THREADS)
     // sum partial triplets over the cluster (same order in every CTA)
     auto cluster_sum = [&](double out[3]) {
         out[0] = out[1] = out[2] = 0.0;
-        for (int o = 0; o < FLAT_CS; ++o) {
+        for (int o = 0; o < (int)cluster.num_blocks(); ++o) {
             const double *pp = cluster.map_shared_rank(part, o);
             out[0] += pp[0];
             out[1] += pp[1];
@@ -493,6 +494,63 @@ __global__ void k_flat_setup(long long npix, const double *__restrict__ d, const
     }
 }
 
+// Cluster size of one solve of an n x n grid: FLAT_CS_MAX CTAs (half the columns and rows of
+// each CTA, on twice the SMs) where the device co-schedules such a cluster with this kernel's
+// shared memory and n >= 32 (the packed row FFTs need two rows per CTA), FLAT_CS otherwise.
+// Decided once per device, after the kernel's shared-memory limit is set.
+int flat_cluster_size(int n)
+{
+    if (n < 2 * FLAT_CS_MAX) return FLAT_CS;
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return FLAT_CS;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache[dev]) return cache[dev];
+    int cs = FLAT_CS;
+    if (cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        const int nm = FLAT_MAXN, nhm = nm / 2 + 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(FLAT_CS_MAX);
+        cfg.blockDim = dim3(FLAT_THREADS);
+        cfg.dynamicSmemBytes = flat_smem(nm, (nhm + FLAT_CS_MAX - 1) / FLAT_CS_MAX, nm / FLAT_CS_MAX, nhm);
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = FLAT_CS_MAX;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, k_flat_solve, &cfg) == cudaSuccess && ncl >= 1) cs = FLAT_CS_MAX;
+    }
+    cudaGetLastError();  // an unsupported size leaves the portable one
+    cache[dev] = cs;
+    return cs;
+}
+
+// one solve: a single cluster of cs CTAs
+wf_status flat_launch(const FlatArgs &A, int cs, size_t smem, cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs);
+    cfg.blockDim = dim3(FLAT_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = cs;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    WF_CUDA(cudaLaunchKernelEx(&cfg, k_flat_solve, A));
+    return WF_OK;
+}
+
 }  // namespace
 
 wf_status flat_create(wf_plan p)
@@ -507,12 +565,9 @@ wf_status flat_create(wf_plan p)
     f->logn = 0;
     while ((1 << f->logn) < n) ++f->logn;
     f->nh = n / 2 + 1;
-    f->P = (f->nh + FLAT_CS - 1) / FLAT_CS;
-    f->RP = n / FLAT_CS;
     p->npix = (long long)n * n;
     p->nalm = (long long)n * f->nh;
     p->omega = 1.0;
-    f->smem = flat_smem(n, f->P, f->RP, f->nh);
     wf_status st;
     if ((st = plan_alloc(p, (void **)&f->r, p->npix * 8)) != WF_OK) return st;
     if ((st = plan_alloc(p, (void **)&f->nu, p->npix * 8)) != WF_OK) return st;
@@ -526,6 +581,10 @@ wf_status flat_create(wf_plan p)
         const size_t smax = flat_smem(nm, Pm, RPm, nhm);
         WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     }
+    f->cs = flat_cluster_size(n);
+    f->P = (f->nh + f->cs - 1) / f->cs;
+    f->RP = n / f->cs;
+    f->smem = flat_smem(n, f->P, f->RP, f->nh);
     return WF_OK;
 }
 
@@ -644,9 +703,8 @@ wf_status flat_solve(wf_plan p, const double *d, const double *noise_var, const 
     A.tr_cap = f->tr_cap;
     A.status = f->status;
     pr.begin(WF_K_FLAT);
-    k_flat_solve<<<FLAT_CS, FLAT_THREADS, f->smem, p->stream>>>(A);
+    if (wf_status ls = flat_launch(A, f->cs, f->smem, p->stream)) return ls;
     WF_COUNT_LAUNCH(p);
-    WF_CUDA(cudaGetLastError());
     pr.end();
     FlatStatus fs;
     WF_CUDA(cudaMemcpyAsync(&fs, f->status, sizeof fs, cudaMemcpyDeviceToHost, p->stream));
@@ -848,8 +906,7 @@ extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double 
     A.logn = 0;
     while ((1 << A.logn) < n) ++A.logn;
     A.nh = nh;
-    A.P = (nh + FLAT_CS - 1) / FLAT_CS;
-    A.RP = n / FLAT_CS;
+    // (the cluster size is chosen below, once the kernel's shared-memory limit is set)
     A.r = r;
     A.nu = nu;
     A.S = S;
@@ -868,7 +925,6 @@ extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double 
     A.tr_res = tr + 2 * NOALLOC_MAXITER;
     A.tr_cap = NOALLOC_MAXITER;
     A.status = status;
-    const size_t smem = flat_smem(n, A.P, A.RP, nh);
     {
         // the dynamic shared-memory limit is per function: set it for the largest grid this
         // entry point takes (n = NOALLOC_MAXN), on every call (a plan may have changed it)
@@ -876,8 +932,10 @@ extern "C" wf_status wf_flat_solve_noalloc(int n, const double *d, const double 
         const size_t smax = flat_smem(nm, Pm, RPm, nhm);
         WF_CUDA(cudaFuncSetAttribute(k_flat_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax));
     }
-    k_flat_solve<<<FLAT_CS, FLAT_THREADS, smem, stream>>>(A);
-    WF_CUDA(cudaGetLastError());
+    const int cs = flat_cluster_size(n);
+    A.P = (nh + cs - 1) / cs;
+    A.RP = n / cs;
+    if (wf_status ls = flat_launch(A, cs, flat_smem(n, A.P, A.RP, nh), stream)) return ls;
     FlatStatus fs;
     WF_CUDA(cudaMemcpyAsync(&fs, status, sizeof fs, cudaMemcpyDeviceToHost, stream));
     WF_CUDA(cudaStreamSynchronize(stream));
