@@ -1183,15 +1183,23 @@ __device__ __forceinline__ void mx_ana_run(const MxPairs<NP> &P, int m, int L, i
             const int i = lane >> 2, q = lane & 3;
             const float4 *row = stage + 32 * i + 8 * q;
             const int c = q + 4 * (i & 1);
-            float4 v = row[c];
-            float2 sr = make_float2(v.x, v.y), si = make_float2(v.z, v.w);
+            // the eight stores summed as a tree of depth 3 (a chain of 7 dependent adds held
+            // each lane on its loads' latency)
+            float2 tr[8], ti[8];
 #pragma unroll
-            for (int j = 1; j < 8; ++j) {
-                v = row[j ^ c];
-                sr = __fadd2_rn(sr, make_float2(v.x, v.y));
-                si = __fadd2_rn(si, make_float2(v.z, v.w));
+            for (int j = 0; j < 8; ++j) {
+                const float4 v = row[j ^ c];
+                tr[j] = make_float2(v.x, v.y);
+                ti[j] = make_float2(v.z, v.w);
             }
-            float vr = sr.x + sr.y, vi = si.x + si.y;
+#pragma unroll
+            for (int w = 4; w >= 1; w >>= 1)
+#pragma unroll
+                for (int j = 0; j < w; ++j) {
+                    tr[j] = __fadd2_rn(tr[j], tr[j + w]);
+                    ti[j] = __fadd2_rn(ti[j], ti[j + w]);
+                }
+            float vr = tr[0].x + tr[0].y, vi = ti[0].x + ti[0].y;
             vr += __shfl_xor_sync(0xffffffffu, vr, 1);
             vi += __shfl_xor_sync(0xffffffffu, vi, 1);
             vr += __shfl_xor_sync(0xffffffffu, vr, 2);
