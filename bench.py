@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "tf32", "bf16"],
+                    help="mixed: FP32 Legendre kernels (the workload's default); tf32 / bf16: the same with the "
+                         "synthesis on the tensor cores (3xTF32 / split BF16); fp64: the FP64 path")
     ap.add_argument("--tol", type=float, default=None,
                     help="relative residual at which a solve stops (default 1e-6 on the flat grid, 1e-4 on the "
                          "HEALPix workloads, where 1e-6 is out of reach of the messenger iteration: its residual "
@@ -352,7 +354,7 @@ def run_ours(args):
     alm_out = torch.empty(plan.nalm, dtype=torch.complex128, device=dev)
     sched = 1 if args.schedule == "bound" else 0
     wf.wf_set_options(plan, profile=1, maxiter=args.maxiter, schedule=sched,
-                      refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0,
+                      refine_sweeps=args.refine_sweeps if args.precision != "fp64" else 0,
                       mixed_tol_factor=args.mixed_tol_factor)
     if args.full_band_iters > 0:
         wf.wf_set_schedule(plan, [1.0] * args.full_band_iters, [lmax] * args.full_band_iters)
@@ -421,16 +423,19 @@ def run_ours(args):
                           "2070 MHz = %.1f TFLOP/s" % (peak_meas["packed"], peak_meas["scalar"], n_sm, peak_units),
             "peak_units_tflops": peak_units,
             "flops_per_triple": LEG_FLOPS_PER_TRIPLE, "kernel_ms": leg_ms,
+            "note": "the synthesis runs on the tensor cores: the FP32 peak bounds the analysis only"
+                    if args.precision in ("tf32", "bf16") else None,
             "share_of_step": leg_ms / max(1e-9, sum(kms.values()))}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": {"mixed": "f32+f64", "fp64": "f64", "tf32": "tf32x3+f32+f64",
+                                            "bf16": "bf16x3+f32+f64"}[args.precision], "data": "synthetic",
            "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
                       "tol": args.tol, "schedule": args.schedule, "legendre_tiles": list(tiles),
                       "tol_check": "the result's residual under the FP64 operator (correction sweeps); the FP32 "
                                    "iteration stops at %g x tol" % args.mixed_tol_factor
-                                   if args.precision == "mixed" and args.refine_sweeps > 0 else "own operator",
+                                   if args.precision != "fp64" and args.refine_sweeps > 0 else "own operator",
                       "l2": "inputs (1.2 GB) larger than L2",
                       "parallelism": "replicas"},
            "time_to_tol_s": t_ms / args.steps / 1e3 if last["converged"] else None,
@@ -454,7 +459,7 @@ def run_ours(args):
         nvh, mh, clh = P["noise_var"], P["mask"], P["c_ell"]
         sh = np.empty(plan.npix)
         wf.wf_set_options(plan, profile=0, maxiter=args.maxiter, schedule=sched,
-                          refine_sweeps=args.refine_sweeps if args.precision == "mixed" else 0,
+                          refine_sweeps=args.refine_sweeps if args.precision != "fp64" else 0,
                           mixed_tol_factor=args.mixed_tol_factor)
         wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)  # warm
         t0 = time.perf_counter()
