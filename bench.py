@@ -454,10 +454,16 @@ def run_ours(args):
            "roofline": roof, "clocks": ck}
 
     if rank == 0 and not args.no_e2e:
-        # e2e: host buffers in, host map out, through wf_solve_host
-        dh = d.cpu().numpy()
-        nvh, mh, clh = P["noise_var"], P["mask"], P["c_ell"]
-        sh = np.empty(plan.npix)
+        # e2e: host buffers in, host map out, through wf_solve_host; the buffers are pinned
+        # (page-locked) host memory, so the copies run as DMA at the link's rate
+        def pinned(a):
+            t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+            t.numpy()[...] = a
+            return t.numpy()
+
+        dh = pinned(d.cpu().numpy())
+        nvh, mh, clh = pinned(P["noise_var"]), pinned(P["mask"]), pinned(P["c_ell"])
+        sh = torch.empty(plan.npix, dtype=torch.float64, pin_memory=True).numpy()
         wf.wf_set_options(plan, profile=0, maxiter=args.maxiter, schedule=sched,
                           refine_sweeps=args.refine_sweeps if args.precision != "fp64" else 0,
                           mixed_tol_factor=args.mixed_tol_factor)
@@ -467,7 +473,8 @@ def run_ours(args):
         te = time.perf_counter() - t0
         out["e2e"] = {"value": rep["iters"] / te, "unit": UNIT,
                       "h2d_bytes_per_step": int(dh.nbytes + nvh.nbytes + mh.nbytes + clh.nbytes),
-                      "d2h_bytes_per_step": int(sh.nbytes), "seconds_per_solve": te}
+                      "d2h_bytes_per_step": int(sh.nbytes), "seconds_per_solve": te,
+                      "host_buffers": "pinned"}
     if rank == 0 and ws == 1 and not args.no_cpu:
         # the oracle on a bounded sample of one iteration (timed), and the GPU's transforms of the
         # same inputs compared with the oracle's values on the sampled rings and m
@@ -1060,7 +1067,10 @@ def run_config2(args):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = Clocks(0)
-    for prec in ("fp64", "mixed"):
+    # fp64: the FP64 pipe throughout; fp64_emulated: the same FP64 plan with its Legendre transforms in
+    # double-float arithmetic on the FP32 pipe (about 48 significant bits; wf_options.fp64_emulation)
+    for leg in ("fp64", "fp64_emulated", "mixed"):
+        prec = "mixed" if leg == "mixed" else "fp64"
         plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec)
         if prec == "mixed":
             wf.wf_plan_autotune(plan)
@@ -1069,12 +1079,12 @@ def run_config2(args):
         d = s_sig + T(P["noise"])
         nv, mk, cl = T(P["noise_var"]), T(P["mask"]), T(P["c_ell"])
         s_out = torch.empty(plan.npix, dtype=torch.float64, device=dev)
-        wf.wf_set_options(plan, maxiter=args.maxiter, profile=1)
-        steps = args.steps if prec == "fp64" else max(1, args.steps)
-        for _ in range(args.warmup if prec == "fp64" else 1):
+        wf.wf_set_options(plan, maxiter=args.maxiter, profile=1, fp64_emulation=1 if leg == "fp64_emulated" else 0)
+        steps = args.steps if leg == "fp64" else max(1, args.steps)
+        for _ in range(args.warmup if leg == "fp64" else 1):
             wf.wf_solve(plan, d, nv, mk, cl, args.tol, s_out)
         torch.cuda.synchronize()
-        if prec == "fp64":
+        if leg == "fp64":
             clocks.start()
         step_ms, reps = [], []
         for _ in range(steps):
@@ -1083,7 +1093,7 @@ def run_config2(args):
             e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-        if prec == "fp64":
+        if leg == "fp64":
             out["clocks"] = clocks.stop()
         last = reps[-1]
         it_ms = np.concatenate([r["iter_ms_trace"] for r in reps])
@@ -1094,7 +1104,11 @@ def run_config2(args):
                "final_residual": float(last["final_residual"]), "chi2_over_ndof": float(last["chi2_over_ndof"]),
                "iter_ms_full_band": _pcts(it_ms[full]) if full.any() else None,
                "time_to_residual_s": time_to_residual(last), "ms_per_step": float(np.mean(step_ms))}
-        out[prec] = rec
+        if leg == "fp64_emulated":
+            rec["max_rel_diff_vs_fp64_map"] = float(torch.max(torch.abs(s_out - s_fp64)) / torch.max(torch.abs(s_fp64)))
+        if leg == "fp64":
+            s_fp64 = s_out.clone()
+        out[leg] = rec
         plan.close()
     out["value"] = out["fp64"]["iters_per_s"]
     out["ms_per_step"] = out["fp64"]["ms_per_step"]
