@@ -12,6 +12,9 @@ Sampled m: 0, 1, the middle, lmax - 1 and lmax.
 
 Tolerances (max norm relative to the max of the oracle's output):
   * FP64 plans: 1e-10.
+  * tf32 and bf16 plans (tensor-core synthesis, 3xTF32 or three-piece BF16 products
+    accumulated in FP32; FP32 analysis): 1e-4, as the mixed plans, whose FP32
+    contraction they replace with one of the same accuracy.
   * mixed plans (FP32 recurrence and contraction from FP64 seeds, FP64 low-l
     block): 1e-4.  The FP32 three-term recurrence over up to lmax steps has a
     worst-case relative error growth of ~L eps_32 (4096 x 6e-8 = 2.4e-4) and
@@ -58,7 +61,8 @@ def _m_slice(lmax, m):
     return slice(i0, i0 + lmax + 1 - m)
 
 
-@pytest.mark.parametrize("nside,precision", [(1024, "mixed"), (2048, "mixed"), (1024, "fp64"), (2048, "fp64")])
+@pytest.mark.parametrize("nside,precision", [(1024, "mixed"), (2048, "mixed"), (1024, "fp64"), (2048, "fp64"),
+                                             (2048, "tf32"), (1024, "bf16")])
 def test_fullsize_basis_change_on_sampled_rings_and_m(wf, nside, precision):
     import torch
 
@@ -67,8 +71,8 @@ def test_fullsize_basis_change_on_sampled_rings_and_m(wf, nside, precision):
     cl = gen.cmb_like_cl(lmax, 5.0)
     a = gen.alm_unit_gaussian(rng, lmax) * np.sqrt(cl[gen.alm_ell(lmax)] + 1e-30)
     plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=precision)
-    tiles = wf.wf_plan_autotune(plan) if precision == "mixed" else None
-    tol = 1e-4 if precision == "mixed" else 1e-10
+    tiles = wf.wf_plan_autotune(plan) if precision != "fp64" else None
+    tol = 1e-10 if precision == "fp64" else 1e-4
     m_gpu = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
     wf.wf_alm2map(plan, T(a), lmax, m_gpu)
     mg = m_gpu.cpu().numpy()
@@ -89,4 +93,34 @@ def test_fullsize_basis_change_on_sampled_rings_and_m(wf, nside, precision):
         errs["m %d" % m] = float(np.max(np.abs(bg[sl] - ref)) / np.max(np.abs(ref)))
     plan.close()
     print("nside %d %s tiles %s: %s" % (nside, precision, tiles, errs))
+    assert max(errs.values()) < tol, errs
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_fullsize_polarised_synthesis_on_sampled_rings(wf, precision):
+    """(I, Q, U) synthesis of CMB-like (T, E, B) at nside 1024 / lmax 2048, the largest maps
+    of the 32-map polarised workload, against the oracle's spin-0 and spin-2 sums on the
+    sampled rings (tolerances as above)."""
+    import torch
+
+    nside, lmax = 1024, 2048
+    rng = np.random.default_rng(9100)
+    ell = gen.alm_ell(lmax)
+    tt = gen.cmb_like_cl(lmax, 5.0)
+    a = np.stack([gen.alm_unit_gaussian(rng, lmax) * np.sqrt(tt[ell] * f + 1e-30) for f in (1.0, 0.05, 0.005)])
+    a[1:, ell < 2] = 0.0
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=precision, ncomp=3)
+    tol = 1e-4 if precision == "mixed" else 1e-10
+    m = torch.empty(3 * plan.npix, dtype=torch.float64, device="cuda")
+    wf.wf_alm2map(plan, T(a.ravel()), lmax, m)
+    got = m.cpu().numpy().reshape(3, plan.npix)
+    plan.close()
+    errs = {}
+    for r, n in _rings(nside):
+        sl = _ring_slice(nside, r)
+        I = oracle.synthesis(nside, lmax, lmax, a[0], rings=(r, r + 1))[sl]
+        Q, U = oracle.synthesis_pol(nside, lmax, lmax, a[1], a[2], rings=(r, r + 1))
+        for c, ref in enumerate((I, Q[sl], U[sl])):
+            errs["ring %d comp %d" % (r, c)] = float(np.max(np.abs(got[c][sl] - ref)) / np.max(np.abs(ref)))
+    print("pol nside %d %s: %s" % (nside, precision, max(errs.values())))
     assert max(errs.values()) < tol, errs
