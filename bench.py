@@ -83,7 +83,9 @@ def parse():
     ap.add_argument("--pol-nsides", default="32,64,128", help="nside choices of the polarised maps (lmax = 2 nside)")
     ap.add_argument("--pol-tol", type=float, default=1e-4)
     ap.add_argument("--pol-maxiter", type=int, default=3000)
-    ap.add_argument("--pol-precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--pol-precision", default="mixed", choices=["mixed", "fp64", "tf32", "bf16"],
+                    help="tf32 / bf16: the T and spin-2 syntheses on the tensor cores, maps of one nside "
+                         "sharing one launch per step")
     ap.add_argument("--pol-no-alone", action="store_true", help="time the batch only (no one-by-one comparison)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batching workload instead: this many solves of mixed nside (64-256), "
@@ -962,7 +964,8 @@ def run_pol_batch(args):
            "batched": out["batched"], "by_nside": by_nside, "per_item": per_item, "err_vs_oracle": err,
            "speedup": out["one_by_one"]["ms"] / out["batched"]["ms"] if "one_by_one" in out else None,
            "full_band_iteration": {"nside": nb, "lmax": 2 * nb, "ms": iter_ms, "families_ms": fam},
-           "dtype": "f64" if prec == "fp64" else "f32+f64", "data": "synthetic",
+           "dtype": {"fp64": "f64", "mixed": "f32+f64", "tf32": "tf32x3+f32+f64", "bf16": "bf16x3+f32+f64"}[prec],
+           "data": "synthetic",
            "config": {"workload": "batch_IQU_CR_nside" + "-".join(str(c) for c in choices), "precision": prec,
                       "tol": args.pol_tol, "maxiter": args.pol_maxiter,
                       "timing": "CUDA events around the whole call, median of --steps runs"}}

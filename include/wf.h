@@ -67,7 +67,9 @@ typedef enum {
                                (tcgen05): the FP32 recurrence values and c a_lm split into TF32 head + tail,
                                hi*hi + hi*lo + lo*hi accumulated in FP32 ("3xTF32", FP32-grade accuracy).
                                Maps of one geometry in one wf_solve_batch share the recurrence (one launch).
-                               Temperature HEALPix plans (ncomp = 1) */
+                               HEALPix plans; polarised ones (ncomp = 3) run the spin-2 synthesis on the
+                               tensor cores too (the (Re, Im) of E + iB and E - iB against the spin +-2
+                               recurrences) */
     WF_PREC_MIXED_SPLITBF16 = 3 /* as MIXED_TF32 with BF16 operands: each value split into three BF16 pieces
                                    (successive round-to-nearest of the exact remainders, ~24 significant bits)
                                    and the six products of total order <= 2 accumulated in FP32 */
@@ -77,7 +79,7 @@ typedef struct {
     wf_geom_kind kind;
     int nx, ny;  /* flat only: nx = ny, a power of two, 16 <= n <= 128 */
     int nside;   /* HEALPix only */
-    int ncomp;   /* 1 (temperature) or 3 (polarised I, Q, U: HEALPix, FP64 or mixed) */
+    int ncomp;   /* 1 (temperature) or 3 (polarised I, Q, U: HEALPix, any precision) */
 } wf_geometry;
 
 /* Options of the cooling schedule and stopping rule (Sect. 3).  Zero-filled

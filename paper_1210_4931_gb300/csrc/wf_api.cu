@@ -703,6 +703,18 @@ struct HpRun {
 
 wf_status hp_begin_pol(HpRun &R);
 wf_status hp_launch_pol(HpRun &R);
+// a bounded wait of a tensor-core kernel that gave up voids the result (WF_ETIMEOUT; the flag is cleared)
+wf_status tc_check(wf_plan p)
+{
+    if (!tc_prec(p->prec)) return WF_OK;
+    int tc_err = 0;
+    WF_CUDA(cudaMemcpyAsync(&tc_err, p->ws.tc_err, sizeof tc_err, cudaMemcpyDeviceToHost, p->stream));
+    WF_CUDA(cudaStreamSynchronize(p->stream));
+    if (!tc_err) return WF_OK;
+    WF_CUDA(cudaMemsetAsync(p->ws.tc_err, 0, sizeof(int), p->stream));
+    return set_error(WF_ETIMEOUT, "a tensor-core kernel's bounded wait for its MMAs gave up");
+}
+
 wf_status hp_end_pol(HpRun &R);
 
 wf_status hp_begin(HpRun &R)
@@ -1086,16 +1098,7 @@ wf_status hp_end(HpRun &R)
     }
     pr.finish();
     wf_status result = R.result;
-    if (tc_prec(p->prec)) {
-        // a bounded wait of a tensor-core kernel that gave up voids the result
-        int tc_err = 0;
-        WF_CUDA(cudaMemcpyAsync(&tc_err, p->ws.tc_err, sizeof tc_err, cudaMemcpyDeviceToHost, p->stream));
-        WF_CUDA(cudaStreamSynchronize(p->stream));
-        if (tc_err) {
-            WF_CUDA(cudaMemsetAsync(p->ws.tc_err, 0, sizeof(int), p->stream));
-            return set_error(WF_ETIMEOUT, "a tensor-core kernel's bounded wait for its MMAs gave up");
-        }
-    }
+    if (wf_status te = tc_check(p)) return te;
     if (result == WF_OK && !R.replay && !R.converged) result = WF_ENOCONV;
     if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", R.last_resid);
     if (result == WF_EDIVERGE && R.chi2_bad) set_error(result, "chi^2 is not finite at iteration %d", R.k);
@@ -1375,6 +1378,7 @@ wf_status hp_end_pol(HpRun &R)
             info->refine_sweeps = si.iters;
             info->mixed_lc = R.lc;
         }
+        if ((st = tc_check(p)) != WF_OK) return st;
         if (si.converged) return WF_OK;
         set_error(WF_ENOCONV, "not converged after %d FP64 sweeps (residual %.3e)", si.iters, si.final_residual);
         return R.replay ? WF_OK : WF_ENOCONV;
@@ -1413,6 +1417,7 @@ wf_status hp_end_pol(HpRun &R)
         info->mixed_lc = R.lc;
     }
     R.pr.finish();
+    if ((st = tc_check(p)) != WF_OK) return st;
     wf_status result = R.result;
     if (result == WF_OK && !R.replay && !R.converged) result = WF_ENOCONV;
     if (result == WF_ENOCONV) set_error(result, "iteration cap reached (residual %.3e)", R.last_resid);
@@ -1576,23 +1581,38 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
                 const int i0 = cfg[u].first;
                 wf_plan p0 = plans[i0];
                 if (!tc_prec(p0->prec) || R[i0].rigorous || group_of[i0] >= 0) continue;
+                // polarised items group with polarised items of the same spin-2 FP64 block; their
+                // T columns (the temperature kernel) and E, B columns (the spin-2 kernel) share a launch each
+                const bool pol = p0->pol != nullptr;
+                const int cap = pol ? std::min(TC_MAX_COLUMNS, TCP_MAX_COLUMNS) : TC_MAX_COLUMNS;
                 std::vector<int> mem{i0};
-                for (size_t v = u + 1; v < cfg.size() && (int)mem.size() < TC_MAX_COLUMNS; ++v) {
+                for (size_t v = u + 1; v < cfg.size() && (int)mem.size() < cap; ++v) {
                     const int j = cfg[v].first;
                     wf_plan pj = plans[j];
                     if (group_of[j] < 0 && pj->prec == p0->prec && !R[j].rigorous &&
-                        pj->nside == p0->nside && pj->lmax == p0->lmax && pj->tab.lc_mx == p0->tab.lc_mx)
+                        pj->nside == p0->nside && pj->lmax == p0->lmax && pj->tab.lc_mx == p0->tab.lc_mx &&
+                        (pj->pol != nullptr) == pol && (!pol || pj->pol->lc == p0->pol->lc))
                         mem.push_back(j);
                 }
-                std::vector<const double2 *> ga;
-                std::vector<float2 *> gG, gca;
+                std::vector<const double2 *> ga, gE, gB;
+                std::vector<float2 *> gG, gca, gQ, gU;
+                std::vector<float4 *> gac;
                 std::vector<int> gL;
                 int Lmax = 0;
                 for (int j : mem) {
                     group_of[j] = ngroups;
-                    ga.push_back(plans[j]->ws.a);
-                    gca.push_back(plans[j]->ws.ca32);
-                    gG.push_back((float2 *)plans[j]->ws.G);
+                    wf_plan pj = plans[j];
+                    const double2 *a = pol ? pj->pol->a : pj->ws.a;
+                    ga.push_back(a);
+                    gca.push_back(pj->ws.ca32);
+                    gG.push_back((float2 *)pj->ws.G);
+                    if (pol) {
+                        gE.push_back(a + pj->nalm);
+                        gB.push_back(a + 2 * pj->nalm);
+                        gac.push_back(pj->pol->ac32);
+                        gQ.push_back((float2 *)pj->pol->GQ);
+                        gU.push_back((float2 *)pj->pol->GU);
+                    }
                     gL.push_back(R[j].L);
                     Lmax = std::max(Lmax, R[j].L);
                 }
@@ -1601,6 +1621,9 @@ wf_status hp_solve_batch(int n, wf_plan *plans, const wf_batch_item *items, cuda
                 const int fam = p0->kfam;
                 p0->kfam = WF_K_LEG_SYN;
                 st = hp_tc_synthesis(p0, (int)mem.size(), ga.data(), gca.data(), gG.data(), gL.data(), Lmax, origin);
+                if (st == WF_OK && pol)
+                    st = hp_pol_tc_synthesis(p0, (int)mem.size(), gE.data(), gB.data(), gac.data(), gQ.data(),
+                                             gU.data(), gL.data(), Lmax, origin);
                 p0->kfam = fam;
                 for (int f = 0; f < WF_NK; ++f) {
                     group_cnt[i0][f] = p0->kcnt[f] - k0[f];
@@ -1763,6 +1786,7 @@ long long hp_estimate_bytes(int nside, int lmax, wf_precision prec, bool staging
     if (tc_prec(prec)) b += nalm * 8;                            // c a_lm in FP32 (tensor-core synthesis)
     if (ncomp == 3) {  // polarisation (PolState)
         const long long lcap = (lmax + 1) / 8 + 1;                  // FP64-block allowance, as above
+        if (tc_prec(prec)) b += nalm * 16;                           // spin-2 B operand source (FP32 x 4)
         b += nalm * 8 * 3 + ns * (4 + 32);                           // al, be, ga; ls and the four seeds
         b += 3 * 3 * nalm * 16;                                      // a, a_new, b for T, E, B
         b += 4 * np * (lmax + 1) * 2 * ec;                           // GQ, GU, FQ, FU
@@ -1813,8 +1837,8 @@ wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void
     if (prec != WF_PREC_FP64 && prec != WF_PREC_MIXED_FP32 && prec != WF_PREC_MIXED_TF32 &&
         prec != WF_PREC_MIXED_SPLITBF16)
         return set_error(WF_EINVAL, "unknown precision");
-    if (tc_prec(prec) && (g->kind != WF_GEOM_HEALPIX || g->ncomp == 3))
-        return set_error(WF_EUNSUPPORTED, "tensor-core plans are temperature HEALPix plans");
+    if (tc_prec(prec) && g->kind != WF_GEOM_HEALPIX)
+        return set_error(WF_EUNSUPPORTED, "tensor-core plans are HEALPix plans");
     wf_plan p = new (std::nothrow) wf_plan_s();
     if (!p) return set_error(WF_ENOMEM, "host allocation");
     p->g = *g;

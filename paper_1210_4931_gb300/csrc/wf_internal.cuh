@@ -89,6 +89,7 @@ struct PolState {
     double *c = nullptr;       // per alm
     int *ls_mx = nullptr;      // per (m, pair): first l of the FP32 recurrence
     float4 *seed = nullptr;    // per (m, pair): mu+ at ls_mx, ls_mx + 1; mu- at ls_mx, ls_mx + 1
+    float4 *ac32 = nullptr;    // tensor-core plans: c (Re A, Im A, Re C, Im C) in FP32, the spin-2 B operand's source
     float2 *GQlow = nullptr, *GUlow = nullptr;  // FP64 block's ring coefficients [pair][m < lc][hemisphere]
     double2 *Elow = nullptr, *Blow = nullptr;   // FP64 block's (E, B)
     int lc = -1, low_cap = 0;
@@ -255,6 +256,11 @@ wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 
                           const int *L, int Lmax, cudaStream_t stream);
 size_t tc_syn_smem(int nc, int L);
 wf_status tc_prepare(int lmax);
+// polarised plans: the spin-2 synthesis of up to TCP_MAX_COLUMNS columns (four B rows per column)
+constexpr int TCP_MAX_COLUMNS = 8;
+wf_status hp_pol_tc_synthesis(wf_plan p, int ncols, const double2 *const *E, const double2 *const *B,
+                              float4 *const *ac, float2 *const *GQ, float2 *const *GU, const int *L, int Lmax,
+                              cudaStream_t stream);
 
 // ring transforms (wf_ring.cu)
 wf_status hp_build_ring_tables(wf_plan p);

@@ -79,7 +79,6 @@ const char *request_error(const wf_request &r)
     if (r.nside < 1 || r.lmax < 2 || r.lmax > 2 * r.nside) return "need 2 <= lmax <= 2 nside";
     if (r.precision != WF_PREC_FP64 && r.precision != WF_PREC_MIXED_FP32 && !wf::tc_prec(r.precision))
         return "unknown precision";
-    if (wf::tc_prec(r.precision) && r.ncomp == 3) return "tensor-core precisions are for temperature requests";
     if (r.ncomp != 0 && r.ncomp != 1 && r.ncomp != 3) return "ncomp must be 0, 1 or 3";
     if (!(r.tol > 0)) return "tol must be > 0";
     if (!r.noise_var || !r.C_ell || !r.s_out) return "noise_var, C_ell and s_out are required";

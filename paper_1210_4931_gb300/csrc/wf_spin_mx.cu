@@ -617,6 +617,7 @@ wf_status hp_pol_create_mx(wf_plan p)
     if ((st = plan_alloc(p, (void **)&s->Blow, nalm * sizeof(double2))) != WF_OK) return st;
     if ((st = to_device(p, s->c, c.data(), nalm * sizeof(double))) != WF_OK) return st;
     if ((st = to_device(p, s->tab, tab.data(), nalm * sizeof(float4))) != WF_OK) return st;
+    if (tc_prec(p->prec) && (st = plan_alloc(p, (void **)&s->ac32, nalm * sizeof(float4))) != WF_OK) return st;
     s->lc = -1;
     if ((st = hp_pol_set_low_block(p, 0)) != WF_OK) return st;
     const size_t syn_max = syn_pm_smem<SYN_NP>(lmax, 0), ana_max = ana_pm_smem(lmax);
@@ -659,6 +660,12 @@ wf_status hp_pol_legendre_synthesis_mx(wf_plan p, const double2 *E, const double
     const HpTables &t = p->tab;
     wf_status st;
     if (s->lc > 0 && (st = hp_pol_legendre_synthesis_low(p, E, B, L, s->lc, s->GQlow, s->GUlow)) != WF_OK) return st;
+    if (tc_prec(p->prec)) {
+        // on the tensor cores; in a batch step the group launch (wf_solve_batch) has written GQ, GU already
+        if (p->tc_deferred) return WF_OK;
+        float2 *gq = (float2 *)s->GQ, *gu = (float2 *)s->GU;
+        return hp_pol_tc_synthesis(p, 1, &E, &B, &s->ac32, &gq, &gu, &L, L, p->stream);
+    }
     const int per_cta = PM_THREADS * SYN_NP;
     dim3 grid((p->npairs + per_cta - 1) / per_cta, L + 1);
     k_legsyn_pol_mx<SYN_NP><<<grid, PM_THREADS, syn_pm_smem<SYN_NP>(L, 0), p->stream>>>(

@@ -522,11 +522,362 @@ __global__ void k_tc_ca(int lmax, int ncols, const double *__restrict__ c64, TcP
     }
 }
 
+// ---------------------------------------------------------------------------
+// Spin-2 synthesis of polarised plans on the tensor cores.  Per m the FP32
+// kernels accumulate, for each ring pair and parity h of l - m,
+//     Ap_h = sum A mu+,  Am_h = sum A mu-,  Cp_h = sum C mu+,  Cm_h = sum C mu-,
+// A = c (E + iB), C = c (E - iB), and combine them into Q and U on the north
+// and south rings.  Here those sums are two products per parity,
+//     D+_h[p, n] = sum_k mu+[p, k] B_h[k, n],   D-_h[p, n] = sum_k mu-[p, k] B_h[k, n],
+// with the columns n = (Re A, Im A, Re C, Im C) of every map, so four
+// accumulators of nc = 4 ncols (rounded up to 16) columns, and an A operand of
+// two functions x two parities per chunk.  Arithmetic, layouts, waits and
+// staging as in k_legsyn_tc.
+// ---------------------------------------------------------------------------
+constexpr int TCP_BITEMS = 2;       // B items per thread per chunk (8 maps x 32 l / 128 threads)
+constexpr int TCP_TMEM_COLS = 256;  // D+E, D+O, D-E, D-O (nc <= 32 each) + the A operand (<= 128 columns)
+
+struct TcPolArgs {
+    int lmax, Lmax, npairs, ncols, nc;
+    const float4 *tab;             // per alm: (A, A be, A (1 + be) - 2, A (1 - be) - 2) of the mu+- recurrences
+    const int *ls;                 // per (m, pair): first l of the FP32 recurrences (> lmax: none)
+    const float4 *seed;            // per (m, pair): mu+ at ls, ls + 1; mu- at ls, ls + 1
+    const float *xp, *wp;          // per pair: x = cos theta and w = 1 - x
+    const float4 *ac[TCP_MAX_COLUMNS];  // per column: c (Re A, Im A, Re C, Im C) in FP32 (zero above its band limit)
+    float2 *GQ[TCP_MAX_COLUMNS], *GU[TCP_MAX_COLUMNS];  // per column: ring coefficients [pair][m][hemisphere]
+    int *err;                      // set when a bounded wait gives up
+};
+
+// one double step (l, l + 1) of both recurrences for one ring pair (scalar form of the
+// FP32 spin-2 step); t0, t1: the table entries of l and l + 1
+template <bool DIFF>
+__device__ __forceinline__ void tcp_step(float4 t0, float4 t1, float x, float w, float &Spa, float &Spb, float &Sqa,
+                                         float &Sqb, float &p0, float &p1, float &q0, float &q1)
+{
+    if (DIFF) {
+        float D = fmaf(fmaf(-t0.x, w, t0.z), Spb, Spa);
+        p0 = Spb + D;
+        D = fmaf(fmaf(-t1.x, w, t1.z), p0, D);
+        p1 = p0 + D;
+        Spa = D;
+        Spb = p1;
+        float Dq = fmaf(fmaf(-t0.x, w, t0.w), Sqb, Sqa);
+        q0 = Sqb + Dq;
+        Dq = fmaf(fmaf(-t1.x, w, t1.w), q0, Dq);
+        q1 = q0 + Dq;
+        Sqa = Dq;
+        Sqb = q1;
+    } else {
+        p0 = fmaf(fmaf(t0.x, x, t0.y), Spb, -Spa);
+        p1 = fmaf(fmaf(t1.x, x, t1.y), p0, -Spb);
+        q0 = fmaf(fmaf(t0.x, x, -t0.y), Sqb, -Sqa);
+        q1 = fmaf(fmaf(t1.x, x, -t1.y), q0, -Sqb);
+        Spa = p0;
+        Spb = p1;
+        Sqa = q0;
+        Sqb = q1;
+    }
+}
+
+template <bool DIFF, bool INJ>
+__device__ __forceinline__ void tcp_chunk(int l0, int ls, float4 sd, float x, float w, const float4 *tb, float &Spa,
+                                          float &Spb, float &Sqa, float &Sqb, float (&mup)[TC_KC],
+                                          float (&mum)[TC_KC])
+{
+#pragma unroll
+    for (int j = 0; j < TC_KC / 2; ++j) {
+        float p0, p1, q0, q1;
+        tcp_step<DIFF>(tb[2 * j], tb[2 * j + 1], x, w, Spa, Spb, Sqa, Sqb, p0, p1, q0, q1);
+        if (INJ && l0 + 2 * j == ls) {
+            p0 = sd.x;
+            p1 = sd.y;
+            q0 = sd.z;
+            q1 = sd.w;
+            Spa = DIFF ? sd.y - sd.x : sd.x;
+            Spb = sd.y;
+            Sqa = DIFF ? sd.w - sd.z : sd.z;
+            Sqb = sd.w;
+        }
+        mup[2 * j] = p0;
+        mup[2 * j + 1] = p1;
+        mum[2 * j] = q0;
+        mum[2 * j + 1] = q1;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(TC_THREADS) k_legsyn_pol_tc(TcPolArgs P)
+{
+    using AR = TcArith<KIND>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int qmin_s;
+    const int m = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int p = blockIdx.x * TC_THREADS + tid;
+    const int nc = P.nc;
+    const long long base = tc_mbase(P.lmax, m);
+    const size_t pstride = (size_t)(P.lmax + 1) * 2;
+
+    int ls = INT_MAX;
+    float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
+    float x = 0.f, w = 1.f;
+    if (p < P.npairs) {
+        const size_t si = (size_t)m * P.npairs + p;
+        const int l = P.ls[si];
+        if (l <= P.Lmax) {
+            ls = l;
+            sd = P.seed[si];
+        }
+        x = P.xp[p];
+        w = P.wp[p];
+    }
+    if (tid == 0) qmin_s = INT_MAX;
+    __syncthreads();
+    if (ls != INT_MAX) atomicMin(&qmin_s, (ls - m) / TC_KC);
+    __syncthreads();
+    const int q0 = qmin_s, q1 = (P.Lmax - m) / TC_KC;
+    if (q0 > q1) {  // no pair of the CTA has a term (block-uniform exit)
+        if (p < P.npairs)
+            for (int c = 0; c < P.ncols; ++c) {
+                const size_t o = (size_t)p * pstride + 2 * (size_t)m;
+                *reinterpret_cast<float4 *>(P.GQ[c] + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4 *>(P.GU[c] + o) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        return;
+    }
+    const bool diff = __shfl_sync(0xffffffffu, x > TC_X_DIFF ? 1 : 0, 0) != 0;
+
+    // shared: the B tiles ([parity][piece], nc x 16 k each), then the recurrence table of every l
+    // of the chunks this CTA runs, indexed by l - m (zero past lmax)
+    const uint32_t btile = (uint32_t)nc * 16 * AR::EB;
+    unsigned char *B = smem;
+    float4 *tb = reinterpret_cast<float4 *>(smem + 2 * AR::PIECES * btile);
+    for (int i = tid; i < (int)(2 * AR::PIECES * btile / 4); i += TC_THREADS) reinterpret_cast<uint32_t *>(B)[i] = 0u;
+    for (int j = TC_KC * q0 + tid; j < TC_KC * (q1 + 1); j += TC_THREADS)
+        tb[j] = m + j <= P.lmax ? P.tab[base + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nitems = P.ncols * TC_KC;
+    float4 pa[TCP_BITEMS];
+    auto prefetch = [&](int q) {
+#pragma unroll
+        for (int r = 0; r < TCP_BITEMS; ++r) {
+            const int it = tid + r * TC_THREADS;
+            pa[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (it < nitems && q <= q1) {
+                const int c = it / TC_KC, l = m + TC_KC * q + it % TC_KC;
+                if (l <= P.lmax) pa[r] = P.ac[c][base + (l - m)];
+            }
+        }
+    };
+    prefetch(q0);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "n"(TCP_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    // columns: D+ E, D+ O, D- E, D- O (nc each); A at 4 nc, laid out [function][parity][piece] in
+    // blocks of ACOLS columns
+    const uint32_t dP = tmem, dM = tmem + 2u * nc;
+    const uint32_t aT = tmem + 4u * nc;
+    const uint32_t idesc = idesc_of(AR::FMT, 128, nc);
+    const uint32_t lbo = (uint32_t)(nc >> 3) * 128, sbo = 128;
+    const uint32_t bsm = smem_addr(B);
+    uint64_t bdesc[2][AR::PIECES][AR::KSTEPS];
+#pragma unroll
+    for (int par = 0; par < 2; ++par)
+#pragma unroll
+        for (int h = 0; h < AR::PIECES; ++h)
+#pragma unroll
+            for (int s2 = 0; s2 < AR::KSTEPS; ++s2)
+                bdesc[par][h][s2] =
+                    smem_desc(bsm + (uint32_t)(AR::PIECES * par + h) * btile + 2 * s2 * lbo, lbo, sbo);
+    float Spa = 0.f, Spb = 0.f, Sqa = 0.f, Sqb = 0.f;
+    bool ok = true;
+    uint32_t phase = 0;
+    for (int q = q0; q <= q1; ++q) {
+        const int l0 = m + TC_KC * q;
+        float mup[TC_KC], mum[TC_KC];
+        const bool inj = __any_sync(0xffffffffu, ls >= l0 && ls < l0 + TC_KC);
+        const float4 *tq = tb + TC_KC * q;
+        if (diff) {
+            if (inj) tcp_chunk<true, true>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
+            else tcp_chunk<true, false>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
+        } else {
+            if (inj) tcp_chunk<false, true>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
+            else tcp_chunk<false, false>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
+        }
+        if (q > q0) {
+            ok = ok && mbar_wait(&mbar, phase, P.err);
+            phase ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int fn = 0; fn < 2; ++fn) {
+            const float(&mu)[TC_KC] = fn ? mum : mup;
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                const uint32_t blk = aT + lane_base + (uint32_t)((2 * fn + par) * AR::PIECES * AR::ACOLS);
+                if constexpr (KIND == 0) {
+                    uint32_t hi[16], lo[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) split_tf32(mu[2 * j + par], hi[j], lo[j]);
+                    tmem_st16(blk, hi);
+                    tmem_st16(blk + 16, lo);
+                } else {
+                    uint32_t pk[3][8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        uint16_t e0[3], e1[3];
+                        split_bf16(mu[4 * j + par], e0);
+                        split_bf16(mu[4 * j + 2 + par], e1);
+#pragma unroll
+                        for (int h = 0; h < 3; ++h) pk[h][j] = (uint32_t)e0[h] | ((uint32_t)e1[h] << 16);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 3; ++h) tmem_st8(blk + 8 * h, pk[h]);
+                }
+            }
+        }
+        // B: the four coefficient rows of every column for the chunk's 32 l, split the same way
+#pragma unroll
+        for (int r = 0; r < TCP_BITEMS; ++r) {
+            const int it = tid + r * TC_THREADS;
+            if (it >= nitems) break;
+            const int c = it / TC_KC, i = it % TC_KC;
+            const int k = i >> 1, par = i & 1;
+            unsigned char *Bp = B + (size_t)(AR::PIECES * par) * btile;
+            const float v[4] = {pa[r].x, pa[r].y, pa[r].z, pa[r].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t off = b_offset(4 * c + e, k, nc, AR::EB);
+                if constexpr (KIND == 0) {
+                    uint32_t h0, h1;
+                    split_tf32(v[e], h0, h1);
+                    *reinterpret_cast<uint32_t *>(Bp + off) = h0;
+                    *reinterpret_cast<uint32_t *>(Bp + btile + off) = h1;
+                } else {
+                    uint16_t b3[3];
+                    split_bf16(v[e], b3);
+#pragma unroll
+                    for (int h = 0; h < 3; ++h) *reinterpret_cast<uint16_t *>(Bp + h * btile + off) = b3[h];
+                }
+            }
+        }
+        prefetch(q + 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc0 = q > q0 ? 1u : 0u;
+#pragma unroll
+            for (int fn = 0; fn < 2; ++fn)
+#pragma unroll
+                for (int par = 0; par < 2; ++par) {
+                    const uint32_t d = (fn ? dM : dP) + (par ? nc : 0);
+                    const uint32_t a0 = aT + (uint32_t)((2 * fn + par) * AR::PIECES * AR::ACOLS);
+#pragma unroll
+                    for (int s2 = 0; s2 < AR::KSTEPS; ++s2)
+#pragma unroll
+                        for (int u = 0; u < AR::NPROD; ++u) {
+                            const uint32_t a = a0 + AR::ACOLS * AR::pa(u) + 8 * s2;
+                            const uint32_t acc = (s2 == 0 && u == 0) ? acc0 : 1u;
+                            if constexpr (KIND == 0) mma_tf32_ts(d, a, bdesc[par][AR::pb(u)][s2], idesc, acc);
+                            else mma_f16_ts(d, a, bdesc[par][AR::pb(u)][s2], idesc, acc);
+                        }
+                }
+            mma_commit(&mbar);
+        }
+    }
+    ok = ok && mbar_wait(&mbar, phase, P.err);
+    ok = __syncthreads_and(ok) != 0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue, four columns (16 tensor-memory columns) per pass:
+    //   north: SAP = Ap_E + Ap_O, SCM = Cm_E + Cm_O;  south: SAP = Am_E - Am_O, SCM = Cp_E - Cp_O;
+    //   Q = -(SAP + SCM),  U = i (SAP - SCM)
+    if (ok) {
+        for (int c0 = 0; c0 < P.ncols; c0 += 4) {
+            uint32_t pe[16], po[16], me[16], mo[16];
+            tmem_ld16(dP + lane_base + 4 * c0, pe);
+            tmem_ld16(dP + nc + lane_base + 4 * c0, po);
+            tmem_ld16(dM + lane_base + 4 * c0, me);
+            tmem_ld16(dM + nc + lane_base + 4 * c0, mo);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (p < P.npairs) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c0 + j;
+                    if (c < P.ncols) {
+                        auto f = [&](const uint32_t(&v)[16], int e) { return __uint_as_float(v[4 * j + e]); };
+                        const float sapNr = f(pe, 0) + f(po, 0), sapNi = f(pe, 1) + f(po, 1);
+                        const float scmNr = f(me, 2) + f(mo, 2), scmNi = f(me, 3) + f(mo, 3);
+                        const float sapSr = f(me, 0) - f(mo, 0), sapSi = f(me, 1) - f(mo, 1);
+                        const float scmSr = f(pe, 2) - f(po, 2), scmSi = f(pe, 3) - f(po, 3);
+                        const size_t o = (size_t)p * pstride + 2 * (size_t)m;
+                        *reinterpret_cast<float4 *>(P.GQ[c] + o) =
+                            make_float4(-(sapNr + scmNr), -(sapNi + scmNi), -(sapSr + scmSr), -(sapSi + scmSi));
+                        *reinterpret_cast<float4 *>(P.GU[c] + o) =
+                            make_float4(-(sapNi - scmNi), sapNr - scmNr, -(sapSi - scmSi), sapSr - scmSr);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TCP_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// c (Re A, Im A, Re C, Im C) with A = E + iB, C = E - iB, in FP32 for every column (zero above the
+// column's band limit): the polarised B operand's source
+struct TcPolPrepArgs {
+    const double2 *E[TCP_MAX_COLUMNS], *B[TCP_MAX_COLUMNS];
+    float4 *ac[TCP_MAX_COLUMNS];
+    int L[TCP_MAX_COLUMNS];
+};
+
+__global__ void k_tcp_ac(int lmax, int ncols, const double *__restrict__ c, TcPolPrepArgs A)
+{
+    const int m = blockIdx.y;
+    const long long base = tc_mbase(lmax, m);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= lmax - m; j += gridDim.x * blockDim.x) {
+        const double cc = c[base + j];
+        for (int k = 0; k < ncols; ++k) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (m + j <= A.L[k]) {
+                const double2 e = A.E[k][base + j], b = A.B[k][base + j];
+                v = make_float4((float)((e.x - b.y) * cc), (float)((e.y + b.x) * cc), (float)((e.x + b.y) * cc),
+                                (float)((e.y - b.x) * cc));
+            }
+            A.ac[k][base + j] = v;
+        }
+    }
+}
+
 }  // namespace
 
 // B tiles (the larger of the two variants: 4 x 64 or 6 x 32 bytes per row) plus the coefficient
 // table of up to L / 32 + 1 chunks
 size_t tc_syn_smem(int nc, int L) { return (size_t)4 * nc * 64 + (size_t)16 * 16 * (L / TC_KC + 1) + 64; }
+
+// polarised: B tiles (nc <= 32) plus one table entry per l of up to L / 32 + 1 chunks
+size_t tcp_syn_smem(int nc, int L) { return (size_t)4 * nc * 64 + (size_t)16 * TC_KC * (L / TC_KC + 1) + 64; }
 
 // raise the synthesis kernels' shared-memory limits for plans up to lmax (at plan creation,
 // outside any stream capture)
@@ -534,6 +885,8 @@ wf_status tc_prepare(int lmax)
 {
     wf_status st = raise_smem_limit((const void *)k_legsyn_tc<0>, tc_syn_smem(32, lmax));
     if (st == WF_OK) st = raise_smem_limit((const void *)k_legsyn_tc<1>, tc_syn_smem(32, lmax));
+    if (st == WF_OK) st = raise_smem_limit((const void *)k_legsyn_pol_tc<0>, tcp_syn_smem(32, lmax));
+    if (st == WF_OK) st = raise_smem_limit((const void *)k_legsyn_pol_tc<1>, tcp_syn_smem(32, lmax));
     return st;
 }
 
@@ -581,6 +934,55 @@ wf_status hp_tc_synthesis(wf_plan p, int ncols, const double2 *const *a, float2 
     dim3 grid((p->npairs + TC_THREADS - 1) / TC_THREADS, Lmax + 1);
     if (p->prec == WF_PREC_MIXED_SPLITBF16) k_legsyn_tc<1><<<grid, TC_THREADS, sm, stream>>>(A);
     else k_legsyn_tc<0><<<grid, TC_THREADS, sm, stream>>>(A);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+// Spin-2 synthesis of ncols polarised columns sharing p's geometry and FP32 seeds (every
+// column's plan has p's nside, lmax and spin-2 FP64 block): one launch on `stream`, counted on p.
+wf_status hp_pol_tc_synthesis(wf_plan p, int ncols, const double2 *const *E, const double2 *const *B,
+                              float4 *const *ac, float2 *const *GQ, float2 *const *GU, const int *L, int Lmax,
+                              cudaStream_t stream)
+{
+    if (ncols < 1 || ncols > TCP_MAX_COLUMNS)
+        return set_error(WF_EINVAL, "polarised tensor-core synthesis: 1..%d columns", TCP_MAX_COLUMNS);
+    const PolState *s = p->pol;
+    const HpTables &t = p->tab;
+    {
+        TcPolPrepArgs pa{};
+        for (int c = 0; c < ncols; ++c) {
+            pa.E[c] = E[c];
+            pa.B[c] = B[c];
+            pa.ac[c] = ac[c];
+            pa.L[c] = L[c];
+        }
+        dim3 g((Lmax + 256) / 256, Lmax + 1);
+        k_tcp_ac<<<g, 256, 0, stream>>>(p->lmax, ncols, s->c, pa);
+        WF_COUNT_LAUNCH(p);
+        WF_CUDA(cudaGetLastError());
+    }
+    TcPolArgs A{};
+    A.lmax = p->lmax;
+    A.Lmax = Lmax;
+    A.npairs = p->npairs;
+    A.ncols = ncols;
+    A.nc = ((4 * ncols + 15) / 16) * 16;
+    A.tab = s->tab;
+    A.ls = s->ls_mx;
+    A.seed = s->seed;
+    A.xp = t.x32;
+    A.wp = t.w32;
+    for (int c = 0; c < ncols; ++c) {
+        A.ac[c] = ac[c];
+        A.GQ[c] = GQ[c];
+        A.GU[c] = GU[c];
+    }
+    A.err = p->ws.tc_err;
+    const size_t sm = tcp_syn_smem(A.nc, Lmax);  // the limit is raised at plan creation (tc_prepare)
+    dim3 grid((p->npairs + TC_THREADS - 1) / TC_THREADS, Lmax + 1);
+    if (p->prec == WF_PREC_MIXED_SPLITBF16) k_legsyn_pol_tc<1><<<grid, TC_THREADS, sm, stream>>>(A);
+    else k_legsyn_pol_tc<0><<<grid, TC_THREADS, sm, stream>>>(A);
     WF_COUNT_LAUNCH(p);
     WF_CUDA(cudaGetLastError());
     return WF_OK;

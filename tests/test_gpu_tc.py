@@ -70,11 +70,67 @@ def test_tc_synthesis_band_limit(wf, L, prec):
 def test_tc_plan_rejections(wf):
     for prec in ("tf32", "bf16"):
         with pytest.raises(wf.WfError) as e:
-            wf.wf_plan_create("healpix", nside=16, lmax=32, precision=prec, ncomp=3)
-        assert e.value.status == wf.WF_EUNSUPPORTED
-        with pytest.raises(wf.WfError) as e:
             wf.wf_plan_create("flat", n=32, precision=prec)
         assert e.value.status == wf.WF_EUNSUPPORTED
+
+
+def _cmb_teb(lmax, seed):
+    """CMB-like (T, E, B) with EE = 0.05 TT and BB = 0.005 TT, so that E and B both reach
+    the spin-2 synthesis, and no E, B power below l = 2."""
+    rng = np.random.default_rng(seed)
+    ell = gen.alm_ell(lmax)
+    tt = gen.cmb_like_cl(lmax, 4 * 3438.0 / lmax)
+    a = np.stack([gen.alm_unit_gaussian(rng, lmax) * np.sqrt(tt[ell] * f) for f in (1.0, 0.05, 0.005)])
+    a[1:, ell < 2] = 0.0
+    return a
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("nside,lmax", [(4, 8), (16, 32), (64, 100), (128, 256), (200, 400)])
+def test_tc_pol_synthesis_matches_oracle(wf, nside, lmax, prec):
+    """(I, Q, U) synthesis of a polarised tensor-core plan: T through the temperature
+    tensor-core kernel, E and B through the spin-2 one (the Re and Im of E + iB and E - iB
+    against the spin +2 and -2 recurrences, even and odd l - m in separate accumulators).
+    Each component within 5e-5 of the oracle (relative to its largest value, as the FP32
+    polarised kernels) and of the FP32 plan."""
+    import torch
+
+    a = _cmb_teb(lmax, 300 + nside)
+    I = oracle.synthesis(nside, lmax, lmax, a[0])
+    Q, U = oracle.synthesis_pol(nside, lmax, lmax, a[1], a[2])
+    out = {}
+    for pr in (prec, "mixed"):
+        plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=pr, ncomp=3)
+        m = torch.empty(3 * plan.npix, dtype=torch.float64, device="cuda")
+        wf.wf_alm2map(plan, T(a.ravel()), lmax, m)
+        out[pr] = m.cpu().numpy().reshape(3, plan.npix)
+        plan.close()
+    for c, ref in enumerate((I, Q, U)):
+        assert rel(out[prec][c], ref) < 5e-5, (c, rel(out[prec][c], ref))
+        assert rel(out[prec][c], out["mixed"][c]) < 5e-5, (c, rel(out[prec][c], out["mixed"][c]))
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("L", [0, 2, 33, 95])
+def test_tc_pol_synthesis_band_limit(wf, L, prec):
+    import torch
+
+    nside, lmax = 48, 96
+    rng = np.random.default_rng(17)
+    a = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+    a[1:, gen.alm_ell(lmax) < 2] = 0.0
+    plan = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3)
+    m = torch.empty(3 * plan.npix, dtype=torch.float64, device="cuda")
+    wf.wf_alm2map(plan, T(a.ravel()), L, m)
+    got = m.cpu().numpy().reshape(3, plan.npix)
+    plan.close()
+    I = oracle.synthesis(nside, lmax, L, a[0])
+    Q, U = oracle.synthesis_pol(nside, lmax, L, a[1], a[2])
+    for c, ref in enumerate((I, Q, U)):
+        if np.max(np.abs(ref)) == 0.0:
+            assert np.max(np.abs(got[c])) == 0.0
+        else:
+            assert rel(got[c], ref) < 5e-5, (c, rel(got[c], ref))
 
 
 @pytest.mark.parametrize("prec", ["tf32", "bf16"])
@@ -180,3 +236,52 @@ def test_tc_fluct_matches_mixed(wf, prec):
         plan.close()
     print("fluct rel diff", prec, rel(res[prec], res["mixed"]))
     assert rel(res[prec], res["mixed"]) < 1e-3
+
+
+@pytest.mark.parametrize("prec,nmaps", [("tf32", 3), ("tf32", 5), ("bf16", 2)])
+def test_tc_pol_batch_columns(wf, prec, nmaps):
+    """Polarised Wiener-filter + fluctuation pairs of one geometry and noise model in
+    wf_solve_batch: every step runs one temperature and one spin-2 tensor-core synthesis
+    for up to 8 items (5 maps = 10 items span two groups), and each item's result equals
+    the same solve run alone (same iterations and lambda trace, maps to 1e-12)."""
+    import torch
+
+    from gpu_util import healpix_pol_case
+
+    nside, lmax = 32, 64
+    P, basis, d, nu, obs, N6, C4 = healpix_pol_case(nside, lmax, gen.seed_for(4, 600 + nmaps))
+    npx = 12 * nside * nside
+    rng = np.random.default_rng(6000 + nmaps)
+    items = []
+    for k in range(nmaps):
+        dk = d + 0.1 * np.std(d) * rng.standard_normal(d.shape)
+        g1 = rng.standard_normal((3, npx))
+        g2 = np.stack([gen.alm_unit_gaussian(rng, lmax) for _ in range(3)])
+        common = {"noise_var": T(N6.ravel()), "mask": T(P["mask"]), "C_ell": T(C4.ravel()), "tol": 1e-4}
+        items.append(dict(common, kind="wf", d=T(dk.ravel()),
+                          s_out=torch.full((3 * npx,), float("nan"), dtype=torch.float64, device="cuda")))
+        items.append(dict(common, kind="fluct", g1=T(g1.ravel()), g2=T(g2.ravel()),
+                          s_out=torch.full((3 * npx,), float("nan"), dtype=torch.float64, device="cuda")))
+    alone = []
+    for it in items:
+        pl = wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3)
+        s = torch.empty_like(it["s_out"])
+        if it["kind"] == "wf":
+            rep = wf.wf_solve(pl, it["d"], it["noise_var"], it["mask"], it["C_ell"], it["tol"], s, trace_cap=20000)
+        else:
+            rep = wf.wf_fluct(pl, it["noise_var"], it["mask"], it["C_ell"], it["g1"], it["g2"], it["tol"], s,
+                              trace_cap=20000)
+        pl.close()
+        alone.append((s.cpu().numpy(), rep))
+    plans = [wf.wf_plan_create("healpix", nside=nside, lmax=lmax, precision=prec, ncomp=3) for _ in items]
+    reps = wf.wf_solve_batch(plans, items, trace_cap=20000)
+    for i, (it, rep, (s_alone, rep_alone)) in enumerate(zip(items, reps, alone)):
+        assert rep["status"] == wf.WF_OK and rep["converged"], (i, rep["status"], rep["final_residual"])
+        assert rep["iters"] == rep_alone["iters"], (i, rep["iters"], rep_alone["iters"])
+        np.testing.assert_array_equal(rep["lambda_trace"], rep_alone["lambda_trace"])
+        assert rel(it["s_out"].cpu().numpy(), s_alone) < 1e-12, (i, rel(it["s_out"].cpu().numpy(), s_alone))
+    ls = [r["kernel_launches"]["leg_syn"] for r in reps]
+    ls_alone = [r["kernel_launches"]["leg_syn"] for _, r in alone]
+    assert sum(ls) < sum(ls_alone)
+    for p in plans:
+        p.close()
