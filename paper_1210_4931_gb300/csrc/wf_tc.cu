@@ -548,60 +548,48 @@ struct TcPolArgs {
     int *err;                      // set when a bounded wait gives up
 };
 
-// one double step (l, l + 1) of both recurrences for one ring pair (scalar form of the
-// FP32 spin-2 step); t0, t1: the table entries of l and l + 1
+// one double step (l, l + 1) of both recurrences for one ring pair, the + and - functions in
+// the two halves of packed f32x2 operations (each half is the FP32 spin-2 kernels' step, with
+// the same roundings); t0, t1: the table entries of l and l + 1.  State S = (S+, S-).
 template <bool DIFF>
-__device__ __forceinline__ void tcp_step(float4 t0, float4 t1, float x, float w, float &Spa, float &Spb, float &Sqa,
-                                         float &Sqb, float &p0, float &p1, float &q0, float &q1)
+__device__ __forceinline__ void tcp_step(float4 t0, float4 t1, float2 x2, float2 w2, float2 &Sa, float2 &Sb,
+                                         float2 &V0, float2 &V1)
 {
     if (DIFF) {
-        float D = fmaf(fmaf(-t0.x, w, t0.z), Spb, Spa);
-        p0 = Spb + D;
-        D = fmaf(fmaf(-t1.x, w, t1.z), p0, D);
-        p1 = p0 + D;
-        Spa = D;
-        Spb = p1;
-        float Dq = fmaf(fmaf(-t0.x, w, t0.w), Sqb, Sqa);
-        q0 = Sqb + Dq;
-        Dq = fmaf(fmaf(-t1.x, w, t1.w), q0, Dq);
-        q1 = q0 + Dq;
-        Sqa = Dq;
-        Sqb = q1;
+        float2 D = __ffma2_rn(__ffma2_rn(make_float2(-t0.x, -t0.x), w2, make_float2(t0.z, t0.w)), Sb, Sa);
+        V0 = __fadd2_rn(Sb, D);
+        D = __ffma2_rn(__ffma2_rn(make_float2(-t1.x, -t1.x), w2, make_float2(t1.z, t1.w)), V0, D);
+        V1 = __fadd2_rn(V0, D);
+        Sa = D;
+        Sb = V1;
     } else {
-        p0 = fmaf(fmaf(t0.x, x, t0.y), Spb, -Spa);
-        p1 = fmaf(fmaf(t1.x, x, t1.y), p0, -Spb);
-        q0 = fmaf(fmaf(t0.x, x, -t0.y), Sqb, -Sqa);
-        q1 = fmaf(fmaf(t1.x, x, -t1.y), q0, -Sqb);
-        Spa = p0;
-        Spb = p1;
-        Sqa = q0;
-        Sqb = q1;
+        V0 = __ffma2_rn(__ffma2_rn(make_float2(t0.x, t0.x), x2, make_float2(t0.y, -t0.y)), Sb,
+                        make_float2(-Sa.x, -Sa.y));
+        V1 = __ffma2_rn(__ffma2_rn(make_float2(t1.x, t1.x), x2, make_float2(t1.y, -t1.y)), V0,
+                        make_float2(-Sb.x, -Sb.y));
+        Sa = V0;
+        Sb = V1;
     }
 }
 
 template <bool DIFF, bool INJ>
-__device__ __forceinline__ void tcp_chunk(int l0, int ls, float4 sd, float x, float w, const float4 *tb, float &Spa,
-                                          float &Spb, float &Sqa, float &Sqb, float (&mup)[TC_KC],
-                                          float (&mum)[TC_KC])
+__device__ __forceinline__ void tcp_chunk(int l0, int ls, float4 sd, float2 x2, float2 w2, const float4 *tb,
+                                          float2 &Sa, float2 &Sb, float (&mup)[TC_KC], float (&mum)[TC_KC])
 {
 #pragma unroll
     for (int j = 0; j < TC_KC / 2; ++j) {
-        float p0, p1, q0, q1;
-        tcp_step<DIFF>(tb[2 * j], tb[2 * j + 1], x, w, Spa, Spb, Sqa, Sqb, p0, p1, q0, q1);
+        float2 V0, V1;
+        tcp_step<DIFF>(tb[2 * j], tb[2 * j + 1], x2, w2, Sa, Sb, V0, V1);
         if (INJ && l0 + 2 * j == ls) {
-            p0 = sd.x;
-            p1 = sd.y;
-            q0 = sd.z;
-            q1 = sd.w;
-            Spa = DIFF ? sd.y - sd.x : sd.x;
-            Spb = sd.y;
-            Sqa = DIFF ? sd.w - sd.z : sd.z;
-            Sqb = sd.w;
+            V0 = make_float2(sd.x, sd.z);
+            V1 = make_float2(sd.y, sd.w);
+            Sa = DIFF ? make_float2(sd.y - sd.x, sd.w - sd.z) : V0;
+            Sb = V1;
         }
-        mup[2 * j] = p0;
-        mup[2 * j + 1] = p1;
-        mum[2 * j] = q0;
-        mum[2 * j + 1] = q1;
+        mup[2 * j] = V0.x;
+        mup[2 * j + 1] = V1.x;
+        mum[2 * j] = V0.y;
+        mum[2 * j + 1] = V1.y;
     }
 }
 
@@ -702,7 +690,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_pol_tc(TcPolArgs P)
             for (int s2 = 0; s2 < AR::KSTEPS; ++s2)
                 bdesc[par][h][s2] =
                     smem_desc(bsm + (uint32_t)(AR::PIECES * par + h) * btile + 2 * s2 * lbo, lbo, sbo);
-    float Spa = 0.f, Spb = 0.f, Sqa = 0.f, Sqb = 0.f;
+    float2 Sa = make_float2(0.f, 0.f), Sb = make_float2(0.f, 0.f);
+    const float2 x2 = make_float2(x, x), w2 = make_float2(w, w);
     bool ok = true;
     uint32_t phase = 0;
     for (int q = q0; q <= q1; ++q) {
@@ -711,11 +700,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_pol_tc(TcPolArgs P)
         const bool inj = __any_sync(0xffffffffu, ls >= l0 && ls < l0 + TC_KC);
         const float4 *tq = tb + TC_KC * q;
         if (diff) {
-            if (inj) tcp_chunk<true, true>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
-            else tcp_chunk<true, false>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
+            if (inj) tcp_chunk<true, true>(l0, ls, sd, x2, w2, tq, Sa, Sb, mup, mum);
+            else tcp_chunk<true, false>(l0, ls, sd, x2, w2, tq, Sa, Sb, mup, mum);
         } else {
-            if (inj) tcp_chunk<false, true>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
-            else tcp_chunk<false, false>(l0, ls, sd, x, w, tq, Spa, Spb, Sqa, Sqb, mup, mum);
+            if (inj) tcp_chunk<false, true>(l0, ls, sd, x2, w2, tq, Sa, Sb, mup, mum);
+            else tcp_chunk<false, false>(l0, ls, sd, x2, w2, tq, Sa, Sb, mup, mum);
         }
         if (q > q0) {
             ok = ok && mbar_wait(&mbar, phase, P.err);
