@@ -52,6 +52,12 @@ constexpr int TC_KC = 32;         // l values per chunk (16 even, 16 odd)
 constexpr int TC_MAXC = TC_MAX_COLUMNS;  // columns (maps) per launch
 constexpr float TC_X_DIFF = 0.4f; // rings with x > 0.4 run the difference form (as the FP32 kernels)
 constexpr long long TC_SPIN = 1LL << 22;  // bound on every mbarrier wait (then the error flag is set)
+// Chunks per tensor-memory accumulation run (temperature synthesis): the accumulators restart
+// from zero every TC_FLUSH chunks and each run is added into FP32 sums in shared memory with
+// round-to-nearest adds.  The tensor core adds its products into a running accumulator without that
+// rounding, so a run of hundreds of chunks drifts with the size of the running sum (2.5e-5 of
+// the largest value at lmax 4096, against 5e-6 for the FP32 FMA kernel).
+constexpr int TC_FLUSH = 4;
 
 __host__ __device__ inline long long tc_mbase(int lmax, int m) { return (long long)m * (2 * lmax + 3 - m) / 2; }
 
@@ -143,14 +149,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
         : "r"(taddr));
 }
 
-// x = hi + lo exactly: hi keeps the sign, exponent and top 10 mantissa bits of x
-// (the TF32 head, by truncation: one logical operation), lo = x - hi is exact in
-// FP32 with |lo| < 2^-10 |x|; the tensor core truncates lo to TF32 in turn, an
-// error below 2^-21 |x|
+// x ~ hi + lo: hi keeps the sign, exponent and top 10 mantissa bits of x (the TF32
+// head, by truncation: one logical operation); x - hi is exact in FP32 with
+// |x - hi| < 2^-10 |x|, and lo is it rounded to the nearest TF32 value (an error
+// below 2^-21 |x| of either sign), which the tensor core then takes exactly.  Letting
+// the tensor core truncate x - hi instead biases every tail towards zero, and the
+// biases of up to 4097 terms of one sign add up.
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
 {
     hi = __float_as_uint(x) & 0xFFFFE000u;
-    lo = __float_as_uint(x - __uint_as_float(hi));
+    lo = (__float_as_uint(x - __uint_as_float(hi)) + 0x1000u) & 0xFFFFE000u;
 }
 
 // x = b0 + b1 + b2 + (below 2^-24 |x|): three BF16 pieces by successive round-
@@ -310,9 +318,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     // indexed by (l - m) / 2 (zero past lmax: those terms have B = 0)
     const uint32_t btile = (uint32_t)nc * 16 * AR::EB;
     unsigned char *B = smem;
-    float4 *coef = reinterpret_cast<float4 *>(smem + 2 * AR::PIECES * btile);
+    // FP32 sums of the finished accumulation runs: entry j (D_E columns, then D_O) of thread t
+    // at j * TC_THREADS + t
+    float *fsum = reinterpret_cast<float *>(smem + 2 * AR::PIECES * btile);
+    float4 *coef = reinterpret_cast<float4 *>(fsum + 2 * nc * TC_THREADS);
     for (int i = tid; i < (int)(2 * AR::PIECES * btile / 4); i += TC_THREADS)
         reinterpret_cast<uint32_t *>(B)[i] = 0u;  // padding rows stay zero
+    for (int j = 0; j < 2 * nc; ++j) fsum[j * TC_THREADS + tid] = 0.f;
     for (int j = 16 * q0 + tid; j < 16 * (q1 + 1); j += TC_THREADS) {
         const int la = m + 2 * j, lb = la + 1;
         coef[j] = make_float4(la <= P.lmax ? P.A32[base + (la - m)] : 0.f, la <= P.lmax ? P.B32[base + (la - m)] : 0.f,
@@ -366,6 +378,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
             for (int s2 = 0; s2 < AR::KSTEPS; ++s2)
                 bdesc[par][h][s2] =
                     smem_desc(bsm + (uint32_t)(AR::PIECES * par + h) * btile + 2 * s2 * lbo, lbo, sbo);
+    // a finished run (this thread's lane of D_E and D_O) into the FP32 sums
+    auto flush = [&]() {
+        for (int b = 0; 16 * b < nc; ++b) {
+            uint32_t e[16], o[16];
+            tmem_ld16(dE + lane_base + 16 * b, e);
+            tmem_ld16(dO + lane_base + 16 * b, o);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                fsum[(16 * b + j) * TC_THREADS + tid] += __uint_as_float(e[j]);
+                fsum[(nc + 16 * b + j) * TC_THREADS + tid] += __uint_as_float(o[j]);
+            }
+        }
+    };
     float Sa = 0.f, Sb = 0.f;
     bool ok = true;
     uint32_t phase = 0;
@@ -387,6 +413,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
             phase ^= 1u;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (q > q0 && (q - q0) % TC_FLUSH == 0) flush();  // this chunk's MMAs restart the run
 #pragma unroll
         for (int par = 0; par < 2; ++par) {
             if constexpr (KIND == 0) {
@@ -444,7 +471,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t acc0 = q > q0 ? 1u : 0u;
+            const uint32_t acc0 = (q > q0 && (q - q0) % TC_FLUSH != 0) ? 1u : 0u;
             {
 #pragma unroll
                 for (int par = 0; par < 2; ++par) {
@@ -467,23 +494,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_legsyn_tc(TcSynArgs P)
     ok = ok && mbar_wait(&mbar, phase, P.err);
     ok = __syncthreads_and(ok) != 0;  // block-uniform: the loads below are warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: G_N = E + O, G_S = E - O per column (8 columns per pass of 16 tensor-memory columns)
+    // epilogue: the last run into the sums, then G_N = E + O, G_S = E - O per column
     if (ok) {
-        for (int c0 = 0; c0 < P.ncols; c0 += 8) {
-            uint32_t e[16], o[16];
-            tmem_ld16(dE + lane_base + 2 * c0, e);
-            tmem_ld16(dO + lane_base + 2 * c0, o);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (p < P.npairs) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int c = c0 + j;
-                    if (c < P.ncols) {
-                        const float er = __uint_as_float(e[2 * j]), ei = __uint_as_float(e[2 * j + 1]);
-                        const float orr = __uint_as_float(o[2 * j]), oi = __uint_as_float(o[2 * j + 1]);
-                        float2 *g = P.G[c] + (size_t)p * pstride + 2 * (size_t)m;
-                        *reinterpret_cast<float4 *>(g) = make_float4(er + orr, ei + oi, er - orr, ei - oi);
-                    }
+        flush();
+        if (p < P.npairs) {
+            for (int c = 0; c < P.ncols; ++c) {
+                {
+                    const float er = fsum[(2 * c) * TC_THREADS + tid], ei = fsum[(2 * c + 1) * TC_THREADS + tid];
+                    const float orr = fsum[(nc + 2 * c) * TC_THREADS + tid];
+                    const float oi = fsum[(nc + 2 * c + 1) * TC_THREADS + tid];
+                    float2 *g = P.G[c] + (size_t)p * pstride + 2 * (size_t)m;
+                    *reinterpret_cast<float4 *>(g) = make_float4(er + orr, ei + oi, er - orr, ei - oi);
                 }
             }
         }
@@ -861,9 +882,12 @@ __global__ void k_tcp_ac(int lmax, int ncols, const double *__restrict__ c, TcPo
 
 }  // namespace
 
-// B tiles (the larger of the two variants: 4 x 64 or 6 x 32 bytes per row) plus the coefficient
-// table of up to L / 32 + 1 chunks
-size_t tc_syn_smem(int nc, int L) { return (size_t)4 * nc * 64 + (size_t)16 * 16 * (L / TC_KC + 1) + 64; }
+// B tiles (the larger of the two variants: 4 x 64 or 6 x 32 bytes per row), the run sums, and the
+// coefficient table of up to L / 32 + 1 chunks
+size_t tc_syn_smem(int nc, int L)
+{
+    return (size_t)4 * nc * 64 + (size_t)2 * nc * TC_THREADS * 4 + (size_t)16 * 16 * (L / TC_KC + 1) + 64;
+}
 
 // polarised: B tiles (nc <= 32) plus one table entry per l of up to L / 32 + 1 chunks
 size_t tcp_syn_smem(int nc, int L) { return (size_t)4 * nc * 64 + (size_t)16 * TC_KC * (L / TC_KC + 1) + 64; }
