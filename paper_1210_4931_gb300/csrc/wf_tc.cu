@@ -152,9 +152,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 // x ~ hi + lo: hi keeps the sign, exponent and top 10 mantissa bits of x (the TF32
 // head, by truncation: one logical operation); x - hi is exact in FP32 with
 // |x - hi| < 2^-10 |x|, and lo is it rounded to the nearest TF32 value (an error
-// below 2^-21 |x| of either sign), which the tensor core then takes exactly.  Letting
-// the tensor core truncate x - hi instead biases every tail towards zero, and the
-// biases of up to 4097 terms of one sign add up.
+// below 2^-21 |x| of either sign, not a truncation towards zero), which the tensor
+// core then takes exactly.
 __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
 {
     hi = __float_as_uint(x) & 0xFFFFE000u;
