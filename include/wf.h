@@ -318,11 +318,9 @@ wf_status wf_probe_fp32_fma(void *cuda_stream, int packed, double *tflops);
  * n: power of two in [16, 128]; opt: may be NULL (defaults), opt->maxiter <=
  * 20000; anything larger is rejected with WF_EINVAL.  d, noise_var, mask, S,
  * s_wf, alm_out: device pointers as for wf_solve; cuda_stream: the stream to
- * use.  S must be finite and >= 0 (WF_EINVAL otherwise).  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current) and caches it per device: make that first call before
- * any stream capture, and do not use this entry point on a device after a
- * cudaDeviceReset of it (the cached address is then stale).  All calls share
+ * use.  S must be finite and >= 0 (WF_EINVAL otherwise).  Each call looks up
+ * the array's device address on the current device (cudaGetSymbolAddress);
+ * nothing is cached between calls.  All calls share
  * the array, so calls that overlap on the GPU race; each call writes what it
  * reads first.  Every copy of the call (status, traces) is ordered on
  * cuda_stream, and the call returns after that stream has synchronised. */

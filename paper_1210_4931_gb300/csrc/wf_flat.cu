@@ -761,12 +761,10 @@ wf_status flat_map2alm(wf_plan p, const double *map, double *alm)
 // iteration traces) in one file-scope device array instead of plan memory.
 // Limits: n <= 128 (a power of two >= 16) and at most 20000 iterations;
 // the array is 0.71 MiB and stays resident on every device that loads the
-// library.  In host code the array's symbol is not a device address: the
-// first call on a device looks up its address with cudaGetSymbolAddress
-// (with that device current) and caches it per device ordinal, so that first
-// call should come before any stream capture; a cudaDeviceReset of the device
-// invalidates the cached address, so the library must not be used on that
-// device afterwards.  All calls share the one array: calls that overlap on the
+// library.  In host code the array's symbol is not a device address: every
+// call looks up its address on the current device with cudaGetSymbolAddress,
+// so no address outlives the context it belongs to (a cudaDeviceReset between
+// calls is safe).  All calls share the one array: calls that overlap on the
 // GPU race; everything a call reads is written by that call first.  The prior
 // S must be finite and >= 0 (the largest S per radius is taken as an integer
 // maximum over the bit patterns, an order that holds for S >= 0 only).
@@ -823,21 +821,11 @@ __global__ void k_flat_radial_max(int n, const double *__restrict__ S, double *_
 static __device__ __align__(256) unsigned char g_flat_noalloc_scratch[NA_BYTES];
 
 namespace {
-std::mutex g_na_mutex;
-unsigned char *g_na_base[128] = {};
-
 wf_status noalloc_base(unsigned char **out)
 {
-    int dev = 0;
-    WF_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) return set_error(WF_EUNSUPPORTED, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_base[dev]) {
-        void *p = nullptr;
-        WF_CUDA(cudaGetSymbolAddress(&p, g_flat_noalloc_scratch));
-        g_na_base[dev] = (unsigned char *)p;
-    }
-    *out = g_na_base[dev];
+    void *p = nullptr;
+    WF_CUDA(cudaGetSymbolAddress(&p, g_flat_noalloc_scratch));
+    *out = (unsigned char *)p;
     return WF_OK;
 }
 }  // namespace
