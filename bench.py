@@ -58,11 +58,12 @@ def parse():
                          "HEALPix workloads, where 1e-6 is out of reach of the messenger iteration: its residual "
                          "tail decays as a power law)")
     ap.add_argument("--maxiter", type=int, default=3000, help="iteration cap of one solve (one step)")
-    ap.add_argument("--mixed-tol-factor", type=float, default=0.75,
+    ap.add_argument("--mixed-tol-factor", type=float, default=0.85,
                     help="mixed precision: the FP32 iteration stops at tol x factor, then FP64 sweeps check the "
                          "result against tol under the FP64 operator")
-    ap.add_argument("--refine-sweeps", type=int, default=2,
-                    help="FP64 lambda = 1 correction sweeps after the mixed iteration (0: none)")
+    ap.add_argument("--refine-sweeps", type=int, default=6,
+                    help="at most this many FP64 lambda = 1 correction sweeps after the mixed iteration; they stop "
+                         "once the FP64 operator's residual is below tol (0: none)")
     ap.add_argument("--schedule", default="heuristic", choices=["heuristic", "bound"],
                     help="cooling: the heuristic of Sect. 3 (default) or the chi^2 bound of Sect. 2.2")
     ap.add_argument("--nside", type=int, default=CFG["nside"])
@@ -436,7 +437,8 @@ def run_ours(args):
            "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
                       "tol": args.tol, "schedule": args.schedule, "legendre_tiles": list(tiles),
                       "tol_check": "the result's residual under the FP64 operator (correction sweeps); the FP32 "
-                                   "iteration stops at %g x tol" % args.mixed_tol_factor
+                                   "iteration stops at %g x tol, then at most %d sweeps"
+                                   % (args.mixed_tol_factor, args.refine_sweeps)
                                    if args.precision != "fp64" and args.refine_sweeps > 0 else "own operator",
                       "l2": "inputs (1.2 GB) larger than L2",
                       "parallelism": "replicas"},
