@@ -414,9 +414,9 @@ def run_ours(args):
     peak_meas = {"packed": wf.wf_probe_fp32_fma(True), "scalar": wf.wf_probe_fp32_fma(False)}
     peak = max(peak_meas.values())
     # DRAM bytes (read + write) of one full-band k_legsyn_mx<8> + k_legana_mx<8, 8> pair at nside 2048,
-    # lmax 4096, from a one-pass ncu capture of these kernels (665.6 + 737.2 MB); other sizes or tiles
+    # lmax 4096, from a one-pass ncu capture of these kernels (666.1 + 738.0 MB); other sizes or tiles
     # were not captured
-    traffic = 1402759680 if (nside, lmax, tuple(tiles), args.precision) == (2048, 4096, (8, 8), "mixed") else None
+    traffic = 1404146432 if (nside, lmax, tuple(tiles), args.precision) == (2048, 4096, (8, 8), "mixed") else None
     roof = {"bound": "alu", "kernel": "legendre synthesis + analysis (k_legsyn, k_legana)",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
             "traffic_basis": "DRAM bytes of one full-band synthesis + analysis pair (ncu dram__bytes_read.sum + "
