@@ -58,7 +58,11 @@ def parse():
                          "HEALPix workloads, where 1e-6 is out of reach of the messenger iteration: its residual "
                          "tail decays as a power law)")
     ap.add_argument("--maxiter", type=int, default=3000, help="iteration cap of one solve (one step)")
-    ap.add_argument("--mixed-tol-factor", type=float, default=0.85,
+    ap.add_argument("--mixed-correction", type=float, default=1.5,
+                    help="mixed precision: at lambda = 1 on the full band, once the residual is below tol x this, "
+                         "one FP64 step and then the FP32 iteration on the correction to that step's iterate "
+                         "(0: off)")
+    ap.add_argument("--mixed-tol-factor", type=float, default=0.98,
                     help="mixed precision: the FP32 iteration stops at tol x factor, then FP64 sweeps check the "
                          "result against tol under the FP64 operator")
     ap.add_argument("--refine-sweeps", type=int, default=6,
@@ -358,7 +362,8 @@ def run_ours(args):
     sched = 1 if args.schedule == "bound" else 0
     wf.wf_set_options(plan, profile=1, maxiter=args.maxiter, schedule=sched,
                       refine_sweeps=args.refine_sweeps if args.precision != "fp64" else 0,
-                      mixed_tol_factor=args.mixed_tol_factor)
+                      mixed_tol_factor=args.mixed_tol_factor,
+                      mixed_correction=args.mixed_correction if args.precision != "fp64" else 0.0)
     if args.full_band_iters > 0:
         wf.wf_set_schedule(plan, [1.0] * args.full_band_iters, [lmax] * args.full_band_iters)
     cap = max(args.maxiter, args.full_band_iters) + 16
@@ -394,10 +399,24 @@ def run_ours(args):
     # per-iteration times (p50/p99) at the full band, lambda = 1
     full = (last["lambda_trace"] == 1.0) & (last["L_trace"] == lmax)
     nsw = [int(r.get("refine_sweeps") or 0) for r in reps]
-    it_ms = np.concatenate([r["iter_ms_trace"][: len(r["iter_ms_trace"]) - k][
-        (r["lambda_trace"][: len(r["lambda_trace"]) - k] == 1.0) & (r["L_trace"][: len(r["L_trace"]) - k] == lmax)]
-        for r, k in zip(reps, nsw)])
+
+    def switch_index(r):
+        # the correction form's FP64 step: the first iteration with no chi^2 (-1: no switch)
+        nan = np.flatnonzero(np.isnan(r["chi2_trace"]))
+        return int(nan[0]) if nan.size and args.precision != "fp64" and args.mixed_correction > 0 else -1
+
+    def fp32_full_band(r, k):
+        # the mixed path's own full-band lambda = 1 iterations: no FP64 sweep, no FP64 switch step
+        n = len(r["iter_ms_trace"]) - k
+        sel = (r["lambda_trace"][:n] == 1.0) & (r["L_trace"][:n] == lmax)
+        j = switch_index(r)
+        if 0 <= j < n:
+            sel[j] = False
+        return r["iter_ms_trace"][:n][sel]
+
+    it_ms = np.concatenate([fp32_full_band(r, k) for r, k in zip(reps, nsw)])
     all_ms = np.concatenate([r["iter_ms_trace"] for r in reps])
+    sw = switch_index(last)
 
     # roofline of the dominant kernel: Legendre synthesis + analysis (FP32 ALU)
     kms = {k: sum(r["kernel_ms"][k] for r in reps) for k in reps[0]["kernel_ms"]}
@@ -437,8 +456,9 @@ def run_ours(args):
            "config": {"workload": CFG["workload"], "nside": nside, "lmax": lmax, "precision": args.precision,
                       "tol": args.tol, "schedule": args.schedule, "legendre_tiles": list(tiles),
                       "tol_check": "the result's residual under the FP64 operator (correction sweeps); the FP32 "
-                                   "iteration stops at %g x tol, then at most %d sweeps"
-                                   % (args.mixed_tol_factor, args.refine_sweeps)
+                                   "iteration (in correction form once lambda = 1 and its residual is below %g x "
+                                   "tol) stops at %g x tol, then at most %d sweeps"
+                                   % (args.mixed_correction, args.mixed_tol_factor, args.refine_sweeps)
                                    if args.precision != "fp64" and args.refine_sweeps > 0 else "own operator",
                       "l2": "inputs (1.2 GB) larger than L2",
                       "parallelism": "replicas"},
@@ -447,6 +467,8 @@ def run_ours(args):
            "time_to_paper_stop_s": time_to_dchi2(last, lmax),
            "iters_per_solve": last["iters"],
            "maxiter": args.maxiter, "mixed_lc": last.get("mixed_lc"), "fp64_sweeps": last.get("refine_sweeps"),
+           "correction_switch": {"iter": sw, "fp64_step_ms": float(last["iter_ms_trace"][sw]),
+                                 "fp64_residual_at_switch": float(last["resid_trace"][sw])} if sw >= 0 else None,
            "final_residual": last["final_residual"], "converged": last["converged"],
            "chi2_over_ndof": last["chi2_over_ndof"],
            "iter_ms_full_band": {"p50": float(np.percentile(it_ms, 50)) if it_ms.size else None,
@@ -470,7 +492,8 @@ def run_ours(args):
         sh = torch.empty(plan.npix, dtype=torch.float64, pin_memory=True).numpy()
         wf.wf_set_options(plan, profile=0, maxiter=args.maxiter, schedule=sched,
                           refine_sweeps=args.refine_sweeps if args.precision != "fp64" else 0,
-                          mixed_tol_factor=args.mixed_tol_factor)
+                          mixed_tol_factor=args.mixed_tol_factor,
+                          mixed_correction=args.mixed_correction if args.precision != "fp64" else 0.0)
         wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)  # warm
         t0 = time.perf_counter()
         rep = wf.wf_solve_host(plan, dh, nvh, mh, clh, args.tol, sh)

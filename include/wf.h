@@ -125,6 +125,18 @@ typedef struct {
                            thread) in place of the default or autotuned one; 0 keeps it */
     int tile_ana;       /* mixed plans: > 0 sets the FP32 Legendre analysis tile (2, 4 or 8 ring pairs per
                            lane); 0 keeps it */
+    double mixed_correction; /* mixed temperature plans, single solves (wf_solve, wf_fluct, their host forms
+                                and requests of the request loop; not wf_solve_batch): > 0 switches the FP32 iteration to correction form once, at lambda = 1
+                                on the full band, when its residual is below tol x mixed_correction.  The
+                                messenger iteration is affine, a_{k+1} = B a_k + c (Eqs. 3-4).  One FP64
+                                iteration from the current iterate x0 (double-float Legendre transforms, as
+                                in the correction sweeps) gives d0 = B x0 + c - x0; the FP32 kernels then
+                                iterate on delta = a - x0, delta <- d0 + B delta (the same kernels with the
+                                source set to zero), so their rounding scales with |delta| instead of |a|,
+                                and the residual they report is the FP64 operator's to that rounding.  The
+                                FP64 iteration counts as one iteration of the trace (chi^2 NaN from there on:
+                                the kernels no longer see the iterate itself).  Allocates three a_lm arrays
+                                and one FP32 map on first use.  0 (default): off */
 } wf_options;
 
 /* Kernel families reported in wf_info (HEALPix path; the flat path is one

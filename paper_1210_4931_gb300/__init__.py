@@ -42,7 +42,8 @@ class wf_options(ctypes.Structure):
                 ("mixed_kappa", ctypes.c_double), ("mixed_lc", ctypes.c_int), ("schedule", ctypes.c_int),
                 ("m_sigma", ctypes.c_double), ("stall_tol", ctypes.c_double),
                 ("mixed_table_bytes", ctypes.c_longlong), ("fp64_emulation", ctypes.c_int),
-                ("mixed_tol_factor", ctypes.c_double), ("tile_syn", ctypes.c_int), ("tile_ana", ctypes.c_int)]
+                ("mixed_tol_factor", ctypes.c_double), ("tile_syn", ctypes.c_int), ("tile_ana", ctypes.c_int),
+                ("mixed_correction", ctypes.c_double)]
 
 
 class wf_info(ctypes.Structure):

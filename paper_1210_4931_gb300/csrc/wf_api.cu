@@ -301,6 +301,16 @@ __global__ void k_map_to_T(long long n, const double *__restrict__ in, T *__rest
         out[i] = (T)in[i];
 }
 
+// out = x + s y over n complex coefficients (the correction form of the mixed iteration);
+// out may be x or y
+__global__ void k_alm_axpy(long long n, const double2 *x, const double2 *y, double s, double2 *out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 a = x[i], b = y[i];
+        out[i] = make_double2(a.x + s * b.x, a.y + s * b.y);
+    }
+}
+
 
 // Template marginalisation (Sect. 3, Eq. 12): d = d_raw - V (V^T V)^-1 V^T d_raw,
 // V = masked monopole and dipole templates (1, sin th cos ph, sin th sin ph, cos th).
@@ -698,6 +708,7 @@ struct HpRun {
     wf_status result = WF_OK;
     double lam = 1.0, chi2_bound = NAN;  // the current iteration
     int L = 0;
+    bool corr = false, corr_pending = false;  // correction form (mixed_correction): on / due at the next launch
     Prof pr;
 };
 
@@ -830,6 +841,103 @@ bool hp_pick(HpRun &R)
     return true;
 }
 
+wf_status alm_axpy(wf_plan p, const double2 *x, const double2 *y, double s, double2 *out)
+{
+    k_alm_axpy<<<grid_for(p->nalm, p->nsm), 256, 0, p->stream>>>(p->nalm, x, y, s, out);
+    WF_COUNT_LAUNCH(p);
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+}
+
+wf_status hp_launch(HpRun &R);
+bool hp_absorb(HpRun &R);
+
+// The switch to the correction form of the mixed iteration (wf_options.mixed_correction).
+// The messenger iteration (Eqs. 3-4) is affine, G(a) = B a + c.  One FP64 iteration from the
+// current iterate x0, on the FP64 sub-plan of the correction sweeps, gives a1 = G(x0); the
+// plan's a then holds delta = a - x0, starting at d0 = a1 - x0, and the FP32 kernels apply
+// G(x0 + delta) - x0 = d0 + B delta (hp_launch).  The FP64 iteration is one iteration of the
+// trace (synchronous; its residual is the FP64 operator's at x0).
+wf_status hp_enter_correction(HpRun &R)
+{
+    wf_plan p = R.p;
+    const wf_options &o = R.o;
+    const int lmax = R.lmax;
+    const size_t abytes = (size_t)p->nalm * sizeof(double2);
+    wf_status st;
+    if (!p->ws.cx0) {
+        if ((st = plan_alloc(p, (void **)&p->ws.cx0, abytes)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.cd0, abytes)) != WF_OK) return st;
+        if ((st = plan_alloc(p, (void **)&p->ws.caold, abytes)) != WF_OK) return st;
+        if ((st = plan_alloc(p, &p->ws.r0, (size_t)p->npix * sizeof(float))) != WF_OK) return st;
+        WF_CUDA(cudaMemsetAsync(p->ws.r0, 0, (size_t)p->npix * sizeof(float), p->stream));
+    }
+    if (!p->sub) {
+        wf_plan sub = nullptr;
+        if ((st = wf_plan_create(&p->g, lmax, WF_PREC_FP64, (void *)p->stream, &sub)) != WF_OK) return st;
+        p->sub = sub;
+    }
+    wf_plan sub = p->sub;
+    sub->df_legendre = o.fp64_emulation >= 0;
+    sub->stream = p->stream;
+    sub->opt = p->opt;
+    sub->opt.profile = o.profile;
+    sub->opt.refine_sweeps = 0;
+    sub->opt.schedule = 0;
+    sub->opt.mixed_correction = 0;
+    sub->replay_lambda.assign(1, 1.0);
+    sub->replay_L.assign(1, lmax);
+    WF_CUDA(cudaMemcpyAsync(p->ws.cx0, p->ws.a, abytes, cudaMemcpyDeviceToDevice, p->stream));
+    double t_lam = NAN, t_chi2 = NAN, t_res = NAN, t_ms = NAN;
+    int t_L = 0;
+    wf_info si{};
+    si.lambda_trace = &t_lam;
+    si.L_trace = &t_L;
+    si.chi2_trace = &t_chi2;
+    si.resid_trace = &t_res;
+    si.iter_ms_trace = &t_ms;
+    si.trace_cap = 1;
+    HpRun S;
+    S.p = sub;
+    S.d = R.d;
+    S.nv = R.nv;
+    S.mask = R.mask;
+    S.C_ell = R.C_ell;
+    S.tol = R.tol;
+    S.fluct = R.fluct;
+    S.g1 = R.g1;
+    S.g2 = R.g2;
+    S.s_out = R.s_out;  // scratch of the fluctuation source; written again at the end
+    S.info = &si;
+    S.a_init = p->ws.cx0;
+    sub->bnorm_given = R.bnorm;
+    st = hp_begin(S);
+    if (st == WF_OK) {
+        if (!hp_pick(S)) {
+            st = set_error(WF_ECUDA, "correction form: the FP64 step did not run");
+        } else if ((st = hp_launch(S)) == WF_OK) {
+            WF_CUDA(cudaStreamSynchronize(p->stream));
+            hp_absorb(S);
+        }
+    }
+    sub->bnorm_given = 0;
+    S.pr.finish();
+    if (st != WF_OK) return st;
+    // delta_0 = d0 = a1 - x0 (a1 is the sub-plan's iterate after the absorb)
+    if ((st = alm_axpy(p, sub->ws.a, p->ws.cx0, -1.0, p->ws.cd0)) != WF_OK) return st;
+    WF_CUDA(cudaMemcpyAsync(p->ws.a, p->ws.cd0, abytes, cudaMemcpyDeviceToDevice, p->stream));
+    for (int f = 0; f < WF_NK; ++f) {
+        R.pr.ms[f] += si.kernel_ms[f];
+        R.pr.cnt[f] += si.kernel_launches[f];
+    }
+    R.pr.launches += si.launches;
+    record(R.info, R.k, 1.0, lmax, NAN, S.last_resid, t_ms);
+    ++R.k;
+    R.last_resid = S.last_resid;
+    R.corr = true;
+    return WF_OK;
+}
+
 // one messenger iteration (Eqs. 3-4) and its sums, enqueued on the plan's
 // stream; the chi^2-bound schedule synchronises inside to find lambda
 wf_status hp_launch(HpRun &R)
@@ -840,6 +948,10 @@ wf_status hp_launch(HpRun &R)
     const wf_options &o = R.o;
     const double tau = R.tau;
     wf_status st;
+    if (R.corr_pending) {
+        R.corr_pending = false;
+        if ((st = hp_enter_correction(R)) != WF_OK) return st;
+    }
     pr.iter_begin();
     R.chi2_bound = NAN;
     if (R.rigorous) {
@@ -891,7 +1003,11 @@ wf_status hp_launch(HpRun &R)
         // one ring kernel: fold, inverse DFT, Eq. 3 and the forward DFT of t, which never
         // leaves shared memory (its time is reported under the ring synthesis)
         pr.begin(WF_K_RING_SYN);
-        if ((st = hp_ring_synthesis_analysis(p, R.L, R.lam, tau)) != WF_OK) return st;
+        void *r_src = p->ws.r;
+        if (R.corr) p->ws.r = p->ws.r0;  // correction form: B delta, the iteration without its source
+        st = hp_ring_synthesis_analysis(p, R.L, R.lam, tau);
+        p->ws.r = r_src;
+        if (st != WF_OK) return st;
         pr.end();
     }
     const int L = R.L;
@@ -906,9 +1022,17 @@ wf_status hp_launch(HpRun &R)
     ba.tauh = R.tau_h;
     ba.S = R.C_ell;
     ba.want_resid = full ? 1 : 0;
+    const double2 *a_old = p->ws.a;
+    if (R.corr) {
+        // the epilogue's residual compares its output B delta_k with delta_k - d0, i.e.
+        // delta_{k+1} = d0 + B delta_k with delta_k; d0 is added to the output below
+        if ((st = alm_axpy(p, p->ws.a, p->ws.cd0, -1.0, p->ws.caold)) != WF_OK) return st;
+        a_old = p->ws.caold;
+    }
     pr.begin(WF_K_LEG_ANA);
-    if ((st = hp_legendre_analysis(p, L, LEG_BLEND, ba, p->ws.a, p->ws.a_new)) != WF_OK) return st;
+    if ((st = hp_legendre_analysis(p, L, LEG_BLEND, ba, a_old, p->ws.a_new)) != WF_OK) return st;
     pr.end();
+    if (R.corr && (st = alm_axpy(p, p->ws.a_new, p->ws.cd0, 1.0, p->ws.a_new)) != WF_OK) return st;
     SumSpec sp{};
     sp.in[0] = p->ws.part_pix;
     sp.n[0] = p->npairs;
@@ -932,7 +1056,8 @@ bool hp_absorb(HpRun &R)
     const double ims = R.pr.iter_end();
     R.pr.collect();
     const bool full = (R.lam == 1.0 && R.L == R.lmax);
-    const double chi2 = R.rigorous ? R.chi2_bound : p->ws.h_scal[0] + p->ws.h_scal[1];
+    // (in correction form the kernels see delta, not the iterate: no chi^2)
+    const double chi2 = R.corr ? NAN : R.rigorous ? R.chi2_bound : p->ws.h_scal[0] + p->ws.h_scal[1];
     const double resid = full ? std::sqrt(p->ws.h_scal[2]) / R.bnorm : NAN;
     R.h_cur = p->ws.h_scal[3];  // x_{k+1}^T S^-1 x_{k+1} and x^T S^-2 x for the next lambda
     R.q_cur = p->ws.h_scal[4];
@@ -950,7 +1075,7 @@ bool hp_absorb(HpRun &R)
         }
         R.best_resid = std::min(R.best_resid, resid);
     }
-    if (!std::isfinite(chi2)) {
+    if (!R.corr && !std::isfinite(chi2)) {
         R.result = WF_EDIVERGE;
         R.chi2_bad = true;
         return false;
@@ -975,6 +1100,9 @@ bool hp_absorb(HpRun &R)
             R.converged = true;
             return false;
         }
+        if (full && !R.corr && R.o.mixed_correction > 0.0 && p->prec != WF_PREC_FP64 && !p->pol && !R.copy_back &&
+            resid < R.tol * R.o.mixed_correction)
+            R.corr_pending = true;
     } else {
         ++R.level_iters;
         const bool plateau = R.have_prev && std::fabs(chi2 - R.prev_chi2) < R.o.eta * R.sigma;
@@ -1004,6 +1132,11 @@ wf_status hp_end(HpRun &R)
     const int lmax = R.lmax;
     Prof &pr = R.pr;
     wf_status st;
+    if (R.corr) {
+        // correction form: a = x0 + delta
+        if ((st = alm_axpy(p, p->ws.cx0, p->ws.a, 1.0, p->ws.a)) != WF_OK) return st;
+        R.corr = false;
+    }
     // Mixed precision, row a9: FP64 correction sweeps.  Up to refine_sweeps
     // messenger iterations at lambda = 1 on the full band run in FP64 from the
     // mixed-precision iterate (an FP64 sub-plan of the same geometry); their

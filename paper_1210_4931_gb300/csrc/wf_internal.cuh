@@ -115,6 +115,10 @@ struct Workspace {
     int *flag = nullptr;          // device flags (invalid input)
     int *tc_err = nullptr;        // tensor-core kernels: set when a bounded wait gave up
     double *redu = nullptr;       // reduction scratch
+    // mixed plans in correction form (wf_options.mixed_correction), allocated on first use:
+    // the iterate x0 at the switch, d0 = G(x0) - x0, delta - d0, and a zero FP32 source map
+    double2 *cx0 = nullptr, *cd0 = nullptr, *caold = nullptr;
+    void *r0 = nullptr;
 };
 
 struct HpTables {

@@ -60,8 +60,14 @@ long long request_bytes(const wf_request &r)
     g.ncomp = ncomp_of(r);
     long long b = wf_plan_estimate_bytes(&g, r.lmax, r.precision, 1);
     if (b < 0) return b;
-    if (r.precision != WF_PREC_FP64 && r.opt.refine_sweeps > 0)  // FP64 sub-plan of the correction sweeps
+    // FP64 sub-plan of the correction sweeps and of the correction form's FP64 step
+    if (r.precision != WF_PREC_FP64 && (r.opt.refine_sweeps > 0 || r.opt.mixed_correction > 0.0))
         b += wf_plan_estimate_bytes(&g, r.lmax, WF_PREC_FP64, 0);
+    // the correction form's buffers: x0, d0 and delta - d0 (a_lm, FP64) and a zero FP32 source map
+    if (r.precision != WF_PREC_FP64 && r.opt.mixed_correction > 0.0 && g.ncomp == 1) {
+        const long long nalm = (long long)(r.lmax + 1) * (r.lmax + 2) / 2;
+        b += 3 * nalm * 16 + 12LL * r.nside * r.nside * 4;
+    }
     return b;
 }
 
