@@ -312,6 +312,11 @@ wf_status wf_fluct_host(wf_plan p, const double *noise_var, const uint8_t *mask,
 
 const char *wf_strerror(wf_status s);
 const char *wf_last_error(void);
+/* Size in bytes of one of this header's structs as the library was built, by its name
+ * ("wf_geometry", "wf_options", "wf_info", "wf_batch_item", "wf_request", "wf_result",
+ * "wf_server_stats"); 0 for any other name or a null pointer.  A binding that mirrors the
+ * structs compares the sizes with its own layouts before it passes one.  Host only. */
+long long wf_abi_sizeof(const char *name);
 
 /* Measurement utility; the paper has no counterpart.  Times an FP32 FMA loop
  * (independent chains, two 512-thread CTAs per SM; packed != 0 issues packed

@@ -94,12 +94,14 @@ class wf_server_stats(ctypes.Structure):
 
 
 _lib = None
+ABI_STRUCTS = (wf_geometry, wf_options, wf_info, wf_batch_item, wf_request, wf_result, wf_server_stats)
+
 EXPORTS = ["wf_plan_create", "wf_plan_destroy", "wf_set_options", "wf_set_schedule", "wf_set_start", "wf_solve", "wf_solve_host",
            "wf_fluct", "wf_alm2map", "wf_map2alm_adjoint", "wf_npix", "wf_nalm", "wf_plan_device_bytes",
            "wf_strerror", "wf_last_error", "wf_flat_solve_noalloc", "wf_remove_templates", "wf_fluct_host",
            "wf_plan_estimate_bytes", "wf_plan_set_stream", "wf_server_create", "wf_server_submit", "wf_server_poll",
            "wf_server_wait", "wf_server_get_stats", "wf_server_destroy", "wf_solve_batch", "wf_plan_autotune",
-           "wf_plan_tiles", "wf_probe_fp32_fma", "wf_combine_datasets"]
+           "wf_plan_tiles", "wf_probe_fp32_fma", "wf_combine_datasets", "wf_abi_sizeof"]
 
 
 def load(path: str = LIB_PATH):
@@ -165,6 +167,15 @@ def load(path: str = LIB_PATH):
     L.wf_strerror.restype = ctypes.c_char_p
     L.wf_last_error.argtypes = []
     L.wf_last_error.restype = ctypes.c_char_p
+    L.wf_abi_sizeof.argtypes = [ctypes.c_char_p]
+    L.wf_abi_sizeof.restype = ctypes.c_longlong
+    # the structs above mirror include/wf.h field by field: a library built from another
+    # header would read them wrongly, so their sizes must agree before any call passes one
+    for st in ABI_STRUCTS:
+        n = L.wf_abi_sizeof(st.__name__.encode())
+        if n != ctypes.sizeof(st):
+            raise ImportError("%s: %d bytes in libwf.so, %d in this binding (rebuild the library)"
+                              % (st.__name__, n, ctypes.sizeof(st)))
     for f in ("wf_plan_create", "wf_set_options", "wf_set_schedule", "wf_solve", "wf_solve_host", "wf_fluct",
               "wf_alm2map", "wf_map2alm_adjoint"):
         getattr(L, f).restype = ctypes.c_int

@@ -1959,6 +1959,21 @@ const char *wf_strerror(wf_status s)
 
 const char *wf_last_error(void) { return wf::g_err; }
 
+long long wf_abi_sizeof(const char *name)
+{
+    if (!name) return 0;
+    const struct {
+        const char *name;
+        size_t size;
+    } sizes[] = {{"wf_geometry", sizeof(wf_geometry)},     {"wf_options", sizeof(wf_options)},
+                 {"wf_info", sizeof(wf_info)},             {"wf_batch_item", sizeof(wf_batch_item)},
+                 {"wf_request", sizeof(wf_request)},       {"wf_result", sizeof(wf_result)},
+                 {"wf_server_stats", sizeof(wf_server_stats)}};
+    for (const auto &e : sizes)
+        if (std::strcmp(name, e.name) == 0) return (long long)e.size;
+    return 0;
+}
+
 wf_status wf_plan_create(const wf_geometry *g, int lmax, wf_precision prec, void *cuda_stream, wf_plan *out)
 {
     if (!g || !out) return set_error(WF_EINVAL, "null argument");

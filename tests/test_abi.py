@@ -58,3 +58,20 @@ def test_solve_records_as_json_lines(tmp_path):
     assert len(lines) == 2 and lines[1]["iters"] == 4 and lines[1]["err_vs_oracle"] == 3e-12
     assert lines[0]["iter_ms_p50"] == 2.0 and lines[0]["lambda_trace"] == [4.0, 1.0, 1.0]
     assert lines[0]["L_trace"] == [10, 32, 32] and lines[0]["chi2_over_ndof"] == 0.998
+
+
+def test_binding_structs_match_the_library():
+    """Every struct the binding mirrors has the size the library was built with
+    (load() refuses a library whose layouts differ); unknown names give 0."""
+    import ctypes
+
+    import paper_1210_4931_gb300 as wf
+
+    lib = wf.load()
+    for st in wf.ABI_STRUCTS:
+        assert lib.wf_abi_sizeof(st.__name__.encode()) == ctypes.sizeof(st), st.__name__
+    assert lib.wf_abi_sizeof(b"wf_plan") == 0 and lib.wf_abi_sizeof(None) == 0
+    # every struct the header defines is covered
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "wf.h")).read(), flags=re.S)
+    defined = set(re.findall(r"typedef struct\s*\{[^{}]*\}\s*(wf_[a-z_]+)\s*;", src))
+    assert defined == {st.__name__ for st in wf.ABI_STRUCTS}
