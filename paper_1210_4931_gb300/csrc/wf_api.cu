@@ -865,12 +865,15 @@ wf_status hp_enter_correction(HpRun &R)
     const int lmax = R.lmax;
     const size_t abytes = (size_t)p->nalm * sizeof(double2);
     wf_status st;
-    if (!p->ws.cx0) {
-        if ((st = plan_alloc(p, (void **)&p->ws.cx0, abytes)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.cd0, abytes)) != WF_OK) return st;
-        if ((st = plan_alloc(p, (void **)&p->ws.caold, abytes)) != WF_OK) return st;
-        if ((st = plan_alloc(p, &p->ws.r0, (size_t)p->npix * sizeof(float))) != WF_OK) return st;
-        WF_CUDA(cudaMemsetAsync(p->ws.r0, 0, (size_t)p->npix * sizeof(float), p->stream));
+    // each buffer on its own, so that a failed allocation leaves no half-set state behind
+    if (!p->ws.cx0 && (st = plan_alloc(p, (void **)&p->ws.cx0, abytes)) != WF_OK) return st;
+    if (!p->ws.cd0 && (st = plan_alloc(p, (void **)&p->ws.cd0, abytes)) != WF_OK) return st;
+    if (!p->ws.caold && (st = plan_alloc(p, (void **)&p->ws.caold, abytes)) != WF_OK) return st;
+    if (!p->ws.r0) {
+        void *z = nullptr;
+        if ((st = plan_alloc(p, &z, (size_t)p->npix * sizeof(float))) != WF_OK) return st;
+        WF_CUDA(cudaMemsetAsync(z, 0, (size_t)p->npix * sizeof(float), p->stream));
+        p->ws.r0 = z;  // set once it is zero
     }
     if (!p->sub) {
         wf_plan sub = nullptr;
