@@ -26,9 +26,7 @@ def recipe(nside):
                 noise_range=1e4)
 
 
-@pytest.fixture(scope="module", params=[8, 16])
-def system(oracle, request):
-    NSIDE = request.param
+def _make_system(oracle, NSIDE):
     LMAX = 2 * NSIDE
     P = gen.healpix_problem(NSIDE, LMAX, gen.seed_for(3, 5), **recipe(NSIDE))
     basis = oracle.HealpixBasis(NSIDE, LMAX)
@@ -61,6 +59,38 @@ def system(oracle, request):
         return wnorm(basis.w, (inv_S + 1.0 / tau_h) * (a - G(a)), active) / bnorm
 
     return dict(G=G, M=M, F=F, Finv=Finv, c=c, dot=dot, resid=resid, active=active, shape=S.shape, nside=NSIDE)
+
+
+@pytest.fixture(scope="module", params=[8, 16])
+def system(oracle, request):
+    return _make_system(oracle, request.param)
+
+
+@pytest.fixture(scope="module")
+def system8(oracle):
+    return _make_system(oracle, 8)
+
+
+def _pcg(M, F, dot, rhs, steps, stop=None):
+    """Conjugate gradients on M y = rhs preconditioned by F, from y = 0; stop(y, r)
+    ends them early.  Returns y and the steps taken."""
+    y = np.zeros_like(rhs)
+    rv = rhs.copy()
+    z = F * rv
+    p = z.copy()
+    rz = dot(rv, z)
+    for k in range(1, steps + 1):
+        Ap = M(p)
+        alpha = rz / dot(p, Ap)
+        y = y + alpha * p
+        rv = rv - alpha * Ap
+        z = F * rv
+        rz_new = dot(rv, z)
+        if stop is not None and stop(y, rz_new):
+            return y, k
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return y, steps
 
 
 def _random_alm(rng, shape, active):
@@ -124,3 +154,42 @@ def test_conjugate_gradients_on_the_same_system_cut_the_tail(system):
     for _ in range(5):
         y = G(y)
     assert np.abs(y - x).max() <= 1e-5 * np.abs(x).max()
+
+
+def test_cg_with_a_rounded_operator_needs_fp64_residuals(system8):
+    """With each application of B perturbed by 1e-6 of its operand's RMS (the
+    FP32 kernels' rounding, modelled), CG stalls far above 1e-6; restarted on
+    the residual of the FP64 operator (iterative refinement: the correction
+    form's idea applied to CG), it goes on to 1e-8 in a few restarts."""
+    S8 = system8
+    G, M, F, Finv, c, dot, resid, act = (S8[k] for k in ("G", "M", "F", "Finv", "c", "dot", "resid", "active"))
+    G0 = c
+    rng = np.random.default_rng(12104931)
+
+    def M_rounded(v):
+        Bv = G(v) - G0
+        rms = np.sqrt(np.mean(np.abs(v[act]) ** 2))
+        Bv = Bv + 1e-6 * rms * (rng.standard_normal(v.shape) + 1j * rng.standard_normal(v.shape)) * act
+        return Finv * (v - Bv)
+
+    b = Finv * c
+    best = [1.0]
+
+    def track(y, _):
+        best[0] = min(best[0], resid(y))
+        return False
+
+    _pcg(M_rounded, F, dot, b, 400, stop=track)
+    print("CG with the rounded operator: best residual %.2e in 400 steps" % best[0])
+    assert best[0] > 1e-5
+    x = np.zeros_like(b)
+    restarts, total = 0, 0
+    while resid(x) > 1e-8 and restarts < 6:
+        restarts += 1
+        r64 = b - M(x)  # the residual of the FP64 operator
+        n0 = math.sqrt(dot(r64, F * r64))
+        y, k = _pcg(M_rounded, F, dot, r64, 1000, stop=lambda y, rz: math.sqrt(rz) < 1e-3 * n0)
+        x = x + y
+        total += k
+    print("refined CG: %d restarts, %d steps, residual %.2e" % (restarts, total, resid(x)))
+    assert resid(x) <= 1e-8 and restarts <= 4
